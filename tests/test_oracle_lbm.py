@@ -1,0 +1,184 @@
+"""Pins of the lattice Boltzmann oracle (oracle/lbm_oracle.c) against what the paper
+and the mathematics fix, independent of the oracle's own code."""
+import numpy as np
+import pytest
+
+from oracle import analytic as A
+from oracle import geometry as G
+from oracle import lbm, mst
+
+import lattice_theory as LT
+
+RNG = np.random.default_rng(1234)
+
+
+# --- equilibria (Eq. equilibrium distribution functions) -----------------------
+
+def test_equilibrium_zeroth_moments():
+    """sum_i e_i^eq = eps_r E and sum_i h_i^eq = mu_r H (mu_r = 1): the moments the
+    fields are reconstructed from are conserved by the collision."""
+    for _ in range(5):
+        E, H, eps = RNG.normal(size=3), RNG.normal(size=3), RNG.uniform(1, 12)
+        eeq, heq = lbm.equilibria(eps, E, H)
+        assert np.allclose(eeq.sum(0), eps * E, atol=1e-14)
+        assert np.allclose(heq.sum(0), H, atol=1e-14)
+
+
+def test_equilibrium_first_moments_give_maxwell():
+    """sum_i c_i,a e_i,k^eq = -(1/3) eps_kac H_c and sum_i c_i,a h_i,k^eq = +(1/3) eps_kac E_c:
+    the Chapman-Enskog flux of the scheme is dD/dt = (1/3) curl H, dB/dt = -(1/3) curl E
+    (Maxwell's equations with light speed 1/3 cell per step)."""
+    c = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], float)
+    lc = np.zeros((3, 3, 3))
+    lc[0, 1, 2] = lc[1, 2, 0] = lc[2, 0, 1] = 1
+    lc[0, 2, 1] = lc[2, 1, 0] = lc[1, 0, 2] = -1
+    for _ in range(5):
+        E, H = RNG.normal(size=3), RNG.normal(size=3)
+        eeq, heq = lbm.equilibria(3.0, E, H)
+        fe = np.einsum("ia,ik->ak", c, eeq)
+        fh = np.einsum("ia,ik->ak", c, heq)
+        assert np.allclose(fe, -np.einsum("kac,c->ak", lc, H) / 3.0, atol=1e-14)
+        assert np.allclose(fh, np.einsum("kac,c->ak", lc, E) / 3.0, atol=1e-14)
+
+
+# --- exact discrete plane wave ------------------------------------------------------
+
+@pytest.mark.parametrize("kind", [lbm.SRC_OPEN, lbm.SRC_HARD])
+@pytest.mark.parametrize("period", [24, 60])
+def test_exact_discrete_plane_wave(kind, period):
+    """The exact right-going plane wave of the lattice (dispersion relation derived
+    by hand) stays exact: update rule, streaming, open edges and source agree."""
+    nx, ny, t0 = 70, 5, 11
+    sim = lbm.Simulation(np.ones((ny, nx)), period=period, source_kind=kind, nthreads=2)
+    sim.f[:] = LT.vacuum_plane_wave_state(period, nx, ny, t0)
+    sim.t = t0
+    sim.advance(3 * period + 5)
+    assert np.max(np.abs(sim.f - LT.vacuum_plane_wave_state(period, nx, ny, sim.t))) < 1e-12
+
+
+def test_plane_wave_continuum_limit():
+    """Long waves travel at 1/3 cell per step (period T = 3 lambda), with second-order
+    dispersion error."""
+    errs = []
+    for T in (60, 120, 240):
+        k = np.angle(LT.vacuum_w(T))
+        errs.append(abs(k / (3 * 2 * np.pi / T) - 1))
+    assert errs[0] < 2e-3 and errs[1] / errs[2] > 3.5
+
+
+def test_injected_wave_from_rest_and_medium_dispersion():
+    """From a zero state the ramped source drives a dielectric slab (eps = 4) in
+    vacuum.  Inside the slab the steady field is exactly the sum of the two
+    counter-propagating modes of the medium's discrete dispersion relation; their
+    wavenumber is close to the continuum 3 omega sqrt(eps) (phase speed
+    1/(3 sqrt(eps))) and the ratio H_y / E_z of each mode is the discrete impedance
+    (b - a) / (1 - a - b - c_h), close to -+sqrt(eps)."""
+    T, nx, ny, eps_r = 96, 200, 4, 4.0
+    eps = np.ones((ny, nx))
+    eps[:, 60:120] = eps_r          # short slab: Fabry-Perot transients (|r|^2 = 1/9
+    sim = lbm.Simulation(eps, period=T, ramp_steps=T, nthreads=2)   # per round trip) decay
+    sim.advance(70 * T)
+    sim.advance(T, accumulate=True)
+    Ez, Hx, Hy = sim.phasors()
+    assert np.max(np.abs(Hx)) < 1e-10
+    k = LT.medium_k(T, eps_r).real
+    assert abs(k / (3 * 2 * np.pi / T * np.sqrt(eps_r)) - 1) < 1e-2
+    xs = np.arange(70, 110)
+    basis = np.stack([np.exp(1j * k * xs), np.exp(-1j * k * xs)], axis=1)
+    ce, *_ = np.linalg.lstsq(basis, Ez[1, xs], rcond=None)
+    ch, *_ = np.linalg.lstsq(basis, Hy[1, xs], rcond=None)
+    assert np.abs(basis @ ce - Ez[1, xs]).max() < 1e-6 * np.abs(Ez[1, xs]).max()
+    z = np.exp(-1j * 2 * np.pi / T)
+    for j, w in enumerate((np.exp(1j * k), np.exp(-1j * k))):
+        a = 1.0 / (3.0 * (w * z + 1.0))
+        b = 1.0 / (3.0 * (z / w + 1.0))
+        c_h = (4.0 / 3.0) / (z + 1.0)
+        Z = (b - a) / (1.0 - a - b - c_h)
+        assert abs(ch[j] / ce[j] - Z) < 1e-6 * abs(Z)
+        assert abs(Z - (-1) ** (j + 1) * np.sqrt(eps_r)) < 0.02 * np.sqrt(eps_r)
+
+
+# --- geometry (staircase Janus disc, Sec. II) -----------------------------------------
+
+def test_janus_rasterisation_brute_force_and_orientation():
+    nx, ny, a = 23, 18, 6.3
+    for phi0 in (0.0, 0.7, np.pi / 2, 2.5, 3 * np.pi / 2, 5.9):
+        reg = G.janus_regions(nx, ny, a, phi0)
+        cx, cy = (nx - 1) / 2, (ny - 1) / 2
+        for y in range(ny):
+            for x in range(nx):
+                dx, dy = x - cx, y - cy
+                if dx * dx + dy * dy > a * a:
+                    assert reg[y, x] == 0
+                else:
+                    s = -dx * np.sin(phi0) - dy * np.cos(phi0)
+                    assert reg[y, x] == (1 if s > 1e-9 else 2)
+    # phi0 = pi/2: region II (dielectric) faces the source at x = 0 (Sec. IV.A)
+    reg = G.janus_regions(64, 64, 20, np.pi / 2)
+    xs = np.nonzero(reg == 1)[1]
+    assert xs.max() < 32
+    # phi0 = 3 pi/2: region III faces the source; phi0 = 0: region III along +y (Appendix A)
+    reg = G.janus_regions(64, 64, 20, 1.5 * np.pi)
+    assert np.nonzero(reg == 2)[1].max() < 32
+    reg = G.janus_regions(64, 64, 20, 0.0)
+    assert np.nonzero(reg == 2)[0].min() >= 32
+    # halves of equal area
+    reg = G.janus_regions(400, 400, 150, 0.37)
+    n2, n3 = (reg == 1).sum(), (reg == 2).sum()
+    assert abs(n2 - n3) < 0.01 * (n2 + n3)
+    assert abs((n2 + n3) / (np.pi * 150 ** 2) - 1) < 0.005
+
+
+# --- physics of the whole step (Sec. III-IV) ------------------------------------------
+
+def _run(nx, ny, a, phi0, eps1, eps2, pec2, T, periods, R, nthreads=8):
+    eps, pec, _ = G.janus_material(nx, ny, a, phi0, eps1, eps2, pec2)
+    sim = lbm.Simulation(eps, pec, period=T, ramp_steps=T, nthreads=nthreads)
+    sim.advance((periods - 1) * T)
+    sim.advance(T, accumulate=True)
+    cx, cy = G.default_center(nx, ny)
+    Ez, Hx, Hy = sim.phasors()
+    F = mst.force_torque(Ez, Hx, Hy, cx, cy, R, mst.default_n_points(R), a)
+    return F, (Ez, Hx, Hy), (cx, cy)
+
+
+def test_homogeneous_cylinder_matches_bessel_series():
+    """256^2 lattice, eps_r = 2.25, a = 20, lambda = 40 (T = 120), 20 periods, contour
+    radius 40: drag within 1 % of the Bessel series at the lattice wavenumber (Sec. III
+    quotes 5 % for lambda / dx >= 10); lift and torque vanish by symmetry."""
+    T, a = 120, 20.0
+    F, (Ez, Hx, Hy), (cx, cy) = _run(256, 256, a, 0.0, 2.25, 2.25, False, T, 20, 40)
+    k = np.angle(LT.vacuum_w(T))
+    B, D = A.homogeneous_BD(k, a, 2.25, np.pi)
+    exact = A.forces_quadrature(B, D, k, a, np.pi)
+    assert abs(F[0] - exact[0]) < 0.01 * exact[0]
+    assert abs(F[1]) < 1e-12 and abs(F[2]) < 1e-12
+    # lossless: the net Poynting flux through the contour is at the level of the
+    # open-boundary reflections (Sec. III: <= 1e-3), relative to the incident power
+    # crossing the contour's width (intensity 1/2 x 2R)
+    P = mst.poynting_net(Ez, Hx, Hy, cx, cy, 40, mst.default_n_points(40))
+    assert abs(P) < 1e-3 * 0.5 * 2 * 40
+
+
+@pytest.mark.parametrize("eps1,phi0", [(2.0, 7 * np.pi / 36), (5.0, 0.611), (2.0, np.pi / 2)])
+def test_md_janus_matches_analytic(eps1, phi0):
+    """Metallo-dielectric Janus cylinder at the paper's force resolution (a/dx = 40,
+    L/a = 4, a/lambda = 1): within 5 % of drag scale of the analytic solution."""
+    T, a = 120, 40.0
+    F, _, _ = _run(160, 160, a, phi0, eps1, 1.0, True, T, 20, 60)
+    k = np.angle(LT.vacuum_w(T))
+    B, D, _ = A.md_janus_BD_galerkin(k, a, eps1, phi0, n_basis=320)
+    exact = A.forces_quadrature(B, D, k, a, phi0, r=1.5 * a)
+    assert np.max(np.abs(F - exact)) < 0.05 * abs(exact[0])
+
+
+def test_mirror_symmetry_is_exact():
+    """phi0 <-> pi - phi0 is the mirror y -> -y of the lattice: drag equal, lift and
+    torque opposite (Sec. IV.A), to rounding."""
+    args = dict(nx=96, ny=96, a=16.0, eps1=3.0, eps2=7.0, pec2=False, T=48, periods=6, R=28)
+    F1, _, _ = _run(phi0=0.4, **args)
+    F2, _, _ = _run(phi0=np.pi - 0.4, **args)
+    scale = abs(F1[0])
+    assert abs(F1[0] - F2[0]) < 1e-12 * scale
+    assert abs(F1[1] + F2[1]) < 1e-12 * scale and abs(F1[2] + F2[2]) < 1e-12 * scale
+    assert abs(F1[1]) > 1e-3 and abs(F1[2]) > 1e-3
