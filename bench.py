@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark of the lattice Boltzmann Maxwell hot path on GB300.
+
+One benchmark step = the whole hot path over the metallo-dielectric Janus workload
+(512 x 512, a = 32, lambda = 32 (T = 96), theta in {0, 30, ..., 180} deg, eps_r1 ~ U[2, 10],
+30 periods each): for every instance re-rasterise the disc, reset the lattice, run
+29 periods of fused stream-collide steps, one period with Fourier accumulation, and
+the stress-tensor contour integral -> (F~x, F~y, M~z).  The metric is lattice
+updates per second (MLUPS) over all steps of all instances.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+Under torchrun each rank runs its own seeded copy of the workload (weak scaling, no
+collective on the data path) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & HBM GB/s (% of peak) per precision form; design-map cells/sec at <=1e-3 force err"
+WORKLOAD = "md_janus_512"
+BYTES_PER_LU = {"f64": 16 * 8 * 2 + 1, "f32": 16 * 4 * 2 + 1}
+STEP_KERNEL = {"f64": "k_step<double, false>", "f32": "k_step<float, false>"}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU-baseline sample")
+    return p.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for name in ("common.cuh", "step.cu"):
+        with open(os.path.join(ROOT, "paper_2509_22308_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(precision):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None
+    when the summary is missing or the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"k_step_{precision}_{WORKLOAD}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != kernel_source_sha():
+        return None
+    return float(m_b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), max=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["max"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+def instance_lus(inst):
+    return inst["nx"] * inst["ny"] * inst["periods"] * inst["period"]
+
+
+def cpu_baseline(inst, target_s):
+    """The oracle as it stands, on the host cores: a bounded sample of one instance."""
+    import numpy as np
+    from oracle import geometry as G
+    from oracle import lbm as OL
+    from oracle import mst
+    eps, pec, _ = G.janus_material(inst["nx"], inst["ny"], inst["a"], inst["phi0"], inst["eps1"],
+                                   inst["eps2"], inst["pec2"])
+    threads = os.cpu_count() or 1
+    sim = OL.Simulation(eps, pec, period=inst["period"], ramp_steps=inst["ramp"], nthreads=threads)
+    t0 = time.perf_counter()
+    sim.advance(8)
+    per_step = (time.perf_counter() - t0) / 8
+    T = inst["period"]
+    n_plain = max(0, int(target_s / per_step) - T)
+    t0 = time.perf_counter()
+    sim.advance(n_plain)
+    sim.advance(T, accumulate=True)
+    cx, cy = G.default_center(inst["nx"], inst["ny"])
+    mst.force_torque(*sim.phasors(), cx, cy, inst["R"], mst.default_n_points(inst["R"]), inst["a"])
+    el = time.perf_counter() - t0
+    steps = n_plain + T
+    return {"value": inst["nx"] * inst["ny"] * steps / el / 1e6, "unit": "MLUPS", "cores": threads,
+            "kind": "oracle",
+            "sample": (f"FP64 full-vector C oracle, {threads} OpenMP threads: one {inst['nx']}x{inst['ny']} "
+                       f"instance of {WORKLOAD}, {n_plain} steps + 1 accumulated period ({T} steps) + "
+                       f"contour integral, {el:.1f} s")}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle on the host cores (bounded sample per step)."""
+    if rank != 0:
+        return
+    from paper_2509_22308_gb300 import workloads as W
+    from oracle import lbm as OL
+    OL.build()
+    inst = W.md_janus_512(1)[0]
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(inst, budget)
+        if i >= args.warmup:
+            vals.append(cb)
+    value = statistics.median(v["value"] for v in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": 512, "ny": 512, "instances_sampled": 1},
+            "cpu_baseline": {"kind": "oracle", "cores": vals[0]["cores"], "sample": vals[0]["sample"],
+                             "value": value, "unit": "MLUPS"},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2509_22308_gb300 import build as B
+    B.build()
+    from paper_2509_22308_gb300 import lbm_em as L
+    from paper_2509_22308_gb300 import workloads as W
+
+    prec = args.precision
+    instances = W.md_janus_512(1 + rank)
+    stream = torch.cuda.Stream()
+    solvers = [L.solver_for_instance(inst, prec, stream) for inst in instances]
+    janus = [L.make_janus(i["a"], i["phi0"], i["eps1"], i["eps2"], i["pec2"]) for i in instances]
+    contours = [L.make_contour(i["R"], i["a"]) for i in instances]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    lus_per_step = sum(instance_lus(i) for i in instances)
+    launches_per_step = sum(2 + i["periods"] * i["period"] for i in instances)
+
+    def one_step(plain_events=None):
+        res = []
+        for s, inst, j, c in zip(solvers, instances, janus, contours):
+            s.set_janus(j)
+            s.reset()
+            n_plain = (inst["periods"] - 1) * inst["period"]
+            if plain_events is not None:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.step(n_plain)
+                e1.record(stream)
+                plain_events.append((e0, e1, n_plain, inst["nx"] * inst["ny"]))
+            else:
+                s.step(n_plain)
+            res.append(s.force_torque(c))
+        return np.array(res)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, plain = [], []
+    results = None
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        results = one_step(plain)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = lus_per_step * args.steps * world / (total_ms / 1e3) / 1e6
+
+    # roofline of the dominant kernel: the plain step, timed on its own stream
+    plain_ms = sum(a.elapsed_time(b) for a, b, _, _ in plain)
+    plain_launches = sum(n for _, _, n, _ in plain)
+    plain_bytes = sum(n * sites * BYTES_PER_LU[prec] for _, _, n, sites in plain)
+    avg_launch_us = plain_ms * 1e3 / plain_launches
+    achieved = plain_bytes / (plain_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = profiled_traffic(prec)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": STEP_KERNEL[prec], "peak_source": f"{peak_kind} copy bandwidth",
+                "algorithmic_bytes_per_launch": 512 * 512 * BYTES_PER_LU[prec],
+                "avg_launch_us": round(avg_launch_us, 3)}
+
+    out = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+           "config": {"workload": WORKLOAD, "nx": 512, "ny": 512, "instances": len(instances),
+                      "a": 32, "period_steps": 96, "periods": 30,
+                      "lattice_updates_per_step": lus_per_step,
+                      "l2": "flushed (256 MiB write) between timed steps; a 512^2 lattice's ping-pong "
+                            "state can stay L2-resident across the lattice time steps of one run",
+                      "parallelism": f"replicas x{world} (independent instances per rank)"},
+           "roofline": roofline, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+           "forces_last_step": results.round(6).tolist()}
+
+    if not args.no_e2e:
+        # end to end through the C ABI with host buffers: create from host eps/PEC maps,
+        # run, read the three results back, destroy
+        maps = []
+        for i, j in zip(instances, janus):
+            reg = L.rasterize_janus(j, i["nx"], i["ny"])
+            eps = np.ones((i["ny"], i["nx"]))
+            eps[reg == 1] = i["eps1"]
+            pec = (reg == 2).astype(np.uint8)
+            maps.append((eps, pec))
+        e2e_ms = []
+        for k in range(args.steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for inst, (eps, pec), c in zip(instances, maps, contours):
+                with L.Solver(inst["nx"], inst["ny"], prec, eps_map=eps, pec_mask=pec,
+                              source=L.make_source(inst["period"], inst["ramp"]), stream=stream) as s:
+                    s.step((inst["periods"] - 1) * inst["period"])
+                    s.force_torque(c)
+            torch.cuda.synchronize()
+            if k > 0:
+                e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e_total = sum(e2e_ms)
+        if dist:
+            t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_total = float(t.item())
+        h2d = 0
+        for i in instances:
+            pitch = (i["nx"] + 31) // 32 * 32
+            n_pts = 2 * int(np.ceil(2 * np.pi * i["R"]))
+            # material ids, material table, phase table, contour slot map, contour points
+            h2d += i["nx"] * i["ny"] + 256 * 32 + i["period"] * 16 + pitch * i["ny"] * 4 + n_pts * 64
+        out["e2e"] = {"value": round(lus_per_step * args.steps * world / (e2e_total / 1e3) / 1e6, 1),
+                      "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(len(instances) * (3 * 8 + 4))}
+
+    if not args.no_forms and rank == 0:
+        forms = {}
+        for fp in ("f32", "f64"):
+            if fp == prec:
+                forms[fp] = {"mlups": out["value"] / world, "step_kernel_gbs": roofline["achieved"],
+                             "frac": roofline["frac"]}
+                continue
+            ss = [L.solver_for_instance(inst, fp, stream) for inst in instances]
+            ev = []
+            res = []
+            t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0e.record(stream)
+            for s, inst, c in zip(ss, instances, contours):
+                n_plain = (inst["periods"] - 1) * inst["period"]
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s.step(n_plain)
+                b.record(stream)
+                ev.append((a, b, n_plain))
+                res.append(s.force_torque(c))
+            t1e.record(stream)
+            t1e.synchronize()
+            ms = t0e.elapsed_time(t1e)
+            pms = sum(a.elapsed_time(b) for a, b, _ in ev)
+            pn = sum(n for _, _, n in ev)
+            gbs = pn * 512 * 512 * BYTES_PER_LU[fp] / (pms / 1e3) / 1e9
+            res = np.array(res)
+            ref = results if prec == "f64" else res
+            drag = np.abs(ref[:, 0])
+            err = np.abs(res - ref) / drag[:, None]
+            forms[fp] = {"mlups": round(lus_per_step / (ms / 1e3) / 1e6, 1), "step_kernel_gbs": round(gbs, 1),
+                         "frac": round(gbs / peak, 4),
+                         "max_drag_err_rel": float(err[:, 0].max()),
+                         "max_lift_torque_err_drag_scale": float(err[:, 1:].max())}
+            for s in ss:
+                s.close()
+        out["forms"] = forms
+
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        out["cpu_baseline"] = cpu_baseline(instances[0], args.cpu_seconds)
+
+    for s in solvers:
+        s.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

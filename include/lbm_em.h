@@ -1,0 +1,229 @@
+/*
+ * lbm_em.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann Maxwell solver for
+ * radiation forces and torques on Janus cylinders (arXiv 2509.22308).
+ *
+ * Method (paper Sec. III): D3Q7 lattice Boltzmann for TM^z fields (E_z, H_x, H_y),
+ *   e_i(r + c_i, t + 1) = 2 e_i^eq(r, t) - e_i(r, t),  h_i likewise   (Eq. LBGK equation)
+ *   e_i^eq = (E - c_i x H)/6, h_i^eq = (H + c_i x E)/6 (i != 0), e_0^eq = (eps_r - 1) E
+ *                                                       (Eq. equilibrium distribution functions)
+ * with a plane-wave source on the left edge, open (first-order extrapolation) edges,
+ * PEC cells, Fourier accumulation over one period and the period-averaged Maxwell
+ * stress tensor integrated on a closed contour (Sec. II.B, Eq. stress tensor average,
+ * Eq. force, Eq. torque), normalised by F0 = pi a E0^2 / 4 and M0 = 2 F0 a.
+ *
+ * Units: lattice cell = time step = 1, eps0 = mu0 = 1; light travels 1/3 cell per
+ * step, so an incident period of T steps has wavelength T/3.  The wave travels
+ * along +x; F~x is the drag and F~y the lift towards +y.
+ *
+ * Conventions shared by every call:
+ *  - Arrays of sites are row-major [ny][nx] (x fastest), host memory unless a
+ *    name says "device".  The caller owns every buffer it passes; the library
+ *    copies what it keeps.
+ *  - Every call returns an lbm_em_status; no exception or longjmp crosses the ABI.
+ *    lbm_em_last_error() gives a message for the calling thread's last failure.
+ *  - Calls on one handle must not overlap (one host thread at a time per handle).
+ *  - The library needs a CUDA device; without one (or without the sm_103a
+ *    image) create calls fail with LBM_EM_ECUDA.  There is no CPU fallback.
+ */
+#ifndef LBM_EM_H
+#define LBM_EM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_EM_OK = 0,
+    LBM_EM_EINVAL = 1,     /* bad argument (NULL, size, eps < 1, too many materials ...) */
+    LBM_EM_ENOMEM = 2,     /* device or host allocation failed                          */
+    LBM_EM_ECUDA = 3,      /* a CUDA runtime call failed (no device, launch error ...)  */
+    LBM_EM_EUNSTABLE = 4,  /* a field became non-finite or reached 3*2^20 (sticky)     */
+    LBM_EM_ETIMEOUT = 5,   /* a bounded device-side wait gave up                        */
+    LBM_EM_ESTATE = 6      /* call not valid in the handle's state                       */
+} lbm_em_status;
+
+/* Storage of the distributions.  Arithmetic is FP64 for F64, FP32 otherwise;
+ * Fourier accumulators and the stress-tensor integral are FP64 in every form. */
+typedef enum {
+    LBM_EM_F64 = 0,      /* 16 FP64 populations per site                                */
+    LBM_EM_F32 = 1,      /* 16 FP32 populations per site                                */
+    LBM_EM_F16DEV = 2    /* FP32 fields (E_z, H_x, H_y) + 16 FP16 scaled deviations
+                            f - f^eq per site                                           */
+} lbm_em_precision;
+
+/* Left-edge plane-wave source (Sec. III: "introduced through the left boundary"). */
+typedef enum {
+    LBM_EM_SRC_OPEN = 0,  /* incoming +x populations at x = 0: zero-gradient copy of the
+                             scattered part + the exact discrete incident plane wave     */
+    LBM_EM_SRC_HARD = 1,  /* incoming +x populations at x = 0: incident wave only        */
+    LBM_EM_SRC_NONE = 2   /* no source (all edges open)                                  */
+} lbm_em_source_kind;
+
+typedef struct {
+    int32_t nx, ny;       /* lattice size, each >= 4                                      */
+    int32_t precision;    /* lbm_em_precision                                             */
+    int32_t reserved;     /* 0                                                            */
+    void *stream;         /* cudaStream_t every kernel of the handle runs on; NULL: the
+                             library creates a private non-blocking stream                */
+} lbm_em_grid;
+
+typedef struct {
+    int32_t period_steps; /* T >= 4: steps per period (wavelength T/3)                    */
+    int32_t ramp_steps;   /* >= 0: amplitude ramp sin^2(pi t / (2 ramp)) for t < ramp     */
+    int32_t kind;         /* lbm_em_source_kind                                           */
+    int32_t reserved;     /* 0                                                            */
+    double E0;            /* incident amplitude (the force scale F0 uses it)              */
+} lbm_em_source;
+
+/* Janus cylinder (Sec. II): radius a, region II (eps1) where d . n_d > 1e-9 with
+ * n_d = (-sin phi0, -cos phi0) and d the offset from the centre, region III (eps2, or
+ * PEC) elsewhere inside |d| <= a, vacuum outside.  A homogeneous cylinder is eps1 == eps2. */
+typedef struct {
+    double a;             /* radius in cells, > 0                                         */
+    double phi0;          /* interface orientation, radians                               */
+    double eps1;          /* region II relative permittivity, >= 1                        */
+    double eps2;          /* region III relative permittivity, >= 1 (ignored if pec2)     */
+    int32_t pec2;         /* 1: region III is a perfect electric conductor                */
+    int32_t reserved;     /* 0                                                            */
+    double cx, cy;        /* centre in lattice coordinates; NaN: ((nx-1)/2, (ny-1)/2)     */
+} lbm_em_janus;
+
+/* Stress-tensor contour (Sec. II.B): circle of radius R about (cx, cy), n_points
+ * samples phi_k = 2 pi k / n_points, phasors bilinearly interpolated.  The circle
+ * must lie strictly inside the lattice (1 <= cx +- R <= nx - 2, same for y). */
+typedef struct {
+    double cx, cy;        /* centre; NaN: lattice centre                                  */
+    double radius;        /* R > 0                                                        */
+    int32_t n_points;     /* >= 8, or 0 for 2 ceil(2 pi R)                                 */
+    int32_t reserved;     /* 0                                                            */
+    double a;             /* cylinder radius used for F0 = pi a E0^2/4, M0 = 2 F0 a       */
+} lbm_em_contour;
+
+typedef struct lbm_em lbm_em_t;
+
+/* Create a solver from a host permittivity map eps_map[ny][nx] (each value >= 1) and
+ * an optional host PEC mask pec_mask[ny][nx] (non-zero = PEC; NULL = none).  At most
+ * 255 distinct permittivities.  Distributions start at zero (time 0).
+ * Paper: Sec. III (per-cell eps_r, mu_r = 1), Sec. II (regions I-III). */
+lbm_em_status lbm_em_create(const lbm_em_grid *g, const double *eps_map, const uint8_t *pec_mask,
+                            const lbm_em_source *s, lbm_em_t **out);
+
+/* Create a solver whose material map is the staircase Janus disc j, rasterised on the
+ * device (region ids 0 = vacuum, 1 = region II, 2 = region III).  Sec. II, Sec. IV.A. */
+lbm_em_status lbm_em_create_janus(const lbm_em_grid *g, const lbm_em_janus *j,
+                                  const lbm_em_source *s, lbm_em_t **out);
+
+/* Return the handle to time 0: distributions, Fourier accumulators and the error flag
+ * are cleared on the device (no allocation).  Asynchronous on the handle's stream. */
+lbm_em_status lbm_em_reset(lbm_em_t *h);
+
+/* Re-rasterise a Janus disc j into the handle's material map in place (same lattice;
+ * region ids 0/1/2 as in lbm_em_create_janus), e.g. the next cell of a design map.
+ * Does not touch the distributions (call lbm_em_reset for a fresh run).  Sec. II. */
+lbm_em_status lbm_em_set_janus(lbm_em_t *h, const lbm_em_janus *j);
+
+/* Release every resource of the handle (NULL is accepted). */
+lbm_em_status lbm_em_destroy(lbm_em_t *h);
+
+/* Enqueue n >= 0 time steps (fused stream-collide over every site, source, open
+ * edges, PEC), Eq. (LBGK equation).  Asynchronous on the handle's stream. */
+lbm_em_status lbm_em_step(lbm_em_t *h, int64_t n);
+
+/* Wait for the handle's stream; returns LBM_EM_EUNSTABLE if any step flagged a
+ * non-finite or runaway field since creation (the flag is sticky). */
+lbm_em_status lbm_em_sync(lbm_em_t *h);
+
+/* Current time step count (host view; equals the number of steps enqueued). */
+lbm_em_status lbm_em_get_time(lbm_em_t *h, int64_t *t);
+
+/* Define the stress-tensor contour and clear the Fourier accumulators (Sec. III:
+ * phasors from Fourier analysis over one period). */
+lbm_em_status lbm_em_set_contour(lbm_em_t *h, const lbm_em_contour *c);
+
+/* Enqueue n steps that also add (E_z, H_x, H_y)(t) * e^{i w t}, w = 2 pi / T, at every
+ * site the contour interpolates from, before each step's collision.  Requires a contour. */
+lbm_em_status lbm_em_accumulate(lbm_em_t *h, int64_t n);
+
+/* From the accumulators (n accumulated steps, phasor = (2/n) * sum): the
+ * period-averaged stress tensor on the contour -> out[3] = {F~x, F~y, M~z}
+ * (Eq. stress tensor average, force, torque; F0, M0 of Sec. II.B).  Synchronous. */
+lbm_em_status lbm_em_contour_integral(lbm_em_t *h, double out[3]);
+
+/* set_contour(c) + accumulate(T) + contour_integral(out): advances one period. */
+lbm_em_status lbm_em_force_torque(lbm_em_t *h, const lbm_em_contour *c, double out[3]);
+
+/* Fields at the current time into host arrays [ny][nx] (any may be NULL).  Synchronous. */
+lbm_em_status lbm_em_get_fields(lbm_em_t *h, double *ez, double *hx, double *hy);
+
+/* Phasors at the contour's stencil sites: site_xy[2*k] = x, [2*k+1] = y and
+ * phasors[6*k .. 6*k+5] = Re/Im of E_z, H_x, H_y (already scaled by 2/n).  With
+ * NULL arrays only *n_sites is written.  Synchronous. */
+lbm_em_status lbm_em_get_phasors(lbm_em_t *h, int32_t *site_xy, double *phasors, int32_t *n_sites);
+
+/* Material ids [ny][nx] (host) and, if eps_table is not NULL, eps_table[256] with the
+ * relative permittivity of each id (0 for PEC ids, 1 for unused ids).  Synchronous. */
+lbm_em_status lbm_em_get_material(lbm_em_t *h, uint8_t *ids, double *eps_table);
+
+/* Checkpoint: with buf == NULL writes the size needed to *bytes; otherwise copies the
+ * distributions, time and accumulators into buf (capacity *bytes).  Synchronous. */
+lbm_em_status lbm_em_save_state(lbm_em_t *h, void *buf, size_t *bytes);
+
+/* Restore a checkpoint written by lbm_em_save_state of a handle with the same grid,
+ * precision, source and contour.  A resumed run equals an unsplit run bit for bit. */
+lbm_em_status lbm_em_load_state(lbm_em_t *h, const void *buf, size_t bytes);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *lbm_em_last_error(void);
+
+/* Rasterise a Janus disc on the device into host region ids [ny][nx]
+ * (0 vacuum, 1 region II, 2 region III).  Sec. II, Sec. IV.A staircase. */
+lbm_em_status lbm_em_rasterize_janus(const lbm_em_janus *j, int32_t nx, int32_t ny, uint8_t *regions);
+
+/* ---- batched design diagrams (Sec. IV maps over eps and phi0) ---------------------- */
+
+typedef struct {
+    int32_t nx, ny;          /* lattice of this instance                                   */
+    int32_t period_steps;    /* T                                                          */
+    int32_t periods;         /* run length in periods; the last one is Fourier-averaged    */
+    int32_t ramp_steps;      /* source ramp                                                */
+    int32_t n_points;        /* contour samples (0: 2 ceil(2 pi R))                         */
+    double E0;               /* incident amplitude                                         */
+    double contour_radius;   /* R                                                          */
+    lbm_em_janus janus;      /* geometry (centre NaN: lattice centre)                      */
+} lbm_em_instance;
+
+typedef struct {
+    int32_t precision;       /* LBM_EM_F32 or LBM_EM_F64                                    */
+    int32_t tile_w, tile_h;  /* tile shape of the packed tile list; 0: autotuned           */
+    int32_t ctas_per_sm;     /* persistent CTAs per SM; 0: autotuned                       */
+    int32_t reserved;        /* 0                                                          */
+    void *stream;            /* cudaStream_t; NULL: private stream                         */
+} lbm_em_batch_opts;
+
+typedef struct lbm_em_batch lbm_em_batch_t;
+
+/* Pack n instances (uneven sizes allowed) into one multi-domain layout on the device. */
+lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n,
+                                  const lbm_em_batch_opts *o, lbm_em_batch_t **out);
+
+/* Run every instance to completion (persistent kernel over the packed tile list,
+ * replayed under a CUDA graph), then the contour integral of each.  Asynchronous. */
+lbm_em_status lbm_em_batch_run(lbm_em_batch_t *b);
+
+/* Wait and fetch results: out[3*i .. 3*i+2] = {F~x, F~y, M~z} of instance i and
+ * status[i] (an lbm_em_status) per instance; either may be NULL. */
+lbm_em_status lbm_em_batch_results(lbm_em_batch_t *b, double *out, int32_t *status);
+
+/* Chosen tile shape and CTAs per SM (after autotuning), for reporting. */
+lbm_em_status lbm_em_batch_config(lbm_em_batch_t *b, int32_t *tile_w, int32_t *tile_h,
+                                  int32_t *ctas_per_sm);
+
+lbm_em_status lbm_em_batch_destroy(lbm_em_batch_t *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_EM_H */

@@ -1,0 +1,737 @@
+// Host runtime of the single-domain solver: the C ABI of include/lbm_em.h.
+//
+// Time handling.  Every step kernel reads the current time t from one of two device
+// words and writes t + 1 into the other (the pair alternates with the ping-pong
+// distribution buffers), so a captured run of an even number of steps is replayed
+// unchanged for any start time: source phases and Fourier weights come from t.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm_em.h"
+#include "common.cuh"
+#include "runtime.h"
+
+using namespace lbmem;
+
+namespace lbmem {
+thread_local std::string g_last_error;
+
+lbm_em_status set_error(lbm_em_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+lbm_em_status cuda_status(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return LBM_EM_OK;
+    cudaGetLastError();  // clear a non-sticky error
+    return set_error(e == cudaErrorMemoryAllocation ? LBM_EM_ENOMEM : LBM_EM_ECUDA,
+                     std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void incident_constants(int period, double E0, double *pr, double *pi, double *qr, double *qi) {
+    // Right-going vacuum branch of the lattice dispersion relation: w = (3 - z)/(z(3z - 1)),
+    // z = e^{-i omega}; E_z = Re[E w^x z^t] with E = i E0, and the +x population of e_z is
+    // Re[P w^x z^t] with P = 2E / (3(wz + 1)).
+    const double om = 2.0 * M_PI / (double)period;
+    const std::complex<double> z = std::exp(std::complex<double>(0.0, -om));
+    const std::complex<double> w = (3.0 - z) / (z * (3.0 * z - 1.0));
+    const std::complex<double> E(0.0, E0);
+    const std::complex<double> P = 2.0 * E / (3.0 * (w * z + 1.0));
+    const std::complex<double> Q = P * w;
+    *pr = P.real();
+    *pi = P.imag();
+    *qr = Q.real();
+    *qi = Q.imag();
+}
+
+std::vector<double2> phase_table(int period) {
+    std::vector<double2> cs(period);
+    const double om = 2.0 * M_PI / (double)period;
+    for (int t = 0; t < period; ++t) cs[t] = make_double2(std::cos(om * (double)t), std::sin(om * (double)t));
+    return cs;
+}
+
+lbm_em_status check_source(const lbm_em_source *s) {
+    if (!s) return set_error(LBM_EM_EINVAL, "source is NULL");
+    if (s->period_steps < 4) return set_error(LBM_EM_EINVAL, "source.period_steps must be >= 4");
+    if (s->ramp_steps < 0) return set_error(LBM_EM_EINVAL, "source.ramp_steps must be >= 0");
+    if (s->kind < 0 || s->kind > 2) return set_error(LBM_EM_EINVAL, "source.kind out of range");
+    if (!std::isfinite(s->E0)) return set_error(LBM_EM_EINVAL, "source.E0 must be finite");
+    return LBM_EM_OK;
+}
+
+lbm_em_status check_janus(const lbm_em_janus *j) {
+    if (!j) return set_error(LBM_EM_EINVAL, "janus spec is NULL");
+    if (!(j->a > 0.0) || !std::isfinite(j->a)) return set_error(LBM_EM_EINVAL, "janus.a must be > 0");
+    if (!std::isfinite(j->phi0)) return set_error(LBM_EM_EINVAL, "janus.phi0 must be finite");
+    if (!(j->eps1 >= 1.0) || !std::isfinite(j->eps1)) return set_error(LBM_EM_EINVAL, "janus.eps1 must be >= 1");
+    if (!j->pec2 && (!(j->eps2 >= 1.0) || !std::isfinite(j->eps2)))
+        return set_error(LBM_EM_EINVAL, "janus.eps2 must be >= 1");
+    return LBM_EM_OK;
+}
+
+void janus_center(const lbm_em_janus *j, int nx, int ny, double *cx, double *cy) {
+    *cx = std::isnan(j->cx) ? 0.5 * (double)(nx - 1) : j->cx;
+    *cy = std::isnan(j->cy) ? 0.5 * (double)(ny - 1) : j->cy;
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+lbm_em_status build_contour(int nx, int ny, const lbm_em_contour *c, ContourHost *out) {
+    if (!c) return set_error(LBM_EM_EINVAL, "contour is NULL");
+    if (!(c->radius > 0.0) || !std::isfinite(c->radius)) return set_error(LBM_EM_EINVAL, "contour.radius must be > 0");
+    if (!(c->a > 0.0) || !std::isfinite(c->a)) return set_error(LBM_EM_EINVAL, "contour.a must be > 0");
+    if (c->n_points != 0 && c->n_points < 8) return set_error(LBM_EM_EINVAL, "contour.n_points must be 0 or >= 8");
+    const double cx = std::isnan(c->cx) ? 0.5 * (double)(nx - 1) : c->cx;
+    const double cy = std::isnan(c->cy) ? 0.5 * (double)(ny - 1) : c->cy;
+    const double R = c->radius;
+    if (!(cx - R >= 1.0 && cx + R <= (double)(nx - 2) && cy - R >= 1.0 && cy + R <= (double)(ny - 2)))
+        return set_error(LBM_EM_EINVAL, "contour circle must lie inside the lattice (1 cell margin)");
+    const int N = c->n_points > 0 ? c->n_points : (int)(2.0 * std::ceil(2.0 * M_PI * R));
+    out->R = R;
+    out->dl = R * 2.0 * M_PI / (double)N;
+    out->pts.resize(N);
+    std::map<long long, int> slots;
+    out->site_xy.clear();
+    out->y0 = ny;
+    out->y1 = -1;
+    for (int k = 0; k < N; ++k) {
+        const double phi = 2.0 * M_PI * (double)k / (double)N;
+        const double px = cx + R * std::cos(phi), py = cy + R * std::sin(phi);
+        const int i = (int)std::floor(px), jj = (int)std::floor(py);
+        const double fx = px - i, fy = py - jj;
+        ContourPt &p = out->pts[k];
+        const int cxs[4] = {i, i + 1, i, i + 1}, cys[4] = {jj, jj, jj + 1, jj + 1};
+        p.w[0] = (1 - fx) * (1 - fy);
+        p.w[1] = fx * (1 - fy);
+        p.w[2] = (1 - fx) * fy;
+        p.w[3] = fx * fy;
+        for (int q = 0; q < 4; ++q) {
+            const long long key = (long long)cys[q] * nx + cxs[q];
+            auto it = slots.find(key);
+            int s;
+            if (it == slots.end()) {
+                s = (int)slots.size();
+                slots.emplace(key, s);
+                out->site_xy.push_back(cxs[q]);
+                out->site_xy.push_back(cys[q]);
+                out->y0 = std::min(out->y0, cys[q]);
+                out->y1 = std::max(out->y1, cys[q]);
+            } else {
+                s = it->second;
+            }
+            p.s[q] = s;
+        }
+        p.nx = std::cos(phi);
+        p.ny = std::sin(phi);
+    }
+    out->n_slots = (int)slots.size();
+    out->F0 = M_PI * c->a * out->E0 * out->E0 / 4.0;
+    out->M0 = 2.0 * out->F0 * c->a;
+    return LBM_EM_OK;
+}
+}  // namespace lbmem
+
+struct lbm_em {
+    int dev = 0;
+    int nx = 0, ny = 0, pitch = 0, prec = 0;
+    size_t pstride = 0, elem = 0;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    bool own_stream = false;
+    void *buf[2] = {nullptr, nullptr};
+    uint8_t *d_mat = nullptr;
+    void *d_mtab = nullptr;
+    double eps_table[256];
+    bool pec_id[256];
+    long long *d_time = nullptr;
+    unsigned *d_err = nullptr;
+    double2 *d_cs = nullptr;
+    SourceParams src{};
+    lbm_em_source srccfg{};
+    int64_t t = 0;
+    // contour and accumulators
+    bool has_contour = false;
+    lbm_em_contour contour{};
+    ContourHost ch;
+    int *d_slot = nullptr;
+    double *d_acc = nullptr;
+    ContourPt *d_pts = nullptr;
+    double *d_out = nullptr;
+    int64_t n_acc = 0;
+    // graphs of kGraphSteps steps starting at an even time
+    cudaGraphExec_t g_plain = nullptr, g_acc = nullptr;
+    double *d_fields = nullptr;
+};
+
+static const int kGraphSteps = 32;
+
+template <typename T>
+static StepArgs<T> make_args(const lbm_em *h) {
+    StepArgs<T> a{};
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.pitch = h->pitch;
+    a.pstride = h->pstride;
+    a.mat = h->d_mat;
+    a.mtab = (const MatT<T> *)h->d_mtab;
+    a.src = h->src;
+    a.accp.slot = h->d_slot;
+    a.accp.acc = h->d_acc;
+    a.accp.y0 = h->ch.y0;
+    a.accp.y1 = h->ch.y1;
+    a.err = h->d_err;
+    return a;
+}
+
+static cudaError_t enqueue_step(lbm_em *h, bool acc, cudaStream_t s, int64_t t) {
+    const int p = (int)(t & 1);
+    if (h->prec == LBM_EM_F64)
+        return launch_step<double>(make_args<double>(h), (const double *)h->buf[p], (double *)h->buf[1 - p],
+                                   h->d_time + p, h->d_time + (1 - p), acc, s);
+    return launch_step<float>(make_args<float>(h), (const float *)h->buf[p], (float *)h->buf[1 - p],
+                              h->d_time + p, h->d_time + (1 - p), acc, s);
+}
+
+static lbm_em_status build_graph(lbm_em *h, bool acc, cudaGraphExec_t *out) {
+    cudaGraph_t g = nullptr;
+    lbm_em_status st = cuda_status(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal),
+                                   "cudaStreamBeginCapture");
+    if (st) return st;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) e = enqueue_step(h, acc, h->cap, i);
+    cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_status(e != cudaSuccess ? e : e2, "capturing the step graph");
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return cuda_status(e, "cudaGraphInstantiate");
+}
+
+static lbm_em_status run_steps(lbm_em *h, int64_t n, bool acc) {
+    while (n > 0) {
+        if ((h->t & 1) == 0 && n >= kGraphSteps) {
+            cudaGraphExec_t *g = acc ? &h->g_acc : &h->g_plain;
+            if (!*g) {
+                lbm_em_status st = build_graph(h, acc, g);
+                if (st) return st;
+            }
+            lbm_em_status st = cuda_status(cudaGraphLaunch(*g, h->stream), "cudaGraphLaunch");
+            if (st) return st;
+            h->t += kGraphSteps;
+            n -= kGraphSteps;
+        } else {
+            lbm_em_status st = cuda_status(enqueue_step(h, acc, h->stream, h->t), "step launch");
+            if (st) return st;
+            h->t += 1;
+            n -= 1;
+        }
+    }
+    return LBM_EM_OK;
+}
+
+static void free_contour(lbm_em *h) {
+    if (h->g_acc) cudaGraphExecDestroy(h->g_acc);
+    h->g_acc = nullptr;
+    cudaFree(h->d_slot);
+    cudaFree(h->d_acc);
+    cudaFree(h->d_pts);
+    h->d_slot = nullptr;
+    h->d_acc = nullptr;
+    h->d_pts = nullptr;
+    h->has_contour = false;
+}
+
+static void free_handle(lbm_em *h) {
+    if (!h) return;
+    cudaSetDevice(h->dev);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_contour(h);
+    if (h->g_plain) cudaGraphExecDestroy(h->g_plain);
+    cudaFree(h->buf[0]);
+    cudaFree(h->buf[1]);
+    cudaFree(h->d_mat);
+    cudaFree(h->d_mtab);
+    cudaFree(h->d_time);
+    cudaFree(h->d_err);
+    cudaFree(h->d_cs);
+    cudaFree(h->d_out);
+    cudaFree(h->d_fields);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+template <typename T>
+static std::vector<MatT<T>> material_table(const double *eps, const bool *pec) {
+    std::vector<MatT<T>> tab(256);
+    for (int i = 0; i < 256; ++i) {
+        if (pec[i]) {
+            tab[i] = MatT<T>{(T)0, (T)0, (T)0, (T)0};
+        } else {
+            tab[i] = MatT<T>{(T)(1.0 / (3.0 * eps[i])), (T)(6.0 * (eps[i] - 1.0)), (T)(1.0 / eps[i]), (T)0};
+        }
+    }
+    return tab;
+}
+
+// Allocate and initialise everything except the material ids.
+static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s, lbm_em **out) {
+    if (!g || !out) return set_error(LBM_EM_EINVAL, "grid/out is NULL");
+    *out = nullptr;
+    if (g->nx < 4 || g->ny < 4) return set_error(LBM_EM_EINVAL, "nx and ny must be >= 4");
+    if ((long long)g->nx * g->ny > (1LL << 31)) return set_error(LBM_EM_EINVAL, "lattice too large (> 2^31 sites)");
+    if (g->precision != LBM_EM_F64 && g->precision != LBM_EM_F32)
+        return set_error(LBM_EM_EINVAL, "precision not supported by this build");
+    lbm_em_status st = check_source(s);
+    if (st) return st;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return set_error(LBM_EM_ECUDA, "no CUDA device available (the solver has no CPU path)");
+    }
+    lbm_em *h = new lbm_em();
+    cudaGetDevice(&h->dev);
+    h->nx = g->nx;
+    h->ny = g->ny;
+    h->prec = g->precision;
+    h->elem = g->precision == LBM_EM_F64 ? sizeof(double) : sizeof(float);
+    h->pitch = round_up(g->nx, 32);
+    h->pstride = (size_t)h->pitch * (size_t)g->ny;
+    h->srccfg = *s;
+    for (int i = 0; i < 256; ++i) {
+        h->eps_table[i] = 1.0;
+        h->pec_id[i] = false;
+    }
+#define TRY(call, what)                       \
+    do {                                      \
+        st = cuda_status((call), what);       \
+        if (st) {                             \
+            free_handle(h);                   \
+            return st;                        \
+        }                                     \
+    } while (0)
+    if (g->stream) {
+        h->stream = (cudaStream_t)g->stream;
+    } else {
+        TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        h->own_stream = true;
+    }
+    TRY(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    const size_t bytes = (size_t)NPLANES * h->pstride * h->elem;
+    for (int b = 0; b < 2; ++b) {
+        TRY(cudaMalloc(&h->buf[b], bytes), "cudaMalloc(distributions)");
+        TRY(cudaMemsetAsync(h->buf[b], 0, bytes, h->stream), "cudaMemset");
+    }
+    TRY(cudaMalloc(&h->d_mat, h->pstride), "cudaMalloc(material)");
+    TRY(cudaMemsetAsync(h->d_mat, 0, h->pstride, h->stream), "cudaMemset");
+    TRY(cudaMalloc(&h->d_mtab, 256 * sizeof(MatT<double>)), "cudaMalloc(table)");
+    TRY(cudaMalloc(&h->d_time, 2 * sizeof(long long)), "cudaMalloc(time)");
+    TRY(cudaMemsetAsync(h->d_time, 0, 2 * sizeof(long long), h->stream), "cudaMemset");
+    TRY(cudaMalloc(&h->d_err, sizeof(unsigned)), "cudaMalloc(err)");
+    TRY(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream), "cudaMemset");
+    TRY(cudaMalloc(&h->d_out, 4 * sizeof(double)), "cudaMalloc(out)");
+    std::vector<double2> cs = phase_table(s->period_steps);
+    TRY(cudaMalloc(&h->d_cs, cs.size() * sizeof(double2)), "cudaMalloc(phase table)");
+    TRY(cudaMemcpyAsync(h->d_cs, cs.data(), cs.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream),
+        "cudaMemcpy(phase table)");
+    h->src.kind = s->kind;
+    h->src.period = s->period_steps;
+    h->src.ramp = s->ramp_steps;
+    incident_constants(s->period_steps, s->E0, &h->src.pr, &h->src.pi, &h->src.qr, &h->src.qi);
+    h->src.cs = h->d_cs;
+    TRY(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+#undef TRY
+    *out = h;
+    return LBM_EM_OK;
+}
+
+static lbm_em_status upload_table(lbm_em *h) {
+    cudaError_t e;
+    if (h->prec == LBM_EM_F64) {
+        auto tab = material_table<double>(h->eps_table, h->pec_id);
+        e = cudaMemcpyAsync(h->d_mtab, tab.data(), tab.size() * sizeof(tab[0]), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    } else {
+        auto tab = material_table<float>(h->eps_table, h->pec_id);
+        e = cudaMemcpyAsync(h->d_mtab, tab.data(), tab.size() * sizeof(tab[0]), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
+    return cuda_status(e, "uploading the material table");
+}
+
+extern "C" {
+
+const char *lbm_em_last_error(void) { return g_last_error.c_str(); }
+
+lbm_em_status lbm_em_create(const lbm_em_grid *g, const double *eps_map, const uint8_t *pec_mask,
+                            const lbm_em_source *s, lbm_em_t **out) {
+    if (!eps_map) return set_error(LBM_EM_EINVAL, "eps_map is NULL");
+    if (!g || !out) return set_error(LBM_EM_EINVAL, "grid/out is NULL");
+    if (g->nx < 4 || g->ny < 4) return set_error(LBM_EM_EINVAL, "nx and ny must be >= 4");
+    const size_t n = (size_t)g->nx * (size_t)g->ny;
+    // material ids: distinct permittivities in order of first appearance, one id for PEC
+    std::map<double, int> ids;
+    std::vector<uint8_t> idv(n);
+    double eps_tab[256];
+    bool pec_tab[256];
+    for (int i = 0; i < 256; ++i) {
+        eps_tab[i] = 1.0;
+        pec_tab[i] = false;
+    }
+    int pec_slot = -1, next = 0;
+    for (size_t i = 0; i < n; ++i) {
+        if (pec_mask && pec_mask[i]) {
+            if (pec_slot < 0) {
+                if (next >= 256) return set_error(LBM_EM_EINVAL, "more than 256 materials");
+                pec_slot = next++;
+                pec_tab[pec_slot] = true;
+                eps_tab[pec_slot] = 0.0;
+            }
+            idv[i] = (uint8_t)pec_slot;
+            continue;
+        }
+        const double e = eps_map[i];
+        if (!(e >= 1.0) || !std::isfinite(e)) return set_error(LBM_EM_EINVAL, "eps_map values must be finite and >= 1");
+        auto it = ids.find(e);
+        if (it == ids.end()) {
+            if (next >= 256) return set_error(LBM_EM_EINVAL, "more than 256 distinct materials");
+            eps_tab[next] = e;
+            it = ids.emplace(e, next++).first;
+        }
+        idv[i] = (uint8_t)it->second;
+    }
+    lbm_em *h = nullptr;
+    lbm_em_status st = create_common(g, s, &h);
+    if (st) return st;
+    std::memcpy(h->eps_table, eps_tab, sizeof(eps_tab));
+    std::memcpy(h->pec_id, pec_tab, sizeof(pec_tab));
+    st = cuda_status(cudaMemcpy2DAsync(h->d_mat, h->pitch, idv.data(), h->nx, h->nx, h->ny, cudaMemcpyHostToDevice,
+                                       h->stream),
+                     "uploading material ids");
+    if (!st) st = upload_table(h);
+    if (st) {
+        free_handle(h);
+        return st;
+    }
+    *out = h;
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_create_janus(const lbm_em_grid *g, const lbm_em_janus *j, const lbm_em_source *s,
+                                  lbm_em_t **out) {
+    lbm_em_status st = check_janus(j);
+    if (st) return st;
+    lbm_em *h = nullptr;
+    st = create_common(g, s, &h);
+    if (st) return st;
+    double cx, cy;
+    janus_center(j, h->nx, h->ny, &cx, &cy);
+    h->eps_table[0] = 1.0;
+    h->eps_table[1] = j->eps1;
+    h->eps_table[2] = j->pec2 ? 0.0 : j->eps2;
+    h->pec_id[2] = j->pec2 != 0;
+    st = cuda_status(launch_rasterize(h->nx, h->ny, h->pitch, cx, cy, j->a, -std::sin(j->phi0), -std::cos(j->phi0),
+                                      h->d_mat, h->stream),
+                     "rasterising the Janus disc");
+    if (!st) st = upload_table(h);
+    if (st) {
+        free_handle(h);
+        return st;
+    }
+    *out = h;
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_reset(lbm_em_t *h) {
+    if (!h) return set_error(LBM_EM_EINVAL, "handle is NULL");
+    cudaSetDevice(h->dev);
+    const size_t bytes = (size_t)NPLANES * h->pstride * h->elem;
+    lbm_em_status st = cuda_status(cudaMemsetAsync(h->buf[0], 0, bytes, h->stream), "clearing distributions");
+    if (!st) st = cuda_status(cudaMemsetAsync(h->d_time, 0, 2 * sizeof(long long), h->stream), "clearing time");
+    if (!st) st = cuda_status(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream), "clearing error flag");
+    if (!st && h->has_contour)
+        st = cuda_status(cudaMemsetAsync(h->d_acc, 0, (size_t)h->ch.n_slots * 6 * sizeof(double), h->stream),
+                         "clearing accumulators");
+    if (st) return st;
+    h->t = 0;
+    h->n_acc = 0;
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_set_janus(lbm_em_t *h, const lbm_em_janus *j) {
+    if (!h) return set_error(LBM_EM_EINVAL, "handle is NULL");
+    lbm_em_status st = check_janus(j);
+    if (st) return st;
+    cudaSetDevice(h->dev);
+    double cx, cy;
+    janus_center(j, h->nx, h->ny, &cx, &cy);
+    for (int i = 0; i < 256; ++i) {
+        h->eps_table[i] = 1.0;
+        h->pec_id[i] = false;
+    }
+    h->eps_table[1] = j->eps1;
+    h->eps_table[2] = j->pec2 ? 0.0 : j->eps2;
+    h->pec_id[2] = j->pec2 != 0;
+    st = cuda_status(launch_rasterize(h->nx, h->ny, h->pitch, cx, cy, j->a, -std::sin(j->phi0), -std::cos(j->phi0),
+                                      h->d_mat, h->stream),
+                     "rasterising the Janus disc");
+    if (!st) st = upload_table(h);
+    return st;
+}
+
+lbm_em_status lbm_em_destroy(lbm_em_t *h) {
+    free_handle(h);
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_step(lbm_em_t *h, int64_t n) {
+    if (!h) return set_error(LBM_EM_EINVAL, "handle is NULL");
+    if (n < 0) return set_error(LBM_EM_EINVAL, "n must be >= 0");
+    cudaSetDevice(h->dev);
+    return run_steps(h, n, false);
+}
+
+lbm_em_status lbm_em_sync(lbm_em_t *h) {
+    if (!h) return set_error(LBM_EM_EINVAL, "handle is NULL");
+    cudaSetDevice(h->dev);
+    unsigned err = 0;
+    lbm_em_status st = cuda_status(cudaMemcpyAsync(&err, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream),
+                                   "reading the error flag");
+    if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (st) return st;
+    if (err) return set_error(LBM_EM_EUNSTABLE, "a field became non-finite or exceeded 3*2^20");
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_get_time(lbm_em_t *h, int64_t *t) {
+    if (!h || !t) return set_error(LBM_EM_EINVAL, "NULL argument");
+    *t = h->t;
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_set_contour(lbm_em_t *h, const lbm_em_contour *c) {
+    if (!h) return set_error(LBM_EM_EINVAL, "handle is NULL");
+    cudaSetDevice(h->dev);
+    if (h->has_contour && c && std::memcmp(c, &h->contour, sizeof(*c)) == 0) {
+        lbm_em_status st = cuda_status(
+            cudaMemsetAsync(h->d_acc, 0, (size_t)h->ch.n_slots * 6 * sizeof(double), h->stream), "clearing acc");
+        if (!st) h->n_acc = 0;
+        return st;
+    }
+    ContourHost ch;
+    ch.E0 = h->srccfg.E0;
+    lbm_em_status st = build_contour(h->nx, h->ny, c, &ch);
+    if (st) return st;
+    st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (st) return st;
+    free_contour(h);
+    h->contour = *c;
+    h->ch = ch;
+    std::vector<int> slot_map(h->pstride, -1);
+    for (int s = 0; s < ch.n_slots; ++s)
+        slot_map[(size_t)ch.site_xy[2 * s + 1] * h->pitch + ch.site_xy[2 * s]] = s;
+    st = cuda_status(cudaMalloc(&h->d_slot, h->pstride * sizeof(int)), "cudaMalloc(slots)");
+    if (!st) st = cuda_status(cudaMalloc(&h->d_acc, (size_t)ch.n_slots * 6 * sizeof(double)), "cudaMalloc(acc)");
+    if (!st) st = cuda_status(cudaMalloc(&h->d_pts, ch.pts.size() * sizeof(ContourPt)), "cudaMalloc(contour)");
+    if (!st)
+        st = cuda_status(cudaMemcpy(h->d_slot, slot_map.data(), h->pstride * sizeof(int), cudaMemcpyHostToDevice),
+                         "uploading slots");
+    if (!st)
+        st = cuda_status(cudaMemcpy(h->d_pts, ch.pts.data(), ch.pts.size() * sizeof(ContourPt), cudaMemcpyHostToDevice),
+                         "uploading contour");
+    if (!st) st = cuda_status(cudaMemset(h->d_acc, 0, (size_t)ch.n_slots * 6 * sizeof(double)), "clearing acc");
+    if (st) {
+        free_contour(h);
+        return st;
+    }
+    h->n_acc = 0;
+    h->has_contour = true;
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_accumulate(lbm_em_t *h, int64_t n) {
+    if (!h) return set_error(LBM_EM_EINVAL, "handle is NULL");
+    if (!h->has_contour) return set_error(LBM_EM_ESTATE, "no contour set");
+    if (n < 0) return set_error(LBM_EM_EINVAL, "n must be >= 0");
+    cudaSetDevice(h->dev);
+    lbm_em_status st = run_steps(h, n, true);
+    if (!st) h->n_acc += n;
+    return st;
+}
+
+lbm_em_status lbm_em_contour_integral(lbm_em_t *h, double out[3]) {
+    if (!h || !out) return set_error(LBM_EM_EINVAL, "NULL argument");
+    if (!h->has_contour || h->n_acc <= 0) return set_error(LBM_EM_ESTATE, "no accumulated steps");
+    cudaSetDevice(h->dev);
+    lbm_em_status st = cuda_status(launch_contour(h->d_acc, 2.0 / (double)h->n_acc, h->d_pts, (int)h->ch.pts.size(),
+                                                  h->ch.R, h->ch.dl, h->ch.F0, h->ch.M0, h->d_out, h->stream),
+                                   "contour kernel");
+    double res[3];
+    if (!st)
+        st = cuda_status(cudaMemcpyAsync(res, h->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                         "reading forces");
+    if (!st) st = lbm_em_sync(h);
+    if (st) return st;
+    out[0] = res[0];
+    out[1] = res[1];
+    out[2] = res[2];
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_force_torque(lbm_em_t *h, const lbm_em_contour *c, double out[3]) {
+    lbm_em_status st = lbm_em_set_contour(h, c);
+    if (!st) st = lbm_em_accumulate(h, h->srccfg.period_steps);
+    if (!st) st = lbm_em_contour_integral(h, out);
+    return st;
+}
+
+lbm_em_status lbm_em_get_fields(lbm_em_t *h, double *ez, double *hx, double *hy) {
+    if (!h) return set_error(LBM_EM_EINVAL, "handle is NULL");
+    cudaSetDevice(h->dev);
+    const size_t n = (size_t)h->nx * h->ny;
+    lbm_em_status st = LBM_EM_OK;
+    if (!h->d_fields) st = cuda_status(cudaMalloc(&h->d_fields, 3 * n * sizeof(double)), "cudaMalloc(fields)");
+    if (st) return st;
+    const int p = (int)(h->t & 1);
+    cudaError_t e;
+    if (h->prec == LBM_EM_F64)
+        e = launch_fields<double>(make_args<double>(h), (const double *)h->buf[p], h->d_time + p, h->d_fields,
+                                  h->d_fields + n, h->d_fields + 2 * n, h->stream);
+    else
+        e = launch_fields<float>(make_args<float>(h), (const float *)h->buf[p], h->d_time + p, h->d_fields,
+                                 h->d_fields + n, h->d_fields + 2 * n, h->stream);
+    st = cuda_status(e, "fields kernel");
+    double *dst[3] = {ez, hx, hy};
+    for (int k = 0; k < 3 && !st; ++k)
+        if (dst[k])
+            st = cuda_status(cudaMemcpyAsync(dst[k], h->d_fields + k * n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                             h->stream),
+                             "reading fields");
+    if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return st;
+}
+
+lbm_em_status lbm_em_get_phasors(lbm_em_t *h, int32_t *site_xy, double *phasors, int32_t *n_sites) {
+    if (!h || !n_sites) return set_error(LBM_EM_EINVAL, "NULL argument");
+    if (!h->has_contour) return set_error(LBM_EM_ESTATE, "no contour set");
+    *n_sites = h->ch.n_slots;
+    if (site_xy) std::memcpy(site_xy, h->ch.site_xy.data(), h->ch.site_xy.size() * sizeof(int32_t));
+    if (phasors) {
+        if (h->n_acc <= 0) return set_error(LBM_EM_ESTATE, "no accumulated steps");
+        cudaSetDevice(h->dev);
+        lbm_em_status st = cuda_status(cudaMemcpyAsync(phasors, h->d_acc, (size_t)h->ch.n_slots * 6 * sizeof(double),
+                                                       cudaMemcpyDeviceToHost, h->stream),
+                                       "reading accumulators");
+        if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        if (st) return st;
+        const double sc = 2.0 / (double)h->n_acc;
+        for (size_t i = 0; i < (size_t)h->ch.n_slots * 6; ++i) phasors[i] *= sc;
+    }
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_get_material(lbm_em_t *h, uint8_t *ids, double *eps_table) {
+    if (!h) return set_error(LBM_EM_EINVAL, "handle is NULL");
+    cudaSetDevice(h->dev);
+    if (eps_table)
+        for (int i = 0; i < 256; ++i) eps_table[i] = h->pec_id[i] ? 0.0 : h->eps_table[i];
+    if (ids) {
+        lbm_em_status st = cuda_status(cudaMemcpy2DAsync(ids, h->nx, h->d_mat, h->pitch, h->nx, h->ny,
+                                                         cudaMemcpyDeviceToHost, h->stream),
+                                       "reading material ids");
+        if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        return st;
+    }
+    return LBM_EM_OK;
+}
+
+struct StateHeader {
+    uint64_t magic;
+    int32_t prec, nx, ny, n_slots;
+    int64_t t, n_acc;
+};
+static const uint64_t kMagic = 0x4c424d454d535431ULL;
+
+lbm_em_status lbm_em_save_state(lbm_em_t *h, void *buf, size_t *bytes) {
+    if (!h || !bytes) return set_error(LBM_EM_EINVAL, "NULL argument");
+    const size_t dist = (size_t)NPLANES * h->pstride * h->elem;
+    const size_t accb = h->has_contour ? (size_t)h->ch.n_slots * 6 * sizeof(double) : 0;
+    const size_t need = sizeof(StateHeader) + dist + accb;
+    if (!buf) {
+        *bytes = need;
+        return LBM_EM_OK;
+    }
+    if (*bytes < need) return set_error(LBM_EM_EINVAL, "checkpoint buffer too small");
+    cudaSetDevice(h->dev);
+    StateHeader hd{kMagic, h->prec, h->nx, h->ny, h->has_contour ? h->ch.n_slots : -1, h->t, h->n_acc};
+    std::memcpy(buf, &hd, sizeof(hd));
+    char *p = (char *)buf + sizeof(hd);
+    lbm_em_status st = cuda_status(
+        cudaMemcpyAsync(p, h->buf[h->t & 1], dist, cudaMemcpyDeviceToHost, h->stream), "saving distributions");
+    if (!st && accb)
+        st = cuda_status(cudaMemcpyAsync(p + dist, h->d_acc, accb, cudaMemcpyDeviceToHost, h->stream), "saving acc");
+    if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (!st) *bytes = need;
+    return st;
+}
+
+lbm_em_status lbm_em_load_state(lbm_em_t *h, const void *buf, size_t bytes) {
+    if (!h || !buf) return set_error(LBM_EM_EINVAL, "NULL argument");
+    StateHeader hd;
+    if (bytes < sizeof(hd)) return set_error(LBM_EM_EINVAL, "checkpoint too small");
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (hd.magic != kMagic || hd.prec != h->prec || hd.nx != h->nx || hd.ny != h->ny)
+        return set_error(LBM_EM_EINVAL, "checkpoint does not match this handle");
+    const int want_slots = h->has_contour ? h->ch.n_slots : -1;
+    if (hd.n_slots != want_slots) return set_error(LBM_EM_EINVAL, "checkpoint contour does not match");
+    const size_t dist = (size_t)NPLANES * h->pstride * h->elem;
+    const size_t accb = h->has_contour ? (size_t)h->ch.n_slots * 6 * sizeof(double) : 0;
+    if (bytes < sizeof(hd) + dist + accb) return set_error(LBM_EM_EINVAL, "checkpoint truncated");
+    cudaSetDevice(h->dev);
+    const char *p = (const char *)buf + sizeof(hd);
+    long long tt = hd.t;
+    lbm_em_status st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (!st) st = cuda_status(cudaMemcpy(h->buf[hd.t & 1], p, dist, cudaMemcpyHostToDevice), "loading distributions");
+    if (!st && accb) st = cuda_status(cudaMemcpy(h->d_acc, p + dist, accb, cudaMemcpyHostToDevice), "loading acc");
+    if (!st)
+        st = cuda_status(cudaMemcpy(h->d_time + (hd.t & 1), &tt, sizeof(tt), cudaMemcpyHostToDevice), "loading time");
+    if (st) return st;
+    h->t = hd.t;
+    h->n_acc = hd.n_acc;
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_rasterize_janus(const lbm_em_janus *j, int32_t nx, int32_t ny, uint8_t *regions) {
+    lbm_em_status st = check_janus(j);
+    if (st) return st;
+    if (nx < 1 || ny < 1 || !regions) return set_error(LBM_EM_EINVAL, "bad size or NULL output");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return set_error(LBM_EM_ECUDA, "no CUDA device available (the solver has no CPU path)");
+    }
+    double cx, cy;
+    janus_center(j, nx, ny, &cx, &cy);
+    const int pitch = round_up(nx, 32);
+    uint8_t *d = nullptr;
+    cudaStream_t s = nullptr;
+    st = cuda_status(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!st) st = cuda_status(cudaMalloc(&d, (size_t)pitch * ny), "cudaMalloc");
+    if (!st) st = cuda_status(launch_rasterize(nx, ny, pitch, cx, cy, j->a, -std::sin(j->phi0), -std::cos(j->phi0), d, s),
+                              "rasterise kernel");
+    if (!st)
+        st = cuda_status(cudaMemcpy2DAsync(regions, nx, d, pitch, nx, ny, cudaMemcpyDeviceToHost, s), "reading regions");
+    if (!st) st = cuda_status(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    cudaFree(d);
+    if (s) cudaStreamDestroy(s);
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+// Device-side definitions shared by the lattice Boltzmann Maxwell kernels.
+//
+// TM^z reduction of the D3Q7 vector scheme (arXiv 2509.22308, Sec. III).  With
+// E = (0, 0, E_z) and H = (H_x, H_y, 0) the equilibria of
+// Eq. (equilibrium distribution functions) only feed these 16 scalars per site:
+//   e_z components of e_0, e_+z (= e_-z, stored once, weight 2), e_+x, e_-x, e_+y, e_-y
+//   h_x components of h_+x, h_-x, h_+y, h_-y, h_+z (= h_-z, weight 2)
+//   h_y components of h_+x, h_-x, h_+y, h_-y, h_+z (= h_-z, weight 2)
+// The other 26 components of the 42-scalar vector state never reach E_z, H_x, H_y
+// (h_0 = 0 because mu_r = 1; the x/y parts of e_+-z cancel in every moment).
+//
+// Storage: 16 structure-of-arrays planes, plane p of site (x, y) at
+// p * pstride + y * pitch + x.  A buffer holds the post-collision values f*(t-1);
+// the step kernel at time t pulls f_i(r, t) = f*_i(r - c_i, t - 1) ("pull" streaming),
+// so every plane is read once and written once per step.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmem {
+
+enum Plane {
+    P_E0 = 0, P_EZ, P_EPX, P_EMX, P_EPY, P_EMY,
+    P_HXPX, P_HXMX, P_HXPY, P_HXMY, P_HXZ,
+    P_HYPX, P_HYMX, P_HYPY, P_HYMY, P_HYZ,
+    NPLANES
+};
+
+enum SourceKind { SRC_OPEN = 0, SRC_HARD = 1, SRC_NONE = 2 };
+
+// Per-material constants in the kernel's arithmetic type:
+// inv_eps3 = 1/(3 eps_r) (0 for PEC: E := 0), six_em1 = 6 (eps_r - 1), inv_eps = 1/eps_r.
+template <typename T>
+struct MatT {
+    T inv_eps3, six_em1, inv_eps, pad;
+};
+
+// Left-edge source: the exact discrete plane wave of the lattice.  With
+// z = e^{-i w}, w = 2 pi / T, the +x population of e_z carries Re[P z^t] at x = 0 and
+// Re[P w z^t] at x = 1 (P, w from the dispersion relation, computed on the host).
+struct SourceParams {
+    int kind, period, ramp, pad;
+    double pr, pi;        // P
+    double qr, qi;        // P * w
+    const double2 *cs;    // cs[t mod T] = (cos w t, sin w t)
+};
+
+// Accumulation at the contour's stencil sites (Sec. III: Fourier analysis over one period).
+struct AccParams {
+    const int *slot;      // per-site slot (pitch layout), -1: not a stencil site
+    double *acc;          // 6 doubles per slot: Re/Im of E_z, H_x, H_y
+    int y0, y1;           // rows holding stencil sites
+};
+
+template <typename T>
+struct StepArgs {
+    int nx, ny, pitch, pad;
+    size_t pstride;
+    const uint8_t *mat;   // material id per site (pitch layout)
+    const MatT<T> *mtab;  // 256 entries
+    SourceParams src;
+    AccParams accp;
+    unsigned *err;        // sticky error word
+};
+
+template <typename T>
+struct Pop {
+    T e0, ez, epx, emx, epy, emy;
+    T hxpx, hxmx, hxpy, hxmy, hxz;
+    T hypx, hymx, hypy, hymy, hyz;
+};
+
+// Source values at time t: *g_open = ramp (Re[P z^t] - Re[P w z^t]) (added to the
+// extrapolated incoming population), *inc = ramp Re[P z^t] (the incident one).
+__device__ __forceinline__ void source_values(const SourceParams &s, long long t, double *g_open,
+                                              double *inc) {
+    const int tm = (int)(t % (long long)s.period);
+    const double2 c = s.cs[tm];
+    const double p0 = s.pr * c.x + s.pi * c.y;
+    const double p1 = s.qr * c.x + s.qi * c.y;
+    double ramp = 1.0;
+    if (t < (long long)s.ramp) {
+        const double v = sin(0.5 * 3.14159265358979323846 * (double)t / (double)s.ramp);
+        ramp = v * v;
+    }
+    *g_open = ramp * (p0 - p1);
+    *inc = ramp * p0;
+}
+
+// f_i(r, t) = f*_i(r - c_i, t - 1); an upstream site outside the lattice is replaced
+// by the site itself (open edge: zero-gradient copy along the population's own
+// direction); at x = 0 the +x populations also receive the source (t >= 1).
+template <typename T>
+__device__ __forceinline__ void pull_site(const StepArgs<T> &a, const T *__restrict__ f, int x,
+                                          int y, long long t, Pop<T> &p) {
+    const size_t ps = a.pstride;
+    const int xm = x > 0 ? x - 1 : 0;
+    const int xp = x < a.nx - 1 ? x + 1 : x;
+    const size_t r = (size_t)y * a.pitch;
+    const size_t rm = (size_t)(y > 0 ? y - 1 : 0) * a.pitch;
+    const size_t rp = (size_t)(y < a.ny - 1 ? y + 1 : y) * a.pitch;
+    p.e0 = f[P_E0 * ps + r + x];
+    p.ez = f[P_EZ * ps + r + x];
+    p.epx = f[P_EPX * ps + r + xm];
+    p.emx = f[P_EMX * ps + r + xp];
+    p.epy = f[P_EPY * ps + rm + x];
+    p.emy = f[P_EMY * ps + rp + x];
+    p.hxpx = f[P_HXPX * ps + r + xm];
+    p.hxmx = f[P_HXMX * ps + r + xp];
+    p.hxpy = f[P_HXPY * ps + rm + x];
+    p.hxmy = f[P_HXMY * ps + rp + x];
+    p.hxz = f[P_HXZ * ps + r + x];
+    p.hypx = f[P_HYPX * ps + r + xm];
+    p.hymx = f[P_HYMX * ps + r + xp];
+    p.hypy = f[P_HYPY * ps + rm + x];
+    p.hymy = f[P_HYMY * ps + rp + x];
+    p.hyz = f[P_HYZ * ps + r + x];
+    if (x == 0 && t >= 1 && a.src.kind != SRC_NONE) {
+        double g, inc;
+        source_values(a.src, t, &g, &inc);
+        if (a.src.kind == SRC_OPEN) {
+            p.epx += (T)g;
+            p.hypx -= (T)g;
+        } else {
+            p.epx = (T)inc;
+            p.hxpx = (T)0;
+            p.hypx = (T)(-inc);
+        }
+    }
+}
+
+// Moments (Sec. III): D = sum e_i (the +-z pair twice), E_z = D / eps_r, H = sum h_i.
+// Returns E_z/3 (the scale every equilibrium uses) and H_x, H_y.
+template <typename T>
+__device__ __forceinline__ void moments(const Pop<T> &p, T inv_eps3, T *E3, T *Hx, T *Hy, T *D) {
+    const T d = p.e0 + p.epx + p.emx + p.epy + p.emy + (T)2 * p.ez;
+    *D = d;
+    *E3 = d * inv_eps3;
+    *Hx = p.hxpx + p.hxmx + p.hxpy + p.hxmy + (T)2 * p.hxz;
+    *Hy = p.hypx + p.hymx + p.hypy + p.hymy + (T)2 * p.hyz;
+}
+
+// Post-collision f* = 2 f^eq - f (Eq. LBGK equation), with 2 f^eq written out from
+// Eq. (equilibrium distribution functions) for the TM^z components:
+//   e_z:  +x (E-H_y)/3, -x (E+H_y)/3, +y (E+H_x)/3, -y (E-H_x)/3, z E/3, rest 2(eps-1)E
+//   h_x:  +-x H_x/3, +y (H_x+E)/3, -y (H_x-E)/3, z H_x/3
+//   h_y:  +x (H_y-E)/3, -x (H_y+E)/3, +-y H_y/3, z H_y/3
+template <typename T>
+__device__ __forceinline__ void collide(Pop<T> &p, T E3, T Hx, T Hy, T six_em1) {
+    const T third = (T)(1.0 / 3.0);
+    const T hx3 = Hx * third, hy3 = Hy * third;
+    const T A = E3 - hy3, B = E3 + hy3, C = E3 + hx3, D = E3 - hx3;
+    p.e0 = six_em1 * E3 - p.e0;
+    p.ez = E3 - p.ez;
+    p.epx = A - p.epx;
+    p.emx = B - p.emx;
+    p.epy = C - p.epy;
+    p.emy = D - p.emy;
+    p.hxpx = hx3 - p.hxpx;
+    p.hxmx = hx3 - p.hxmx;
+    p.hxpy = C - p.hxpy;
+    p.hxmy = -D - p.hxmy;
+    p.hxz = hx3 - p.hxz;
+    p.hypx = -A - p.hypx;
+    p.hymx = B - p.hymx;
+    p.hypy = hy3 - p.hypy;
+    p.hymy = hy3 - p.hymy;
+    p.hyz = hy3 - p.hyz;
+}
+
+// |E_z/3| >= 2^20 or non-finite, tested on the exponent bits (integer ALU only).
+__device__ __forceinline__ bool field_runaway(double e3) {
+    return (unsigned)(__double2hiint(e3) & 0x7ff00000) >= 0x41300000u;
+}
+__device__ __forceinline__ bool field_runaway(float e3) {
+    return (__float_as_uint(e3) & 0x7f800000u) >= ((127u + 20u) << 23);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_site(T *__restrict__ f, size_t ps, size_t idx, const Pop<T> &p) {
+    f[P_E0 * ps + idx] = p.e0;
+    f[P_EZ * ps + idx] = p.ez;
+    f[P_EPX * ps + idx] = p.epx;
+    f[P_EMX * ps + idx] = p.emx;
+    f[P_EPY * ps + idx] = p.epy;
+    f[P_EMY * ps + idx] = p.emy;
+    f[P_HXPX * ps + idx] = p.hxpx;
+    f[P_HXMX * ps + idx] = p.hxmx;
+    f[P_HXPY * ps + idx] = p.hxpy;
+    f[P_HXMY * ps + idx] = p.hxmy;
+    f[P_HXZ * ps + idx] = p.hxz;
+    f[P_HYPX * ps + idx] = p.hypx;
+    f[P_HYMX * ps + idx] = p.hymx;
+    f[P_HYPY * ps + idx] = p.hypy;
+    f[P_HYMY * ps + idx] = p.hymy;
+    f[P_HYZ * ps + idx] = p.hyz;
+}
+
+// Contour sample: four stencil slots with bilinear weights, outward normal.
+struct ContourPt {
+    int s[4];
+    double w[4];
+    double nx, ny;
+};
+
+// ---- host-side launchers (defined in the .cu files) ----------------------------------
+template <typename T>
+cudaError_t launch_step(const StepArgs<T> &a, const T *fin, T *fout, const long long *t_in,
+                        long long *t_out, bool accumulate, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fields(const StepArgs<T> &a, const T *f, const long long *t_dev, double *ez,
+                          double *hx, double *hy, cudaStream_t s);
+cudaError_t launch_rasterize(int nx, int ny, int pitch, double cx, double cy, double a,
+                             double ndx, double ndy, uint8_t *ids, cudaStream_t s);
+cudaError_t launch_contour(const double *acc, double scale, const ContourPt *pts, int npts,
+                           double R, double dl, double F0, double M0, double *out, cudaStream_t s);
+
+}  // namespace lbmem

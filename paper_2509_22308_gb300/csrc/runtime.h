@@ -1,0 +1,35 @@
+// Host-side helpers shared by the single-domain and the batched runtimes.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/lbm_em.h"
+#include "common.cuh"
+
+namespace lbmem {
+
+extern thread_local std::string g_last_error;
+lbm_em_status set_error(lbm_em_status st, const std::string &msg);
+lbm_em_status cuda_status(cudaError_t e, const char *what);
+
+// Constants of the exact discrete incident plane wave for period T (see common.cuh).
+void incident_constants(int period, double E0, double *pr, double *pi, double *qr, double *qi);
+// (cos w t, sin w t) for t = 0..T-1, w = 2 pi / T.
+std::vector<double2> phase_table(int period);
+
+lbm_em_status check_source(const lbm_em_source *s);
+lbm_em_status check_janus(const lbm_em_janus *j);
+void janus_center(const lbm_em_janus *j, int nx, int ny, double *cx, double *cy);
+int round_up(int v, int m);
+
+// Circle contour in lattice coordinates with its unique stencil sites.
+struct ContourHost {
+    double E0 = 1.0, R = 0.0, dl = 0.0, F0 = 1.0, M0 = 1.0;
+    std::vector<ContourPt> pts;
+    std::vector<int> site_xy;  // 2 per slot
+    int n_slots = 0, y0 = 0, y1 = -1;
+};
+lbm_em_status build_contour(int nx, int ny, const lbm_em_contour *c, ContourHost *out);
+
+}  // namespace lbmem

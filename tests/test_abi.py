@@ -1,0 +1,64 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol the header
+declares; without a GPU it refuses to run (there is no CPU fallback)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm_em.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_em_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2509_22308_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbm_em_create", "lbm_em_step", "lbm_em_force_torque", "lbm_em_batch_create",
+                     "lbm_em_batch_run", "lbm_em_batch_results", "lbm_em_destroy", "lbm_em_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"missing export {name}"
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2509_22308_gb300 import lbm_em
+    names = set(declared_functions()) - {"lbm_em_last_error"}
+    assert names == set(lbm_em.SIGNATURES)
+
+
+def test_no_cpu_fallback_without_gpu(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2509_22308_gb300 import lbm_em
+    with pytest.raises(lbm_em.LbmEmError) as e:
+        lbm_em.Solver(32, 32, "f64", janus=lbm_em.make_janus(5, 0.3, 2.0), source=lbm_em.make_source(24))
+    assert e.value.status == lbm_em.ECUDA
+
+
+def test_argument_validation_needs_no_gpu(lib):
+    from paper_2509_22308_gb300 import lbm_em
+    with pytest.raises(lbm_em.LbmEmError) as e:
+        lbm_em.Solver(32, 32, "f64", janus=lbm_em.make_janus(-1, 0.3, 2.0), source=lbm_em.make_source(24))
+    assert e.value.status == lbm_em.EINVAL
+    with pytest.raises(lbm_em.LbmEmError) as e:
+        lbm_em.Solver(32, 32, "f64", janus=lbm_em.make_janus(5, 0.3, 0.5), source=lbm_em.make_source(24))
+    assert e.value.status == lbm_em.EINVAL
+    with pytest.raises(lbm_em.LbmEmError) as e:
+        lbm_em.Solver(32, 32, "f64", janus=lbm_em.make_janus(5, 0.3, 2.0), source=lbm_em.make_source(2))
+    assert e.value.status == lbm_em.EINVAL
