@@ -30,8 +30,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS & HBM GB/s (% of peak) per precision form; design-map cells/sec at <=1e-3 force err"
 WORKLOAD = "md_janus_512"
-BYTES_PER_LU = {"f64": 16 * 8 * 2 + 1, "f32": 16 * 4 * 2 + 1}
-STEP_KERNEL = {"f64": "k_step<double, false>", "f32": "k_step<float, false>"}
+BYTES_PER_LU = {"f64": 16 * 8 * 2 + 1, "f32": 16 * 4 * 2 + 1, "f16dev": 2 * (16 * 2 + 3 * 4) + 1}
+STEP_KERNEL = {"f64": "k_step<double, false>", "f32": "k_step<float, false>", "f16dev": "k_step_f16<false>"}
+# FP64 pipe operations per lattice update of the step kernel: 16 for the moments
+# (sums of 6, 5 and 5 populations, one scaling), 20 for the equilibria and 2 f^eq - f
+FP64_OPS_PER_LU = 36
+SMS, FP64_OPS_PER_CLK_PER_SM = 152, 2
 
 
 def parse_args():
@@ -40,7 +44,12 @@ def parse_args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    p.add_argument("--precision", default="f64", choices=["f64", "f32", "f16dev"])
+    p.add_argument("--no-hbm-scale", action="store_true")
+    p.add_argument("--no-design-map", action="store_true")
+    p.add_argument("--design-map-instances", type=int, default=24)
+    p.add_argument("--profile-case", action="store_true",
+                   help="small case for ncu: a 2048^2 MD-Janus lattice, 2 steps per storage form, then exit")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -193,6 +202,23 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def profile_case():
+    """Two launches of each storage form's step kernel on a 2048^2 lattice (state
+    0.27-1.1 GB per buffer, larger than L2, a few GB on the device in total)."""
+    import torch
+    from paper_2509_22308_gb300 import build as B
+    B.build()
+    from paper_2509_22308_gb300 import lbm_em as L
+    inst = dict(nx=2048, ny=2048, a=128.0, phi0=0.5, eps1=4.0, eps2=1.0, pec2=True, period=240, periods=1,
+                R=192.0, ramp=240)
+    for fp in ("f64", "f32", "f16dev"):
+        with L.solver_for_instance(inst, fp) as s:
+            s.step(2)
+            s.sync()
+    torch.cuda.synchronize()
+    print("profile case done")
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", 0))
@@ -200,6 +226,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.profile_case:
+        profile_case()
         return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -283,11 +312,29 @@ def main():
     achieved = plain_bytes / (plain_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     traffic = profiled_traffic(prec)
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": STEP_KERNEL[prec], "peak_source": f"{peak_kind} copy bandwidth",
-                "algorithmic_bytes_per_launch": 512 * 512 * BYTES_PER_LU[prec],
-                "avg_launch_us": round(avg_launch_us, 3)}
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    if prec == "f64":
+        # the FP64 step is bound by the FP64 pipe: 2 FP64 operations per clock per SM
+        ops = sum(n * sites for _, _, n, sites in plain) * FP64_OPS_PER_LU
+        achieved_t = ops / (plain_ms / 1e3) / 1e12
+        peak_t = SMS * FP64_OPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
+        roofline = {"bound": "alu", "achieved": round(achieved_t, 4), "peak": round(peak_t, 4), "unit": "TFLOP/s",
+                    "frac": round(achieved_t / peak_t, 4), "traffic": traffic, "kernel": STEP_KERNEL[prec],
+                    "flop_convention": f"FP64 pipe operations (add, multiply or FMA = 1), {FP64_OPS_PER_LU} per "
+                                       "lattice update",
+                    "peak_source": f"derived: {SMS} SMs x {FP64_OPS_PER_CLK_PER_SM} FP64 ops/clk x median SM clock "
+                                   f"{sm_mhz:.0f} MHz",
+                    "algorithmic_ops_per_launch": 512 * 512 * FP64_OPS_PER_LU,
+                    "avg_launch_us": round(avg_launch_us, 3),
+                    "hbm_view": {"achieved_gbs": round(achieved, 1), "peak_gbs": peak,
+                                 "frac": round(achieved / peak, 4),
+                                 "algorithmic_bytes_per_launch": 512 * 512 * BYTES_PER_LU[prec]}}
+    else:
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": traffic,
+                    "kernel": STEP_KERNEL[prec], "peak_source": f"{peak_kind} copy bandwidth",
+                    "algorithmic_bytes_per_launch": 512 * 512 * BYTES_PER_LU[prec],
+                    "avg_launch_us": round(avg_launch_us, 3)}
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
@@ -340,10 +387,10 @@ def main():
 
     if not args.no_forms and rank == 0:
         forms = {}
-        for fp in ("f32", "f64"):
+        for fp in ("f32", "f16dev", "f64"):
             if fp == prec:
-                forms[fp] = {"mlups": out["value"] / world, "step_kernel_gbs": roofline["achieved"],
-                             "frac": roofline["frac"]}
+                forms[fp] = {"mlups": out["value"] / world, "step_kernel_gbs": round(achieved, 1),
+                             "frac_hbm": round(achieved / peak, 4)}
                 continue
             ss = [L.solver_for_instance(inst, fp, stream) for inst in instances]
             ev = []
@@ -369,12 +416,68 @@ def main():
             drag = np.abs(ref[:, 0])
             err = np.abs(res - ref) / drag[:, None]
             forms[fp] = {"mlups": round(lus_per_step / (ms / 1e3) / 1e6, 1), "step_kernel_gbs": round(gbs, 1),
-                         "frac": round(gbs / peak, 4),
+                         "frac_hbm": round(gbs / peak, 4),
                          "max_drag_err_rel": float(err[:, 0].max()),
                          "max_lift_torque_err_drag_scale": float(err[:, 1:].max())}
             for s in ss:
                 s.close()
         out["forms"] = forms
+
+    if not args.no_hbm_scale and rank == 0:
+        # single-domain step kernel on an 8192^2 lattice (state far larger than the
+        # 129 MB L2): algorithmic bytes per launch / CUDA-event time per launch
+        big = W.md_janus_8192()[0]
+        hs = {}
+        for fp in ("f32", "f16dev", "f64"):
+            with L.solver_for_instance(big, fp, stream) as s:
+                s.step(4)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                n = 16
+                a.record(stream)
+                s.step(n)
+                b.record(stream)
+                b.synchronize()
+                us = a.elapsed_time(b) * 1e3 / n
+                sites = big["nx"] * big["ny"]
+                gbs = sites * BYTES_PER_LU[fp] / (us / 1e6) / 1e9
+                hs[fp] = {"kernel": STEP_KERNEL[fp], "us_per_launch": round(us, 2),
+                          "glups": round(sites / (us / 1e6) / 1e9, 2), "achieved_gbs": round(gbs, 1),
+                          "frac_hbm": round(gbs / peak, 4), "bytes_per_lu": BYTES_PER_LU[fp]}
+                if fp == "f64":
+                    t_ops = sites * FP64_OPS_PER_LU / (us / 1e6) / 1e12
+                    hs[fp]["fp64_tops"] = round(t_ops, 4)
+                    hs[fp]["frac_fp64_pipe"] = round(t_ops / (SMS * FP64_OPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12), 4)
+        out["single_domain_8192"] = hs
+
+    if not args.no_design_map and rank == 0:
+        # batched design diagram: seeded dielectric Janus instances, uneven sizes
+        # (a in {16, 32, 64}, grid 16 a) and run lengths (20 periods of T = 3 a),
+        # one persistent kernel under a CUDA graph; FP32 lattice, FP64 accumulation,
+        # force error against the same batch in FP64
+        dm = W.design_map_256(4, args.design_map_instances)
+        res = {}
+        for fp in ("f32", "f64"):
+            bt = L.Batch(dm, fp, stream=stream)
+            bt.run()
+            bt.results()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bt.run()
+            b.record(stream)
+            b.synchronize()
+            F, _ = bt.results()
+            res[fp] = (a.elapsed_time(b), F, bt.config())
+            bt.close()
+        ms32, F32, cfg = res["f32"]
+        ms64, F64, _ = res["f64"]
+        err = np.max(np.abs(F32 - F64) / np.abs(F64[:, :1]))
+        lus = sum(instance_lus(i) for i in dm)
+        out["design_map"] = {"instances": len(dm), "cells_per_s": round(len(dm) / (ms32 / 1e3), 2),
+                             "mlups": round(lus / (ms32 / 1e3) / 1e6, 1), "ms": round(ms32, 1),
+                             "fp64_cells_per_s": round(len(dm) / (ms64 / 1e3), 2),
+                             "max_force_err_drag_scale": float(err),
+                             "tile_w": cfg[0], "tile_h": cfg[1], "ctas_per_sm": cfg[2],
+                             "precision": "f32 lattice, f64 accumulation"}
 
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(instances[0], args.cpu_seconds)

@@ -15,6 +15,7 @@
 #include "../../include/lbm_em.h"
 #include "common.cuh"
 #include "runtime.h"
+#include "step_f16.cuh"
 
 using namespace lbmem;
 
@@ -140,7 +141,7 @@ lbm_em_status build_contour(int nx, int ny, const lbm_em_contour *c, ContourHost
 struct lbm_em {
     int dev = 0;
     int nx = 0, ny = 0, pitch = 0, prec = 0;
-    size_t pstride = 0, elem = 0;
+    size_t pstride = 0, elem = 0, buf_bytes = 0;
     cudaStream_t stream = nullptr, cap = nullptr;
     bool own_stream = false;
     void *buf[2] = {nullptr, nullptr};
@@ -188,8 +189,39 @@ static StepArgs<T> make_args(const lbm_em *h) {
     return a;
 }
 
+static F16Args make_f16_args(const lbm_em *h, int p) {
+    F16Args a{};
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.pitch = h->pitch;
+    a.pstride = h->pstride;
+    a.mat = h->d_mat;
+    a.mtab = (const MatT<float> *)h->d_mtab;
+    a.src = h->src;
+    a.accp.slot = h->d_slot;
+    a.accp.acc = h->d_acc;
+    a.accp.y0 = h->ch.y0;
+    a.accp.y1 = h->ch.y1;
+    a.err = h->d_err;
+    a.scale = kF16Scale;
+    a.inv_scale = 1.0f / kF16Scale;
+    const size_t hb = f16_half_bytes(h->pstride), fb = f16_plane_bytes(h->pstride);
+    char *in = (char *)h->buf[p], *out = (char *)h->buf[1 - p];
+    a.g = (const __half *)in;
+    a.fe = (const float *)(in + hb);
+    a.fhx = (const float *)(in + hb + fb);
+    a.fhy = (const float *)(in + hb + 2 * fb);
+    a.g_out = (__half *)out;
+    a.fe_out = (float *)(out + hb);
+    a.fhx_out = (float *)(out + hb + fb);
+    a.fhy_out = (float *)(out + hb + 2 * fb);
+    return a;
+}
+
 static cudaError_t enqueue_step(lbm_em *h, bool acc, cudaStream_t s, int64_t t) {
     const int p = (int)(t & 1);
+    if (h->prec == LBM_EM_F16DEV)
+        return launch_step_f16(make_f16_args(h, p), h->d_time + p, h->d_time + (1 - p), acc, s);
     if (h->prec == LBM_EM_F64)
         return launch_step<double>(make_args<double>(h), (const double *)h->buf[p], (double *)h->buf[1 - p],
                                    h->d_time + p, h->d_time + (1 - p), acc, s);
@@ -287,8 +319,8 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     *out = nullptr;
     if (g->nx < 4 || g->ny < 4) return set_error(LBM_EM_EINVAL, "nx and ny must be >= 4");
     if ((long long)g->nx * g->ny > (1LL << 31)) return set_error(LBM_EM_EINVAL, "lattice too large (> 2^31 sites)");
-    if (g->precision != LBM_EM_F64 && g->precision != LBM_EM_F32)
-        return set_error(LBM_EM_EINVAL, "precision not supported by this build");
+    if (g->precision != LBM_EM_F64 && g->precision != LBM_EM_F32 && g->precision != LBM_EM_F16DEV)
+        return set_error(LBM_EM_EINVAL, "precision must be LBM_EM_F64, LBM_EM_F32 or LBM_EM_F16DEV");
     lbm_em_status st = check_source(s);
     if (st) return st;
     int ndev = 0;
@@ -324,7 +356,9 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
         h->own_stream = true;
     }
     TRY(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
-    const size_t bytes = (size_t)NPLANES * h->pstride * h->elem;
+    h->buf_bytes = g->precision == LBM_EM_F16DEV ? f16_buffer_bytes(h->pstride)
+                                                  : (size_t)NPLANES * h->pstride * h->elem;
+    const size_t bytes = h->buf_bytes;
     for (int b = 0; b < 2; ++b) {
         TRY(cudaMalloc(&h->buf[b], bytes), "cudaMalloc(distributions)");
         TRY(cudaMemsetAsync(h->buf[b], 0, bytes, h->stream), "cudaMemset");
@@ -452,8 +486,7 @@ lbm_em_status lbm_em_create_janus(const lbm_em_grid *g, const lbm_em_janus *j, c
 lbm_em_status lbm_em_reset(lbm_em_t *h) {
     if (!h) return set_error(LBM_EM_EINVAL, "handle is NULL");
     cudaSetDevice(h->dev);
-    const size_t bytes = (size_t)NPLANES * h->pstride * h->elem;
-    lbm_em_status st = cuda_status(cudaMemsetAsync(h->buf[0], 0, bytes, h->stream), "clearing distributions");
+    lbm_em_status st = cuda_status(cudaMemsetAsync(h->buf[0], 0, h->buf_bytes, h->stream), "clearing distributions");
     if (!st) st = cuda_status(cudaMemsetAsync(h->d_time, 0, 2 * sizeof(long long), h->stream), "clearing time");
     if (!st) st = cuda_status(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream), "clearing error flag");
     if (!st && h->has_contour)
@@ -601,7 +634,10 @@ lbm_em_status lbm_em_get_fields(lbm_em_t *h, double *ez, double *hx, double *hy)
     if (st) return st;
     const int p = (int)(h->t & 1);
     cudaError_t e;
-    if (h->prec == LBM_EM_F64)
+    if (h->prec == LBM_EM_F16DEV)
+        e = launch_fields_f16(make_f16_args(h, p), h->d_time + p, h->d_fields, h->d_fields + n,
+                              h->d_fields + 2 * n, h->stream);
+    else if (h->prec == LBM_EM_F64)
         e = launch_fields<double>(make_args<double>(h), (const double *)h->buf[p], h->d_time + p, h->d_fields,
                                   h->d_fields + n, h->d_fields + 2 * n, h->stream);
     else
@@ -661,7 +697,7 @@ static const uint64_t kMagic = 0x4c424d454d535431ULL;
 
 lbm_em_status lbm_em_save_state(lbm_em_t *h, void *buf, size_t *bytes) {
     if (!h || !bytes) return set_error(LBM_EM_EINVAL, "NULL argument");
-    const size_t dist = (size_t)NPLANES * h->pstride * h->elem;
+    const size_t dist = h->buf_bytes;
     const size_t accb = h->has_contour ? (size_t)h->ch.n_slots * 6 * sizeof(double) : 0;
     const size_t need = sizeof(StateHeader) + dist + accb;
     if (!buf) {
@@ -691,7 +727,7 @@ lbm_em_status lbm_em_load_state(lbm_em_t *h, const void *buf, size_t bytes) {
         return set_error(LBM_EM_EINVAL, "checkpoint does not match this handle");
     const int want_slots = h->has_contour ? h->ch.n_slots : -1;
     if (hd.n_slots != want_slots) return set_error(LBM_EM_EINVAL, "checkpoint contour does not match");
-    const size_t dist = (size_t)NPLANES * h->pstride * h->elem;
+    const size_t dist = h->buf_bytes;
     const size_t accb = h->has_contour ? (size_t)h->ch.n_slots * 6 * sizeof(double) : 0;
     if (bytes < sizeof(hd) + dist + accb) return set_error(LBM_EM_EINVAL, "checkpoint truncated");
     cudaSetDevice(h->dev);

@@ -1,24 +1,556 @@
-// Batched design diagrams: packed multi-domain layout and persistent step kernel.
+// Batched design diagrams (the force/torque maps of arXiv 2509.22308, Sec. IV.A-B):
+// many Janus instances of uneven size and run length advance together.
+//
+// Layout: every instance keeps its own 16 structure-of-arrays planes (pitch rounded
+// to 32 sites), packed one after another in two ping-pong buffers; material ids,
+// contour slot maps and Fourier accumulators are packed the same way.  A tile list
+// covers every instance with tile_w x tile_h tiles, ordered by decreasing run length,
+// so at any time the tiles still running form a prefix of the list.
+//
+// Kernel: a persistent grid (ctas_per_sm x SMs) walks the tile list with a grid
+// stride once per time step, running the same per-site pull / moments / collide as
+// the single-domain step; a tile whose instance has finished is skipped, a tile in
+// its instance's last period also accumulates the Fourier sums.  Two steps are
+// captured in a CUDA graph and replayed; time comes from the device words as in the
+// single-domain path.  Tile shape and CTAs per SM are chosen by timing a few steps of
+// each candidate on the actual packed data (then the state is cleared).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
 #include "../../include/lbm_em.h"
+#include "common.cuh"
 #include "runtime.h"
 
 using namespace lbmem;
 
-struct lbm_em_batch {
-    int n;
+namespace lbmem {
+
+struct InstDesc {
+    int nx, ny, pitch, period;
+    size_t pstride, base, mat_base, slot_base;
+    long long steps, acc_from;
+    int acc_base, y0, y1, pad;
+    SourceParams src;
+    double mtab[3][3];  // per region id: inv_eps3, six_em1, inv_eps
 };
+
+struct Tile {
+    int inst, x0, y0, pad;
+};
+
+template <typename T>
+struct BatchArgs {
+    const InstDesc *inst;
+    const Tile *tiles;
+    int n_tiles, tile_w, tile_h, pad;
+    const T *fin;
+    T *fout;
+    const uint8_t *mat;
+    const int *slot;
+    double *acc;
+    unsigned *err;  // one word per instance
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_batch_step(const BatchArgs<T> b, const long long *__restrict__ t_in,
+                                                    long long *__restrict__ t_out) {
+    const long long t = *t_in;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + 1;
+    __shared__ MatT<T> smat[3];
+    const int tsz = b.tile_w * b.tile_h;
+    for (int tile = blockIdx.x; tile < b.n_tiles; tile += gridDim.x) {
+        const Tile tl = b.tiles[tile];
+        const InstDesc &d = b.inst[tl.inst];
+        const long long steps = d.steps;
+        if (t >= steps) continue;  // uniform over the block
+        const bool acc = t >= d.acc_from;
+        __syncthreads();
+        if (threadIdx.x < 3)
+            smat[threadIdx.x] = MatT<T>{(T)d.mtab[threadIdx.x][0], (T)d.mtab[threadIdx.x][1],
+                                        (T)d.mtab[threadIdx.x][2], (T)0};
+        __syncthreads();
+        StepArgs<T> a;
+        a.nx = d.nx;
+        a.ny = d.ny;
+        a.pitch = d.pitch;
+        a.pstride = d.pstride;
+        a.src = d.src;
+        const T *fin = b.fin + d.base;
+        T *fout = b.fout + d.base;
+        const uint8_t *mat = b.mat + d.mat_base;
+        for (int k = threadIdx.x; k < tsz; k += blockDim.x) {
+            const int x = tl.x0 + k % b.tile_w, y = tl.y0 + k / b.tile_w;
+            if (x >= d.nx || y >= d.ny) continue;
+            Pop<T> p;
+            pull_site(a, fin, x, y, t, p);
+            const size_t idx = (size_t)y * d.pitch + x;
+            const MatT<T> m = smat[mat[idx]];
+            T E3, Hx, Hy, D;
+            moments(p, m.inv_eps3, &E3, &Hx, &Hy, &D);
+            if (field_runaway(E3)) atomicOr(b.err + tl.inst, 1u);
+            if (acc && y >= d.y0 && y <= d.y1) {
+                const int s = b.slot[d.slot_base + idx];
+                if (s >= 0) {
+                    const double2 c = d.src.cs[(int)(t % (long long)d.period)];
+                    const double ez = (double)(D * m.inv_eps), hx = (double)Hx, hy = (double)Hy;
+                    double *q = b.acc + 6 * ((size_t)d.acc_base + s);
+                    q[0] += ez * c.x;
+                    q[1] += ez * c.y;
+                    q[2] += hx * c.x;
+                    q[3] += hx * c.y;
+                    q[4] += hy * c.x;
+                    q[5] += hy * c.y;
+                }
+            }
+            collide(p, E3, Hx, Hy, m.six_em1);
+            store_site(fout, d.pstride, idx, p);
+        }
+    }
+}
+
+// Per-instance stress-tensor integral: block i reduces instance i's contour.
+struct ContourDesc {
+    int pt_base, npts, acc_base, pad;
+    double scale, R, dl, F0, M0;
+};
+
+__device__ __forceinline__ double wsum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_batch_contour(const ContourDesc *__restrict__ cd,
+                                                       const ContourPt *__restrict__ pts,
+                                                       const double *__restrict__ acc, double *out) {
+    const ContourDesc c = cd[blockIdx.x];
+    const double *A = acc + 6 * (size_t)c.acc_base;
+    double fx = 0.0, fy = 0.0, mz = 0.0;
+    for (int k = threadIdx.x; k < c.npts; k += blockDim.x) {
+        const ContourPt p = pts[c.pt_base + k];
+        double v[6] = {0, 0, 0, 0, 0, 0};
+        for (int q = 0; q < 4; ++q)
+            for (int j = 0; j < 6; ++j) v[j] += p.w[q] * A[6 * (size_t)p.s[q] + j];
+        for (int j = 0; j < 6; ++j) v[j] *= c.scale;
+        const double e2 = v[0] * v[0] + v[1] * v[1];
+        const double hx2 = v[2] * v[2] + v[3] * v[3];
+        const double hy2 = v[4] * v[4] + v[5] * v[5];
+        const double tr = 0.5 * (e2 + hx2 + hy2);
+        const double txx = 0.5 * (hx2 - tr), tyy = 0.5 * (hy2 - tr);
+        const double txy = 0.5 * (v[2] * v[4] + v[3] * v[5]);
+        const double tnx = txx * p.nx + txy * p.ny, tny = txy * p.nx + tyy * p.ny;
+        fx += tnx;
+        fy += tny;
+        mz += c.R * (p.nx * tny - p.ny * tnx);
+    }
+    __shared__ double sh[3][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    fx = wsum(fx);
+    fy = wsum(fy);
+    mz = wsum(mz);
+    if (lane == 0) {
+        sh[0][wid] = fx;
+        sh[1][wid] = fy;
+        sh[2][wid] = mz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double F[3] = {0, 0, 0};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            for (int j = 0; j < 3; ++j) F[j] += sh[j][w];
+        out[3 * blockIdx.x + 0] = F[0] * c.dl / c.F0;
+        out[3 * blockIdx.x + 1] = F[1] * c.dl / c.F0;
+        out[3 * blockIdx.x + 2] = F[2] * c.dl / c.M0;
+    }
+}
+
+}  // namespace lbmem
+
+struct lbm_em_batch {
+    int dev = 0, n = 0, prec = LBM_EM_F32, sms = 0;
+    size_t elem = 4;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    bool own_stream = false;
+    std::vector<lbm_em_instance> specs;
+    std::vector<InstDesc> desc;
+    std::vector<long long> order;  // instance indices by decreasing steps
+    long long max_steps = 0;
+    void *buf[2] = {nullptr, nullptr};
+    size_t buf_elems = 0, mat_bytes = 0, slot_elems = 0, acc_slots = 0;
+    uint8_t *d_mat = nullptr;
+    int *d_slot = nullptr;
+    double *d_acc = nullptr, *d_out = nullptr;
+    double2 *d_cs = nullptr;
+    InstDesc *d_desc = nullptr;
+    Tile *d_tiles = nullptr;
+    int n_tiles = 0;
+    ContourDesc *d_cdesc = nullptr;
+    ContourPt *d_pts = nullptr;
+    long long *d_time = nullptr;
+    unsigned *d_err = nullptr;
+    int tile_w = 0, tile_h = 0, ctas = 0;
+    cudaGraphExec_t graph = nullptr;
+    bool ran = false;
+};
+
+static void batch_free(lbm_em_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->dev);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->buf[0]);
+    cudaFree(b->buf[1]);
+    cudaFree(b->d_mat);
+    cudaFree(b->d_slot);
+    cudaFree(b->d_acc);
+    cudaFree(b->d_out);
+    cudaFree(b->d_cs);
+    cudaFree(b->d_desc);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_cdesc);
+    cudaFree(b->d_pts);
+    cudaFree(b->d_time);
+    cudaFree(b->d_err);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+static lbm_em_status batch_tiles(lbm_em_batch *b, int tw, int th) {
+    std::vector<Tile> tiles;
+    for (long long ii : b->order) {
+        const int i = (int)ii;
+        const InstDesc &d = b->desc[i];
+        for (int y0 = 0; y0 < d.ny; y0 += th)
+            for (int x0 = 0; x0 < d.nx; x0 += tw) tiles.push_back(Tile{i, x0, y0, 0});
+    }
+    cudaFree(b->d_tiles);
+    b->d_tiles = nullptr;
+    lbm_em_status st = cuda_status(cudaMalloc(&b->d_tiles, tiles.size() * sizeof(Tile)), "cudaMalloc(tiles)");
+    if (!st)
+        st = cuda_status(cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice),
+                         "uploading tiles");
+    b->n_tiles = (int)tiles.size();
+    b->tile_w = tw;
+    b->tile_h = th;
+    return st;
+}
+
+static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, long long t) {
+    const int p = (int)(t & 1);
+    const int grid = b->ctas * b->sms;
+    if (b->prec == LBM_EM_F64) {
+        BatchArgs<double> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, 0,
+                            (const double *)b->buf[p], (double *)b->buf[1 - p], b->d_mat, b->d_slot,
+                            b->d_acc, b->d_err};
+        k_batch_step<double><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
+    } else {
+        BatchArgs<float> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, 0,
+                           (const float *)b->buf[p], (float *)b->buf[1 - p], b->d_mat, b->d_slot,
+                           b->d_acc, b->d_err};
+        k_batch_step<float><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
+    }
+    return cudaGetLastError();
+}
+
+static lbm_em_status batch_clear(lbm_em_batch *b) {
+    lbm_em_status st = cuda_status(cudaMemsetAsync(b->buf[0], 0, b->buf_elems * b->elem, b->stream), "clear");
+    if (!st) st = cuda_status(cudaMemsetAsync(b->d_acc, 0, b->acc_slots * 6 * sizeof(double), b->stream), "clear");
+    if (!st) st = cuda_status(cudaMemsetAsync(b->d_time, 0, 2 * sizeof(long long), b->stream), "clear");
+    if (!st) st = cuda_status(cudaMemsetAsync(b->d_err, 0, b->n * sizeof(unsigned), b->stream), "clear");
+    return st;
+}
+
+// Time a few steps of each (tile shape, CTAs per SM) candidate from the cleared state.
+static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int want_c) {
+    struct Cand {
+        int w, h, c;
+    };
+    std::vector<Cand> cands;
+    const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 8}, {128, 4}, {256, 2}, {128, 8}, {256, 4}};
+    const int ctas[] = {2, 4, 8};
+    for (auto &sh : shapes)
+        for (int c : ctas) {
+            if (want_w && sh[0] != want_w) continue;
+            if (want_h && sh[1] != want_h) continue;
+            if (want_c && c != want_c) continue;
+            cands.push_back(Cand{sh[0], sh[1], c});
+        }
+    if (cands.empty()) cands.push_back(Cand{want_w ? want_w : 64, want_h ? want_h : 4, want_c ? want_c : 4});
+    if (cands.size() == 1) {
+        b->ctas = cands[0].c;
+        return batch_tiles(b, cands[0].w, cands[0].h);
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    Cand bc = cands[0];
+    const int trial = 4;
+    lbm_em_status st = LBM_EM_OK;
+    for (const Cand &c : cands) {
+        st = batch_tiles(b, c.w, c.h);
+        if (st) break;
+        b->ctas = c.c;
+        st = batch_clear(b);
+        if (st) break;
+        cudaError_t e = batch_launch(b, b->stream, 0);  // warm-up
+        cudaEventRecord(e0, b->stream);
+        for (int k = 1; k <= trial && e == cudaSuccess; ++k) e = batch_launch(b, b->stream, k);
+        cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        st = cuda_status(e, "autotune launch");
+        if (st) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bc = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    b->ctas = bc.c;
+    st = batch_tiles(b, bc.w, bc.h);
+    if (!st) st = batch_clear(b);
+    return st;
+}
 
 extern "C" {
 
-lbm_em_status lbm_em_batch_create(const lbm_em_instance *, int32_t, const lbm_em_batch_opts *, lbm_em_batch_t **out) {
-    if (out) *out = nullptr;
-    return set_error(LBM_EM_ESTATE, "batched runs are not available in this build yet");
+lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const lbm_em_batch_opts *o,
+                                  lbm_em_batch_t **out) {
+    if (!specs || n <= 0 || !o || !out) return set_error(LBM_EM_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    if (o->precision != LBM_EM_F32 && o->precision != LBM_EM_F64)
+        return set_error(LBM_EM_EINVAL, "batch precision must be LBM_EM_F32 or LBM_EM_F64");
+    if (o->tile_w < 0 || o->tile_h < 0 || o->ctas_per_sm < 0 || o->ctas_per_sm > 8)
+        return set_error(LBM_EM_EINVAL, "bad tile shape or CTAs per SM");
+    if (o->tile_w && (o->tile_w % 32 || o->tile_w > 256)) return set_error(LBM_EM_EINVAL, "tile_w: multiple of 32, <= 256");
+    if (o->tile_h && (o->tile_h > 16)) return set_error(LBM_EM_EINVAL, "tile_h must be <= 16");
+    for (int i = 0; i < n; ++i) {
+        const lbm_em_instance &s = specs[i];
+        if (s.nx < 4 || s.ny < 4 || s.period_steps < 4 || s.periods < 1 || s.ramp_steps < 0 || !std::isfinite(s.E0))
+            return set_error(LBM_EM_EINVAL, "bad instance " + std::to_string(i));
+        lbm_em_status st = check_janus(&s.janus);
+        if (st) return st;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return set_error(LBM_EM_ECUDA, "no CUDA device available (the solver has no CPU path)");
+    }
+    lbm_em_batch *b = new lbm_em_batch();
+    cudaGetDevice(&b->dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev);
+    b->n = n;
+    b->prec = o->precision;
+    b->elem = b->prec == LBM_EM_F64 ? 8 : 4;
+    b->specs.assign(specs, specs + n);
+    lbm_em_status st = LBM_EM_OK;
+#define BTRY(call, what)            \
+    do {                            \
+        st = cuda_status(call, what); \
+        if (st) {                   \
+            batch_free(b);          \
+            return st;              \
+        }                           \
+    } while (0)
+    if (o->stream) {
+        b->stream = (cudaStream_t)o->stream;
+    } else {
+        BTRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        b->own_stream = true;
+    }
+    BTRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    // layout
+    std::vector<ContourHost> ch(n);
+    std::vector<double2> cs_all;
+    std::vector<size_t> cs_off(n);
+    b->desc.resize(n);
+    size_t base = 0, mat = 0, slot = 0, accs = 0;
+    for (int i = 0; i < n; ++i) {
+        const lbm_em_instance &s = specs[i];
+        InstDesc &d = b->desc[i];
+        std::memset(&d, 0, sizeof(d));
+        d.nx = s.nx;
+        d.ny = s.ny;
+        d.pitch = round_up(s.nx, 32);
+        d.period = s.period_steps;
+        d.pstride = (size_t)d.pitch * s.ny;
+        d.base = base;
+        d.mat_base = mat;
+        d.slot_base = slot;
+        base += (size_t)NPLANES * d.pstride;
+        mat += d.pstride;
+        slot += d.pstride;
+        d.steps = (long long)s.periods * s.period_steps;
+        d.acc_from = d.steps - s.period_steps;
+        b->max_steps = std::max(b->max_steps, d.steps);
+        lbm_em_contour c{std::nan(""), std::nan(""), s.contour_radius, s.n_points, 0, s.janus.a};
+        if (!std::isnan(s.janus.cx)) c.cx = s.janus.cx;
+        if (!std::isnan(s.janus.cy)) c.cy = s.janus.cy;
+        ch[i].E0 = s.E0;
+        st = build_contour(s.nx, s.ny, &c, &ch[i]);
+        if (st) {
+            batch_free(b);
+            return set_error(st, "instance " + std::to_string(i) + ": " + g_last_error);
+        }
+        d.acc_base = (int)accs;
+        accs += ch[i].n_slots;
+        d.y0 = ch[i].y0;
+        d.y1 = ch[i].y1;
+        d.src.kind = SRC_OPEN;
+        d.src.period = s.period_steps;
+        d.src.ramp = s.ramp_steps;
+        incident_constants(s.period_steps, s.E0, &d.src.pr, &d.src.pi, &d.src.qr, &d.src.qi);
+        cs_off[i] = cs_all.size();
+        std::vector<double2> cs = phase_table(s.period_steps);
+        cs_all.insert(cs_all.end(), cs.begin(), cs.end());
+        const double eps[3] = {1.0, s.janus.eps1, s.janus.pec2 ? 0.0 : s.janus.eps2};
+        for (int r = 0; r < 3; ++r) {
+            const bool pec = r == 2 && s.janus.pec2;
+            d.mtab[r][0] = pec ? 0.0 : 1.0 / (3.0 * eps[r]);
+            d.mtab[r][1] = pec ? 0.0 : 6.0 * (eps[r] - 1.0);
+            d.mtab[r][2] = pec ? 0.0 : 1.0 / eps[r];
+        }
+    }
+    b->buf_elems = base;
+    b->mat_bytes = mat;
+    b->slot_elems = slot;
+    b->acc_slots = accs;
+    BTRY(cudaMalloc(&b->buf[0], base * b->elem), "cudaMalloc(batch distributions)");
+    BTRY(cudaMalloc(&b->buf[1], base * b->elem), "cudaMalloc(batch distributions)");
+    BTRY(cudaMalloc(&b->d_mat, mat), "cudaMalloc(batch materials)");
+    BTRY(cudaMalloc(&b->d_slot, slot * sizeof(int)), "cudaMalloc(batch slots)");
+    BTRY(cudaMalloc(&b->d_acc, std::max<size_t>(accs, 1) * 6 * sizeof(double)), "cudaMalloc(batch acc)");
+    BTRY(cudaMalloc(&b->d_out, (size_t)n * 3 * sizeof(double)), "cudaMalloc(batch out)");
+    BTRY(cudaMalloc(&b->d_cs, cs_all.size() * sizeof(double2)), "cudaMalloc(batch phases)");
+    BTRY(cudaMalloc(&b->d_desc, n * sizeof(InstDesc)), "cudaMalloc(batch desc)");
+    BTRY(cudaMalloc(&b->d_time, 2 * sizeof(long long)), "cudaMalloc(time)");
+    BTRY(cudaMalloc(&b->d_err, n * sizeof(unsigned)), "cudaMalloc(err)");
+    BTRY(cudaMemcpy(b->d_cs, cs_all.data(), cs_all.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload");
+    for (int i = 0; i < n; ++i) b->desc[i].src.cs = b->d_cs + cs_off[i];
+    BTRY(cudaMemcpy(b->d_desc, b->desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice), "upload");
+    // slot maps, contour points and per-instance contour descriptors
+    {
+        std::vector<int> smap(slot, -1);
+        std::vector<ContourPt> pts;
+        std::vector<ContourDesc> cd(n);
+        for (int i = 0; i < n; ++i) {
+            const InstDesc &d = b->desc[i];
+            for (int s = 0; s < ch[i].n_slots; ++s)
+                smap[d.slot_base + (size_t)ch[i].site_xy[2 * s + 1] * d.pitch + ch[i].site_xy[2 * s]] = s;
+            cd[i] = ContourDesc{(int)pts.size(), (int)ch[i].pts.size(), d.acc_base, 0,
+                                2.0 / (double)specs[i].period_steps, ch[i].R, ch[i].dl, ch[i].F0, ch[i].M0};
+            pts.insert(pts.end(), ch[i].pts.begin(), ch[i].pts.end());
+        }
+        BTRY(cudaMemcpy(b->d_slot, smap.data(), slot * sizeof(int), cudaMemcpyHostToDevice), "upload slots");
+        BTRY(cudaMalloc(&b->d_pts, pts.size() * sizeof(ContourPt)), "cudaMalloc(points)");
+        BTRY(cudaMemcpy(b->d_pts, pts.data(), pts.size() * sizeof(ContourPt), cudaMemcpyHostToDevice), "upload");
+        BTRY(cudaMalloc(&b->d_cdesc, n * sizeof(ContourDesc)), "cudaMalloc(contour desc)");
+        BTRY(cudaMemcpy(b->d_cdesc, cd.data(), n * sizeof(ContourDesc), cudaMemcpyHostToDevice), "upload");
+    }
+    // rasterise every instance on the device
+    for (int i = 0; i < n; ++i) {
+        const InstDesc &d = b->desc[i];
+        double cx, cy;
+        janus_center(&specs[i].janus, d.nx, d.ny, &cx, &cy);
+        BTRY(launch_rasterize(d.nx, d.ny, d.pitch, cx, cy, specs[i].janus.a, -std::sin(specs[i].janus.phi0),
+                              -std::cos(specs[i].janus.phi0), b->d_mat + d.mat_base, b->stream),
+             "rasterise");
+    }
+    // run order: decreasing number of steps
+    b->order.resize(n);
+    std::iota(b->order.begin(), b->order.end(), 0);
+    std::stable_sort(b->order.begin(), b->order.end(),
+                     [&](long long x, long long y) { return b->desc[x].steps > b->desc[y].steps; });
+    st = batch_autotune(b, o->tile_w, o->tile_h, o->ctas_per_sm);
+    if (!st) st = cuda_status(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    if (st) {
+        batch_free(b);
+        return st;
+    }
+#undef BTRY
+    *out = b;
+    return LBM_EM_OK;
 }
-lbm_em_status lbm_em_batch_run(lbm_em_batch_t *) { return set_error(LBM_EM_ESTATE, "no batch"); }
-lbm_em_status lbm_em_batch_results(lbm_em_batch_t *, double *, int32_t *) { return set_error(LBM_EM_ESTATE, "no batch"); }
-lbm_em_status lbm_em_batch_config(lbm_em_batch_t *, int32_t *, int32_t *, int32_t *) {
-    return set_error(LBM_EM_ESTATE, "no batch");
+
+lbm_em_status lbm_em_batch_run(lbm_em_batch_t *b) {
+    if (!b) return set_error(LBM_EM_EINVAL, "batch is NULL");
+    cudaSetDevice(b->dev);
+    lbm_em_status st = b->ran ? batch_clear(b) : LBM_EM_OK;
+    if (st) return st;
+    if (!b->graph) {
+        cudaGraph_t g = nullptr;
+        st = cuda_status(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        if (st) return st;
+        cudaError_t e = batch_launch(b, b->cap, 0);
+        if (e == cudaSuccess) e = batch_launch(b, b->cap, 1);
+        cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_status(e != cudaSuccess ? e : e2, "capturing the batch graph");
+        }
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        st = cuda_status(e, "cudaGraphInstantiate");
+        if (st) return st;
+    }
+    long long t = 0;
+    while (t + 2 <= b->max_steps) {
+        st = cuda_status(cudaGraphLaunch(b->graph, b->stream), "cudaGraphLaunch");
+        if (st) return st;
+        t += 2;
+    }
+    if (t < b->max_steps) {
+        st = cuda_status(batch_launch(b, b->stream, t), "batch step");
+        if (st) return st;
+    }
+    k_batch_contour<<<b->n, 256, 0, b->stream>>>(b->d_cdesc, b->d_pts, b->d_acc, b->d_out);
+    st = cuda_status(cudaGetLastError(), "batch contour");
+    b->ran = true;
+    return st;
 }
-lbm_em_status lbm_em_batch_destroy(lbm_em_batch_t *) { return LBM_EM_OK; }
+
+lbm_em_status lbm_em_batch_results(lbm_em_batch_t *b, double *out, int32_t *status) {
+    if (!b) return set_error(LBM_EM_EINVAL, "batch is NULL");
+    if (!b->ran) return set_error(LBM_EM_ESTATE, "batch has not run");
+    cudaSetDevice(b->dev);
+    std::vector<double> res((size_t)b->n * 3);
+    std::vector<unsigned> err(b->n);
+    lbm_em_status st = cuda_status(
+        cudaMemcpyAsync(res.data(), b->d_out, res.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "read");
+    if (!st)
+        st = cuda_status(cudaMemcpyAsync(err.data(), b->d_err, err.size() * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                         b->stream),
+                         "read");
+    if (!st) st = cuda_status(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    if (st) return st;
+    if (out) std::memcpy(out, res.data(), res.size() * sizeof(double));
+    bool any = false;
+    for (int i = 0; i < b->n; ++i) {
+        if (status) status[i] = err[i] ? LBM_EM_EUNSTABLE : LBM_EM_OK;
+        any |= err[i] != 0;
+    }
+    if (any) return set_error(LBM_EM_EUNSTABLE, "at least one instance became unstable");
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_batch_config(lbm_em_batch_t *b, int32_t *tile_w, int32_t *tile_h, int32_t *ctas_per_sm) {
+    if (!b) return set_error(LBM_EM_EINVAL, "batch is NULL");
+    if (tile_w) *tile_w = b->tile_w;
+    if (tile_h) *tile_h = b->tile_h;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas;
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_batch_destroy(lbm_em_batch_t *b) {
+    batch_free(b);
+    return LBM_EM_OK;
+}
 
 }  // extern "C"

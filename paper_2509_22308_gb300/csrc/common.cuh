@@ -141,32 +141,38 @@ __device__ __forceinline__ void moments(const Pop<T> &p, T inv_eps3, T *E3, T *H
     *Hy = p.hypx + p.hymx + p.hypy + p.hymy + (T)2 * p.hyz;
 }
 
+template <typename T>
+__device__ __forceinline__ T fmat(T a, T b, T c) { return fma(a, b, c); }
+
 // Post-collision f* = 2 f^eq - f (Eq. LBGK equation), with 2 f^eq written out from
 // Eq. (equilibrium distribution functions) for the TM^z components:
 //   e_z:  +x (E-H_y)/3, -x (E+H_y)/3, +y (E+H_x)/3, -y (E-H_x)/3, z E/3, rest 2(eps-1)E
 //   h_x:  +-x H_x/3, +y (H_x+E)/3, -y (H_x-E)/3, z H_x/3
 //   h_y:  +x (H_y-E)/3, -x (H_y+E)/3, +-y H_y/3, z H_y/3
+// 36 arithmetic operations per site with the moments (FP64 is bound by its pipe on
+// GB300): every 2 f^eq that is E/3 +- H/3 is one fused multiply-add, and H/3 itself is
+// never formed.
 template <typename T>
 __device__ __forceinline__ void collide(Pop<T> &p, T E3, T Hx, T Hy, T six_em1) {
-    const T third = (T)(1.0 / 3.0);
-    const T hx3 = Hx * third, hy3 = Hy * third;
-    const T A = E3 - hy3, B = E3 + hy3, C = E3 + hx3, D = E3 - hx3;
-    p.e0 = six_em1 * E3 - p.e0;
+    const T third = (T)(1.0 / 3.0), mthird = (T)(-1.0 / 3.0);
+    const T A = fmat(Hy, mthird, E3), B = fmat(Hy, third, E3);
+    const T C = fmat(Hx, third, E3), D = fmat(Hx, mthird, E3);
+    p.e0 = fmat(six_em1, E3, -p.e0);
     p.ez = E3 - p.ez;
     p.epx = A - p.epx;
     p.emx = B - p.emx;
     p.epy = C - p.epy;
     p.emy = D - p.emy;
-    p.hxpx = hx3 - p.hxpx;
-    p.hxmx = hx3 - p.hxmx;
+    p.hxpx = fmat(Hx, third, -p.hxpx);
+    p.hxmx = fmat(Hx, third, -p.hxmx);
     p.hxpy = C - p.hxpy;
     p.hxmy = -D - p.hxmy;
-    p.hxz = hx3 - p.hxz;
+    p.hxz = fmat(Hx, third, -p.hxz);
     p.hypx = -A - p.hypx;
     p.hymx = B - p.hymx;
-    p.hypy = hy3 - p.hypy;
-    p.hymy = hy3 - p.hymy;
-    p.hyz = hy3 - p.hyz;
+    p.hypy = fmat(Hy, third, -p.hypy);
+    p.hymy = fmat(Hy, third, -p.hymy);
+    p.hyz = fmat(Hy, third, -p.hyz);
 }
 
 // |E_z/3| >= 2^20 or non-finite, tested on the exponent bits (integer ALU only).
