@@ -144,6 +144,17 @@ class ClockSampler:
                 "power_w_max": max(r["power"] for r in rows)}
 
 
+def max_over_ranks(value, dist=None):
+    """Maximum of a per-rank float over all ranks (the job finishes with its slowest rank)."""
+    if dist is None:
+        return float(value)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def instance_lus(inst):
     return inst["nx"] * inst["ny"] * inst["periods"] * inst["period"]
 
@@ -247,7 +258,7 @@ def main():
     from paper_2509_22308_gb300 import workloads as W
 
     prec = args.precision
-    instances = W.md_janus_512(1 + rank)
+    instances = W.rank_workload(WORKLOAD, rank)
     stream = torch.cuda.Stream()
     solvers = [L.solver_for_instance(inst, prec, stream) for inst in instances]
     janus = [L.make_janus(i["a"], i["phi0"], i["eps1"], i["eps2"], i["pec2"]) for i in instances]
@@ -297,11 +308,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist)
     value = lus_per_step * args.steps * world / (total_ms / 1e3) / 1e6
 
     # roofline of the dominant kernel: the plain step, timed on its own stream
@@ -370,11 +377,7 @@ def main():
             torch.cuda.synchronize()
             if k > 0:
                 e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        e2e_total = sum(e2e_ms)
-        if dist:
-            t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_total = float(t.item())
+        e2e_total = max_over_ranks(sum(e2e_ms), dist)
         h2d = 0
         for i in instances:
             pitch = (i["nx"] + 31) // 32 * 32

@@ -90,6 +90,22 @@ def small_cases():
     ]
 
 
+def shard(instances, rank: int, world: int):
+    """Instances of one rank when a list of independent instances is spread over
+    world ranks (round robin; no instance is shared, every instance is covered)."""
+    return list(instances[rank::world])
+
+
+def rank_workload(name: str, rank: int, **kw):
+    """The seeded workload a rank runs under weak scaling: rank r uses seed base + r,
+    so the ranks solve distinct but statistically identical problem sets."""
+    fn = WORKLOADS[name]
+    if "seed" in fn.__code__.co_varnames:
+        base = kw.pop("seed", fn.__defaults__[0] if fn.__defaults__ else 0)
+        return fn(seed=base + rank, **kw)
+    return fn(**kw)
+
+
 WORKLOADS = {
     "homogeneous_dielectric_256": homogeneous_dielectric_256,
     "md_janus_512": md_janus_512,
