@@ -49,7 +49,7 @@ def parse_args():
     p.add_argument("--no-design-map", action="store_true")
     p.add_argument("--design-map-instances", type=int, default=24)
     p.add_argument("--profile-case", action="store_true",
-                   help="small case for ncu: a 2048^2 MD-Janus lattice, 2 steps per storage form, then exit")
+                   help="small case for ncu: 2 steps per storage form on a 2048^2 lattice and 2 FP64 steps on the 512^2 workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -215,7 +215,8 @@ def run_reference(args, rank, world):
 
 def profile_case():
     """Two launches of each storage form's step kernel on a 2048^2 lattice (state
-    0.27-1.1 GB per buffer, larger than L2, a few GB on the device in total)."""
+    0.27-1.1 GB per buffer, larger than L2, a few GB on the device in total), then two
+    launches of the FP64 step on one 512^2 instance of the benchmark workload."""
     import torch
     from paper_2509_22308_gb300 import build as B
     B.build()
@@ -226,6 +227,11 @@ def profile_case():
         with L.solver_for_instance(inst, fp) as s:
             s.step(2)
             s.sync()
+    # and two launches of the benchmark's own 512^2 FP64 instance (theta = 0)
+    from paper_2509_22308_gb300 import workloads as W
+    with L.solver_for_instance(W.md_janus_512()[0], "f64") as s:
+        s.step(2)
+        s.sync()
     torch.cuda.synchronize()
     print("profile case done")
 

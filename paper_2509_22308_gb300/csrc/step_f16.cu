@@ -77,61 +77,167 @@ __device__ __forceinline__ void pull_f16(const F16Args &a, int x, int y, long lo
 
 __device__ __forceinline__ void st_dev(__half *p, float v, float scale) { *p = __float2half_rn(v * scale); }
 
+// Deviations from the new equilibrium, g_i = f_i - f_i^eq(F(t)), scaled.
+__device__ __forceinline__ void deviations(const Pop<float> &p, float Ez, float Hx, float Hy, float em1,
+                                           float g[NPLANES]) {
+    const float s6 = 1.0f / 6.0f;
+    g[P_E0] = p.e0 - em1 * Ez;
+    g[P_EZ] = p.ez - Ez * s6;
+    g[P_EPX] = p.epx - (Ez - Hy) * s6;
+    g[P_EMX] = p.emx - (Ez + Hy) * s6;
+    g[P_EPY] = p.epy - (Ez + Hx) * s6;
+    g[P_EMY] = p.emy - (Ez - Hx) * s6;
+    g[P_HXPX] = p.hxpx - Hx * s6;
+    g[P_HXMX] = p.hxmx - Hx * s6;
+    g[P_HXPY] = p.hxpy - (Hx + Ez) * s6;
+    g[P_HXMY] = p.hxmy - (Hx - Ez) * s6;
+    g[P_HXZ] = p.hxz - Hx * s6;
+    g[P_HYPX] = p.hypx - (Hy - Ez) * s6;
+    g[P_HYMX] = p.hymx - (Hy + Ez) * s6;
+    g[P_HYPY] = p.hypy - Hy * s6;
+    g[P_HYMY] = p.hymy - Hy * s6;
+    g[P_HYZ] = p.hyz - Hy * s6;
+}
+
+__device__ __forceinline__ void accumulate_site(const F16Args &a, size_t idx, int y, long long t, float Ez,
+                                                float Hx, float Hy) {
+    if (y < a.accp.y0 || y > a.accp.y1) return;
+    const int s = a.accp.slot[idx];
+    if (s < 0) return;
+    const double2 c = a.src.cs[(int)(t % (long long)a.src.period)];
+    double *q = a.accp.acc + 6 * (size_t)s;
+    q[0] += (double)Ez * c.x;
+    q[1] += (double)Ez * c.y;
+    q[2] += (double)Hx * c.x;
+    q[3] += (double)Hx * c.y;
+    q[4] += (double)Hy * c.x;
+    q[5] += (double)Hy * c.y;
+}
+
+// Two sites (x0, x0 + 1), x0 even, per thread: the x-aligned planes, the fields of the
+// pair and its rows y -+ 1, the material ids and every store move as 2-element
+// vectors; the +-x planes and the fields one site beyond the pair are single loads at
+// the clamped upstream index.  A warp covers 64 sites of one row.
 template <bool ACC>
 __global__ void __launch_bounds__(BX *BY) k_step_f16(const F16Args a, const long long *__restrict__ t_in,
                                                      long long *__restrict__ t_out) {
-    const int x = blockIdx.x * BX + threadIdx.x;
+    const int x0 = 2 * (blockIdx.x * BX + threadIdx.x);
     const int y = blockIdx.y * BY + threadIdx.y;
     const long long t = *t_in;
-    if (x == 0 && y == 0) *t_out = t + 1;
-    if (x >= a.nx || y >= a.ny) return;
-    const size_t idx = (size_t)y * a.pitch + x;
-    const MatT<float> m = a.mtab[a.mat[idx]];
-    const float em1 = m.six_em1 * (1.0f / 6.0f);
-    Pop<float> p;
-    pull_f16(a, x, y, t, p, em1);
-    float E3, Hx, Hy, D;
-    moments(p, m.inv_eps3, &E3, &Hx, &Hy, &D);
-    if (field_runaway(E3)) atomicOr(a.err, 1u);
-    const float Ez = 3.0f * E3;
-    if (ACC) {
-        if (y >= a.accp.y0 && y <= a.accp.y1) {
-            const int s = a.accp.slot[idx];
-            if (s >= 0) {
-                const double2 c = a.src.cs[(int)(t % (long long)a.src.period)];
-                double *q = a.accp.acc + 6 * (size_t)s;
-                q[0] += (double)Ez * c.x;
-                q[1] += (double)Ez * c.y;
-                q[2] += (double)Hx * c.x;
-                q[3] += (double)Hx * c.y;
-                q[4] += (double)Hy * c.x;
-                q[5] += (double)Hy * c.y;
-            }
+    if (x0 == 0 && y == 0) *t_out = t + 1;
+    if (x0 >= a.nx || y >= a.ny) return;
+    const bool has1 = x0 + 1 < a.nx;
+    const size_t ps = a.pstride;
+    const size_t r = (size_t)y * a.pitch;
+    const size_t rm = (size_t)(y > 0 ? y - 1 : 0) * a.pitch;
+    const size_t rp = (size_t)(y < a.ny - 1 ? y + 1 : y) * a.pitch;
+    const int xw = x0 > 0 ? x0 - 1 : 0;                   // +x upstream of site 0
+    const int xe = x0 + 2 < a.nx ? x0 + 2 : a.nx - 1;      // -x upstream of site 1
+    const float is = a.inv_scale, s6 = 1.0f / 6.0f;
+    const __half *g = a.g;
+
+    // fields at time t - 1 of the pair, of its rows y -+ 1 and of the sites x0 - 1, x0 + 2
+    const float2 Ec = *(const float2 *)(a.fe + r + x0), Xc = *(const float2 *)(a.fhx + r + x0),
+                 Yc = *(const float2 *)(a.fhy + r + x0);
+    const float2 Es = *(const float2 *)(a.fe + rm + x0), Xs = *(const float2 *)(a.fhx + rm + x0),
+                 Ys = *(const float2 *)(a.fhy + rm + x0);
+    const float2 En = *(const float2 *)(a.fe + rp + x0), Xn = *(const float2 *)(a.fhx + rp + x0),
+                 Yn = *(const float2 *)(a.fhy + rp + x0);
+    const float Ew = a.fe[r + xw], Xw = a.fhx[r + xw], Yw = a.fhy[r + xw];
+    const float Ee = a.fe[r + xe], Xe = a.fhx[r + xe], Ye = a.fhy[r + xe];
+    // -x upstream of site 0 is x0 + 1 (clamped to x0 at the last column)
+    const float E0e = has1 ? Ec.y : Ec.x, X0e = has1 ? Xc.y : Xc.x, Y0e = has1 ? Yc.y : Yc.x;
+
+    auto h2 = [&](int plane, size_t row) { return __half22float2(*(const __half2 *)(g + plane * ps + row + x0)); };
+    auto h1 = [&](int plane, size_t row, int x) { return __half2float(g[plane * ps + row + x]); };
+
+    const uchar2 id = *(const uchar2 *)(a.mat + r + x0);
+    const MatT<float> m0 = a.mtab[id.x], m1 = a.mtab[id.y];
+    const float em10 = m0.six_em1 * s6, em11 = m1.six_em1 * s6;
+
+    Pop<float> p0, p1;
+    float2 v;
+    v = h2(P_E0, r);
+    p0.e0 = em10 * Ec.x - v.x * is;
+    p1.e0 = em11 * Ec.y - v.y * is;
+    v = h2(P_EZ, r);
+    p0.ez = Ec.x * s6 - v.x * is;
+    p1.ez = Ec.y * s6 - v.y * is;
+    v = h2(P_EPX, r);
+    p0.epx = (Ew - Yw) * s6 - h1(P_EPX, r, xw) * is;
+    p1.epx = (Ec.x - Yc.x) * s6 - v.x * is;
+    v = h2(P_EMX, r);
+    p0.emx = (E0e + Y0e) * s6 - (has1 ? v.y : v.x) * is;
+    p1.emx = (Ee + Ye) * s6 - h1(P_EMX, r, xe) * is;
+    v = h2(P_EPY, rm);
+    p0.epy = (Es.x + Xs.x) * s6 - v.x * is;
+    p1.epy = (Es.y + Xs.y) * s6 - v.y * is;
+    v = h2(P_EMY, rp);
+    p0.emy = (En.x - Xn.x) * s6 - v.x * is;
+    p1.emy = (En.y - Xn.y) * s6 - v.y * is;
+    v = h2(P_HXPX, r);
+    p0.hxpx = Xw * s6 - h1(P_HXPX, r, xw) * is;
+    p1.hxpx = Xc.x * s6 - v.x * is;
+    v = h2(P_HXMX, r);
+    p0.hxmx = X0e * s6 - (has1 ? v.y : v.x) * is;
+    p1.hxmx = Xe * s6 - h1(P_HXMX, r, xe) * is;
+    v = h2(P_HXPY, rm);
+    p0.hxpy = (Xs.x + Es.x) * s6 - v.x * is;
+    p1.hxpy = (Xs.y + Es.y) * s6 - v.y * is;
+    v = h2(P_HXMY, rp);
+    p0.hxmy = (Xn.x - En.x) * s6 - v.x * is;
+    p1.hxmy = (Xn.y - En.y) * s6 - v.y * is;
+    v = h2(P_HXZ, r);
+    p0.hxz = Xc.x * s6 - v.x * is;
+    p1.hxz = Xc.y * s6 - v.y * is;
+    v = h2(P_HYPX, r);
+    p0.hypx = (Yw - Ew) * s6 - h1(P_HYPX, r, xw) * is;
+    p1.hypx = (Yc.x - Ec.x) * s6 - v.x * is;
+    v = h2(P_HYMX, r);
+    p0.hymx = (Y0e + E0e) * s6 - (has1 ? v.y : v.x) * is;
+    p1.hymx = (Ye + Ee) * s6 - h1(P_HYMX, r, xe) * is;
+    v = h2(P_HYPY, rm);
+    p0.hypy = Ys.x * s6 - v.x * is;
+    p1.hypy = Ys.y * s6 - v.y * is;
+    v = h2(P_HYMY, rp);
+    p0.hymy = Yn.x * s6 - v.x * is;
+    p1.hymy = Yn.y * s6 - v.y * is;
+    v = h2(P_HYZ, r);
+    p0.hyz = Yc.x * s6 - v.x * is;
+    p1.hyz = Yc.y * s6 - v.y * is;
+    if (x0 == 0 && t >= 1 && a.src.kind != SRC_NONE) {
+        double gs, inc;
+        source_values(a.src, t, &gs, &inc);
+        if (a.src.kind == SRC_OPEN) {
+            p0.epx += (float)gs;
+            p0.hypx -= (float)gs;
+        } else {
+            p0.epx = (float)inc;
+            p0.hxpx = 0.0f;
+            p0.hypx = (float)(-inc);
         }
     }
-    // deviations from the new equilibrium, g_i = f_i - f_i^eq(F(t))
-    const float s6 = 1.0f / 6.0f, sc = a.scale;
-    const size_t ps = a.pstride;
-    __half *go = a.g_out;
-    st_dev(go + P_E0 * ps + idx, p.e0 - em1 * Ez, sc);
-    st_dev(go + P_EZ * ps + idx, p.ez - Ez * s6, sc);
-    st_dev(go + P_EPX * ps + idx, p.epx - (Ez - Hy) * s6, sc);
-    st_dev(go + P_EMX * ps + idx, p.emx - (Ez + Hy) * s6, sc);
-    st_dev(go + P_EPY * ps + idx, p.epy - (Ez + Hx) * s6, sc);
-    st_dev(go + P_EMY * ps + idx, p.emy - (Ez - Hx) * s6, sc);
-    st_dev(go + P_HXPX * ps + idx, p.hxpx - Hx * s6, sc);
-    st_dev(go + P_HXMX * ps + idx, p.hxmx - Hx * s6, sc);
-    st_dev(go + P_HXPY * ps + idx, p.hxpy - (Hx + Ez) * s6, sc);
-    st_dev(go + P_HXMY * ps + idx, p.hxmy - (Hx - Ez) * s6, sc);
-    st_dev(go + P_HXZ * ps + idx, p.hxz - Hx * s6, sc);
-    st_dev(go + P_HYPX * ps + idx, p.hypx - (Hy - Ez) * s6, sc);
-    st_dev(go + P_HYMX * ps + idx, p.hymx - (Hy + Ez) * s6, sc);
-    st_dev(go + P_HYPY * ps + idx, p.hypy - Hy * s6, sc);
-    st_dev(go + P_HYMY * ps + idx, p.hymy - Hy * s6, sc);
-    st_dev(go + P_HYZ * ps + idx, p.hyz - Hy * s6, sc);
-    a.fe_out[idx] = Ez;
-    a.fhx_out[idx] = Hx;
-    a.fhy_out[idx] = Hy;
+
+    float E30, Hx0, Hy0, D0, E31, Hx1, Hy1, D1;
+    moments(p0, m0.inv_eps3, &E30, &Hx0, &Hy0, &D0);
+    moments(p1, m1.inv_eps3, &E31, &Hx1, &Hy1, &D1);
+    if (field_runaway(E30) || (has1 && field_runaway(E31))) atomicOr(a.err, 1u);
+    const float Ez0 = 3.0f * E30, Ez1 = 3.0f * E31;
+    const size_t idx = r + x0;
+    if (ACC) {
+        accumulate_site(a, idx, y, t, Ez0, Hx0, Hy0);
+        if (has1) accumulate_site(a, idx + 1, y, t, Ez1, Hx1, Hy1);
+    }
+    float g0[NPLANES], g1[NPLANES];
+    deviations(p0, Ez0, Hx0, Hy0, em10, g0);
+    deviations(p1, Ez1, Hx1, Hy1, em11, g1);
+    const float sc = a.scale;
+#pragma unroll
+    for (int q = 0; q < NPLANES; ++q)
+        *(__half2 *)(a.g_out + q * ps + idx) = __floats2half2_rn(g0[q] * sc, g1[q] * sc);
+    *(float2 *)(a.fe_out + idx) = make_float2(Ez0, Ez1);
+    *(float2 *)(a.fhx_out + idx) = make_float2(Hx0, Hx1);
+    *(float2 *)(a.fhy_out + idx) = make_float2(Hy0, Hy1);
 }
 
 __global__ void __launch_bounds__(BX *BY) k_fields_f16(const F16Args a, const long long *__restrict__ t_dev,
@@ -153,7 +259,7 @@ __global__ void __launch_bounds__(BX *BY) k_fields_f16(const F16Args a, const lo
 
 cudaError_t launch_step_f16(const F16Args &a, const long long *t_in, long long *t_out, bool accumulate,
                             cudaStream_t s) {
-    dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY), block(BX, BY);
+    dim3 grid((a.nx + 2 * BX - 1) / (2 * BX), (a.ny + BY - 1) / BY), block(BX, BY);
     if (accumulate)
         k_step_f16<true><<<grid, block, 0, s>>>(a, t_in, t_out);
     else
