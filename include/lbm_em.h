@@ -182,6 +182,26 @@ const char *lbm_em_last_error(void);
  * (0 vacuum, 1 region II, 2 region III).  Sec. II, Sec. IV.A staircase. */
 lbm_em_status lbm_em_rasterize_janus(const lbm_em_janus *j, int32_t nx, int32_t ny, uint8_t *regions);
 
+/* Size of the fixed device array used by lbm_em_rasterize_janus_noalloc. */
+#define LBM_EM_NOALLOC_RASTER_BYTES (4u * 1024u * 1024u)
+
+/* The same rasterisation as lbm_em_rasterize_janus, for callers that must not allocate
+ * device memory: for example an application whose own memory pool already holds the
+ * device's free memory, or a latency-critical loop in which cudaMalloc / cudaFree would
+ * synchronise the device.  The paper has no counterpart; this is a service of the library.
+ * It calls no cudaMalloc, cudaFree or other allocating routine: the region ids are written
+ * into one 4 MiB array compiled into this library's device image (every GPU that loads the
+ * library holds it until the process exits) and then copied into regions[ny][nx] (host).
+ *  - ny * (nx rounded up to a multiple of 32) must not exceed LBM_EM_NOALLOC_RASTER_BYTES;
+ *    a larger request returns LBM_EM_EINVAL with a message and launches nothing.
+ *  - The first call on a device looks up the array's address on that device
+ *    (cudaGetSymbolAddress) and keeps it; make that first call before any CUDA stream
+ *    capture is active.
+ *  - Runs on the legacy default stream and returns once regions is filled.
+ *  - Every call shares the one array, which keeps the last call's contents; calls that
+ *    overlap on the GPU (several host threads at once) race, so serialise them. */
+lbm_em_status lbm_em_rasterize_janus_noalloc(const lbm_em_janus *j, int32_t nx, int32_t ny, uint8_t *regions);
+
 /* ---- batched design diagrams (Sec. IV maps over eps and phi0) ---------------------- */
 
 typedef struct {

@@ -1,0 +1,77 @@
+// Rasterisation of a Janus disc for callers that must not allocate device memory.
+//
+// Some hosts of this library cannot call cudaMalloc: an application whose own memory
+// pool has already reserved the device's free memory, or a latency-critical loop in
+// which cudaMalloc / cudaFree would synchronise the whole device.  This entry point
+// writes the region ids into one fixed scratch array that lives in this library's
+// device image instead of a per-call allocation.
+//
+// The array is a file-scope __device__ variable: every GPU that loads the library
+// holds its 4 MiB until the process exits.  Host code cannot use the variable's name
+// as a device address (on the host it is only a stand-in symbol), so the first call on
+// each device looks the device address up with cudaGetSymbolAddress while that device
+// is current, caches it, and passes it to the kernel.
+#include <cmath>
+#include <mutex>
+
+#include "../../include/lbm_em.h"
+#include "common.cuh"
+#include "runtime.h"
+
+using namespace lbmem;
+
+namespace {
+
+static __device__ __align__(256) uint8_t g_raster_scratch[LBM_EM_NOALLOC_RASTER_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_raster_scratch on the current device (looked up once per device).
+lbm_em_status scratch_address(int dev, void **out) {
+    if (dev < 0 || dev >= kMaxDevices) return set_error(LBM_EM_EINVAL, "device index beyond 63");
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_raster_scratch);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(no-allocation scratch)");
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return LBM_EM_OK;
+}
+
+}  // namespace
+
+extern "C" lbm_em_status lbm_em_rasterize_janus_noalloc(const lbm_em_janus *j, int32_t nx, int32_t ny,
+                                                        uint8_t *regions) {
+    lbm_em_status st = check_janus(j);
+    if (st) return st;
+    if (nx < 1 || ny < 1 || !regions) return set_error(LBM_EM_EINVAL, "bad size or NULL output");
+    const int pitch = round_up(nx, 32);
+    if ((size_t)pitch * (size_t)ny > (size_t)LBM_EM_NOALLOC_RASTER_BYTES)
+        return set_error(LBM_EM_EINVAL, "lattice too large for the no-allocation scratch: ny * (nx rounded up to "
+                                        "a multiple of 32) must be <= LBM_EM_NOALLOC_RASTER_BYTES (4 MiB)");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return set_error(LBM_EM_ECUDA, "no CUDA device available (the solver has no CPU path)");
+    }
+    int dev = 0;
+    st = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st) return st;
+    void *scratch = nullptr;
+    st = scratch_address(dev, &scratch);
+    if (st) return st;
+    double cx, cy;
+    janus_center(j, nx, ny, &cx, &cy);
+    // every site of the nx x ny window is written, so nothing needs clearing first
+    st = cuda_status(launch_rasterize(nx, ny, pitch, cx, cy, j->a, -std::sin(j->phi0), -std::cos(j->phi0),
+                                      (uint8_t *)scratch, 0),
+                     "rasterise kernel");
+    if (!st)
+        st = cuda_status(cudaMemcpy2D(regions, nx, scratch, pitch, nx, ny, cudaMemcpyDeviceToHost),
+                         "reading regions from the no-allocation scratch");
+    return st;
+}

@@ -81,6 +81,7 @@ SIGNATURES = {
     "lbm_em_save_state": [_vp, _vp, _P(ctypes.c_size_t)],
     "lbm_em_load_state": [_vp, _vp, ctypes.c_size_t],
     "lbm_em_rasterize_janus": [_P(Janus), ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_uint8)],
+    "lbm_em_rasterize_janus_noalloc": [_P(Janus), ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_uint8)],
     "lbm_em_batch_create": [_P(Instance), ctypes.c_int32, _P(BatchOpts), _P(_vp)],
     "lbm_em_batch_run": [_vp],
     "lbm_em_batch_results": [_vp, _P(ctypes.c_double), _P(ctypes.c_int32)],
@@ -257,6 +258,13 @@ class Solver:
 def rasterize_janus(j: Janus, nx, ny):
     out = np.zeros((ny, nx), dtype=np.uint8)
     _call("lbm_em_rasterize_janus", ctypes.byref(j), int(nx), int(ny), _u8ptr(out))
+    return out
+
+
+def rasterize_janus_noalloc(j: Janus, nx, ny):
+    """Like ``rasterize_janus`` without any device allocation (fixed 4 MiB device array)."""
+    out = np.zeros((ny, nx), dtype=np.uint8)
+    _call("lbm_em_rasterize_janus_noalloc", ctypes.byref(j), int(nx), int(ny), _u8ptr(out))
     return out
 
 
