@@ -31,7 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS & HBM GB/s (% of peak) per precision form; design-map cells/sec at <=1e-3 force err"
 WORKLOAD = "md_janus_512"
 BYTES_PER_LU = {"f64": 16 * 8 * 2 + 1, "f32": 16 * 4 * 2 + 1, "f16dev": 2 * (16 * 2 + 3 * 4) + 1}
-STEP_KERNEL = {"f64": "k_step<double, false>", "f32": "k_step<float, false>", "f16dev": "k_step_f16<false>"}
+STEP_KERNEL = {"f64": "k_step<double, false>", "f32": "k_step2_f32<false> (two steps per launch)",
+               "f16dev": "k_step2_f16<false> (two steps per launch)"}
 # FP64 pipe operations per lattice update of the step kernel: 16 for the moments
 # (sums of 6, 5 and 5 populations, one scaling), 20 for the equilibria and 2 f^eq - f
 FP64_OPS_PER_LU = 36
@@ -265,30 +266,42 @@ def main():
 
     prec = args.precision
     instances = W.rank_workload(WORKLOAD, rank)
-    stream = torch.cuda.Stream()
-    solvers = [L.solver_for_instance(inst, prec, stream) for inst in instances]
+    n_inst = len(instances)
+    # one stream per instance: the instances are independent, so their runs overlap and
+    # fill the GPU (a 512^2 step alone is only 1.7 waves of thread blocks)
+    main = torch.cuda.Stream()
+    streams = [torch.cuda.Stream() for _ in instances]
+    solvers = [L.solver_for_instance(inst, prec, st) for inst, st in zip(instances, streams)]
     janus = [L.make_janus(i["a"], i["phi0"], i["eps1"], i["eps2"], i["pec2"]) for i in instances]
     contours = [L.make_contour(i["R"], i["a"]) for i in instances]
+    d_out = torch.zeros((n_inst, 3), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     lus_per_step = sum(instance_lus(i) for i in instances)
     launches_per_step = sum(2 + i["periods"] * i["period"] for i in instances)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
 
     def one_step(plain_events=None):
-        res = []
-        for s, inst, j, c in zip(solvers, instances, janus, contours):
+        """Whole hot path of every instance, all instances in flight; returns the
+        (start, end) events on the main stream."""
+        e_start, e_end = ev(), ev()
+        e_start.record(main)
+        for s, st, inst, j, c, k in zip(solvers, streams, instances, janus, contours, range(n_inst)):
+            st.wait_event(e_start)
             s.set_janus(j)
             s.reset()
             n_plain = (inst["periods"] - 1) * inst["period"]
+            a, b = ev(), ev()
+            a.record(st)
+            s.step(n_plain)
+            b.record(st)
             if plain_events is not None:
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                s.step(n_plain)
-                e1.record(stream)
-                plain_events.append((e0, e1, n_plain, inst["nx"] * inst["ny"]))
-            else:
-                s.step(n_plain)
-            res.append(s.force_torque(c))
-        return np.array(res)
+                plain_events.append((a, b, n_plain, inst["nx"] * inst["ny"]))
+            s.force_torque_device(c, d_out[k].data_ptr())
+            done = ev()
+            done.record(st)
+            main.wait_event(done)
+        e_end.record(main)
+        return e_start, e_end
 
     for _ in range(args.warmup):
         one_step()
@@ -298,18 +311,20 @@ def main():
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
-    step_ms, plain = [], []
-    results = None
+    step_ms, plain, windows = [], [], []
     for _ in range(args.steps):
-        with torch.cuda.stream(stream):
+        with torch.cuda.stream(main):
             flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        results = one_step(plain)
-        e1.record(stream)
+        n0 = len(plain)
+        e0, e1 = one_step(plain)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
+        # the plain-step phase of this benchmark step: first start to last end over the streams
+        starts = [e0.elapsed_time(a) for a, _, _, _ in plain[n0:]]
+        ends = [e0.elapsed_time(b) for _, b, _, _ in plain[n0:]]
+        windows.append(max(ends) - min(starts))
     torch.cuda.synchronize()
+    results = d_out.cpu().numpy()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -317,10 +332,12 @@ def main():
     total_ms = max_over_ranks(sum(step_ms), dist)
     value = lus_per_step * args.steps * world / (total_ms / 1e3) / 1e6
 
-    # roofline of the dominant kernel: the plain step, timed on its own stream
-    plain_ms = sum(a.elapsed_time(b) for a, b, _, _ in plain)
-    plain_launches = sum(n for _, _, n, _ in plain)
-    plain_bytes = sum(n * sites * BYTES_PER_LU[prec] for _, _, n, sites in plain)
+    # roofline of the dominant kernel, the plain step: its algorithmic work over the
+    # window in which the plain steps of all instances ran (CUDA events on their streams)
+    plain_ms = sum(windows)
+    plain_launches = sum(n for _, _, n, _ in plain) // n_inst
+    plain_sites_steps = sum(n * sites for _, _, n, sites in plain)
+    plain_bytes = plain_sites_steps * BYTES_PER_LU[prec]
     avg_launch_us = plain_ms * 1e3 / plain_launches
     achieved = plain_bytes / (plain_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
@@ -328,7 +345,7 @@ def main():
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     if prec == "f64":
         # the FP64 step is bound by the FP64 pipe: 2 FP64 operations per clock per SM
-        ops = sum(n * sites for _, _, n, sites in plain) * FP64_OPS_PER_LU
+        ops = plain_sites_steps * FP64_OPS_PER_LU
         achieved_t = ops / (plain_ms / 1e3) / 1e12
         peak_t = SMS * FP64_OPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
         roofline = {"bound": "alu", "achieved": round(achieved_t, 4), "peak": round(peak_t, 4), "unit": "TFLOP/s",
@@ -339,6 +356,8 @@ def main():
                                    f"{sm_mhz:.0f} MHz",
                     "algorithmic_ops_per_launch": 512 * 512 * FP64_OPS_PER_LU,
                     "avg_launch_us": round(avg_launch_us, 3),
+                    "timing": f"{n_inst} instances on {n_inst} streams; avg_launch_us = plain-step window / "
+                              "launches per instance, so one launch slot covers all instances",
                     "hbm_view": {"achieved_gbs": round(achieved, 1), "peak_gbs": peak,
                                  "frac": round(achieved / peak, 4),
                                  "algorithmic_bytes_per_launch": 512 * 512 * BYTES_PER_LU[prec]}}
@@ -357,7 +376,8 @@ def main():
                       "lattice_updates_per_step": lus_per_step,
                       "l2": "flushed (256 MiB write) between timed steps; a 512^2 lattice's ping-pong "
                             "state can stay L2-resident across the lattice time steps of one run",
-                      "parallelism": f"replicas x{world} (independent instances per rank)"},
+                      "parallelism": f"replicas x{world} (independent instances per rank), "
+                                     f"{n_inst} concurrent streams per GPU"},
            "roofline": roofline, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
            "forces_last_step": results.round(6).tolist()}
 
@@ -375,14 +395,20 @@ def main():
         for k in range(args.steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            for inst, (eps, pec), c in zip(instances, maps, contours):
-                with L.Solver(inst["nx"], inst["ny"], prec, eps_map=eps, pec_mask=pec,
-                              source=L.make_source(inst["period"], inst["ramp"]), stream=stream) as s:
-                    s.step((inst["periods"] - 1) * inst["period"])
-                    s.force_torque(c)
+            hs, outs = [], torch.zeros((n_inst, 3), dtype=torch.float64, device="cuda")
+            for inst, (eps, pec), st in zip(instances, maps, streams):
+                hs.append(L.Solver(inst["nx"], inst["ny"], prec, eps_map=eps, pec_mask=pec,
+                                   source=L.make_source(inst["period"], inst["ramp"]), stream=st))
+            for kk, (h_, inst, c) in enumerate(zip(hs, instances, contours)):
+                h_.step((inst["periods"] - 1) * inst["period"])
+                h_.force_torque_device(c, outs[kk].data_ptr())
             torch.cuda.synchronize()
+            host = outs.cpu().numpy()
+            for h_ in hs:
+                h_.close()
             if k > 0:
                 e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            assert np.allclose(host, results, rtol=1e-9, atol=1e-12)
         e2e_total = max_over_ranks(sum(e2e_ms), dist)
         h2d = 0
         for i in instances:
@@ -401,24 +427,29 @@ def main():
                 forms[fp] = {"mlups": out["value"] / world, "step_kernel_gbs": round(achieved, 1),
                              "frac_hbm": round(achieved / peak, 4)}
                 continue
-            ss = [L.solver_for_instance(inst, fp, stream) for inst in instances]
-            ev = []
+            # sequential on one stream: a 512^2 FP32/FP16 state stays resident in L2 across steps
+            ss = [L.solver_for_instance(inst, fp, main) for inst in instances]
+            for s, c in zip(ss, contours):  # warm-up (graphs, contour set-up)
+                s.step(64)
+                s.force_torque(c)
+                s.reset()
+            ev_ = []
             res = []
             t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            t0e.record(stream)
+            t0e.record(main)
             for s, inst, c in zip(ss, instances, contours):
                 n_plain = (inst["periods"] - 1) * inst["period"]
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
+                a.record(main)
                 s.step(n_plain)
-                b.record(stream)
-                ev.append((a, b, n_plain))
+                b.record(main)
+                ev_.append((a, b, n_plain))
                 res.append(s.force_torque(c))
-            t1e.record(stream)
+            t1e.record(main)
             t1e.synchronize()
             ms = t0e.elapsed_time(t1e)
-            pms = sum(a.elapsed_time(b) for a, b, _ in ev)
-            pn = sum(n for _, _, n in ev)
+            pms = sum(a.elapsed_time(b) for a, b, _ in ev_)
+            pn = sum(n for _, _, n in ev_)
             gbs = pn * 512 * 512 * BYTES_PER_LU[fp] / (pms / 1e3) / 1e9
             res = np.array(res)
             ref = results if prec == "f64" else res
@@ -434,22 +465,24 @@ def main():
 
     if not args.no_hbm_scale and rank == 0:
         # single-domain step kernel on an 8192^2 lattice (state far larger than the
-        # 129 MB L2): algorithmic bytes per launch / CUDA-event time per launch
+        # 129 MB L2): algorithmic bytes per lattice update x updates / CUDA-event time.
+        # The FP32 and FP16-deviation kernels advance two steps per launch (temporal
+        # blocking), so they can exceed the one-read-one-write-per-step roofline.
         big = W.md_janus_8192()[0]
         hs = {}
         for fp in ("f32", "f16dev", "f64"):
-            with L.solver_for_instance(big, fp, stream) as s:
+            with L.solver_for_instance(big, fp, main) as s:
                 s.step(4)
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 n = 16
-                a.record(stream)
+                a.record(main)
                 s.step(n)
-                b.record(stream)
+                b.record(main)
                 b.synchronize()
                 us = a.elapsed_time(b) * 1e3 / n
                 sites = big["nx"] * big["ny"]
                 gbs = sites * BYTES_PER_LU[fp] / (us / 1e6) / 1e9
-                hs[fp] = {"kernel": STEP_KERNEL[fp], "us_per_launch": round(us, 2),
+                hs[fp] = {"kernel": STEP_KERNEL[fp], "us_per_step": round(us, 2),
                           "glups": round(sites / (us / 1e6) / 1e9, 2), "achieved_gbs": round(gbs, 1),
                           "frac_hbm": round(gbs / peak, 4), "bytes_per_lu": BYTES_PER_LU[fp]}
                 if fp == "f64":
@@ -466,13 +499,13 @@ def main():
         dm = W.design_map_256(4, args.design_map_instances)
         res = {}
         for fp in ("f32", "f64"):
-            bt = L.Batch(dm, fp, stream=stream)
+            bt = L.Batch(dm, fp, stream=main)
             bt.run()
             bt.results()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
+            a.record(main)
             bt.run()
-            b.record(stream)
+            b.record(main)
             b.synchronize()
             F, _ = bt.results()
             res[fp] = (a.elapsed_time(b), F, bt.config())

@@ -62,10 +62,16 @@ typedef enum {
     LBM_EM_SRC_NONE = 2   /* no source (all edges open)                                  */
 } lbm_em_source_kind;
 
+/* lbm_em_grid.flags: run the FP32 and FP16-deviation forms one time step per kernel
+ * launch.  By default they advance two steps per launch (the intermediate state stays in
+ * shared memory); FP32 results are bit-identical either way, FP16-deviation keeps every
+ * second intermediate state in FP32 instead of FP16. */
+#define LBM_EM_FLAG_SINGLE_STEP 1
+
 typedef struct {
     int32_t nx, ny;       /* lattice size, each >= 4                                      */
     int32_t precision;    /* lbm_em_precision                                             */
-    int32_t reserved;     /* 0                                                            */
+    int32_t flags;        /* 0 or LBM_EM_FLAG_SINGLE_STEP                                 */
     void *stream;         /* cudaStream_t every kernel of the handle runs on; NULL: the
                              library creates a private non-blocking stream                */
 } lbm_em_grid;
@@ -122,7 +128,8 @@ lbm_em_status lbm_em_reset(lbm_em_t *h);
 
 /* Re-rasterise a Janus disc j into the handle's material map in place (same lattice;
  * region ids 0/1/2 as in lbm_em_create_janus), e.g. the next cell of a design map.
- * Does not touch the distributions (call lbm_em_reset for a fresh run).  Sec. II. */
+ * Does not touch the distributions (call lbm_em_reset for a fresh run).  Asynchronous
+ * on the handle's stream.  Sec. II. */
 lbm_em_status lbm_em_set_janus(lbm_em_t *h, const lbm_em_janus *j);
 
 /* Release every resource of the handle (NULL is accepted). */
@@ -154,6 +161,15 @@ lbm_em_status lbm_em_contour_integral(lbm_em_t *h, double out[3]);
 
 /* set_contour(c) + accumulate(T) + contour_integral(out): advances one period. */
 lbm_em_status lbm_em_force_torque(lbm_em_t *h, const lbm_em_contour *c, double out[3]);
+
+/* As lbm_em_contour_integral, but asynchronous: the three doubles are written to the
+ * device buffer d_out (8-byte aligned, caller-owned) on the handle's stream. */
+lbm_em_status lbm_em_contour_integral_device(lbm_em_t *h, double *d_out);
+
+/* As lbm_em_force_torque, but asynchronous with the result in the device buffer d_out:
+ * several handles on different streams can then run their periods concurrently.
+ * (Setting a contour that differs from the current one allocates and synchronises.) */
+lbm_em_status lbm_em_force_torque_device(lbm_em_t *h, const lbm_em_contour *c, double *d_out);
 
 /* Fields at the current time into host arrays [ny][nx] (any may be NULL).  Synchronous. */
 lbm_em_status lbm_em_get_fields(lbm_em_t *h, double *ez, double *hx, double *hy);
@@ -229,7 +245,7 @@ typedef struct lbm_em_batch lbm_em_batch_t;
 lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n,
                                   const lbm_em_batch_opts *o, lbm_em_batch_t **out);
 
-/* Run every instance to completion (persistent kernel over the packed tile list,
+/* Rasterise every instance, then run each to completion (persistent kernel over the packed tile list,
  * replayed under a CUDA graph), then the contour integral of each.  Asynchronous. */
 lbm_em_status lbm_em_batch_run(lbm_em_batch_t *b);
 

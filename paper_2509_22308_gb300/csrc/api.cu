@@ -15,6 +15,7 @@
 #include "../../include/lbm_em.h"
 #include "common.cuh"
 #include "runtime.h"
+#include "step2.cuh"
 #include "step_f16.cuh"
 
 using namespace lbmem;
@@ -155,6 +156,8 @@ struct lbm_em {
     SourceParams src{};
     lbm_em_source srccfg{};
     int64_t t = 0;
+    int cur = 0;      // buffer holding the current state (and device time word)
+    bool tb = false;  // two steps per launch (temporal blocking) for the HBM-bound forms
     // contour and accumulators
     bool has_contour = false;
     lbm_em_contour contour{};
@@ -167,6 +170,8 @@ struct lbm_em {
     // graphs of kGraphSteps steps starting at an even time
     cudaGraphExec_t g_plain = nullptr, g_acc = nullptr;
     double *d_fields = nullptr;
+    void *h_stage = nullptr;       // pinned staging of the material table (async uploads)
+    cudaEvent_t stage_ev = nullptr;  // the last table upload from h_stage
 };
 
 static const int kGraphSteps = 32;
@@ -218,8 +223,8 @@ static F16Args make_f16_args(const lbm_em *h, int p) {
     return a;
 }
 
-static cudaError_t enqueue_step(lbm_em *h, bool acc, cudaStream_t s, int64_t t) {
-    const int p = (int)(t & 1);
+// One step: state in buf[p] -> buf[1 - p], time word p -> 1 - p.
+static cudaError_t enqueue_step(lbm_em *h, bool acc, cudaStream_t s, int p) {
     if (h->prec == LBM_EM_F16DEV)
         return launch_step_f16(make_f16_args(h, p), h->d_time + p, h->d_time + (1 - p), acc, s);
     if (h->prec == LBM_EM_F64)
@@ -229,13 +234,25 @@ static cudaError_t enqueue_step(lbm_em *h, bool acc, cudaStream_t s, int64_t t) 
                               h->d_time + p, h->d_time + (1 - p), acc, s);
 }
 
+// Two steps in one launch (temporal blocking): buf[p] -> buf[1 - p].
+static cudaError_t enqueue_step2(lbm_em *h, bool acc, cudaStream_t s, int p) {
+    if (h->prec == LBM_EM_F16DEV)
+        return launch_step2_f16(make_f16_args(h, p), h->d_time + p, h->d_time + (1 - p), acc, s);
+    return launch_step2_f32(make_args<float>(h), (const float *)h->buf[p], (float *)h->buf[1 - p], h->d_time + p,
+                            h->d_time + (1 - p), acc, s);
+}
+
+// kGraphSteps steps starting from buffer 0 (an even number of launches, so the
+// state is back in buffer 0 at the end).
 static lbm_em_status build_graph(lbm_em *h, bool acc, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     lbm_em_status st = cuda_status(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal),
                                    "cudaStreamBeginCapture");
     if (st) return st;
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) e = enqueue_step(h, acc, h->cap, i);
+    const int launches = h->tb ? kGraphSteps / 2 : kGraphSteps;
+    for (int i = 0; i < launches && e == cudaSuccess; ++i)
+        e = h->tb ? enqueue_step2(h, acc, h->cap, i & 1) : enqueue_step(h, acc, h->cap, i & 1);
     cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -246,9 +263,13 @@ static lbm_em_status build_graph(lbm_em *h, bool acc, cudaGraphExec_t *out) {
     return cuda_status(e, "cudaGraphInstantiate");
 }
 
+// With two steps per launch, launches start at even t only (an odd start takes one
+// single step first), so which intermediate states skip the storage rounding of the
+// FP16-deviation form does not depend on how a run is split into calls.
 static lbm_em_status run_steps(lbm_em *h, int64_t n, bool acc) {
     while (n > 0) {
-        if ((h->t & 1) == 0 && n >= kGraphSteps) {
+        const bool even = (h->t & 1) == 0;
+        if (h->cur == 0 && n >= kGraphSteps && (even || !h->tb)) {
             cudaGraphExec_t *g = acc ? &h->g_acc : &h->g_plain;
             if (!*g) {
                 lbm_em_status st = build_graph(h, acc, g);
@@ -258,9 +279,16 @@ static lbm_em_status run_steps(lbm_em *h, int64_t n, bool acc) {
             if (st) return st;
             h->t += kGraphSteps;
             n -= kGraphSteps;
-        } else {
-            lbm_em_status st = cuda_status(enqueue_step(h, acc, h->stream, h->t), "step launch");
+        } else if (h->tb && n >= 2 && even) {
+            lbm_em_status st = cuda_status(enqueue_step2(h, acc, h->stream, h->cur), "step launch");
             if (st) return st;
+            h->cur ^= 1;
+            h->t += 2;
+            n -= 2;
+        } else {
+            lbm_em_status st = cuda_status(enqueue_step(h, acc, h->stream, h->cur), "step launch");
+            if (st) return st;
+            h->cur ^= 1;
             h->t += 1;
             n -= 1;
         }
@@ -296,6 +324,8 @@ static void free_handle(lbm_em *h) {
     cudaFree(h->d_out);
     cudaFree(h->d_fields);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->stage_ev) cudaEventDestroy(h->stage_ev);
+    if (h->h_stage) cudaFreeHost(h->h_stage);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -318,6 +348,7 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     if (!g || !out) return set_error(LBM_EM_EINVAL, "grid/out is NULL");
     *out = nullptr;
     if (g->nx < 4 || g->ny < 4) return set_error(LBM_EM_EINVAL, "nx and ny must be >= 4");
+    if (g->flags & ~LBM_EM_FLAG_SINGLE_STEP) return set_error(LBM_EM_EINVAL, "unknown grid flags");
     if ((long long)g->nx * g->ny > (1LL << 31)) return set_error(LBM_EM_EINVAL, "lattice too large (> 2^31 sites)");
     if (g->precision != LBM_EM_F64 && g->precision != LBM_EM_F32 && g->precision != LBM_EM_F16DEV)
         return set_error(LBM_EM_EINVAL, "precision must be LBM_EM_F64, LBM_EM_F32 or LBM_EM_F16DEV");
@@ -337,6 +368,7 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     h->pitch = round_up(g->nx, 32);
     h->pstride = (size_t)h->pitch * (size_t)g->ny;
     h->srccfg = *s;
+    h->tb = (g->precision == LBM_EM_F32 || g->precision == LBM_EM_F16DEV) && !(g->flags & LBM_EM_FLAG_SINGLE_STEP);
     for (int i = 0; i < 256; ++i) {
         h->eps_table[i] = 1.0;
         h->pec_id[i] = false;
@@ -356,6 +388,7 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
         h->own_stream = true;
     }
     TRY(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (h->tb) TRY(step2_prepare(), "configuring the two-step kernels");
     h->buf_bytes = g->precision == LBM_EM_F16DEV ? f16_buffer_bytes(h->pstride)
                                                   : (size_t)NPLANES * h->pstride * h->elem;
     const size_t bytes = h->buf_bytes;
@@ -371,6 +404,9 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     TRY(cudaMalloc(&h->d_err, sizeof(unsigned)), "cudaMalloc(err)");
     TRY(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream), "cudaMemset");
     TRY(cudaMalloc(&h->d_out, 4 * sizeof(double)), "cudaMalloc(out)");
+    TRY(cudaMallocHost(&h->h_stage, 256 * sizeof(MatT<double>)), "cudaMallocHost(table staging)");
+    TRY(cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming), "cudaEventCreate");
+    TRY(cudaEventRecord(h->stage_ev, h->stream), "cudaEventRecord");
     std::vector<double2> cs = phase_table(s->period_steps);
     TRY(cudaMalloc(&h->d_cs, cs.size() * sizeof(double2)), "cudaMalloc(phase table)");
     TRY(cudaMemcpyAsync(h->d_cs, cs.data(), cs.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream),
@@ -386,17 +422,22 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     return LBM_EM_OK;
 }
 
+// Material table -> device without blocking the host on the stream: the table goes
+// through a pinned staging buffer that is reused once its previous copy has finished.
 static lbm_em_status upload_table(lbm_em *h) {
-    cudaError_t e;
+    cudaError_t e = cudaEventSynchronize(h->stage_ev);
+    size_t bytes;
     if (h->prec == LBM_EM_F64) {
         auto tab = material_table<double>(h->eps_table, h->pec_id);
-        e = cudaMemcpyAsync(h->d_mtab, tab.data(), tab.size() * sizeof(tab[0]), cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        bytes = tab.size() * sizeof(tab[0]);
+        std::memcpy(h->h_stage, tab.data(), bytes);
     } else {
         auto tab = material_table<float>(h->eps_table, h->pec_id);
-        e = cudaMemcpyAsync(h->d_mtab, tab.data(), tab.size() * sizeof(tab[0]), cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        bytes = tab.size() * sizeof(tab[0]);
+        std::memcpy(h->h_stage, tab.data(), bytes);
     }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_mtab, h->h_stage, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->stage_ev, h->stream);
     return cuda_status(e, "uploading the material table");
 }
 
@@ -494,6 +535,7 @@ lbm_em_status lbm_em_reset(lbm_em_t *h) {
                          "clearing accumulators");
     if (st) return st;
     h->t = 0;
+    h->cur = 0;
     h->n_acc = 0;
     return LBM_EM_OK;
 }
@@ -618,6 +660,22 @@ lbm_em_status lbm_em_contour_integral(lbm_em_t *h, double out[3]) {
     return LBM_EM_OK;
 }
 
+lbm_em_status lbm_em_contour_integral_device(lbm_em_t *h, double *d_out) {
+    if (!h || !d_out) return set_error(LBM_EM_EINVAL, "NULL argument");
+    if (!h->has_contour || h->n_acc <= 0) return set_error(LBM_EM_ESTATE, "no accumulated steps");
+    cudaSetDevice(h->dev);
+    return cuda_status(launch_contour(h->d_acc, 2.0 / (double)h->n_acc, h->d_pts, (int)h->ch.pts.size(), h->ch.R,
+                                      h->ch.dl, h->ch.F0, h->ch.M0, d_out, h->stream),
+                       "contour kernel");
+}
+
+lbm_em_status lbm_em_force_torque_device(lbm_em_t *h, const lbm_em_contour *c, double *d_out) {
+    lbm_em_status st = lbm_em_set_contour(h, c);
+    if (!st) st = lbm_em_accumulate(h, h->srccfg.period_steps);
+    if (!st) st = lbm_em_contour_integral_device(h, d_out);
+    return st;
+}
+
 lbm_em_status lbm_em_force_torque(lbm_em_t *h, const lbm_em_contour *c, double out[3]) {
     lbm_em_status st = lbm_em_set_contour(h, c);
     if (!st) st = lbm_em_accumulate(h, h->srccfg.period_steps);
@@ -632,7 +690,7 @@ lbm_em_status lbm_em_get_fields(lbm_em_t *h, double *ez, double *hx, double *hy)
     lbm_em_status st = LBM_EM_OK;
     if (!h->d_fields) st = cuda_status(cudaMalloc(&h->d_fields, 3 * n * sizeof(double)), "cudaMalloc(fields)");
     if (st) return st;
-    const int p = (int)(h->t & 1);
+    const int p = h->cur;
     cudaError_t e;
     if (h->prec == LBM_EM_F16DEV)
         e = launch_fields_f16(make_f16_args(h, p), h->d_time + p, h->d_fields, h->d_fields + n,
@@ -710,7 +768,7 @@ lbm_em_status lbm_em_save_state(lbm_em_t *h, void *buf, size_t *bytes) {
     std::memcpy(buf, &hd, sizeof(hd));
     char *p = (char *)buf + sizeof(hd);
     lbm_em_status st = cuda_status(
-        cudaMemcpyAsync(p, h->buf[h->t & 1], dist, cudaMemcpyDeviceToHost, h->stream), "saving distributions");
+        cudaMemcpyAsync(p, h->buf[h->cur], dist, cudaMemcpyDeviceToHost, h->stream), "saving distributions");
     if (!st && accb)
         st = cuda_status(cudaMemcpyAsync(p + dist, h->d_acc, accb, cudaMemcpyDeviceToHost, h->stream), "saving acc");
     if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
@@ -734,10 +792,10 @@ lbm_em_status lbm_em_load_state(lbm_em_t *h, const void *buf, size_t bytes) {
     const char *p = (const char *)buf + sizeof(hd);
     long long tt = hd.t;
     lbm_em_status st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
-    if (!st) st = cuda_status(cudaMemcpy(h->buf[hd.t & 1], p, dist, cudaMemcpyHostToDevice), "loading distributions");
+    if (!st) st = cuda_status(cudaMemcpy(h->buf[h->cur], p, dist, cudaMemcpyHostToDevice), "loading distributions");
     if (!st && accb) st = cuda_status(cudaMemcpy(h->d_acc, p + dist, accb, cudaMemcpyHostToDevice), "loading acc");
     if (!st)
-        st = cuda_status(cudaMemcpy(h->d_time + (hd.t & 1), &tt, sizeof(tt), cudaMemcpyHostToDevice), "loading time");
+        st = cuda_status(cudaMemcpy(h->d_time + h->cur, &tt, sizeof(tt), cudaMemcpyHostToDevice), "loading time");
     if (st) return st;
     h->t = hd.t;
     h->n_acc = hd.n_acc;

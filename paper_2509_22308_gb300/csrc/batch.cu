@@ -238,6 +238,20 @@ static lbm_em_status batch_tiles(lbm_em_batch *b, int tw, int th) {
     return st;
 }
 
+// Staircase Janus disc of every instance into the packed material ids (Sec. II).
+static cudaError_t batch_rasterize(lbm_em_batch *b) {
+    for (int i = 0; i < b->n; ++i) {
+        const InstDesc &d = b->desc[i];
+        const lbm_em_janus &j = b->specs[i].janus;
+        double cx, cy;
+        janus_center(&j, d.nx, d.ny, &cx, &cy);
+        cudaError_t e = launch_rasterize(d.nx, d.ny, d.pitch, cx, cy, j.a, -std::sin(j.phi0), -std::cos(j.phi0),
+                                         b->d_mat + d.mat_base, b->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, long long t) {
     const int p = (int)(t & 1);
     const int grid = b->ctas * b->sms;
@@ -454,15 +468,8 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
         BTRY(cudaMalloc(&b->d_cdesc, n * sizeof(ContourDesc)), "cudaMalloc(contour desc)");
         BTRY(cudaMemcpy(b->d_cdesc, cd.data(), n * sizeof(ContourDesc), cudaMemcpyHostToDevice), "upload");
     }
-    // rasterise every instance on the device
-    for (int i = 0; i < n; ++i) {
-        const InstDesc &d = b->desc[i];
-        double cx, cy;
-        janus_center(&specs[i].janus, d.nx, d.ny, &cx, &cy);
-        BTRY(launch_rasterize(d.nx, d.ny, d.pitch, cx, cy, specs[i].janus.a, -std::sin(specs[i].janus.phi0),
-                              -std::cos(specs[i].janus.phi0), b->d_mat + d.mat_base, b->stream),
-             "rasterise");
-    }
+    // rasterise every instance on the device (again at every run)
+    BTRY(batch_rasterize(b), "rasterise");
     // run order: decreasing number of steps
     b->order.resize(n);
     std::iota(b->order.begin(), b->order.end(), 0);
@@ -483,6 +490,7 @@ lbm_em_status lbm_em_batch_run(lbm_em_batch_t *b) {
     if (!b) return set_error(LBM_EM_EINVAL, "batch is NULL");
     cudaSetDevice(b->dev);
     lbm_em_status st = b->ran ? batch_clear(b) : LBM_EM_OK;
+    if (!st) st = cuda_status(batch_rasterize(b), "rasterise");
     if (st) return st;
     if (!b->graph) {
         cudaGraph_t g = nullptr;

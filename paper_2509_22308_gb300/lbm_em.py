@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm_em.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
 F64, F32, F16DEV = 0, 1, 2
+FLAG_SINGLE_STEP = 1
 SRC_OPEN, SRC_HARD, SRC_NONE = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ETIMEOUT", 6: "ESTATE"}
 PRECISIONS = {"f64": F64, "f32": F32, "f16dev": F16DEV}
@@ -29,7 +30,7 @@ class LbmEmError(RuntimeError):
 
 class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class Source(ctypes.Structure):
@@ -75,6 +76,8 @@ SIGNATURES = {
     "lbm_em_accumulate": [_vp, ctypes.c_int64],
     "lbm_em_contour_integral": [_vp, _P(ctypes.c_double)],
     "lbm_em_force_torque": [_vp, _P(Contour), _P(ctypes.c_double)],
+    "lbm_em_contour_integral_device": [_vp, _vp],
+    "lbm_em_force_torque_device": [_vp, _P(Contour), _vp],
     "lbm_em_get_fields": [_vp, _P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_double)],
     "lbm_em_get_phasors": [_vp, _P(ctypes.c_int32), _P(ctypes.c_double), _P(ctypes.c_int32)],
     "lbm_em_get_material": [_vp, _P(ctypes.c_uint8), _P(ctypes.c_double)],
@@ -155,11 +158,12 @@ class Solver:
     """Owner of one ``lbm_em_t`` handle; methods map one-to-one onto the C calls."""
 
     def __init__(self, nx, ny, precision="f64", *, janus: Janus | None = None, eps_map=None, pec_mask=None,
-                 source: Source, stream=None):
+                 source: Source, stream=None, single_step=False):
         L = load()
         self.nx, self.ny = int(nx), int(ny)
         self.source = source
-        g = Grid(self.nx, self.ny, PRECISIONS.get(precision, precision), 0, _stream_ptr(stream))
+        g = Grid(self.nx, self.ny, PRECISIONS.get(precision, precision), FLAG_SINGLE_STEP if single_step else 0,
+                 _stream_ptr(stream))
         h = ctypes.c_void_p()
         if janus is not None:
             _call("lbm_em_create_janus", ctypes.byref(g), ctypes.byref(janus), ctypes.byref(source), ctypes.byref(h))
@@ -222,6 +226,10 @@ class Solver:
         _call("lbm_em_force_torque", self.h, ctypes.byref(c), _dptr(out))
         return out
 
+    def force_torque_device(self, c: Contour, d_out_ptr: int):
+        """Asynchronous force/torque into a device buffer of 3 doubles (e.g. a torch tensor's data_ptr)."""
+        _call("lbm_em_force_torque_device", self.h, ctypes.byref(c), ctypes.c_void_p(int(d_out_ptr)))
+
     def fields(self):
         ez = np.empty((self.ny, self.nx))
         hx = np.empty_like(ez)
@@ -268,17 +276,17 @@ def rasterize_janus_noalloc(j: Janus, nx, ny):
     return out
 
 
-def solver_for_instance(inst: dict, precision="f64", stream=None, kind=SRC_OPEN) -> Solver:
+def solver_for_instance(inst: dict, precision="f64", stream=None, kind=SRC_OPEN, single_step=False) -> Solver:
     """Solver for one workload instance dictionary (see ``workloads``)."""
     j = make_janus(inst["a"], inst["phi0"], inst["eps1"], inst["eps2"], inst["pec2"])
     s = make_source(inst["period"], inst.get("ramp"), kind)
-    return Solver(inst["nx"], inst["ny"], precision, janus=j, source=s, stream=stream)
+    return Solver(inst["nx"], inst["ny"], precision, janus=j, source=s, stream=stream, single_step=single_step)
 
 
-def run_instance(inst: dict, precision="f64", stream=None) -> np.ndarray:
+def run_instance(inst: dict, precision="f64", stream=None, single_step=False) -> np.ndarray:
     """Full hot path for one instance: (periods - 1) periods of steps, one accumulated
     period, contour integral -> (F~x, F~y, M~z)."""
-    with solver_for_instance(inst, precision, stream) as s:
+    with solver_for_instance(inst, precision, stream, single_step=single_step) as s:
         s.step((inst["periods"] - 1) * inst["period"])
         return s.force_torque(make_contour(inst["R"], inst["a"]))
 

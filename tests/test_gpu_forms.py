@@ -113,3 +113,35 @@ def test_batch_reports_unstable_instance():
                                        st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
     assert rc == L.EUNSTABLE and st[0] == L.OK and st[1] == L.EUNSTABLE
     L.load().lbm_em_batch_destroy(h)
+
+
+@pytest.mark.parametrize("inst", W.small_cases()[:3], ids=lambda i: f"{i['nx']}x{i['ny']}")
+def test_two_steps_per_launch_is_bit_identical_in_fp32(inst):
+    """FP32 with two steps per launch (temporal blocking) equals one step per launch bit
+    for bit, for even and odd step counts and through the accumulating period."""
+    with L.solver_for_instance(inst, "f32") as a, L.solver_for_instance(inst, "f32", single_step=True) as b:
+        for n in (1, 2, 5, 32, 33, 64, 3):
+            a.step(n)
+            b.step(n)
+            for x, y in zip(a.fields(), b.fields()):
+                assert np.array_equal(x, y)
+        c = L.make_contour(inst["R"], inst["a"])
+        assert np.array_equal(a.force_torque(c), b.force_torque(c))
+
+
+def test_f16dev_split_runs_agree_bitwise():
+    """The FP16-deviation form gives the same bits however a run is split into calls."""
+    inst = W.small_cases()[2]
+    with L.solver_for_instance(inst, "f16dev") as a, L.solver_for_instance(inst, "f16dev") as b:
+        a.step(77)
+        for n in (3, 30, 1, 43):
+            b.step(n)
+        for x, y in zip(a.fields(), b.fields()):
+            assert np.array_equal(x, y)
+
+
+def test_f16dev_single_step_mode_within_tolerance():
+    inst = W.homogeneous_dielectric_256()[0]
+    F64 = L.run_instance(inst, "f64")
+    F16 = L.run_instance(inst, "f16dev", single_step=True)
+    assert np.max(np.abs(F16 - F64)) < 1e-3 * abs(F64[0])
