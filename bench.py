@@ -30,12 +30,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS & HBM GB/s (% of peak) per precision form; design-map cells/sec at <=1e-3 force err"
 WORKLOAD = "md_janus_512"
-BYTES_PER_LU = {"f64": 16 * 8 * 2 + 1, "f32": 16 * 4 * 2 + 1, "f16dev": 2 * (16 * 2 + 3 * 4) + 1}
+# algorithmic bytes per lattice update: the 11 stored planes read and written once, plus
+# the 1-byte material id (FP16-deviation: 11 FP16 deviations + 3 FP32 fields each way)
+BYTES_PER_LU = {"f64": 11 * 8 * 2 + 1, "f32": 11 * 4 * 2 + 1, "f16dev": 2 * (11 * 2 + 3 * 4) + 1}
 STEP_KERNEL = {"f64": "k_step<double, false>", "f32": "k_step2_f32<false> (two steps per launch)",
                "f16dev": "k_step2_f16<false> (two steps per launch)"}
-# FP64 pipe operations per lattice update of the step kernel: 16 for the moments
-# (sums of 6, 5 and 5 populations, one scaling), 20 for the equilibria and 2 f^eq - f
-FP64_OPS_PER_LU = 36
+# FP64 pipe operations per lattice update of the step kernel: 12 for the moments
+# (sums of 5, 5 and 5 stored populations, one scaling), 16 for the equilibria and 2 f^eq - f
+FP64_OPS_PER_LU = 28
 SMS, FP64_OPS_PER_CLK_PER_SM = 152, 2
 
 
@@ -50,7 +52,7 @@ def parse_args():
     p.add_argument("--no-design-map", action="store_true")
     p.add_argument("--design-map-instances", type=int, default=24)
     p.add_argument("--profile-case", action="store_true",
-                   help="small case for ncu: 2 steps per storage form on a 2048^2 lattice and 2 FP64 steps on the 512^2 workload")
+                   help="small case for ncu: two launches of each step kernel on a 2048^2 lattice and of the FP64 step on the 512^2 workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -215,18 +217,19 @@ def run_reference(args, rank, world):
 
 
 def profile_case():
-    """Two launches of each storage form's step kernel on a 2048^2 lattice (state
-    0.27-1.1 GB per buffer, larger than L2, a few GB on the device in total), then two
-    launches of the FP64 step on one 512^2 instance of the benchmark workload."""
+    """Two launches of each step kernel (FP64; FP32 and FP16-deviation with two steps
+    per launch, then with one) on a 2048^2 lattice (state 0.3-0.7 GB per buffer, larger
+    than L2, a few GB on the device in total), then two launches of the FP64 step on
+    one 512^2 instance of the benchmark workload."""
     import torch
     from paper_2509_22308_gb300 import build as B
     B.build()
     from paper_2509_22308_gb300 import lbm_em as L
     inst = dict(nx=2048, ny=2048, a=128.0, phi0=0.5, eps1=4.0, eps2=1.0, pec2=True, period=240, periods=1,
                 R=192.0, ramp=240)
-    for fp in ("f64", "f32", "f16dev"):
-        with L.solver_for_instance(inst, fp) as s:
-            s.step(2)
+    for fp, single in (("f64", False), ("f32", False), ("f16dev", False), ("f32", True), ("f16dev", True)):
+        with L.solver_for_instance(inst, fp, single_step=single) as s:
+            s.step(2 if single or fp == "f64" else 4)
             s.sync()
     # and two launches of the benchmark's own 512^2 FP64 instance (theta = 0)
     from paper_2509_22308_gb300 import workloads as W
@@ -470,8 +473,9 @@ def main():
         # blocking), so they can exceed the one-read-one-write-per-step roofline.
         big = W.md_janus_8192()[0]
         hs = {}
-        for fp in ("f32", "f16dev", "f64"):
-            with L.solver_for_instance(big, fp, main) as s:
+        for fp, single in (("f32", False), ("f16dev", False), ("f32", True), ("f16dev", True), ("f64", False)):
+            key = fp + ("_one_step_per_launch" if single else "")
+            with L.solver_for_instance(big, fp, main, single_step=single) as s:
                 s.step(4)
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 n = 16
@@ -482,13 +486,15 @@ def main():
                 us = a.elapsed_time(b) * 1e3 / n
                 sites = big["nx"] * big["ny"]
                 gbs = sites * BYTES_PER_LU[fp] / (us / 1e6) / 1e9
-                hs[fp] = {"kernel": STEP_KERNEL[fp], "us_per_step": round(us, 2),
+                hs[key] = {"kernel": STEP_KERNEL[fp] if not single else
+                           {"f32": "k_step<float, false>", "f16dev": "k_step_f16<false>"}[fp],
+                           "us_per_step": round(us, 2),
                           "glups": round(sites / (us / 1e6) / 1e9, 2), "achieved_gbs": round(gbs, 1),
                           "frac_hbm": round(gbs / peak, 4), "bytes_per_lu": BYTES_PER_LU[fp]}
                 if fp == "f64":
                     t_ops = sites * FP64_OPS_PER_LU / (us / 1e6) / 1e12
-                    hs[fp]["fp64_tops"] = round(t_ops, 4)
-                    hs[fp]["frac_fp64_pipe"] = round(t_ops / (SMS * FP64_OPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12), 4)
+                    hs[key]["fp64_tops"] = round(t_ops, 4)
+                    hs[key]["frac_fp64_pipe"] = round(t_ops / (SMS * FP64_OPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12), 4)
         out["single_domain_8192"] = hs
 
     if not args.no_design_map and rank == 0:

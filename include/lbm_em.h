@@ -171,6 +171,28 @@ lbm_em_status lbm_em_contour_integral_device(lbm_em_t *h, double *d_out);
  * (Setting a contour that differs from the current one allocates and synchronises.) */
 lbm_em_status lbm_em_force_torque_device(lbm_em_t *h, const lbm_em_contour *c, double *d_out);
 
+/* Far-field scattering intensity |S(phi)|^2 = k0 r |E^S|^2 / |E^I|^2 (Sec. II.A, Eq.
+ * scattering intensity) at n_angles observation angles (radians, lattice frame: 0 is
+ * forward, along +x) from the accumulated phasors on the current contour, by a
+ * near-to-far-field transform (Green's theorem with the Hankel asymptote; the scattered
+ * near field is the phasor minus the lattice's exact incident plane wave).  Uses the
+ * lattice wavenumber of the source period.  Host arrays; synchronous. */
+lbm_em_status lbm_em_far_field(lbm_em_t *h, const double *angles, int32_t n_angles, double *s2);
+
+/* Total electromagnetic energy of the lattice at the current time,
+ * W = sum over sites of (eps_r E_z^2 + H_x^2 + H_y^2) / 2 (lattice units), the quantity whose
+ * approach to a constant the paper uses as its convergence criterion (Sec. III).  Synchronous. */
+lbm_em_status lbm_em_energy(lbm_em_t *h, double *W);
+
+/* Run whole periods until the energy sampled at the end of each period (so always at
+ * the same phase) has changed by at most tol * W twice in a row, after at least
+ * min_periods - 1 periods, or until max_periods - 1 periods have run; then (one step
+ * later if it converged, as the batched path does) one accumulated period and the
+ * contour integral into out[3] as lbm_em_force_torque.  *steps_run (may be NULL)
+ * receives the number of steps taken.  Convergence criterion of Sec. III. */
+lbm_em_status lbm_em_run_converged(lbm_em_t *h, const lbm_em_contour *c, double tol, int32_t min_periods,
+                                   int32_t max_periods, double out[3], int64_t *steps_run);
+
 /* Fields at the current time into host arrays [ny][nx] (any may be NULL).  Synchronous. */
 lbm_em_status lbm_em_get_fields(lbm_em_t *h, double *ez, double *hx, double *hy);
 
@@ -235,7 +257,12 @@ typedef struct {
     int32_t precision;       /* LBM_EM_F32 or LBM_EM_F64                                    */
     int32_t tile_w, tile_h;  /* tile shape of the packed tile list; 0: autotuned           */
     int32_t ctas_per_sm;     /* persistent CTAs per SM; 0: autotuned                       */
+    int32_t min_periods;     /* convergence exits: fewest periods an instance runs         */
     int32_t reserved;        /* 0                                                          */
+    double conv_tol;         /* 0: every instance runs its `periods`; > 0: an instance stops
+                                early once its domain energy, sampled at each period end,
+                                changes by <= conv_tol * W twice in a row (Sec. III), then
+                                runs one accumulated period; `periods` is the maximum     */
     void *stream;            /* cudaStream_t; NULL: private stream                         */
 } lbm_em_batch_opts;
 
@@ -252,6 +279,10 @@ lbm_em_status lbm_em_batch_run(lbm_em_batch_t *b);
 /* Wait and fetch results: out[3*i .. 3*i+2] = {F~x, F~y, M~z} of instance i and
  * status[i] (an lbm_em_status) per instance; either may be NULL. */
 lbm_em_status lbm_em_batch_results(lbm_em_batch_t *b, double *out, int32_t *status);
+
+/* Steps each instance ran in the last lbm_em_batch_run (its run length, shortened by a
+ * convergence exit when conv_tol > 0), steps[n].  Synchronous. */
+lbm_em_status lbm_em_batch_steps(lbm_em_batch_t *b, int64_t *steps);
 
 /* Chosen tile shape and CTAs per SM (after autotuning), for reporting. */
 lbm_em_status lbm_em_batch_config(lbm_em_batch_t *b, int32_t *tile_w, int32_t *tile_h,

@@ -14,6 +14,7 @@
 
 #include "../../include/lbm_em.h"
 #include "common.cuh"
+#include "launchers.h"
 #include "runtime.h"
 #include "step2.cuh"
 #include "step_f16.cuh"
@@ -49,6 +50,12 @@ void incident_constants(int period, double E0, double *pr, double *pi, double *q
     *pi = P.imag();
     *qr = Q.real();
     *qi = Q.imag();
+}
+
+double lattice_wavenumber(int period) {
+    const double om = 2.0 * M_PI / (double)period;
+    const std::complex<double> z = std::exp(std::complex<double>(0.0, -om));
+    return std::arg((3.0 - z) / (z * (3.0 * z - 1.0)));
 }
 
 std::vector<double2> phase_table(int period) {
@@ -165,6 +172,7 @@ struct lbm_em {
     int *d_slot = nullptr;
     double *d_acc = nullptr;
     ContourPt *d_pts = nullptr;
+    double2 *d_inc = nullptr;   // incident E_z phasor at every stencil site (far field)
     double *d_out = nullptr;
     int64_t n_acc = 0;
     // graphs of kGraphSteps steps starting at an even time
@@ -302,9 +310,11 @@ static void free_contour(lbm_em *h) {
     cudaFree(h->d_slot);
     cudaFree(h->d_acc);
     cudaFree(h->d_pts);
+    cudaFree(h->d_inc);
     h->d_slot = nullptr;
     h->d_acc = nullptr;
     h->d_pts = nullptr;
+    h->d_inc = nullptr;
     h->has_contour = false;
 }
 
@@ -337,7 +347,7 @@ static std::vector<MatT<T>> material_table(const double *eps, const bool *pec) {
         if (pec[i]) {
             tab[i] = MatT<T>{(T)0, (T)0, (T)0, (T)0};
         } else {
-            tab[i] = MatT<T>{(T)(1.0 / (3.0 * eps[i])), (T)(6.0 * (eps[i] - 1.0)), (T)(1.0 / eps[i]), (T)0};
+            tab[i] = MatT<T>{(T)(1.0 / (3.0 * eps[i])), (T)(6.0 * eps[i] - 4.0), (T)(1.0 / eps[i]), (T)0};
         }
     }
     return tab;
@@ -622,6 +632,21 @@ lbm_em_status lbm_em_set_contour(lbm_em_t *h, const lbm_em_contour *c) {
         st = cuda_status(cudaMemcpy(h->d_pts, ch.pts.data(), ch.pts.size() * sizeof(ContourPt), cudaMemcpyHostToDevice),
                          "uploading contour");
     if (!st) st = cuda_status(cudaMemset(h->d_acc, 0, (size_t)ch.n_slots * 6 * sizeof(double)), "clearing acc");
+    if (!st) {
+        // incident E_z phasor i E0 e^{i k x} of the lattice's plane wave at each stencil site
+        std::vector<double2> inc(ch.n_slots, make_double2(0.0, 0.0));
+        if (h->srccfg.kind != LBM_EM_SRC_NONE) {
+            const double k = lattice_wavenumber(h->srccfg.period_steps);
+            for (int s = 0; s < ch.n_slots; ++s) {
+                const double kx = k * (double)ch.site_xy[2 * s];
+                inc[s] = make_double2(-h->srccfg.E0 * std::sin(kx), h->srccfg.E0 * std::cos(kx));
+            }
+        }
+        st = cuda_status(cudaMalloc(&h->d_inc, inc.size() * sizeof(double2)), "cudaMalloc(incident)");
+        if (!st)
+            st = cuda_status(cudaMemcpy(h->d_inc, inc.data(), inc.size() * sizeof(double2), cudaMemcpyHostToDevice),
+                             "uploading incident");
+    }
     if (st) {
         free_contour(h);
         return st;
@@ -680,6 +705,89 @@ lbm_em_status lbm_em_force_torque(lbm_em_t *h, const lbm_em_contour *c, double o
     lbm_em_status st = lbm_em_set_contour(h, c);
     if (!st) st = lbm_em_accumulate(h, h->srccfg.period_steps);
     if (!st) st = lbm_em_contour_integral(h, out);
+    return st;
+}
+
+lbm_em_status lbm_em_far_field(lbm_em_t *h, const double *angles, int32_t n_angles, double *s2) {
+    if (!h || !angles || !s2 || n_angles < 1) return set_error(LBM_EM_EINVAL, "bad far-field arguments");
+    if (!h->has_contour || h->n_acc <= 0) return set_error(LBM_EM_ESTATE, "no accumulated steps");
+    cudaSetDevice(h->dev);
+    double *d = nullptr;
+    lbm_em_status st = cuda_status(cudaMalloc(&d, (size_t)n_angles * 4 * sizeof(double)), "cudaMalloc(far field)");
+    if (st) return st;
+    double *d_ang = d + 3 * (size_t)n_angles;
+    std::vector<double> res(3 * (size_t)n_angles);
+    st = cuda_status(cudaMemcpyAsync(d_ang, angles, n_angles * sizeof(double), cudaMemcpyHostToDevice, h->stream),
+                     "uploading angles");
+    if (!st)
+        st = cuda_status(launch_farfield(h->d_acc, 2.0 / (double)h->n_acc, h->d_pts, (int)h->ch.pts.size(), h->d_inc,
+                                         h->ch.R, h->ch.dl, lattice_wavenumber(h->srccfg.period_steps), h->srccfg.E0,
+                                         d_ang, n_angles, d, h->stream),
+                         "far-field kernel");
+    if (!st)
+        st = cuda_status(cudaMemcpyAsync(res.data(), d, res.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                         "reading far field");
+    if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    cudaFree(d);
+    if (st) return st;
+    for (int j = 0; j < n_angles; ++j) s2[j] = res[3 * (size_t)j];
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_energy(lbm_em_t *h, double *W) {
+    if (!h || !W) return set_error(LBM_EM_EINVAL, "NULL argument");
+    cudaSetDevice(h->dev);
+    const int p = h->cur;
+    double *d = h->d_out + 3;  // the fourth word of the result buffer
+    lbm_em_status st = cuda_status(cudaMemsetAsync(d, 0, sizeof(double), h->stream), "clearing energy");
+    cudaError_t e = cudaSuccess;
+    if (!st) {
+        if (h->prec == LBM_EM_F16DEV)
+            e = launch_energy_f16(make_f16_args(h, p), h->d_time + p, d, h->stream);
+        else if (h->prec == LBM_EM_F64)
+            e = launch_energy<double>(make_args<double>(h), (const double *)h->buf[p], h->d_time + p, d, h->stream);
+        else
+            e = launch_energy<float>(make_args<float>(h), (const float *)h->buf[p], h->d_time + p, d, h->stream);
+        st = cuda_status(e, "energy kernel");
+    }
+    double w = 0.0;
+    if (!st) st = cuda_status(cudaMemcpyAsync(&w, d, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "reading energy");
+    if (!st) st = lbm_em_sync(h);
+    if (!st) *W = w;
+    return st;
+}
+
+lbm_em_status lbm_em_run_converged(lbm_em_t *h, const lbm_em_contour *c, double tol, int32_t min_periods,
+                                   int32_t max_periods, double out[3], int64_t *steps_run) {
+    if (!h || !c || !out) return set_error(LBM_EM_EINVAL, "NULL argument");
+    if (!(tol >= 0.0) || min_periods < 1 || max_periods < min_periods)
+        return set_error(LBM_EM_EINVAL, "need tol >= 0 and 1 <= min_periods <= max_periods");
+    const int T = h->srccfg.period_steps;
+    const int64_t t0 = h->t;
+    double prev = -1.0;
+    int p = 0, settled = 0;
+    bool converged = false;
+    lbm_em_status st = LBM_EM_OK;
+    while (p < max_periods - 1) {
+        st = lbm_em_step(h, T);
+        if (st) return st;
+        ++p;
+        double W = 0.0;
+        st = lbm_em_energy(h, &W);
+        if (st) return st;
+        // settled when two successive samples (same phase of the period) change by <= tol
+        settled = (prev > 0.0 && std::fabs(W - prev) <= tol * W) ? settled + 1 : 0;
+        prev = W;
+        if (p + 1 >= min_periods && settled >= 2) {
+            converged = true;
+            break;
+        }
+    }
+    // the decision uses the fields of the boundary step itself, so the averaging period
+    // starts one step later (the batched path runs the same schedule)
+    if (converged) st = lbm_em_step(h, 1);
+    if (!st) st = lbm_em_force_torque(h, c, out);
+    if (!st && steps_run) *steps_run = h->t - t0;
     return st;
 }
 

@@ -22,6 +22,7 @@
 
 #include "../../include/lbm_em.h"
 #include "common.cuh"
+#include "launchers.h"
 #include "runtime.h"
 
 using namespace lbmem;
@@ -34,7 +35,7 @@ struct InstDesc {
     long long steps, acc_from;
     int acc_base, y0, y1, pad;
     SourceParams src;
-    double mtab[3][3];  // per region id: inv_eps3, six_em1, inv_eps
+    double mtab[3][3];  // per region id: inv_eps3, c_d = 6 eps - 4, inv_eps
 };
 
 struct Tile {
@@ -51,7 +52,9 @@ struct BatchArgs {
     const uint8_t *mat;
     const int *slot;
     double *acc;
-    unsigned *err;  // one word per instance
+    unsigned *err;     // one word per instance
+    double *energy;    // per-instance energy sum of the current period-boundary step
+    int conv;          // 1: sample the energy at period boundaries (convergence exits)
 };
 
 template <typename T>
@@ -67,6 +70,8 @@ __global__ void __launch_bounds__(256) k_batch_step(const BatchArgs<T> b, const 
         const long long steps = d.steps;
         if (t >= steps) continue;  // uniform over the block
         const bool acc = t >= d.acc_from;
+        const bool sample = b.conv && t > 0 && t < d.acc_from && (t % (long long)d.period) == 0;
+        double wsum_t = 0.0;
         __syncthreads();
         if (threadIdx.x < 3)
             smat[threadIdx.x] = MatT<T>{(T)d.mtab[threadIdx.x][0], (T)d.mtab[threadIdx.x][1],
@@ -89,7 +94,7 @@ __global__ void __launch_bounds__(256) k_batch_step(const BatchArgs<T> b, const 
             const size_t idx = (size_t)y * d.pitch + x;
             const MatT<T> m = smat[mat[idx]];
             T E3, Hx, Hy, D;
-            moments(p, m.inv_eps3, &E3, &Hx, &Hy, &D);
+            moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
             if (field_runaway(E3)) atomicOr(b.err + tl.inst, 1u);
             if (acc && y >= d.y0 && y <= d.y1) {
                 const int s = b.slot[d.slot_base + idx];
@@ -105,9 +110,46 @@ __global__ void __launch_bounds__(256) k_batch_step(const BatchArgs<T> b, const 
                     q[5] += hy * c.y;
                 }
             }
-            collide(p, E3, Hx, Hy, m.six_em1);
+            if (sample)
+                wsum_t += 0.5 * ((double)D * (double)(D * m.inv_eps) + (double)Hx * (double)Hx + (double)Hy * (double)Hy);
+            collide(p, E3, Hx, Hy);
             store_site(fout, d.pstride, idx, p);
         }
+        if (sample) {  // block sum of the tile's energy into the instance's accumulator
+            __shared__ double wsh[8];
+            for (int o = 16; o > 0; o >>= 1) wsum_t += __shfl_down_sync(0xffffffffu, wsum_t, o);
+            if ((threadIdx.x & 31) == 0) wsh[threadIdx.x >> 5] = wsum_t;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double w = 0.0;
+                for (int q = 0; q < (int)(blockDim.x >> 5); ++q) w += wsh[q];
+                atomicAdd(b.energy + tl.inst, w);
+            }
+        }
+    }
+}
+
+// After a step of time t (*t_next = t + 1): every instance at a period boundary compares
+// its energy with the previous boundary's (Sec. III convergence criterion); once two
+// successive changes are <= tol * W and at least min_periods - 1 periods have run, the
+// instance runs one more period, with Fourier accumulation, and stops.
+__global__ void k_batch_converge(InstDesc *desc, double *energy, double *prev, int *settled,
+                                 const long long *__restrict__ t_next, double tol, int min_periods, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long t = *t_next - 1;
+    InstDesc &d = desc[i];
+    if (t <= 0 || t >= d.acc_from || (t % (long long)d.period) != 0) return;
+    const double W = energy[i];
+    energy[i] = 0.0;
+    const double P = prev[i];
+    const int s = (P > 0.0 && fabs(W - P) <= tol * W) ? settled[i] + 1 : 0;
+    settled[i] = s;
+    prev[i] = W;
+    const long long periods_done = t / d.period;
+    if (s >= 2 && periods_done + 1 >= min_periods) {
+        d.acc_from = t + 1;
+        d.steps = t + 1 + d.period;
     }
 }
 
@@ -193,6 +235,11 @@ struct lbm_em_batch {
     int tile_w = 0, tile_h = 0, ctas = 0;
     cudaGraphExec_t graph = nullptr;
     bool ran = false;
+    // convergence exits
+    double conv_tol = 0.0;
+    int min_periods = 1;
+    double *d_energy = nullptr, *d_prev = nullptr;
+    int *d_settled = nullptr;
 };
 
 static void batch_free(lbm_em_batch *b) {
@@ -213,6 +260,9 @@ static void batch_free(lbm_em_batch *b) {
     cudaFree(b->d_pts);
     cudaFree(b->d_time);
     cudaFree(b->d_err);
+    cudaFree(b->d_energy);
+    cudaFree(b->d_prev);
+    cudaFree(b->d_settled);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -258,15 +308,21 @@ static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, long long t) {
     if (b->prec == LBM_EM_F64) {
         BatchArgs<double> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, 0,
                             (const double *)b->buf[p], (double *)b->buf[1 - p], b->d_mat, b->d_slot,
-                            b->d_acc, b->d_err};
+                            b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
         k_batch_step<double><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
     } else {
         BatchArgs<float> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, 0,
                            (const float *)b->buf[p], (float *)b->buf[1 - p], b->d_mat, b->d_slot,
-                           b->d_acc, b->d_err};
+                           b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
         k_batch_step<float><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
     }
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && b->conv_tol > 0.0) {
+        k_batch_converge<<<(b->n + 127) / 128, 128, 0, s>>>(b->d_desc, b->d_energy, b->d_prev, b->d_settled,
+                                                           b->d_time + (1 - p), b->conv_tol, b->min_periods, b->n);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 static lbm_em_status batch_clear(lbm_em_batch *b) {
@@ -274,6 +330,15 @@ static lbm_em_status batch_clear(lbm_em_batch *b) {
     if (!st) st = cuda_status(cudaMemsetAsync(b->d_acc, 0, b->acc_slots * 6 * sizeof(double), b->stream), "clear");
     if (!st) st = cuda_status(cudaMemsetAsync(b->d_time, 0, 2 * sizeof(long long), b->stream), "clear");
     if (!st) st = cuda_status(cudaMemsetAsync(b->d_err, 0, b->n * sizeof(unsigned), b->stream), "clear");
+    if (!st) st = cuda_status(cudaMemsetAsync(b->d_energy, 0, b->n * sizeof(double), b->stream), "clear");
+    if (!st) st = cuda_status(cudaMemsetAsync(b->d_prev, 0, b->n * sizeof(double), b->stream), "clear");
+    if (!st) st = cuda_status(cudaMemsetAsync(b->d_settled, 0, b->n * sizeof(int), b->stream), "clear");
+    // run lengths may have been shortened on the device by a convergence exit
+    if (!st)
+        st = cuda_status(cudaMemcpyAsync(b->d_desc, b->desc.data(), b->n * sizeof(InstDesc), cudaMemcpyHostToDevice,
+                                         b->stream),
+                         "restoring descriptors");
+    if (!st) st = cuda_status(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
     return st;
 }
 
@@ -344,6 +409,7 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
     if (o->tile_w < 0 || o->tile_h < 0 || o->ctas_per_sm < 0 || o->ctas_per_sm > 8)
         return set_error(LBM_EM_EINVAL, "bad tile shape or CTAs per SM");
     if (o->tile_w && (o->tile_w % 32 || o->tile_w > 256)) return set_error(LBM_EM_EINVAL, "tile_w: multiple of 32, <= 256");
+    if (!(o->conv_tol >= 0.0) || o->min_periods < 0) return set_error(LBM_EM_EINVAL, "conv_tol >= 0, min_periods >= 0");
     if (o->tile_h && (o->tile_h > 16)) return set_error(LBM_EM_EINVAL, "tile_h must be <= 16");
     for (int i = 0; i < n; ++i) {
         const lbm_em_instance &s = specs[i];
@@ -428,7 +494,7 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
         for (int r = 0; r < 3; ++r) {
             const bool pec = r == 2 && s.janus.pec2;
             d.mtab[r][0] = pec ? 0.0 : 1.0 / (3.0 * eps[r]);
-            d.mtab[r][1] = pec ? 0.0 : 6.0 * (eps[r] - 1.0);
+            d.mtab[r][1] = pec ? 0.0 : 6.0 * eps[r] - 4.0;
             d.mtab[r][2] = pec ? 0.0 : 1.0 / eps[r];
         }
     }
@@ -446,6 +512,11 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
     BTRY(cudaMalloc(&b->d_desc, n * sizeof(InstDesc)), "cudaMalloc(batch desc)");
     BTRY(cudaMalloc(&b->d_time, 2 * sizeof(long long)), "cudaMalloc(time)");
     BTRY(cudaMalloc(&b->d_err, n * sizeof(unsigned)), "cudaMalloc(err)");
+    BTRY(cudaMalloc(&b->d_energy, n * sizeof(double)), "cudaMalloc(energy)");
+    BTRY(cudaMalloc(&b->d_prev, n * sizeof(double)), "cudaMalloc(energy)");
+    BTRY(cudaMalloc(&b->d_settled, n * sizeof(int)), "cudaMalloc(energy)");
+    b->conv_tol = o->conv_tol;
+    b->min_periods = o->min_periods > 0 ? o->min_periods : 1;
     BTRY(cudaMemcpy(b->d_cs, cs_all.data(), cs_all.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload");
     for (int i = 0; i < n; ++i) b->desc[i].src.cs = b->d_cs + cs_off[i];
     BTRY(cudaMemcpy(b->d_desc, b->desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice), "upload");
@@ -545,6 +616,19 @@ lbm_em_status lbm_em_batch_results(lbm_em_batch_t *b, double *out, int32_t *stat
         any |= err[i] != 0;
     }
     if (any) return set_error(LBM_EM_EUNSTABLE, "at least one instance became unstable");
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_batch_steps(lbm_em_batch_t *b, int64_t *steps) {
+    if (!b || !steps) return set_error(LBM_EM_EINVAL, "NULL argument");
+    if (!b->ran) return set_error(LBM_EM_ESTATE, "batch has not run");
+    cudaSetDevice(b->dev);
+    std::vector<InstDesc> d(b->n);
+    lbm_em_status st = cuda_status(
+        cudaMemcpyAsync(d.data(), b->d_desc, b->n * sizeof(InstDesc), cudaMemcpyDeviceToHost, b->stream), "read");
+    if (!st) st = cuda_status(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    if (st) return st;
+    for (int i = 0; i < b->n; ++i) steps[i] = d[i].steps;
     return LBM_EM_OK;
 }
 

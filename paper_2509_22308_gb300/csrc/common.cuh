@@ -2,17 +2,23 @@
 //
 // TM^z reduction of the D3Q7 vector scheme (arXiv 2509.22308, Sec. III).  With
 // E = (0, 0, E_z) and H = (H_x, H_y, 0) the equilibria of
-// Eq. (equilibrium distribution functions) only feed these 16 scalars per site:
-//   e_z components of e_0, e_+z (= e_-z, stored once, weight 2), e_+x, e_-x, e_+y, e_-y
-//   h_x components of h_+x, h_-x, h_+y, h_-y, h_+z (= h_-z, weight 2)
-//   h_y components of h_+x, h_-x, h_+y, h_-y, h_+z (= h_-z, weight 2)
-// The other 26 components of the 42-scalar vector state never reach E_z, H_x, H_y
-// (h_0 = 0 because mu_r = 1; the x/y parts of e_+-z cancel in every moment).
+// Eq. (equilibrium distribution functions) only reach 16 of the 42 vector components:
+// the e_z component of e_0, e_+-x, e_+-y, e_+-z and the h_x, h_y components of h_+-x,
+// h_+-y, h_+-z (h_0 = 0 because mu_r = 1; the x/y parts of e_+-z cancel in every moment).
+// Starting from zero, five more relations hold exactly at every step, because the two
+// populations involved move together and have equal or opposite equilibria, so their
+// difference only changes sign in the collision (the source, the open edges and PEC
+// cells preserve them too):
+//   e_+z,z = e_-z,z,  h_+z = h_-z,
+//   h_+x,y = -e_+x,z,  h_-x,y = e_-x,z,  h_+y,x = e_+y,z,  h_-y,x = -e_-y,z,
+//   e_0,z = 6 (eps_r - 1) e_z,z  (0 in PEC cells).
+// The state is therefore 11 scalars per site, stored as structure-of-arrays planes:
+//   e_z of the z pair and of +x, -x, +y, -y;  h_x of +x, -x, z;  h_y of +y, -y, z.
 //
-// Storage: 16 structure-of-arrays planes, plane p of site (x, y) at
-// p * pstride + y * pitch + x.  A buffer holds the post-collision values f*(t-1);
-// the step kernel at time t pulls f_i(r, t) = f*_i(r - c_i, t - 1) ("pull" streaming),
-// so every plane is read once and written once per step.
+// Storage: plane p of site (x, y) at p * pstride + y * pitch + x.  A buffer holds the
+// post-collision values f*(t-1); the step kernel at time t pulls
+// f_i(r, t) = f*_i(r - c_i, t - 1) ("pull" streaming), so every plane is read once and
+// written once per step.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -21,19 +27,20 @@
 namespace lbmem {
 
 enum Plane {
-    P_E0 = 0, P_EZ, P_EPX, P_EMX, P_EPY, P_EMY,
-    P_HXPX, P_HXMX, P_HXPY, P_HXMY, P_HXZ,
-    P_HYPX, P_HYMX, P_HYPY, P_HYMY, P_HYZ,
+    P_EZ = 0, P_EPX, P_EMX, P_EPY, P_EMY,
+    P_HXPX, P_HXMX, P_HXZ,
+    P_HYPY, P_HYMY, P_HYZ,
     NPLANES
 };
 
 enum SourceKind { SRC_OPEN = 0, SRC_HARD = 1, SRC_NONE = 2 };
 
 // Per-material constants in the kernel's arithmetic type:
-// inv_eps3 = 1/(3 eps_r) (0 for PEC: E := 0), six_em1 = 6 (eps_r - 1), inv_eps = 1/eps_r.
+// inv_eps3 = 1/(3 eps_r) (0 for PEC: E := 0), c_d = 6 eps_r - 4 (the weight of the z pair
+// in D once e_0 = 6 (eps_r - 1) e_z is substituted), inv_eps = 1/eps_r.
 template <typename T>
 struct MatT {
-    T inv_eps3, six_em1, inv_eps, pad;
+    T inv_eps3, c_d, inv_eps, pad;
 };
 
 // Left-edge source: the exact discrete plane wave of the lattice.  With
@@ -66,9 +73,9 @@ struct StepArgs {
 
 template <typename T>
 struct Pop {
-    T e0, ez, epx, emx, epy, emy;
-    T hxpx, hxmx, hxpy, hxmy, hxz;
-    T hypx, hymx, hypy, hymy, hyz;
+    T ez, epx, emx, epy, emy;
+    T hxpx, hxmx, hxz;
+    T hypy, hymy, hyz;
 };
 
 // Source values at time t: *g_open = ramp (Re[P z^t] - Re[P w z^t]) (added to the
@@ -90,7 +97,8 @@ __device__ __forceinline__ void source_values(const SourceParams &s, long long t
 
 // f_i(r, t) = f*_i(r - c_i, t - 1); an upstream site outside the lattice is replaced
 // by the site itself (open edge: zero-gradient copy along the population's own
-// direction); at x = 0 the +x populations also receive the source (t >= 1).
+// direction); at x = 0 the +x populations also receive the source (t >= 1), which
+// adds to e_+x,z and (through h_+x,y = -e_+x,z) subtracts from h_+x,y.
 template <typename T>
 __device__ __forceinline__ void pull_site(const StepArgs<T> &a, const T *__restrict__ f, int x,
                                           int y, long long t, Pop<T> &p) {
@@ -100,7 +108,6 @@ __device__ __forceinline__ void pull_site(const StepArgs<T> &a, const T *__restr
     const size_t r = (size_t)y * a.pitch;
     const size_t rm = (size_t)(y > 0 ? y - 1 : 0) * a.pitch;
     const size_t rp = (size_t)(y < a.ny - 1 ? y + 1 : y) * a.pitch;
-    p.e0 = f[P_E0 * ps + r + x];
     p.ez = f[P_EZ * ps + r + x];
     p.epx = f[P_EPX * ps + r + xm];
     p.emx = f[P_EMX * ps + r + xp];
@@ -108,11 +115,7 @@ __device__ __forceinline__ void pull_site(const StepArgs<T> &a, const T *__restr
     p.emy = f[P_EMY * ps + rp + x];
     p.hxpx = f[P_HXPX * ps + r + xm];
     p.hxmx = f[P_HXMX * ps + r + xp];
-    p.hxpy = f[P_HXPY * ps + rm + x];
-    p.hxmy = f[P_HXMY * ps + rp + x];
     p.hxz = f[P_HXZ * ps + r + x];
-    p.hypx = f[P_HYPX * ps + r + xm];
-    p.hymx = f[P_HYMX * ps + r + xp];
     p.hypy = f[P_HYPY * ps + rm + x];
     p.hymy = f[P_HYMY * ps + rp + x];
     p.hyz = f[P_HYZ * ps + r + x];
@@ -121,43 +124,39 @@ __device__ __forceinline__ void pull_site(const StepArgs<T> &a, const T *__restr
         source_values(a.src, t, &g, &inc);
         if (a.src.kind == SRC_OPEN) {
             p.epx += (T)g;
-            p.hypx -= (T)g;
         } else {
             p.epx = (T)inc;
             p.hxpx = (T)0;
-            p.hypx = (T)(-inc);
         }
     }
-}
-
-// Moments (Sec. III): D = sum e_i (the +-z pair twice), E_z = D / eps_r, H = sum h_i.
-// Returns E_z/3 (the scale every equilibrium uses) and H_x, H_y.
-template <typename T>
-__device__ __forceinline__ void moments(const Pop<T> &p, T inv_eps3, T *E3, T *Hx, T *Hy, T *D) {
-    const T d = p.e0 + p.epx + p.emx + p.epy + p.emy + (T)2 * p.ez;
-    *D = d;
-    *E3 = d * inv_eps3;
-    *Hx = p.hxpx + p.hxmx + p.hxpy + p.hxmy + (T)2 * p.hxz;
-    *Hy = p.hypx + p.hymx + p.hypy + p.hymy + (T)2 * p.hyz;
 }
 
 template <typename T>
 __device__ __forceinline__ T fmat(T a, T b, T c) { return fma(a, b, c); }
 
-// Post-collision f* = 2 f^eq - f (Eq. LBGK equation), with 2 f^eq written out from
-// Eq. (equilibrium distribution functions) for the TM^z components:
-//   e_z:  +x (E-H_y)/3, -x (E+H_y)/3, +y (E+H_x)/3, -y (E-H_x)/3, z E/3, rest 2(eps-1)E
-//   h_x:  +-x H_x/3, +y (H_x+E)/3, -y (H_x-E)/3, z H_x/3
-//   h_y:  +x (H_y-E)/3, -x (H_y+E)/3, +-y H_y/3, z H_y/3
-// 36 arithmetic operations per site with the moments (FP64 is bound by its pipe on
-// GB300): every 2 f^eq that is E/3 +- H/3 is one fused multiply-add, and H/3 itself is
-// never formed.
+// Moments (Sec. III): D = sum e_i = (6 eps_r - 4) e_z + e_+x + e_-x + e_+y + e_-y (the rest
+// population and the z pair folded in), E_z = D / eps_r, H = sum h_i with the tied
+// populations substituted.  Returns D, E_z/3 (the scale every equilibrium uses), H_x, H_y.
 template <typename T>
-__device__ __forceinline__ void collide(Pop<T> &p, T E3, T Hx, T Hy, T six_em1) {
+__device__ __forceinline__ void moments(const Pop<T> &p, T inv_eps3, T c_d, T *E3, T *Hx, T *Hy, T *D) {
+    const T d = fmat(c_d, p.ez, p.epx) + p.emx + p.epy + p.emy;
+    *D = d;
+    *E3 = d * inv_eps3;
+    *Hx = fmat((T)2, p.hxz, p.hxpx + p.hxmx) + (p.epy - p.emy);
+    *Hy = fmat((T)2, p.hyz, p.hypy + p.hymy) + (p.emx - p.epx);
+}
+
+// Post-collision f* = 2 f^eq - f (Eq. LBGK equation), with 2 f^eq written out from
+// Eq. (equilibrium distribution functions) for the stored components:
+//   e_z:  z E/3, +x (E-H_y)/3, -x (E+H_y)/3, +y (E+H_x)/3, -y (E-H_x)/3
+//   h_x:  +-x and z H_x/3;   h_y: +-y and z H_y/3
+// 28 arithmetic operations per site with the moments (FP64 is bound by its pipe on
+// GB300): every 2 f^eq that is E/3 +- H/3 is one fused multiply-add.
+template <typename T>
+__device__ __forceinline__ void collide(Pop<T> &p, T E3, T Hx, T Hy) {
     const T third = (T)(1.0 / 3.0), mthird = (T)(-1.0 / 3.0);
     const T A = fmat(Hy, mthird, E3), B = fmat(Hy, third, E3);
     const T C = fmat(Hx, third, E3), D = fmat(Hx, mthird, E3);
-    p.e0 = fmat(six_em1, E3, -p.e0);
     p.ez = E3 - p.ez;
     p.epx = A - p.epx;
     p.emx = B - p.emx;
@@ -165,11 +164,7 @@ __device__ __forceinline__ void collide(Pop<T> &p, T E3, T Hx, T Hy, T six_em1) 
     p.emy = D - p.emy;
     p.hxpx = fmat(Hx, third, -p.hxpx);
     p.hxmx = fmat(Hx, third, -p.hxmx);
-    p.hxpy = C - p.hxpy;
-    p.hxmy = -D - p.hxmy;
     p.hxz = fmat(Hx, third, -p.hxz);
-    p.hypx = -A - p.hypx;
-    p.hymx = B - p.hymx;
     p.hypy = fmat(Hy, third, -p.hypy);
     p.hymy = fmat(Hy, third, -p.hymy);
     p.hyz = fmat(Hy, third, -p.hyz);
@@ -185,7 +180,6 @@ __device__ __forceinline__ bool field_runaway(float e3) {
 
 template <typename T>
 __device__ __forceinline__ void store_site(T *__restrict__ f, size_t ps, size_t idx, const Pop<T> &p) {
-    f[P_E0 * ps + idx] = p.e0;
     f[P_EZ * ps + idx] = p.ez;
     f[P_EPX * ps + idx] = p.epx;
     f[P_EMX * ps + idx] = p.emx;
@@ -193,11 +187,7 @@ __device__ __forceinline__ void store_site(T *__restrict__ f, size_t ps, size_t 
     f[P_EMY * ps + idx] = p.emy;
     f[P_HXPX * ps + idx] = p.hxpx;
     f[P_HXMX * ps + idx] = p.hxmx;
-    f[P_HXPY * ps + idx] = p.hxpy;
-    f[P_HXMY * ps + idx] = p.hxmy;
     f[P_HXZ * ps + idx] = p.hxz;
-    f[P_HYPX * ps + idx] = p.hypx;
-    f[P_HYMX * ps + idx] = p.hymx;
     f[P_HYPY * ps + idx] = p.hypy;
     f[P_HYMY * ps + idx] = p.hymy;
     f[P_HYZ * ps + idx] = p.hyz;
@@ -209,17 +199,5 @@ struct ContourPt {
     double w[4];
     double nx, ny;
 };
-
-// ---- host-side launchers (defined in the .cu files) ----------------------------------
-template <typename T>
-cudaError_t launch_step(const StepArgs<T> &a, const T *fin, T *fout, const long long *t_in,
-                        long long *t_out, bool accumulate, cudaStream_t s);
-template <typename T>
-cudaError_t launch_fields(const StepArgs<T> &a, const T *f, const long long *t_dev, double *ez,
-                          double *hx, double *hy, cudaStream_t s);
-cudaError_t launch_rasterize(int nx, int ny, int pitch, double cx, double cy, double a,
-                             double ndx, double ndy, uint8_t *ids, cudaStream_t s);
-cudaError_t launch_contour(const double *acc, double scale, const ContourPt *pts, int npts,
-                           double R, double dl, double F0, double M0, double *out, cudaStream_t s);
 
 }  // namespace lbmem

@@ -1,0 +1,55 @@
+// Convergence monitor: total electromagnetic energy of the lattice (arXiv 2509.22308,
+// Sec. III: the energy in the domain approaches a constant at steady state).
+#include "common.cuh"
+#include "launchers.h"
+
+namespace lbmem {
+
+constexpr int BX = 32, BY = 8;
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31, wid = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    v = (wid == 0 && lane < nw) ? sh[lane] : 0.0;
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Total electromagnetic energy sum over sites of (eps E_z^2 + H_x^2 + H_y^2) / 2 at time
+// *t_dev (the convergence monitor of Sec. III), accumulated into *energy (FP64).
+template <typename T>
+__global__ void __launch_bounds__(BX *BY) k_energy(const StepArgs<T> a, const T *__restrict__ f,
+                                                   const long long *__restrict__ t_dev, double *energy) {
+    const int x = blockIdx.x * BX + threadIdx.x;
+    const int y = blockIdx.y * BY + threadIdx.y;
+    double w = 0.0;
+    if (x < a.nx && y < a.ny) {
+        Pop<T> p;
+        pull_site(a, f, x, y, *t_dev, p);
+        const MatT<T> m = a.mtab[a.mat[(size_t)y * a.pitch + x]];
+        T E3, Hx, Hy, D;
+        moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
+        const double ez = (double)(D * m.inv_eps);
+        w = 0.5 * ((double)D * ez + (double)Hx * (double)Hx + (double)Hy * (double)Hy);
+    }
+    w = block_sum(w);
+    if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(energy, w);
+}
+
+template <typename T>
+cudaError_t launch_energy(const StepArgs<T> &a, const T *f, const long long *t_dev, double *energy, cudaStream_t s) {
+    dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY), block(BX, BY);
+    k_energy<T><<<grid, block, 0, s>>>(a, f, t_dev, energy);
+    return cudaGetLastError();
+}
+template cudaError_t launch_energy<double>(const StepArgs<double> &, const double *, const long long *, double *,
+                                           cudaStream_t);
+template cudaError_t launch_energy<float>(const StepArgs<float> &, const float *, const long long *, double *,
+                                          cudaStream_t);
+
+}  // namespace lbmem

@@ -16,6 +16,7 @@
 
 #include "../../include/lbm_em.h"
 #include "common.cuh"
+#include "launchers.h"
 #include "runtime.h"
 
 using namespace lbmem;

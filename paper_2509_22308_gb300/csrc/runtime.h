@@ -15,6 +15,8 @@ lbm_em_status cuda_status(cudaError_t e, const char *what);
 
 // Constants of the exact discrete incident plane wave for period T (see common.cuh).
 void incident_constants(int period, double E0, double *pr, double *pi, double *qr, double *qi);
+// Wavenumber of the lattice's right-going vacuum plane wave of period T (arg w).
+double lattice_wavenumber(int period);
 // (cos w t, sin w t) for t = 0..T-1, w = 2 pi / T.
 std::vector<double2> phase_table(int period);
 

@@ -2,6 +2,7 @@
 // (arXiv 2509.22308, Sec. III) for the FP64 and FP32 storage forms, plus the
 // kernel that reconstructs the fields at the current time.
 #include "common.cuh"
+#include "launchers.h"
 
 namespace lbmem {
 
@@ -25,7 +26,7 @@ __global__ void __launch_bounds__(BX *BY) k_step(const StepArgs<T> a, const T *_
     const size_t idx = (size_t)y * a.pitch + x;
     const MatT<T> m = a.mtab[a.mat[idx]];
     T E3, Hx, Hy, D;
-    moments(p, m.inv_eps3, &E3, &Hx, &Hy, &D);
+    moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
     if (field_runaway(E3)) atomicOr(a.err, 1u);
     if (ACC) {
         if (y >= a.accp.y0 && y <= a.accp.y1) {
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(BX *BY) k_step(const StepArgs<T> a, const T *_
             }
         }
     }
-    collide(p, E3, Hx, Hy, m.six_em1);
+    collide(p, E3, Hx, Hy);
     store_site(fout, a.pstride, idx, p);
 }
 
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(BX *BY) k_fields(const StepArgs<T> a, const T 
     const size_t idx = (size_t)y * a.pitch + x;
     const MatT<T> m = a.mtab[a.mat[idx]];
     T E3, Hx, Hy, D;
-    moments(p, m.inv_eps3, &E3, &Hx, &Hy, &D);
+    moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
     const size_t o = (size_t)y * a.nx + x;
     ez[o] = (double)(D * m.inv_eps);
     hx[o] = (double)Hx;

@@ -7,9 +7,9 @@
 // writes f*(t + 1) (FP32) or the fields and deviations of t + 1 (FP16-deviation) to
 // global memory.  Each state element crosses HBM once per two steps (plus the halo,
 // which neighbouring CTAs read at about the same time and L2 serves); the per-site
-// arithmetic is the one-step kernel's, so the FP32 result is bit-identical to two
-// one-step launches.  The FP16-deviation form keeps the intermediate f*(t) in FP32,
-// so only every second state is rounded to FP16.
+// arithmetic is the one-step kernel's, so the result is bit-identical to two one-step
+// launches (the FP16-deviation form rounds the intermediate state to FP16 exactly as
+// storing and reloading it would).
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -26,7 +26,6 @@ __device__ __forceinline__ float &smv(float *sm, int plane, int ly, int lx) {
 }
 
 __device__ __forceinline__ void put_smem(float *sm, int ly, int lx, const Pop<float> &p) {
-    smv(sm, P_E0, ly, lx) = p.e0;
     smv(sm, P_EZ, ly, lx) = p.ez;
     smv(sm, P_EPX, ly, lx) = p.epx;
     smv(sm, P_EMX, ly, lx) = p.emx;
@@ -34,11 +33,7 @@ __device__ __forceinline__ void put_smem(float *sm, int ly, int lx, const Pop<fl
     smv(sm, P_EMY, ly, lx) = p.emy;
     smv(sm, P_HXPX, ly, lx) = p.hxpx;
     smv(sm, P_HXMX, ly, lx) = p.hxmx;
-    smv(sm, P_HXPY, ly, lx) = p.hxpy;
-    smv(sm, P_HXMY, ly, lx) = p.hxmy;
     smv(sm, P_HXZ, ly, lx) = p.hxz;
-    smv(sm, P_HYPX, ly, lx) = p.hypx;
-    smv(sm, P_HYMX, ly, lx) = p.hymx;
     smv(sm, P_HYPY, ly, lx) = p.hypy;
     smv(sm, P_HYMY, ly, lx) = p.hymy;
     smv(sm, P_HYZ, ly, lx) = p.hyz;
@@ -50,7 +45,6 @@ __device__ __forceinline__ void pull_smem(float *sm, const SourceParams &src, in
                                           int cx, int cy, long long t1, Pop<float> &p) {
     const int xm = x > 0 ? cx - 1 : cx, xp = x < nx - 1 ? cx + 1 : cx;
     const int ym = y > 0 ? cy - 1 : cy, yp = y < ny - 1 ? cy + 1 : cy;
-    p.e0 = smv(sm, P_E0, cy, cx);
     p.ez = smv(sm, P_EZ, cy, cx);
     p.epx = smv(sm, P_EPX, cy, xm);
     p.emx = smv(sm, P_EMX, cy, xp);
@@ -58,26 +52,11 @@ __device__ __forceinline__ void pull_smem(float *sm, const SourceParams &src, in
     p.emy = smv(sm, P_EMY, yp, cx);
     p.hxpx = smv(sm, P_HXPX, cy, xm);
     p.hxmx = smv(sm, P_HXMX, cy, xp);
-    p.hxpy = smv(sm, P_HXPY, ym, cx);
-    p.hxmy = smv(sm, P_HXMY, yp, cx);
     p.hxz = smv(sm, P_HXZ, cy, cx);
-    p.hypx = smv(sm, P_HYPX, cy, xm);
-    p.hymx = smv(sm, P_HYMX, cy, xp);
     p.hypy = smv(sm, P_HYPY, ym, cx);
     p.hymy = smv(sm, P_HYMY, yp, cx);
     p.hyz = smv(sm, P_HYZ, cy, cx);
-    if (x == 0 && t1 >= 1 && src.kind != SRC_NONE) {
-        double g, inc;
-        source_values(src, t1, &g, &inc);
-        if (src.kind == SRC_OPEN) {
-            p.epx += (float)g;
-            p.hypx -= (float)g;
-        } else {
-            p.epx = (float)inc;
-            p.hxpx = 0.0f;
-            p.hypx = (float)(-inc);
-        }
-    }
+    f16_source(src, x, t1, p);
 }
 
 __device__ __forceinline__ void acc_site(const AccParams &ap, const SourceParams &src, size_t idx, int y,
@@ -111,11 +90,11 @@ __global__ void __launch_bounds__(NT) k_step2_f32(const StepArgs<float> a, const
         const size_t idx = (size_t)y * a.pitch + x;
         const MatT<float> m = a.mtab[a.mat[idx]];
         float E3, Hx, Hy, D;
-        moments(p, m.inv_eps3, &E3, &Hx, &Hy, &D);
+        moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
         if (field_runaway(E3)) atomicOr(a.err, 1u);
         if (ACC && lx >= 1 && lx <= TW && ly >= 1 && ly <= TH)
             acc_site(a.accp, a.src, idx, y, t, (double)(D * m.inv_eps), (double)Hx, (double)Hy);
-        collide(p, E3, Hx, Hy, m.six_em1);
+        collide(p, E3, Hx, Hy);
         put_smem(sm, ly, lx, p);
     }
     __syncthreads();
@@ -127,10 +106,10 @@ __global__ void __launch_bounds__(NT) k_step2_f32(const StepArgs<float> a, const
         const size_t idx = (size_t)y * a.pitch + x;
         const MatT<float> m = a.mtab[a.mat[idx]];
         float E3, Hx, Hy, D;
-        moments(p, m.inv_eps3, &E3, &Hx, &Hy, &D);
+        moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
         if (field_runaway(E3)) atomicOr(a.err, 1u);
         if (ACC) acc_site(a.accp, a.src, idx, y, t + 1, (double)(D * m.inv_eps), (double)Hx, (double)Hy);
-        collide(p, E3, Hx, Hy, m.six_em1);
+        collide(p, E3, Hx, Hy);
         store_site(fout, a.pstride, idx, p);
     }
 }
@@ -142,23 +121,28 @@ __global__ void __launch_bounds__(NT) k_step2_f16(const F16Args a, const long lo
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
     const long long t = *t_in;
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *t_out = t + 2;
+    // phase 1: time t; the shared memory receives what a pull would rebuild from the
+    // stored (FP16-rounded) state of time t, so this equals two one-step launches
     for (int k = threadIdx.x; k < SW * SH; k += NT) {
         const int lx = k % SW, ly = k / SW, x = x0 - 1 + lx, y = y0 - 1 + ly;
         if (x < 0 || x >= a.nx || y < 0 || y >= a.ny) continue;
         const size_t idx = (size_t)y * a.pitch + x;
         const MatT<float> m = a.mtab[a.mat[idx]];
         Pop<float> p;
-        pull_f16(a, x, y, t, p, m.six_em1 * (1.0f / 6.0f));
+        pull_f16(a, x, y, t, p);
         float E3, Hx, Hy, D;
-        moments(p, m.inv_eps3, &E3, &Hx, &Hy, &D);
+        moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
         if (field_runaway(E3)) atomicOr(a.err, 1u);
+        const float Ez = 3.0f * E3;
         if (ACC && lx >= 1 && lx <= TW && ly >= 1 && ly <= TH)
-            acc_site(a.accp, a.src, idx, y, t, (double)(3.0f * E3), (double)Hx, (double)Hy);
-        collide(p, E3, Hx, Hy, m.six_em1);
-        put_smem(sm, ly, lx, p);
+            acc_site(a.accp, a.src, idx, y, t, (double)Ez, (double)Hx, (double)Hy);
+        __half g[NPLANES];
+        encode_all(p, Ez, Hx, Hy, a.scale, g);
+        Pop<float> q;
+        rebuild_all(g, Ez, Hx, Hy, a.inv_scale, q);
+        put_smem(sm, ly, lx, q);
     }
     __syncthreads();
-    const float sc = a.scale, s6 = 1.0f / 6.0f;
     const size_t ps = a.pstride;
     for (int k = threadIdx.x; k < TW * TH; k += NT) {
         const int lx = k % TW, ly = k / TW, x = x0 + lx, y = y0 + ly;
@@ -168,14 +152,14 @@ __global__ void __launch_bounds__(NT) k_step2_f16(const F16Args a, const long lo
         const size_t idx = (size_t)y * a.pitch + x;
         const MatT<float> m = a.mtab[a.mat[idx]];
         float E3, Hx, Hy, D;
-        moments(p, m.inv_eps3, &E3, &Hx, &Hy, &D);
+        moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
         if (field_runaway(E3)) atomicOr(a.err, 1u);
-        const float Ez = 3.0f * E3, em1 = m.six_em1 * s6;
+        const float Ez = 3.0f * E3;
         if (ACC) acc_site(a.accp, a.src, idx, y, t + 1, (double)Ez, (double)Hx, (double)Hy);
-        float g[NPLANES];
-        deviations(p, Ez, Hx, Hy, em1, g);
+        __half g[NPLANES];
+        encode_all(p, Ez, Hx, Hy, a.scale, g);
 #pragma unroll
-        for (int q = 0; q < NPLANES; ++q) a.g_out[q * ps + idx] = __float2half_rn(g[q] * sc);
+        for (int q = 0; q < NPLANES; ++q) a.g_out[q * ps + idx] = g[q];
         a.fe_out[idx] = Ez;
         a.fhx_out[idx] = Hx;
         a.fhy_out[idx] = Hy;

@@ -1,13 +1,13 @@
 // FP16-deviation storage form of the fused stream-collide step (arXiv 2509.22308,
 // Sec. III, Eq. LBGK equation), FP32 arithmetic.
 //
-// Stored per site for time t: the fields F = (E_z, H_x, H_y)(t) in FP32 and the 16
+// Stored per site for time t: the fields F = (E_z, H_x, H_y)(t) in FP32 and the 11
 // deviations g_i(t) = f_i(t) - f_i^eq(F(t)) in FP16, multiplied by 2^10.  Because
 // the scheme's post-collision value is f*_i = 2 f_i^eq - f_i = f_i^eq - g_i, the pull
 // for time t + 1 rebuilds f_i(r, t + 1) = f_i^eq(F(s, t)) - g_i(s, t) from the
 // upstream site s = r - c_i; the deviations are small (of the order of the field
 // change over one cell), so FP16 keeps about 11 bits of them.
-// Bytes per lattice update: 16 x 2 + 3 x 4 (+1 material) read, 16 x 2 + 3 x 4 written.
+// Bytes per lattice update: 11 x 2 + 3 x 4 (+1 material) read, 11 x 2 + 3 x 4 written.
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -33,7 +33,7 @@ __device__ __forceinline__ void accumulate_site(const F16Args &a, size_t idx, in
 }
 
 // Two sites (x0, x0 + 1), x0 even, per thread: the x-aligned planes, the fields of the
-// pair and its rows y -+ 1, the material ids and every store move as 2-element
+// pair and of its rows y -+ 1, the material ids and every store move as 2-element
 // vectors; the +-x planes and the fields one site beyond the pair are single loads at
 // the clamped upstream index.  A warp covers 64 sites of one row.
 template <bool ACC>
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(BX *BY) k_step_f16(const F16Args a, const long
     const size_t rp = (size_t)(y < a.ny - 1 ? y + 1 : y) * a.pitch;
     const int xw = x0 > 0 ? x0 - 1 : 0;                   // +x upstream of site 0
     const int xe = x0 + 2 < a.nx ? x0 + 2 : a.nx - 1;      // -x upstream of site 1
-    const float is = a.inv_scale, s6 = 1.0f / 6.0f;
+    const float is = a.inv_scale;
     const __half *g = a.g;
 
     // fields at time t - 1 of the pair, of its rows y -+ 1 and of the sites x0 - 1, x0 + 2
@@ -66,79 +66,52 @@ __global__ void __launch_bounds__(BX *BY) k_step_f16(const F16Args a, const long
     // -x upstream of site 0 is x0 + 1 (clamped to x0 at the last column)
     const float E0e = has1 ? Ec.y : Ec.x, X0e = has1 ? Xc.y : Xc.x, Y0e = has1 ? Yc.y : Yc.x;
 
-    auto h2 = [&](int plane, size_t row) { return __half22float2(*(const __half2 *)(g + plane * ps + row + x0)); };
-    auto h1 = [&](int plane, size_t row, int x) { return __half2float(g[plane * ps + row + x]); };
+    auto h2 = [&](int plane, size_t row) { return *(const __half2 *)(g + plane * ps + row + x0); };
+    auto h1 = [&](int plane, size_t row, int x) { return g[plane * ps + row + x]; };
 
     const uchar2 id = *(const uchar2 *)(a.mat + r + x0);
     const MatT<float> m0 = a.mtab[id.x], m1 = a.mtab[id.y];
-    const float em10 = m0.six_em1 * s6, em11 = m1.six_em1 * s6;
 
     Pop<float> p0, p1;
-    float2 v;
-    v = h2(P_E0, r);
-    p0.e0 = em10 * Ec.x - v.x * is;
-    p1.e0 = em11 * Ec.y - v.y * is;
+    __half2 v;
     v = h2(P_EZ, r);
-    p0.ez = Ec.x * s6 - v.x * is;
-    p1.ez = Ec.y * s6 - v.y * is;
+    p0.ez = rebuild(Ec.x, __low2half(v), is);
+    p1.ez = rebuild(Ec.y, __high2half(v), is);
     v = h2(P_EPX, r);
-    p0.epx = (Ew - Yw) * s6 - h1(P_EPX, r, xw) * is;
-    p1.epx = (Ec.x - Yc.x) * s6 - v.x * is;
+    p0.epx = rebuild(eq6_epx(Ew, Xw, Yw), h1(P_EPX, r, xw), is);
+    p1.epx = rebuild(eq6_epx(Ec.x, Xc.x, Yc.x), __low2half(v), is);
     v = h2(P_EMX, r);
-    p0.emx = (E0e + Y0e) * s6 - (has1 ? v.y : v.x) * is;
-    p1.emx = (Ee + Ye) * s6 - h1(P_EMX, r, xe) * is;
+    p0.emx = rebuild(eq6_emx(E0e, X0e, Y0e), has1 ? __high2half(v) : __low2half(v), is);
+    p1.emx = rebuild(eq6_emx(Ee, Xe, Ye), h1(P_EMX, r, xe), is);
     v = h2(P_EPY, rm);
-    p0.epy = (Es.x + Xs.x) * s6 - v.x * is;
-    p1.epy = (Es.y + Xs.y) * s6 - v.y * is;
+    p0.epy = rebuild(eq6_epy(Es.x, Xs.x, Ys.x), __low2half(v), is);
+    p1.epy = rebuild(eq6_epy(Es.y, Xs.y, Ys.y), __high2half(v), is);
     v = h2(P_EMY, rp);
-    p0.emy = (En.x - Xn.x) * s6 - v.x * is;
-    p1.emy = (En.y - Xn.y) * s6 - v.y * is;
+    p0.emy = rebuild(eq6_emy(En.x, Xn.x, Yn.x), __low2half(v), is);
+    p1.emy = rebuild(eq6_emy(En.y, Xn.y, Yn.y), __high2half(v), is);
     v = h2(P_HXPX, r);
-    p0.hxpx = Xw * s6 - h1(P_HXPX, r, xw) * is;
-    p1.hxpx = Xc.x * s6 - v.x * is;
+    p0.hxpx = rebuild(Xw, h1(P_HXPX, r, xw), is);
+    p1.hxpx = rebuild(Xc.x, __low2half(v), is);
     v = h2(P_HXMX, r);
-    p0.hxmx = X0e * s6 - (has1 ? v.y : v.x) * is;
-    p1.hxmx = Xe * s6 - h1(P_HXMX, r, xe) * is;
-    v = h2(P_HXPY, rm);
-    p0.hxpy = (Xs.x + Es.x) * s6 - v.x * is;
-    p1.hxpy = (Xs.y + Es.y) * s6 - v.y * is;
-    v = h2(P_HXMY, rp);
-    p0.hxmy = (Xn.x - En.x) * s6 - v.x * is;
-    p1.hxmy = (Xn.y - En.y) * s6 - v.y * is;
+    p0.hxmx = rebuild(X0e, has1 ? __high2half(v) : __low2half(v), is);
+    p1.hxmx = rebuild(Xe, h1(P_HXMX, r, xe), is);
     v = h2(P_HXZ, r);
-    p0.hxz = Xc.x * s6 - v.x * is;
-    p1.hxz = Xc.y * s6 - v.y * is;
-    v = h2(P_HYPX, r);
-    p0.hypx = (Yw - Ew) * s6 - h1(P_HYPX, r, xw) * is;
-    p1.hypx = (Yc.x - Ec.x) * s6 - v.x * is;
-    v = h2(P_HYMX, r);
-    p0.hymx = (Y0e + E0e) * s6 - (has1 ? v.y : v.x) * is;
-    p1.hymx = (Ye + Ee) * s6 - h1(P_HYMX, r, xe) * is;
+    p0.hxz = rebuild(Xc.x, __low2half(v), is);
+    p1.hxz = rebuild(Xc.y, __high2half(v), is);
     v = h2(P_HYPY, rm);
-    p0.hypy = Ys.x * s6 - v.x * is;
-    p1.hypy = Ys.y * s6 - v.y * is;
+    p0.hypy = rebuild(Ys.x, __low2half(v), is);
+    p1.hypy = rebuild(Ys.y, __high2half(v), is);
     v = h2(P_HYMY, rp);
-    p0.hymy = Yn.x * s6 - v.x * is;
-    p1.hymy = Yn.y * s6 - v.y * is;
+    p0.hymy = rebuild(Yn.x, __low2half(v), is);
+    p1.hymy = rebuild(Yn.y, __high2half(v), is);
     v = h2(P_HYZ, r);
-    p0.hyz = Yc.x * s6 - v.x * is;
-    p1.hyz = Yc.y * s6 - v.y * is;
-    if (x0 == 0 && t >= 1 && a.src.kind != SRC_NONE) {
-        double gs, inc;
-        source_values(a.src, t, &gs, &inc);
-        if (a.src.kind == SRC_OPEN) {
-            p0.epx += (float)gs;
-            p0.hypx -= (float)gs;
-        } else {
-            p0.epx = (float)inc;
-            p0.hxpx = 0.0f;
-            p0.hypx = (float)(-inc);
-        }
-    }
+    p0.hyz = rebuild(Yc.x, __low2half(v), is);
+    p1.hyz = rebuild(Yc.y, __high2half(v), is);
+    f16_source(a.src, x0, t, p0);
 
     float E30, Hx0, Hy0, D0, E31, Hx1, Hy1, D1;
-    moments(p0, m0.inv_eps3, &E30, &Hx0, &Hy0, &D0);
-    moments(p1, m1.inv_eps3, &E31, &Hx1, &Hy1, &D1);
+    moments(p0, m0.inv_eps3, m0.c_d, &E30, &Hx0, &Hy0, &D0);
+    moments(p1, m1.inv_eps3, m1.c_d, &E31, &Hx1, &Hy1, &D1);
     if (field_runaway(E30) || (has1 && field_runaway(E31))) atomicOr(a.err, 1u);
     const float Ez0 = 3.0f * E30, Ez1 = 3.0f * E31;
     const size_t idx = r + x0;
@@ -146,13 +119,11 @@ __global__ void __launch_bounds__(BX *BY) k_step_f16(const F16Args a, const long
         accumulate_site(a, idx, y, t, Ez0, Hx0, Hy0);
         if (has1) accumulate_site(a, idx + 1, y, t, Ez1, Hx1, Hy1);
     }
-    float g0[NPLANES], g1[NPLANES];
-    deviations(p0, Ez0, Hx0, Hy0, em10, g0);
-    deviations(p1, Ez1, Hx1, Hy1, em11, g1);
-    const float sc = a.scale;
+    __half g0[NPLANES], g1[NPLANES];
+    encode_all(p0, Ez0, Hx0, Hy0, a.scale, g0);
+    encode_all(p1, Ez1, Hx1, Hy1, a.scale, g1);
 #pragma unroll
-    for (int q = 0; q < NPLANES; ++q)
-        *(__half2 *)(a.g_out + q * ps + idx) = __floats2half2_rn(g0[q] * sc, g1[q] * sc);
+    for (int q = 0; q < NPLANES; ++q) *(__half2 *)(a.g_out + q * ps + idx) = __halves2half2(g0[q], g1[q]);
     *(float2 *)(a.fe_out + idx) = make_float2(Ez0, Ez1);
     *(float2 *)(a.fhx_out + idx) = make_float2(Hx0, Hx1);
     *(float2 *)(a.fhy_out + idx) = make_float2(Hy0, Hy1);
@@ -166,13 +137,45 @@ __global__ void __launch_bounds__(BX *BY) k_fields_f16(const F16Args a, const lo
     const size_t idx = (size_t)y * a.pitch + x;
     const MatT<float> m = a.mtab[a.mat[idx]];
     Pop<float> p;
-    pull_f16(a, x, y, *t_dev, p, m.six_em1 * (1.0f / 6.0f));
+    pull_f16(a, x, y, *t_dev, p);
     float E3, Hx, Hy, D;
-    moments(p, m.inv_eps3, &E3, &Hx, &Hy, &D);
+    moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
     const size_t o = (size_t)y * a.nx + x;
     ez[o] = (double)(3.0f * E3);
     hx[o] = (double)Hx;
     hy[o] = (double)Hy;
+}
+
+// Total electromagnetic energy (eps E_z^2 + H_x^2 + H_y^2) / 2 summed over sites.
+__global__ void __launch_bounds__(BX *BY) k_energy_f16(const F16Args a, const long long *__restrict__ t_dev,
+                                                       double *energy) {
+    __shared__ double sh[32];
+    const int x = blockIdx.x * BX + threadIdx.x;
+    const int y = blockIdx.y * BY + threadIdx.y;
+    double w = 0.0;
+    if (x < a.nx && y < a.ny) {
+        const MatT<float> m = a.mtab[a.mat[(size_t)y * a.pitch + x]];
+        Pop<float> p;
+        pull_f16(a, x, y, *t_dev, p);
+        float E3, Hx, Hy, D;
+        moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
+        w = 0.5 * ((double)D * (double)(3.0f * E3) + (double)Hx * (double)Hx + (double)Hy * (double)Hy);
+    }
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    if ((tid & 31) == 0) sh[tid >> 5] = w;
+    __syncthreads();
+    if (tid < 32) {
+        w = tid < (BX * BY) / 32 ? sh[tid] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+        if (tid == 0) atomicAdd(energy, w);
+    }
+}
+
+cudaError_t launch_energy_f16(const F16Args &a, const long long *t_dev, double *energy, cudaStream_t s) {
+    dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY), block(BX, BY);
+    k_energy_f16<<<grid, block, 0, s>>>(a, t_dev, energy);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step_f16(const F16Args &a, const long long *t_in, long long *t_out, bool accumulate,

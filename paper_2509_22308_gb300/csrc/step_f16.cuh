@@ -1,4 +1,10 @@
-// Arguments of the FP16-deviation storage form (see step_f16.cu).
+// FP16-deviation storage form: arguments, layout and the per-population arithmetic
+// shared by every kernel of this form (see step_f16.cu).
+//
+// A population is stored as its deviation from the equilibrium of its own site,
+// g_i = f_i - f_i^eq(F), in FP16 scaled by 2^10, next to the FP32 fields F.  Every
+// kernel rebuilds and re-encodes a population with the explicitly rounded helpers
+// below, so the one-step, two-step and field kernels of this form agree bit for bit.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -20,100 +26,118 @@ struct F16Args {
     AccParams accp;
     unsigned *err;
     float scale, inv_scale;
-    const __half *g;            // 16 deviation planes (input, time t)
+    const __half *g;              // 11 deviation planes (input)
     const float *fe, *fhx, *fhy;  // field planes (input)
     __half *g_out;
     float *fe_out, *fhx_out, *fhy_out;
 };
 
-// Byte layout of one FP16-deviation buffer: 16 half planes, then 3 float planes,
+// Byte layout of one FP16-deviation buffer: 11 half planes, then 3 float planes,
 // each plane pstride elements (offsets rounded to 256 bytes).
 inline size_t f16_half_bytes(size_t pstride) { return ((size_t)NPLANES * pstride * 2 + 255) / 256 * 256; }
 inline size_t f16_plane_bytes(size_t pstride) { return (pstride * 4 + 255) / 256 * 256; }
 inline size_t f16_buffer_bytes(size_t pstride) { return f16_half_bytes(pstride) + 3 * f16_plane_bytes(pstride); }
 
-// Equilibria (Eq. equilibrium distribution functions, TM^z components), each /6:
-//   e_z: +x (E-Hy), -x (E+Hy), +y (E+Hx), -y (E-Hx), z E;     e_0 = (eps - 1) E
-//   h_x: +-x Hx, +y (Hx+E), -y (Hx-E), z Hx;   h_y: +x (Hy-E), -x (Hy+E), +-y Hy, z Hy
+// 6 f_i^eq of each stored population as a function of the fields of its site
+// (Eq. equilibrium distribution functions): e_z: z E, +x E - H_y, -x E + H_y, +y E + H_x,
+// -y E - H_x;  h_x: +-x, z H_x;  h_y: +-y, z H_y.
+__device__ __forceinline__ float eq6_epx(float e, float hx, float hy) { return __fsub_rn(e, hy); }
+__device__ __forceinline__ float eq6_emx(float e, float hx, float hy) { return __fadd_rn(e, hy); }
+__device__ __forceinline__ float eq6_epy(float e, float hx, float hy) { return __fadd_rn(e, hx); }
+__device__ __forceinline__ float eq6_emy(float e, float hx, float hy) { return __fsub_rn(e, hx); }
+
+// f = eq6 / 6 - g / 2^10
+__device__ __forceinline__ float rebuild(float eq6, __half g, float inv_scale) {
+    return __fmaf_rn(-__half2float(g), inv_scale, __fmul_rn(eq6, 1.0f / 6.0f));
+}
+// g = (f - eq6 / 6) * 2^10, rounded to FP16
+__device__ __forceinline__ __half encode(float f, float eq6, float scale) {
+    return __float2half_rn(__fmul_rn(__fsub_rn(f, __fmul_rn(eq6, 1.0f / 6.0f)), scale));
+}
+
 struct Fld {
     float e, hx, hy;
 };
 
-__device__ __forceinline__ Fld load_fld(const F16Args &a, size_t i) {
-    return Fld{a.fe[i], a.fhx[i], a.fhy[i]};
+__device__ __forceinline__ Fld load_fld(const F16Args &a, size_t i) { return Fld{a.fe[i], a.fhx[i], a.fhy[i]}; }
+
+// Source at x = 0 (t >= 1): adds to e_+x (and so, through the tie h_+x,y = -e_+x,z, to h_+x,y).
+__device__ __forceinline__ void f16_source(const SourceParams &src, int x, long long t, Pop<float> &p) {
+    if (x == 0 && t >= 1 && src.kind != SRC_NONE) {
+        double gs, inc;
+        source_values(src, t, &gs, &inc);
+        if (src.kind == SRC_OPEN) {
+            p.epx += (float)gs;
+        } else {
+            p.epx = (float)inc;
+            p.hxpx = 0.0f;
+        }
+    }
 }
 
-__device__ __forceinline__ float ldg_dev(const __half *p, float inv_scale) {
-    return __half2float(*p) * inv_scale;
-}
-
-// f_i(r, t+1) for all 16 populations of site (x, y); F of time t at the neighbours.
-__device__ __forceinline__ void pull_f16(const F16Args &a, int x, int y, long long t1, Pop<float> &p,
-                                         float em1) {
+// f_i(r, t) for the 11 populations of site (x, y), rebuilt from the upstream sites'
+// fields and deviations of time t - 1 (one site per call).
+__device__ __forceinline__ void pull_f16(const F16Args &a, int x, int y, long long t, Pop<float> &p) {
     const size_t ps = a.pstride;
     const int xm = x > 0 ? x - 1 : 0;
     const int xp = x < a.nx - 1 ? x + 1 : x;
     const size_t r = (size_t)y * a.pitch;
     const size_t rm = (size_t)(y > 0 ? y - 1 : 0) * a.pitch;
     const size_t rp = (size_t)(y < a.ny - 1 ? y + 1 : y) * a.pitch;
-    const float is = a.inv_scale, s6 = 1.0f / 6.0f;
+    const float is = a.inv_scale;
     const Fld c = load_fld(a, r + x), w = load_fld(a, r + xm), e = load_fld(a, r + xp);
     const Fld so = load_fld(a, rm + x), no = load_fld(a, rp + x);
     const __half *g = a.g;
-    p.e0 = em1 * c.e - ldg_dev(g + P_E0 * ps + r + x, is);
-    p.ez = c.e * s6 - ldg_dev(g + P_EZ * ps + r + x, is);
-    p.epx = (w.e - w.hy) * s6 - ldg_dev(g + P_EPX * ps + r + xm, is);
-    p.emx = (e.e + e.hy) * s6 - ldg_dev(g + P_EMX * ps + r + xp, is);
-    p.epy = (so.e + so.hx) * s6 - ldg_dev(g + P_EPY * ps + rm + x, is);
-    p.emy = (no.e - no.hx) * s6 - ldg_dev(g + P_EMY * ps + rp + x, is);
-    p.hxpx = w.hx * s6 - ldg_dev(g + P_HXPX * ps + r + xm, is);
-    p.hxmx = e.hx * s6 - ldg_dev(g + P_HXMX * ps + r + xp, is);
-    p.hxpy = (so.hx + so.e) * s6 - ldg_dev(g + P_HXPY * ps + rm + x, is);
-    p.hxmy = (no.hx - no.e) * s6 - ldg_dev(g + P_HXMY * ps + rp + x, is);
-    p.hxz = c.hx * s6 - ldg_dev(g + P_HXZ * ps + r + x, is);
-    p.hypx = (w.hy - w.e) * s6 - ldg_dev(g + P_HYPX * ps + r + xm, is);
-    p.hymx = (e.hy + e.e) * s6 - ldg_dev(g + P_HYMX * ps + r + xp, is);
-    p.hypy = so.hy * s6 - ldg_dev(g + P_HYPY * ps + rm + x, is);
-    p.hymy = no.hy * s6 - ldg_dev(g + P_HYMY * ps + rp + x, is);
-    p.hyz = c.hy * s6 - ldg_dev(g + P_HYZ * ps + r + x, is);
-    if (x == 0 && t1 >= 1 && a.src.kind != SRC_NONE) {
-        double gs, inc;
-        source_values(a.src, t1, &gs, &inc);
-        if (a.src.kind == SRC_OPEN) {
-            p.epx += (float)gs;
-            p.hypx -= (float)gs;
-        } else {
-            p.epx = (float)inc;
-            p.hxpx = 0.0f;
-            p.hypx = (float)(-inc);
-        }
-    }
+    p.ez = rebuild(c.e, g[P_EZ * ps + r + x], is);
+    p.epx = rebuild(eq6_epx(w.e, w.hx, w.hy), g[P_EPX * ps + r + xm], is);
+    p.emx = rebuild(eq6_emx(e.e, e.hx, e.hy), g[P_EMX * ps + r + xp], is);
+    p.epy = rebuild(eq6_epy(so.e, so.hx, so.hy), g[P_EPY * ps + rm + x], is);
+    p.emy = rebuild(eq6_emy(no.e, no.hx, no.hy), g[P_EMY * ps + rp + x], is);
+    p.hxpx = rebuild(w.hx, g[P_HXPX * ps + r + xm], is);
+    p.hxmx = rebuild(e.hx, g[P_HXMX * ps + r + xp], is);
+    p.hxz = rebuild(c.hx, g[P_HXZ * ps + r + x], is);
+    p.hypy = rebuild(so.hy, g[P_HYPY * ps + rm + x], is);
+    p.hymy = rebuild(no.hy, g[P_HYMY * ps + rp + x], is);
+    p.hyz = rebuild(c.hy, g[P_HYZ * ps + r + x], is);
+    f16_source(a.src, x, t, p);
 }
 
-// Deviations from the new equilibrium, g_i = f_i - f_i^eq(F(t)), scaled.
-__device__ __forceinline__ void deviations(const Pop<float> &p, float Ez, float Hx, float Hy, float em1,
-                                           float g[NPLANES]) {
-    const float s6 = 1.0f / 6.0f;
-    g[P_E0] = p.e0 - em1 * Ez;
-    g[P_EZ] = p.ez - Ez * s6;
-    g[P_EPX] = p.epx - (Ez - Hy) * s6;
-    g[P_EMX] = p.emx - (Ez + Hy) * s6;
-    g[P_EPY] = p.epy - (Ez + Hx) * s6;
-    g[P_EMY] = p.emy - (Ez - Hx) * s6;
-    g[P_HXPX] = p.hxpx - Hx * s6;
-    g[P_HXMX] = p.hxmx - Hx * s6;
-    g[P_HXPY] = p.hxpy - (Hx + Ez) * s6;
-    g[P_HXMY] = p.hxmy - (Hx - Ez) * s6;
-    g[P_HXZ] = p.hxz - Hx * s6;
-    g[P_HYPX] = p.hypx - (Hy - Ez) * s6;
-    g[P_HYMX] = p.hymx - (Hy + Ez) * s6;
-    g[P_HYPY] = p.hypy - Hy * s6;
-    g[P_HYMY] = p.hymy - Hy * s6;
-    g[P_HYZ] = p.hyz - Hy * s6;
+// The 11 encoded deviations of a site whose pulled populations are p and fields F.
+__device__ __forceinline__ void encode_all(const Pop<float> &p, float Ez, float Hx, float Hy, float sc,
+                                           __half g[NPLANES]) {
+    g[P_EZ] = encode(p.ez, Ez, sc);
+    g[P_EPX] = encode(p.epx, eq6_epx(Ez, Hx, Hy), sc);
+    g[P_EMX] = encode(p.emx, eq6_emx(Ez, Hx, Hy), sc);
+    g[P_EPY] = encode(p.epy, eq6_epy(Ez, Hx, Hy), sc);
+    g[P_EMY] = encode(p.emy, eq6_emy(Ez, Hx, Hy), sc);
+    g[P_HXPX] = encode(p.hxpx, Hx, sc);
+    g[P_HXMX] = encode(p.hxmx, Hx, sc);
+    g[P_HXZ] = encode(p.hxz, Hx, sc);
+    g[P_HYPY] = encode(p.hypy, Hy, sc);
+    g[P_HYMY] = encode(p.hymy, Hy, sc);
+    g[P_HYZ] = encode(p.hyz, Hy, sc);
+}
+
+// What the next step's pull rebuilds from this site (its fields and encoded deviations):
+// the post-collision populations exactly as storage followed by a pull would give them.
+__device__ __forceinline__ void rebuild_all(const __half g[NPLANES], float Ez, float Hx, float Hy, float is,
+                                            Pop<float> &q) {
+    q.ez = rebuild(Ez, g[P_EZ], is);
+    q.epx = rebuild(eq6_epx(Ez, Hx, Hy), g[P_EPX], is);
+    q.emx = rebuild(eq6_emx(Ez, Hx, Hy), g[P_EMX], is);
+    q.epy = rebuild(eq6_epy(Ez, Hx, Hy), g[P_EPY], is);
+    q.emy = rebuild(eq6_emy(Ez, Hx, Hy), g[P_EMY], is);
+    q.hxpx = rebuild(Hx, g[P_HXPX], is);
+    q.hxmx = rebuild(Hx, g[P_HXMX], is);
+    q.hxz = rebuild(Hx, g[P_HXZ], is);
+    q.hypy = rebuild(Hy, g[P_HYPY], is);
+    q.hymy = rebuild(Hy, g[P_HYMY], is);
+    q.hyz = rebuild(Hy, g[P_HYZ], is);
 }
 
 cudaError_t launch_step_f16(const F16Args &a, const long long *t_in, long long *t_out, bool accumulate,
                             cudaStream_t s);
+cudaError_t launch_energy_f16(const F16Args &a, const long long *t_dev, double *energy, cudaStream_t s);
 cudaError_t launch_fields_f16(const F16Args &a, const long long *t_dev, double *ez, double *hx, double *hy,
                               cudaStream_t s);
 

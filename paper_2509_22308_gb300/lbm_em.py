@@ -57,7 +57,8 @@ class Instance(ctypes.Structure):
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("ctas_per_sm", ctypes.c_int32), ("min_periods", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("conv_tol", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
 
 _P = ctypes.POINTER
@@ -78,6 +79,10 @@ SIGNATURES = {
     "lbm_em_force_torque": [_vp, _P(Contour), _P(ctypes.c_double)],
     "lbm_em_contour_integral_device": [_vp, _vp],
     "lbm_em_force_torque_device": [_vp, _P(Contour), _vp],
+    "lbm_em_energy": [_vp, _P(ctypes.c_double)],
+    "lbm_em_run_converged": [_vp, _P(Contour), ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                             _P(ctypes.c_double), _P(ctypes.c_int64)],
+    "lbm_em_far_field": [_vp, _P(ctypes.c_double), ctypes.c_int32, _P(ctypes.c_double)],
     "lbm_em_get_fields": [_vp, _P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_double)],
     "lbm_em_get_phasors": [_vp, _P(ctypes.c_int32), _P(ctypes.c_double), _P(ctypes.c_int32)],
     "lbm_em_get_material": [_vp, _P(ctypes.c_uint8), _P(ctypes.c_double)],
@@ -88,6 +93,7 @@ SIGNATURES = {
     "lbm_em_batch_create": [_P(Instance), ctypes.c_int32, _P(BatchOpts), _P(_vp)],
     "lbm_em_batch_run": [_vp],
     "lbm_em_batch_results": [_vp, _P(ctypes.c_double), _P(ctypes.c_int32)],
+    "lbm_em_batch_steps": [_vp, _P(ctypes.c_int64)],
     "lbm_em_batch_config": [_vp, _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_int32)],
     "lbm_em_batch_destroy": [_vp],
 }
@@ -230,6 +236,26 @@ class Solver:
         """Asynchronous force/torque into a device buffer of 3 doubles (e.g. a torch tensor's data_ptr)."""
         _call("lbm_em_force_torque_device", self.h, ctypes.byref(c), ctypes.c_void_p(int(d_out_ptr)))
 
+    def energy(self) -> float:
+        v = ctypes.c_double()
+        _call("lbm_em_energy", self.h, ctypes.byref(v))
+        return v.value
+
+    def run_converged(self, c: Contour, tol=1e-3, min_periods=5, max_periods=100):
+        """Periods until the per-period energy settles, then force/torque -> (F, steps run)."""
+        out = np.zeros(3)
+        n = ctypes.c_int64()
+        _call("lbm_em_run_converged", self.h, ctypes.byref(c), float(tol), int(min_periods), int(max_periods),
+              _dptr(out), ctypes.byref(n))
+        return out, n.value
+
+    def far_field(self, angles):
+        """|S(phi)|^2 at the given lattice-frame angles from the accumulated phasors."""
+        ang = np.ascontiguousarray(angles, dtype=np.float64)
+        out = np.zeros(len(ang))
+        _call("lbm_em_far_field", self.h, _dptr(ang), len(ang), _dptr(out))
+        return out
+
     def fields(self):
         ez = np.empty((self.ny, self.nx))
         hx = np.empty_like(ez)
@@ -294,7 +320,8 @@ def run_instance(inst: dict, precision="f64", stream=None, single_step=False) ->
 class Batch:
     """Owner of one ``lbm_em_batch_t``."""
 
-    def __init__(self, instances, precision="f32", tile_w=0, tile_h=0, ctas_per_sm=0, stream=None):
+    def __init__(self, instances, precision="f32", tile_w=0, tile_h=0, ctas_per_sm=0, stream=None,
+                 conv_tol=0.0, min_periods=0):
         L = load()
         n = len(instances)
         arr = (Instance * n)()
@@ -303,8 +330,8 @@ class Batch:
                               int(inst.get("ramp", inst["period"])), int(inst.get("n_points", 0)), 1.0,
                               float(inst["R"]),
                               make_janus(inst["a"], inst["phi0"], inst["eps1"], inst["eps2"], inst["pec2"]))
-        o = BatchOpts(PRECISIONS.get(precision, precision), int(tile_w), int(tile_h), int(ctas_per_sm), 0,
-                      _stream_ptr(stream))
+        o = BatchOpts(PRECISIONS.get(precision, precision), int(tile_w), int(tile_h), int(ctas_per_sm),
+                      int(min_periods), 0, float(conv_tol), _stream_ptr(stream))
         b = ctypes.c_void_p()
         _call("lbm_em_batch_create", arr, n, ctypes.byref(o), ctypes.byref(b))
         self.b, self.n, self._L = b, n, L
@@ -317,6 +344,11 @@ class Batch:
         st = np.zeros(self.n, dtype=np.int32)
         _call("lbm_em_batch_results", self.b, _dptr(out), st.ctypes.data_as(_P(ctypes.c_int32)))
         return out.reshape(-1, 3), st
+
+    def steps(self):
+        out = np.zeros(self.n, dtype=np.int64)
+        _call("lbm_em_batch_steps", self.b, out.ctypes.data_as(_P(ctypes.c_int64)))
+        return out
 
     def config(self):
         w, h, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

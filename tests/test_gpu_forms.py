@@ -103,7 +103,7 @@ def test_batch_reports_unstable_instance():
         arr[i] = L.Instance(inst["nx"], inst["ny"], inst["period"], inst["periods"], inst["ramp"], 0,
                             1e9 if i == 1 else 1.0, inst["R"],
                             L.make_janus(inst["a"], inst["phi0"], inst["eps1"], inst["eps2"], inst["pec2"]))
-    o = L.BatchOpts(L.F32, 64, 4, 2, 0, None)
+    o = L.BatchOpts(L.F32, 64, 4, 2, 0, 0, 0.0, None)
     h = ctypes.c_void_p()
     L._call("lbm_em_batch_create", arr, 2, ctypes.byref(o), ctypes.byref(h))
     L._call("lbm_em_batch_run", h)
@@ -145,3 +145,51 @@ def test_f16dev_single_step_mode_within_tolerance():
     F64 = L.run_instance(inst, "f64")
     F16 = L.run_instance(inst, "f16dev", single_step=True)
     assert np.max(np.abs(F16 - F64)) < 1e-3 * abs(F64[0])
+
+
+def test_far_field_matches_oracle_transform():
+    """GPU near-to-far-field transform against the oracle's transform of the oracle's
+    own phasors (same seeded instance)."""
+    from oracle import geometry as G
+    from oracle import lbm as OL
+    from oracle import ntff
+    inst = W.small_cases()[1]
+    eps, pec, _ = G.janus_material(inst["nx"], inst["ny"], inst["a"], inst["phi0"], inst["eps1"],
+                                   inst["eps2"], inst["pec2"])
+    sim = OL.Simulation(eps, pec, period=inst["period"], ramp_steps=inst["ramp"])
+    sim.advance((inst["periods"] - 1) * inst["period"])
+    sim.advance(inst["period"], accumulate=True)
+    cx, cy = G.default_center(inst["nx"], inst["ny"])
+    phis = np.linspace(0, 2 * np.pi, 25)[:-1]
+    ref = ntff.scattering_intensity_lattice(*sim.phasors(), inst["period"], cx, cy, inst["R"],
+                                            2 * int(np.ceil(2 * np.pi * inst["R"])), phis)
+    with L.solver_for_instance(inst, "f64") as s:
+        s.step((inst["periods"] - 1) * inst["period"])
+        s.force_torque(L.make_contour(inst["R"], inst["a"]))
+        got = s.far_field(phis)
+    assert np.max(np.abs(got - ref)) < 1e-10 * np.max(ref)
+
+
+@pytest.mark.parametrize("eps1,phi0", [(1.0, 0.0), (2.0, -np.pi / 4), (5.0, 0.0)])
+def test_far_field_validation_at_paper_resolution(eps1, phi0):
+    """Sec. IV.A far-field validation: metallo-dielectric Janus cylinder, a = lambda,
+    lambda_eps / dx = 50 inside the dielectric, L/a = 10; the LBM |S(phi)|^2 agrees with
+    the analytic one within 5 % at most scattering angles."""
+    from oracle import analytic as A
+    from oracle import ntff
+    lam = 50.0 * np.sqrt(eps1)
+    T = int(round(3 * lam))
+    a = T / 3.0
+    n = int(round(10 * a)) // 2 * 2
+    inst = dict(nx=n, ny=n, a=a, phi0=phi0, eps1=eps1, eps2=1.0, pec2=True, period=T, periods=30,
+                R=1.5 * a, ramp=T)
+    phis = np.linspace(0, 2 * np.pi, 73)[:-1]
+    with L.solver_for_instance(inst, "f32") as s:
+        s.step(29 * T)
+        s.force_torque(L.make_contour(inst["R"], a))
+        S = s.far_field(phis)
+    k = ntff.lattice_wavenumber(T)
+    B, D, _ = A.md_janus_BD_galerkin(k, a, eps1, phi0, n_basis=320)
+    Sa = A.scattering_intensity(B, D, phis + phi0 + np.pi)
+    rel = np.abs(S - Sa) / Sa
+    assert np.median(rel) < 0.05 and np.mean(rel < 0.05) > 0.6, (np.median(rel), np.mean(rel < 0.05))

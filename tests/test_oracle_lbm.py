@@ -182,3 +182,28 @@ def test_mirror_symmetry_is_exact():
     assert abs(F1[0] - F2[0]) < 1e-12 * scale
     assert abs(F1[1] + F2[1]) < 1e-12 * scale and abs(F1[2] + F2[2]) < 1e-12 * scale
     assert abs(F1[1]) > 1e-3 and abs(F1[2]) > 1e-3
+
+
+@pytest.mark.parametrize("kind", [lbm.SRC_OPEN, lbm.SRC_HARD])
+def test_reduced_state_invariants(kind):
+    """Exact relations of the TM^z state from a zero start, on the full 42-component
+    state: populations that move together and have equal or opposite equilibria stay
+    equal or opposite (their difference only flips sign in the collision), and the rest
+    population is tied to the z pair, e_0 = 6 (eps_r - 1) e_z (0 in PEC cells).  The CUDA
+    path stores 11 planes on the strength of these relations."""
+    from paper_2509_22308_gb300 import workloads as W
+    for inst in W.small_cases():
+        eps, pec, _ = G.janus_material(inst["nx"], inst["ny"], inst["a"], inst["phi0"], inst["eps1"],
+                                       inst["eps2"], inst["pec2"])
+        sim = lbm.Simulation(eps, pec, period=inst["period"], ramp_steps=inst["ramp"], source_kind=kind,
+                             nthreads=4)
+        sim.advance(3 * inst["period"] + 7)
+        e, h = sim.f[:, :, :7, :], sim.f[:, :, 7:, :]
+        assert np.array_equal(e[:, :, 1, 2], -h[:, :, 1, 1])     # e_+x,z = -h_+x,y
+        assert np.array_equal(e[:, :, 2, 2], h[:, :, 2, 1])      # e_-x,z =  h_-x,y
+        assert np.array_equal(e[:, :, 3, 2], h[:, :, 3, 0])      # e_+y,z =  h_+y,x
+        assert np.array_equal(e[:, :, 4, 2], -h[:, :, 4, 0])     # e_-y,z = -h_-y,x
+        assert np.array_equal(e[:, :, 5, 2], e[:, :, 6, 2])      # e_+z,z =  e_-z,z
+        assert np.array_equal(h[:, :, 5, :2], h[:, :, 6, :2])    # h_+z = h_-z (x, y)
+        ratio = np.where(pec == 1, 0.0, 6.0 * (eps - 1.0))
+        assert np.max(np.abs(e[:, :, 0, 2] - ratio * e[:, :, 5, 2])) < 1e-13 * np.abs(sim.f).max()
