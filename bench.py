@@ -33,8 +33,7 @@ WORKLOAD = "md_janus_512"
 # algorithmic bytes per lattice update: the 11 stored planes read and written once, plus
 # the 1-byte material id (FP16-deviation: 11 FP16 deviations + 3 FP32 fields each way)
 BYTES_PER_LU = {"f64": 11 * 8 * 2 + 1, "f32": 11 * 4 * 2 + 1, "f16dev": 2 * (11 * 2 + 3 * 4) + 1}
-STEP_KERNEL = {"f64": "k_step<double, false>", "f32": "k_step2_f32<false> (two steps per launch)",
-               "f16dev": "k_step2_f16<false> (two steps per launch)"}
+STEP_KERNEL = {"f64": "k_step<double, false>", "f32": "k_step<float, false>", "f16dev": "k_step_f16<false>"}
 # FP64 pipe operations per lattice update of the step kernel: 12 for the moments
 # (sums of 5, 5 and 5 stored populations, one scaling), 16 for the equilibria and 2 f^eq - f
 FP64_OPS_PER_LU = 28
@@ -227,9 +226,9 @@ def profile_case():
     from paper_2509_22308_gb300 import lbm_em as L
     inst = dict(nx=2048, ny=2048, a=128.0, phi0=0.5, eps1=4.0, eps2=1.0, pec2=True, period=240, periods=1,
                 R=192.0, ramp=240)
-    for fp, single in (("f64", False), ("f32", False), ("f16dev", False), ("f32", True), ("f16dev", True)):
-        with L.solver_for_instance(inst, fp, single_step=single) as s:
-            s.step(2 if single or fp == "f64" else 4)
+    for fp, mode in (("f64", "auto"), ("f32", "two"), ("f16dev", "two"), ("f32", "one"), ("f16dev", "one")):
+        with L.solver_for_instance(inst, fp, steps_per_launch=mode) as s:
+            s.step(4 if mode == "two" else 2)
             s.sync()
     # and two launches of the benchmark's own 512^2 FP64 instance (theta = 0)
     from paper_2509_22308_gb300 import workloads as W
@@ -473,9 +472,13 @@ def main():
         # blocking), so they can exceed the one-read-one-write-per-step roofline.
         big = W.md_janus_8192()[0]
         hs = {}
-        for fp, single in (("f32", False), ("f16dev", False), ("f32", True), ("f16dev", True), ("f64", False)):
-            key = fp + ("_one_step_per_launch" if single else "")
-            with L.solver_for_instance(big, fp, main, single_step=single) as s:
+        for fp, mode in (("f32", "auto"), ("f32", "one"), ("f16dev", "auto"), ("f16dev", "two"), ("f64", "auto")):
+            key = fp + {"auto": "", "one": "_one_step_per_launch", "two": "_two_steps_per_launch"}[mode]
+            kern = {("f32", "auto"): "k_step2_f32<false> (two steps per launch)",
+                    ("f32", "one"): "k_step<float, false>", ("f16dev", "auto"): "k_step_f16<false>",
+                    ("f16dev", "two"): "k_step2_f16<false> (two steps per launch)",
+                    ("f64", "auto"): "k_step<double, false>"}[(fp, mode)]
+            with L.solver_for_instance(big, fp, main, steps_per_launch=mode) as s:
                 s.step(4)
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 n = 16
@@ -486,9 +489,7 @@ def main():
                 us = a.elapsed_time(b) * 1e3 / n
                 sites = big["nx"] * big["ny"]
                 gbs = sites * BYTES_PER_LU[fp] / (us / 1e6) / 1e9
-                hs[key] = {"kernel": STEP_KERNEL[fp] if not single else
-                           {"f32": "k_step<float, false>", "f16dev": "k_step_f16<false>"}[fp],
-                           "us_per_step": round(us, 2),
+                hs[key] = {"kernel": kern, "us_per_step": round(us, 2),
                           "glups": round(sites / (us / 1e6) / 1e9, 2), "achieved_gbs": round(gbs, 1),
                           "frac_hbm": round(gbs / peak, 4), "bytes_per_lu": BYTES_PER_LU[fp]}
                 if fp == "f64":

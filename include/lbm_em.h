@@ -62,16 +62,17 @@ typedef enum {
     LBM_EM_SRC_NONE = 2   /* no source (all edges open)                                  */
 } lbm_em_source_kind;
 
-/* lbm_em_grid.flags: run the FP32 and FP16-deviation forms one time step per kernel
- * launch.  By default they advance two steps per launch (the intermediate state stays in
- * shared memory); FP32 results are bit-identical either way, FP16-deviation keeps every
- * second intermediate state in FP32 instead of FP16. */
-#define LBM_EM_FLAG_SINGLE_STEP 1
+/* lbm_em_grid.flags: how many time steps one kernel launch advances.  By default FP64 and
+ * FP16-deviation advance one step per launch and FP32 two (the intermediate state of each
+ * tile stays in shared memory) on lattices of at least 2^25 sites, one below that.  The
+ * result does not depend on the choice: both modes give the same bits. */
+#define LBM_EM_FLAG_SINGLE_STEP 1  /* always one step per launch                          */
+#define LBM_EM_FLAG_TWO_STEP 2     /* two steps per launch for FP32 and FP16-deviation    */
 
 typedef struct {
     int32_t nx, ny;       /* lattice size, each >= 4                                      */
     int32_t precision;    /* lbm_em_precision                                             */
-    int32_t flags;        /* 0 or LBM_EM_FLAG_SINGLE_STEP                                 */
+    int32_t flags;        /* 0, LBM_EM_FLAG_SINGLE_STEP or LBM_EM_FLAG_TWO_STEP           */
     void *stream;         /* cudaStream_t every kernel of the handle runs on; NULL: the
                              library creates a private non-blocking stream                */
 } lbm_em_grid;
@@ -255,7 +256,7 @@ typedef struct {
 
 typedef struct {
     int32_t precision;       /* LBM_EM_F32 or LBM_EM_F64                                    */
-    int32_t tile_w, tile_h;  /* tile shape of the packed tile list; 0: autotuned           */
+    int32_t tile_w, tile_h;  /* tile shape (tile_w 32/64/128/256, tile_h <= 16); 0: autotuned */
     int32_t ctas_per_sm;     /* persistent CTAs per SM; 0: autotuned                       */
     int32_t min_periods;     /* convergence exits: fewest periods an instance runs         */
     int32_t reserved;        /* 0                                                          */

@@ -358,7 +358,9 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     if (!g || !out) return set_error(LBM_EM_EINVAL, "grid/out is NULL");
     *out = nullptr;
     if (g->nx < 4 || g->ny < 4) return set_error(LBM_EM_EINVAL, "nx and ny must be >= 4");
-    if (g->flags & ~LBM_EM_FLAG_SINGLE_STEP) return set_error(LBM_EM_EINVAL, "unknown grid flags");
+    if (g->flags & ~(LBM_EM_FLAG_SINGLE_STEP | LBM_EM_FLAG_TWO_STEP)) return set_error(LBM_EM_EINVAL, "unknown grid flags");
+    if ((g->flags & LBM_EM_FLAG_SINGLE_STEP) && (g->flags & LBM_EM_FLAG_TWO_STEP))
+        return set_error(LBM_EM_EINVAL, "LBM_EM_FLAG_SINGLE_STEP and LBM_EM_FLAG_TWO_STEP exclude each other");
     if ((long long)g->nx * g->ny > (1LL << 31)) return set_error(LBM_EM_EINVAL, "lattice too large (> 2^31 sites)");
     if (g->precision != LBM_EM_F64 && g->precision != LBM_EM_F32 && g->precision != LBM_EM_F16DEV)
         return set_error(LBM_EM_EINVAL, "precision must be LBM_EM_F64, LBM_EM_F32 or LBM_EM_F16DEV");
@@ -378,7 +380,14 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     h->pitch = round_up(g->nx, 32);
     h->pstride = (size_t)h->pitch * (size_t)g->ny;
     h->srccfg = *s;
-    h->tb = (g->precision == LBM_EM_F32 || g->precision == LBM_EM_F16DEV) && !(g->flags & LBM_EM_FLAG_SINGLE_STEP);
+    // two steps per launch: forced by the flag, else by default for FP32 lattices large
+    // enough (>= 2^25 sites) that the shared-memory tiles fill the GPU many times over;
+    // measured on GB300 it loses on smaller FP32 lattices and on the FP16-deviation form
+    if (g->flags & LBM_EM_FLAG_TWO_STEP)
+        h->tb = g->precision != LBM_EM_F64;
+    else
+        h->tb = g->precision == LBM_EM_F32 && !(g->flags & LBM_EM_FLAG_SINGLE_STEP) &&
+                (long long)g->nx * g->ny >= (1LL << 25);
     for (int i = 0; i < 256; ++i) {
         h->eps_table[i] = 1.0;
         h->pec_id[i] = false;

@@ -46,7 +46,7 @@ template <typename T>
 struct BatchArgs {
     const InstDesc *inst;
     const Tile *tiles;
-    int n_tiles, tile_w, tile_h, pad;
+    int n_tiles, tile_w, tile_h, log2_tile_w;
     const T *fin;
     T *fout;
     const uint8_t *mat;
@@ -57,9 +57,10 @@ struct BatchArgs {
     int conv;          // 1: sample the energy at period boundaries (convergence exits)
 };
 
+// FP32: at most 85 registers so that 3 CTAs of 256 threads stay resident per SM.
 template <typename T>
-__global__ void __launch_bounds__(256) k_batch_step(const BatchArgs<T> b, const long long *__restrict__ t_in,
-                                                    long long *__restrict__ t_out) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+    k_batch_step(const BatchArgs<T> b, const long long *__restrict__ t_in, long long *__restrict__ t_out) {
     const long long t = *t_in;
     if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + 1;
     __shared__ MatT<T> smat[3];
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(256) k_batch_step(const BatchArgs<T> b, const 
         T *fout = b.fout + d.base;
         const uint8_t *mat = b.mat + d.mat_base;
         for (int k = threadIdx.x; k < tsz; k += blockDim.x) {
-            const int x = tl.x0 + k % b.tile_w, y = tl.y0 + k / b.tile_w;
+            const int x = tl.x0 + (k & (b.tile_w - 1)), y = tl.y0 + (k >> b.log2_tile_w);
             if (x >= d.nx || y >= d.ny) continue;
             Pop<T> p;
             pull_site(a, fin, x, y, t, p);
@@ -288,6 +289,12 @@ static lbm_em_status batch_tiles(lbm_em_batch *b, int tw, int th) {
     return st;
 }
 
+static int ilog2(int v) {
+    int l = 0;
+    while ((1 << (l + 1)) <= v) ++l;
+    return l;
+}
+
 // Staircase Janus disc of every instance into the packed material ids (Sec. II).
 static cudaError_t batch_rasterize(lbm_em_batch *b) {
     for (int i = 0; i < b->n; ++i) {
@@ -306,12 +313,12 @@ static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, long long t) {
     const int p = (int)(t & 1);
     const int grid = b->ctas * b->sms;
     if (b->prec == LBM_EM_F64) {
-        BatchArgs<double> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, 0,
+        BatchArgs<double> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, ilog2(b->tile_w),
                             (const double *)b->buf[p], (double *)b->buf[1 - p], b->d_mat, b->d_slot,
                             b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
         k_batch_step<double><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
     } else {
-        BatchArgs<float> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, 0,
+        BatchArgs<float> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, ilog2(b->tile_w),
                            (const float *)b->buf[p], (float *)b->buf[1 - p], b->d_mat, b->d_slot,
                            b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
         k_batch_step<float><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
@@ -408,7 +415,8 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
         return set_error(LBM_EM_EINVAL, "batch precision must be LBM_EM_F32 or LBM_EM_F64");
     if (o->tile_w < 0 || o->tile_h < 0 || o->ctas_per_sm < 0 || o->ctas_per_sm > 8)
         return set_error(LBM_EM_EINVAL, "bad tile shape or CTAs per SM");
-    if (o->tile_w && (o->tile_w % 32 || o->tile_w > 256)) return set_error(LBM_EM_EINVAL, "tile_w: multiple of 32, <= 256");
+    if (o->tile_w && o->tile_w != 32 && o->tile_w != 64 && o->tile_w != 128 && o->tile_w != 256)
+        return set_error(LBM_EM_EINVAL, "tile_w must be 32, 64, 128 or 256");
     if (!(o->conv_tol >= 0.0) || o->min_periods < 0) return set_error(LBM_EM_EINVAL, "conv_tol >= 0, min_periods >= 0");
     if (o->tile_h && (o->tile_h > 16)) return set_error(LBM_EM_EINVAL, "tile_h must be <= 16");
     for (int i = 0; i < n; ++i) {

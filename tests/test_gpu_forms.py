@@ -115,11 +115,14 @@ def test_batch_reports_unstable_instance():
     L.load().lbm_em_batch_destroy(h)
 
 
+@pytest.mark.parametrize("prec", ["f32", "f16dev"])
 @pytest.mark.parametrize("inst", W.small_cases()[:3], ids=lambda i: f"{i['nx']}x{i['ny']}")
-def test_two_steps_per_launch_is_bit_identical_in_fp32(inst):
-    """FP32 with two steps per launch (temporal blocking) equals one step per launch bit
-    for bit, for even and odd step counts and through the accumulating period."""
-    with L.solver_for_instance(inst, "f32") as a, L.solver_for_instance(inst, "f32", single_step=True) as b:
+def test_two_steps_per_launch_is_bit_identical(inst, prec):
+    """Two steps per launch (temporal blocking) equals one step per launch bit for bit,
+    for even and odd step counts and through the accumulating period; the FP16-deviation
+    form rounds the intermediate state exactly as storing it would."""
+    with L.solver_for_instance(inst, prec, steps_per_launch="two") as a, \
+            L.solver_for_instance(inst, prec, steps_per_launch="one") as b:
         for n in (1, 2, 5, 32, 33, 64, 3):
             a.step(n)
             b.step(n)
@@ -132,7 +135,8 @@ def test_two_steps_per_launch_is_bit_identical_in_fp32(inst):
 def test_f16dev_split_runs_agree_bitwise():
     """The FP16-deviation form gives the same bits however a run is split into calls."""
     inst = W.small_cases()[2]
-    with L.solver_for_instance(inst, "f16dev") as a, L.solver_for_instance(inst, "f16dev") as b:
+    with L.solver_for_instance(inst, "f16dev", steps_per_launch="two") as a, \
+            L.solver_for_instance(inst, "f16dev", steps_per_launch="two") as b:
         a.step(77)
         for n in (3, 30, 1, 43):
             b.step(n)
@@ -140,10 +144,10 @@ def test_f16dev_split_runs_agree_bitwise():
             assert np.array_equal(x, y)
 
 
-def test_f16dev_single_step_mode_within_tolerance():
+def test_f16dev_two_step_mode_within_tolerance():
     inst = W.homogeneous_dielectric_256()[0]
     F64 = L.run_instance(inst, "f64")
-    F16 = L.run_instance(inst, "f16dev", single_step=True)
+    F16 = L.run_instance(inst, "f16dev", steps_per_launch="two")
     assert np.max(np.abs(F16 - F64)) < 1e-3 * abs(F64[0])
 
 
@@ -185,11 +189,32 @@ def test_far_field_validation_at_paper_resolution(eps1, phi0):
                 R=1.5 * a, ramp=T)
     phis = np.linspace(0, 2 * np.pi, 73)[:-1]
     with L.solver_for_instance(inst, "f32") as s:
-        s.step(29 * T)
-        s.force_torque(L.make_contour(inst["R"], a))
+        # run until the domain energy has settled (Sec. III); high contrast needs long runs
+        _, steps = s.run_converged(L.make_contour(inst["R"], a), tol=1e-5, min_periods=20, max_periods=120)
         S = s.far_field(phis)
     k = ntff.lattice_wavenumber(T)
     B, D, _ = A.md_janus_BD_galerkin(k, a, eps1, phi0, n_basis=320)
     Sa = A.scattering_intensity(B, D, phis + phi0 + np.pi)
     rel = np.abs(S - Sa) / Sa
-    assert np.median(rel) < 0.05 and np.mean(rel < 0.05) > 0.6, (np.median(rel), np.mean(rel < 0.05))
+    print(f"eps1={eps1} phi0={phi0:.3f} steps={steps} median={np.median(rel):.4f} within5%={np.mean(rel < 0.05):.2f}")
+    assert np.median(rel) < 0.05 and np.mean(rel < 0.05) > 0.6, (np.median(rel), np.mean(rel < 0.05), steps)
+
+
+def test_design_map_symmetry_and_trajectory():
+    """A metallo-dielectric design map over phi0 from one batched run: drag symmetric,
+    lift and torque antisymmetric about phi0 = pi/2 (Sec. IV.A), no torque at pi/2 and
+    3 pi/2; a trajectory started off a torque-free orientation settles on a stable one."""
+    from paper_2509_22308_gb300 import trajectory as TR
+    n = 24
+    F = TR.design_map(2.0, pec2=True, n_phi=n, a=16, periods=20, precision="f32")
+    scale = np.abs(F[:, 0]).max()
+    k = np.arange(n)
+    mirror = (n // 2 - k) % n                     # phi0 -> pi - phi0
+    assert np.max(np.abs(F[:, 0] - F[mirror, 0])) < 1e-4 * scale
+    assert np.max(np.abs(F[:, 1] + F[mirror, 1])) < 1e-4 * scale
+    assert np.max(np.abs(F[:, 2] + F[mirror, 2])) < 1e-4 * scale
+    assert abs(F[n // 4, 2]) < 1e-4 * scale and abs(F[3 * n // 4, 2]) < 1e-4 * scale
+    fmap = TR.PeriodicMap(F[:, 0], F[:, 1], F[:, 2])
+    tr = TR.integrate(fmap, 0.1, t_final=2.0e4, dt=2.0)
+    assert abs(fmap(tr[-1, 3])[0, 2]) < 1e-3 * scale
+    assert tr[-1, 1] > 0                          # drag pushes along +x
