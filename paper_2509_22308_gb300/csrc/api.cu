@@ -343,13 +343,7 @@ static void free_handle(lbm_em *h) {
 template <typename T>
 static std::vector<MatT<T>> material_table(const double *eps, const bool *pec) {
     std::vector<MatT<T>> tab(256);
-    for (int i = 0; i < 256; ++i) {
-        if (pec[i]) {
-            tab[i] = MatT<T>{(T)0, (T)0, (T)0, (T)0};
-        } else {
-            tab[i] = MatT<T>{(T)(1.0 / (3.0 * eps[i])), (T)(6.0 * eps[i] - 4.0), (T)(1.0 / eps[i]), (T)0};
-        }
-    }
+    for (int i = 0; i < 256; ++i) tab[i] = material_entry<T>(eps[i], pec[i]);
     return tab;
 }
 

@@ -35,7 +35,7 @@ struct InstDesc {
     long long steps, acc_from;
     int acc_base, y0, y1, pad;
     SourceParams src;
-    double mtab[3][3];  // per region id: inv_eps3, c_d = 6 eps - 4, inv_eps
+    double mtab[3][4];  // per region id: MatT in the batch's type, widened (exactly) to double
 };
 
 struct Tile {
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
         __syncthreads();
         if (threadIdx.x < 3)
             smat[threadIdx.x] = MatT<T>{(T)d.mtab[threadIdx.x][0], (T)d.mtab[threadIdx.x][1],
-                                        (T)d.mtab[threadIdx.x][2], (T)0};
+                                        (T)d.mtab[threadIdx.x][2], (T)d.mtab[threadIdx.x][3]};
         __syncthreads();
         StepArgs<T> a;
         a.nx = d.nx;
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
             const size_t idx = (size_t)y * d.pitch + x;
             const MatT<T> m = smat[mat[idx]];
             T E3, Hx, Hy, D;
-            moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
+            moments(p, m, &E3, &Hx, &Hy, &D);
             if (field_runaway(E3)) atomicOr(b.err + tl.inst, 1u);
             if (acc && y >= d.y0 && y <= d.y1) {
                 const int s = b.slot[d.slot_base + idx];
@@ -501,9 +501,14 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
         const double eps[3] = {1.0, s.janus.eps1, s.janus.pec2 ? 0.0 : s.janus.eps2};
         for (int r = 0; r < 3; ++r) {
             const bool pec = r == 2 && s.janus.pec2;
-            d.mtab[r][0] = pec ? 0.0 : 1.0 / (3.0 * eps[r]);
-            d.mtab[r][1] = pec ? 0.0 : 6.0 * eps[r] - 4.0;
-            d.mtab[r][2] = pec ? 0.0 : 1.0 / eps[r];
+            double *e = d.mtab[r];
+            if (b->prec == LBM_EM_F32) {
+                const MatT<float> m = material_entry<float>(eps[r], pec);
+                e[0] = m.inv_eps3, e[1] = m.c_d, e[2] = m.inv_eps, e[3] = m.c3;
+            } else {
+                const MatT<double> m = material_entry<double>(eps[r], pec);
+                e[0] = m.inv_eps3, e[1] = m.c_d, e[2] = m.inv_eps, e[3] = m.c3;
+            }
         }
     }
     b->buf_elems = base;

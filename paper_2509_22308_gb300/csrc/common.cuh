@@ -37,10 +37,11 @@ enum SourceKind { SRC_OPEN = 0, SRC_HARD = 1, SRC_NONE = 2 };
 
 // Per-material constants in the kernel's arithmetic type:
 // inv_eps3 = 1/(3 eps_r) (0 for PEC: E := 0), c_d = 6 eps_r - 4 (the weight of the z pair
-// in D once e_0 = 6 (eps_r - 1) e_z is substituted), inv_eps = 1/eps_r.
+// in D once e_0 = 6 (eps_r - 1) e_z is substituted), inv_eps = 1/eps_r, c3 = 3 eps_r
+// (1 for PEC).  The host builds the table so that c_d + 4 = 2 c3 holds exactly in T.
 template <typename T>
 struct MatT {
-    T inv_eps3, c_d, inv_eps, pad;
+    T inv_eps3, c_d, inv_eps, c3;
 };
 
 // Left-edge source: the exact discrete plane wave of the lattice.  With
@@ -134,14 +135,32 @@ __device__ __forceinline__ void pull_site(const StepArgs<T> &a, const T *__restr
 template <typename T>
 __device__ __forceinline__ T fmat(T a, T b, T c) { return fma(a, b, c); }
 
+// num / den in FP32 without a fixed bias: q = num * inv carries the rounding of the
+// constant inv ~ 1/den, the same relative error at every site and step; the residual
+// num - q den is exact in one FMA, and adding residual * inv corrects q to within about
+// one unit in the last place of the true quotient, with a sign that varies from site to
+// site (one Newton-Raphson residual correction, as in Markstein's division scheme).
+// Why it matters: the scheme at tau = 1/2 has no damping, so a relative bias b in the
+// equilibria (1/3 rounded to FP32 is 1/3 (1 + 3.0e-8)) multiplies the wave by (1 + 2b)
+// every step: +7e-4 in amplitude after 12 000 steps, twice that in the forces.
+__device__ __forceinline__ float quot(float num, float den, float inv) {
+    const float q = __fmul_rn(num, inv);
+    return __fmaf_rn(__fmaf_rn(-q, den, num), inv, q);
+}
+
 // Moments (Sec. III): D = sum e_i = (6 eps_r - 4) e_z + e_+x + e_-x + e_+y + e_-y (the rest
 // population and the z pair folded in), E_z = D / eps_r, H = sum h_i with the tied
 // populations substituted.  Returns D, E_z/3 (the scale every equilibrium uses), H_x, H_y.
+// FP32 takes E_z/3 = D / c3 through quot(); with c_d + 4 = 2 c3 exact in the table the
+// collision then conserves D up to that one unbiased rounding.
 template <typename T>
-__device__ __forceinline__ void moments(const Pop<T> &p, T inv_eps3, T c_d, T *E3, T *Hx, T *Hy, T *D) {
-    const T d = fmat(c_d, p.ez, p.epx) + p.emx + p.epy + p.emy;
+__device__ __forceinline__ void moments(const Pop<T> &p, const MatT<T> &m, T *E3, T *Hx, T *Hy, T *D) {
+    const T d = fmat(m.c_d, p.ez, p.epx) + p.emx + p.epy + p.emy;
     *D = d;
-    *E3 = d * inv_eps3;
+    if constexpr (sizeof(T) == 4)
+        *E3 = quot(d, m.c3, m.inv_eps3);
+    else
+        *E3 = d * m.inv_eps3;
     *Hx = fmat((T)2, p.hxz, p.hxpx + p.hxmx) + (p.epy - p.emy);
     *Hy = fmat((T)2, p.hyz, p.hypy + p.hymy) + (p.emx - p.epx);
 }
@@ -150,24 +169,42 @@ __device__ __forceinline__ void moments(const Pop<T> &p, T inv_eps3, T c_d, T *E
 // Eq. (equilibrium distribution functions) for the stored components:
 //   e_z:  z E/3, +x (E-H_y)/3, -x (E+H_y)/3, +y (E+H_x)/3, -y (E-H_x)/3
 //   h_x:  +-x and z H_x/3;   h_y: +-y and z H_y/3
-// 28 arithmetic operations per site with the moments (FP64 is bound by its pipe on
-// GB300): every 2 f^eq that is E/3 +- H/3 is one fused multiply-add.
+// FP64: 28 arithmetic operations per site with the moments (FP64 is bound by its pipe
+// on GB300): every 2 f^eq that is E/3 +- H/3 is one fused multiply-add; the bias of 1/3
+// rounded to FP64 (2^-54 relative) stays below 1e-11 over 10^5 steps.  FP32 forms H/3
+// once per component through quot() (see there) and adds or subtracts it.
 template <typename T>
 __device__ __forceinline__ void collide(Pop<T> &p, T E3, T Hx, T Hy) {
-    const T third = (T)(1.0 / 3.0), mthird = (T)(-1.0 / 3.0);
-    const T A = fmat(Hy, mthird, E3), B = fmat(Hy, third, E3);
-    const T C = fmat(Hx, third, E3), D = fmat(Hx, mthird, E3);
-    p.ez = E3 - p.ez;
-    p.epx = A - p.epx;
-    p.emx = B - p.emx;
-    p.epy = C - p.epy;
-    p.emy = D - p.emy;
-    p.hxpx = fmat(Hx, third, -p.hxpx);
-    p.hxmx = fmat(Hx, third, -p.hxmx);
-    p.hxz = fmat(Hx, third, -p.hxz);
-    p.hypy = fmat(Hy, third, -p.hypy);
-    p.hymy = fmat(Hy, third, -p.hymy);
-    p.hyz = fmat(Hy, third, -p.hyz);
+    if constexpr (sizeof(T) == 4) {
+        const float third = 1.0f / 3.0f;
+        const float hx3 = quot(Hx, 3.0f, third), hy3 = quot(Hy, 3.0f, third);
+        p.ez = E3 - p.ez;
+        p.epx = (E3 - hy3) - p.epx;
+        p.emx = (E3 + hy3) - p.emx;
+        p.epy = (E3 + hx3) - p.epy;
+        p.emy = (E3 - hx3) - p.emy;
+        p.hxpx = hx3 - p.hxpx;
+        p.hxmx = hx3 - p.hxmx;
+        p.hxz = hx3 - p.hxz;
+        p.hypy = hy3 - p.hypy;
+        p.hymy = hy3 - p.hymy;
+        p.hyz = hy3 - p.hyz;
+    } else {
+        const T third = (T)(1.0 / 3.0), mthird = (T)(-1.0 / 3.0);
+        const T A = fmat(Hy, mthird, E3), B = fmat(Hy, third, E3);
+        const T C = fmat(Hx, third, E3), D = fmat(Hx, mthird, E3);
+        p.ez = E3 - p.ez;
+        p.epx = A - p.epx;
+        p.emx = B - p.emx;
+        p.epy = C - p.epy;
+        p.emy = D - p.emy;
+        p.hxpx = fmat(Hx, third, -p.hxpx);
+        p.hxmx = fmat(Hx, third, -p.hxmx);
+        p.hxz = fmat(Hx, third, -p.hxz);
+        p.hypy = fmat(Hy, third, -p.hypy);
+        p.hymy = fmat(Hy, third, -p.hymy);
+        p.hyz = fmat(Hy, third, -p.hyz);
+    }
 }
 
 // |E_z/3| >= 2^20 or non-finite, tested on the exponent bits (integer ALU only).

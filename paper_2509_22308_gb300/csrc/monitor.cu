@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(BX *BY) k_energy(const StepArgs<T> a, const T 
         pull_site(a, f, x, y, *t_dev, p);
         const MatT<T> m = a.mtab[a.mat[(size_t)y * a.pitch + x]];
         T E3, Hx, Hy, D;
-        moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
+        moments(p, m, &E3, &Hx, &Hy, &D);
         const double ez = (double)(D * m.inv_eps);
         w = 0.5 * ((double)D * ez + (double)Hx * (double)Hx + (double)Hy * (double)Hy);
     }

@@ -20,6 +20,17 @@ double lattice_wavenumber(int period);
 // (cos w t, sin w t) for t = 0..T-1, w = 2 pi / T.
 std::vector<double2> phase_table(int period);
 
+// Constants of one material in the kernel's type.  3 eps_r is rounded once and
+// c_d = 2 (3 eps_r) - 4 is derived from the rounded value (exact in FP32 and FP64 for
+// eps_r < 2^20), so that (c_d + 4) / c3 = 2 holds in the table: the collision conserves D
+// up to the one rounding of D / c3 instead of scaling it by a fixed rounded constant.
+template <typename T>
+inline MatT<T> material_entry(double eps, bool pec) {
+    if (pec) return MatT<T>{(T)0, (T)0, (T)0, (T)1};
+    const T c3 = (T)(3.0 * eps);
+    return MatT<T>{(T)(1.0 / (3.0 * eps)), (T)2 * c3 - (T)4, (T)(1.0 / eps), c3};
+}
+
 lbm_em_status check_source(const lbm_em_source *s);
 lbm_em_status check_janus(const lbm_em_janus *j);
 void janus_center(const lbm_em_janus *j, int nx, int ny, double *cx, double *cy);

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(BX *BY) k_step(const StepArgs<T> a, const T *_
     const size_t idx = (size_t)y * a.pitch + x;
     const MatT<T> m = a.mtab[a.mat[idx]];
     T E3, Hx, Hy, D;
-    moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
+    moments(p, m, &E3, &Hx, &Hy, &D);
     if (field_runaway(E3)) atomicOr(a.err, 1u);
     if (ACC) {
         if (y >= a.accp.y0 && y <= a.accp.y1) {
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(BX *BY) k_fields(const StepArgs<T> a, const T 
     const size_t idx = (size_t)y * a.pitch + x;
     const MatT<T> m = a.mtab[a.mat[idx]];
     T E3, Hx, Hy, D;
-    moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
+    moments(p, m, &E3, &Hx, &Hy, &D);
     const size_t o = (size_t)y * a.nx + x;
     ez[o] = (double)(D * m.inv_eps);
     hx[o] = (double)Hx;

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(NT) k_step2_f32(const StepArgs<float> a, const
         const size_t idx = (size_t)y * a.pitch + x;
         const MatT<float> m = a.mtab[a.mat[idx]];
         float E3, Hx, Hy, D;
-        moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
+        moments(p, m, &E3, &Hx, &Hy, &D);
         if (field_runaway(E3)) atomicOr(a.err, 1u);
         if (ACC && lx >= 1 && lx <= TW && ly >= 1 && ly <= TH)
             acc_site(a.accp, a.src, idx, y, t, (double)(D * m.inv_eps), (double)Hx, (double)Hy);
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(NT) k_step2_f32(const StepArgs<float> a, const
         const size_t idx = (size_t)y * a.pitch + x;
         const MatT<float> m = a.mtab[a.mat[idx]];
         float E3, Hx, Hy, D;
-        moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
+        moments(p, m, &E3, &Hx, &Hy, &D);
         if (field_runaway(E3)) atomicOr(a.err, 1u);
         if (ACC) acc_site(a.accp, a.src, idx, y, t + 1, (double)(D * m.inv_eps), (double)Hx, (double)Hy);
         collide(p, E3, Hx, Hy);
@@ -131,15 +131,15 @@ __global__ void __launch_bounds__(NT) k_step2_f16(const F16Args a, const long lo
         Pop<float> p;
         pull_f16(a, x, y, t, p);
         float E3, Hx, Hy, D;
-        moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
+        moments(p, m, &E3, &Hx, &Hy, &D);
         if (field_runaway(E3)) atomicOr(a.err, 1u);
-        const float Ez = 3.0f * E3;
         if (ACC && lx >= 1 && lx <= TW && ly >= 1 && ly <= TH)
-            acc_site(a.accp, a.src, idx, y, t, (double)Ez, (double)Hx, (double)Hy);
+            acc_site(a.accp, a.src, idx, y, t, 3.0 * (double)E3, (double)Hx, (double)Hy);
+        const Fld F = stored_fields(E3, Hx, Hy);
         __half g[NPLANES];
-        encode_all(p, Ez, Hx, Hy, a.scale, g);
+        encode_all(p, F, a.scale, g);
         Pop<float> q;
-        rebuild_all(g, Ez, Hx, Hy, a.inv_scale, q);
+        rebuild_all(g, F, a.inv_scale, q);
         put_smem(sm, ly, lx, q);
     }
     __syncthreads();
@@ -152,17 +152,17 @@ __global__ void __launch_bounds__(NT) k_step2_f16(const F16Args a, const long lo
         const size_t idx = (size_t)y * a.pitch + x;
         const MatT<float> m = a.mtab[a.mat[idx]];
         float E3, Hx, Hy, D;
-        moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
+        moments(p, m, &E3, &Hx, &Hy, &D);
         if (field_runaway(E3)) atomicOr(a.err, 1u);
-        const float Ez = 3.0f * E3;
-        if (ACC) acc_site(a.accp, a.src, idx, y, t + 1, (double)Ez, (double)Hx, (double)Hy);
+        if (ACC) acc_site(a.accp, a.src, idx, y, t + 1, 3.0 * (double)E3, (double)Hx, (double)Hy);
+        const Fld F = stored_fields(E3, Hx, Hy);
         __half g[NPLANES];
-        encode_all(p, Ez, Hx, Hy, a.scale, g);
+        encode_all(p, F, a.scale, g);
 #pragma unroll
         for (int q = 0; q < NPLANES; ++q) a.g_out[q * ps + idx] = g[q];
-        a.fe_out[idx] = Ez;
-        a.fhx_out[idx] = Hx;
-        a.fhy_out[idx] = Hy;
+        a.fe_out[idx] = F.e;
+        a.fhx_out[idx] = F.hx;
+        a.fhy_out[idx] = F.hy;
     }
 }
 

@@ -1,8 +1,8 @@
 // FP16-deviation storage form of the fused stream-collide step (arXiv 2509.22308,
 // Sec. III, Eq. LBGK equation), FP32 arithmetic.
 //
-// Stored per site for time t: the fields F = (E_z, H_x, H_y)(t) in FP32 and the 11
-// deviations g_i(t) = f_i(t) - f_i^eq(F(t)) in FP16, multiplied by 2^10.  Because
+// Stored per site for time t: the fields F = (E_z/3, H_x/3, H_y/3)(t) in FP32 and the
+// 11 deviations g_i(t) = f_i(t) - f_i^eq(F(t)) in FP16, multiplied by 2^10.  Because
 // the scheme's post-collision value is f*_i = 2 f_i^eq - f_i = f_i^eq - g_i, the pull
 // for time t + 1 rebuilds f_i(r, t + 1) = f_i^eq(F(s, t)) - g_i(s, t) from the
 // upstream site s = r - c_i; the deviations are small (of the order of the field
@@ -17,19 +17,19 @@ namespace lbmem {
 
 constexpr int BX = 32, BY = 8;
 
-__device__ __forceinline__ void accumulate_site(const F16Args &a, size_t idx, int y, long long t, float Ez,
-                                                float Hx, float Hy) {
+__device__ __forceinline__ void accumulate_site(const F16Args &a, size_t idx, int y, long long t, double Ez,
+                                                double Hx, double Hy) {
     if (y < a.accp.y0 || y > a.accp.y1) return;
     const int s = a.accp.slot[idx];
     if (s < 0) return;
     const double2 c = a.src.cs[(int)(t % (long long)a.src.period)];
     double *q = a.accp.acc + 6 * (size_t)s;
-    q[0] += (double)Ez * c.x;
-    q[1] += (double)Ez * c.y;
-    q[2] += (double)Hx * c.x;
-    q[3] += (double)Hx * c.y;
-    q[4] += (double)Hy * c.x;
-    q[5] += (double)Hy * c.y;
+    q[0] += Ez * c.x;
+    q[1] += Ez * c.y;
+    q[2] += Hx * c.x;
+    q[3] += Hx * c.y;
+    q[4] += Hy * c.x;
+    q[5] += Hy * c.y;
 }
 
 // Two sites (x0, x0 + 1), x0 even, per thread: the x-aligned planes, the fields of the
@@ -78,17 +78,17 @@ __global__ void __launch_bounds__(BX *BY) k_step_f16(const F16Args a, const long
     p0.ez = rebuild(Ec.x, __low2half(v), is);
     p1.ez = rebuild(Ec.y, __high2half(v), is);
     v = h2(P_EPX, r);
-    p0.epx = rebuild(eq6_epx(Ew, Xw, Yw), h1(P_EPX, r, xw), is);
-    p1.epx = rebuild(eq6_epx(Ec.x, Xc.x, Yc.x), __low2half(v), is);
+    p0.epx = rebuild(eq2_epx(Ew, Xw, Yw), h1(P_EPX, r, xw), is);
+    p1.epx = rebuild(eq2_epx(Ec.x, Xc.x, Yc.x), __low2half(v), is);
     v = h2(P_EMX, r);
-    p0.emx = rebuild(eq6_emx(E0e, X0e, Y0e), has1 ? __high2half(v) : __low2half(v), is);
-    p1.emx = rebuild(eq6_emx(Ee, Xe, Ye), h1(P_EMX, r, xe), is);
+    p0.emx = rebuild(eq2_emx(E0e, X0e, Y0e), has1 ? __high2half(v) : __low2half(v), is);
+    p1.emx = rebuild(eq2_emx(Ee, Xe, Ye), h1(P_EMX, r, xe), is);
     v = h2(P_EPY, rm);
-    p0.epy = rebuild(eq6_epy(Es.x, Xs.x, Ys.x), __low2half(v), is);
-    p1.epy = rebuild(eq6_epy(Es.y, Xs.y, Ys.y), __high2half(v), is);
+    p0.epy = rebuild(eq2_epy(Es.x, Xs.x, Ys.x), __low2half(v), is);
+    p1.epy = rebuild(eq2_epy(Es.y, Xs.y, Ys.y), __high2half(v), is);
     v = h2(P_EMY, rp);
-    p0.emy = rebuild(eq6_emy(En.x, Xn.x, Yn.x), __low2half(v), is);
-    p1.emy = rebuild(eq6_emy(En.y, Xn.y, Yn.y), __high2half(v), is);
+    p0.emy = rebuild(eq2_emy(En.x, Xn.x, Yn.x), __low2half(v), is);
+    p1.emy = rebuild(eq2_emy(En.y, Xn.y, Yn.y), __high2half(v), is);
     v = h2(P_HXPX, r);
     p0.hxpx = rebuild(Xw, h1(P_HXPX, r, xw), is);
     p1.hxpx = rebuild(Xc.x, __low2half(v), is);
@@ -110,23 +110,23 @@ __global__ void __launch_bounds__(BX *BY) k_step_f16(const F16Args a, const long
     f16_source(a.src, x0, t, p0);
 
     float E30, Hx0, Hy0, D0, E31, Hx1, Hy1, D1;
-    moments(p0, m0.inv_eps3, m0.c_d, &E30, &Hx0, &Hy0, &D0);
-    moments(p1, m1.inv_eps3, m1.c_d, &E31, &Hx1, &Hy1, &D1);
+    moments(p0, m0, &E30, &Hx0, &Hy0, &D0);
+    moments(p1, m1, &E31, &Hx1, &Hy1, &D1);
     if (field_runaway(E30) || (has1 && field_runaway(E31))) atomicOr(a.err, 1u);
-    const float Ez0 = 3.0f * E30, Ez1 = 3.0f * E31;
     const size_t idx = r + x0;
     if (ACC) {
-        accumulate_site(a, idx, y, t, Ez0, Hx0, Hy0);
-        if (has1) accumulate_site(a, idx + 1, y, t, Ez1, Hx1, Hy1);
+        accumulate_site(a, idx, y, t, 3.0 * (double)E30, Hx0, Hy0);
+        if (has1) accumulate_site(a, idx + 1, y, t, 3.0 * (double)E31, Hx1, Hy1);
     }
+    const Fld F0 = stored_fields(E30, Hx0, Hy0), F1 = stored_fields(E31, Hx1, Hy1);
     __half g0[NPLANES], g1[NPLANES];
-    encode_all(p0, Ez0, Hx0, Hy0, a.scale, g0);
-    encode_all(p1, Ez1, Hx1, Hy1, a.scale, g1);
+    encode_all(p0, F0, a.scale, g0);
+    encode_all(p1, F1, a.scale, g1);
 #pragma unroll
     for (int q = 0; q < NPLANES; ++q) *(__half2 *)(a.g_out + q * ps + idx) = __halves2half2(g0[q], g1[q]);
-    *(float2 *)(a.fe_out + idx) = make_float2(Ez0, Ez1);
-    *(float2 *)(a.fhx_out + idx) = make_float2(Hx0, Hx1);
-    *(float2 *)(a.fhy_out + idx) = make_float2(Hy0, Hy1);
+    *(float2 *)(a.fe_out + idx) = make_float2(F0.e, F1.e);
+    *(float2 *)(a.fhx_out + idx) = make_float2(F0.hx, F1.hx);
+    *(float2 *)(a.fhy_out + idx) = make_float2(F0.hy, F1.hy);
 }
 
 __global__ void __launch_bounds__(BX *BY) k_fields_f16(const F16Args a, const long long *__restrict__ t_dev,
@@ -139,9 +139,9 @@ __global__ void __launch_bounds__(BX *BY) k_fields_f16(const F16Args a, const lo
     Pop<float> p;
     pull_f16(a, x, y, *t_dev, p);
     float E3, Hx, Hy, D;
-    moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
+    moments(p, m, &E3, &Hx, &Hy, &D);
     const size_t o = (size_t)y * a.nx + x;
-    ez[o] = (double)(3.0f * E3);
+    ez[o] = 3.0 * (double)E3;
     hx[o] = (double)Hx;
     hy[o] = (double)Hy;
 }
@@ -158,8 +158,8 @@ __global__ void __launch_bounds__(BX *BY) k_energy_f16(const F16Args a, const lo
         Pop<float> p;
         pull_f16(a, x, y, *t_dev, p);
         float E3, Hx, Hy, D;
-        moments(p, m.inv_eps3, m.c_d, &E3, &Hx, &Hy, &D);
-        w = 0.5 * ((double)D * (double)(3.0f * E3) + (double)Hx * (double)Hx + (double)Hy * (double)Hy);
+        moments(p, m, &E3, &Hx, &Hy, &D);
+        w = 0.5 * ((double)D * (3.0 * (double)E3) + (double)Hx * (double)Hx + (double)Hy * (double)Hy);
     }
     for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
     const int tid = threadIdx.y * BX + threadIdx.x;

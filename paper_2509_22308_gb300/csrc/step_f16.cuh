@@ -2,7 +2,10 @@
 // shared by every kernel of this form (see step_f16.cu).
 //
 // A population is stored as its deviation from the equilibrium of its own site,
-// g_i = f_i - f_i^eq(F), in FP16 scaled by 2^10, next to the FP32 fields F.  Every
+// g_i = f_i - f_i^eq(F), in FP16 scaled by 2^10, next to the site's fields in FP32,
+// kept as F = (E_z/3, H_x/3, H_y/3): every 2 f^eq is then a sum or difference of two
+// stored values and f^eq itself an exact halving, so no rounded constant (1/3, 1/6)
+// enters the state (see quot() in common.cuh for why a fixed bias must not).  Every
 // kernel rebuilds and re-encodes a population with the explicitly rounded helpers
 // below, so the one-step, two-step and field kernels of this form agree bit for bit.
 #pragma once
@@ -38,28 +41,34 @@ inline size_t f16_half_bytes(size_t pstride) { return ((size_t)NPLANES * pstride
 inline size_t f16_plane_bytes(size_t pstride) { return (pstride * 4 + 255) / 256 * 256; }
 inline size_t f16_buffer_bytes(size_t pstride) { return f16_half_bytes(pstride) + 3 * f16_plane_bytes(pstride); }
 
-// 6 f_i^eq of each stored population as a function of the fields of its site
-// (Eq. equilibrium distribution functions): e_z: z E, +x E - H_y, -x E + H_y, +y E + H_x,
-// -y E - H_x;  h_x: +-x, z H_x;  h_y: +-y, z H_y.
-__device__ __forceinline__ float eq6_epx(float e, float hx, float hy) { return __fsub_rn(e, hy); }
-__device__ __forceinline__ float eq6_emx(float e, float hx, float hy) { return __fadd_rn(e, hy); }
-__device__ __forceinline__ float eq6_epy(float e, float hx, float hy) { return __fadd_rn(e, hx); }
-__device__ __forceinline__ float eq6_emy(float e, float hx, float hy) { return __fsub_rn(e, hx); }
+// 2 f_i^eq of each stored population from the stored fields of its site
+// (Eq. equilibrium distribution functions): e_z: z E/3, +x E/3 - H_y/3, -x E/3 + H_y/3,
+// +y E/3 + H_x/3, -y E/3 - H_x/3;  h_x: +-x, z H_x/3;  h_y: +-y, z H_y/3.
+__device__ __forceinline__ float eq2_epx(float e, float hx, float hy) { return __fsub_rn(e, hy); }
+__device__ __forceinline__ float eq2_emx(float e, float hx, float hy) { return __fadd_rn(e, hy); }
+__device__ __forceinline__ float eq2_epy(float e, float hx, float hy) { return __fadd_rn(e, hx); }
+__device__ __forceinline__ float eq2_emy(float e, float hx, float hy) { return __fsub_rn(e, hx); }
 
-// f = eq6 / 6 - g / 2^10
-__device__ __forceinline__ float rebuild(float eq6, __half g, float inv_scale) {
-    return __fmaf_rn(-__half2float(g), inv_scale, __fmul_rn(eq6, 1.0f / 6.0f));
+// f = eq2 / 2 - g / 2^10
+__device__ __forceinline__ float rebuild(float eq2, __half g, float inv_scale) {
+    return __fmaf_rn(-__half2float(g), inv_scale, __fmul_rn(eq2, 0.5f));
 }
-// g = (f - eq6 / 6) * 2^10, rounded to FP16
-__device__ __forceinline__ __half encode(float f, float eq6, float scale) {
-    return __float2half_rn(__fmul_rn(__fsub_rn(f, __fmul_rn(eq6, 1.0f / 6.0f)), scale));
+// g = (f - eq2 / 2) * 2^10, rounded to FP16
+__device__ __forceinline__ __half encode(float f, float eq2, float scale) {
+    return __float2half_rn(__fmul_rn(__fsub_rn(f, __fmul_rn(eq2, 0.5f)), scale));
 }
 
+// Stored fields of a site: E_z/3, H_x/3, H_y/3.
 struct Fld {
     float e, hx, hy;
 };
 
 __device__ __forceinline__ Fld load_fld(const F16Args &a, size_t i) { return Fld{a.fe[i], a.fhx[i], a.fhy[i]}; }
+
+// The stored fields from the moments (E3 = E_z/3 already; H/3 through quot()).
+__device__ __forceinline__ Fld stored_fields(float E3, float Hx, float Hy) {
+    return Fld{E3, quot(Hx, 3.0f, 1.0f / 3.0f), quot(Hy, 3.0f, 1.0f / 3.0f)};
+}
 
 // Source at x = 0 (t >= 1): adds to e_+x (and so, through the tie h_+x,y = -e_+x,z, to h_+x,y).
 __device__ __forceinline__ void f16_source(const SourceParams &src, int x, long long t, Pop<float> &p) {
@@ -89,10 +98,10 @@ __device__ __forceinline__ void pull_f16(const F16Args &a, int x, int y, long lo
     const Fld so = load_fld(a, rm + x), no = load_fld(a, rp + x);
     const __half *g = a.g;
     p.ez = rebuild(c.e, g[P_EZ * ps + r + x], is);
-    p.epx = rebuild(eq6_epx(w.e, w.hx, w.hy), g[P_EPX * ps + r + xm], is);
-    p.emx = rebuild(eq6_emx(e.e, e.hx, e.hy), g[P_EMX * ps + r + xp], is);
-    p.epy = rebuild(eq6_epy(so.e, so.hx, so.hy), g[P_EPY * ps + rm + x], is);
-    p.emy = rebuild(eq6_emy(no.e, no.hx, no.hy), g[P_EMY * ps + rp + x], is);
+    p.epx = rebuild(eq2_epx(w.e, w.hx, w.hy), g[P_EPX * ps + r + xm], is);
+    p.emx = rebuild(eq2_emx(e.e, e.hx, e.hy), g[P_EMX * ps + r + xp], is);
+    p.epy = rebuild(eq2_epy(so.e, so.hx, so.hy), g[P_EPY * ps + rm + x], is);
+    p.emy = rebuild(eq2_emy(no.e, no.hx, no.hy), g[P_EMY * ps + rp + x], is);
     p.hxpx = rebuild(w.hx, g[P_HXPX * ps + r + xm], is);
     p.hxmx = rebuild(e.hx, g[P_HXMX * ps + r + xp], is);
     p.hxz = rebuild(c.hx, g[P_HXZ * ps + r + x], is);
@@ -102,37 +111,36 @@ __device__ __forceinline__ void pull_f16(const F16Args &a, int x, int y, long lo
     f16_source(a.src, x, t, p);
 }
 
-// The 11 encoded deviations of a site whose pulled populations are p and fields F.
-__device__ __forceinline__ void encode_all(const Pop<float> &p, float Ez, float Hx, float Hy, float sc,
-                                           __half g[NPLANES]) {
-    g[P_EZ] = encode(p.ez, Ez, sc);
-    g[P_EPX] = encode(p.epx, eq6_epx(Ez, Hx, Hy), sc);
-    g[P_EMX] = encode(p.emx, eq6_emx(Ez, Hx, Hy), sc);
-    g[P_EPY] = encode(p.epy, eq6_epy(Ez, Hx, Hy), sc);
-    g[P_EMY] = encode(p.emy, eq6_emy(Ez, Hx, Hy), sc);
-    g[P_HXPX] = encode(p.hxpx, Hx, sc);
-    g[P_HXMX] = encode(p.hxmx, Hx, sc);
-    g[P_HXZ] = encode(p.hxz, Hx, sc);
-    g[P_HYPY] = encode(p.hypy, Hy, sc);
-    g[P_HYMY] = encode(p.hymy, Hy, sc);
-    g[P_HYZ] = encode(p.hyz, Hy, sc);
+// The 11 encoded deviations of a site whose pulled populations are p and stored fields F.
+__device__ __forceinline__ void encode_all(const Pop<float> &p, const Fld &F, float sc, __half g[NPLANES]) {
+    g[P_EZ] = encode(p.ez, F.e, sc);
+    g[P_EPX] = encode(p.epx, eq2_epx(F.e, F.hx, F.hy), sc);
+    g[P_EMX] = encode(p.emx, eq2_emx(F.e, F.hx, F.hy), sc);
+    g[P_EPY] = encode(p.epy, eq2_epy(F.e, F.hx, F.hy), sc);
+    g[P_EMY] = encode(p.emy, eq2_emy(F.e, F.hx, F.hy), sc);
+    g[P_HXPX] = encode(p.hxpx, F.hx, sc);
+    g[P_HXMX] = encode(p.hxmx, F.hx, sc);
+    g[P_HXZ] = encode(p.hxz, F.hx, sc);
+    g[P_HYPY] = encode(p.hypy, F.hy, sc);
+    g[P_HYMY] = encode(p.hymy, F.hy, sc);
+    g[P_HYZ] = encode(p.hyz, F.hy, sc);
 }
 
-// What the next step's pull rebuilds from this site (its fields and encoded deviations):
-// the post-collision populations exactly as storage followed by a pull would give them.
-__device__ __forceinline__ void rebuild_all(const __half g[NPLANES], float Ez, float Hx, float Hy, float is,
-                                            Pop<float> &q) {
-    q.ez = rebuild(Ez, g[P_EZ], is);
-    q.epx = rebuild(eq6_epx(Ez, Hx, Hy), g[P_EPX], is);
-    q.emx = rebuild(eq6_emx(Ez, Hx, Hy), g[P_EMX], is);
-    q.epy = rebuild(eq6_epy(Ez, Hx, Hy), g[P_EPY], is);
-    q.emy = rebuild(eq6_emy(Ez, Hx, Hy), g[P_EMY], is);
-    q.hxpx = rebuild(Hx, g[P_HXPX], is);
-    q.hxmx = rebuild(Hx, g[P_HXMX], is);
-    q.hxz = rebuild(Hx, g[P_HXZ], is);
-    q.hypy = rebuild(Hy, g[P_HYPY], is);
-    q.hymy = rebuild(Hy, g[P_HYMY], is);
-    q.hyz = rebuild(Hy, g[P_HYZ], is);
+// What the next step's pull rebuilds from this site (its stored fields and encoded
+// deviations): the post-collision populations exactly as storage followed by a pull
+// would give them.
+__device__ __forceinline__ void rebuild_all(const __half g[NPLANES], const Fld &F, float is, Pop<float> &q) {
+    q.ez = rebuild(F.e, g[P_EZ], is);
+    q.epx = rebuild(eq2_epx(F.e, F.hx, F.hy), g[P_EPX], is);
+    q.emx = rebuild(eq2_emx(F.e, F.hx, F.hy), g[P_EMX], is);
+    q.epy = rebuild(eq2_epy(F.e, F.hx, F.hy), g[P_EPY], is);
+    q.emy = rebuild(eq2_emy(F.e, F.hx, F.hy), g[P_EMY], is);
+    q.hxpx = rebuild(F.hx, g[P_HXPX], is);
+    q.hxmx = rebuild(F.hx, g[P_HXMX], is);
+    q.hxz = rebuild(F.hx, g[P_HXZ], is);
+    q.hypy = rebuild(F.hy, g[P_HYPY], is);
+    q.hymy = rebuild(F.hy, g[P_HYMY], is);
+    q.hyz = rebuild(F.hy, g[P_HYZ], is);
 }
 
 cudaError_t launch_step_f16(const F16Args &a, const long long *t_in, long long *t_out, bool accumulate,

@@ -43,15 +43,31 @@ def md_janus_512(seed: int = 1):
     return out
 
 
+def transit_periods(nx, ny, period, R):
+    """Periods the incident front needs from the source column x = 0 to the far side of
+    the contour (x = centre + R) at the vacuum speed of 1/3 cell per step, rounded up."""
+    cx = (nx - 1) / 2.0
+    return int(math.ceil(3.0 * (cx + R) / period))
+
+
+def settled(inst, periods_after_transit: int = 20):
+    """Copy of an instance whose run covers the transit of the incident front past the
+    contour and then ``periods_after_transit`` more periods (the last one accumulated)."""
+    out = dict(inst)
+    out["periods"] = transit_periods(inst["nx"], inst["ny"], inst["period"], inst["R"]) + periods_after_transit
+    return out
+
+
 def dielectric_janus_2048():
     """Dielectric Janus cylinders, 2048 x 2048, a = 128, eps1 = 2, eps2 in {2, 4.5, 7, 9.5, 12},
     size parameter k0 a in {5, 10, 20} (wavelength rounded so that T = 3 lambda is an
-    integer), phi0 = 30 deg, 20 periods, contour radius 1.6 a."""
+    integer), phi0 = 30 deg, contour radius 1.6 a; 20 periods after the incident front has
+    crossed the contour (the front needs up to 31 periods to get there at k0 a = 20)."""
     out = []
     for k0a in (5.0, 10.0, 20.0):
         lam = round(2.0 * math.pi * 128.0 / k0a)
         for e2 in (2.0, 4.5, 7.0, 9.5, 12.0):
-            out.append(_inst(2048, 128, math.radians(30.0), 2.0, e2, False, 3 * lam, 20, 1.6 * 128))
+            out.append(settled(_inst(2048, 128, math.radians(30.0), 2.0, e2, False, 3 * lam, 20, 1.6 * 128)))
     return out
 
 
@@ -72,7 +88,9 @@ def design_map_256(seed: int = 4, n: int = 256):
 def md_janus_8192(seed: int = 5):
     """Large single domain: 8192 x 8192 metallo-dielectric Janus, a = 512, wavelength 80
     (k0 a ~ 40, T = 240), eps ~ U[2, 12] and theta ~ U[0, 180) deg (seeded), 50 periods,
-    contour radius 1.5 a."""
+    contour radius 1.5 a.  After 50 periods the incident front has only just reached the
+    cylinder (it crosses the contour after 61 periods); ``settled`` gives the run whose
+    forces are those of the steady state."""
     rng = np.random.default_rng(seed)
     e1 = float(rng.uniform(2.0, 12.0))
     th = float(rng.uniform(0.0, 180.0))

@@ -32,6 +32,7 @@ def test_dielectric_janus_2048_forms(k0a):
     within 1e-3 of drag scale."""
     insts = [i for i in W.dielectric_janus_2048() if abs(2 * np.pi * 128 / (i["period"] / 3) - k0a) < 0.2 * k0a]
     assert len(insts) == 5
+    assert all(i["periods"] * i["period"] > 3 * (1023.5 + i["R"]) + 19 * i["period"] for i in insts)
     for inst in insts[1::2]:                      # eps2 = 4.5 and 9.5
         ref = L.run_instance(inst, "f64")
         d32, lt32 = _errors(L.run_instance(inst, "f32"), ref)
@@ -41,9 +42,11 @@ def test_dielectric_janus_2048_forms(k0a):
 
 
 def test_md_janus_8192_forms():
-    """8192^2 metallo-dielectric Janus (a = 512, T = 240, 50 periods): FP32 and
+    """8192^2 metallo-dielectric Janus (a = 512, T = 240), run until 20 periods after the
+    incident front has crossed the contour (81 periods, 19 440 steps): FP32 and
     FP16-deviation storage against the FP64 run."""
-    inst = W.md_janus_8192()[0]
+    inst = W.settled(W.md_janus_8192()[0])
+    assert inst["periods"] == 81
     ref = L.run_instance(inst, "f64")
     d32, lt32 = _errors(L.run_instance(inst, "f32"), ref)
     d16, lt16 = _errors(L.run_instance(inst, "f16dev"), ref)
