@@ -48,17 +48,23 @@ typedef enum {
 /* Storage of the distributions.  Arithmetic is FP64 for F64, FP32 otherwise;
  * Fourier accumulators and the stress-tensor integral are FP64 in every form. */
 typedef enum {
-    LBM_EM_F64 = 0,      /* 16 FP64 populations per site                                */
-    LBM_EM_F32 = 1,      /* 16 FP32 populations per site                                */
-    LBM_EM_F16DEV = 2    /* FP32 fields (E_z, H_x, H_y) + 16 FP16 scaled deviations
-                            f - f^eq per site                                           */
+    LBM_EM_F64 = 0,      /* 11 FP64 populations per site (the independent part of the
+                            TM^z state; the other five follow from exact invariants)    */
+    LBM_EM_F32 = 1,      /* 11 FP32 populations per site                                */
+    LBM_EM_F16DEV = 2    /* FP32 fields (E_z/3, H_x/3, H_y/3) + 11 FP16 scaled
+                            deviations f - f^eq per site                                */
 } lbm_em_precision;
 
-/* Left-edge plane-wave source (Sec. III: "introduced through the left boundary"). */
+/* Left-edge plane-wave source (Sec. III: the wave enters through the left boundary, the
+ * other boundaries let outgoing waves leave).  HARD is the default: energy-stable over
+ * hundreds of periods.  OPEN keeps a zero-gradient copy of the scattered part on the left
+ * edge as well; with four copy edges a static field can build up around a PEC (a DC
+ * line current) and the domain energy grows slowly, without effect on the phasors. */
 typedef enum {
-    LBM_EM_SRC_OPEN = 0,  /* incoming +x populations at x = 0: zero-gradient copy of the
+    LBM_EM_SRC_HARD = 0,  /* incoming +x populations at x = 0: the exact discrete incident
+                             plane wave only (outgoing waves leave freely)               */
+    LBM_EM_SRC_OPEN = 1,  /* incoming +x populations at x = 0: zero-gradient copy of the
                              scattered part + the exact discrete incident plane wave     */
-    LBM_EM_SRC_HARD = 1,  /* incoming +x populations at x = 0: incident wave only        */
     LBM_EM_SRC_NONE = 2   /* no source (all edges open)                                  */
 } lbm_em_source_kind;
 
@@ -259,7 +265,7 @@ typedef struct {
     int32_t tile_w, tile_h;  /* tile shape (tile_w 32/64/128/256, tile_h <= 16); 0: autotuned */
     int32_t ctas_per_sm;     /* persistent CTAs per SM; 0: autotuned                       */
     int32_t min_periods;     /* convergence exits: fewest periods an instance runs         */
-    int32_t reserved;        /* 0                                                          */
+    int32_t source_kind;     /* lbm_em_source_kind of every instance (0: HARD)              */
     double conv_tol;         /* 0: every instance runs its `periods`; > 0: an instance stops
                                 early once its domain energy, sampled at each period end,
                                 changes by <= conv_tol * W twice in a row (Sec. III), then

@@ -13,7 +13,11 @@ towards the polar angle phi0 + pi; region II is the half 0 < phi < pi.
 Functions
   homogeneous_BD   Bessel series of a homogeneous dielectric or PEC cylinder:
                    continuity of E_z and H_phi at r = a (the textbook special
-                   case of Sec. II; the paper uses it as its PEC reference).
+                   case of Sec. II; the paper uses it as its PEC reference), and
+                   the TE^z counterpart (series of H_z).  By the duality
+                   E <-> H (eps0 = mu0 = 1 outside) every function below applies to
+                   TE coefficients unchanged, with (E_z, H_r, H_phi) read as
+                   (H_z, E_r, E_phi).
   md_janus_BD      metallo-dielectric Janus cylinder, solved the way Sec. IV.A
                    does: the integral equation (Eq. integral equation) on N
                    nodes with spacing pi/(N-1), then Eq. (constants_Bm_Dm).
@@ -40,8 +44,15 @@ def mode_count(x: float, extra: int = 10) -> int:
 
 
 def homogeneous_BD(k0: float, a: float, eps: float, phi0: float, M: int | None = None,
-                   pec: bool = False):
-    """B_m, D_m (m = 0..M) of Eq. (scattered field) for a homogeneous cylinder."""
+                   pec: bool = False, te: bool = False):
+    """B_m, D_m (m = 0..M) of Eq. (scattered field) for a homogeneous cylinder.
+
+    TM (default): the series is E_z; E_z and H_phi ~ dE_z/dr are continuous at r = a
+    (E_z = 0 on a PEC).  TE (``te``, the polarization the paper leaves for future work):
+    the same series describes H_z with unit incident amplitude; H_z and
+    E_phi ~ (1/eps) dH_z/dr are continuous (dH_z/dr = 0 on a PEC), so the dielectric
+    coefficient is the TM one with the inner wavenumber k replaced by k / eps in the
+    derivative terms."""
     k = k0 * np.sqrt(eps) if not pec else k0
     if M is None:
         M = mode_count(max(k0 * a, k * a))
@@ -50,11 +61,12 @@ def homogeneous_BD(k0: float, a: float, eps: float, phi0: float, M: int | None =
     J0, J0p = sp.jv(m, x0), sp.jvp(m, x0)
     H0, H0p = sp.hankel1(m, x0), sp.h1vp(m, x0)
     if pec:
-        c = -J0 / H0
+        c = -J0p / H0p if te else -J0 / H0
     else:
         x1 = k * a
         J1, J1p = sp.jv(m, x1), sp.jvp(m, x1)
-        c = (k * J0 * J1p - k0 * J0p * J1) / (k0 * H0p * J1 - k * H0 * J1p)
+        kd = k / eps if te else k      # factor of the inner radial derivative
+        c = (kd * J0 * J1p - k0 * J0p * J1) / (k0 * H0p * J1 - kd * H0 * J1p)
     pre = alpha(m) * (-1j) ** m * c
     return pre * np.cos(m * phi0), pre * np.sin(m * phi0)
 

@@ -26,6 +26,7 @@ _lib = None
 
 SITE_DOUBLES = 42
 SRC_OPEN, SRC_HARD, SRC_NONE = 0, 1, 2
+POLARIZATIONS = {"tm": 0, "te": 1}
 
 
 class OracleCfg(ctypes.Structure):
@@ -37,6 +38,7 @@ class OracleCfg(ctypes.Structure):
         ("ramp_steps", ctypes.c_int),
         ("source_kind", ctypes.c_int),
         ("nthreads", ctypes.c_int),
+        ("polarization", ctypes.c_int),
     ]
 
 
@@ -97,18 +99,21 @@ class Simulation:
     ``eps`` is the per-site relative permittivity [ny, nx]; ``pec`` a per-site
     0/1 mask of perfect-electric-conductor cells.  ``f`` holds the pre-collision
     populations at time ``t`` as [ny, nx, 14, 3] (e_0..e_6, h_0..h_6).
+    ``polarization`` "tm" (E_z, H_x, H_y; the paper's case) or "te" (H_z, E_x, E_y):
+    the field triple the source drives, ``fields`` returns and ``phasors`` accumulates.
     """
 
     def __init__(self, eps, pec=None, period=120, E0=1.0, ramp_steps=0,
-                 source_kind=SRC_OPEN, nthreads=None):
+                 source_kind=SRC_HARD, nthreads=None, polarization="tm"):
         eps = np.ascontiguousarray(eps, dtype=np.float64)
         self.ny, self.nx = eps.shape
         self.eps = eps
         self.pec = None if pec is None else np.ascontiguousarray(pec, dtype=np.uint8)
         if nthreads is None:
             nthreads = int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
+        self.polarization = polarization
         self.cfg = OracleCfg(self.nx, self.ny, int(period), float(E0), int(ramp_steps),
-                             int(source_kind), int(nthreads))
+                             int(source_kind), int(nthreads), POLARIZATIONS[polarization])
         self.period = int(period)
         self.f = np.zeros((self.ny, self.nx, 14, 3))
         self._post = np.zeros_like(self.f)
@@ -133,7 +138,8 @@ class Simulation:
         self.acc_steps = 0
 
     def fields(self):
-        """(E_z, H_x, H_y) of every site at time t, each [ny, nx]."""
+        """The field triple of every site at time t, each [ny, nx]: (E_z, H_x, H_y) for
+        TM, (H_z, E_x, E_y) for TE."""
         ez = np.empty((self.ny, self.nx))
         hx = np.empty_like(ez)
         hy = np.empty_like(ez)

@@ -26,6 +26,10 @@
  *     (dispersion relation w = (3 - z) / (z (3 z - 1)), z = e^{-i omega}); kind
  *     OPEN adds it on top of the zero-gradient copy of the scattered part, kind
  *     HARD replaces the incoming populations by the incident ones.
+ *   - polarization: TM^z (E_z, H_x, H_y), the paper's case, or TE^z (H_z, E_x,
+ *     E_y), which the paper leaves for future work.  The scheme is the same; only
+ *     the incident wave (E_y = H_z = E0 sin(omega t - k x) instead of
+ *     E_z = -H_y = E0 sin(omega t - k x)) and the reported field triple differ.
  */
 #include <complex.h>
 #include <math.h>
@@ -48,6 +52,7 @@ static const int CV[NVEL][3] = {
     {0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
 
 enum { SRC_OPEN = 0, SRC_HARD = 1, SRC_NONE = 2 };
+enum { POL_TM = 0, POL_TE = 1 };
 
 typedef struct {
     int nx, ny;        /* lattice size; site (x, y) is at index y * nx + x      */
@@ -56,6 +61,7 @@ typedef struct {
     int ramp_steps;    /* sin^2 ramp of the source over this many steps (0: none) */
     int source_kind;   /* SRC_OPEN / SRC_HARD / SRC_NONE                       */
     int nthreads;      /* OpenMP threads (<= 0: 1)                             */
+    int polarization;  /* POL_TM / POL_TE                                      */
 } oracle_cfg;
 
 static void cross3(const double a[3], const double b[3], double o[3]) {
@@ -105,7 +111,10 @@ void oracle_site_fields(const double *site, double eps_r, int pec, double E[3], 
 /* Incident discrete plane wave: E_z(x, t) = Re[Ehat w^x z^t] with
  * Ehat = i E0, so E_z(x, t) = E0 sin(omega t - k x); the +x population of the
  * e_z component carries Re[P w^x z^t] with P = 2 Ehat / (3 (w z + 1)), the
- * y component of h_{+x} carries the negative of it.                          */
+ * y component of h_{+x} carries the negative of it.  TE: the same wave in
+ * E_y = H_z, carried by the y component of e_{+x} and the z component of h_{+x}
+ * (the equilibria of a wave along x only mix the populations of one transverse
+ * component pair, so the one-dimensional dynamics is the same).                */
 static void incident_plus_x(const oracle_cfg *cfg, long t, double *p0, double *p1) {
     const double omega = 2.0 * M_PI / (double)cfg->period;
     double complex z = cexp(-I * omega);
@@ -122,24 +131,39 @@ static void incident_plus_x(const oracle_cfg *cfg, long t, double *p0, double *p
     *p1 = ramp * creal(P * w * zt);
 }
 
-/* Field values E_z, H_x, H_y of every site at the current time. */
+/* The three field components a polarization has: TM (E_z, H_x, H_y), TE (H_z, E_x, E_y). */
+static void field_triple(int polarization, const double E[3], const double H[3], double out[3]) {
+    if (polarization == POL_TE) {
+        out[0] = H[2];
+        out[1] = E[0];
+        out[2] = E[1];
+    } else {
+        out[0] = E[2];
+        out[1] = H[0];
+        out[2] = H[1];
+    }
+}
+
+/* The field triple of every site at the current time (TM: E_z, H_x, H_y;
+ * TE: H_z, E_x, E_y). */
 void oracle_fields(const oracle_cfg *cfg, const double *eps, const unsigned char *pec,
                    const double *f, double *ez, double *hx, double *hy) {
     const size_t n = (size_t)cfg->nx * (size_t)cfg->ny;
     for (size_t s = 0; s < n; ++s) {
-        double E[3], H[3];
+        double E[3], H[3], v[3];
         oracle_site_fields(f + s * SITE_DOUBLES, eps[s], pec ? pec[s] : 0, E, H);
-        if (ez) ez[s] = E[2];
-        if (hx) hx[s] = H[0];
-        if (hy) hy[s] = H[1];
+        field_triple(cfg->polarization, E, H, v);
+        if (ez) ez[s] = v[0];
+        if (hx) hx[s] = v[1];
+        if (hy) hy[s] = v[2];
     }
 }
 
 /*
  * Advance the state f (pre-collision populations at time t0, nx*ny*42 doubles)
  * by nsteps steps.  fpost is caller scratch of the same size.  If acc is not
- * NULL, every step adds (E_z, H_x, H_y)(t) * (cos w t, sin w t) of every site
- * into acc[site*6 + {0..5}] = {Re Ez, Im Ez, Re Hx, Im Hx, Re Hy, Im Hy}.
+ * NULL, every step adds the field triple (TM: E_z, H_x, H_y; TE: H_z, E_x, E_y)
+ * times (cos w t, sin w t) of every site into acc[site*6 + {0..5}].
  * Returns 0, or -1 on invalid arguments.
  */
 int oracle_advance(const oracle_cfg *cfg, const double *eps, const unsigned char *pec,
@@ -149,6 +173,7 @@ int oracle_advance(const oracle_cfg *cfg, const double *eps, const unsigned char
     const int nx = cfg->nx, ny = cfg->ny;
     const int nth = cfg->nthreads > 0 ? cfg->nthreads : 1;
     const double omega = 2.0 * M_PI / (double)cfg->period;
+    const int te = cfg->polarization == POL_TE;
     (void)nth;
 
     for (long step = 0; step < nsteps; ++step) {
@@ -167,10 +192,11 @@ int oracle_advance(const oracle_cfg *cfg, const double *eps, const unsigned char
                 double E[3], H[3], eeq[NVEL * 3], heq[NVEL * 3];
                 oracle_site_fields(site, eps[s], is_pec, E, H);
                 if (acc) {
-                    double *a = acc + s * 6;
-                    a[0] += E[2] * cw; a[1] += E[2] * sw;
-                    a[2] += H[0] * cw; a[3] += H[0] * sw;
-                    a[4] += H[1] * cw; a[5] += H[1] * sw;
+                    double *a = acc + s * 6, v[3];
+                    field_triple(cfg->polarization, E, H, v);
+                    a[0] += v[0] * cw; a[1] += v[0] * sw;
+                    a[2] += v[1] * cw; a[3] += v[1] * sw;
+                    a[4] += v[2] * cw; a[5] += v[2] * sw;
                 }
                 oracle_equilibria(eps[s], 1.0, E, H, eeq, heq);
                 for (int j = 0; j < NVEL * 3; ++j) {
@@ -199,17 +225,20 @@ int oracle_advance(const oracle_cfg *cfg, const double *eps, const unsigned char
                         dst[3 * (NVEL + i) + k] =
                             fpost[src * SITE_DOUBLES + 3 * (NVEL + i) + k];
                     }
+                    /* incident +x pair: TM e_+x,z = P, h_+x,y = -P; TE e_+x,y = P, h_+x,z = P */
+                    const int ek = te ? 1 : 2, hk = te ? 2 : 1;
+                    const double hs = te ? 1.0 : -1.0;
                     if (x == 0 && i == 1 && cfg->source_kind == SRC_OPEN) {
                         /* scattered part extrapolated, incident part exact */
-                        dst[3 * 1 + 2] += p0 - p1;
-                        dst[3 * (NVEL + 1) + 1] -= p0 - p1;
+                        dst[3 * 1 + ek] += p0 - p1;
+                        dst[3 * (NVEL + 1) + hk] += hs * (p0 - p1);
                     } else if (x == 0 && i == 1 && cfg->source_kind == SRC_HARD) {
                         for (int k = 0; k < 3; ++k) {
                             dst[3 * 1 + k] = 0.0;
                             dst[3 * (NVEL + 1) + k] = 0.0;
                         }
-                        dst[3 * 1 + 2] = p0;
-                        dst[3 * (NVEL + 1) + 1] = -p0;
+                        dst[3 * 1 + ek] = p0;
+                        dst[3 * (NVEL + 1) + hk] = hs * p0;
                     }
                 }
             }

@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
     const long long t = *t_in;
     if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + 1;
     __shared__ MatT<T> smat[3];
+    __shared__ double ssrc[2];  // source values of the tile's instance at time t (column-0 tiles)
     const int tsz = b.tile_w * b.tile_h;
     for (int tile = blockIdx.x; tile < b.n_tiles; tile += gridDim.x) {
         const Tile tl = b.tiles[tile];
@@ -77,6 +78,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
         if (threadIdx.x < 3)
             smat[threadIdx.x] = MatT<T>{(T)d.mtab[threadIdx.x][0], (T)d.mtab[threadIdx.x][1],
                                         (T)d.mtab[threadIdx.x][2], (T)d.mtab[threadIdx.x][3]};
+        // once per tile, not per site (see pull_site)
+        const bool src = tl.x0 == 0 && t >= 1 && d.src.kind != SRC_NONE;
+        if (threadIdx.x == 32 && src) source_values(d.src, t, &ssrc[0], &ssrc[1]);
         __syncthreads();
         StepArgs<T> a;
         a.nx = d.nx;
@@ -91,7 +95,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
             const int x = tl.x0 + (k & (b.tile_w - 1)), y = tl.y0 + (k >> b.log2_tile_w);
             if (x >= d.nx || y >= d.ny) continue;
             Pop<T> p;
-            pull_site(a, fin, x, y, t, p);
+            pull_planes(a, fin, x, y, p);
+            if (x == 0 && src) inject_source(d.src.kind, ssrc[0], ssrc[1], p);
             const size_t idx = (size_t)y * d.pitch + x;
             const MatT<T> m = smat[mat[idx]];
             T E3, Hx, Hy, D;
@@ -491,7 +496,7 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
         accs += ch[i].n_slots;
         d.y0 = ch[i].y0;
         d.y1 = ch[i].y1;
-        d.src.kind = SRC_OPEN;
+        d.src.kind = o->source_kind;
         d.src.period = s.period_steps;
         d.src.ramp = s.ramp_steps;
         incident_constants(s.period_steps, s.E0, &d.src.pr, &d.src.pi, &d.src.qr, &d.src.qi);

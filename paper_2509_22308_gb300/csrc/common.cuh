@@ -33,7 +33,7 @@ enum Plane {
     NPLANES
 };
 
-enum SourceKind { SRC_OPEN = 0, SRC_HARD = 1, SRC_NONE = 2 };
+enum SourceKind { SRC_HARD = 0, SRC_OPEN = 1, SRC_NONE = 2 };  // values of lbm_em_source_kind
 
 // Per-material constants in the kernel's arithmetic type:
 // inv_eps3 = 1/(3 eps_r) (0 for PEC: E := 0), c_d = 6 eps_r - 4 (the weight of the z pair
@@ -96,13 +96,26 @@ __device__ __forceinline__ void source_values(const SourceParams &s, long long t
     *inc = ramp * p0;
 }
 
-// f_i(r, t) = f*_i(r - c_i, t - 1); an upstream site outside the lattice is replaced
-// by the site itself (open edge: zero-gradient copy along the population's own
-// direction); at x = 0 the +x populations also receive the source (t >= 1), which
-// adds to e_+x,z and (through h_+x,y = -e_+x,z) subtracts from h_+x,y.
+// Adds the left-edge source of time t to the pulled populations of a site at x = 0, from
+// the values source_values() gives for t: OPEN adds g_open to e_+x,z (and so, through
+// h_+x,y = -e_+x,z, subtracts it from h_+x,y); HARD replaces the incoming pair by the
+// incident one.
 template <typename T>
-__device__ __forceinline__ void pull_site(const StepArgs<T> &a, const T *__restrict__ f, int x,
-                                          int y, long long t, Pop<T> &p) {
+__device__ __forceinline__ void inject_source(int kind, double g_open, double inc, Pop<T> &p) {
+    if (kind == SRC_OPEN) {
+        p.epx += (T)g_open;
+    } else {
+        p.epx = (T)inc;
+        p.hxpx = (T)0;
+    }
+}
+
+// f_i(r, t) = f*_i(r - c_i, t - 1) without the source; an upstream site outside the
+// lattice is replaced by the site itself (open edge: zero-gradient copy along the
+// population's own direction).
+template <typename T>
+__device__ __forceinline__ void pull_planes(const StepArgs<T> &a, const T *__restrict__ f, int x, int y,
+                                            Pop<T> &p) {
     const size_t ps = a.pstride;
     const int xm = x > 0 ? x - 1 : 0;
     const int xp = x < a.nx - 1 ? x + 1 : x;
@@ -120,15 +133,21 @@ __device__ __forceinline__ void pull_site(const StepArgs<T> &a, const T *__restr
     p.hypy = f[P_HYPY * ps + rm + x];
     p.hymy = f[P_HYMY * ps + rp + x];
     p.hyz = f[P_HYZ * ps + r + x];
+}
+
+// pull_planes plus the source at x = 0 (t >= 1), evaluated by the thread that needs it.
+// Kernels that pull many sites per thread in a loop evaluate source_values() once per
+// block instead and call inject_source(): the evaluation (a double-precision sine and
+// the phase) does not depend on the site, and a compiler may hoist it out of the loop,
+// running it in every thread on the low-throughput FP64 pipe.
+template <typename T>
+__device__ __forceinline__ void pull_site(const StepArgs<T> &a, const T *__restrict__ f, int x,
+                                          int y, long long t, Pop<T> &p) {
+    pull_planes(a, f, x, y, p);
     if (x == 0 && t >= 1 && a.src.kind != SRC_NONE) {
         double g, inc;
         source_values(a.src, t, &g, &inc);
-        if (a.src.kind == SRC_OPEN) {
-            p.epx += (T)g;
-        } else {
-            p.epx = (T)inc;
-            p.hxpx = (T)0;
-        }
+        inject_source(a.src.kind, g, inc, p);
     }
 }
 

@@ -41,8 +41,7 @@ __device__ __forceinline__ void put_smem(float *sm, int ly, int lx, const Pop<fl
 
 // f_i(r, t + 1) from the shared-memory f*(t); (cx, cy) is the site's cell in the tile
 // with halo, the upstream cell is clamped at the lattice edge exactly as pull_site does.
-__device__ __forceinline__ void pull_smem(float *sm, const SourceParams &src, int nx, int ny, int x, int y,
-                                          int cx, int cy, long long t1, Pop<float> &p) {
+__device__ __forceinline__ void pull_smem(float *sm, int nx, int ny, int x, int y, int cx, int cy, Pop<float> &p) {
     const int xm = x > 0 ? cx - 1 : cx, xp = x < nx - 1 ? cx + 1 : cx;
     const int ym = y > 0 ? cy - 1 : cy, yp = y < ny - 1 ? cy + 1 : cy;
     p.ez = smv(sm, P_EZ, cy, cx);
@@ -56,7 +55,22 @@ __device__ __forceinline__ void pull_smem(float *sm, const SourceParams &src, in
     p.hypy = smv(sm, P_HYPY, ym, cx);
     p.hymy = smv(sm, P_HYMY, yp, cx);
     p.hyz = smv(sm, P_HYZ, cy, cx);
-    f16_source(src, x, t1, p);
+}
+
+// Source values of the two times of a launch (t, t + 1), evaluated once per block by one
+// thread of the blocks that own column 0 (see pull_site for why not per site).
+struct SrcPair {
+    double g0, inc0, g1, inc1;
+};
+__device__ __forceinline__ void source_pair(const SourceParams &src, int x0, long long t, SrcPair *sp) {
+    if (threadIdx.x == 0) {
+        SrcPair v{0.0, 0.0, 0.0, 0.0};
+        if (x0 == 0 && src.kind != SRC_NONE) {
+            if (t >= 1) source_values(src, t, &v.g0, &v.inc0);
+            source_values(src, t + 1, &v.g1, &v.inc1);
+        }
+        *sp = v;
+    }
 }
 
 __device__ __forceinline__ void acc_site(const AccParams &ap, const SourceParams &src, size_t idx, int y,
@@ -79,14 +93,19 @@ __global__ void __launch_bounds__(NT) k_step2_f32(const StepArgs<float> a, const
                                                   float *__restrict__ fout, const long long *__restrict__ t_in,
                                                   long long *__restrict__ t_out) {
     extern __shared__ float sm[];
+    __shared__ SrcPair sp;
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
     const long long t = *t_in;
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *t_out = t + 2;
+    source_pair(a.src, x0, t, &sp);
+    __syncthreads();
+    const bool src0 = t >= 1 && a.src.kind != SRC_NONE, src1 = a.src.kind != SRC_NONE;
     for (int k = threadIdx.x; k < SW * SH; k += NT) {
         const int lx = k % SW, ly = k / SW, x = x0 - 1 + lx, y = y0 - 1 + ly;
         if (x < 0 || x >= a.nx || y < 0 || y >= a.ny) continue;
         Pop<float> p;
-        pull_site(a, fin, x, y, t, p);
+        pull_planes(a, fin, x, y, p);
+        if (x == 0 && src0) inject_source(a.src.kind, sp.g0, sp.inc0, p);
         const size_t idx = (size_t)y * a.pitch + x;
         const MatT<float> m = a.mtab[a.mat[idx]];
         float E3, Hx, Hy, D;
@@ -102,7 +121,8 @@ __global__ void __launch_bounds__(NT) k_step2_f32(const StepArgs<float> a, const
         const int lx = k % TW, ly = k / TW, x = x0 + lx, y = y0 + ly;
         if (x >= a.nx || y >= a.ny) continue;
         Pop<float> p;
-        pull_smem(sm, a.src, a.nx, a.ny, x, y, lx + 1, ly + 1, t + 1, p);
+        pull_smem(sm, a.nx, a.ny, x, y, lx + 1, ly + 1, p);
+        if (x == 0 && src1) inject_source(a.src.kind, sp.g1, sp.inc1, p);
         const size_t idx = (size_t)y * a.pitch + x;
         const MatT<float> m = a.mtab[a.mat[idx]];
         float E3, Hx, Hy, D;
@@ -118,9 +138,13 @@ template <bool ACC>
 __global__ void __launch_bounds__(NT) k_step2_f16(const F16Args a, const long long *__restrict__ t_in,
                                                   long long *__restrict__ t_out) {
     extern __shared__ float sm[];
+    __shared__ SrcPair sp;
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
     const long long t = *t_in;
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *t_out = t + 2;
+    source_pair(a.src, x0, t, &sp);
+    __syncthreads();
+    const bool src0 = t >= 1 && a.src.kind != SRC_NONE, src1 = a.src.kind != SRC_NONE;
     // phase 1: time t; the shared memory receives what a pull would rebuild from the
     // stored (FP16-rounded) state of time t, so this equals two one-step launches
     for (int k = threadIdx.x; k < SW * SH; k += NT) {
@@ -129,7 +153,8 @@ __global__ void __launch_bounds__(NT) k_step2_f16(const F16Args a, const long lo
         const size_t idx = (size_t)y * a.pitch + x;
         const MatT<float> m = a.mtab[a.mat[idx]];
         Pop<float> p;
-        pull_f16(a, x, y, t, p);
+        pull_f16_planes(a, x, y, p);
+        if (x == 0 && src0) inject_source(a.src.kind, sp.g0, sp.inc0, p);
         float E3, Hx, Hy, D;
         moments(p, m, &E3, &Hx, &Hy, &D);
         if (field_runaway(E3)) atomicOr(a.err, 1u);
@@ -148,7 +173,8 @@ __global__ void __launch_bounds__(NT) k_step2_f16(const F16Args a, const long lo
         const int lx = k % TW, ly = k / TW, x = x0 + lx, y = y0 + ly;
         if (x >= a.nx || y >= a.ny) continue;
         Pop<float> p;
-        pull_smem(sm, a.src, a.nx, a.ny, x, y, lx + 1, ly + 1, t + 1, p);
+        pull_smem(sm, a.nx, a.ny, x, y, lx + 1, ly + 1, p);
+        if (x == 0 && src1) inject_source(a.src.kind, sp.g1, sp.inc1, p);
         const size_t idx = (size_t)y * a.pitch + x;
         const MatT<float> m = a.mtab[a.mat[idx]];
         float E3, Hx, Hy, D;

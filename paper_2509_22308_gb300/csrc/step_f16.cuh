@@ -75,18 +75,13 @@ __device__ __forceinline__ void f16_source(const SourceParams &src, int x, long 
     if (x == 0 && t >= 1 && src.kind != SRC_NONE) {
         double gs, inc;
         source_values(src, t, &gs, &inc);
-        if (src.kind == SRC_OPEN) {
-            p.epx += (float)gs;
-        } else {
-            p.epx = (float)inc;
-            p.hxpx = 0.0f;
-        }
+        inject_source(src.kind, gs, inc, p);
     }
 }
 
 // f_i(r, t) for the 11 populations of site (x, y), rebuilt from the upstream sites'
-// fields and deviations of time t - 1 (one site per call).
-__device__ __forceinline__ void pull_f16(const F16Args &a, int x, int y, long long t, Pop<float> &p) {
+// fields and deviations of time t - 1 (one site per call), without the source.
+__device__ __forceinline__ void pull_f16_planes(const F16Args &a, int x, int y, Pop<float> &p) {
     const size_t ps = a.pstride;
     const int xm = x > 0 ? x - 1 : 0;
     const int xp = x < a.nx - 1 ? x + 1 : x;
@@ -108,6 +103,11 @@ __device__ __forceinline__ void pull_f16(const F16Args &a, int x, int y, long lo
     p.hypy = rebuild(so.hy, g[P_HYPY * ps + rm + x], is);
     p.hymy = rebuild(no.hy, g[P_HYMY * ps + rp + x], is);
     p.hyz = rebuild(c.hy, g[P_HYZ * ps + r + x], is);
+}
+
+// pull_f16_planes plus the source (see pull_site for when to use inject_source instead).
+__device__ __forceinline__ void pull_f16(const F16Args &a, int x, int y, long long t, Pop<float> &p) {
+    pull_f16_planes(a, x, y, p);
     f16_source(a.src, x, t, p);
 }
 

@@ -18,7 +18,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
 F64, F32, F16DEV = 0, 1, 2
 FLAG_SINGLE_STEP, FLAG_TWO_STEP = 1, 2
 STEP_MODES = {"auto": 0, "one": FLAG_SINGLE_STEP, "two": FLAG_TWO_STEP}
-SRC_OPEN, SRC_HARD, SRC_NONE = 0, 1, 2
+SRC_HARD, SRC_OPEN, SRC_NONE = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ETIMEOUT", 6: "ESTATE"}
 PRECISIONS = {"f64": F64, "f32": F32, "f16dev": F16DEV}
 
@@ -58,7 +58,7 @@ class Instance(ctypes.Structure):
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("min_periods", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("min_periods", ctypes.c_int32), ("source_kind", ctypes.c_int32),
                 ("conv_tol", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
 
@@ -144,7 +144,7 @@ def make_janus(a, phi0, eps1, eps2=1.0, pec2=False, cx=None, cy=None) -> Janus:
                  math.nan if cx is None else float(cx), math.nan if cy is None else float(cy))
 
 
-def make_source(period, ramp=None, kind=SRC_OPEN, E0=1.0) -> Source:
+def make_source(period, ramp=None, kind=SRC_HARD, E0=1.0) -> Source:
     return Source(int(period), int(period if ramp is None else ramp), int(kind), 0, float(E0))
 
 
@@ -303,7 +303,7 @@ def rasterize_janus_noalloc(j: Janus, nx, ny):
     return out
 
 
-def solver_for_instance(inst: dict, precision="f64", stream=None, kind=SRC_OPEN, steps_per_launch="auto") -> Solver:
+def solver_for_instance(inst: dict, precision="f64", stream=None, kind=SRC_HARD, steps_per_launch="auto") -> Solver:
     """Solver for one workload instance dictionary (see ``workloads``)."""
     j = make_janus(inst["a"], inst["phi0"], inst["eps1"], inst["eps2"], inst["pec2"])
     s = make_source(inst["period"], inst.get("ramp"), kind)
@@ -323,7 +323,7 @@ class Batch:
     """Owner of one ``lbm_em_batch_t``."""
 
     def __init__(self, instances, precision="f32", tile_w=0, tile_h=0, ctas_per_sm=0, stream=None,
-                 conv_tol=0.0, min_periods=0):
+                 conv_tol=0.0, min_periods=0, kind=SRC_HARD):
         L = load()
         n = len(instances)
         arr = (Instance * n)()
@@ -333,7 +333,7 @@ class Batch:
                               float(inst["R"]),
                               make_janus(inst["a"], inst["phi0"], inst["eps1"], inst["eps2"], inst["pec2"]))
         o = BatchOpts(PRECISIONS.get(precision, precision), int(tile_w), int(tile_h), int(ctas_per_sm),
-                      int(min_periods), 0, float(conv_tol), _stream_ptr(stream))
+                      int(min_periods), int(kind), float(conv_tol), _stream_ptr(stream))
         b = ctypes.c_void_p()
         _call("lbm_em_batch_create", arr, n, ctypes.byref(o), ctypes.byref(b))
         self.b, self.n, self._L = b, n, L

@@ -61,6 +61,50 @@ def design_map(eps1, eps2=1.0, pec2=False, n_phi=36, a=32, wavelength=None, peri
     return F
 
 
+def janus_map(materials, phi0_values, *, a=40, L_over_a=4, a_over_lambda=1.0, R_over_a=1.5, periods=30,
+              precision="f32", conv_tol=0.0, min_periods=8, stream=None, chunk=4096):
+    """F~x, F~y, M~z [len(materials), len(phi0_values), 3] and the steps each instance ran
+    [len(materials), len(phi0_values)], for every (material, orientation) pair, from batched
+    GPU runs of at most ``chunk`` instances each.
+
+    ``materials`` is a list of (eps1, eps2, pec2).  Defaults are the paper's force
+    resolution for metallo-dielectric cylinders (Sec. III: a/dx = 40, L/a = 4, a/lambda = 1);
+    dielectric Janus maps use a = 50.  With ``conv_tol`` > 0 each instance stops once its
+    energy has settled (at least ``min_periods``, at most ``periods``)."""
+    from paper_2509_22308_gb300 import lbm_em as L
+    n = int(round(L_over_a * a))
+    T = int(round(3 * a / a_over_lambda))
+    insts = [dict(nx=n, ny=n, a=float(a), phi0=float(p), eps1=float(e1), eps2=float(e2), pec2=bool(pec),
+                  period=T, periods=periods, R=R_over_a * a, ramp=T)
+             for (e1, e2, pec) in materials for p in phi0_values]
+    F = np.empty((len(insts), 3))
+    steps = np.empty(len(insts), dtype=np.int64)
+    for lo in range(0, len(insts), chunk):
+        b = L.Batch(insts[lo:lo + chunk], precision, stream=stream, conv_tol=conv_tol,
+                    min_periods=min(min_periods, periods))
+        try:
+            b.run()
+            F[lo:lo + chunk], _ = b.results()
+            steps[lo:lo + chunk] = b.steps()
+        finally:
+            b.close()
+    shape = (len(materials), len(phi0_values))
+    return F.reshape(shape + (3,)), steps.reshape(shape)
+
+
+def md_janus_map(eps1_values, phi0_values, **kw):
+    """Sec. IV.A map: dielectric half eps_r1, the other half PEC (paper: eps_r1 = 1 ... 5 in
+    steps of 0.04, phi0 = 0 ... 2 pi in steps of pi/90, a/dx = 40, L/a = 4)."""
+    return janus_map([(e, 1.0, True) for e in eps1_values], phi0_values, **kw)
+
+
+def dielectric_janus_map(eps1, ratios, phi0_values, **kw):
+    """Sec. IV.B map at fixed eps_r1: eps_r2 = ratio * eps_r1 (paper: eps_r1 in {1, 2, 5},
+    ratio = 1 ... 5 in steps of 0.04, phi0 in steps of pi/90, a/dx = 50, L/a = 4)."""
+    kw.setdefault("a", 50)
+    return janus_map([(eps1, r * eps1, False) for r in ratios], phi0_values, **kw)
+
+
 def integrate(fmap, phi0_init, t_final=1.0e4, log_l_over_a=math.log(10.0), dt=1.0, x0=0.0, y0=0.0):
     """RK4 trajectory (t~, x~, y~, phi0) from (x0, y0, phi0_init) to t~ = t_final (Sec. IV.C
     starts at the origin and integrates to 10^4)."""

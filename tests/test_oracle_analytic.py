@@ -131,3 +131,36 @@ def test_md_janus_quoted_values(row):
     f = A.forces_quadrature(B, D, K0, A_RAD, phi0, r=1.5 * A_RAD)
     assert qty == "drag"
     assert abs(f[0] - value) <= tol
+
+
+# --- TE^z (H_z, E_x, E_y): the polarization the paper leaves for future work ---------
+
+@pytest.mark.parametrize("eps,pec", [(2.25, False), (6.0, False), (1.0, True)])
+def test_te_homogeneous_routes_agree_and_conserve(eps, pec):
+    """TE coefficients: near-field stress quadrature at two radii, the closed form and
+    the far-field momentum balance give one force (the stress tensor of the dual fields
+    (H_z, E_r, E_phi) has the TM form); lossless energy balance."""
+    B, D = A.homogeneous_BD(K0, 20.0, eps, 0.7, pec=pec, te=True)
+    q = A.forces_quadrature(B, D, K0, 20.0, 0.7)
+    assert np.allclose(q, A.forces_closed_form(B, D, K0, 20.0, 0.7), atol=1e-12)
+    assert np.allclose(q, A.forces_quadrature(B, D, K0, 20.0, 0.7, r=45.0), atol=1e-12)
+    assert np.allclose(q[:2], A.far_field_forces(B, D, K0, 20.0, 0.7), atol=1e-12)
+    pn, ps = A.net_flux(B, D, K0, 30.0, 0.7)
+    assert abs(pn) < 1e-12 * ps
+    assert abs(q[1]) < 1e-12 and abs(q[2]) < 1e-12 and q[0] > 0
+
+
+def test_te_rayleigh_limits():
+    """Small cylinders (k0 a << 1), textbook TE limits that differ from TM: a dielectric
+    scatters through the in-plane dipole, c_1 -> +j pi (k0 a)^2 (eps - 1) / (4 (eps + 1))
+    with c_0 of order (k0 a)^4; a PEC through c_0 -> -j pi (k0 a)^2 / 4 and
+    c_1 -> +j pi (k0 a)^2 / 4 (dH_z/dr = 0 on the surface)."""
+    x, eps = 1e-3, 2.0
+    B, _ = A.homogeneous_BD(x, 1.0, eps, 0.0, te=True)
+    c = B / (A.alpha(np.arange(len(B))) * (-1j) ** np.arange(len(B)))
+    assert abs(c[1] - 1j * np.pi * x ** 2 * (eps - 1) / (4 * (eps + 1))) < 1e-4 * abs(c[1])
+    assert abs(c[0]) < 1e-4 * abs(c[1])
+    B, _ = A.homogeneous_BD(x, 1.0, 1.0, 0.0, pec=True, te=True)
+    c = B / (A.alpha(np.arange(len(B))) * (-1j) ** np.arange(len(B)))
+    assert abs(c[0] + 1j * np.pi * x ** 2 / 4) < 1e-4 * np.pi * x ** 2 / 4
+    assert abs(c[1] - 1j * np.pi * x ** 2 / 4) < 1e-4 * np.pi * x ** 2 / 4
