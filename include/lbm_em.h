@@ -74,11 +74,18 @@ typedef enum {
  * result does not depend on the choice: both modes give the same bits. */
 #define LBM_EM_FLAG_SINGLE_STEP 1  /* always one step per launch                          */
 #define LBM_EM_FLAG_TWO_STEP 2     /* two steps per launch for FP32 and FP16-deviation    */
+/* TE^z polarization (H_z, E_x, E_y), which the paper leaves for future work (Sec. I): the
+ * same scheme and storage (11 planes), incident wave E_y = H_z = E0 sin(w t - k x).  Every
+ * call that reports the TM triple (E_z, H_x, H_y) reports (H_z, E_x, E_y) instead: fields,
+ * phasors, the stress-tensor contour integral (same form by duality) and the far field (of
+ * H_z).  FP64 and FP32 only; LBM_EM_F16DEV with this flag is EINVAL. */
+#define LBM_EM_FLAG_TE 4
 
 typedef struct {
     int32_t nx, ny;       /* lattice size, each >= 4                                      */
     int32_t precision;    /* lbm_em_precision                                             */
-    int32_t flags;        /* 0, LBM_EM_FLAG_SINGLE_STEP or LBM_EM_FLAG_TWO_STEP           */
+    int32_t flags;        /* 0, LBM_EM_FLAG_SINGLE_STEP or LBM_EM_FLAG_TWO_STEP, optionally
+                             | LBM_EM_FLAG_TE                                             */
     void *stream;         /* cudaStream_t every kernel of the handle runs on; NULL: the
                              library creates a private non-blocking stream                */
 } lbm_em_grid;

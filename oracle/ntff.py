@@ -32,34 +32,39 @@ def lattice_wavenumber(period: int) -> float:
     return float(np.angle((3.0 - z) / (z * (3.0 * z - 1.0))))
 
 
-def far_field_amplitude_from_contour(ez, hx, hy, px, py, nx_, ny_, cx, cy, dl, k, phis):
+def far_field_amplitude_from_contour(ez, hx, hy, px, py, nx_, ny_, cx, cy, dl, k, phis, te=False):
     """A(phi) from scattered phasors ez, hx, hy sampled at contour points (px, py) with
-    outward normals (nx_, ny_), line element dl, about the centre (cx, cy)."""
+    outward normals (nx_, ny_), line element dl, about the centre (cx, cy).
+
+    TE^z: (ez, hx, hy) are (H_z, E_x, E_y) and the transformed scalar is H_z; curl H = -i k E
+    gives dH_z/dn = -i k (-n_x E_y + n_y E_x), the TM normal derivative with the sign flipped."""
     phis = np.asarray(phis)[:, None]
     rx, ry = px[None, :] - cx, py[None, :] - cy
     ux, uy = np.cos(phis), np.sin(phis)
     phase = np.exp(-1j * k * (ux * rx + uy * ry))
-    integrand = (ux * nx_[None, :] + uy * ny_[None, :]) * ez[None, :] + (-nx_ * hy + ny_ * hx)[None, :]
+    sgn = -1.0 if te else 1.0
+    integrand = (ux * nx_[None, :] + uy * ny_[None, :]) * ez[None, :] + sgn * (-nx_ * hy + ny_ * hx)[None, :]
     return (k / 4.0) * np.sum(integrand * phase, axis=1) * dl
 
 
-def scattered_phasors(Ez, Hx, Hy, period: int, E0: float = 1.0):
-    """Lattice phasor fields minus the exact incident plane wave at every site."""
+def scattered_phasors(Ez, Hx, Hy, period: int, E0: float = 1.0, te=False):
+    """Lattice phasor fields minus the exact incident plane wave at every site (TM: E_z^I =
+    i E0 e^{i k x}, H_y^I = -E_z^I; TE: H_z^I = i E0 e^{i k x}, E_y^I = +H_z^I)."""
     k = lattice_wavenumber(period)
     x = np.arange(Ez.shape[1])[None, :]
     Einc = 1j * E0 * np.exp(1j * k * x)
-    return Ez - Einc, Hx, Hy + Einc
+    return Ez - Einc, Hx, (Hy - Einc) if te else (Hy + Einc)
 
 
-def scattering_intensity_lattice(Ez, Hx, Hy, period, cx, cy, R, n_points, phis, E0=1.0):
+def scattering_intensity_lattice(Ez, Hx, Hy, period, cx, cy, R, n_points, phis, E0=1.0, te=False):
     """|S(phi)|^2 (Eq. scattering intensity) from LBM phasor fields [ny, nx] via the
-    transform on a circle of radius R about (cx, cy)."""
+    transform on a circle of radius R about (cx, cy); TE: the triple is (H_z, E_x, E_y)."""
     k = lattice_wavenumber(period)
-    Es, Hxs, Hys = scattered_phasors(Ez, Hx, Hy, period, E0)
+    Es, Hxs, Hys = scattered_phasors(Ez, Hx, Hy, period, E0, te)
     px, py, phi = mst.contour_points(cx, cy, R, n_points)
     ez = mst.bilinear(Es, px, py)
     hx = mst.bilinear(Hxs, px, py)
     hy = mst.bilinear(Hys, px, py)
     A = far_field_amplitude_from_contour(ez, hx, hy, px, py, np.cos(phi), np.sin(phi), cx, cy,
-                                         R * 2.0 * np.pi / n_points, k, phis)
+                                         R * 2.0 * np.pi / n_points, k, phis, te)
     return (2.0 / np.pi) * np.abs(A) ** 2 / (E0 * E0)

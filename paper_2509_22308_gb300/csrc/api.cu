@@ -149,6 +149,7 @@ lbm_em_status build_contour(int nx, int ny, const lbm_em_contour *c, ContourHost
 struct lbm_em {
     int dev = 0;
     int nx = 0, ny = 0, pitch = 0, prec = 0;
+    int pol = POL_TM;  // POL_TM or POL_TE (LBM_EM_FLAG_TE)
     size_t pstride = 0, elem = 0, buf_bytes = 0;
     cudaStream_t stream = nullptr, cap = nullptr;
     bool own_stream = false;
@@ -190,6 +191,7 @@ static StepArgs<T> make_args(const lbm_em *h) {
     a.nx = h->nx;
     a.ny = h->ny;
     a.pitch = h->pitch;
+    a.pol = h->pol;
     a.pstride = h->pstride;
     a.mat = h->d_mat;
     a.mtab = (const MatT<T> *)h->d_mtab;
@@ -352,7 +354,10 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     if (!g || !out) return set_error(LBM_EM_EINVAL, "grid/out is NULL");
     *out = nullptr;
     if (g->nx < 4 || g->ny < 4) return set_error(LBM_EM_EINVAL, "nx and ny must be >= 4");
-    if (g->flags & ~(LBM_EM_FLAG_SINGLE_STEP | LBM_EM_FLAG_TWO_STEP)) return set_error(LBM_EM_EINVAL, "unknown grid flags");
+    if (g->flags & ~(LBM_EM_FLAG_SINGLE_STEP | LBM_EM_FLAG_TWO_STEP | LBM_EM_FLAG_TE))
+        return set_error(LBM_EM_EINVAL, "unknown grid flags");
+    if ((g->flags & LBM_EM_FLAG_TE) && g->precision == LBM_EM_F16DEV)
+        return set_error(LBM_EM_EINVAL, "TE^z is available in LBM_EM_F64 and LBM_EM_F32");
     if ((g->flags & LBM_EM_FLAG_SINGLE_STEP) && (g->flags & LBM_EM_FLAG_TWO_STEP))
         return set_error(LBM_EM_EINVAL, "LBM_EM_FLAG_SINGLE_STEP and LBM_EM_FLAG_TWO_STEP exclude each other");
     if ((long long)g->nx * g->ny > (1LL << 31)) return set_error(LBM_EM_EINVAL, "lattice too large (> 2^31 sites)");
@@ -370,6 +375,7 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     h->nx = g->nx;
     h->ny = g->ny;
     h->prec = g->precision;
+    h->pol = (g->flags & LBM_EM_FLAG_TE) ? POL_TE : POL_TM;
     h->elem = g->precision == LBM_EM_F64 ? sizeof(double) : sizeof(float);
     h->pitch = round_up(g->nx, 32);
     h->pstride = (size_t)h->pitch * (size_t)g->ny;
@@ -725,7 +731,7 @@ lbm_em_status lbm_em_far_field(lbm_em_t *h, const double *angles, int32_t n_angl
     if (!st)
         st = cuda_status(launch_farfield(h->d_acc, 2.0 / (double)h->n_acc, h->d_pts, (int)h->ch.pts.size(), h->d_inc,
                                          h->ch.R, h->ch.dl, lattice_wavenumber(h->srccfg.period_steps), h->srccfg.E0,
-                                         d_ang, n_angles, d, h->stream),
+                                         h->pol, d_ang, n_angles, d, h->stream),
                          "far-field kernel");
     if (!st)
         st = cuda_status(cudaMemcpyAsync(res.data(), d, res.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream),

@@ -100,10 +100,13 @@ __global__ void __launch_bounds__(256) k_contour(const double *__restrict__ acc,
 // with scattered phasors = total - incident (incident E_z phasor per stencil site given,
 // H_y^I = -E^I, H_x^I = 0), interpolated bilinearly; out[3 j] = (2/pi)|A|^2 / E0^2,
 // out[3 j + 1 .. 2] = Re, Im A.
+// TE^z (triple H_z, E_x, E_y): the same transform of H_z with dH_z/dn = -i k (-n_x E_y + n_y E_x)
+// (curl H = -i k E) and the incident wave E_y^I = +H_z^I, so sgn = -1 flips both.
 __global__ void __launch_bounds__(256) k_farfield(const double *__restrict__ acc, double scale,
                                                   const ContourPt *__restrict__ pts, int npts,
                                                   const double2 *__restrict__ inc, double R, double dl, double k,
-                                                  double E0, const double *__restrict__ angles, double *out) {
+                                                  double E0, double sgn, const double *__restrict__ angles,
+                                                  double *out) {
     const double phi = angles[blockIdx.x];
     double su, cu;
     sincos(phi, &su, &cu);
@@ -118,12 +121,12 @@ __global__ void __launch_bounds__(256) k_farfield(const double *__restrict__ acc
             v[1] += p.w[c] * (a[1] * scale - ei.y);
             v[2] += p.w[c] * (a[2] * scale);
             v[3] += p.w[c] * (a[3] * scale);
-            v[4] += p.w[c] * (a[4] * scale + ei.x);
-            v[5] += p.w[c] * (a[5] * scale + ei.y);
+            v[4] += p.w[c] * (a[4] * scale + sgn * ei.x);
+            v[5] += p.w[c] * (a[5] * scale + sgn * ei.y);
         }
         const double un = cu * p.nx + su * p.ny;
-        const double fr = un * v[0] + (-p.nx * v[4] + p.ny * v[2]);
-        const double fi = un * v[1] + (-p.nx * v[5] + p.ny * v[3]);
+        const double fr = un * v[0] + sgn * (-p.nx * v[4] + p.ny * v[2]);
+        const double fi = un * v[1] + sgn * (-p.nx * v[5] + p.ny * v[3]);
         double sp, cp;
         sincos(-k * R * un, &sp, &cp);
         sr += fr * cp - fi * sp;
@@ -152,9 +155,10 @@ __global__ void __launch_bounds__(256) k_farfield(const double *__restrict__ acc
 }
 
 cudaError_t launch_farfield(const double *acc, double scale, const ContourPt *pts, int npts, const double2 *inc,
-                            double R, double dl, double k, double E0, const double *angles, int n_angles,
+                            double R, double dl, double k, double E0, int pol, const double *angles, int n_angles,
                             double *out, cudaStream_t s) {
-    k_farfield<<<n_angles, 256, 0, s>>>(acc, scale, pts, npts, inc, R, dl, k, E0, angles, out);
+    k_farfield<<<n_angles, 256, 0, s>>>(acc, scale, pts, npts, inc, R, dl, k, E0, pol == POL_TE ? -1.0 : 1.0,
+                                        angles, out);
     return cudaGetLastError();
 }
 

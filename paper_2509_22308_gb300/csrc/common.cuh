@@ -34,6 +34,7 @@ enum Plane {
 };
 
 enum SourceKind { SRC_HARD = 0, SRC_OPEN = 1, SRC_NONE = 2 };  // values of lbm_em_source_kind
+enum Polarization { POL_TM = 0, POL_TE = 1 };
 
 // Per-material constants in the kernel's arithmetic type:
 // inv_eps3 = 1/(3 eps_r) (0 for PEC: E := 0), c_d = 6 eps_r - 4 (the weight of the z pair
@@ -63,7 +64,7 @@ struct AccParams {
 
 template <typename T>
 struct StepArgs {
-    int nx, ny, pitch, pad;
+    int nx, ny, pitch, pol;  // pol: POL_TM or POL_TE
     size_t pstride;
     const uint8_t *mat;   // material id per site (pitch layout)
     const MatT<T> *mtab;  // 256 entries
@@ -226,6 +227,66 @@ __device__ __forceinline__ void collide(Pop<T> &p, T E3, T Hx, T Hy) {
     }
 }
 
+// ---- TE^z (H_z, E_x, E_y), the polarization the paper leaves for future work ----------
+// The same scheme with E = (E_x, E_y, 0), H = (0, 0, H_z).  By the argument given for TM
+// at the top of this file the state reduces exactly to 11 scalars per site, and they
+// stream like the TM planes, so TE keeps them in the same planes (same pull, source and
+// edge handling):
+//   P_EZ   e_y of the z pair   P_HXZ  e_x of the z pair   P_HYZ  h_z of the z pair
+//   P_EPX  e_+x,y   P_EMX  e_-x,y   P_EPY  e_+y,y   P_EMY  e_-y,y
+//   P_HXPX e_+x,x   P_HXMX e_-x,x   P_HYPY e_+y,x   P_HYMY e_-y,x
+// with h_+x,z = e_+x,y, h_-x,z = -e_-x,y, h_+y,z = -e_+y,x, h_-y,z = e_-y,x, e_+z = e_-z,
+// h_+z,z = h_-z,z and e_0 = 6 (eps_r - 1) e_z (0 in PEC cells); h_+-z in x and y cancel
+// pairwise and never reach a field.  The incident wave E_y = H_z enters through e_+x,y as
+// the TM wave enters through e_+x,z, and its e_+x,x is zero (the HARD source's h_+x,x slot).
+
+// TE moments: D_y and D_x formed like D of TM, E/3 = D / (3 eps_r),
+// H_z = 2 h_z,z + e_+x,y - e_-x,y - e_+y,x + e_-y,x.
+template <typename T>
+__device__ __forceinline__ void moments_te(const Pop<T> &p, const MatT<T> &m, T *Ey3, T *Ex3, T *Hz, T *Dy,
+                                           T *Dx) {
+    const T dy = fmat(m.c_d, p.ez, p.epx) + p.emx + p.epy + p.emy;
+    const T dx = fmat(m.c_d, p.hxz, p.hxpx) + p.hxmx + p.hypy + p.hymy;
+    *Dy = dy;
+    *Dx = dx;
+    if constexpr (sizeof(T) == 4) {
+        *Ey3 = quot(dy, m.c3, m.inv_eps3);
+        *Ex3 = quot(dx, m.c3, m.inv_eps3);
+    } else {
+        *Ey3 = dy * m.inv_eps3;
+        *Ex3 = dx * m.inv_eps3;
+    }
+    *Hz = fmat((T)2, p.hyz, p.epx - p.emx) + (p.hymy - p.hypy);
+}
+
+// TE collision f* = 2 f^eq - f: e_x of z, +-x: E_x/3; of +y: E_x/3 - H_z/3; of -y:
+// E_x/3 + H_z/3; e_y of z, +-y: E_y/3; of +x: E_y/3 + H_z/3; of -x: E_y/3 - H_z/3;
+// h_z of the z pair: H_z/3.
+template <typename T>
+__device__ __forceinline__ void collide_te(Pop<T> &p, T Ey3, T Ex3, T Hz) {
+    if constexpr (sizeof(T) == 4) {
+        const float hz3 = quot(Hz, 3.0f, 1.0f / 3.0f);
+        p.epx = (Ey3 + hz3) - p.epx;
+        p.emx = (Ey3 - hz3) - p.emx;
+        p.hypy = (Ex3 - hz3) - p.hypy;
+        p.hymy = (Ex3 + hz3) - p.hymy;
+        p.hyz = hz3 - p.hyz;
+    } else {
+        const T third = (T)(1.0 / 3.0), mthird = (T)(-1.0 / 3.0);
+        p.epx = fmat(Hz, third, Ey3) - p.epx;
+        p.emx = fmat(Hz, mthird, Ey3) - p.emx;
+        p.hypy = fmat(Hz, mthird, Ex3) - p.hypy;
+        p.hymy = fmat(Hz, third, Ex3) - p.hymy;
+        p.hyz = fmat(Hz, third, -p.hyz);
+    }
+    p.ez = Ey3 - p.ez;
+    p.epy = Ey3 - p.epy;
+    p.emy = Ey3 - p.emy;
+    p.hxpx = Ex3 - p.hxpx;
+    p.hxmx = Ex3 - p.hxmx;
+    p.hxz = Ex3 - p.hxz;
+}
+
 // |E_z/3| >= 2^20 or non-finite, tested on the exponent bits (integer ALU only).
 __device__ __forceinline__ bool field_runaway(double e3) {
     return (unsigned)(__double2hiint(e3) & 0x7ff00000) >= 0x41300000u;
@@ -247,6 +308,40 @@ __device__ __forceinline__ void store_site(T *__restrict__ f, size_t ps, size_t 
     f[P_HYPY * ps + idx] = p.hypy;
     f[P_HYMY * ps + idx] = p.hymy;
     f[P_HYZ * ps + idx] = p.hyz;
+}
+
+// One site of either polarization: the field triple (TM: E_z, H_x, H_y; TE: H_z, E_x, E_y)
+// from the moments, into f3 when wanted; the energy density (D.E + H^2)/2 when wanted;
+// then, if COLLIDE, the post-collision populations.  Returns whether the field ran away.
+template <int POL, bool COLLIDE, typename T>
+__device__ __forceinline__ bool update_site(Pop<T> &p, const MatT<T> &m, double *f3, double *w) {
+    bool bad;
+    if constexpr (POL == POL_TM) {
+        T E3, Hx, Hy, D;
+        moments(p, m, &E3, &Hx, &Hy, &D);
+        bad = field_runaway(E3);
+        if (f3) {
+            f3[0] = (double)(D * m.inv_eps);
+            f3[1] = (double)Hx;
+            f3[2] = (double)Hy;
+        }
+        if (w) *w = 0.5 * ((double)D * (double)(D * m.inv_eps) + (double)Hx * (double)Hx + (double)Hy * (double)Hy);
+        if (COLLIDE) collide(p, E3, Hx, Hy);
+    } else {
+        T Ey3, Ex3, Hz, Dy, Dx;
+        moments_te(p, m, &Ey3, &Ex3, &Hz, &Dy, &Dx);
+        bad = field_runaway(Ey3) || field_runaway(Ex3);
+        if (f3) {
+            f3[0] = (double)Hz;
+            f3[1] = (double)(Dx * m.inv_eps);
+            f3[2] = (double)(Dy * m.inv_eps);
+        }
+        if (w)
+            *w = 0.5 * ((double)Dx * (double)(Dx * m.inv_eps) + (double)Dy * (double)(Dy * m.inv_eps) +
+                        (double)Hz * (double)Hz);
+        if (COLLIDE) collide_te(p, Ey3, Ex3, Hz);
+    }
+    return bad;
 }
 
 // Contour sample: four stencil slots with bilinear weights, outward normal.

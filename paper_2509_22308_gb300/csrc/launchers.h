@@ -18,7 +18,7 @@ cudaError_t launch_rasterize(int nx, int ny, int pitch, double cx, double cy, do
 cudaError_t launch_contour(const double *acc, double scale, const ContourPt *pts, int npts,
                            double R, double dl, double F0, double M0, double *out, cudaStream_t s);
 cudaError_t launch_farfield(const double *acc, double scale, const ContourPt *pts, int npts, const double2 *inc,
-                            double R, double dl, double k, double E0, const double *angles, int n_angles,
+                            double R, double dl, double k, double E0, int pol, const double *angles, int n_angles,
                             double *out, cudaStream_t s);
 
 }  // namespace lbmem

@@ -20,9 +20,10 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;
 }
 
-// Total electromagnetic energy sum over sites of (eps E_z^2 + H_x^2 + H_y^2) / 2 at time
-// *t_dev (the convergence monitor of Sec. III), accumulated into *energy (FP64).
-template <typename T>
+// Total electromagnetic energy sum over sites of (D . E + H . H) / 2 at time *t_dev (the
+// convergence monitor of Sec. III), accumulated into *energy (FP64); TM D.E = eps E_z^2,
+// TE D.E = eps (E_x^2 + E_y^2).
+template <typename T, int POL>
 __global__ void __launch_bounds__(BX *BY) k_energy(const StepArgs<T> a, const T *__restrict__ f,
                                                    const long long *__restrict__ t_dev, double *energy) {
     const int x = blockIdx.x * BX + threadIdx.x;
@@ -31,11 +32,7 @@ __global__ void __launch_bounds__(BX *BY) k_energy(const StepArgs<T> a, const T 
     if (x < a.nx && y < a.ny) {
         Pop<T> p;
         pull_site(a, f, x, y, *t_dev, p);
-        const MatT<T> m = a.mtab[a.mat[(size_t)y * a.pitch + x]];
-        T E3, Hx, Hy, D;
-        moments(p, m, &E3, &Hx, &Hy, &D);
-        const double ez = (double)(D * m.inv_eps);
-        w = 0.5 * ((double)D * ez + (double)Hx * (double)Hx + (double)Hy * (double)Hy);
+        update_site<POL, false>(p, a.mtab[a.mat[(size_t)y * a.pitch + x]], nullptr, &w);
     }
     w = block_sum(w);
     if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(energy, w);
@@ -44,7 +41,10 @@ __global__ void __launch_bounds__(BX *BY) k_energy(const StepArgs<T> a, const T 
 template <typename T>
 cudaError_t launch_energy(const StepArgs<T> &a, const T *f, const long long *t_dev, double *energy, cudaStream_t s) {
     dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY), block(BX, BY);
-    k_energy<T><<<grid, block, 0, s>>>(a, f, t_dev, energy);
+    if (a.pol == POL_TE)
+        k_energy<T, POL_TE><<<grid, block, 0, s>>>(a, f, t_dev, energy);
+    else
+        k_energy<T, POL_TM><<<grid, block, 0, s>>>(a, f, t_dev, energy);
     return cudaGetLastError();
 }
 template cudaError_t launch_energy<double>(const StepArgs<double> &, const double *, const long long *, double *,

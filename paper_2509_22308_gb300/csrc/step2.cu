@@ -88,7 +88,7 @@ __device__ __forceinline__ void acc_site(const AccParams &ap, const SourceParams
     q[5] += hy * c.y;
 }
 
-template <bool ACC>
+template <bool ACC, int POL>
 __global__ void __launch_bounds__(NT) k_step2_f32(const StepArgs<float> a, const float *__restrict__ fin,
                                                   float *__restrict__ fout, const long long *__restrict__ t_in,
                                                   long long *__restrict__ t_out) {
@@ -107,13 +107,10 @@ __global__ void __launch_bounds__(NT) k_step2_f32(const StepArgs<float> a, const
         pull_planes(a, fin, x, y, p);
         if (x == 0 && src0) inject_source(a.src.kind, sp.g0, sp.inc0, p);
         const size_t idx = (size_t)y * a.pitch + x;
-        const MatT<float> m = a.mtab[a.mat[idx]];
-        float E3, Hx, Hy, D;
-        moments(p, m, &E3, &Hx, &Hy, &D);
-        if (field_runaway(E3)) atomicOr(a.err, 1u);
-        if (ACC && lx >= 1 && lx <= TW && ly >= 1 && ly <= TH)
-            acc_site(a.accp, a.src, idx, y, t, (double)(D * m.inv_eps), (double)Hx, (double)Hy);
-        collide(p, E3, Hx, Hy);
+        const bool acc = ACC && lx >= 1 && lx <= TW && ly >= 1 && ly <= TH;
+        double f3[3];
+        if (update_site<POL, true>(p, a.mtab[a.mat[idx]], acc ? f3 : nullptr, nullptr)) atomicOr(a.err, 1u);
+        if (acc) acc_site(a.accp, a.src, idx, y, t, f3[0], f3[1], f3[2]);
         put_smem(sm, ly, lx, p);
     }
     __syncthreads();
@@ -124,12 +121,9 @@ __global__ void __launch_bounds__(NT) k_step2_f32(const StepArgs<float> a, const
         pull_smem(sm, a.nx, a.ny, x, y, lx + 1, ly + 1, p);
         if (x == 0 && src1) inject_source(a.src.kind, sp.g1, sp.inc1, p);
         const size_t idx = (size_t)y * a.pitch + x;
-        const MatT<float> m = a.mtab[a.mat[idx]];
-        float E3, Hx, Hy, D;
-        moments(p, m, &E3, &Hx, &Hy, &D);
-        if (field_runaway(E3)) atomicOr(a.err, 1u);
-        if (ACC) acc_site(a.accp, a.src, idx, y, t + 1, (double)(D * m.inv_eps), (double)Hx, (double)Hy);
-        collide(p, E3, Hx, Hy);
+        double f3[3];
+        if (update_site<POL, true>(p, a.mtab[a.mat[idx]], ACC ? f3 : nullptr, nullptr)) atomicOr(a.err, 1u);
+        if (ACC) acc_site(a.accp, a.src, idx, y, t + 1, f3[0], f3[1], f3[2]);
         store_site(fout, a.pstride, idx, p);
     }
 }
@@ -193,23 +187,35 @@ __global__ void __launch_bounds__(NT) k_step2_f16(const F16Args a, const long lo
 }
 
 cudaError_t step2_prepare() {
-    cudaError_t e = cudaFuncSetAttribute(k_step2_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStep2Smem);
+    const int b = (int)kStep2Smem;
+    cudaError_t e = cudaFuncSetAttribute(k_step2_f32<false, POL_TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step2_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStep2Smem);
+        e = cudaFuncSetAttribute(k_step2_f32<true, POL_TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step2_f16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStep2Smem);
+        e = cudaFuncSetAttribute(k_step2_f32<false, POL_TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step2_f16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStep2Smem);
+        e = cudaFuncSetAttribute(k_step2_f32<true, POL_TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step2_f16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step2_f16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     return e;
 }
 
 cudaError_t launch_step2_f32(const StepArgs<float> &a, const float *fin, float *fout, const long long *t_in,
                              long long *t_out, bool accumulate, cudaStream_t s) {
     dim3 grid((a.nx + TW - 1) / TW, (a.ny + TH - 1) / TH), block(NT);
-    if (accumulate)
-        k_step2_f32<true><<<grid, block, kStep2Smem, s>>>(a, fin, fout, t_in, t_out);
-    else
-        k_step2_f32<false><<<grid, block, kStep2Smem, s>>>(a, fin, fout, t_in, t_out);
+    if (a.pol == POL_TE) {
+        if (accumulate)
+            k_step2_f32<true, POL_TE><<<grid, block, kStep2Smem, s>>>(a, fin, fout, t_in, t_out);
+        else
+            k_step2_f32<false, POL_TE><<<grid, block, kStep2Smem, s>>>(a, fin, fout, t_in, t_out);
+    } else {
+        if (accumulate)
+            k_step2_f32<true, POL_TM><<<grid, block, kStep2Smem, s>>>(a, fin, fout, t_in, t_out);
+        else
+            k_step2_f32<false, POL_TM><<<grid, block, kStep2Smem, s>>>(a, fin, fout, t_in, t_out);
+    }
     return cudaGetLastError();
 }
 

@@ -18,6 +18,8 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
 F64, F32, F16DEV = 0, 1, 2
 FLAG_SINGLE_STEP, FLAG_TWO_STEP = 1, 2
 STEP_MODES = {"auto": 0, "one": FLAG_SINGLE_STEP, "two": FLAG_TWO_STEP}
+FLAG_TE = 4
+POLARIZATION_FLAGS = {"tm": 0, "te": FLAG_TE}
 SRC_HARD, SRC_OPEN, SRC_NONE = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ETIMEOUT", 6: "ESTATE"}
 PRECISIONS = {"f64": F64, "f32": F32, "f16dev": F16DEV}
@@ -165,11 +167,13 @@ class Solver:
     """Owner of one ``lbm_em_t`` handle; methods map one-to-one onto the C calls."""
 
     def __init__(self, nx, ny, precision="f64", *, janus: Janus | None = None, eps_map=None, pec_mask=None,
-                 source: Source, stream=None, steps_per_launch="auto"):
+                 source: Source, stream=None, steps_per_launch="auto", polarization="tm"):
         L = load()
         self.nx, self.ny = int(nx), int(ny)
         self.source = source
-        g = Grid(self.nx, self.ny, PRECISIONS.get(precision, precision), STEP_MODES[steps_per_launch],
+        self.polarization = polarization
+        g = Grid(self.nx, self.ny, PRECISIONS.get(precision, precision),
+                 STEP_MODES[steps_per_launch] | POLARIZATION_FLAGS[polarization],
                  _stream_ptr(stream))
         h = ctypes.c_void_p()
         if janus is not None:
@@ -303,18 +307,20 @@ def rasterize_janus_noalloc(j: Janus, nx, ny):
     return out
 
 
-def solver_for_instance(inst: dict, precision="f64", stream=None, kind=SRC_HARD, steps_per_launch="auto") -> Solver:
+def solver_for_instance(inst: dict, precision="f64", stream=None, kind=SRC_HARD, steps_per_launch="auto",
+                        polarization="tm") -> Solver:
     """Solver for one workload instance dictionary (see ``workloads``)."""
     j = make_janus(inst["a"], inst["phi0"], inst["eps1"], inst["eps2"], inst["pec2"])
     s = make_source(inst["period"], inst.get("ramp"), kind)
     return Solver(inst["nx"], inst["ny"], precision, janus=j, source=s, stream=stream,
-                  steps_per_launch=steps_per_launch)
+                  steps_per_launch=steps_per_launch, polarization=polarization)
 
 
-def run_instance(inst: dict, precision="f64", stream=None, steps_per_launch="auto") -> np.ndarray:
+def run_instance(inst: dict, precision="f64", stream=None, steps_per_launch="auto", polarization="tm") -> np.ndarray:
     """Full hot path for one instance: (periods - 1) periods of steps, one accumulated
     period, contour integral -> (F~x, F~y, M~z)."""
-    with solver_for_instance(inst, precision, stream, steps_per_launch=steps_per_launch) as s:
+    with solver_for_instance(inst, precision, stream, steps_per_launch=steps_per_launch,
+                             polarization=polarization) as s:
         s.step((inst["periods"] - 1) * inst["period"])
         return s.force_torque(make_contour(inst["R"], inst["a"]))
 

@@ -62,3 +62,7 @@ def test_argument_validation_needs_no_gpu(lib):
     with pytest.raises(lbm_em.LbmEmError) as e:
         lbm_em.Solver(32, 32, "f64", janus=lbm_em.make_janus(5, 0.3, 2.0), source=lbm_em.make_source(2))
     assert e.value.status == lbm_em.EINVAL
+    with pytest.raises(lbm_em.LbmEmError) as e:     # TE^z has no FP16-deviation form
+        lbm_em.Solver(32, 32, "f16dev", janus=lbm_em.make_janus(5, 0.3, 2.0), source=lbm_em.make_source(24),
+                      polarization="te")
+    assert e.value.status == lbm_em.EINVAL

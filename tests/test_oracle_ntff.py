@@ -71,3 +71,18 @@ def test_lbm_far_field_matches_analytic_md_janus():
     Sa = A.scattering_intensity(B, D, phis + phi0 + np.pi)   # lattice angle -> paper angle
     rel = np.abs(S - Sa) / Sa
     assert np.median(rel) < 0.05 and np.mean(rel < 0.05) > 0.6
+
+
+@pytest.mark.parametrize("pec", [False, True])
+def test_te_transform_reproduces_analytic_far_field(pec):
+    """TE^z: the transform of the exact scattered H_z, with E from curl H = -i k E (the
+    negative of the TM helper's H), equals the Hankel asymptote of the H_z series."""
+    k0, phi0, a = 2 * np.pi / 40, 0.7, 20.0
+    B, D = A.homogeneous_BD(k0, a, 1.0 if pec else 2.25, phi0, pec=pec, te=True)
+    R, N = 1.5 * a, 720
+    phi, Hs, ex, ey = _analytic_near_field(B, D, k0, R, N)
+    phis = np.linspace(0, 2 * np.pi, 37)
+    An = ntff.far_field_amplitude_from_contour(Hs, -ex, -ey, R * np.cos(phi), R * np.sin(phi), np.cos(phi),
+                                               np.sin(phi), 0.0, 0.0, R * 2 * np.pi / N, k0, phis, te=True)
+    Aa = A.far_field_amplitude(B, D, phis)
+    assert np.max(np.abs(An - Aa)) < 1e-12 * np.max(np.abs(Aa))
