@@ -33,7 +33,7 @@ WORKLOAD = "md_janus_512"
 # algorithmic bytes per lattice update: the 11 stored planes read and written once, plus
 # the 1-byte material id (FP16-deviation: 11 FP16 deviations + 3 FP32 fields each way)
 BYTES_PER_LU = {"f64": 11 * 8 * 2 + 1, "f32": 11 * 4 * 2 + 1, "f16dev": 2 * (11 * 2 + 3 * 4) + 1}
-STEP_KERNEL = {"f64": "k_step<double, false>", "f32": "k_step<float, false>", "f16dev": "k_step_f16<false>"}
+STEP_KERNEL = {"f64": "k_step<double, false, TM>", "f32": "k_step<float, false, TM>", "f16dev": "k_step_f16<false>"}
 # FP64 pipe operations per lattice update of the step kernel: 12 for the moments
 # (sums of 5, 5 and 5 stored populations, one scaling), 16 for the equilibria and 2 f^eq - f
 FP64_OPS_PER_LU = 28
@@ -472,13 +472,18 @@ def main():
         # blocking), so they can exceed the one-read-one-write-per-step roofline.
         big = W.md_janus_8192()[0]
         hs = {}
-        for fp, mode in (("f32", "auto"), ("f32", "one"), ("f16dev", "auto"), ("f16dev", "two"), ("f64", "auto")):
+        # TE^z lines: the same lattice and kernels with the TE moments and collision
+        for fp, mode, pol in (("f32", "auto", "tm"), ("f32", "one", "tm"), ("f16dev", "auto", "tm"),
+                              ("f16dev", "two", "tm"), ("f64", "auto", "tm"), ("f32", "auto", "te"),
+                              ("f64", "auto", "te")):
             key = fp + {"auto": "", "one": "_one_step_per_launch", "two": "_two_steps_per_launch"}[mode]
-            kern = {("f32", "auto"): "k_step2_f32<false> (two steps per launch)",
-                    ("f32", "one"): "k_step<float, false>", ("f16dev", "auto"): "k_step_f16<false>",
+            key += "_te" if pol == "te" else ""
+            P = "TE" if pol == "te" else "TM"
+            kern = {("f32", "auto"): f"k_step2_f32<false, {P}> (two steps per launch)",
+                    ("f32", "one"): f"k_step<float, false, {P}>", ("f16dev", "auto"): "k_step_f16<false>",
                     ("f16dev", "two"): "k_step2_f16<false> (two steps per launch)",
-                    ("f64", "auto"): "k_step<double, false>"}[(fp, mode)]
-            with L.solver_for_instance(big, fp, main, steps_per_launch=mode) as s:
+                    ("f64", "auto"): f"k_step<double, false, {P}>"}[(fp, mode)]
+            with L.solver_for_instance(big, fp, main, steps_per_launch=mode, polarization=pol) as s:
                 s.step(4)
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 n = 16
