@@ -498,7 +498,9 @@ def main():
                           "glups": round(sites / (us / 1e6) / 1e9, 2), "achieved_gbs": round(gbs, 1),
                           "frac_hbm": round(gbs / peak, 4), "bytes_per_lu": BYTES_PER_LU[fp]}
                 if fp == "f64":
-                    t_ops = sites * FP64_OPS_PER_LU / (us / 1e6) / 1e12
+                    ops = FP64_OPS_PER_LU + (1 if pol == "te" else 0)   # TE: 29 per update
+                    hs[key]["fp64_ops_per_lu"] = ops
+                    t_ops = sites * ops / (us / 1e6) / 1e12
                     hs[key]["fp64_tops"] = round(t_ops, 4)
                     hs[key]["frac_fp64_pipe"] = round(t_ops / (SMS * FP64_OPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12), 4)
         out["single_domain_8192"] = hs

@@ -214,8 +214,11 @@ def test_far_field_validation_at_paper_resolution(eps1, phi0):
     phis = np.linspace(0, 2 * np.pi, 73)[:-1]
     with L.solver_for_instance(inst, "f64") as s:
         # run until the domain energy has settled (Sec. III); high contrast needs long runs
-        _, steps = s.run_converged(L.make_contour(inst["R"], a), tol=1e-5, min_periods=20, max_periods=400)
-        assert steps < 400 * T, "energy did not settle"
+        # eps1 = 5 has a high-Q resonance: at tol 1e-5 the energy test passes after 76
+        # periods while the far field is still settling (55 % of angles within 5 %); at
+        # 1e-6 it runs 455 periods (64 %), as long as a 1e-7 run capped at 600 (65 %)
+        _, steps = s.run_converged(L.make_contour(inst["R"], a), tol=1e-6, min_periods=20, max_periods=800)
+        assert steps < 800 * T, "energy did not settle"
         S = s.far_field(phis)
     k = ntff.lattice_wavenumber(T)
     B, D, _ = A.md_janus_BD_galerkin(k, a, eps1, phi0, n_basis=320)
