@@ -9,6 +9,7 @@
 #include <complex>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -146,6 +147,53 @@ lbm_em_status build_contour(int nx, int ny, const lbm_em_contour *c, ContourHost
 }
 }  // namespace lbmem
 
+// ---- memory ---------------------------------------------------------------------------
+// Device buffers of a handle come from the device's default stream-ordered pool
+// (cudaMallocAsync / cudaFreeAsync on the handle's stream): no call waits for the device,
+// and up to kPoolKeepBytes of freed memory stay in the pool for the next handle, so
+// creating and destroying handles in a loop does not map and unmap memory each time.
+// Host-to-device uploads go through pinned blocks that the process keeps for reuse
+// (cudaMallocHost is slow); each block is reused only after its last copy has completed.
+static const uint64_t kPoolKeepBytes = 4ull << 30;
+static std::mutex g_pool_mu;
+static bool g_pool_ready[128];
+static std::multimap<size_t, void *> g_pinned_free;  // capacity -> pinned block
+
+static void prepare_pool(int dev) {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (dev < 0 || dev >= 128 || g_pool_ready[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = kPoolKeepBytes;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    g_pool_ready[dev] = true;
+}
+
+static cudaError_t pinned_get(size_t bytes, void **p, size_t *cap) {
+    size_t c = 4096;
+    while (c < bytes) c <<= 1;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        auto it = g_pinned_free.lower_bound(c);
+        if (it != g_pinned_free.end()) {
+            *cap = it->first;
+            *p = it->second;
+            g_pinned_free.erase(it);
+            return cudaSuccess;
+        }
+    }
+    *cap = c;
+    return cudaMallocHost(p, c);
+}
+
+static void pinned_put(void *p, size_t cap) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    g_pinned_free.emplace(cap, p);
+}
+
 struct lbm_em {
     int dev = 0;
     int nx = 0, ny = 0, pitch = 0, prec = 0;
@@ -180,8 +228,39 @@ struct lbm_em {
     cudaGraphExec_t g_plain = nullptr, g_acc = nullptr;
     double *d_fields = nullptr;
     void *h_stage = nullptr;       // pinned staging of the material table (async uploads)
+    size_t stage_cap = 0;
     cudaEvent_t stage_ev = nullptr;  // the last table upload from h_stage
+    void *h_up = nullptr;          // pinned staging of the other uploads (ids, contour)
+    size_t up_cap = 0;
+    cudaEvent_t up_ev = nullptr;   // the last upload from h_up
 };
+
+template <typename P>
+static cudaError_t dev_alloc(lbm_em *h, P **p, size_t bytes) {
+    return cudaMallocAsync((void **)p, bytes, h->stream);
+}
+
+template <typename P>
+static void dev_free(lbm_em *h, P *&p) {
+    if (p) cudaFreeAsync((void *)p, h->stream);
+    p = nullptr;
+}
+
+// Pinned staging of at least `bytes` for an upload on the handle's stream: waits for the
+// previous upload from it (normally long finished), growing the block when needed.
+static cudaError_t upload_staging(lbm_em *h, size_t bytes, void **p) {
+    cudaError_t e = cudaEventSynchronize(h->up_ev);
+    if (e != cudaSuccess) return e;
+    if (h->up_cap < bytes) {
+        pinned_put(h->h_up, h->up_cap);
+        h->h_up = nullptr;
+        h->up_cap = 0;
+        e = pinned_get(bytes, &h->h_up, &h->up_cap);
+        if (e != cudaSuccess) return e;
+    }
+    *p = h->h_up;
+    return cudaSuccess;
+}
 
 static const int kGraphSteps = 32;
 
@@ -306,38 +385,40 @@ static lbm_em_status run_steps(lbm_em *h, int64_t n, bool acc) {
     return LBM_EM_OK;
 }
 
+// Stream-ordered: the buffers go back to the pool after the work already queued on the
+// handle's stream (an executable graph still in flight is freed when it completes).
 static void free_contour(lbm_em *h) {
     if (h->g_acc) cudaGraphExecDestroy(h->g_acc);
     h->g_acc = nullptr;
-    cudaFree(h->d_slot);
-    cudaFree(h->d_acc);
-    cudaFree(h->d_pts);
-    cudaFree(h->d_inc);
-    h->d_slot = nullptr;
-    h->d_acc = nullptr;
-    h->d_pts = nullptr;
-    h->d_inc = nullptr;
+    dev_free(h, h->d_slot);
+    dev_free(h, h->d_acc);
+    dev_free(h, h->d_pts);
+    dev_free(h, h->d_inc);
     h->has_contour = false;
 }
 
 static void free_handle(lbm_em *h) {
     if (!h) return;
     cudaSetDevice(h->dev);
-    if (h->stream) cudaStreamSynchronize(h->stream);
-    free_contour(h);
+    if (h->stream) {
+        free_contour(h);
+        dev_free(h, h->buf[0]);
+        dev_free(h, h->buf[1]);
+        dev_free(h, h->d_mat);
+        dev_free(h, h->d_mtab);
+        dev_free(h, h->d_time);
+        dev_free(h, h->d_err);
+        dev_free(h, h->d_cs);
+        dev_free(h, h->d_out);
+        dev_free(h, h->d_fields);
+        cudaStreamSynchronize(h->stream);  // the pinned blocks are reused by other handles
+    }
     if (h->g_plain) cudaGraphExecDestroy(h->g_plain);
-    cudaFree(h->buf[0]);
-    cudaFree(h->buf[1]);
-    cudaFree(h->d_mat);
-    cudaFree(h->d_mtab);
-    cudaFree(h->d_time);
-    cudaFree(h->d_err);
-    cudaFree(h->d_cs);
-    cudaFree(h->d_out);
-    cudaFree(h->d_fields);
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->stage_ev) cudaEventDestroy(h->stage_ev);
-    if (h->h_stage) cudaFreeHost(h->h_stage);
+    if (h->up_ev) cudaEventDestroy(h->up_ev);
+    pinned_put(h->h_stage, h->stage_cap);
+    pinned_put(h->h_up, h->up_cap);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -408,34 +489,40 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     }
     TRY(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
     if (h->tb) TRY(step2_prepare(), "configuring the two-step kernels");
+    prepare_pool(h->dev);
     h->buf_bytes = g->precision == LBM_EM_F16DEV ? f16_buffer_bytes(h->pstride)
                                                   : (size_t)NPLANES * h->pstride * h->elem;
     const size_t bytes = h->buf_bytes;
     for (int b = 0; b < 2; ++b) {
-        TRY(cudaMalloc(&h->buf[b], bytes), "cudaMalloc(distributions)");
+        TRY(dev_alloc(h, &h->buf[b], bytes), "allocating the distributions");
         TRY(cudaMemsetAsync(h->buf[b], 0, bytes, h->stream), "cudaMemset");
     }
-    TRY(cudaMalloc(&h->d_mat, h->pstride), "cudaMalloc(material)");
+    TRY(dev_alloc(h, &h->d_mat, h->pstride), "allocating the material ids");
     TRY(cudaMemsetAsync(h->d_mat, 0, h->pstride, h->stream), "cudaMemset");
-    TRY(cudaMalloc(&h->d_mtab, 256 * sizeof(MatT<double>)), "cudaMalloc(table)");
-    TRY(cudaMalloc(&h->d_time, 2 * sizeof(long long)), "cudaMalloc(time)");
+    TRY(dev_alloc(h, &h->d_mtab, 256 * sizeof(MatT<double>)), "allocating the material table");
+    TRY(dev_alloc(h, &h->d_time, 2 * sizeof(long long)), "allocating the time words");
     TRY(cudaMemsetAsync(h->d_time, 0, 2 * sizeof(long long), h->stream), "cudaMemset");
-    TRY(cudaMalloc(&h->d_err, sizeof(unsigned)), "cudaMalloc(err)");
+    TRY(dev_alloc(h, &h->d_err, sizeof(unsigned)), "allocating the error word");
     TRY(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream), "cudaMemset");
-    TRY(cudaMalloc(&h->d_out, 4 * sizeof(double)), "cudaMalloc(out)");
-    TRY(cudaMallocHost(&h->h_stage, 256 * sizeof(MatT<double>)), "cudaMallocHost(table staging)");
+    TRY(dev_alloc(h, &h->d_out, 4 * sizeof(double)), "allocating the results");
+    TRY(pinned_get(256 * sizeof(MatT<double>), &h->h_stage, &h->stage_cap), "cudaMallocHost(table staging)");
     TRY(cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming), "cudaEventCreate");
     TRY(cudaEventRecord(h->stage_ev, h->stream), "cudaEventRecord");
+    TRY(cudaEventCreateWithFlags(&h->up_ev, cudaEventDisableTiming), "cudaEventCreate");
+    TRY(cudaEventRecord(h->up_ev, h->stream), "cudaEventRecord");
     std::vector<double2> cs = phase_table(s->period_steps);
-    TRY(cudaMalloc(&h->d_cs, cs.size() * sizeof(double2)), "cudaMalloc(phase table)");
-    TRY(cudaMemcpyAsync(h->d_cs, cs.data(), cs.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream),
+    TRY(dev_alloc(h, &h->d_cs, cs.size() * sizeof(double2)), "allocating the phase table");
+    void *up = nullptr;
+    TRY(upload_staging(h, cs.size() * sizeof(double2), &up), "pinned staging");
+    std::memcpy(up, cs.data(), cs.size() * sizeof(double2));
+    TRY(cudaMemcpyAsync(h->d_cs, up, cs.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream),
         "cudaMemcpy(phase table)");
+    TRY(cudaEventRecord(h->up_ev, h->stream), "cudaEventRecord");
     h->src.kind = s->kind;
     h->src.period = s->period_steps;
     h->src.ramp = s->ramp_steps;
     incident_constants(s->period_steps, s->E0, &h->src.pr, &h->src.pi, &h->src.qr, &h->src.qi);
     h->src.cs = h->d_cs;
-    TRY(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
 #undef TRY
     *out = h;
     return LBM_EM_OK;
@@ -506,9 +593,15 @@ lbm_em_status lbm_em_create(const lbm_em_grid *g, const double *eps_map, const u
     if (st) return st;
     std::memcpy(h->eps_table, eps_tab, sizeof(eps_tab));
     std::memcpy(h->pec_id, pec_tab, sizeof(pec_tab));
-    st = cuda_status(cudaMemcpy2DAsync(h->d_mat, h->pitch, idv.data(), h->nx, h->nx, h->ny, cudaMemcpyHostToDevice,
-                                       h->stream),
-                     "uploading material ids");
+    void *up = nullptr;
+    st = cuda_status(upload_staging(h, n, &up), "pinned staging");
+    if (!st) {
+        std::memcpy(up, idv.data(), n);
+        st = cuda_status(cudaMemcpy2DAsync(h->d_mat, h->pitch, up, h->nx, h->nx, h->ny, cudaMemcpyHostToDevice,
+                                           h->stream),
+                         "uploading material ids");
+    }
+    if (!st) st = cuda_status(cudaEventRecord(h->up_ev, h->stream), "cudaEventRecord");
     if (!st) st = upload_table(h);
     if (st) {
         free_handle(h);
@@ -623,39 +716,57 @@ lbm_em_status lbm_em_set_contour(lbm_em_t *h, const lbm_em_contour *c) {
     ch.E0 = h->srccfg.E0;
     lbm_em_status st = build_contour(h->nx, h->ny, c, &ch);
     if (st) return st;
-    st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
-    if (st) return st;
+    // everything below is ordered on the handle's stream: the old buffers are released
+    // after the steps already queued, and the host does not wait for them
     free_contour(h);
     h->contour = *c;
     h->ch = ch;
-    std::vector<int> slot_map(h->pstride, -1);
-    for (int s = 0; s < ch.n_slots; ++s)
-        slot_map[(size_t)ch.site_xy[2 * s + 1] * h->pitch + ch.site_xy[2 * s]] = s;
-    st = cuda_status(cudaMalloc(&h->d_slot, h->pstride * sizeof(int)), "cudaMalloc(slots)");
-    if (!st) st = cuda_status(cudaMalloc(&h->d_acc, (size_t)ch.n_slots * 6 * sizeof(double)), "cudaMalloc(acc)");
-    if (!st) st = cuda_status(cudaMalloc(&h->d_pts, ch.pts.size() * sizeof(ContourPt)), "cudaMalloc(contour)");
-    if (!st)
-        st = cuda_status(cudaMemcpy(h->d_slot, slot_map.data(), h->pstride * sizeof(int), cudaMemcpyHostToDevice),
+    // slot map: -1 everywhere, the stencil slots only in rows y0..y1 (the kernels read the
+    // map in those rows only), uploaded as one band
+    const int y0 = std::max(ch.y0, 0), y1 = std::min(ch.y1, h->ny - 1);
+    const size_t band = y1 >= y0 ? (size_t)(y1 - y0 + 1) * h->pitch : 0;
+    std::vector<double2> inc(ch.n_slots, make_double2(0.0, 0.0));
+    if (h->srccfg.kind != LBM_EM_SRC_NONE) {
+        // incident phasor i E0 e^{i k x} of the lattice's plane wave at each stencil site
+        // (far field: E_z^I for TM, H_z^I for TE)
+        const double k = lattice_wavenumber(h->srccfg.period_steps);
+        for (int s = 0; s < ch.n_slots; ++s) {
+            const double kx = k * (double)ch.site_xy[2 * s];
+            inc[s] = make_double2(-h->srccfg.E0 * std::sin(kx), h->srccfg.E0 * std::cos(kx));
+        }
+    }
+    const size_t b_slot = band * sizeof(int), b_pts = ch.pts.size() * sizeof(ContourPt),
+                 b_inc = inc.size() * sizeof(double2);
+    const size_t o_pts = (b_slot + 255) / 256 * 256, o_inc = o_pts + (b_pts + 255) / 256 * 256;
+    st = cuda_status(dev_alloc(h, &h->d_slot, h->pstride * sizeof(int)), "allocating the slot map");
+    if (!st) st = cuda_status(dev_alloc(h, &h->d_acc, (size_t)ch.n_slots * 6 * sizeof(double)), "allocating acc");
+    if (!st) st = cuda_status(dev_alloc(h, &h->d_pts, b_pts), "allocating the contour");
+    if (!st) st = cuda_status(dev_alloc(h, &h->d_inc, b_inc), "allocating the incident table");
+    char *up = nullptr;
+    if (!st) st = cuda_status(upload_staging(h, o_inc + b_inc, (void **)&up), "pinned staging");
+    if (!st) {
+        int *sl = (int *)up;
+        std::fill(sl, sl + band, -1);
+        for (int s = 0; s < ch.n_slots; ++s)
+            sl[(size_t)(ch.site_xy[2 * s + 1] - y0) * h->pitch + ch.site_xy[2 * s]] = s;
+        std::memcpy(up + o_pts, ch.pts.data(), b_pts);
+        std::memcpy(up + o_inc, inc.data(), b_inc);
+        st = cuda_status(cudaMemsetAsync(h->d_slot, 0xff, h->pstride * sizeof(int), h->stream), "clearing slots");
+    }
+    if (!st && band)
+        st = cuda_status(cudaMemcpyAsync(h->d_slot + (size_t)y0 * h->pitch, up, b_slot, cudaMemcpyHostToDevice,
+                                         h->stream),
                          "uploading slots");
     if (!st)
-        st = cuda_status(cudaMemcpy(h->d_pts, ch.pts.data(), ch.pts.size() * sizeof(ContourPt), cudaMemcpyHostToDevice),
+        st = cuda_status(cudaMemcpyAsync(h->d_pts, up + o_pts, b_pts, cudaMemcpyHostToDevice, h->stream),
                          "uploading contour");
-    if (!st) st = cuda_status(cudaMemset(h->d_acc, 0, (size_t)ch.n_slots * 6 * sizeof(double)), "clearing acc");
-    if (!st) {
-        // incident E_z phasor i E0 e^{i k x} of the lattice's plane wave at each stencil site
-        std::vector<double2> inc(ch.n_slots, make_double2(0.0, 0.0));
-        if (h->srccfg.kind != LBM_EM_SRC_NONE) {
-            const double k = lattice_wavenumber(h->srccfg.period_steps);
-            for (int s = 0; s < ch.n_slots; ++s) {
-                const double kx = k * (double)ch.site_xy[2 * s];
-                inc[s] = make_double2(-h->srccfg.E0 * std::sin(kx), h->srccfg.E0 * std::cos(kx));
-            }
-        }
-        st = cuda_status(cudaMalloc(&h->d_inc, inc.size() * sizeof(double2)), "cudaMalloc(incident)");
-        if (!st)
-            st = cuda_status(cudaMemcpy(h->d_inc, inc.data(), inc.size() * sizeof(double2), cudaMemcpyHostToDevice),
-                             "uploading incident");
-    }
+    if (!st)
+        st = cuda_status(cudaMemcpyAsync(h->d_inc, up + o_inc, b_inc, cudaMemcpyHostToDevice, h->stream),
+                         "uploading incident");
+    if (!st) st = cuda_status(cudaEventRecord(h->up_ev, h->stream), "cudaEventRecord");
+    if (!st)
+        st = cuda_status(cudaMemsetAsync(h->d_acc, 0, (size_t)ch.n_slots * 6 * sizeof(double), h->stream),
+                         "clearing acc");
     if (st) {
         free_contour(h);
         return st;
@@ -722,7 +833,7 @@ lbm_em_status lbm_em_far_field(lbm_em_t *h, const double *angles, int32_t n_angl
     if (!h->has_contour || h->n_acc <= 0) return set_error(LBM_EM_ESTATE, "no accumulated steps");
     cudaSetDevice(h->dev);
     double *d = nullptr;
-    lbm_em_status st = cuda_status(cudaMalloc(&d, (size_t)n_angles * 4 * sizeof(double)), "cudaMalloc(far field)");
+    lbm_em_status st = cuda_status(dev_alloc(h, &d, (size_t)n_angles * 4 * sizeof(double)), "allocating the far field");
     if (st) return st;
     double *d_ang = d + 3 * (size_t)n_angles;
     std::vector<double> res(3 * (size_t)n_angles);
@@ -737,7 +848,7 @@ lbm_em_status lbm_em_far_field(lbm_em_t *h, const double *angles, int32_t n_angl
         st = cuda_status(cudaMemcpyAsync(res.data(), d, res.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
                          "reading far field");
     if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
-    cudaFree(d);
+    dev_free(h, d);
     if (st) return st;
     for (int j = 0; j < n_angles; ++j) s2[j] = res[3 * (size_t)j];
     return LBM_EM_OK;
@@ -805,7 +916,7 @@ lbm_em_status lbm_em_get_fields(lbm_em_t *h, double *ez, double *hx, double *hy)
     cudaSetDevice(h->dev);
     const size_t n = (size_t)h->nx * h->ny;
     lbm_em_status st = LBM_EM_OK;
-    if (!h->d_fields) st = cuda_status(cudaMalloc(&h->d_fields, 3 * n * sizeof(double)), "cudaMalloc(fields)");
+    if (!h->d_fields) st = cuda_status(dev_alloc(h, &h->d_fields, 3 * n * sizeof(double)), "allocating the fields");
     if (st) return st;
     const int p = h->cur;
     cudaError_t e;
