@@ -24,6 +24,7 @@
 #include "common.cuh"
 #include "launchers.h"
 #include "runtime.h"
+#include "step2.cuh"
 
 using namespace lbmem;
 
@@ -135,6 +136,100 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
     }
 }
 
+// Fourier accumulation of one site of an instance at time t (its slot map and accumulators).
+__device__ __forceinline__ void batch_acc(const double *f3, const int *slot, double *acc, const InstDesc &d,
+                                          size_t idx, long long t) {
+    const int s = slot[d.slot_base + idx];
+    if (s < 0) return;
+    const double2 c = d.src.cs[(int)(t % (long long)d.period)];
+    double *q = acc + 6 * ((size_t)d.acc_base + s);
+    q[0] += f3[0] * c.x;
+    q[1] += f3[0] * c.y;
+    q[2] += f3[1] * c.x;
+    q[3] += f3[1] * c.y;
+    q[4] += f3[2] * c.x;
+    q[5] += f3[2] * c.y;
+}
+
+// Two steps per launch for the FP32 batch with fixed run lengths (temporal blocking as in
+// step2.cu): each TW x TH tile of an instance is advanced to t + 1 together with a
+// one-site halo into shared memory, then to t + 2 from there, so the packed state crosses
+// HBM once per two steps.  The per-site arithmetic is the one-step kernel's (same bits).
+// An instance whose run ends at t + 1 takes only the first step (its state is not needed
+// afterwards; its forces come from the accumulators).  Convergence exits need a decision
+// between any two steps, so they keep the one-step kernel.
+__global__ void __launch_bounds__(NT, 4) k_batch_step2(const BatchArgs<float> b, const long long *__restrict__ t_in,
+                                                    long long *__restrict__ t_out) {
+    extern __shared__ float sm[];
+    __shared__ MatT<float> smat[3];
+    __shared__ double ssrc[4];  // source values of t and t + 1 (tiles at x = 0)
+    const long long t = *t_in;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + 2;
+    for (int tile = blockIdx.x; tile < b.n_tiles; tile += gridDim.x) {
+        const Tile tl = b.tiles[tile];
+        const InstDesc &d = b.inst[tl.inst];
+        if (t >= d.steps) continue;  // uniform over the block
+        const bool two = t + 1 < d.steps;
+        __syncthreads();             // the previous tile is done with the shared memory
+        if (threadIdx.x < 3)
+            smat[threadIdx.x] = MatT<float>{(float)d.mtab[threadIdx.x][0], (float)d.mtab[threadIdx.x][1],
+                                            (float)d.mtab[threadIdx.x][2], (float)d.mtab[threadIdx.x][3]};
+        if (threadIdx.x == 32) {
+            ssrc[0] = ssrc[1] = ssrc[2] = ssrc[3] = 0.0;
+            if (tl.x0 == 0 && d.src.kind != SRC_NONE) {
+                if (t >= 1) source_values(d.src, t, &ssrc[0], &ssrc[1]);
+                source_values(d.src, t + 1, &ssrc[2], &ssrc[3]);
+            }
+        }
+        __syncthreads();
+        StepArgs<float> a;
+        a.nx = d.nx;
+        a.ny = d.ny;
+        a.pitch = d.pitch;
+        a.pstride = d.pstride;
+        const float *fin = b.fin + d.base;
+        float *fout = b.fout + d.base;
+        const uint8_t *mat = b.mat + d.mat_base;
+        const bool src0 = t >= 1 && d.src.kind != SRC_NONE, src1 = d.src.kind != SRC_NONE;
+        for (int k = threadIdx.x; k < SW * SH; k += NT) {
+            const int lx = k % SW, ly = k / SW, x = tl.x0 - 1 + lx, y = tl.y0 - 1 + ly;
+            if (x < 0 || x >= d.nx || y < 0 || y >= d.ny) continue;
+            const bool interior = lx >= 1 && lx <= TW && ly >= 1 && ly <= TH;
+            if (!two && !interior) continue;
+            Pop<float> p;
+            pull_planes(a, fin, x, y, p);
+            if (x == 0 && src0) inject_source(d.src.kind, ssrc[0], ssrc[1], p);
+            const size_t idx = (size_t)y * d.pitch + x;
+            const bool acc = interior && t >= d.acc_from && y >= d.y0 && y <= d.y1;
+            double f3[3];
+            if (update_site<POL_TM, true>(p, smat[mat[idx]], acc ? f3 : nullptr, nullptr))
+                atomicOr(b.err + tl.inst, 1u);
+            if (acc) batch_acc(f3, b.slot, b.acc, d, idx, t);
+            if (two)
+                put_smem(sm, ly, lx, p);
+            else
+                store_site(fout, d.pstride, idx, p);
+        }
+        if (!two) continue;
+        __syncthreads();
+        const bool acc1 = t + 1 >= d.acc_from;
+        for (int k = threadIdx.x; k < TW * TH; k += NT) {
+            const int lx = k % TW, ly = k / TW, x = tl.x0 + lx, y = tl.y0 + ly;
+            if (x >= d.nx || y >= d.ny) continue;
+            Pop<float> p;
+            pull_smem(sm, d.nx, d.ny, x, y, lx + 1, ly + 1, p);
+            if (x == 0 && src1) inject_source(d.src.kind, ssrc[2], ssrc[3], p);
+            const size_t idx = (size_t)y * d.pitch + x;
+            const bool acc = acc1 && y >= d.y0 && y <= d.y1;
+            double f3[3];
+            if (update_site<POL_TM, true>(p, smat[mat[idx]], acc ? f3 : nullptr, nullptr))
+                atomicOr(b.err + tl.inst, 1u);
+            if (acc) batch_acc(f3, b.slot, b.acc, d, idx, t + 1);
+            store_site(fout, d.pstride, idx, p);
+        }
+    }
+}
+
 // After a step of time t (*t_next = t + 1): every instance at a period boundary compares
 // its energy with the previous boundary's (Sec. III convergence criterion); once two
 // successive changes are <= tol * W and at least min_periods - 1 periods have run, the
@@ -239,6 +334,7 @@ struct lbm_em_batch {
     long long *d_time = nullptr;
     unsigned *d_err = nullptr;
     int tile_w = 0, tile_h = 0, ctas = 0;
+    bool two = false;  // two steps per launch (FP32, fixed run lengths; TW x TH tiles)
     cudaGraphExec_t graph = nullptr;
     bool ran = false;
     // convergence exits
@@ -314,8 +410,9 @@ static cudaError_t batch_rasterize(lbm_em_batch *b) {
     return cudaSuccess;
 }
 
-static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, long long t) {
-    const int p = (int)(t & 1);
+// One launch from the state in buf[p] (time word p) to buf[1 - p]: one step, or two with
+// b->two.  The caller alternates p launch by launch.
+static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, int p) {
     const int grid = b->ctas * b->sms;
     if (b->prec == LBM_EM_F64) {
         BatchArgs<double> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, ilog2(b->tile_w),
@@ -326,7 +423,10 @@ static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, long long t) {
         BatchArgs<float> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, ilog2(b->tile_w),
                            (const float *)b->buf[p], (float *)b->buf[1 - p], b->d_mat, b->d_slot,
                            b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
-        k_batch_step<float><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
+        if (b->two)
+            k_batch_step2<<<grid, NT, kStep2Smem, s>>>(a, b->d_time + p, b->d_time + (1 - p));
+        else
+            k_batch_step<float><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && b->conv_tol > 0.0) {
@@ -334,6 +434,15 @@ static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, long long t) {
                                                            b->d_time + (1 - p), b->conv_tol, b->min_periods, b->n);
         e = cudaGetLastError();
     }
+    return e;
+}
+
+// A single step with the one-step kernel (the odd tail of a two-step run).
+static cudaError_t batch_launch_one(lbm_em_batch *b, cudaStream_t s, int p) {
+    const bool two = b->two;
+    b->two = false;
+    cudaError_t e = batch_launch(b, s, p);
+    b->two = two;
     return e;
 }
 
@@ -354,10 +463,13 @@ static lbm_em_status batch_clear(lbm_em_batch *b) {
     return st;
 }
 
-// Time a few steps of each (tile shape, CTAs per SM) candidate from the cleared state.
+// Time a few steps of each (tile shape, CTAs per SM, steps per launch) candidate from the
+// cleared state; two steps per launch (TW x TH tiles) is a candidate for FP32 runs of
+// fixed length.
 static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int want_c) {
     struct Cand {
         int w, h, c;
+        bool two;
     };
     std::vector<Cand> cands;
     const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 8}, {128, 4}, {256, 2}, {128, 8}, {256, 4}};
@@ -367,11 +479,15 @@ static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int
             if (want_w && sh[0] != want_w) continue;
             if (want_h && sh[1] != want_h) continue;
             if (want_c && c != want_c) continue;
-            cands.push_back(Cand{sh[0], sh[1], c});
+            cands.push_back(Cand{sh[0], sh[1], c, false});
         }
-    if (cands.empty()) cands.push_back(Cand{want_w ? want_w : 64, want_h ? want_h : 4, want_c ? want_c : 4});
+    if (b->prec == LBM_EM_F32 && b->conv_tol <= 0.0 && (!want_w || want_w == TW) && (!want_h || want_h == TH))
+        for (int c : {2, 3, 4})
+            if (!want_c || want_c == c) cands.push_back(Cand{TW, TH, c, true});
+    if (cands.empty()) cands.push_back(Cand{want_w ? want_w : 64, want_h ? want_h : 4, want_c ? want_c : 4, false});
     if (cands.size() == 1) {
         b->ctas = cands[0].c;
+        b->two = cands[0].two;
         return batch_tiles(b, cands[0].w, cands[0].h);
     }
     cudaEvent_t e0, e1;
@@ -379,17 +495,19 @@ static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int
     cudaEventCreate(&e1);
     float best = 1e30f;
     Cand bc = cands[0];
-    const int trial = 4;
+    const int trial = 4;  // steps timed per candidate
     lbm_em_status st = LBM_EM_OK;
     for (const Cand &c : cands) {
         st = batch_tiles(b, c.w, c.h);
         if (st) break;
         b->ctas = c.c;
+        b->two = c.two;
         st = batch_clear(b);
         if (st) break;
+        const int launches = c.two ? trial / 2 : trial;
         cudaError_t e = batch_launch(b, b->stream, 0);  // warm-up
         cudaEventRecord(e0, b->stream);
-        for (int k = 1; k <= trial && e == cudaSuccess; ++k) e = batch_launch(b, b->stream, k);
+        for (int k = 1; k <= launches && e == cudaSuccess; ++k) e = batch_launch(b, b->stream, k & 1);
         cudaEventRecord(e1, b->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         st = cuda_status(e, "autotune launch");
@@ -405,6 +523,7 @@ static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int
     cudaEventDestroy(e1);
     if (st) return st;
     b->ctas = bc.c;
+    b->two = bc.two;
     st = batch_tiles(b, bc.w, bc.h);
     if (!st) st = batch_clear(b);
     return st;
@@ -597,14 +716,24 @@ lbm_em_status lbm_em_batch_run(lbm_em_batch_t *b) {
         st = cuda_status(e, "cudaGraphInstantiate");
         if (st) return st;
     }
+    // the graph holds two launches (state buf[0] -> buf[1] -> buf[0]): 2 steps, or 4 with
+    // two steps per launch; the tail runs at most one two-step and one one-step launch
+    const long long per_graph = b->two ? 4 : 2;
     long long t = 0;
-    while (t + 2 <= b->max_steps) {
+    int p = 0;
+    while (t + per_graph <= b->max_steps) {
         st = cuda_status(cudaGraphLaunch(b->graph, b->stream), "cudaGraphLaunch");
         if (st) return st;
+        t += per_graph;
+    }
+    if (b->two && t + 2 <= b->max_steps) {
+        st = cuda_status(batch_launch(b, b->stream, p), "batch step");
+        if (st) return st;
+        p ^= 1;
         t += 2;
     }
     if (t < b->max_steps) {
-        st = cuda_status(batch_launch(b, b->stream, t), "batch step");
+        st = cuda_status(batch_launch_one(b, b->stream, p), "batch step");
         if (st) return st;
     }
     k_batch_contour<<<b->n, 256, 0, b->stream>>>(b->d_cdesc, b->d_pts, b->d_acc, b->d_out);

@@ -18,45 +18,6 @@
 
 namespace lbmem {
 
-constexpr int TW = 64, TH = 14, SW = TW + 2, SH = TH + 2, NT = 256;
-constexpr size_t kStep2Smem = (size_t)NPLANES * SH * SW * sizeof(float);
-
-__device__ __forceinline__ float &smv(float *sm, int plane, int ly, int lx) {
-    return sm[(plane * SH + ly) * SW + lx];
-}
-
-__device__ __forceinline__ void put_smem(float *sm, int ly, int lx, const Pop<float> &p) {
-    smv(sm, P_EZ, ly, lx) = p.ez;
-    smv(sm, P_EPX, ly, lx) = p.epx;
-    smv(sm, P_EMX, ly, lx) = p.emx;
-    smv(sm, P_EPY, ly, lx) = p.epy;
-    smv(sm, P_EMY, ly, lx) = p.emy;
-    smv(sm, P_HXPX, ly, lx) = p.hxpx;
-    smv(sm, P_HXMX, ly, lx) = p.hxmx;
-    smv(sm, P_HXZ, ly, lx) = p.hxz;
-    smv(sm, P_HYPY, ly, lx) = p.hypy;
-    smv(sm, P_HYMY, ly, lx) = p.hymy;
-    smv(sm, P_HYZ, ly, lx) = p.hyz;
-}
-
-// f_i(r, t + 1) from the shared-memory f*(t); (cx, cy) is the site's cell in the tile
-// with halo, the upstream cell is clamped at the lattice edge exactly as pull_site does.
-__device__ __forceinline__ void pull_smem(float *sm, int nx, int ny, int x, int y, int cx, int cy, Pop<float> &p) {
-    const int xm = x > 0 ? cx - 1 : cx, xp = x < nx - 1 ? cx + 1 : cx;
-    const int ym = y > 0 ? cy - 1 : cy, yp = y < ny - 1 ? cy + 1 : cy;
-    p.ez = smv(sm, P_EZ, cy, cx);
-    p.epx = smv(sm, P_EPX, cy, xm);
-    p.emx = smv(sm, P_EMX, cy, xp);
-    p.epy = smv(sm, P_EPY, ym, cx);
-    p.emy = smv(sm, P_EMY, yp, cx);
-    p.hxpx = smv(sm, P_HXPX, cy, xm);
-    p.hxmx = smv(sm, P_HXMX, cy, xp);
-    p.hxz = smv(sm, P_HXZ, cy, cx);
-    p.hypy = smv(sm, P_HYPY, ym, cx);
-    p.hymy = smv(sm, P_HYMY, yp, cx);
-    p.hyz = smv(sm, P_HYZ, cy, cx);
-}
-
 // Source values of the two times of a launch (t, t + 1), evaluated once per block by one
 // thread of the blocks that own column 0 (see pull_site for why not per site).
 struct SrcPair {

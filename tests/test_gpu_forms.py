@@ -115,6 +115,29 @@ def test_batch_explicit_configuration():
     b.close()
 
 
+def test_batch_two_steps_per_launch_is_bit_identical():
+    """The FP32 batch with two steps per launch (64 x 14 tiles, halo in shared memory)
+    gives the same bits as the one-step batch kernel, for uneven sizes and run lengths
+    (odd step counts end with a one-step launch), and matches the single-domain runs."""
+    insts = _batch_instances()
+    insts[0] = dict(insts[0], period=61, ramp=61)    # 305 steps: the run ends with one step
+    insts[1] = dict(insts[1], period=45, ramp=45)    # 135 steps: a launch's second step is skipped
+    b2 = L.Batch(insts, "f32", tile_w=64, tile_h=14, ctas_per_sm=4)
+    b1 = L.Batch(insts, "f32", tile_w=64, tile_h=4, ctas_per_sm=4)
+    assert b2.config() == (64, 14, 4)
+    b2.run()
+    b1.run()
+    F2, s2 = b2.results()
+    F1, _ = b1.results()
+    assert (s2 == L.OK).all()
+    assert np.array_equal(F1, F2)
+    for i, inst in enumerate(insts):
+        ref = L.run_instance(inst, "f32")
+        assert np.max(np.abs(F2[i] - ref)) < 1e-12 * np.sum(np.abs(ref))
+    b1.close()
+    b2.close()
+
+
 def test_batch_reports_unstable_instance():
     insts = _batch_instances()[:2]
     b = L.Batch(insts, "f32")
