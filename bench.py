@@ -32,7 +32,8 @@ METRIC = "MLUPS & HBM GB/s (% of peak) per precision form; design-map cells/sec 
 WORKLOAD = "md_janus_512"
 # algorithmic bytes per lattice update: the 11 stored planes read and written once, plus
 # the 1-byte material id (FP16-deviation: 11 FP16 deviations + 3 FP32 fields each way)
-BYTES_PER_LU = {"f64": 11 * 8 * 2 + 1, "f32": 11 * 4 * 2 + 1, "f16dev": 2 * (11 * 2 + 3 * 4) + 1}
+BYTES_PER_LU = {"f64": 11 * 8 * 2 + 1, "f32": 11 * 4 * 2 + 1, "f16dev": 2 * (11 * 2 + 3 * 4) + 1,
+                "f32x2": 11 * 8 * 2 + 1}
 STEP_KERNEL = {"f64": "k_step<double, false, TM>", "f32": "k_step<float, false, TM>", "f16dev": "k_step_f16<false>"}
 # FP64 pipe operations per lattice update of the step kernel: 12 for the moments
 # (sums of 5, 5 and 5 stored populations, one scaling), 16 for the equilibria and 2 f^eq - f
@@ -424,7 +425,7 @@ def main():
 
     if not args.no_forms and rank == 0:
         forms = {}
-        for fp in ("f32", "f16dev", "f64"):
+        for fp in ("f32", "f16dev", "f32x2", "f64"):
             if fp == prec:
                 forms[fp] = {"mlups": out["value"] / world, "step_kernel_gbs": round(achieved, 1),
                              "frac_hbm": round(achieved / peak, 4)}
@@ -474,15 +475,17 @@ def main():
         hs = {}
         # TE^z lines: the same lattice and kernels with the TE moments and collision
         for fp, mode, pol in (("f32", "auto", "tm"), ("f32", "one", "tm"), ("f16dev", "auto", "tm"),
-                              ("f16dev", "two", "tm"), ("f64", "auto", "tm"), ("f32", "auto", "te"),
-                              ("f64", "auto", "te")):
+                              ("f16dev", "two", "tm"), ("f64", "auto", "tm"), ("f32x2", "auto", "tm"),
+                              ("f32x2", "two", "tm"), ("f32", "auto", "te"), ("f64", "auto", "te")):
             key = fp + {"auto": "", "one": "_one_step_per_launch", "two": "_two_steps_per_launch"}[mode]
             key += "_te" if pol == "te" else ""
             P = "TE" if pol == "te" else "TM"
-            kern = {("f32", "auto"): f"k_step2_f32<false, {P}> (two steps per launch)",
+            kern = {("f32", "auto"): f"k_step2<float, false, {P}> (two steps per launch)",
                     ("f32", "one"): f"k_step<float, false, {P}>", ("f16dev", "auto"): "k_step_f16<false>",
                     ("f16dev", "two"): "k_step2_f16<false> (two steps per launch)",
-                    ("f64", "auto"): f"k_step<double, false, {P}>"}[(fp, mode)]
+                    ("f64", "auto"): f"k_step<double, false, {P}>",
+                    ("f32x2", "auto"): f"k_step<df, false, {P}> (double-float)",
+                    ("f32x2", "two"): f"k_step2<df, false, {P}> (double-float, two steps per launch)"}[(fp, mode)]
             with L.solver_for_instance(big, fp, main, steps_per_launch=mode, polarization=pol) as s:
                 s.step(4)
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -512,7 +515,7 @@ def main():
         # force error against the same batch in FP64
         dm = W.design_map_256(4, args.design_map_instances)
         res = {}
-        for fp in ("f32", "f64"):
+        for fp in ("f32", "f32x2", "f64"):
             bt = L.Batch(dm, fp, stream=main)
             if fp == "f32":            # untimed first run (graph capture, first touch)
                 bt.run()
@@ -527,12 +530,16 @@ def main():
             bt.close()
         ms32, F32, cfg = res["f32"]
         ms64, F64, _ = res["f64"]
+        msx2, FX2, _ = res["f32x2"]
         errs = np.max(np.abs(F32 - F64), axis=1) / np.abs(F64[:, 0])
         lus = sum(instance_lus(i) for i in dm)
         out["design_map"] = {"instances": len(dm), "cells_per_s": round(len(dm) / (ms32 / 1e3), 2),
                              "mlups": round(lus / (ms32 / 1e3) / 1e6, 1), "ms": round(ms32, 1),
                              "fp64_cells_per_s": round(len(dm) / (ms64 / 1e3), 2),
                              "fp64_mlups": round(lus / (ms64 / 1e3) / 1e6, 1), "fp64_ms": round(ms64, 1),
+                             "f32x2_cells_per_s": round(len(dm) / (msx2 / 1e3), 2),
+                             "f32x2_max_force_err_drag_scale":
+                                 float((np.max(np.abs(FX2 - F64), axis=1) / np.abs(F64[:, 0])).max()),
                              "max_force_err_drag_scale": float(errs.max()),
                              "instances_within_1e-3": int(np.sum(errs <= 1e-3)),
                              "tile_w": cfg[0], "tile_h": cfg[1], "ctas_per_sm": cfg[2],

@@ -51,8 +51,14 @@ typedef enum {
     LBM_EM_F64 = 0,      /* 11 FP64 populations per site (the independent part of the
                             TM^z state; the other five follow from exact invariants)    */
     LBM_EM_F32 = 1,      /* 11 FP32 populations per site                                */
-    LBM_EM_F16DEV = 2    /* FP32 fields (E_z/3, H_x/3, H_y/3) + 11 FP16 scaled
+    LBM_EM_F16DEV = 2,   /* FP32 fields (E_z/3, H_x/3, H_y/3) + 11 FP16 scaled
                             deviations f - f^eq per site                                */
+    LBM_EM_F32X2 = 3     /* 11 double-float populations per site: pairs of FP32 (hi + lo,
+                            ~48 significant bits, FP32 exponent range), FP32-pipe
+                            arithmetic by error-free transformations; FP64-class results
+                            (the FP64 parity bound holds) at HBM-bound speed on GB300,
+                            whose FP64 pipe is 1/64 of its FP32 rate.  Not an IEEE
+                            binary64 computation; one step per launch, single domain.  */
 } lbm_em_precision;
 
 /* Left-edge plane-wave source (Sec. III: the wave enters through the left boundary, the
@@ -268,7 +274,7 @@ typedef struct {
 } lbm_em_instance;
 
 typedef struct {
-    int32_t precision;       /* LBM_EM_F32 or LBM_EM_F64                                    */
+    int32_t precision;       /* LBM_EM_F32, LBM_EM_F64 or LBM_EM_F32X2                      */
     int32_t tile_w, tile_h;  /* tile shape (tile_w 32/64/128/256, tile_h <= 16); 0: autotuned.
                                 64 x 14 is the shape of the two-steps-per-launch kernel (FP32,
                                 conv_tol 0: each tile advances two steps with its halo in

@@ -319,6 +319,9 @@ static cudaError_t enqueue_step(lbm_em *h, bool acc, cudaStream_t s, int p) {
     if (h->prec == LBM_EM_F64)
         return launch_step<double>(make_args<double>(h), (const double *)h->buf[p], (double *)h->buf[1 - p],
                                    h->d_time + p, h->d_time + (1 - p), acc, s);
+    if (h->prec == LBM_EM_F32X2)
+        return launch_step<df>(make_args<df>(h), (const df *)h->buf[p], (df *)h->buf[1 - p], h->d_time + p,
+                               h->d_time + (1 - p), acc, s);
     return launch_step<float>(make_args<float>(h), (const float *)h->buf[p], (float *)h->buf[1 - p],
                               h->d_time + p, h->d_time + (1 - p), acc, s);
 }
@@ -327,8 +330,11 @@ static cudaError_t enqueue_step(lbm_em *h, bool acc, cudaStream_t s, int p) {
 static cudaError_t enqueue_step2(lbm_em *h, bool acc, cudaStream_t s, int p) {
     if (h->prec == LBM_EM_F16DEV)
         return launch_step2_f16(make_f16_args(h, p), h->d_time + p, h->d_time + (1 - p), acc, s);
-    return launch_step2_f32(make_args<float>(h), (const float *)h->buf[p], (float *)h->buf[1 - p], h->d_time + p,
-                            h->d_time + (1 - p), acc, s);
+    if (h->prec == LBM_EM_F32X2)
+        return launch_step2<df>(make_args<df>(h), (const df *)h->buf[p], (df *)h->buf[1 - p], h->d_time + p,
+                                h->d_time + (1 - p), acc, s);
+    return launch_step2<float>(make_args<float>(h), (const float *)h->buf[p], (float *)h->buf[1 - p], h->d_time + p,
+                               h->d_time + (1 - p), acc, s);
 }
 
 // kGraphSteps steps starting from buffer 0 (an even number of launches, so the
@@ -442,8 +448,9 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     if ((g->flags & LBM_EM_FLAG_SINGLE_STEP) && (g->flags & LBM_EM_FLAG_TWO_STEP))
         return set_error(LBM_EM_EINVAL, "LBM_EM_FLAG_SINGLE_STEP and LBM_EM_FLAG_TWO_STEP exclude each other");
     if ((long long)g->nx * g->ny > (1LL << 31)) return set_error(LBM_EM_EINVAL, "lattice too large (> 2^31 sites)");
-    if (g->precision != LBM_EM_F64 && g->precision != LBM_EM_F32 && g->precision != LBM_EM_F16DEV)
-        return set_error(LBM_EM_EINVAL, "precision must be LBM_EM_F64, LBM_EM_F32 or LBM_EM_F16DEV");
+    if (g->precision != LBM_EM_F64 && g->precision != LBM_EM_F32 && g->precision != LBM_EM_F16DEV &&
+        g->precision != LBM_EM_F32X2)
+        return set_error(LBM_EM_EINVAL, "precision must be LBM_EM_F64, LBM_EM_F32, LBM_EM_F16DEV or LBM_EM_F32X2");
     lbm_em_status st = check_source(s);
     if (st) return st;
     int ndev = 0;
@@ -457,7 +464,7 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     h->ny = g->ny;
     h->prec = g->precision;
     h->pol = (g->flags & LBM_EM_FLAG_TE) ? POL_TE : POL_TM;
-    h->elem = g->precision == LBM_EM_F64 ? sizeof(double) : sizeof(float);
+    h->elem = (g->precision == LBM_EM_F64 || g->precision == LBM_EM_F32X2) ? 8 : sizeof(float);
     h->pitch = round_up(g->nx, 32);
     h->pstride = (size_t)h->pitch * (size_t)g->ny;
     h->srccfg = *s;
@@ -535,6 +542,10 @@ static lbm_em_status upload_table(lbm_em *h) {
     size_t bytes;
     if (h->prec == LBM_EM_F64) {
         auto tab = material_table<double>(h->eps_table, h->pec_id);
+        bytes = tab.size() * sizeof(tab[0]);
+        std::memcpy(h->h_stage, tab.data(), bytes);
+    } else if (h->prec == LBM_EM_F32X2) {
+        auto tab = material_table<df>(h->eps_table, h->pec_id);
         bytes = tab.size() * sizeof(tab[0]);
         std::memcpy(h->h_stage, tab.data(), bytes);
     } else {
@@ -866,6 +877,8 @@ lbm_em_status lbm_em_energy(lbm_em_t *h, double *W) {
             e = launch_energy_f16(make_f16_args(h, p), h->d_time + p, d, h->stream);
         else if (h->prec == LBM_EM_F64)
             e = launch_energy<double>(make_args<double>(h), (const double *)h->buf[p], h->d_time + p, d, h->stream);
+        else if (h->prec == LBM_EM_F32X2)
+            e = launch_energy<df>(make_args<df>(h), (const df *)h->buf[p], h->d_time + p, d, h->stream);
         else
             e = launch_energy<float>(make_args<float>(h), (const float *)h->buf[p], h->d_time + p, d, h->stream);
         st = cuda_status(e, "energy kernel");
@@ -926,6 +939,9 @@ lbm_em_status lbm_em_get_fields(lbm_em_t *h, double *ez, double *hx, double *hy)
     else if (h->prec == LBM_EM_F64)
         e = launch_fields<double>(make_args<double>(h), (const double *)h->buf[p], h->d_time + p, h->d_fields,
                                   h->d_fields + n, h->d_fields + 2 * n, h->stream);
+    else if (h->prec == LBM_EM_F32X2)
+        e = launch_fields<df>(make_args<df>(h), (const df *)h->buf[p], h->d_time + p, h->d_fields,
+                              h->d_fields + n, h->d_fields + 2 * n, h->stream);
     else
         e = launch_fields<float>(make_args<float>(h), (const float *)h->buf[p], h->d_time + p, h->d_fields,
                                  h->d_fields + n, h->d_fields + 2 * n, h->stream);
@@ -1019,11 +1035,17 @@ lbm_em_status lbm_em_load_state(lbm_em_t *h, const void *buf, size_t bytes) {
     cudaSetDevice(h->dev);
     const char *p = (const char *)buf + sizeof(hd);
     long long tt = hd.t;
-    lbm_em_status st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
-    if (!st) st = cuda_status(cudaMemcpy(h->buf[h->cur], p, dist, cudaMemcpyHostToDevice), "loading distributions");
-    if (!st && accb) st = cuda_status(cudaMemcpy(h->d_acc, p + dist, accb, cudaMemcpyHostToDevice), "loading acc");
+    // ordered on the handle's stream: a synchronous cudaMemcpy from pageable memory may
+    // return before its DMA has reached the device, and the handle's non-blocking stream
+    // would not wait for it
+    lbm_em_status st = cuda_status(
+        cudaMemcpyAsync(h->buf[h->cur], p, dist, cudaMemcpyHostToDevice, h->stream), "loading distributions");
+    if (!st && accb)
+        st = cuda_status(cudaMemcpyAsync(h->d_acc, p + dist, accb, cudaMemcpyHostToDevice, h->stream), "loading acc");
     if (!st)
-        st = cuda_status(cudaMemcpy(h->d_time + h->cur, &tt, sizeof(tt), cudaMemcpyHostToDevice), "loading time");
+        st = cuda_status(cudaMemcpyAsync(h->d_time + h->cur, &tt, sizeof(tt), cudaMemcpyHostToDevice, h->stream),
+                         "loading time");
+    if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (st) return st;
     h->t = hd.t;
     h->n_acc = hd.n_acc;

@@ -382,7 +382,8 @@ static lbm_em_status batch_tiles(lbm_em_batch *b, int tw, int th) {
     b->d_tiles = nullptr;
     lbm_em_status st = cuda_status(cudaMalloc(&b->d_tiles, tiles.size() * sizeof(Tile)), "cudaMalloc(tiles)");
     if (!st)
-        st = cuda_status(cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice),
+        st = cuda_status(cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
+                                         b->stream),
                          "uploading tiles");
     b->n_tiles = (int)tiles.size();
     b->tile_w = tw;
@@ -414,7 +415,12 @@ static cudaError_t batch_rasterize(lbm_em_batch *b) {
 // b->two.  The caller alternates p launch by launch.
 static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, int p) {
     const int grid = b->ctas * b->sms;
-    if (b->prec == LBM_EM_F64) {
+    if (b->prec == LBM_EM_F32X2) {
+        BatchArgs<df> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, ilog2(b->tile_w),
+                        (const df *)b->buf[p], (df *)b->buf[1 - p], b->d_mat, b->d_slot,
+                        b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
+        k_batch_step<df><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
+    } else if (b->prec == LBM_EM_F64) {
         BatchArgs<double> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, ilog2(b->tile_w),
                             (const double *)b->buf[p], (double *)b->buf[1 - p], b->d_mat, b->d_slot,
                             b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
@@ -535,8 +541,8 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
                                   lbm_em_batch_t **out) {
     if (!specs || n <= 0 || !o || !out) return set_error(LBM_EM_EINVAL, "bad batch arguments");
     *out = nullptr;
-    if (o->precision != LBM_EM_F32 && o->precision != LBM_EM_F64)
-        return set_error(LBM_EM_EINVAL, "batch precision must be LBM_EM_F32 or LBM_EM_F64");
+    if (o->precision != LBM_EM_F32 && o->precision != LBM_EM_F64 && o->precision != LBM_EM_F32X2)
+        return set_error(LBM_EM_EINVAL, "batch precision must be LBM_EM_F32, LBM_EM_F64 or LBM_EM_F32X2");
     if (o->tile_w < 0 || o->tile_h < 0 || o->ctas_per_sm < 0 || o->ctas_per_sm > 8)
         return set_error(LBM_EM_EINVAL, "bad tile shape or CTAs per SM");
     if (o->tile_w && o->tile_w != 32 && o->tile_w != 64 && o->tile_w != 128 && o->tile_w != 256)
@@ -560,7 +566,7 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev);
     b->n = n;
     b->prec = o->precision;
-    b->elem = b->prec == LBM_EM_F64 ? 8 : 4;
+    b->elem = b->prec == LBM_EM_F32 ? 4 : 8;
     b->specs.assign(specs, specs + n);
     lbm_em_status st = LBM_EM_OK;
 #define BTRY(call, what)            \
@@ -654,9 +660,9 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
     BTRY(cudaMalloc(&b->d_settled, n * sizeof(int)), "cudaMalloc(energy)");
     b->conv_tol = o->conv_tol;
     b->min_periods = o->min_periods > 0 ? o->min_periods : 1;
-    BTRY(cudaMemcpy(b->d_cs, cs_all.data(), cs_all.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload");
+    BTRY(cudaMemcpyAsync(b->d_cs, cs_all.data(), cs_all.size() * sizeof(double2), cudaMemcpyHostToDevice, b->stream), "upload");
     for (int i = 0; i < n; ++i) b->desc[i].src.cs = b->d_cs + cs_off[i];
-    BTRY(cudaMemcpy(b->d_desc, b->desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice), "upload");
+    BTRY(cudaMemcpyAsync(b->d_desc, b->desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice, b->stream), "upload");
     // slot maps, contour points and per-instance contour descriptors
     {
         std::vector<int> smap(slot, -1);
@@ -670,11 +676,11 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
                                 2.0 / (double)specs[i].period_steps, ch[i].R, ch[i].dl, ch[i].F0, ch[i].M0};
             pts.insert(pts.end(), ch[i].pts.begin(), ch[i].pts.end());
         }
-        BTRY(cudaMemcpy(b->d_slot, smap.data(), slot * sizeof(int), cudaMemcpyHostToDevice), "upload slots");
+        BTRY(cudaMemcpyAsync(b->d_slot, smap.data(), slot * sizeof(int), cudaMemcpyHostToDevice, b->stream), "upload slots");
         BTRY(cudaMalloc(&b->d_pts, pts.size() * sizeof(ContourPt)), "cudaMalloc(points)");
-        BTRY(cudaMemcpy(b->d_pts, pts.data(), pts.size() * sizeof(ContourPt), cudaMemcpyHostToDevice), "upload");
+        BTRY(cudaMemcpyAsync(b->d_pts, pts.data(), pts.size() * sizeof(ContourPt), cudaMemcpyHostToDevice, b->stream), "upload");
         BTRY(cudaMalloc(&b->d_cdesc, n * sizeof(ContourDesc)), "cudaMalloc(contour desc)");
-        BTRY(cudaMemcpy(b->d_cdesc, cd.data(), n * sizeof(ContourDesc), cudaMemcpyHostToDevice), "upload");
+        BTRY(cudaMemcpyAsync(b->d_cdesc, cd.data(), n * sizeof(ContourDesc), cudaMemcpyHostToDevice, b->stream), "upload");
     }
     // rasterise every instance on the device (again at every run)
     BTRY(batch_rasterize(b), "rasterise");

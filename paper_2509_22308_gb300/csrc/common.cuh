@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df32.cuh"
+
 namespace lbmem {
 
 enum Plane {

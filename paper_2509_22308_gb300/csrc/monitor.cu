@@ -52,4 +52,7 @@ template cudaError_t launch_energy<double>(const StepArgs<double> &, const doubl
 template cudaError_t launch_energy<float>(const StepArgs<float> &, const float *, const long long *, double *,
                                           cudaStream_t);
 
+template cudaError_t launch_energy<df>(const StepArgs<df> &, const df *, const long long *, double *,
+                                       cudaStream_t);
+
 }  // namespace lbmem

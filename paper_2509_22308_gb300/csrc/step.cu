@@ -100,4 +100,9 @@ template cudaError_t launch_fields<double>(const StepArgs<double> &, const doubl
 template cudaError_t launch_fields<float>(const StepArgs<float> &, const float *, const long long *,
                                           double *, double *, double *, cudaStream_t);
 
+template cudaError_t launch_step<df>(const StepArgs<df> &, const df *, df *, const long long *, long long *, bool,
+                                     cudaStream_t);
+template cudaError_t launch_fields<df>(const StepArgs<df> &, const df *, const long long *, double *, double *,
+                                       double *, cudaStream_t);
+
 }  // namespace lbmem

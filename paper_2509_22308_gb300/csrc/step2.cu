@@ -49,11 +49,12 @@ __device__ __forceinline__ void acc_site(const AccParams &ap, const SourceParams
     q[5] += hy * c.y;
 }
 
-template <bool ACC, int POL>
-__global__ void __launch_bounds__(NT) k_step2_f32(const StepArgs<float> a, const float *__restrict__ fin,
-                                                  float *__restrict__ fout, const long long *__restrict__ t_in,
-                                                  long long *__restrict__ t_out) {
-    extern __shared__ float sm[];
+// T = float (FP32 form) or df (double-float form).
+template <typename T, bool ACC, int POL>
+__global__ void __launch_bounds__(NT) k_step2(const StepArgs<T> a, const T *__restrict__ fin, T *__restrict__ fout,
+                                              const long long *__restrict__ t_in, long long *__restrict__ t_out) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T *sm = reinterpret_cast<T *>(sm_raw);
     __shared__ SrcPair sp;
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
     const long long t = *t_in;
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(NT) k_step2_f32(const StepArgs<float> a, const
     for (int k = threadIdx.x; k < SW * SH; k += NT) {
         const int lx = k % SW, ly = k / SW, x = x0 - 1 + lx, y = y0 - 1 + ly;
         if (x < 0 || x >= a.nx || y < 0 || y >= a.ny) continue;
-        Pop<float> p;
+        Pop<T> p;
         pull_planes(a, fin, x, y, p);
         if (x == 0 && src0) inject_source(a.src.kind, sp.g0, sp.inc0, p);
         const size_t idx = (size_t)y * a.pitch + x;
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(NT) k_step2_f32(const StepArgs<float> a, const
     for (int k = threadIdx.x; k < TW * TH; k += NT) {
         const int lx = k % TW, ly = k / TW, x = x0 + lx, y = y0 + ly;
         if (x >= a.nx || y >= a.ny) continue;
-        Pop<float> p;
+        Pop<T> p;
         pull_smem(sm, a.nx, a.ny, x, y, lx + 1, ly + 1, p);
         if (x == 0 && src1) inject_source(a.src.kind, sp.g1, sp.inc1, p);
         const size_t idx = (size_t)y * a.pitch + x;
@@ -147,15 +148,23 @@ __global__ void __launch_bounds__(NT) k_step2_f16(const F16Args a, const long lo
     }
 }
 
+template <typename T>
+static cudaError_t allow_smem() {
+    const int b = (int)step2_smem<T>();
+    cudaError_t e = cudaFuncSetAttribute(k_step2<T, false, POL_TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step2<T, true, POL_TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step2<T, false, POL_TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step2<T, true, POL_TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return e;
+}
+
 cudaError_t step2_prepare() {
+    cudaError_t e = allow_smem<float>();
+    if (e == cudaSuccess) e = allow_smem<df>();
     const int b = (int)kStep2Smem;
-    cudaError_t e = cudaFuncSetAttribute(k_step2_f32<false, POL_TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step2_f32<true, POL_TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step2_f32<false, POL_TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step2_f32<true, POL_TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_step2_f16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e == cudaSuccess)
@@ -163,22 +172,28 @@ cudaError_t step2_prepare() {
     return e;
 }
 
-cudaError_t launch_step2_f32(const StepArgs<float> &a, const float *fin, float *fout, const long long *t_in,
-                             long long *t_out, bool accumulate, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_step2(const StepArgs<T> &a, const T *fin, T *fout, const long long *t_in, long long *t_out,
+                         bool accumulate, cudaStream_t s) {
     dim3 grid((a.nx + TW - 1) / TW, (a.ny + TH - 1) / TH), block(NT);
+    const size_t sb = step2_smem<T>();
     if (a.pol == POL_TE) {
         if (accumulate)
-            k_step2_f32<true, POL_TE><<<grid, block, kStep2Smem, s>>>(a, fin, fout, t_in, t_out);
+            k_step2<T, true, POL_TE><<<grid, block, sb, s>>>(a, fin, fout, t_in, t_out);
         else
-            k_step2_f32<false, POL_TE><<<grid, block, kStep2Smem, s>>>(a, fin, fout, t_in, t_out);
+            k_step2<T, false, POL_TE><<<grid, block, sb, s>>>(a, fin, fout, t_in, t_out);
     } else {
         if (accumulate)
-            k_step2_f32<true, POL_TM><<<grid, block, kStep2Smem, s>>>(a, fin, fout, t_in, t_out);
+            k_step2<T, true, POL_TM><<<grid, block, sb, s>>>(a, fin, fout, t_in, t_out);
         else
-            k_step2_f32<false, POL_TM><<<grid, block, kStep2Smem, s>>>(a, fin, fout, t_in, t_out);
+            k_step2<T, false, POL_TM><<<grid, block, sb, s>>>(a, fin, fout, t_in, t_out);
     }
     return cudaGetLastError();
 }
+template cudaError_t launch_step2<float>(const StepArgs<float> &, const float *, float *, const long long *,
+                                         long long *, bool, cudaStream_t);
+template cudaError_t launch_step2<df>(const StepArgs<df> &, const df *, df *, const long long *, long long *, bool,
+                                      cudaStream_t);
 
 cudaError_t launch_step2_f16(const F16Args &a, const long long *t_in, long long *t_out, bool accumulate,
                              cudaStream_t s) {

@@ -7,15 +7,20 @@
 namespace lbmem {
 
 // Tile of the two-steps-per-launch kernels (single-domain and batched): TW x TH sites, with
-// a one-site halo in shared memory (11 FP32 planes of SW x SH = 46.5 KB, 4 CTAs per SM).
+// a one-site halo in shared memory (11 planes of SW x SH values: 46.5 KB in FP32, 4 CTAs
+// per SM; 93 KB in double-float, 2 CTAs per SM).
 constexpr int TW = 64, TH = 14, SW = TW + 2, SH = TH + 2, NT = 256;
 constexpr size_t kStep2Smem = (size_t)NPLANES * SH * SW * sizeof(float);
+template <typename T>
+constexpr size_t step2_smem() { return (size_t)NPLANES * SH * SW * sizeof(T); }
 
-__device__ __forceinline__ float &smv(float *sm, int plane, int ly, int lx) {
+template <typename T>
+__device__ __forceinline__ T &smv(T *sm, int plane, int ly, int lx) {
     return sm[(plane * SH + ly) * SW + lx];
 }
 
-__device__ __forceinline__ void put_smem(float *sm, int ly, int lx, const Pop<float> &p) {
+template <typename T>
+__device__ __forceinline__ void put_smem(T *sm, int ly, int lx, const Pop<T> &p) {
     smv(sm, P_EZ, ly, lx) = p.ez;
     smv(sm, P_EPX, ly, lx) = p.epx;
     smv(sm, P_EMX, ly, lx) = p.emx;
@@ -31,7 +36,8 @@ __device__ __forceinline__ void put_smem(float *sm, int ly, int lx, const Pop<fl
 
 // f_i(r, t + 1) from the shared-memory f*(t); (cx, cy) is the site's cell in the tile
 // with halo, the upstream cell is clamped at the lattice edge exactly as pull_site does.
-__device__ __forceinline__ void pull_smem(float *sm, int nx, int ny, int x, int y, int cx, int cy, Pop<float> &p) {
+template <typename T>
+__device__ __forceinline__ void pull_smem(T *sm, int nx, int ny, int x, int y, int cx, int cy, Pop<T> &p) {
     const int xm = x > 0 ? cx - 1 : cx, xp = x < nx - 1 ? cx + 1 : cx;
     const int ym = y > 0 ? cy - 1 : cy, yp = y < ny - 1 ? cy + 1 : cy;
     p.ez = smv(sm, P_EZ, cy, cx);
@@ -49,8 +55,9 @@ __device__ __forceinline__ void pull_smem(float *sm, int nx, int ny, int x, int 
 
 // Allow the kernels' dynamic shared memory (call once per device, outside stream capture).
 cudaError_t step2_prepare();
-cudaError_t launch_step2_f32(const StepArgs<float> &a, const float *fin, float *fout, const long long *t_in,
-                             long long *t_out, bool accumulate, cudaStream_t s);
+template <typename T>
+cudaError_t launch_step2(const StepArgs<T> &a, const T *fin, T *fout, const long long *t_in, long long *t_out,
+                         bool accumulate, cudaStream_t s);
 cudaError_t launch_step2_f16(const F16Args &a, const long long *t_in, long long *t_out, bool accumulate,
                              cudaStream_t s);
 

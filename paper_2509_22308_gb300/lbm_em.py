@@ -15,14 +15,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblbm_em.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
-F64, F32, F16DEV = 0, 1, 2
+F64, F32, F16DEV, F32X2 = 0, 1, 2, 3
 FLAG_SINGLE_STEP, FLAG_TWO_STEP = 1, 2
 STEP_MODES = {"auto": 0, "one": FLAG_SINGLE_STEP, "two": FLAG_TWO_STEP}
 FLAG_TE = 4
 POLARIZATION_FLAGS = {"tm": 0, "te": FLAG_TE}
 SRC_HARD, SRC_OPEN, SRC_NONE = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ETIMEOUT", 6: "ESTATE"}
-PRECISIONS = {"f64": F64, "f32": F32, "f16dev": F16DEV}
+PRECISIONS = {"f64": F64, "f32": F32, "f16dev": F16DEV, "f32x2": F32X2}
 
 
 class LbmEmError(RuntimeError):

@@ -85,7 +85,7 @@ def _batch_instances():
     return insts
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32x2"])
 def test_batch_matches_single_domain(prec):
     insts = _batch_instances()
     b = L.Batch(insts, prec)
@@ -162,7 +162,7 @@ def test_batch_reports_unstable_instance():
     L.load().lbm_em_batch_destroy(h)
 
 
-@pytest.mark.parametrize("prec", ["f32", "f16dev"])
+@pytest.mark.parametrize("prec", ["f32", "f16dev", "f32x2"])
 @pytest.mark.parametrize("inst", W.small_cases()[:3], ids=lambda i: f"{i['nx']}x{i['ny']}")
 def test_two_steps_per_launch_is_bit_identical(inst, prec):
     """Two steps per launch (temporal blocking) equals one step per launch bit for bit,
