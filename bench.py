@@ -218,16 +218,17 @@ def run_reference(args, rank, world):
 
 def profile_case():
     """Two launches of each step kernel (FP64; FP32 and FP16-deviation with two steps
-    per launch, then with one) on a 2048^2 lattice (state 0.3-0.7 GB per buffer, larger
-    than L2, a few GB on the device in total), then two launches of the FP64 step on
-    one 512^2 instance of the benchmark workload."""
+    per launch, then with one; double-float) on a 2048^2 lattice (state 0.3-0.7 GB per
+    buffer, larger than L2, a few GB on the device in total), then two launches of the FP64
+    step on one 512^2 instance of the benchmark workload."""
     import torch
     from paper_2509_22308_gb300 import build as B
     B.build()
     from paper_2509_22308_gb300 import lbm_em as L
     inst = dict(nx=2048, ny=2048, a=128.0, phi0=0.5, eps1=4.0, eps2=1.0, pec2=True, period=240, periods=1,
                 R=192.0, ramp=240)
-    for fp, mode in (("f64", "auto"), ("f32", "two"), ("f16dev", "two"), ("f32", "one"), ("f16dev", "one")):
+    for fp, mode in (("f64", "auto"), ("f32", "two"), ("f16dev", "two"), ("f32", "one"), ("f16dev", "one"),
+                     ("f32x2", "auto")):
         with L.solver_for_instance(inst, fp, steps_per_launch=mode) as s:
             s.step(4 if mode == "two" else 2)
             s.sync()
