@@ -222,8 +222,8 @@ def run_reference(args, rank, world):
 def profile_case():
     """Two launches of each step kernel (FP64; FP32 and FP16-deviation with two steps
     per launch, then with one; double-float) on a 2048^2 lattice (state 0.3-0.7 GB per
-    buffer, larger than L2, a few GB on the device in total), then two launches of the FP64
-    step on one 512^2 instance of the benchmark workload."""
+    buffer, larger than L2, a few GB on the device in total), two launches of the FP64 step
+    on one 512^2 instance of the benchmark workload, then a 24-instance FP32 design map."""
     import torch
     from paper_2509_22308_gb300 import build as B
     B.build()
@@ -240,6 +240,12 @@ def profile_case():
     with L.solver_for_instance(W.md_janus_512()[0], "f64") as s:
         s.step(2)
         s.sync()
+    # then a 24-instance FP32 design map (about 1 GB on the device) with the batch kernel's
+    # two-steps-per-launch configuration fixed (no autotuning launches before it)
+    b = L.Batch(W.design_map_256(4, 24), "f32", tile_w=64, tile_h=14, ctas_per_sm=4)
+    b.run()
+    b.results()
+    b.close()
     torch.cuda.synchronize()
     print("profile case done")
 

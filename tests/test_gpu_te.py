@@ -105,3 +105,28 @@ def test_te_far_field_matches_oracle_transform():
         s.force_torque(L.make_contour(inst["R"], inst["a"]))
         got = s.far_field(phis)
     assert np.max(np.abs(got - ref)) < 1e-10 * np.max(ref)
+
+
+def test_te_far_field_matches_bessel_series():
+    """Sec. IV.A's far-field validation, carried to TE^z: homogeneous dielectric cylinder
+    (eps = 2.25), a = lambda, lambda_eps / dx = 50, L/a = 10, run until the energy has settled;
+    |S(phi)|^2 of H_z within 5 % of the TE Bessel series at most angles (median)."""
+    from oracle import analytic as A
+    eps = 2.25
+    lam = 50.0 * np.sqrt(eps)
+    T = int(round(3 * lam))
+    a = T / 3.0
+    n = int(round(10 * a)) // 2 * 2
+    inst = dict(nx=n, ny=n, a=a, phi0=0.0, eps1=eps, eps2=eps, pec2=False, period=T, periods=30,
+                R=1.5 * a, ramp=T)
+    phis = np.linspace(0, 2 * np.pi, 73)[:-1]
+    with L.solver_for_instance(inst, "f64", polarization="te") as s:
+        _, steps = s.run_converged(L.make_contour(inst["R"], a), tol=1e-6, min_periods=20, max_periods=800)
+        assert steps < 800 * T
+        S = s.far_field(phis)
+    k = ntff.lattice_wavenumber(T)
+    B, D = A.homogeneous_BD(k, a, eps, 0.0, te=True)
+    Sa = A.scattering_intensity(B, D, phis + np.pi)
+    rel = np.abs(S - Sa) / Sa
+    print(f"TE far field: steps={steps} median={np.median(rel):.4f} within5%={np.mean(rel < 0.05):.2f}")
+    assert np.median(rel) < 0.05, (np.median(rel), steps)
