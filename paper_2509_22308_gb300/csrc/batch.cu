@@ -58,51 +58,37 @@ struct BatchArgs {
     int conv;          // 1: sample the energy at period boundaries (convergence exits)
 };
 
-// FP32: at most 85 registers so that 3 CTAs of 256 threads stay resident per SM.
-template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
-    k_batch_step(const BatchArgs<T> b, const long long *__restrict__ t_in, long long *__restrict__ t_out) {
-    const long long t = *t_in;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + 1;
-    __shared__ MatT<T> smat[3];
-    __shared__ double ssrc[2];  // source values of the tile's instance at time t (column-0 tiles)
+// The sites of one tile at time t.  BOOK: the tile accumulates Fourier sums or samples the
+// energy this step (both uniform over the tile); without it no FP64 operation is compiled
+// in, so none can be predicated into the plain steps (see batch2_tile).  Returns the
+// thread's share of the tile's energy when sampling.
+template <typename T, bool BOOK>
+__device__ __forceinline__ double batch_tile(const BatchArgs<T> &b, const Tile &tl, const InstDesc &d, long long t,
+                                             bool acc, bool sample, bool src, const MatT<T> *smat,
+                                             const double *ssrc) {
+    StepArgs<T> a;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.pitch = d.pitch;
+    a.pstride = d.pstride;
+    a.src = d.src;
+    const T *fin = b.fin + d.base;
+    T *fout = b.fout + d.base;
+    const uint8_t *mat = b.mat + d.mat_base;
     const int tsz = b.tile_w * b.tile_h;
-    for (int tile = blockIdx.x; tile < b.n_tiles; tile += gridDim.x) {
-        const Tile tl = b.tiles[tile];
-        const InstDesc &d = b.inst[tl.inst];
-        const long long steps = d.steps;
-        if (t >= steps) continue;  // uniform over the block
-        const bool acc = t >= d.acc_from;
-        const bool sample = b.conv && t > 0 && t < d.acc_from && (t % (long long)d.period) == 0;
-        double wsum_t = 0.0;
-        __syncthreads();
-        if (threadIdx.x < 3)
-            smat[threadIdx.x] = MatT<T>{(T)d.mtab[threadIdx.x][0], (T)d.mtab[threadIdx.x][1],
-                                        (T)d.mtab[threadIdx.x][2], (T)d.mtab[threadIdx.x][3]};
-        // once per tile, not per site (see pull_site)
-        const bool src = tl.x0 == 0 && t >= 1 && d.src.kind != SRC_NONE;
-        if (threadIdx.x == 32 && src) source_values(d.src, t, &ssrc[0], &ssrc[1]);
-        __syncthreads();
-        StepArgs<T> a;
-        a.nx = d.nx;
-        a.ny = d.ny;
-        a.pitch = d.pitch;
-        a.pstride = d.pstride;
-        a.src = d.src;
-        const T *fin = b.fin + d.base;
-        T *fout = b.fout + d.base;
-        const uint8_t *mat = b.mat + d.mat_base;
-        for (int k = threadIdx.x; k < tsz; k += blockDim.x) {
-            const int x = tl.x0 + (k & (b.tile_w - 1)), y = tl.y0 + (k >> b.log2_tile_w);
-            if (x >= d.nx || y >= d.ny) continue;
-            Pop<T> p;
-            pull_planes(a, fin, x, y, p);
-            if (x == 0 && src) inject_source(d.src.kind, ssrc[0], ssrc[1], p);
-            const size_t idx = (size_t)y * d.pitch + x;
-            const MatT<T> m = smat[mat[idx]];
-            T E3, Hx, Hy, D;
-            moments(p, m, &E3, &Hx, &Hy, &D);
-            if (field_runaway(E3)) atomicOr(b.err + tl.inst, 1u);
+    double wsum_t = 0.0;
+    for (int k = threadIdx.x; k < tsz; k += blockDim.x) {
+        const int x = tl.x0 + (k & (b.tile_w - 1)), y = tl.y0 + (k >> b.log2_tile_w);
+        if (x >= d.nx || y >= d.ny) continue;
+        Pop<T> p;
+        pull_planes(a, fin, x, y, p);
+        if (x == 0 && src) inject_source(d.src.kind, ssrc[0], ssrc[1], p);
+        const size_t idx = (size_t)y * d.pitch + x;
+        const MatT<T> m = smat[mat[idx]];
+        T E3, Hx, Hy, D;
+        moments(p, m, &E3, &Hx, &Hy, &D);
+        if (field_runaway(E3)) atomicOr(b.err + tl.inst, 1u);
+        if (BOOK) {
             if (acc && y >= d.y0 && y <= d.y1) {
                 const int s = b.slot[d.slot_base + idx];
                 if (s >= 0) {
@@ -118,10 +104,43 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
                 }
             }
             if (sample)
-                wsum_t += 0.5 * ((double)D * (double)(D * m.inv_eps) + (double)Hx * (double)Hx + (double)Hy * (double)Hy);
-            collide(p, E3, Hx, Hy);
-            store_site(fout, d.pstride, idx, p);
+                wsum_t += 0.5 * ((double)D * (double)(D * m.inv_eps) + (double)Hx * (double)Hx +
+                                 (double)Hy * (double)Hy);
         }
+        collide(p, E3, Hx, Hy);
+        store_site(fout, d.pstride, idx, p);
+    }
+    return wsum_t;
+}
+
+// FP32: at most 85 registers so that 3 CTAs of 256 threads stay resident per SM.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+    k_batch_step(const BatchArgs<T> b, const long long *__restrict__ t_in, long long *__restrict__ t_out) {
+    const long long t = *t_in;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + 1;
+    __shared__ MatT<T> smat[3];
+    __shared__ double ssrc[2];  // source values of the tile's instance at time t (column-0 tiles)
+    for (int tile = blockIdx.x; tile < b.n_tiles; tile += gridDim.x) {
+        const Tile tl = b.tiles[tile];
+        const InstDesc &d = b.inst[tl.inst];
+        const long long steps = d.steps;
+        if (t >= steps) continue;  // uniform over the block
+        const bool acc = t >= d.acc_from;
+        const bool sample = b.conv && t > 0 && t < d.acc_from && (t % (long long)d.period) == 0;
+        __syncthreads();
+        if (threadIdx.x < 3)
+            smat[threadIdx.x] = MatT<T>{(T)d.mtab[threadIdx.x][0], (T)d.mtab[threadIdx.x][1],
+                                        (T)d.mtab[threadIdx.x][2], (T)d.mtab[threadIdx.x][3]};
+        // once per tile, not per site (see pull_site)
+        const bool src = tl.x0 == 0 && t >= 1 && d.src.kind != SRC_NONE;
+        if (threadIdx.x == 32 && src) source_values(d.src, t, &ssrc[0], &ssrc[1]);
+        __syncthreads();
+        if (!(acc || sample)) {  // uniform over the block
+            batch_tile<T, false>(b, tl, d, t, false, false, src, smat, ssrc);
+            continue;
+        }
+        double wsum_t = batch_tile<T, true>(b, tl, d, t, acc, sample, src, smat, ssrc);
         if (sample) {  // block sum of the tile's energy into the instance's accumulator
             __shared__ double wsh[8];
             for (int o = 16; o > 0; o >>= 1) wsum_t += __shfl_down_sync(0xffffffffu, wsum_t, o);
@@ -158,6 +177,68 @@ __device__ __forceinline__ void batch_acc(const double *f3, const int *slot, dou
 // An instance whose run ends at t + 1 takes only the first step (its state is not needed
 // afterwards; its forces come from the accumulators).  Convergence exits need a decision
 // between any two steps, so they keep the one-step kernel.
+// The two phases of one tile.  ACC: the tile's instance accumulates at t or t + 1; without
+// it no FP64 operation is compiled in (a run-time accumulation test per site let the
+// compiler predicate the FP64 conversions of the field triple into every site's update,
+// and GB300's FP64 pipe made that the kernel's bottleneck).
+template <bool ACC>
+__device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Tile &tl, const InstDesc &d,
+                                            long long t, bool two, float *sm, const MatT<float> *smat,
+                                            const double *ssrc) {
+    StepArgs<float> a;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.pitch = d.pitch;
+    a.pstride = d.pstride;
+    const float *fin = b.fin + d.base;
+    float *fout = b.fout + d.base;
+    const uint8_t *mat = b.mat + d.mat_base;
+    const bool src0 = t >= 1 && d.src.kind != SRC_NONE, src1 = d.src.kind != SRC_NONE;
+    for (int k = threadIdx.x; k < SW * SH; k += NT) {
+        const int lx = k % SW, ly = k / SW, x = tl.x0 - 1 + lx, y = tl.y0 - 1 + ly;
+        if (x < 0 || x >= d.nx || y < 0 || y >= d.ny) continue;
+        const bool interior = lx >= 1 && lx <= TW && ly >= 1 && ly <= TH;
+        if (!two && !interior) continue;
+        Pop<float> p;
+        pull_planes(a, fin, x, y, p);
+        if (x == 0 && src0) inject_source(d.src.kind, ssrc[0], ssrc[1], p);
+        const size_t idx = (size_t)y * d.pitch + x;
+        bool bad;
+        if (ACC && interior && t >= d.acc_from && y >= d.y0 && y <= d.y1) {
+            double f3[3];
+            bad = update_site<POL_TM, true>(p, smat[mat[idx]], f3, nullptr);
+            batch_acc(f3, b.slot, b.acc, d, idx, t);
+        } else {
+            bad = update_site<POL_TM, true>(p, smat[mat[idx]], nullptr, nullptr);
+        }
+        if (bad) atomicOr(b.err + tl.inst, 1u);
+        if (two)
+            put_smem(sm, ly, lx, p);
+        else
+            store_site(fout, d.pstride, idx, p);
+    }
+    if (!two) return;
+    __syncthreads();
+    for (int k = threadIdx.x; k < TW * TH; k += NT) {
+        const int lx = k % TW, ly = k / TW, x = tl.x0 + lx, y = tl.y0 + ly;
+        if (x >= d.nx || y >= d.ny) continue;
+        Pop<float> p;
+        pull_smem(sm, d.nx, d.ny, x, y, lx + 1, ly + 1, p);
+        if (x == 0 && src1) inject_source(d.src.kind, ssrc[2], ssrc[3], p);
+        const size_t idx = (size_t)y * d.pitch + x;
+        bool bad;
+        if (ACC && t + 1 >= d.acc_from && y >= d.y0 && y <= d.y1) {
+            double f3[3];
+            bad = update_site<POL_TM, true>(p, smat[mat[idx]], f3, nullptr);
+            batch_acc(f3, b.slot, b.acc, d, idx, t + 1);
+        } else {
+            bad = update_site<POL_TM, true>(p, smat[mat[idx]], nullptr, nullptr);
+        }
+        if (bad) atomicOr(b.err + tl.inst, 1u);
+        store_site(fout, d.pstride, idx, p);
+    }
+}
+
 __global__ void __launch_bounds__(NT, 4) k_batch_step2(const BatchArgs<float> b, const long long *__restrict__ t_in,
                                                     long long *__restrict__ t_out) {
     extern __shared__ float sm[];
@@ -182,51 +263,10 @@ __global__ void __launch_bounds__(NT, 4) k_batch_step2(const BatchArgs<float> b,
             }
         }
         __syncthreads();
-        StepArgs<float> a;
-        a.nx = d.nx;
-        a.ny = d.ny;
-        a.pitch = d.pitch;
-        a.pstride = d.pstride;
-        const float *fin = b.fin + d.base;
-        float *fout = b.fout + d.base;
-        const uint8_t *mat = b.mat + d.mat_base;
-        const bool src0 = t >= 1 && d.src.kind != SRC_NONE, src1 = d.src.kind != SRC_NONE;
-        for (int k = threadIdx.x; k < SW * SH; k += NT) {
-            const int lx = k % SW, ly = k / SW, x = tl.x0 - 1 + lx, y = tl.y0 - 1 + ly;
-            if (x < 0 || x >= d.nx || y < 0 || y >= d.ny) continue;
-            const bool interior = lx >= 1 && lx <= TW && ly >= 1 && ly <= TH;
-            if (!two && !interior) continue;
-            Pop<float> p;
-            pull_planes(a, fin, x, y, p);
-            if (x == 0 && src0) inject_source(d.src.kind, ssrc[0], ssrc[1], p);
-            const size_t idx = (size_t)y * d.pitch + x;
-            const bool acc = interior && t >= d.acc_from && y >= d.y0 && y <= d.y1;
-            double f3[3];
-            if (update_site<POL_TM, true>(p, smat[mat[idx]], acc ? f3 : nullptr, nullptr))
-                atomicOr(b.err + tl.inst, 1u);
-            if (acc) batch_acc(f3, b.slot, b.acc, d, idx, t);
-            if (two)
-                put_smem(sm, ly, lx, p);
-            else
-                store_site(fout, d.pstride, idx, p);
-        }
-        if (!two) continue;
-        __syncthreads();
-        const bool acc1 = t + 1 >= d.acc_from;
-        for (int k = threadIdx.x; k < TW * TH; k += NT) {
-            const int lx = k % TW, ly = k / TW, x = tl.x0 + lx, y = tl.y0 + ly;
-            if (x >= d.nx || y >= d.ny) continue;
-            Pop<float> p;
-            pull_smem(sm, d.nx, d.ny, x, y, lx + 1, ly + 1, p);
-            if (x == 0 && src1) inject_source(d.src.kind, ssrc[2], ssrc[3], p);
-            const size_t idx = (size_t)y * d.pitch + x;
-            const bool acc = acc1 && y >= d.y0 && y <= d.y1;
-            double f3[3];
-            if (update_site<POL_TM, true>(p, smat[mat[idx]], acc ? f3 : nullptr, nullptr))
-                atomicOr(b.err + tl.inst, 1u);
-            if (acc) batch_acc(f3, b.slot, b.acc, d, idx, t + 1);
-            store_site(fout, d.pstride, idx, p);
-        }
+        if (t + 1 >= d.acc_from)  // uniform over the block
+            batch2_tile<true>(b, tl, d, t, two, sm, smat, ssrc);
+        else
+            batch2_tile<false>(b, tl, d, t, two, sm, smat, ssrc);
     }
 }
 
