@@ -37,6 +37,7 @@ struct InstDesc {
     int acc_base, y0, y1, pad;
     SourceParams src;
     double mtab[3][4];  // per region id: MatT in the batch's type, widened (exactly) to double
+    MatT<float> mtabf[3];  // the same in FP32 (FP32 batches), so no tile converts on the FP64 pipe
 };
 
 struct Tile {
@@ -57,6 +58,16 @@ struct BatchArgs {
     double *energy;    // per-instance energy sum of the current period-boundary step
     int conv;          // 1: sample the energy at period boundaries (convergence exits)
 };
+
+// Material constants of region r of an instance in the kernel's type.
+template <typename T>
+__device__ __forceinline__ MatT<T> mat_entry(const InstDesc &d, int r) {
+    if constexpr (sizeof(T) == 4) {
+        return d.mtabf[r];
+    } else {
+        return MatT<T>{(T)d.mtab[r][0], (T)d.mtab[r][1], (T)d.mtab[r][2], (T)d.mtab[r][3]};
+    }
+}
 
 // The sites of one tile at time t.  BOOK: the tile accumulates Fourier sums or samples the
 // energy this step (both uniform over the tile); without it no FP64 operation is compiled
@@ -130,8 +141,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
         const bool sample = b.conv && t > 0 && t < d.acc_from && (t % (long long)d.period) == 0;
         __syncthreads();
         if (threadIdx.x < 3)
-            smat[threadIdx.x] = MatT<T>{(T)d.mtab[threadIdx.x][0], (T)d.mtab[threadIdx.x][1],
-                                        (T)d.mtab[threadIdx.x][2], (T)d.mtab[threadIdx.x][3]};
+            smat[threadIdx.x] = mat_entry<T>(d, threadIdx.x);
         // once per tile, not per site (see pull_site)
         const bool src = tl.x0 == 0 && t >= 1 && d.src.kind != SRC_NONE;
         if (threadIdx.x == 32 && src) source_values(d.src, t, &ssrc[0], &ssrc[1]);
@@ -253,8 +263,7 @@ __global__ void __launch_bounds__(NT, 4) k_batch_step2(const BatchArgs<float> b,
         const bool two = t + 1 < d.steps;
         __syncthreads();             // the previous tile is done with the shared memory
         if (threadIdx.x < 3)
-            smat[threadIdx.x] = MatT<float>{(float)d.mtab[threadIdx.x][0], (float)d.mtab[threadIdx.x][1],
-                                            (float)d.mtab[threadIdx.x][2], (float)d.mtab[threadIdx.x][3]};
+            smat[threadIdx.x] = d.mtabf[threadIdx.x];
         if (threadIdx.x == 32) {
             ssrc[0] = ssrc[1] = ssrc[2] = ssrc[3] = 0.0;
             if (tl.x0 == 0 && d.src.kind != SRC_NONE) {
@@ -675,6 +684,7 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
             if (b->prec == LBM_EM_F32) {
                 const MatT<float> m = material_entry<float>(eps[r], pec);
                 e[0] = m.inv_eps3, e[1] = m.c_d, e[2] = m.inv_eps, e[3] = m.c3;
+                d.mtabf[r] = m;
             } else {
                 const MatT<double> m = material_entry<double>(eps[r], pec);
                 e[0] = m.inv_eps3, e[1] = m.c_d, e[2] = m.inv_eps, e[3] = m.c3;
