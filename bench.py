@@ -490,7 +490,7 @@ def main():
             key = fp + {"auto": "", "one": "_one_step_per_launch", "two": "_two_steps_per_launch"}[mode]
             key += "_te" if pol == "te" else ""
             P = "TE" if pol == "te" else "TM"
-            kern = {("f32", "auto"): f"k_step2<float, false, {P}> (two steps per launch)",
+            kern = {("f32", "auto"): f"k_step2_tma<false, {P}> (two steps per launch, TMA-staged tiles)",
                     ("f32", "one"): f"k_step<float, false, {P}>", ("f16dev", "auto"): "k_step_f16<false>",
                     ("f16dev", "two"): "k_step2_f16<false> (two steps per launch)",
                     ("f64", "auto"): f"k_step<double, false, {P}>",

@@ -18,6 +18,7 @@
 #include "launchers.h"
 #include "runtime.h"
 #include "step2.cuh"
+#include "step2_tma.h"
 #include "step_f16.cuh"
 
 using namespace lbmem;
@@ -214,6 +215,10 @@ struct lbm_em {
     int64_t t = 0;
     int cur = 0;      // buffer holding the current state (and device time word)
     bool tb = false;  // two steps per launch (temporal blocking) for the HBM-bound forms
+    // FP32 two-step launches: tensor maps of the two state buffers and of the material
+    // ids, and the persistent grid
+    CUtensorMap tmap[2], idmap;
+    int tma_ctas = 0;
     // contour and accumulators
     bool has_contour = false;
     lbm_em_contour contour{};
@@ -333,8 +338,8 @@ static cudaError_t enqueue_step2(lbm_em *h, bool acc, cudaStream_t s, int p) {
     if (h->prec == LBM_EM_F32X2)
         return launch_step2<df>(make_args<df>(h), (const df *)h->buf[p], (df *)h->buf[1 - p], h->d_time + p,
                                 h->d_time + (1 - p), acc, s);
-    return launch_step2<float>(make_args<float>(h), (const float *)h->buf[p], (float *)h->buf[1 - p], h->d_time + p,
-                               h->d_time + (1 - p), acc, s);
+    return launch_step2_tma(make_args<float>(h), &h->tmap[p], &h->idmap, (float *)h->buf[1 - p], h->d_time + p,
+                            h->d_time + (1 - p), acc, h->tma_ctas, s);
 }
 
 // kGraphSteps steps starting from buffer 0 (an even number of launches, so the
@@ -506,6 +511,13 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     }
     TRY(dev_alloc(h, &h->d_mat, h->pstride), "allocating the material ids");
     TRY(cudaMemsetAsync(h->d_mat, 0, h->pstride, h->stream), "cudaMemset");
+    if (h->tb && h->prec == LBM_EM_F32) {
+        TRY(step2_tma_prepare(&h->tma_ctas), "configuring the TMA-staged two-step kernel");
+        for (int b = 0; b < 2; ++b)
+            TRY(encode_plane_map(&h->tmap[b], (const float *)h->buf[b], h->nx, h->ny, h->pitch, h->pstride),
+                "encoding the tensor map of a state buffer");
+        TRY(encode_id_map(&h->idmap, h->d_mat, h->nx, h->ny, h->pitch), "encoding the tensor map of the ids");
+    }
     TRY(dev_alloc(h, &h->d_mtab, 256 * sizeof(MatT<double>)), "allocating the material table");
     TRY(dev_alloc(h, &h->d_time, 2 * sizeof(long long)), "allocating the time words");
     TRY(cudaMemsetAsync(h->d_time, 0, 2 * sizeof(long long), h->stream), "cudaMemset");
@@ -704,6 +716,7 @@ lbm_em_status lbm_em_sync(lbm_em_t *h) {
                                    "reading the error flag");
     if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (st) return st;
+    if (err & kErrTimeout) return set_error(LBM_EM_ETIMEOUT, "a bounded wait for a tile load gave up");
     if (err) return set_error(LBM_EM_EUNSTABLE, "a field became non-finite or exceeded 3*2^20");
     return LBM_EM_OK;
 }

@@ -35,6 +35,10 @@ enum Plane {
     NPLANES
 };
 
+// Bits of the sticky error word that the host reads back: a field became non-finite or
+// ran away, or a bounded device-side wait gave up.
+constexpr unsigned kErrUnstable = 1u, kErrTimeout = 2u;
+
 enum SourceKind { SRC_HARD = 0, SRC_OPEN = 1, SRC_NONE = 2 };  // values of lbm_em_source_kind
 enum Polarization { POL_TM = 0, POL_TE = 1 };
 
@@ -104,13 +108,17 @@ __device__ __forceinline__ void source_values(const SourceParams &s, long long t
 // h_+x,y = -e_+x,z, subtracts it from h_+x,y); HARD replaces the incoming pair by the
 // incident one.
 template <typename T>
-__device__ __forceinline__ void inject_source(int kind, double g_open, double inc, Pop<T> &p) {
+__device__ __forceinline__ void inject_source_t(int kind, T g_open, T inc, Pop<T> &p) {
     if (kind == SRC_OPEN) {
-        p.epx += (T)g_open;
+        p.epx += g_open;
     } else {
-        p.epx = (T)inc;
+        p.epx = inc;
         p.hxpx = (T)0;
     }
+}
+template <typename T>
+__device__ __forceinline__ void inject_source(int kind, double g_open, double inc, Pop<T> &p) {
+    inject_source_t<T>(kind, (T)g_open, (T)inc, p);
 }
 
 // f_i(r, t) = f*_i(r - c_i, t - 1) without the source; an upstream site outside the

@@ -1,5 +1,6 @@
-// Two time steps per launch for the HBM-bound storage forms (FP32, FP16-deviation):
-// temporal blocking of the fused stream-collide step (arXiv 2509.22308, Sec. III).
+// Two time steps per launch for the FP16-deviation and double-float forms: temporal
+// blocking of the fused stream-collide step (arXiv 2509.22308, Sec. III).  (The FP32
+// form's single-domain kernel stages its tiles with the copy engine, step2_tma.cu.)
 //
 // A CTA owns a TW x TH tile.  Phase 1 computes the post-collision f*(t) of the tile and
 // a one-site halo (pulled from global memory exactly as the one-step kernel does) into
@@ -18,38 +19,7 @@
 
 namespace lbmem {
 
-// Source values of the two times of a launch (t, t + 1), evaluated once per block by one
-// thread of the blocks that own column 0 (see pull_site for why not per site).
-struct SrcPair {
-    double g0, inc0, g1, inc1;
-};
-__device__ __forceinline__ void source_pair(const SourceParams &src, int x0, long long t, SrcPair *sp) {
-    if (threadIdx.x == 0) {
-        SrcPair v{0.0, 0.0, 0.0, 0.0};
-        if (x0 == 0 && src.kind != SRC_NONE) {
-            if (t >= 1) source_values(src, t, &v.g0, &v.inc0);
-            source_values(src, t + 1, &v.g1, &v.inc1);
-        }
-        *sp = v;
-    }
-}
-
-__device__ __forceinline__ void acc_site(const AccParams &ap, const SourceParams &src, size_t idx, int y,
-                                         long long t, double ez, double hx, double hy) {
-    if (y < ap.y0 || y > ap.y1) return;
-    const int s = ap.slot[idx];
-    if (s < 0) return;
-    const double2 c = src.cs[(int)(t % (long long)src.period)];
-    double *q = ap.acc + 6 * (size_t)s;
-    q[0] += ez * c.x;
-    q[1] += ez * c.y;
-    q[2] += hx * c.x;
-    q[3] += hx * c.y;
-    q[4] += hy * c.x;
-    q[5] += hy * c.y;
-}
-
-// T = float (FP32 form) or df (double-float form).
+// T = df (double-float form).
 template <typename T, bool ACC, int POL>
 __global__ void __launch_bounds__(NT) k_step2(const StepArgs<T> a, const T *__restrict__ fin, T *__restrict__ fout,
                                               const long long *__restrict__ t_in, long long *__restrict__ t_out) {
@@ -162,8 +132,7 @@ static cudaError_t allow_smem() {
 }
 
 cudaError_t step2_prepare() {
-    cudaError_t e = allow_smem<float>();
-    if (e == cudaSuccess) e = allow_smem<df>();
+    cudaError_t e = allow_smem<df>();
     const int b = (int)kStep2Smem;
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_step2_f16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
@@ -190,8 +159,6 @@ cudaError_t launch_step2(const StepArgs<T> &a, const T *fin, T *fout, const long
     }
     return cudaGetLastError();
 }
-template cudaError_t launch_step2<float>(const StepArgs<float> &, const float *, float *, const long long *,
-                                         long long *, bool, cudaStream_t);
 template cudaError_t launch_step2<df>(const StepArgs<df> &, const df *, df *, const long long *, long long *, bool,
                                       cudaStream_t);
 

@@ -6,9 +6,9 @@
 
 namespace lbmem {
 
-// Tile of the two-steps-per-launch kernels (single-domain and batched): TW x TH sites, with
-// a one-site halo in shared memory (11 planes of SW x SH values: 46.5 KB in FP32, 4 CTAs
-// per SM; 93 KB in double-float, 2 CTAs per SM).
+// Tile of the two-steps-per-launch kernels of step2.cu and of the batch: TW x TH sites,
+// with a one-site halo in shared memory (11 planes of SW x SH values: 46.5 KB in FP32,
+// 4 CTAs per SM; 93 KB in double-float, 2 CTAs per SM).
 constexpr int TW = 64, TH = 14, SW = TW + 2, SH = TH + 2, NT = 256;
 constexpr size_t kStep2Smem = (size_t)NPLANES * SH * SW * sizeof(float);
 template <typename T>
@@ -51,6 +51,37 @@ __device__ __forceinline__ void pull_smem(T *sm, int nx, int ny, int x, int y, i
     p.hypy = smv(sm, P_HYPY, ym, cx);
     p.hymy = smv(sm, P_HYMY, yp, cx);
     p.hyz = smv(sm, P_HYZ, cy, cx);
+}
+
+// Source values of the two times of a launch (t, t + 1), evaluated once per block by one
+// thread of the blocks that own column 0 (see pull_site for why not per site).
+struct SrcPair {
+    double g0, inc0, g1, inc1;
+};
+__device__ __forceinline__ void source_pair(const SourceParams &src, int x0, long long t, SrcPair *sp) {
+    if (threadIdx.x == 0) {
+        SrcPair v{0.0, 0.0, 0.0, 0.0};
+        if (x0 == 0 && src.kind != SRC_NONE) {
+            if (t >= 1) source_values(src, t, &v.g0, &v.inc0);
+            source_values(src, t + 1, &v.g1, &v.inc1);
+        }
+        *sp = v;
+    }
+}
+
+__device__ __forceinline__ void acc_site(const AccParams &ap, const SourceParams &src, size_t idx, int y,
+                                         long long t, double ez, double hx, double hy) {
+    if (y < ap.y0 || y > ap.y1) return;
+    const int s = ap.slot[idx];
+    if (s < 0) return;
+    const double2 c = src.cs[(int)(t % (long long)src.period)];
+    double *q = ap.acc + 6 * (size_t)s;
+    q[0] += ez * c.x;
+    q[1] += ez * c.y;
+    q[2] += hx * c.x;
+    q[3] += hx * c.y;
+    q[4] += hy * c.x;
+    q[5] += hy * c.y;
 }
 
 // Allow the kernels' dynamic shared memory (call once per device, outside stream capture).

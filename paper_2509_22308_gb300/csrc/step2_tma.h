@@ -1,0 +1,34 @@
+// Host-side interface of the TMA-staged two-steps-per-launch FP32 kernel (step2_tma.cu).
+#pragma once
+
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace lbmem {
+
+// Tile of the TMA-staged kernel: kTmaTileW x kTmaTileH sites, kTmaThreads threads per CTA.
+// Shared memory per CTA: one stage (the 11 planes over the tile and a two-site halo,
+// 72 x 12 x 11 floats, and the ids over the same rows, 96 x 12 bytes: 39 KB), the
+// intermediate state with a one-site halo and its ids (29 KB) and the 256-entry material
+// table (4 KB): 72 KB, three CTAs per SM.
+constexpr int kTmaTileW = 64, kTmaTileH = 8, kTmaThreads = 256;
+
+// Tensor map of an FP32 state buffer (11 planes of ny rows of `pitch` floats, plane stride
+// `pstride` floats) with the kernel's box.  base 16-byte aligned, pitch and pstride
+// multiples of 4; cudaErrorInvalidValue otherwise or if the driver rejects the map.
+cudaError_t encode_plane_map(CUtensorMap *map, const float *base, int nx, int ny, int pitch, size_t pstride);
+
+// Tensor map of the material ids (ny rows of `pitch` bytes, pitch a multiple of 16) with
+// the kernel's id box.
+cudaError_t encode_id_map(CUtensorMap *map, const uint8_t *ids, int nx, int ny, int pitch);
+
+// Once per device, outside stream capture: allows the kernels' shared memory and returns
+// the persistent grid (resident CTAs per SM x SMs) in *max_ctas.
+cudaError_t step2_tma_prepare(int *max_ctas);
+
+// Two steps: the state described by *fin (time word t_in) -> fout (t_out = t + 2).
+cudaError_t launch_step2_tma(const StepArgs<float> &a, const CUtensorMap *fin, const CUtensorMap *ids, float *fout,
+                             const long long *t_in, long long *t_out, bool accumulate, int max_ctas, cudaStream_t s);
+
+}  // namespace lbmem
