@@ -242,7 +242,7 @@ def profile_case():
         s.sync()
     # then a 24-instance FP32 design map (about 1 GB on the device) with the batch kernel's
     # two-steps-per-launch configuration fixed (no autotuning launches before it)
-    b = L.Batch(W.design_map_256(4, 24), "f32", tile_w=64, tile_h=14, ctas_per_sm=4)
+    b = L.Batch(W.design_map_256(4, 24), "f32", tile_w=64, tile_h=8, ctas_per_sm=3)
     b.run()
     b.results()
     b.close()

@@ -25,6 +25,8 @@
 #include "launchers.h"
 #include "runtime.h"
 #include "step2.cuh"
+#include "step2_tma.h"
+#include "tile_tma.cuh"
 
 using namespace lbmem;
 
@@ -180,102 +182,133 @@ __device__ __forceinline__ void batch_acc(const double *f3, const int *slot, dou
     q[5] += f3[2] * c.y;
 }
 
-// Two steps per launch for the FP32 batch with fixed run lengths (temporal blocking as in
-// step2.cu): each TW x TH tile of an instance is advanced to t + 1 together with a
-// one-site halo into shared memory, then to t + 2 from there, so the packed state crosses
-// HBM once per two steps.  The per-site arithmetic is the one-step kernel's (same bits).
-// An instance whose run ends at t + 1 takes only the first step (its state is not needed
-// afterwards; its forces come from the accumulators).  Convergence exits need a decision
-// between any two steps, so they keep the one-step kernel.
-// The two phases of one tile.  ACC: the tile's instance accumulates at t or t + 1; without
-// it no FP64 operation is compiled in (a run-time accumulation test per site let the
-// compiler predicate the FP64 conversions of the field triple into every site's update,
-// and GB300's FP64 pipe made that the kernel's bottleneck).
+// Two steps per launch for the FP32 batch with fixed run lengths, on the TMA-staged tile
+// of the single-domain FP32 kernel (tile_tma.cuh, step2_tma.cu): each 64 x 8 tile of an
+// instance arrives in shared memory with a two-site halo and its material ids through
+// the instance's tensor maps, advances to t + 1 together with a one-site halo, then to
+// t + 2, so the packed state crosses HBM once per two steps.  A persistent CTA walks the
+// tile list with a grid stride, skipping tiles of finished instances, and issues the
+// copies of its next tile as soon as phase 1 has read the stage.  The per-site arithmetic
+// is the one-step kernel's (same bits).  An instance whose run ends at t + 1 takes only
+// the first step (its state is not needed afterwards; its forces come from the
+// accumulators).  Convergence exits need a decision between any two steps, so they keep
+// the one-step kernel.
+// ACC: the tile's instance accumulates at t or t + 1; without it no FP64 operation is
+// compiled in (a run-time accumulation test per site let the compiler predicate the FP64
+// conversions of the field triple into every site's update, and GB300's FP64 pipe made
+// that the kernel's bottleneck).
+using namespace tma_tile;
+
+// Tensor maps of instance i: maps[3 i + p] its state in buffer p, maps[3 i + 2] its ids.
+__device__ __forceinline__ void batch_issue(const CUtensorMap *maps, const Tile &tl, int p, unsigned char *stage,
+                                            uint64_t *bar) {
+    issue_tile(maps + 3 * tl.inst + p, maps + 3 * tl.inst + 2, tl.x0, tl.y0, stage, bar);
+}
+
+// The first tile j, j + gridDim.x, ... whose instance still runs at t; -1 if none.
+__device__ __forceinline__ int next_active(const BatchArgs<float> &b, int j, long long t) {
+    while (j < b.n_tiles && t >= b.inst[b.tiles[j].inst].steps) j += gridDim.x;
+    return j < b.n_tiles ? j : -1;
+}
+
 template <bool ACC>
 __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Tile &tl, const InstDesc &d,
-                                            long long t, bool two, float *sm, const MatT<float> *smat,
-                                            const double *ssrc) {
-    StepArgs<float> a;
-    a.nx = d.nx;
-    a.ny = d.ny;
-    a.pitch = d.pitch;
-    a.pstride = d.pstride;
-    const float *fin = b.fin + d.base;
+                                            long long t, bool two, const TileSmem &S, const MatT<float> *smat,
+                                            const SrcPairF &sp, const CUtensorMap *maps, int p, int nxt,
+                                            uint64_t *bar) {
+    const int nx = d.nx, ny = d.ny, x0 = tl.x0, y0 = tl.y0;
     float *fout = b.fout + d.base;
-    const uint8_t *mat = b.mat + d.mat_base;
     const bool src0 = t >= 1 && d.src.kind != SRC_NONE, src1 = d.src.kind != SRC_NONE;
-    for (int k = threadIdx.x; k < SW * SH; k += NT) {
-        const int lx = k % SW, ly = k / SW, x = tl.x0 - 1 + lx, y = tl.y0 - 1 + ly;
-        if (x < 0 || x >= d.nx || y < 0 || y >= d.ny) continue;
-        const bool interior = lx >= 1 && lx <= TW && ly >= 1 && ly <= TH;
+    for (int k = threadIdx.x; k < IW * IH; k += NTH) {
+        const int lx = k % IW, ly = k / IW, x = x0 - 1 + lx, y = y0 - 1 + ly;
+        if (x < 0 || x >= nx || y < 0 || y >= ny) continue;
+        const bool interior = lx >= 1 && lx <= KW && ly >= 1 && ly <= KH;
         if (!two && !interior) continue;
-        Pop<float> p;
-        pull_planes(a, fin, x, y, p);
-        if (x == 0 && src0) inject_source(d.src.kind, ssrc[0], ssrc[1], p);
+        Pop<float> q;
+        pull_buf<RW, RH>(S.raw, nx, ny, x, y, lx + 3, ly + 1, q);
+        if (x == 0 && src0) inject_source_t(d.src.kind, sp.g0, sp.inc0, q);
+        const uint8_t id = S.ids[(ly + 1) * MW + lx + MOFF - 1];
         const size_t idx = (size_t)y * d.pitch + x;
         bool bad;
         if (ACC && interior && t >= d.acc_from && y >= d.y0 && y <= d.y1) {
             double f3[3];
-            bad = update_site<POL_TM, true>(p, smat[mat[idx]], f3, nullptr);
+            bad = update_site<POL_TM, true>(q, smat[id], f3, nullptr);
             batch_acc(f3, b.slot, b.acc, d, idx, t);
         } else {
-            bad = update_site<POL_TM, true>(p, smat[mat[idx]], nullptr, nullptr);
+            bad = update_site<POL_TM, true>(q, smat[id], nullptr, nullptr);
         }
-        if (bad) atomicOr(b.err + tl.inst, 1u);
-        if (two)
-            put_smem(sm, ly, lx, p);
-        else
-            store_site(fout, d.pstride, idx, p);
+        if (bad) atomicOr(b.err + tl.inst, kErrUnstable);
+        if (two) {
+            put_inter(S.inter, ly, lx, q);
+            S.inter_ids[ly * IW + lx] = id;
+        } else {
+            store_site(fout, d.pstride, idx, q);
+        }
+    }
+    __syncthreads();  // the stage is read
+    if (threadIdx.x == 0 && nxt >= 0) {
+        fence_proxy_async_smem();
+        batch_issue(maps, b.tiles[nxt], p, S.stage, bar);
     }
     if (!two) return;
-    __syncthreads();
-    for (int k = threadIdx.x; k < TW * TH; k += NT) {
-        const int lx = k % TW, ly = k / TW, x = tl.x0 + lx, y = tl.y0 + ly;
-        if (x >= d.nx || y >= d.ny) continue;
-        Pop<float> p;
-        pull_smem(sm, d.nx, d.ny, x, y, lx + 1, ly + 1, p);
-        if (x == 0 && src1) inject_source(d.src.kind, ssrc[2], ssrc[3], p);
+    for (int k = threadIdx.x; k < KW * KH; k += NTH) {
+        const int lx = k % KW, ly = k / KW, x = x0 + lx, y = y0 + ly;
+        if (x >= nx || y >= ny) continue;
+        Pop<float> q;
+        pull_buf<IW, IH>(S.inter, nx, ny, x, y, lx + 1, ly + 1, q);
+        if (x == 0 && src1) inject_source_t(d.src.kind, sp.g1, sp.inc1, q);
+        const MatT<float> m = smat[S.inter_ids[(ly + 1) * IW + lx + 1]];
         const size_t idx = (size_t)y * d.pitch + x;
         bool bad;
         if (ACC && t + 1 >= d.acc_from && y >= d.y0 && y <= d.y1) {
             double f3[3];
-            bad = update_site<POL_TM, true>(p, smat[mat[idx]], f3, nullptr);
+            bad = update_site<POL_TM, true>(q, m, f3, nullptr);
             batch_acc(f3, b.slot, b.acc, d, idx, t + 1);
         } else {
-            bad = update_site<POL_TM, true>(p, smat[mat[idx]], nullptr, nullptr);
+            bad = update_site<POL_TM, true>(q, m, nullptr, nullptr);
         }
-        if (bad) atomicOr(b.err + tl.inst, 1u);
-        store_site(fout, d.pstride, idx, p);
+        if (bad) atomicOr(b.err + tl.inst, kErrUnstable);
+        store_site(fout, d.pstride, idx, q);
     }
 }
 
-__global__ void __launch_bounds__(NT, 4) k_batch_step2(const BatchArgs<float> b, const long long *__restrict__ t_in,
-                                                    long long *__restrict__ t_out) {
-    extern __shared__ float sm[];
+__global__ void __launch_bounds__(NTH, 3)
+    k_batch_step2(const BatchArgs<float> b, const CUtensorMap *__restrict__ maps, int p,
+                  const long long *__restrict__ t_in, long long *__restrict__ t_out) {
+    extern __shared__ unsigned char sm_dyn[];
+    __shared__ __align__(8) uint64_t bar;
     __shared__ MatT<float> smat[3];
-    __shared__ double ssrc[4];  // source values of t and t + 1 (tiles at x = 0)
+    __shared__ SrcPairF sp;
+    const TileSmem S = carve(sm_dyn);
     const long long t = *t_in;
     if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + 2;
-    for (int tile = blockIdx.x; tile < b.n_tiles; tile += gridDim.x) {
-        const Tile tl = b.tiles[tile];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int cur = next_active(b, blockIdx.x, t);
+    if (threadIdx.x == 0 && cur >= 0) batch_issue(maps, b.tiles[cur], p, S.stage, &bar);
+    unsigned phase = 0;
+    while (cur >= 0) {  // uniform over the block
+        const Tile tl = b.tiles[cur];
         const InstDesc &d = b.inst[tl.inst];
-        if (t >= d.steps) continue;  // uniform over the block
+        const int nxt = next_active(b, cur + gridDim.x, t);
         const bool two = t + 1 < d.steps;
-        __syncthreads();             // the previous tile is done with the shared memory
-        if (threadIdx.x < 3)
-            smat[threadIdx.x] = d.mtabf[threadIdx.x];
-        if (threadIdx.x == 32) {
-            ssrc[0] = ssrc[1] = ssrc[2] = ssrc[3] = 0.0;
-            if (tl.x0 == 0 && d.src.kind != SRC_NONE) {
-                if (t >= 1) source_values(d.src, t, &ssrc[0], &ssrc[1]);
-                source_values(d.src, t + 1, &ssrc[2], &ssrc[3]);
-            }
+        if (threadIdx.x < 3) smat[threadIdx.x] = d.mtabf[threadIdx.x];
+        if (threadIdx.x == 32) sp = source_pair_f(d.src, tl.x0, t);
+        const bool ok = mbar_wait(&bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {  // the tile's copies never completed: report, leave
+            if (threadIdx.x == 0) atomicOr(b.err + tl.inst, kErrTimeout);
+            return;
         }
-        __syncthreads();
-        if (t + 1 >= d.acc_from)  // uniform over the block
-            batch2_tile<true>(b, tl, d, t, two, sm, smat, ssrc);
+        if (t + 1 >= d.acc_from)
+            batch2_tile<true>(b, tl, d, t, two, S, smat, sp, maps, p, nxt, &bar);
         else
-            batch2_tile<false>(b, tl, d, t, two, sm, smat, ssrc);
+            batch2_tile<false>(b, tl, d, t, two, S, smat, sp, maps, p, nxt, &bar);
+        __syncthreads();  // shared memory is free for the next tile
+        cur = nxt;
     }
 }
 
@@ -383,7 +416,9 @@ struct lbm_em_batch {
     long long *d_time = nullptr;
     unsigned *d_err = nullptr;
     int tile_w = 0, tile_h = 0, ctas = 0;
-    bool two = false;  // two steps per launch (FP32, fixed run lengths; TW x TH tiles)
+    bool two = false;  // two steps per launch (FP32, fixed run lengths; TMA-staged 64 x 8 tiles)
+    CUtensorMap *d_maps = nullptr;  // FP32: per instance, its state in buffer 0 and 1 and its ids
+    int two_ctas = 0;               // resident CTAs per SM of the two-step kernel (0: not available)
     cudaGraphExec_t graph = nullptr;
     bool ran = false;
     // convergence exits
@@ -414,6 +449,7 @@ static void batch_free(lbm_em_batch *b) {
     cudaFree(b->d_energy);
     cudaFree(b->d_prev);
     cudaFree(b->d_settled);
+    cudaFree(b->d_maps);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -479,7 +515,7 @@ static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, int p) {
                            (const float *)b->buf[p], (float *)b->buf[1 - p], b->d_mat, b->d_slot,
                            b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
         if (b->two)
-            k_batch_step2<<<grid, NT, kStep2Smem, s>>>(a, b->d_time + p, b->d_time + (1 - p));
+            k_batch_step2<<<grid, NTH, kSmemBytes, s>>>(a, b->d_maps, p, b->d_time + p, b->d_time + (1 - p));
         else
             k_batch_step<float><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
     }
@@ -519,8 +555,8 @@ static lbm_em_status batch_clear(lbm_em_batch *b) {
 }
 
 // Time a few steps of each (tile shape, CTAs per SM, steps per launch) candidate from the
-// cleared state; two steps per launch (TW x TH tiles) is a candidate for FP32 runs of
-// fixed length.
+// cleared state; two steps per launch (TMA-staged 64 x 8 tiles, as many CTAs per SM as its
+// shared memory allows) is a candidate for FP32 runs of fixed length.
 static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int want_c) {
     struct Cand {
         int w, h, c;
@@ -536,9 +572,9 @@ static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int
             if (want_c && c != want_c) continue;
             cands.push_back(Cand{sh[0], sh[1], c, false});
         }
-    if (b->prec == LBM_EM_F32 && b->conv_tol <= 0.0 && (!want_w || want_w == TW) && (!want_h || want_h == TH))
-        for (int c : {2, 3, 4})
-            if (!want_c || want_c == c) cands.push_back(Cand{TW, TH, c, true});
+    if (b->two_ctas > 0 && b->conv_tol <= 0.0 && (!want_w || want_w == KW) && (!want_h || want_h == KH) &&
+        (!want_c || want_c == b->two_ctas))
+        cands.push_back(Cand{KW, KH, b->two_ctas, true});
     if (cands.empty()) cands.push_back(Cand{want_w ? want_w : 64, want_h ? want_h : 4, want_c ? want_c : 4, false});
     if (cands.size() == 1) {
         b->ctas = cands[0].c;
@@ -732,6 +768,29 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
         BTRY(cudaMalloc(&b->d_cdesc, n * sizeof(ContourDesc)), "cudaMalloc(contour desc)");
         BTRY(cudaMemcpyAsync(b->d_cdesc, cd.data(), n * sizeof(ContourDesc), cudaMemcpyHostToDevice, b->stream), "upload");
     }
+    // FP32: tensor maps of every instance for the two-steps-per-launch kernel
+    if (b->prec == LBM_EM_F32) {
+        int per_sm = 0;
+        BTRY(cudaFuncSetAttribute(k_batch_step2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes),
+             "configuring the two-step batch kernel");
+        BTRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step2, NTH, kSmemBytes),
+             "occupancy of the two-step batch kernel");
+        std::vector<CUtensorMap> maps(3 * (size_t)n);
+        for (int i = 0; i < n; ++i) {
+            const InstDesc &d = b->desc[i];
+            for (int q = 0; q < 2; ++q)
+                BTRY(encode_plane_map(&maps[3 * i + q], (const float *)b->buf[q] + d.base, d.nx, d.ny, d.pitch,
+                                      d.pstride),
+                     "encoding an instance's tensor map");
+            BTRY(encode_id_map(&maps[3 * i + 2], b->d_mat + d.mat_base, d.nx, d.ny, d.pitch),
+                 "encoding an instance's id map");
+        }
+        BTRY(cudaMalloc(&b->d_maps, maps.size() * sizeof(CUtensorMap)), "cudaMalloc(tensor maps)");
+        BTRY(cudaMemcpyAsync(b->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                             b->stream),
+             "upload");
+        b->two_ctas = per_sm;
+    }
     // rasterise every instance on the device (again at every run)
     BTRY(batch_rasterize(b), "rasterise");
     // run order: decreasing number of steps
@@ -813,11 +872,13 @@ lbm_em_status lbm_em_batch_results(lbm_em_batch_t *b, double *out, int32_t *stat
     if (!st) st = cuda_status(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
     if (st) return st;
     if (out) std::memcpy(out, res.data(), res.size() * sizeof(double));
-    bool any = false;
+    bool any = false, timeout = false;
     for (int i = 0; i < b->n; ++i) {
-        if (status) status[i] = err[i] ? LBM_EM_EUNSTABLE : LBM_EM_OK;
+        if (status) status[i] = (err[i] & kErrTimeout) ? LBM_EM_ETIMEOUT : err[i] ? LBM_EM_EUNSTABLE : LBM_EM_OK;
         any |= err[i] != 0;
+        timeout |= (err[i] & kErrTimeout) != 0;
     }
+    if (timeout) return set_error(LBM_EM_ETIMEOUT, "a bounded wait for a tile load gave up");
     if (any) return set_error(LBM_EM_EUNSTABLE, "at least one instance became unstable");
     return LBM_EM_OK;
 }

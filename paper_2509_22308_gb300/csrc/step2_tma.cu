@@ -29,79 +29,13 @@
 #include "common.cuh"
 #include "step2.cuh"
 #include "step2_tma.h"
-#include "tma.cuh"
+#include "tile_tma.cuh"
 
 namespace lbmem {
 
 namespace {
 
-constexpr int KW = kTmaTileW, KH = kTmaTileH, NTH = kTmaThreads;
-constexpr int RW = KW + 8, RH = KH + 4;  // stage: x0 - 4 .. x0 + KW + 3, y0 - 2 .. y0 + KH + 1
-constexpr int IW = KW + 2, IH = KH + 2;  // intermediate: x0 - 1 .. x0 + KW, y0 - 1 .. y0 + KH
-constexpr int MW = 96, MOFF = 16;        // ids: x0 - 16 .. x0 + 79, the stage's rows
-static_assert(RW * sizeof(float) % 16 == 0 && MW % 16 == 0, "TMA box rows must be multiples of 16 bytes");
-static_assert(KW % 16 == 0, "x0 - 4 floats and x0 - 16 bytes must start on 16-byte boundaries");
-static_assert(MW >= MOFF + KW + 2, "the id box must cover x0 - 2 .. x0 + KW + 1");
-
-constexpr int STATE_FLOATS = NPLANES * RH * RW;
-constexpr unsigned STATE_BYTES = STATE_FLOATS * sizeof(float), ID_BYTES = MW * RH;
-constexpr size_t OFF_IDS = (STATE_BYTES + 127) / 128 * 128;          // ids box, 128-byte aligned
-constexpr size_t OFF_INTER = OFF_IDS + (ID_BYTES + 127) / 128 * 128;  // intermediate state
-constexpr size_t OFF_TABLE = OFF_INTER + (size_t)NPLANES * IH * IW * sizeof(float);
-constexpr size_t OFF_INTER_IDS = OFF_TABLE + 256 * sizeof(MatT<float>);
-constexpr size_t kSmemBytes = OFF_INTER_IDS + (IW * IH + 15) / 16 * 16 + 128;  // + alignment slack
-static_assert(STATE_BYTES % 16 == 0 && OFF_TABLE % 16 == 0, "shared-memory layout");
-static_assert(3 * (kSmemBytes + 1024 + 64) <= 233472, "three CTAs per SM");
-
-// f_i(r, t + 1) from post-collision values in a W x H x 11 shared-memory buffer; (cx, cy)
-// is the site's cell in the buffer; the upstream cell clamps at the lattice edge.
-template <int W, int H>
-__device__ __forceinline__ void pull_buf(const float *sm, int nx, int ny, int x, int y, int cx, int cy,
-                                         Pop<float> &p) {
-    const int xm = x > 0 ? cx - 1 : cx, xp = x < nx - 1 ? cx + 1 : cx;
-    const int ym = y > 0 ? cy - 1 : cy, yp = y < ny - 1 ? cy + 1 : cy;
-    auto v = [&](int plane, int yy, int xx) { return sm[(plane * H + yy) * W + xx]; };
-    p.ez = v(P_EZ, cy, cx);
-    p.epx = v(P_EPX, cy, xm);
-    p.emx = v(P_EMX, cy, xp);
-    p.epy = v(P_EPY, ym, cx);
-    p.emy = v(P_EMY, yp, cx);
-    p.hxpx = v(P_HXPX, cy, xm);
-    p.hxmx = v(P_HXMX, cy, xp);
-    p.hxz = v(P_HXZ, cy, cx);
-    p.hypy = v(P_HYPY, ym, cx);
-    p.hymy = v(P_HYMY, yp, cx);
-    p.hyz = v(P_HYZ, cy, cx);
-}
-
-__device__ __forceinline__ void put_inter(float *sm, int ly, int lx, const Pop<float> &p) {
-    auto r = [&](int plane) -> float & { return sm[(plane * IH + ly) * IW + lx]; };
-    r(P_EZ) = p.ez;
-    r(P_EPX) = p.epx;
-    r(P_EMX) = p.emx;
-    r(P_EPY) = p.epy;
-    r(P_EMY) = p.emy;
-    r(P_HXPX) = p.hxpx;
-    r(P_HXMX) = p.hxmx;
-    r(P_HXZ) = p.hxz;
-    r(P_HYPY) = p.hypy;
-    r(P_HYMY) = p.hymy;
-    r(P_HYZ) = p.hyz;
-}
-
-__device__ __forceinline__ void issue_tile(const CUtensorMap *fmap, const CUtensorMap *imap, int tile, int ntx,
-                                           unsigned char *stage, uint64_t *bar) {
-    const int x0 = (tile % ntx) * KW, y0 = (tile / ntx) * KH;
-    mbar_arrive_expect_tx(bar, STATE_BYTES + ID_BYTES);
-    tma_load_3d(stage, fmap, x0 - 4, y0 - 2, 0, bar);
-    tma_load_2d(stage + OFF_IDS, imap, x0 - MOFF, y0 - 2, bar);
-}
-
-// Source values of the launch's two times in FP32, set by one thread per tile at x0 = 0
-// (the double-precision evaluation runs once, not in every thread).
-struct SrcPairF {
-    float g0, inc0, g1, inc1;
-};
+using namespace tma_tile;
 
 template <bool ACC, int POL>
 __global__ void __launch_bounds__(NTH, 3)
@@ -111,12 +45,7 @@ __global__ void __launch_bounds__(NTH, 3)
     extern __shared__ unsigned char sm_dyn[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ SrcPairF sp;
-    unsigned char *stage = sm_dyn + ((128u - (smem_u32(sm_dyn) & 127u)) & 127u);
-    const float *raw = reinterpret_cast<const float *>(stage);
-    const uint8_t *ids = stage + OFF_IDS;
-    float *inter = reinterpret_cast<float *>(stage + OFF_INTER);
-    MatT<float> *smt = reinterpret_cast<MatT<float> *>(stage + OFF_TABLE);
-    uint8_t *inter_ids = stage + OFF_INTER_IDS;
+    const TileSmem S = carve(sm_dyn);
 
     const long long t = *t_in;
     if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + 2;
@@ -125,20 +54,17 @@ __global__ void __launch_bounds__(NTH, 3)
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
-    for (int k = threadIdx.x; k < 256; k += NTH) smt[k] = a.mtab[k];
+    for (int k = threadIdx.x; k < 256; k += NTH) S.table[k] = a.mtab[k];
     __syncthreads();
-    if (threadIdx.x == 0) issue_tile(&fin, &ids_map, blockIdx.x, ntx, stage, &bar);
+    if (threadIdx.x == 0)
+        issue_tile(&fin, &ids_map, (blockIdx.x % ntx) * KW, (blockIdx.x / ntx) * KH, S.stage, &bar);
     const bool src0 = t >= 1 && a.src.kind != SRC_NONE, src1 = a.src.kind != SRC_NONE;
     const int nx = a.nx, ny = a.ny;
 
     for (int i = 0; i < n_mine; ++i) {
         const int tile = blockIdx.x + i * gridDim.x;
         const int x0 = (tile % ntx) * KW, y0 = (tile / ntx) * KH;
-        if (threadIdx.x == 0) {
-            SrcPair v;
-            source_pair(a.src, x0, t, &v);
-            sp = SrcPairF{(float)v.g0, (float)v.inc0, (float)v.g1, (float)v.inc1};
-        }
+        if (threadIdx.x == 0) sp = source_pair_f(a.src, x0, t);
         const bool ok = mbar_wait(&bar, (unsigned)i & 1u);
         if (__syncthreads_or(!ok)) {  // the tile's copies never completed: report, leave
             if (threadIdx.x == 0) atomicOr(a.err, kErrTimeout);
@@ -148,30 +74,31 @@ __global__ void __launch_bounds__(NTH, 3)
             const int lx = k % IW, ly = k / IW, x = x0 - 1 + lx, y = y0 - 1 + ly;
             if (x < 0 || x >= nx || y < 0 || y >= ny) continue;
             Pop<float> p;
-            pull_buf<RW, RH>(raw, nx, ny, x, y, lx + 3, ly + 1, p);
+            pull_buf<RW, RH>(S.raw, nx, ny, x, y, lx + 3, ly + 1, p);
             if (x == 0 && src0) inject_source_t(a.src.kind, sp.g0, sp.inc0, p);
-            const uint8_t id = ids[(ly + 1) * MW + lx + MOFF - 1];
+            const uint8_t id = S.ids[(ly + 1) * MW + lx + MOFF - 1];
             const bool acc = ACC && lx >= 1 && lx <= KW && ly >= 1 && ly <= KH;
             double f3[3];
-            if (update_site<POL, true>(p, smt[id], acc ? f3 : nullptr, nullptr)) atomicOr(a.err, kErrUnstable);
+            if (update_site<POL, true>(p, S.table[id], acc ? f3 : nullptr, nullptr)) atomicOr(a.err, kErrUnstable);
             if (acc) acc_site(a.accp, a.src, (size_t)y * a.pitch + x, y, t, f3[0], f3[1], f3[2]);
-            put_inter(inter, ly, lx, p);
-            inter_ids[ly * IW + lx] = id;
+            put_inter(S.inter, ly, lx, p);
+            S.inter_ids[ly * IW + lx] = id;
         }
         __syncthreads();  // the stage is read, the intermediate state written
         if (threadIdx.x == 0 && i + 1 < n_mine) {
+            const int nt = tile + gridDim.x;
             fence_proxy_async_smem();
-            issue_tile(&fin, &ids_map, tile + gridDim.x, ntx, stage, &bar);
+            issue_tile(&fin, &ids_map, (nt % ntx) * KW, (nt / ntx) * KH, S.stage, &bar);
         }
         for (int k = threadIdx.x; k < KW * KH; k += NTH) {
             const int lx = k % KW, ly = k / KW, x = x0 + lx, y = y0 + ly;
             if (x >= nx || y >= ny) continue;
             Pop<float> p;
-            pull_buf<IW, IH>(inter, nx, ny, x, y, lx + 1, ly + 1, p);
+            pull_buf<IW, IH>(S.inter, nx, ny, x, y, lx + 1, ly + 1, p);
             if (x == 0 && src1) inject_source_t(a.src.kind, sp.g1, sp.inc1, p);
             const size_t idx = (size_t)y * a.pitch + x;
             double f3[3];
-            if (update_site<POL, true>(p, smt[inter_ids[(ly + 1) * IW + lx + 1]], ACC ? f3 : nullptr, nullptr))
+            if (update_site<POL, true>(p, S.table[S.inter_ids[(ly + 1) * IW + lx + 1]], ACC ? f3 : nullptr, nullptr))
                 atomicOr(a.err, kErrUnstable);
             if (ACC) acc_site(a.accp, a.src, idx, y, t + 1, f3[0], f3[1], f3[2]);
             store_site(fout, a.pstride, idx, p);

@@ -1,0 +1,123 @@
+// The tile of the TMA-staged two-steps-per-launch FP32 kernels (single-domain in
+// step2_tma.cu, batched in batch.cu): geometry, shared-memory layout and the per-site
+// helpers both use.
+//
+// A tile is KW x KH sites at (x0, y0).  Its stage holds the 11 planes over the tile and a
+// two-site halo, x0 - 4 .. x0 + KW + 3 and y0 - 2 .. y0 + KH + 1 (RW x RH floats per
+// plane; the box starts at x0 - 4 so that it begins on a 16-byte boundary), and the
+// material ids over the same rows from x0 - 16 (MW bytes per row).  Phase 1 writes the
+// post-collision state of the tile and a one-site halo, x0 - 1 .. x0 + KW and y0 - 1 ..
+// y0 + KH (IW x IH), with each site's id, to the intermediate buffer.
+#pragma once
+
+#include "common.cuh"
+#include "step2_tma.h"
+#include "tma.cuh"
+
+namespace lbmem {
+namespace tma_tile {
+
+constexpr int KW = kTmaTileW, KH = kTmaTileH, NTH = kTmaThreads;
+constexpr int RW = KW + 8, RH = KH + 4;  // stage: x0 - 4 .. x0 + KW + 3, y0 - 2 .. y0 + KH + 1
+constexpr int IW = KW + 2, IH = KH + 2;  // intermediate: x0 - 1 .. x0 + KW, y0 - 1 .. y0 + KH
+constexpr int MW = 96, MOFF = 16;        // ids: x0 - 16 .. x0 + 79, the stage's rows
+static_assert(RW * sizeof(float) % 16 == 0 && MW % 16 == 0, "TMA box rows must be multiples of 16 bytes");
+static_assert(KW % 16 == 0, "x0 - 4 floats and x0 - 16 bytes must start on 16-byte boundaries");
+static_assert(MW >= MOFF + KW + 2, "the id box must cover x0 - 2 .. x0 + KW + 1");
+
+constexpr int STATE_FLOATS = NPLANES * RH * RW;
+constexpr unsigned STATE_BYTES = STATE_FLOATS * sizeof(float), ID_BYTES = MW * RH;
+constexpr size_t OFF_IDS = (STATE_BYTES + 127) / 128 * 128;          // ids box, 128-byte aligned
+constexpr size_t OFF_INTER = OFF_IDS + (ID_BYTES + 127) / 128 * 128;  // intermediate state
+constexpr size_t OFF_TABLE = OFF_INTER + (size_t)NPLANES * IH * IW * sizeof(float);
+constexpr size_t OFF_INTER_IDS = OFF_TABLE + 256 * sizeof(MatT<float>);
+constexpr size_t kSmemBytes = OFF_INTER_IDS + (IW * IH + 15) / 16 * 16 + 128;  // + alignment slack
+static_assert(STATE_BYTES % 16 == 0 && OFF_TABLE % 16 == 0, "shared-memory layout");
+static_assert(3 * (kSmemBytes + 1024 + 64) <= 233472, "three CTAs per SM");
+
+// f_i(r, t + 1) from post-collision values in a W x H x 11 shared-memory buffer; (cx, cy)
+// is the site's cell in the buffer; the upstream cell clamps at the lattice edge.
+template <int W, int H>
+__device__ __forceinline__ void pull_buf(const float *sm, int nx, int ny, int x, int y, int cx, int cy,
+                                         Pop<float> &p) {
+    const int xm = x > 0 ? cx - 1 : cx, xp = x < nx - 1 ? cx + 1 : cx;
+    const int ym = y > 0 ? cy - 1 : cy, yp = y < ny - 1 ? cy + 1 : cy;
+    auto v = [&](int plane, int yy, int xx) { return sm[(plane * H + yy) * W + xx]; };
+    p.ez = v(P_EZ, cy, cx);
+    p.epx = v(P_EPX, cy, xm);
+    p.emx = v(P_EMX, cy, xp);
+    p.epy = v(P_EPY, ym, cx);
+    p.emy = v(P_EMY, yp, cx);
+    p.hxpx = v(P_HXPX, cy, xm);
+    p.hxmx = v(P_HXMX, cy, xp);
+    p.hxz = v(P_HXZ, cy, cx);
+    p.hypy = v(P_HYPY, ym, cx);
+    p.hymy = v(P_HYMY, yp, cx);
+    p.hyz = v(P_HYZ, cy, cx);
+}
+
+__device__ __forceinline__ void put_inter(float *sm, int ly, int lx, const Pop<float> &p) {
+    auto r = [&](int plane) -> float & { return sm[(plane * IH + ly) * IW + lx]; };
+    r(P_EZ) = p.ez;
+    r(P_EPX) = p.epx;
+    r(P_EMX) = p.emx;
+    r(P_EPY) = p.epy;
+    r(P_EMY) = p.emy;
+    r(P_HXPX) = p.hxpx;
+    r(P_HXMX) = p.hxmx;
+    r(P_HXZ) = p.hxz;
+    r(P_HYPY) = p.hypy;
+    r(P_HYMY) = p.hymy;
+    r(P_HYZ) = p.hyz;
+}
+
+// The copies of the tile at (x0, y0): state box and id box, completing on bar.
+__device__ __forceinline__ void issue_tile(const CUtensorMap *fmap, const CUtensorMap *imap, int x0, int y0,
+                                           unsigned char *stage, uint64_t *bar) {
+    mbar_arrive_expect_tx(bar, STATE_BYTES + ID_BYTES);
+    tma_load_3d(stage, fmap, x0 - 4, y0 - 2, 0, bar);
+    tma_load_2d(stage + OFF_IDS, imap, x0 - MOFF, y0 - 2, bar);
+}
+
+// Source values of the launch's two times in FP32, set by one thread per tile at x0 = 0
+// (the double-precision evaluation runs once, not in every thread).
+struct SrcPairF {
+    float g0, inc0, g1, inc1;
+};
+__device__ __forceinline__ SrcPairF source_pair_f(const SourceParams &src, int x0, long long t) {
+    SrcPairF v{0.f, 0.f, 0.f, 0.f};
+    if (x0 == 0 && src.kind != SRC_NONE) {
+        double g, inc;
+        if (t >= 1) {
+            source_values(src, t, &g, &inc);
+            v.g0 = (float)g;
+            v.inc0 = (float)inc;
+        }
+        source_values(src, t + 1, &g, &inc);
+        v.g1 = (float)g;
+        v.inc1 = (float)inc;
+    }
+    return v;
+}
+
+// The regions of the dynamic shared memory (aligned to 128 bytes here).
+struct TileSmem {
+    unsigned char *stage;  // state box, then id box
+    const float *raw;
+    const uint8_t *ids;
+    float *inter;
+    MatT<float> *table;
+    uint8_t *inter_ids;
+};
+__device__ __forceinline__ TileSmem carve(unsigned char *sm_dyn) {
+    unsigned char *s = sm_dyn + ((128u - (smem_u32(sm_dyn) & 127u)) & 127u);
+    return TileSmem{s,
+                    reinterpret_cast<const float *>(s),
+                    s + OFF_IDS,
+                    reinterpret_cast<float *>(s + OFF_INTER),
+                    reinterpret_cast<MatT<float> *>(s + OFF_TABLE),
+                    s + OFF_INTER_IDS};
+}
+
+}  // namespace tma_tile
+}  // namespace lbmem
