@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(NTH, 3)
         const int nxt = next_active(b, cur + gridDim.x, t);
         const bool two = t + 1 < d.steps;
         if (threadIdx.x < 3) smat[threadIdx.x] = d.mtabf[threadIdx.x];
-        if (threadIdx.x == 32) sp = source_pair_f(d.src, tl.x0, t);
+        if (threadIdx.x == 32) sp = tl.x0 == 0 ? source_pair_f(d.src, t) : SrcPairF{0.f, 0.f, 0.f, 0.f};
         const bool ok = mbar_wait(&bar, phase);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {  // the tile's copies never completed: report, leave

@@ -53,18 +53,28 @@ __global__ void __launch_bounds__(NTH, 3)
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
+        sp = source_pair_f(a.src, t);  // the same for every tile of the launch
     }
     for (int k = threadIdx.x; k < 256; k += NTH) S.table[k] = a.mtab[k];
     __syncthreads();
-    if (threadIdx.x == 0)
-        issue_tile(&fin, &ids_map, (blockIdx.x % ntx) * KW, (blockIdx.x / ntx) * KH, S.stage, &bar);
+    // tile coordinates step by the grid stride without a division per tile (a 32-bit
+    // division by a run-time divisor executes on the FP64 pipe here, which GB300 keeps narrow)
+    int tx = (int)blockIdx.x % ntx, ty = (int)blockIdx.x / ntx;
+    const int sx = (int)gridDim.x % ntx, sy = (int)gridDim.x / ntx;
+    auto advance = [&](int &x, int &y) {
+        x += sx;
+        y += sy;
+        if (x >= ntx) {
+            x -= ntx;
+            ++y;
+        }
+    };
+    if (threadIdx.x == 0) issue_tile(&fin, &ids_map, tx * KW, ty * KH, S.stage, &bar);
     const bool src0 = t >= 1 && a.src.kind != SRC_NONE, src1 = a.src.kind != SRC_NONE;
     const int nx = a.nx, ny = a.ny;
 
     for (int i = 0; i < n_mine; ++i) {
-        const int tile = blockIdx.x + i * gridDim.x;
-        const int x0 = (tile % ntx) * KW, y0 = (tile / ntx) * KH;
-        if (threadIdx.x == 0) sp = source_pair_f(a.src, x0, t);
+        const int x0 = tx * KW, y0 = ty * KH;
         const bool ok = mbar_wait(&bar, (unsigned)i & 1u);
         if (__syncthreads_or(!ok)) {  // the tile's copies never completed: report, leave
             if (threadIdx.x == 0) atomicOr(a.err, kErrTimeout);
@@ -85,10 +95,10 @@ __global__ void __launch_bounds__(NTH, 3)
             S.inter_ids[ly * IW + lx] = id;
         }
         __syncthreads();  // the stage is read, the intermediate state written
+        advance(tx, ty);  // the next tile of this CTA
         if (threadIdx.x == 0 && i + 1 < n_mine) {
-            const int nt = tile + gridDim.x;
             fence_proxy_async_smem();
-            issue_tile(&fin, &ids_map, (nt % ntx) * KW, (nt / ntx) * KH, S.stage, &bar);
+            issue_tile(&fin, &ids_map, tx * KW, ty * KH, S.stage, &bar);
         }
         for (int k = threadIdx.x; k < KW * KH; k += NTH) {
             const int lx = k % KW, ly = k / KW, x = x0 + lx, y = y0 + ly;
@@ -103,7 +113,7 @@ __global__ void __launch_bounds__(NTH, 3)
             if (ACC) acc_site(a.accp, a.src, idx, y, t + 1, f3[0], f3[1], f3[2]);
             store_site(fout, a.pstride, idx, p);
         }
-        __syncthreads();  // the intermediate buffer and sp are free for the next tile
+        __syncthreads();  // the intermediate buffer is free for the next tile
     }
 }
 

@@ -79,14 +79,16 @@ __device__ __forceinline__ void issue_tile(const CUtensorMap *fmap, const CUtens
     tma_load_2d(stage + OFF_IDS, imap, x0 - MOFF, y0 - 2, bar);
 }
 
-// Source values of the launch's two times in FP32, set by one thread per tile at x0 = 0
-// (the double-precision evaluation runs once, not in every thread).
+// Source values of a launch's two times t and t + 1 in FP32 (g0, inc0 only for t >= 1).
 struct SrcPairF {
     float g0, inc0, g1, inc1;
 };
-__device__ __forceinline__ SrcPairF source_pair_f(const SourceParams &src, int x0, long long t) {
+// Not inlined on purpose: inlined under a one-thread test, the compiler predicated the
+// double-precision evaluation into every thread of the block, and on GB300's narrow FP64
+// pipe that cost 15 % of the FP32 kernel's time.  Called by one thread.
+static __device__ __noinline__ SrcPairF source_pair_f(const SourceParams src, long long t) {
     SrcPairF v{0.f, 0.f, 0.f, 0.f};
-    if (x0 == 0 && src.kind != SRC_NONE) {
+    if (src.kind != SRC_NONE) {
         double g, inc;
         if (t >= 1) {
             source_values(src, t, &g, &inc);
