@@ -205,20 +205,37 @@ __device__ __forceinline__ void batch_issue(const CUtensorMap *maps, const Tile 
     issue_tile(maps + 3 * tl.inst + p, maps + 3 * tl.inst + 2, tl.x0, tl.y0, stage, bar);
 }
 
-// The first tile j, j + gridDim.x, ... whose instance still runs at t; -1 if none.
-__device__ __forceinline__ int next_active(const BatchArgs<float> &b, int j, long long t) {
-    while (j < b.n_tiles && t >= b.inst[b.tiles[j].inst].steps) j += gridDim.x;
-    return j < b.n_tiles ? j : -1;
+// The first tile j, j + gridDim.x, ... whose instance still runs at t (into *tl); -1 if none.
+__device__ __forceinline__ int next_active(const BatchArgs<float> &b, int j, long long t, Tile *tl) {
+    for (; j < b.n_tiles; j += gridDim.x) {
+        *tl = b.tiles[j];
+        if (t < b.inst[tl->inst].steps) return j;
+    }
+    return -1;
+}
+
+// What a tile needs of its instance's descriptor, in registers (read through a plain
+// reference inside the site loops, the fields would be reloaded after every store, since
+// the compiler cannot rule out aliasing with the state).
+struct TileFields {
+    int nx, ny, pitch, kind, ay0, ay1;
+    size_t ps, base;
+    long long steps, acc_from;
+};
+__device__ __forceinline__ TileFields tile_fields(const InstDesc &d) {
+    return TileFields{d.nx, d.ny, d.pitch, d.src.kind, d.y0, d.y1, d.pstride, d.base, d.steps, d.acc_from};
 }
 
 template <bool ACC>
 __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Tile &tl, const InstDesc &d,
-                                            long long t, bool two, const TileSmem &S, const MatT<float> *smat,
-                                            const SrcPairF &sp, const CUtensorMap *maps, int p, int nxt,
-                                            uint64_t *bar) {
-    const int nx = d.nx, ny = d.ny, x0 = tl.x0, y0 = tl.y0;
-    float *fout = b.fout + d.base;
-    const bool src0 = t >= 1 && d.src.kind != SRC_NONE, src1 = d.src.kind != SRC_NONE;
+                                            const TileFields &f, long long t, const TileSmem &S,
+                                            const MatT<float> *smat, const SrcPairF &sp, const CUtensorMap *maps,
+                                            int p, bool has_next, const Tile &ntl, uint64_t *bar) {
+    const int nx = f.nx, ny = f.ny, x0 = tl.x0, y0 = tl.y0;
+    const bool two = t + 1 < f.steps;
+    float *fout = b.fout + f.base;
+    unsigned *err = b.err + tl.inst;
+    const bool src0 = t >= 1 && f.kind != SRC_NONE, src1 = f.kind != SRC_NONE;
     for (int k = threadIdx.x; k < IW * IH; k += NTH) {
         const int lx = k % IW, ly = k / IW, x = x0 - 1 + lx, y = y0 - 1 + ly;
         if (x < 0 || x >= nx || y < 0 || y >= ny) continue;
@@ -226,29 +243,29 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
         if (!two && !interior) continue;
         Pop<float> q;
         pull_buf<RW, RH>(S.raw, nx, ny, x, y, lx + 3, ly + 1, q);
-        if (x == 0 && src0) inject_source_t(d.src.kind, sp.g0, sp.inc0, q);
+        if (x == 0 && src0) inject_source_t(f.kind, sp.g0, sp.inc0, q);
         const uint8_t id = S.ids[(ly + 1) * MW + lx + MOFF - 1];
-        const size_t idx = (size_t)y * d.pitch + x;
+        const size_t idx = (size_t)y * f.pitch + x;
         bool bad;
-        if (ACC && interior && t >= d.acc_from && y >= d.y0 && y <= d.y1) {
+        if (ACC && interior && t >= f.acc_from && y >= f.ay0 && y <= f.ay1) {
             double f3[3];
             bad = update_site<POL_TM, true>(q, smat[id], f3, nullptr);
             batch_acc(f3, b.slot, b.acc, d, idx, t);
         } else {
             bad = update_site<POL_TM, true>(q, smat[id], nullptr, nullptr);
         }
-        if (bad) atomicOr(b.err + tl.inst, kErrUnstable);
+        if (bad) atomicOr(err, kErrUnstable);
         if (two) {
             put_inter(S.inter, ly, lx, q);
             S.inter_ids[ly * IW + lx] = id;
         } else {
-            store_site(fout, d.pstride, idx, q);
+            store_site(fout, f.ps, idx, q);
         }
     }
     __syncthreads();  // the stage is read
-    if (threadIdx.x == 0 && nxt >= 0) {
+    if (threadIdx.x == 0 && has_next) {
         fence_proxy_async_smem();
-        batch_issue(maps, b.tiles[nxt], p, S.stage, bar);
+        batch_issue(maps, ntl, p, S.stage, bar);
     }
     if (!two) return;
     for (int k = threadIdx.x; k < KW * KH; k += NTH) {
@@ -256,19 +273,19 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
         if (x >= nx || y >= ny) continue;
         Pop<float> q;
         pull_buf<IW, IH>(S.inter, nx, ny, x, y, lx + 1, ly + 1, q);
-        if (x == 0 && src1) inject_source_t(d.src.kind, sp.g1, sp.inc1, q);
+        if (x == 0 && src1) inject_source_t(f.kind, sp.g1, sp.inc1, q);
         const MatT<float> m = smat[S.inter_ids[(ly + 1) * IW + lx + 1]];
-        const size_t idx = (size_t)y * d.pitch + x;
+        const size_t idx = (size_t)y * f.pitch + x;
         bool bad;
-        if (ACC && t + 1 >= d.acc_from && y >= d.y0 && y <= d.y1) {
+        if (ACC && t + 1 >= f.acc_from && y >= f.ay0 && y <= f.ay1) {
             double f3[3];
             bad = update_site<POL_TM, true>(q, m, f3, nullptr);
             batch_acc(f3, b.slot, b.acc, d, idx, t + 1);
         } else {
             bad = update_site<POL_TM, true>(q, m, nullptr, nullptr);
         }
-        if (bad) atomicOr(b.err + tl.inst, kErrUnstable);
-        store_site(fout, d.pstride, idx, q);
+        if (bad) atomicOr(err, kErrUnstable);
+        store_site(fout, f.ps, idx, q);
     }
 }
 
@@ -287,14 +304,16 @@ __global__ void __launch_bounds__(NTH, 3)
         fence_mbar_init();
     }
     __syncthreads();
-    int cur = next_active(b, blockIdx.x, t);
-    if (threadIdx.x == 0 && cur >= 0) batch_issue(maps, b.tiles[cur], p, S.stage, &bar);
+    Tile tl;
+    int cur = next_active(b, blockIdx.x, t, &tl);
+    if (threadIdx.x == 0 && cur >= 0) batch_issue(maps, tl, p, S.stage, &bar);
     unsigned phase = 0;
     while (cur >= 0) {  // uniform over the block
-        const Tile tl = b.tiles[cur];
+        // this tile's descriptor fields and the next tile: their loads overlap the wait below
         const InstDesc &d = b.inst[tl.inst];
-        const int nxt = next_active(b, cur + gridDim.x, t);
-        const bool two = t + 1 < d.steps;
+        const TileFields f = tile_fields(d);
+        Tile ntl;
+        const int nxt = next_active(b, cur + gridDim.x, t, &ntl);
         if (threadIdx.x < 3) smat[threadIdx.x] = d.mtabf[threadIdx.x];
         if (threadIdx.x == 32) sp = tl.x0 == 0 ? source_pair_f(d.src, t) : SrcPairF{0.f, 0.f, 0.f, 0.f};
         const bool ok = mbar_wait(&bar, phase);
@@ -303,12 +322,13 @@ __global__ void __launch_bounds__(NTH, 3)
             if (threadIdx.x == 0) atomicOr(b.err + tl.inst, kErrTimeout);
             return;
         }
-        if (t + 1 >= d.acc_from)
-            batch2_tile<true>(b, tl, d, t, two, S, smat, sp, maps, p, nxt, &bar);
+        if (t + 1 >= f.acc_from)
+            batch2_tile<true>(b, tl, d, f, t, S, smat, sp, maps, p, nxt >= 0, ntl, &bar);
         else
-            batch2_tile<false>(b, tl, d, t, two, S, smat, sp, maps, p, nxt, &bar);
+            batch2_tile<false>(b, tl, d, f, t, S, smat, sp, maps, p, nxt >= 0, ntl, &bar);
         __syncthreads();  // shared memory is free for the next tile
         cur = nxt;
+        tl = ntl;
     }
 }
 
