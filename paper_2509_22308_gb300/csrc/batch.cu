@@ -46,6 +46,18 @@ struct Tile {
     int inst, x0, y0, pad;
 };
 
+// Everything the two-step kernel needs of a tile and its instance: one 128-byte record per
+// tile, built with the tile list, so that a CTA reads it with one vector load per lane of
+// one warp instead of walking tile -> instance -> fields in every warp.
+struct alignas(16) TileCtx {
+    int inst, x0, y0, nx;
+    int ny, pitch, kind, ay0;  // ay0, ay1: rows holding contour stencil sites
+    int ay1, pad0, pad1, pad2;
+    long long base, pstride, steps, acc_from;
+    MatT<float> m[3];  // region table in FP32
+};
+static_assert(sizeof(TileCtx) == 128, "TileCtx is eight 16-byte words");
+
 template <typename T>
 struct BatchArgs {
     const InstDesc *inst;
@@ -200,54 +212,56 @@ __device__ __forceinline__ void batch_acc(const double *f3, const int *slot, dou
 using namespace tma_tile;
 
 // Tensor maps of instance i: maps[3 i + p] its state in buffer p, maps[3 i + 2] its ids.
-__device__ __forceinline__ void batch_issue(const CUtensorMap *maps, const Tile &tl, int p, unsigned char *stage,
-                                            uint64_t *bar) {
-    issue_tile(maps + 3 * tl.inst + p, maps + 3 * tl.inst + 2, tl.x0, tl.y0, stage, bar);
+__device__ __forceinline__ void batch_issue(const CUtensorMap *maps, int inst, int x0, int y0, int p,
+                                            unsigned char *stage, uint64_t *bar) {
+    issue_tile(maps + 3 * inst + p, maps + 3 * inst + 2, x0, y0, stage, bar);
 }
 
-// The first tile j, j + gridDim.x, ... whose instance still runs at t (into *tl); -1 if none.
-__device__ __forceinline__ int next_active(const BatchArgs<float> &b, int j, long long t, Tile *tl) {
-    for (; j < b.n_tiles; j += gridDim.x) {
-        *tl = b.tiles[j];
-        if (t < b.inst[tl->inst].steps) return j;
-    }
+// The first tile j, j + gridDim.x, ... whose instance still runs at t; -1 if none.
+__device__ __forceinline__ int next_active(const TileCtx *ctx, int n, int j, long long t) {
+    for (; j < n; j += gridDim.x)
+        if (t < ctx[j].steps) return j;
     return -1;
 }
 
-// What a tile needs of its instance's descriptor, in registers (read through a plain
-// reference inside the site loops, the fields would be reloaded after every store, since
-// the compiler cannot rule out aliasing with the state).
-struct TileFields {
-    int nx, ny, pitch, kind, ay0, ay1;
-    size_t ps, base;
-    long long steps, acc_from;
-};
-__device__ __forceinline__ TileFields tile_fields(const InstDesc &d) {
-    return TileFields{d.nx, d.ny, d.pitch, d.src.kind, d.y0, d.y1, d.pstride, d.base, d.steps, d.acc_from};
+// Source values of every instance at the launch's two times, once per launch (one thread
+// per instance), so that no step-kernel thread evaluates them in FP64.
+__global__ void k_batch_source(const InstDesc *__restrict__ desc, int n, const long long *__restrict__ t_in,
+                               SrcPairF *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = source_pair_f(desc[i].src, *t_in);
 }
 
-template <bool ACC>
-__device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Tile &tl, const InstDesc &d,
-                                            const TileFields &f, long long t, const TileSmem &S,
-                                            const MatT<float> *smat, const SrcPairF &sp, const CUtensorMap *maps,
-                                            int p, bool has_next, const Tile &ntl, uint64_t *bar) {
-    const int nx = f.nx, ny = f.ny, x0 = tl.x0, y0 = tl.y0;
-    const bool two = t + 1 < f.steps;
-    float *fout = b.fout + f.base;
-    unsigned *err = b.err + tl.inst;
-    const bool src0 = t >= 1 && f.kind != SRC_NONE, src1 = f.kind != SRC_NONE;
+// TWO: the instance runs both steps of the launch (the common case; a run that ends at t + 1
+// takes phase 1 only, on the tile's own sites, straight to global memory).  ACC: the
+// instance accumulates Fourier sums at t or t + 1.  Both are template parameters so that
+// the common body carries no per-site branch on them.  c: the tile's record (shared
+// memory, copied to registers here).
+template <bool ACC, bool TWO>
+__device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const TileCtx &c, long long t,
+                                            const TileSmem &S, const SrcPairF &sp, const CUtensorMap *maps,
+                                            int p, bool has_next, const int4 &next, uint64_t *bar) {
+    const int nx = c.nx, ny = c.ny, x0 = c.x0, y0 = c.y0, pitch = c.pitch, kind = c.kind;
+    const int ay0 = c.ay0, ay1 = c.ay1;
+    const size_t ps = (size_t)c.pstride;
+    const long long acc_from = c.acc_from;
+    const MatT<float> *smat = c.m;
+    float *fout = b.fout + c.base;
+    unsigned *err = b.err + c.inst;
+    const InstDesc &d = b.inst[c.inst];  // read by the accumulation only
+    const bool src0 = t >= 1 && kind != SRC_NONE, src1 = kind != SRC_NONE;
     for (int k = threadIdx.x; k < IW * IH; k += NTH) {
         const int lx = k % IW, ly = k / IW, x = x0 - 1 + lx, y = y0 - 1 + ly;
         if (x < 0 || x >= nx || y < 0 || y >= ny) continue;
         const bool interior = lx >= 1 && lx <= KW && ly >= 1 && ly <= KH;
-        if (!two && !interior) continue;
+        if (!TWO && !interior) continue;
         Pop<float> q;
         pull_buf<RW, RH>(S.raw, nx, ny, x, y, lx + 3, ly + 1, q);
-        if (x == 0 && src0) inject_source_t(f.kind, sp.g0, sp.inc0, q);
+        if (x == 0 && src0) inject_source_t(kind, sp.g0, sp.inc0, q);
         const uint8_t id = S.ids[(ly + 1) * MW + lx + MOFF - 1];
-        const size_t idx = (size_t)y * f.pitch + x;
+        const size_t idx = (size_t)y * pitch + x;
         bool bad;
-        if (ACC && interior && t >= f.acc_from && y >= f.ay0 && y <= f.ay1) {
+        if (ACC && interior && t >= acc_from && y >= ay0 && y <= ay1) {
             double f3[3];
             bad = update_site<POL_TM, true>(q, smat[id], f3, nullptr);
             batch_acc(f3, b.slot, b.acc, d, idx, t);
@@ -255,80 +269,100 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
             bad = update_site<POL_TM, true>(q, smat[id], nullptr, nullptr);
         }
         if (bad) atomicOr(err, kErrUnstable);
-        if (two) {
+        if (TWO) {
             put_inter(S.inter, ly, lx, q);
             S.inter_ids[ly * IW + lx] = id;
         } else {
-            store_site(fout, f.ps, idx, q);
+            store_site(fout, ps, idx, q);
         }
     }
     __syncthreads();  // the stage is read
     if (threadIdx.x == 0 && has_next) {
         fence_proxy_async_smem();
-        batch_issue(maps, ntl, p, S.stage, bar);
+        batch_issue(maps, next.x, next.y, next.z, p, S.stage, bar);
     }
-    if (!two) return;
-    for (int k = threadIdx.x; k < KW * KH; k += NTH) {
-        const int lx = k % KW, ly = k / KW, x = x0 + lx, y = y0 + ly;
-        if (x >= nx || y >= ny) continue;
-        Pop<float> q;
-        pull_buf<IW, IH>(S.inter, nx, ny, x, y, lx + 1, ly + 1, q);
-        if (x == 0 && src1) inject_source_t(f.kind, sp.g1, sp.inc1, q);
-        const MatT<float> m = smat[S.inter_ids[(ly + 1) * IW + lx + 1]];
-        const size_t idx = (size_t)y * f.pitch + x;
-        bool bad;
-        if (ACC && t + 1 >= f.acc_from && y >= f.ay0 && y <= f.ay1) {
-            double f3[3];
-            bad = update_site<POL_TM, true>(q, m, f3, nullptr);
-            batch_acc(f3, b.slot, b.acc, d, idx, t + 1);
-        } else {
-            bad = update_site<POL_TM, true>(q, m, nullptr, nullptr);
+    if constexpr (TWO) {
+        for (int k = threadIdx.x; k < KW * KH; k += NTH) {
+            const int lx = k % KW, ly = k / KW, x = x0 + lx, y = y0 + ly;
+            if (x >= nx || y >= ny) continue;
+            Pop<float> q;
+            pull_buf<IW, IH>(S.inter, nx, ny, x, y, lx + 1, ly + 1, q);
+            if (x == 0 && src1) inject_source_t(kind, sp.g1, sp.inc1, q);
+            const MatT<float> m = smat[S.inter_ids[(ly + 1) * IW + lx + 1]];
+            const size_t idx = (size_t)y * pitch + x;
+            bool bad;
+            if (ACC && t + 1 >= acc_from && y >= ay0 && y <= ay1) {
+                double f3[3];
+                bad = update_site<POL_TM, true>(q, m, f3, nullptr);
+                batch_acc(f3, b.slot, b.acc, d, idx, t + 1);
+            } else {
+                bad = update_site<POL_TM, true>(q, m, nullptr, nullptr);
+            }
+            if (bad) atomicOr(err, kErrUnstable);
+            store_site(fout, ps, idx, q);
         }
-        if (bad) atomicOr(err, kErrUnstable);
-        store_site(fout, f.ps, idx, q);
     }
 }
 
 __global__ void __launch_bounds__(NTH, 3)
-    k_batch_step2(const BatchArgs<float> b, const CUtensorMap *__restrict__ maps, int p,
-                  const long long *__restrict__ t_in, long long *__restrict__ t_out) {
+    k_batch_step2(const BatchArgs<float> b, const TileCtx *__restrict__ ctx, const SrcPairF *__restrict__ srcs,
+                  const CUtensorMap *__restrict__ maps, int p, const long long *__restrict__ t_in,
+                  long long *__restrict__ t_out) {
     extern __shared__ unsigned char sm_dyn[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ MatT<float> smat[3];
+    __shared__ TileCtx sc;  // the current tile's record
     __shared__ SrcPairF sp;
+    __shared__ int s_next;
+    __shared__ int4 s_nhead;  // inst, x0, y0 of the next tile (set and read by thread 0)
     const TileSmem S = carve(sm_dyn);
     const long long t = *t_in;
+    const int n = b.n_tiles;
     if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + 2;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
-    Tile tl;
-    int cur = next_active(b, blockIdx.x, t, &tl);
-    if (threadIdx.x == 0 && cur >= 0) batch_issue(maps, tl, p, S.stage, &bar);
+    // the loop's tile index lives in thread 0 (which finds the next active tile and issues
+    // its copies) and reaches the block through shared memory
+    int cur = next_active(ctx, n, blockIdx.x, t);
+    if (threadIdx.x == 0 && cur >= 0) {
+        const int4 head = reinterpret_cast<const int4 *>(ctx + cur)[0];  // inst, x0, y0
+        batch_issue(maps, head.x, head.y, head.z, p, S.stage, &bar);
+    }
     unsigned phase = 0;
     while (cur >= 0) {  // uniform over the block
-        // this tile's descriptor fields and the next tile: their loads overlap the wait below
-        const InstDesc &d = b.inst[tl.inst];
-        const TileFields f = tile_fields(d);
-        Tile ntl;
-        const int nxt = next_active(b, cur + gridDim.x, t, &ntl);
-        if (threadIdx.x < 3) smat[threadIdx.x] = d.mtabf[threadIdx.x];
-        if (threadIdx.x == 32) sp = tl.x0 == 0 ? source_pair_f(d.src, t) : SrcPairF{0.f, 0.f, 0.f, 0.f};
+        if (threadIdx.x < 8) reinterpret_cast<int4 *>(&sc)[threadIdx.x] = reinterpret_cast<const int4 *>(ctx + cur)[threadIdx.x];
+        if (threadIdx.x == 0) {
+            const int nxt = next_active(ctx, n, cur + gridDim.x, t);
+            s_next = nxt;
+            if (nxt >= 0) s_nhead = reinterpret_cast<const int4 *>(ctx + nxt)[0];
+        }
+        if (threadIdx.x == 32) {
+            const int4 h = reinterpret_cast<const int4 *>(ctx + cur)[0];
+            sp = h.y == 0 ? srcs[h.x] : SrcPairF{0.f, 0.f, 0.f, 0.f};
+        }
         const bool ok = mbar_wait(&bar, phase);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {  // the tile's copies never completed: report, leave
-            if (threadIdx.x == 0) atomicOr(b.err + tl.inst, kErrTimeout);
+            if (threadIdx.x == 0) atomicOr(b.err + sc.inst, kErrTimeout);
             return;
         }
-        if (t + 1 >= f.acc_from)
-            batch2_tile<true>(b, tl, d, f, t, S, smat, sp, maps, p, nxt >= 0, ntl, &bar);
-        else
-            batch2_tile<false>(b, tl, d, f, t, S, smat, sp, maps, p, nxt >= 0, ntl, &bar);
+        const int nxt = s_next;
+        const bool acc = t + 1 >= sc.acc_from, two = t + 1 < sc.steps;  // uniform over the block
+        if (two) {
+            if (acc)
+                batch2_tile<true, true>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+            else
+                batch2_tile<false, true>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+        } else {
+            if (acc)
+                batch2_tile<true, false>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+            else
+                batch2_tile<false, false>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+        }
         __syncthreads();  // shared memory is free for the next tile
         cur = nxt;
-        tl = ntl;
     }
 }
 
@@ -438,6 +472,8 @@ struct lbm_em_batch {
     int tile_w = 0, tile_h = 0, ctas = 0;
     bool two = false;  // two steps per launch (FP32, fixed run lengths; TMA-staged 64 x 8 tiles)
     CUtensorMap *d_maps = nullptr;  // FP32: per instance, its state in buffer 0 and 1 and its ids
+    TileCtx *d_ctx = nullptr;       // FP32: one record per tile of the tile list
+    SrcPairF *d_srcs = nullptr;     // FP32: per instance, the source values of the current launch
     int two_ctas = 0;               // resident CTAs per SM of the two-step kernel (0: not available)
     cudaGraphExec_t graph = nullptr;
     bool ran = false;
@@ -470,6 +506,8 @@ static void batch_free(lbm_em_batch *b) {
     cudaFree(b->d_prev);
     cudaFree(b->d_settled);
     cudaFree(b->d_maps);
+    cudaFree(b->d_ctx);
+    cudaFree(b->d_srcs);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -493,6 +531,26 @@ static lbm_em_status batch_tiles(lbm_em_batch *b, int tw, int th) {
     b->n_tiles = (int)tiles.size();
     b->tile_w = tw;
     b->tile_h = th;
+    if (!st && b->prec == LBM_EM_F32) {  // the two-step kernel's per-tile records
+        std::vector<TileCtx> ctx(tiles.size());
+        for (size_t k = 0; k < tiles.size(); ++k) {
+            const Tile &tl = tiles[k];
+            const InstDesc &d = b->desc[tl.inst];
+            TileCtx &c = ctx[k];
+            std::memset(&c, 0, sizeof(c));
+            c.inst = tl.inst, c.x0 = tl.x0, c.y0 = tl.y0, c.nx = d.nx;
+            c.ny = d.ny, c.pitch = d.pitch, c.kind = d.src.kind, c.ay0 = d.y0, c.ay1 = d.y1;
+            c.base = (long long)d.base, c.pstride = (long long)d.pstride, c.steps = d.steps, c.acc_from = d.acc_from;
+            for (int r = 0; r < 3; ++r) c.m[r] = d.mtabf[r];
+        }
+        cudaFree(b->d_ctx);
+        b->d_ctx = nullptr;
+        st = cuda_status(cudaMalloc(&b->d_ctx, ctx.size() * sizeof(TileCtx)), "cudaMalloc(tile records)");
+        if (!st)
+            st = cuda_status(cudaMemcpyAsync(b->d_ctx, ctx.data(), ctx.size() * sizeof(TileCtx),
+                                             cudaMemcpyHostToDevice, b->stream),
+                             "uploading tile records");  // pageable: staged before the call returns
+    }
     return st;
 }
 
@@ -534,8 +592,11 @@ static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, int p) {
         BatchArgs<float> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, ilog2(b->tile_w),
                            (const float *)b->buf[p], (float *)b->buf[1 - p], b->d_mat, b->d_slot,
                            b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
-        if (b->two)
-            k_batch_step2<<<grid, NTH, kSmemBytes, s>>>(a, b->d_maps, p, b->d_time + p, b->d_time + (1 - p));
+        if (b->two) {
+            k_batch_source<<<(b->n + 127) / 128, 128, 0, s>>>(b->d_desc, b->n, b->d_time + p, b->d_srcs);
+            k_batch_step2<<<grid, NTH, kSmemBytes, s>>>(a, b->d_ctx, b->d_srcs, b->d_maps, p, b->d_time + p,
+                                                        b->d_time + (1 - p));
+        }
         else
             k_batch_step<float><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
     }
@@ -806,6 +867,7 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
                  "encoding an instance's id map");
         }
         BTRY(cudaMalloc(&b->d_maps, maps.size() * sizeof(CUtensorMap)), "cudaMalloc(tensor maps)");
+        BTRY(cudaMalloc(&b->d_srcs, (size_t)n * sizeof(SrcPairF)), "cudaMalloc(source values)");
         BTRY(cudaMemcpyAsync(b->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
                              b->stream),
              "upload");
