@@ -103,20 +103,6 @@ __device__ __forceinline__ void source_values(const SourceParams &s, long long t
     *inc = ramp * p0;
 }
 
-// source_values() for kernels whose blocks own column 0: called by one thread per block,
-// not inlined.  Every row's x = 0 thread evaluating it on its own ran the double-precision
-// evaluation once per warp, and on GB300's narrow FP64 pipe an instruction with one active
-// lane costs as much as a full warp's: 13 % more FP64-pipe work for the FP64 step on a
-// 512^2 lattice.
-struct SrcVals {
-    double g_open, inc;
-};
-static __device__ __noinline__ SrcVals source_values_once(const SourceParams src, long long t) {
-    SrcVals v;
-    source_values(src, t, &v.g_open, &v.inc);
-    return v;
-}
-
 // Adds the left-edge source of time t to the pulled populations of a site at x = 0, from
 // the values source_values() gives for t: OPEN adds g_open to e_+x,z (and so, through
 // h_+x,y = -e_+x,z, subtracts it from h_+x,y); HARD replaces the incoming pair by the

@@ -20,19 +20,10 @@ __global__ void __launch_bounds__(BX *BY) k_step(const StepArgs<T> a, const T *_
     const int y = blockIdx.y * BY + threadIdx.y;
     const long long t = *t_in;
     if (x == 0 && y == 0) *t_out = t + 1;
-    // source values of t for the blocks that own column 0, once per block (see
-    // source_values_once), before any thread of the block leaves
-    __shared__ SrcVals s_src;
-    const bool col0 = blockIdx.x == 0 && t >= 1 && a.src.kind != SRC_NONE;  // uniform over the block
-    if (col0) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) s_src = source_values_once(a.src, t);
-        __syncthreads();
-    }
     if (x >= a.nx || y >= a.ny) return;
 
     Pop<T> p;
-    pull_planes(a, fin, x, y, p);
-    if (x == 0 && col0) inject_source(a.src.kind, s_src.g_open, s_src.inc, p);
+    pull_site(a, fin, x, y, t, p);
     const size_t idx = (size_t)y * a.pitch + x;
     const MatT<T> m = a.mtab[a.mat[idx]];
     const bool acc = ACC && y >= a.accp.y0 && y <= a.accp.y1 && a.accp.slot[idx] >= 0;

@@ -43,14 +43,6 @@ __global__ void __launch_bounds__(BX *BY) k_step_f16(const F16Args a, const long
     const int y = blockIdx.y * BY + threadIdx.y;
     const long long t = *t_in;
     if (x0 == 0 && y == 0) *t_out = t + 1;
-    // source values of t for the blocks that own column 0, once per block (see
-    // source_values_once), before any thread of the block leaves
-    __shared__ SrcVals s_src;
-    const bool col0 = blockIdx.x == 0 && t >= 1 && a.src.kind != SRC_NONE;  // uniform over the block
-    if (col0) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) s_src = source_values_once(a.src, t);
-        __syncthreads();
-    }
     if (x0 >= a.nx || y >= a.ny) return;
     const bool has1 = x0 + 1 < a.nx;
     const size_t ps = a.pstride;
@@ -115,7 +107,7 @@ __global__ void __launch_bounds__(BX *BY) k_step_f16(const F16Args a, const long
     v = h2(P_HYZ, r);
     p0.hyz = rebuild(Yc.x, __low2half(v), is);
     p1.hyz = rebuild(Yc.y, __high2half(v), is);
-    if (x0 == 0 && col0) inject_source(a.src.kind, s_src.g_open, s_src.inc, p0);
+    f16_source(a.src, x0, t, p0);
 
     float E30, Hx0, Hy0, D0, E31, Hx1, Hy1, D1;
     moments(p0, m0, &E30, &Hx0, &Hy0, &D0);
