@@ -143,8 +143,10 @@ cudaError_t allow_smem() {
     return cudaFuncSetAttribute(k_step2_tma<ACC, POL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
 }
 
-cudaError_t encode(CUtensorMap *map, CUtensorMapDataType type, cuuint32_t rank, const void *base,
-                   const cuuint64_t *dims, const cuuint64_t *strides, const cuuint32_t *box) {
+}  // namespace
+
+cudaError_t encode_tiled(CUtensorMap *map, CUtensorMapDataType type, cuuint32_t rank, const void *base,
+                         const cuuint64_t *dims, const cuuint64_t *strides, const cuuint32_t *box) {
     EncodeTiled fn = encoder();
     if (!fn) return cudaErrorNotSupported;
     const cuuint32_t estr[3] = {1, 1, 1};
@@ -154,14 +156,12 @@ cudaError_t encode(CUtensorMap *map, CUtensorMapDataType type, cuuint32_t rank, 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-}  // namespace
-
 cudaError_t encode_plane_map(CUtensorMap *map, const float *base, int nx, int ny, int pitch, size_t pstride) {
     if (((uintptr_t)base & 15u) || (pitch % 4) || (pstride % 4)) return cudaErrorInvalidValue;
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)NPLANES};
     const cuuint64_t strides[2] = {(cuuint64_t)pitch * sizeof(float), (cuuint64_t)pstride * sizeof(float)};
     const cuuint32_t box[3] = {(cuuint32_t)RW, (cuuint32_t)RH, (cuuint32_t)NPLANES};
-    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box);
+    return encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box);
 }
 
 cudaError_t encode_id_map(CUtensorMap *map, const uint8_t *ids, int nx, int ny, int pitch) {
@@ -169,7 +169,7 @@ cudaError_t encode_id_map(CUtensorMap *map, const uint8_t *ids, int nx, int ny, 
     const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
     const cuuint64_t strides[1] = {(cuuint64_t)pitch};
     const cuuint32_t box[2] = {(cuuint32_t)MW, (cuuint32_t)RH};
-    return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, ids, dims, strides, box);
+    return encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, ids, dims, strides, box);
 }
 
 cudaError_t step2_tma_prepare(int *max_ctas) {

@@ -14,6 +14,11 @@ namespace lbmem {
 // table (4 KB): 72 KB, three CTAs per SM.
 constexpr int kTmaTileW = 64, kTmaTileH = 8, kTmaThreads = 256;
 
+// cuTensorMapEncodeTiled (through the driver entry point, no link against libcuda): no
+// interleave, no swizzle, 256-byte L2 promotion, zero fill outside the tensor.
+cudaError_t encode_tiled(CUtensorMap *map, CUtensorMapDataType type, cuuint32_t rank, const void *base,
+                         const cuuint64_t *dims, const cuuint64_t *strides, const cuuint32_t *box);
+
 // Tensor map of an FP32 state buffer (11 planes of ny rows of `pitch` floats, plane stride
 // `pstride` floats) with the kernel's box.  base 16-byte aligned, pitch and pstride
 // multiples of 4; cudaErrorInvalidValue otherwise or if the driver rejects the map.
