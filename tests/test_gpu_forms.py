@@ -179,6 +179,27 @@ def test_two_steps_per_launch_is_bit_identical(inst, prec):
         assert np.array_equal(a.force_torque(c), b.force_torque(c))
 
 
+@pytest.mark.parametrize("shape", [(7, 5), (64, 8), (128, 16), (65, 9), (200, 35)],
+                         ids=lambda s: f"{s[0]}x{s[1]}")
+def test_fp32_two_steps_on_tile_edge_shapes(shape):
+    """The FP32 two-step kernel copies 64 x 8 tiles with their halo in boxes of 72 x 12 sites:
+    a lattice smaller than the box in both directions, exactly one tile, exact multiples of
+    the tile and one site beyond them all give the bits of one step per launch (fields, over
+    even and odd step counts)."""
+    nx, ny = shape
+    a = min(nx, ny) / 3.0
+    inst = dict(nx=nx, ny=ny, a=a, phi0=0.4, eps1=3.0, eps2=1.0, pec2=True, period=24, periods=3,
+                R=a, ramp=24)
+    with L.solver_for_instance(inst, "f32", steps_per_launch="two") as s2, \
+            L.solver_for_instance(inst, "f32", steps_per_launch="one") as s1:
+        for n in (1, 2, 5, 33, 64):
+            s2.step(n)
+            s1.step(n)
+            for x, y in zip(s2.fields(), s1.fields()):
+                assert np.array_equal(x, y)
+        assert np.abs(s2.fields()[0]).max() > 0  # the source has reached the field
+
+
 def test_f16dev_split_runs_agree_bitwise():
     """The FP16-deviation form gives the same bits however a run is split into calls."""
     inst = W.small_cases()[2]
