@@ -514,9 +514,11 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     if (h->tb && h->prec == LBM_EM_F32) {
         TRY(step2_tma_prepare(&h->tma_ctas), "configuring the TMA-staged two-step kernel");
         for (int b = 0; b < 2; ++b)
-            TRY(encode_plane_map(&h->tmap[b], (const float *)h->buf[b], h->nx, h->ny, h->pitch, h->pstride),
+            TRY(encode_plane_map(&h->tmap[b], (const float *)h->buf[b], h->nx, h->ny, h->pitch, h->pstride,
+                                 kTmaTileW, kTmaTileH),
                 "encoding the tensor map of a state buffer");
-        TRY(encode_id_map(&h->idmap, h->d_mat, h->nx, h->ny, h->pitch), "encoding the tensor map of the ids");
+        TRY(encode_id_map(&h->idmap, h->d_mat, h->nx, h->ny, h->pitch, kTmaTileW, kTmaTileH),
+            "encoding the tensor map of the ids");
     }
     TRY(dev_alloc(h, &h->d_mtab, 256 * sizeof(MatT<double>)), "allocating the material table");
     TRY(dev_alloc(h, &h->d_time, 2 * sizeof(long long)), "allocating the time words");

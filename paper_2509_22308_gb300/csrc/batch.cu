@@ -195,7 +195,7 @@ __device__ __forceinline__ void batch_acc(const double *f3, const int *slot, dou
 }
 
 // Two steps per launch for the FP32 batch with fixed run lengths, on the TMA-staged tile
-// of the single-domain FP32 kernel (tile_tma.cuh, step2_tma.cu): each 64 x 8 tile of an
+// of the single-domain FP32 kernel (tile_tma.cuh, step2_tma.cu): each 64 x 8 (or 32 x 16) tile of an
 // instance arrives in shared memory with a two-site halo and its material ids through
 // the instance's tensor maps, advances to t + 1 together with a one-site halo, then to
 // t + 2, so the packed state crosses HBM once per two steps.  A persistent CTA walks the
@@ -212,9 +212,10 @@ __device__ __forceinline__ void batch_acc(const double *f3, const int *slot, dou
 using namespace tma_tile;
 
 // Tensor maps of instance i: maps[3 i + p] its state in buffer p, maps[3 i + 2] its ids.
+template <class G>
 __device__ __forceinline__ void batch_issue(const CUtensorMap *maps, int inst, int x0, int y0, int p,
                                             unsigned char *stage, uint64_t *bar) {
-    issue_tile(maps + 3 * inst + p, maps + 3 * inst + 2, x0, y0, stage, bar);
+    issue_tile<G>(maps + 3 * inst + p, maps + 3 * inst + 2, x0, y0, stage, bar);
 }
 
 // The first tile j, j + gridDim.x, ... whose instance still runs at t; -1 if none.
@@ -237,7 +238,7 @@ __global__ void k_batch_source(const InstDesc *__restrict__ desc, int n, const l
 // instance accumulates Fourier sums at t or t + 1.  Both are template parameters so that
 // the common body carries no per-site branch on them.  c: the tile's record (shared
 // memory, copied to registers here).
-template <bool ACC, bool TWO>
+template <class G, bool ACC, bool TWO>
 __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const TileCtx &c, long long t,
                                             const TileSmem &S, const SrcPairF &sp, const CUtensorMap *maps,
                                             int p, bool has_next, const int4 &next, uint64_t *bar) {
@@ -250,15 +251,15 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
     unsigned *err = b.err + c.inst;
     const InstDesc &d = b.inst[c.inst];  // read by the accumulation only
     const bool src0 = t >= 1 && kind != SRC_NONE, src1 = kind != SRC_NONE;
-    for (int k = threadIdx.x; k < IW * IH; k += NTH) {
-        const int lx = k % IW, ly = k / IW, x = x0 - 1 + lx, y = y0 - 1 + ly;
+    for (int k = threadIdx.x; k < G::IW * G::IH; k += NTH) {
+        const int lx = k % G::IW, ly = k / G::IW, x = x0 - 1 + lx, y = y0 - 1 + ly;
         if (x < 0 || x >= nx || y < 0 || y >= ny) continue;
-        const bool interior = lx >= 1 && lx <= KW && ly >= 1 && ly <= KH;
+        const bool interior = lx >= 1 && lx <= G::KW && ly >= 1 && ly <= G::KH;
         if (!TWO && !interior) continue;
         Pop<float> q;
-        pull_buf<RW, RH>(S.raw, nx, ny, x, y, lx + 3, ly + 1, q);
+        pull_buf<G::RW, G::RH>(S.raw, nx, ny, x, y, lx + 3, ly + 1, q);
         if (x == 0 && src0) inject_source_t(kind, sp.g0, sp.inc0, q);
-        const uint8_t id = S.ids[(ly + 1) * MW + lx + MOFF - 1];
+        const uint8_t id = S.ids[(ly + 1) * G::MW + lx + MOFF - 1];
         const size_t idx = (size_t)y * pitch + x;
         bool bad;
         if (ACC && interior && t >= acc_from && y >= ay0 && y <= ay1) {
@@ -270,8 +271,8 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
         }
         if (bad) atomicOr(err, kErrUnstable);
         if (TWO) {
-            put_inter(S.inter, ly, lx, q);
-            S.inter_ids[ly * IW + lx] = id;
+            put_inter<G>(S.inter, ly, lx, q);
+            S.inter_ids[ly * G::IW + lx] = id;
         } else {
             store_site(fout, ps, idx, q);
         }
@@ -279,16 +280,16 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
     __syncthreads();  // the stage is read
     if (threadIdx.x == 0 && has_next) {
         fence_proxy_async_smem();
-        batch_issue(maps, next.x, next.y, next.z, p, S.stage, bar);
+        batch_issue<G>(maps, next.x, next.y, next.z, p, S.stage, bar);
     }
     if constexpr (TWO) {
-        for (int k = threadIdx.x; k < KW * KH; k += NTH) {
-            const int lx = k % KW, ly = k / KW, x = x0 + lx, y = y0 + ly;
+        for (int k = threadIdx.x; k < G::KW * G::KH; k += NTH) {
+            const int lx = k % G::KW, ly = k / G::KW, x = x0 + lx, y = y0 + ly;
             if (x >= nx || y >= ny) continue;
             Pop<float> q;
-            pull_buf<IW, IH>(S.inter, nx, ny, x, y, lx + 1, ly + 1, q);
+            pull_buf<G::IW, G::IH>(S.inter, nx, ny, x, y, lx + 1, ly + 1, q);
             if (x == 0 && src1) inject_source_t(kind, sp.g1, sp.inc1, q);
-            const MatT<float> m = smat[S.inter_ids[(ly + 1) * IW + lx + 1]];
+            const MatT<float> m = smat[S.inter_ids[(ly + 1) * G::IW + lx + 1]];
             const size_t idx = (size_t)y * pitch + x;
             bool bad;
             if (ACC && t + 1 >= acc_from && y >= ay0 && y <= ay1) {
@@ -304,6 +305,7 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
     }
 }
 
+template <class G>
 __global__ void __launch_bounds__(NTH, 3)
     k_batch_step2(const BatchArgs<float> b, const TileCtx *__restrict__ ctx, const SrcPairF *__restrict__ srcs,
                   const CUtensorMap *__restrict__ maps, int p, const long long *__restrict__ t_in,
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(NTH, 3)
     __shared__ SrcPairF sp;
     __shared__ int s_next;
     __shared__ int4 s_nhead;  // inst, x0, y0 of the next tile (set and read by thread 0)
-    const TileSmem S = carve(sm_dyn);
+    const TileSmem S = carve<G>(sm_dyn);
     const long long t = *t_in;
     const int n = b.n_tiles;
     if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + 2;
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(NTH, 3)
     int cur = next_active(ctx, n, blockIdx.x, t);
     if (threadIdx.x == 0 && cur >= 0) {
         const int4 head = reinterpret_cast<const int4 *>(ctx + cur)[0];  // inst, x0, y0
-        batch_issue(maps, head.x, head.y, head.z, p, S.stage, &bar);
+        batch_issue<G>(maps, head.x, head.y, head.z, p, S.stage, &bar);
     }
     unsigned phase = 0;
     while (cur >= 0) {  // uniform over the block
@@ -352,14 +354,14 @@ __global__ void __launch_bounds__(NTH, 3)
         const bool acc = t + 1 >= sc.acc_from, two = t + 1 < sc.steps;  // uniform over the block
         if (two) {
             if (acc)
-                batch2_tile<true, true>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+                batch2_tile<G, true, true>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
             else
-                batch2_tile<false, true>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+                batch2_tile<G, false, true>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
         } else {
             if (acc)
-                batch2_tile<true, false>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+                batch2_tile<G, true, false>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
             else
-                batch2_tile<false, false>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+                batch2_tile<G, false, false>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
         }
         __syncthreads();  // shared memory is free for the next tile
         cur = nxt;
@@ -470,11 +472,13 @@ struct lbm_em_batch {
     long long *d_time = nullptr;
     unsigned *d_err = nullptr;
     int tile_w = 0, tile_h = 0, ctas = 0;
-    bool two = false;  // two steps per launch (FP32, fixed run lengths; TMA-staged 64 x 8 tiles)
-    CUtensorMap *d_maps = nullptr;  // FP32: per instance, its state in buffer 0 and 1 and its ids
+    bool two = false;  // two steps per launch (FP32, fixed run lengths; TMA-staged 64 x 8 or 32 x 16 tiles)
+    // FP32, per tile shape of the two-step kernel (0: GeoWide, 1: GeoTall): per instance,
+    // tensor maps of its state in buffer 0 and 1 and of its ids; resident CTAs per SM
+    CUtensorMap *d_maps[2] = {nullptr, nullptr};
     TileCtx *d_ctx = nullptr;       // FP32: one record per tile of the tile list
     SrcPairF *d_srcs = nullptr;     // FP32: per instance, the source values of the current launch
-    int two_ctas = 0;               // resident CTAs per SM of the two-step kernel (0: not available)
+    int two_ctas[2] = {0, 0};
     cudaGraphExec_t graph = nullptr;
     bool ran = false;
     // convergence exits
@@ -505,7 +509,8 @@ static void batch_free(lbm_em_batch *b) {
     cudaFree(b->d_energy);
     cudaFree(b->d_prev);
     cudaFree(b->d_settled);
-    cudaFree(b->d_maps);
+    cudaFree(b->d_maps[0]);
+    cudaFree(b->d_maps[1]);
     cudaFree(b->d_ctx);
     cudaFree(b->d_srcs);
     if (b->cap) cudaStreamDestroy(b->cap);
@@ -594,8 +599,12 @@ static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, int p) {
                            b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
         if (b->two) {
             k_batch_source<<<(b->n + 127) / 128, 128, 0, s>>>(b->d_desc, b->n, b->d_time + p, b->d_srcs);
-            k_batch_step2<<<grid, NTH, kSmemBytes, s>>>(a, b->d_ctx, b->d_srcs, b->d_maps, p, b->d_time + p,
-                                                        b->d_time + (1 - p));
+            if (b->tile_w == GeoWide::KW)
+                k_batch_step2<GeoWide><<<grid, NTH, GeoWide::kSmemBytes, s>>>(a, b->d_ctx, b->d_srcs, b->d_maps[0], p,
+                                                                              b->d_time + p, b->d_time + (1 - p));
+            else
+                k_batch_step2<GeoTall><<<grid, NTH, GeoTall::kSmemBytes, s>>>(a, b->d_ctx, b->d_srcs, b->d_maps[1], p,
+                                                                              b->d_time + p, b->d_time + (1 - p));
         }
         else
             k_batch_step<float><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
@@ -636,8 +645,8 @@ static lbm_em_status batch_clear(lbm_em_batch *b) {
 }
 
 // Time a few steps of each (tile shape, CTAs per SM, steps per launch) candidate from the
-// cleared state; two steps per launch (TMA-staged 64 x 8 tiles, as many CTAs per SM as its
-// shared memory allows) is a candidate for FP32 runs of fixed length.
+// cleared state; two steps per launch (TMA-staged 64 x 8 and 32 x 16 tiles, as many CTAs per SM
+// as their shared memory allows) is a candidate for FP32 runs of fixed length.
 static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int want_c) {
     struct Cand {
         int w, h, c;
@@ -653,9 +662,13 @@ static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int
             if (want_c && c != want_c) continue;
             cands.push_back(Cand{sh[0], sh[1], c, false});
         }
-    if (b->two_ctas > 0 && b->conv_tol <= 0.0 && (!want_w || want_w == KW) && (!want_h || want_h == KH) &&
-        (!want_c || want_c == b->two_ctas))
-        cands.push_back(Cand{KW, KH, b->two_ctas, true});
+    const int two_shapes[2][2] = {{GeoWide::KW, GeoWide::KH}, {GeoTall::KW, GeoTall::KH}};
+    for (int g = 0; g < 2; ++g) {
+        const int w = two_shapes[g][0], h = two_shapes[g][1], c = b->two_ctas[g];
+        if (c > 0 && b->conv_tol <= 0.0 && (!want_w || want_w == w) && (!want_h || want_h == h) &&
+            (!want_c || want_c == c))
+            cands.push_back(Cand{w, h, c, true});
+    }
     if (cands.empty()) cands.push_back(Cand{want_w ? want_w : 64, want_h ? want_h : 4, want_c ? want_c : 4, false});
     if (cands.size() == 1) {
         b->ctas = cands[0].c;
@@ -849,29 +862,35 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
         BTRY(cudaMalloc(&b->d_cdesc, n * sizeof(ContourDesc)), "cudaMalloc(contour desc)");
         BTRY(cudaMemcpyAsync(b->d_cdesc, cd.data(), n * sizeof(ContourDesc), cudaMemcpyHostToDevice, b->stream), "upload");
     }
-    // FP32: tensor maps of every instance for the two-steps-per-launch kernel
+    // FP32: tensor maps of every instance for the two-step kernel, for both tile shapes
     if (b->prec == LBM_EM_F32) {
-        int per_sm = 0;
-        BTRY(cudaFuncSetAttribute(k_batch_step2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes),
-             "configuring the two-step batch kernel");
-        BTRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step2, NTH, kSmemBytes),
-             "occupancy of the two-step batch kernel");
-        std::vector<CUtensorMap> maps(3 * (size_t)n);
-        for (int i = 0; i < n; ++i) {
-            const InstDesc &d = b->desc[i];
-            for (int q = 0; q < 2; ++q)
-                BTRY(encode_plane_map(&maps[3 * i + q], (const float *)b->buf[q] + d.base, d.nx, d.ny, d.pitch,
-                                      d.pstride),
-                     "encoding an instance's tensor map");
-            BTRY(encode_id_map(&maps[3 * i + 2], b->d_mat + d.mat_base, d.nx, d.ny, d.pitch),
-                 "encoding an instance's id map");
+        const void *kern[2] = {(const void *)k_batch_step2<GeoWide>, (const void *)k_batch_step2<GeoTall>};
+        const size_t smem[2] = {GeoWide::kSmemBytes, GeoTall::kSmemBytes};
+        const int shape[2][2] = {{GeoWide::KW, GeoWide::KH}, {GeoTall::KW, GeoTall::KH}};
+        for (int g = 0; g < 2; ++g) {
+            int per_sm = 0;
+            BTRY(cudaFuncSetAttribute(kern[g], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem[g]),
+                 "configuring the two-step batch kernel");
+            BTRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[g], NTH, smem[g]),
+                 "occupancy of the two-step batch kernel");
+            std::vector<CUtensorMap> maps(3 * (size_t)n);
+            for (int i = 0; i < n; ++i) {
+                const InstDesc &d = b->desc[i];
+                for (int q = 0; q < 2; ++q)
+                    BTRY(encode_plane_map(&maps[3 * i + q], (const float *)b->buf[q] + d.base, d.nx, d.ny, d.pitch,
+                                          d.pstride, shape[g][0], shape[g][1]),
+                         "encoding an instance's tensor map");
+                BTRY(encode_id_map(&maps[3 * i + 2], b->d_mat + d.mat_base, d.nx, d.ny, d.pitch, shape[g][0],
+                                   shape[g][1]),
+                     "encoding an instance's id map");
+            }
+            BTRY(cudaMalloc(&b->d_maps[g], maps.size() * sizeof(CUtensorMap)), "cudaMalloc(tensor maps)");
+            BTRY(cudaMemcpyAsync(b->d_maps[g], maps.data(), maps.size() * sizeof(CUtensorMap),
+                                 cudaMemcpyHostToDevice, b->stream),
+                 "upload");
+            b->two_ctas[g] = per_sm;
         }
-        BTRY(cudaMalloc(&b->d_maps, maps.size() * sizeof(CUtensorMap)), "cudaMalloc(tensor maps)");
         BTRY(cudaMalloc(&b->d_srcs, (size_t)n * sizeof(SrcPairF)), "cudaMalloc(source values)");
-        BTRY(cudaMemcpyAsync(b->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
-                             b->stream),
-             "upload");
-        b->two_ctas = per_sm;
     }
     // rasterise every instance on the device (again at every run)
     BTRY(batch_rasterize(b), "rasterise");

@@ -36,6 +36,9 @@ namespace lbmem {
 namespace {
 
 using namespace tma_tile;
+using G = GeoWide;
+constexpr int KW = G::KW, KH = G::KH, RW = G::RW, RH = G::RH, IW = G::IW, IH = G::IH, MW = G::MW;
+constexpr size_t kSmemBytes = G::kSmemBytes;
 
 template <bool ACC, int POL>
 __global__ void __launch_bounds__(NTH, 3)
@@ -45,7 +48,7 @@ __global__ void __launch_bounds__(NTH, 3)
     extern __shared__ unsigned char sm_dyn[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ SrcPairF sp;
-    const TileSmem S = carve(sm_dyn);
+    const TileSmem S = carve<G>(sm_dyn);
 
     const long long t = *t_in;
     if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + 2;
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(NTH, 3)
             ++y;
         }
     };
-    if (threadIdx.x == 0) issue_tile(&fin, &ids_map, tx * KW, ty * KH, S.stage, &bar);
+    if (threadIdx.x == 0) issue_tile<G>(&fin, &ids_map, tx * KW, ty * KH, S.stage, &bar);
     const bool src0 = t >= 1 && a.src.kind != SRC_NONE, src1 = a.src.kind != SRC_NONE;
     const int nx = a.nx, ny = a.ny;
 
@@ -91,14 +94,14 @@ __global__ void __launch_bounds__(NTH, 3)
             double f3[3];
             if (update_site<POL, true>(p, S.table[id], acc ? f3 : nullptr, nullptr)) atomicOr(a.err, kErrUnstable);
             if (acc) acc_site(a.accp, a.src, (size_t)y * a.pitch + x, y, t, f3[0], f3[1], f3[2]);
-            put_inter(S.inter, ly, lx, p);
+            put_inter<G>(S.inter, ly, lx, p);
             S.inter_ids[ly * IW + lx] = id;
         }
         __syncthreads();  // the stage is read, the intermediate state written
         advance(tx, ty);  // the next tile of this CTA
         if (threadIdx.x == 0 && i + 1 < n_mine) {
             fence_proxy_async_smem();
-            issue_tile(&fin, &ids_map, tx * KW, ty * KH, S.stage, &bar);
+            issue_tile<G>(&fin, &ids_map, tx * KW, ty * KH, S.stage, &bar);
         }
         for (int k = threadIdx.x; k < KW * KH; k += NTH) {
             const int lx = k % KW, ly = k / KW, x = x0 + lx, y = y0 + ly;
@@ -156,19 +159,35 @@ cudaError_t encode_tiled(CUtensorMap *map, CUtensorMapDataType type, cuuint32_t 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t encode_plane_map(CUtensorMap *map, const float *base, int nx, int ny, int pitch, size_t pstride) {
-    if (((uintptr_t)base & 15u) || (pitch % 4) || (pstride % 4)) return cudaErrorInvalidValue;
+// The boxes of a tile shape: the stage (RW x RH x 11) and the ids (MW x RH).
+static bool tile_boxes(int kw, int kh, int *rw, int *rh, int *mw) {
+    if (kw == GeoWide::KW && kh == GeoWide::KH) {
+        *rw = GeoWide::RW, *rh = GeoWide::RH, *mw = GeoWide::MW;
+    } else if (kw == GeoTall::KW && kh == GeoTall::KH) {
+        *rw = GeoTall::RW, *rh = GeoTall::RH, *mw = GeoTall::MW;
+    } else {
+        return false;
+    }
+    return true;
+}
+
+cudaError_t encode_plane_map(CUtensorMap *map, const float *base, int nx, int ny, int pitch, size_t pstride, int kw,
+                             int kh) {
+    int rw, rh, mw;
+    if (((uintptr_t)base & 15u) || (pitch % 4) || (pstride % 4) || !tile_boxes(kw, kh, &rw, &rh, &mw))
+        return cudaErrorInvalidValue;
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)NPLANES};
     const cuuint64_t strides[2] = {(cuuint64_t)pitch * sizeof(float), (cuuint64_t)pstride * sizeof(float)};
-    const cuuint32_t box[3] = {(cuuint32_t)RW, (cuuint32_t)RH, (cuuint32_t)NPLANES};
+    const cuuint32_t box[3] = {(cuuint32_t)rw, (cuuint32_t)rh, (cuuint32_t)NPLANES};
     return encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box);
 }
 
-cudaError_t encode_id_map(CUtensorMap *map, const uint8_t *ids, int nx, int ny, int pitch) {
-    if (((uintptr_t)ids & 15u) || (pitch % 16)) return cudaErrorInvalidValue;
+cudaError_t encode_id_map(CUtensorMap *map, const uint8_t *ids, int nx, int ny, int pitch, int kw, int kh) {
+    int rw, rh, mw;
+    if (((uintptr_t)ids & 15u) || (pitch % 16) || !tile_boxes(kw, kh, &rw, &rh, &mw)) return cudaErrorInvalidValue;
     const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
     const cuuint64_t strides[1] = {(cuuint64_t)pitch};
-    const cuuint32_t box[2] = {(cuuint32_t)MW, (cuuint32_t)RH};
+    const cuuint32_t box[2] = {(cuuint32_t)mw, (cuuint32_t)rh};
     return encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, ids, dims, strides, box);
 }
 

@@ -7,11 +7,12 @@
 
 namespace lbmem {
 
-// Tile of the TMA-staged kernel: kTmaTileW x kTmaTileH sites, kTmaThreads threads per CTA.
-// Shared memory per CTA: one stage (the 11 planes over the tile and a two-site halo,
-// 72 x 12 x 11 floats, and the ids over the same rows, 96 x 12 bytes: 39 KB), the
-// intermediate state with a one-site halo and its ids (29 KB) and the 256-entry material
-// table (4 KB): 72 KB, three CTAs per SM.
+// Tile of the single-domain TMA-staged kernel: kTmaTileW x kTmaTileH sites, kTmaThreads
+// threads per CTA.  Shared memory per CTA: one stage (the 11 planes over the tile and a
+// two-site halo, 72 x 12 x 11 floats, and the ids over the same rows, 96 x 12 bytes: 39 KB),
+// the intermediate state with a one-site halo and its ids (29 KB) and the 256-entry
+// material table (4 KB): 72 KB, three CTAs per SM.  The batch also runs 32 x 16 tiles
+// (tile_tma.cuh).
 constexpr int kTmaTileW = 64, kTmaTileH = 8, kTmaThreads = 256;
 
 // cuTensorMapEncodeTiled (through the driver entry point, no link against libcuda): no
@@ -20,13 +21,15 @@ cudaError_t encode_tiled(CUtensorMap *map, CUtensorMapDataType type, cuuint32_t 
                          const cuuint64_t *dims, const cuuint64_t *strides, const cuuint32_t *box);
 
 // Tensor map of an FP32 state buffer (11 planes of ny rows of `pitch` floats, plane stride
-// `pstride` floats) with the kernel's box.  base 16-byte aligned, pitch and pstride
-// multiples of 4; cudaErrorInvalidValue otherwise or if the driver rejects the map.
-cudaError_t encode_plane_map(CUtensorMap *map, const float *base, int nx, int ny, int pitch, size_t pstride);
+// `pstride` floats) with the stage box of kw x kh tiles (64 x 8 or 32 x 16).  base 16-byte
+// aligned, pitch and pstride multiples of 4; cudaErrorInvalidValue otherwise or if the
+// driver rejects the map.
+cudaError_t encode_plane_map(CUtensorMap *map, const float *base, int nx, int ny, int pitch, size_t pstride, int kw,
+                             int kh);
 
 // Tensor map of the material ids (ny rows of `pitch` bytes, pitch a multiple of 16) with
-// the kernel's id box.
-cudaError_t encode_id_map(CUtensorMap *map, const uint8_t *ids, int nx, int ny, int pitch);
+// the id box of kw x kh tiles.
+cudaError_t encode_id_map(CUtensorMap *map, const uint8_t *ids, int nx, int ny, int pitch, int kw, int kh);
 
 // Once per device, outside stream capture: allows the kernels' shared memory and returns
 // the persistent grid (resident CTAs per SM x SMs) in *max_ctas.

@@ -2,7 +2,7 @@
 // step2_tma.cu, batched in batch.cu): geometry, shared-memory layout and the per-site
 // helpers both use.
 //
-// A tile is KW x KH sites at (x0, y0).  Its stage holds the 11 planes over the tile and a
+// A tile is KW x KH sites at (x0, y0) (two shapes, Geo below).  Its stage holds the 11 planes over the tile and a
 // two-site halo, x0 - 4 .. x0 + KW + 3 and y0 - 2 .. y0 + KH + 1 (RW x RH floats per
 // plane; the box starts at x0 - 4 so that it begins on a 16-byte boundary), and the
 // material ids over the same rows from x0 - 16 (MW bytes per row).  Phase 1 writes the
@@ -17,23 +17,32 @@
 namespace lbmem {
 namespace tma_tile {
 
-constexpr int KW = kTmaTileW, KH = kTmaTileH, NTH = kTmaThreads;
-constexpr int RW = KW + 8, RH = KH + 4;  // stage: x0 - 4 .. x0 + KW + 3, y0 - 2 .. y0 + KH + 1
-constexpr int IW = KW + 2, IH = KH + 2;  // intermediate: x0 - 1 .. x0 + KW, y0 - 1 .. y0 + KH
-constexpr int MW = 96, MOFF = 16;        // ids: x0 - 16 .. x0 + 79, the stage's rows
-static_assert(RW * sizeof(float) % 16 == 0 && MW % 16 == 0, "TMA box rows must be multiples of 16 bytes");
-static_assert(KW % 16 == 0, "x0 - 4 floats and x0 - 16 bytes must start on 16-byte boundaries");
-static_assert(MW >= MOFF + KW + 2, "the id box must cover x0 - 2 .. x0 + KW + 1");
+constexpr int NTH = kTmaThreads, MOFF = 16;
 
-constexpr int STATE_FLOATS = NPLANES * RH * RW;
-constexpr unsigned STATE_BYTES = STATE_FLOATS * sizeof(float), ID_BYTES = MW * RH;
-constexpr size_t OFF_IDS = (STATE_BYTES + 127) / 128 * 128;          // ids box, 128-byte aligned
-constexpr size_t OFF_INTER = OFF_IDS + (ID_BYTES + 127) / 128 * 128;  // intermediate state
-constexpr size_t OFF_TABLE = OFF_INTER + (size_t)NPLANES * IH * IW * sizeof(float);
-constexpr size_t OFF_INTER_IDS = OFF_TABLE + 256 * sizeof(MatT<float>);
-constexpr size_t kSmemBytes = OFF_INTER_IDS + (IW * IH + 15) / 16 * 16 + 128;  // + alignment slack
-static_assert(STATE_BYTES % 16 == 0 && OFF_TABLE % 16 == 0, "shared-memory layout");
-static_assert(3 * (kSmemBytes + 1024 + 64) <= 233472, "three CTAs per SM");
+// Geometry of a KW_ x KH_ tile (KW_ a multiple of 16): the stage holds x0 - 4 .. x0 + KW + 3
+// and y0 - 2 .. y0 + KH + 1 (RW x RH), the id box x0 - 16 .. x0 - 16 + MW - 1 on the stage's
+// rows, the intermediate buffer x0 - 1 .. x0 + KW and y0 - 1 .. y0 + KH (IW x IH).
+template <int KW_, int KH_>
+struct Geo {
+    static constexpr int KW = KW_, KH = KH_;
+    static constexpr int RW = KW + 8, RH = KH + 4, IW = KW + 2, IH = KH + 2;
+    static constexpr int MW = (MOFF + KW + 2 + 15) / 16 * 16;
+    static_assert(RW * sizeof(float) % 16 == 0 && MW % 16 == 0, "TMA box rows must be multiples of 16 bytes");
+    static_assert(KW % 16 == 0, "x0 - 4 floats and x0 - 16 bytes must start on 16-byte boundaries");
+    static constexpr int STATE_FLOATS = NPLANES * RH * RW;
+    static constexpr unsigned STATE_BYTES = STATE_FLOATS * sizeof(float), ID_BYTES = MW * RH;
+    static constexpr size_t OFF_IDS = (STATE_BYTES + 127) / 128 * 128;          // 128-byte aligned
+    static constexpr size_t OFF_INTER = OFF_IDS + (ID_BYTES + 127) / 128 * 128;  // intermediate state
+    static constexpr size_t OFF_TABLE = OFF_INTER + (size_t)NPLANES * IH * IW * sizeof(float);
+    static constexpr size_t OFF_INTER_IDS = OFF_TABLE + 256 * sizeof(MatT<float>);
+    static constexpr size_t kSmemBytes = OFF_INTER_IDS + (IW * IH + 15) / 16 * 16 + 128;  // + slack
+    static_assert(STATE_BYTES % 16 == 0 && OFF_TABLE % 16 == 0, "shared-memory layout");
+    static_assert(3 * (kSmemBytes + 1024 + 64) <= 233472, "three CTAs per SM");
+};
+// The single-domain kernel's tile, and the second shape the batch autotuner also times
+// (instance sizes that are multiples of 32 but not of 64 fill it without idle columns).
+using GeoWide = Geo<kTmaTileW, kTmaTileH>;
+using GeoTall = Geo<32, 16>;
 
 // f_i(r, t + 1) from post-collision values in a W x H x 11 shared-memory buffer; (cx, cy)
 // is the site's cell in the buffer; the upstream cell clamps at the lattice edge.
@@ -56,8 +65,9 @@ __device__ __forceinline__ void pull_buf(const float *sm, int nx, int ny, int x,
     p.hyz = v(P_HYZ, cy, cx);
 }
 
+template <class G>
 __device__ __forceinline__ void put_inter(float *sm, int ly, int lx, const Pop<float> &p) {
-    auto r = [&](int plane) -> float & { return sm[(plane * IH + ly) * IW + lx]; };
+    auto r = [&](int plane) -> float & { return sm[(plane * G::IH + ly) * G::IW + lx]; };
     r(P_EZ) = p.ez;
     r(P_EPX) = p.epx;
     r(P_EMX) = p.emx;
@@ -72,11 +82,12 @@ __device__ __forceinline__ void put_inter(float *sm, int ly, int lx, const Pop<f
 }
 
 // The copies of the tile at (x0, y0): state box and id box, completing on bar.
+template <class G>
 __device__ __forceinline__ void issue_tile(const CUtensorMap *fmap, const CUtensorMap *imap, int x0, int y0,
                                            unsigned char *stage, uint64_t *bar) {
-    mbar_arrive_expect_tx(bar, STATE_BYTES + ID_BYTES);
+    mbar_arrive_expect_tx(bar, G::STATE_BYTES + G::ID_BYTES);
     tma_load_3d(stage, fmap, x0 - 4, y0 - 2, 0, bar);
-    tma_load_2d(stage + OFF_IDS, imap, x0 - MOFF, y0 - 2, bar);
+    tma_load_2d(stage + G::OFF_IDS, imap, x0 - MOFF, y0 - 2, bar);
 }
 
 // Source values of a launch's two times t and t + 1 in FP32 (g0, inc0 only for t >= 1).
@@ -111,14 +122,15 @@ struct TileSmem {
     MatT<float> *table;
     uint8_t *inter_ids;
 };
+template <class G>
 __device__ __forceinline__ TileSmem carve(unsigned char *sm_dyn) {
     unsigned char *s = sm_dyn + ((128u - (smem_u32(sm_dyn) & 127u)) & 127u);
     return TileSmem{s,
                     reinterpret_cast<const float *>(s),
-                    s + OFF_IDS,
-                    reinterpret_cast<float *>(s + OFF_INTER),
-                    reinterpret_cast<MatT<float> *>(s + OFF_TABLE),
-                    s + OFF_INTER_IDS};
+                    s + G::OFF_IDS,
+                    reinterpret_cast<float *>(s + G::OFF_INTER),
+                    reinterpret_cast<MatT<float> *>(s + G::OFF_TABLE),
+                    s + G::OFF_INTER_IDS};
 }
 
 }  // namespace tma_tile

@@ -115,16 +115,17 @@ def test_batch_explicit_configuration():
     b.close()
 
 
-def test_batch_two_steps_per_launch_is_bit_identical():
-    """The FP32 batch with two steps per launch (64 x 8 tiles staged by TMA with their halo)
+@pytest.mark.parametrize("shape", [(64, 8), (32, 16)], ids=lambda s: f"{s[0]}x{s[1]}")
+def test_batch_two_steps_per_launch_is_bit_identical(shape):
+    """The FP32 batch with two steps per launch (64 x 8 or 32 x 16 tiles staged by TMA with their halo)
     gives the same bits as the one-step batch kernel, for uneven sizes and run lengths
     (odd step counts end with a one-step launch), and matches the single-domain runs."""
     insts = _batch_instances()
     insts[0] = dict(insts[0], period=61, ramp=61)    # 305 steps: the run ends with one step
     insts[1] = dict(insts[1], period=45, ramp=45)    # 135 steps: a launch's second step is skipped
-    b2 = L.Batch(insts, "f32", tile_w=64, tile_h=8, ctas_per_sm=3)
+    b2 = L.Batch(insts, "f32", tile_w=shape[0], tile_h=shape[1], ctas_per_sm=3)
     b1 = L.Batch(insts, "f32", tile_w=64, tile_h=4, ctas_per_sm=4)
-    assert b2.config() == (64, 8, 3)
+    assert b2.config() == (shape[0], shape[1], 3)
     b2.run()
     b1.run()
     F2, s2 = b2.results()
@@ -179,10 +180,10 @@ def test_two_steps_per_launch_is_bit_identical(inst, prec):
         assert np.array_equal(a.force_torque(c), b.force_torque(c))
 
 
-@pytest.mark.parametrize("shape", [(7, 5), (64, 8), (128, 16), (65, 9), (200, 35)],
+@pytest.mark.parametrize("shape", [(7, 5), (32, 16), (128, 48), (33, 17), (200, 35)],
                          ids=lambda s: f"{s[0]}x{s[1]}")
 def test_fp32_two_steps_on_tile_edge_shapes(shape):
-    """The FP32 two-step kernel copies 64 x 8 tiles with their halo in boxes of 72 x 12 sites:
+    """The FP32 two-step kernel copies 32 x 16 tiles with their halo in boxes of 40 x 20 sites:
     a lattice smaller than the box in both directions, exactly one tile, exact multiples of
     the tile and one site beyond them all give the bits of one step per launch (fields, over
     even and odd step counts)."""
