@@ -536,7 +536,7 @@ static lbm_em_status batch_tiles(lbm_em_batch *b, int tw, int th) {
     b->n_tiles = (int)tiles.size();
     b->tile_w = tw;
     b->tile_h = th;
-    if (!st && b->prec == LBM_EM_F32) {  // the two-step kernel's per-tile records
+    if (!st && b->two) {  // the two-step kernel's per-tile records (set b->two first)
         std::vector<TileCtx> ctx(tiles.size());
         for (size_t k = 0; k < tiles.size(); ++k) {
             const Tile &tl = tiles[k];
@@ -683,10 +683,10 @@ static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int
     const int trial = 4;  // steps timed per candidate
     lbm_em_status st = LBM_EM_OK;
     for (const Cand &c : cands) {
-        st = batch_tiles(b, c.w, c.h);
-        if (st) break;
         b->ctas = c.c;
         b->two = c.two;
+        st = batch_tiles(b, c.w, c.h);
+        if (st) break;
         st = batch_clear(b);
         if (st) break;
         const int launches = c.two ? trial / 2 : trial;
