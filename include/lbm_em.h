@@ -236,6 +236,15 @@ lbm_em_status lbm_em_load_state(lbm_em_t *h, const void *buf, size_t bytes);
 /* Message of the calling thread's last failed call ("" if none). */
 const char *lbm_em_last_error(void);
 
+/* Diagnostic of the device-side bounded waits (the paper has no counterpart).  The
+ * TMA-staged kernels wait on an mbarrier for their tile copies and give up after a limit
+ * (about 2e9 clock cycles), reporting LBM_EM_ETIMEOUT instead of spinning forever.  This
+ * call runs the same wait in one block on an mbarrier that nothing arrives on, for at most
+ * limit_cycles (1 .. 2e9) clock cycles, and reports it the way a kernel's timeout is
+ * reported: LBM_EM_ETIMEOUT is the expected result; the device stays usable.  Synchronous,
+ * on the legacy default stream; LBM_EM_EINVAL for a limit outside the range. */
+lbm_em_status lbm_em_probe_bounded_wait(int64_t limit_cycles);
+
 /* Rasterise a Janus disc on the device into host region ids [ny][nx]
  * (0 vacuum, 1 region II, 2 region III).  Sec. II, Sec. IV.A staircase. */
 lbm_em_status lbm_em_rasterize_janus(const lbm_em_janus *j, int32_t nx, int32_t ny, uint8_t *regions);

@@ -74,13 +74,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
     return ok != 0;
 }
 
-// Waits until the phase with the given parity has completed; false once about
-// kWaitCycles have passed without it.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+// Waits until the phase with the given parity has completed; false once about `limit`
+// clock cycles have passed without it.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long limit = kWaitCycles) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 

@@ -93,6 +93,7 @@ SIGNATURES = {
     "lbm_em_load_state": [_vp, _vp, ctypes.c_size_t],
     "lbm_em_rasterize_janus": [_P(Janus), ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_uint8)],
     "lbm_em_rasterize_janus_noalloc": [_P(Janus), ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_uint8)],
+    "lbm_em_probe_bounded_wait": [ctypes.c_int64],
     "lbm_em_batch_create": [_P(Instance), ctypes.c_int32, _P(BatchOpts), _P(_vp)],
     "lbm_em_batch_run": [_vp],
     "lbm_em_batch_results": [_vp, _P(ctypes.c_double), _P(ctypes.c_int32)],

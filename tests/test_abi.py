@@ -66,3 +66,11 @@ def test_argument_validation_needs_no_gpu(lib):
         lbm_em.Solver(32, 32, "f16dev", janus=lbm_em.make_janus(5, 0.3, 2.0), source=lbm_em.make_source(24),
                       polarization="te")
     assert e.value.status == lbm_em.EINVAL
+
+
+def test_bounded_wait_probe_rejects_limits_out_of_range(lib):
+    """The limit is checked before any device work (so this runs without a GPU too)."""
+    fn = lib.lbm_em_probe_bounded_wait
+    fn.argtypes = [ctypes.c_int64]
+    fn.restype = ctypes.c_int
+    assert fn(0) == 1 and fn(-5) == 1 and fn(3_000_000_000) == 1  # LBM_EM_EINVAL
