@@ -62,7 +62,7 @@ template <typename T>
 struct BatchArgs {
     const InstDesc *inst;
     const Tile *tiles;
-    int n_tiles, tile_w, tile_h, log2_tile_w;
+    int n_tiles, tile_w, tile_h, log2_tile_w;  // log2_tile_w < 0: tile_w is not a power of two
     const T *fin;
     T *fout;
     const uint8_t *mat;
@@ -87,7 +87,7 @@ __device__ __forceinline__ MatT<T> mat_entry(const InstDesc &d, int r) {
 // energy this step (both uniform over the tile); without it no FP64 operation is compiled
 // in, so none can be predicated into the plain steps (see batch2_tile).  Returns the
 // thread's share of the tile's energy when sampling.
-template <typename T, bool BOOK>
+template <typename T, bool BOOK, bool POW2>
 __device__ __forceinline__ double batch_tile(const BatchArgs<T> &b, const Tile &tl, const InstDesc &d, long long t,
                                              bool acc, bool sample, bool src, const MatT<T> *smat,
                                              const double *ssrc) {
@@ -103,7 +103,12 @@ __device__ __forceinline__ double batch_tile(const BatchArgs<T> &b, const Tile &
     const int tsz = b.tile_w * b.tile_h;
     double wsum_t = 0.0;
     for (int k = threadIdx.x; k < tsz; k += blockDim.x) {
-        const int x = tl.x0 + (k & (b.tile_w - 1)), y = tl.y0 + (k >> b.log2_tile_w);
+        // POW2: power-of-two widths (every one-step shape) by mask and shift; otherwise (the
+        // 40-wide tiles of the two-step kernel, whose odd-length runs end with one one-step
+        // launch) by division
+        const int lx = POW2 ? (k & (b.tile_w - 1)) : k % b.tile_w;
+        const int ly = POW2 ? (k >> b.log2_tile_w) : k / b.tile_w;
+        const int x = tl.x0 + lx, y = tl.y0 + ly;
         if (x >= d.nx || y >= d.ny) continue;
         Pop<T> p;
         pull_planes(a, fin, x, y, p);
@@ -161,10 +166,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
         if (threadIdx.x == 32 && src) source_values(d.src, t, &ssrc[0], &ssrc[1]);
         __syncthreads();
         if (!(acc || sample)) {  // uniform over the block
-            batch_tile<T, false>(b, tl, d, t, false, false, src, smat, ssrc);
+            if (b.log2_tile_w >= 0)
+                batch_tile<T, false, true>(b, tl, d, t, false, false, src, smat, ssrc);
+            else
+                batch_tile<T, false, false>(b, tl, d, t, false, false, src, smat, ssrc);
             continue;
         }
-        double wsum_t = batch_tile<T, true>(b, tl, d, t, acc, sample, src, smat, ssrc);
+        double wsum_t = b.log2_tile_w >= 0 ? batch_tile<T, true, true>(b, tl, d, t, acc, sample, src, smat, ssrc)
+                                           : batch_tile<T, true, false>(b, tl, d, t, acc, sample, src, smat, ssrc);
         if (sample) {  // block sum of the tile's energy into the instance's accumulator
             __shared__ double wsh[8];
             for (int o = 16; o > 0; o >>= 1) wsum_t += __shfl_down_sync(0xffffffffu, wsum_t, o);
@@ -195,7 +204,7 @@ __device__ __forceinline__ void batch_acc(const double *f3, const int *slot, dou
 }
 
 // Two steps per launch for the FP32 batch with fixed run lengths, on the TMA-staged tile
-// of the single-domain FP32 kernel (tile_tma.cuh, step2_tma.cu): each 64 x 8 (or 32 x 16) tile of an
+// of the single-domain FP32 kernel (tile_tma.cuh, step2_tma.cu): each 64 x 8 (32 x 16, 40 x 12) tile of an
 // instance arrives in shared memory with a two-site halo and its material ids through
 // the instance's tensor maps, advances to t + 1 together with a one-site halo, then to
 // t + 2, so the packed state crosses HBM once per two steps.  A persistent CTA walks the
@@ -251,6 +260,7 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
     unsigned *err = b.err + c.inst;
     const InstDesc &d = b.inst[c.inst];  // read by the accumulation only
     const bool src0 = t >= 1 && kind != SRC_NONE, src1 = kind != SRC_NONE;
+    const int ioff = x0 - 1 - id_box_x(x0);  // column of site x0 - 1 in the id box
     for (int k = threadIdx.x; k < G::IW * G::IH; k += NTH) {
         const int lx = k % G::IW, ly = k / G::IW, x = x0 - 1 + lx, y = y0 - 1 + ly;
         if (x < 0 || x >= nx || y < 0 || y >= ny) continue;
@@ -259,7 +269,7 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
         Pop<float> q;
         pull_buf<G::RW, G::RH>(S.raw, nx, ny, x, y, lx + 3, ly + 1, q);
         if (x == 0 && src0) inject_source_t(kind, sp.g0, sp.inc0, q);
-        const uint8_t id = S.ids[(ly + 1) * G::MW + lx + MOFF - 1];
+        const uint8_t id = S.ids[(ly + 1) * G::MW + lx + ioff];
         const size_t idx = (size_t)y * pitch + x;
         bool bad;
         if (ACC && interior && t >= acc_from && y >= ay0 && y <= ay1) {
@@ -472,13 +482,13 @@ struct lbm_em_batch {
     long long *d_time = nullptr;
     unsigned *d_err = nullptr;
     int tile_w = 0, tile_h = 0, ctas = 0;
-    bool two = false;  // two steps per launch (FP32, fixed run lengths; TMA-staged 64 x 8 or 32 x 16 tiles)
-    // FP32, per tile shape of the two-step kernel (0: GeoWide, 1: GeoTall): per instance,
-    // tensor maps of its state in buffer 0 and 1 and of its ids; resident CTAs per SM
-    CUtensorMap *d_maps[2] = {nullptr, nullptr};
+    bool two = false;  // two steps per launch (FP32, fixed run lengths; TMA-staged 64 x 8, 32 x 16 or 40 x 12 tiles)
+    // FP32, per tile shape of the two-step kernel (0: GeoWide, 1: GeoTall, 2: GeoMid): per
+    // instance, tensor maps of its state in buffer 0 and 1 and of its ids; resident CTAs per SM
+    CUtensorMap *d_maps[3] = {nullptr, nullptr, nullptr};
     TileCtx *d_ctx = nullptr;       // FP32: one record per tile of the tile list
     SrcPairF *d_srcs = nullptr;     // FP32: per instance, the source values of the current launch
-    int two_ctas[2] = {0, 0};
+    int two_ctas[3] = {0, 0, 0};
     cudaGraphExec_t graph = nullptr;
     bool ran = false;
     // convergence exits
@@ -509,8 +519,7 @@ static void batch_free(lbm_em_batch *b) {
     cudaFree(b->d_energy);
     cudaFree(b->d_prev);
     cudaFree(b->d_settled);
-    cudaFree(b->d_maps[0]);
-    cudaFree(b->d_maps[1]);
+    for (CUtensorMap *m : b->d_maps) cudaFree(m);
     cudaFree(b->d_ctx);
     cudaFree(b->d_srcs);
     if (b->cap) cudaStreamDestroy(b->cap);
@@ -559,10 +568,11 @@ static lbm_em_status batch_tiles(lbm_em_batch *b, int tw, int th) {
     return st;
 }
 
+// log2 of a power of two, -1 for any other width.
 static int ilog2(int v) {
     int l = 0;
     while ((1 << (l + 1)) <= v) ++l;
-    return l;
+    return (1 << l) == v ? l : -1;
 }
 
 // Staircase Janus disc of every instance into the packed material ids (Sec. II).
@@ -602,9 +612,12 @@ static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, int p) {
             if (b->tile_w == GeoWide::KW)
                 k_batch_step2<GeoWide><<<grid, NTH, GeoWide::kSmemBytes, s>>>(a, b->d_ctx, b->d_srcs, b->d_maps[0], p,
                                                                               b->d_time + p, b->d_time + (1 - p));
-            else
+            else if (b->tile_w == GeoTall::KW)
                 k_batch_step2<GeoTall><<<grid, NTH, GeoTall::kSmemBytes, s>>>(a, b->d_ctx, b->d_srcs, b->d_maps[1], p,
                                                                               b->d_time + p, b->d_time + (1 - p));
+            else
+                k_batch_step2<GeoMid><<<grid, NTH, GeoMid::kSmemBytes, s>>>(a, b->d_ctx, b->d_srcs, b->d_maps[2], p,
+                                                                            b->d_time + p, b->d_time + (1 - p));
         }
         else
             k_batch_step<float><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
@@ -645,8 +658,8 @@ static lbm_em_status batch_clear(lbm_em_batch *b) {
 }
 
 // Time a few steps of each (tile shape, CTAs per SM, steps per launch) candidate from the
-// cleared state; two steps per launch (TMA-staged 64 x 8 and 32 x 16 tiles, as many CTAs per SM
-// as their shared memory allows) is a candidate for FP32 runs of fixed length.
+// cleared state; two steps per launch (TMA-staged 64 x 8, 32 x 16 and 40 x 12 tiles, as many CTAs
+// per SM as their shared memory allows) is a candidate for FP32 runs of fixed length.
 static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int want_c) {
     struct Cand {
         int w, h, c;
@@ -662,8 +675,8 @@ static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int
             if (want_c && c != want_c) continue;
             cands.push_back(Cand{sh[0], sh[1], c, false});
         }
-    const int two_shapes[2][2] = {{GeoWide::KW, GeoWide::KH}, {GeoTall::KW, GeoTall::KH}};
-    for (int g = 0; g < 2; ++g) {
+    const int two_shapes[3][2] = {{GeoWide::KW, GeoWide::KH}, {GeoTall::KW, GeoTall::KH}, {GeoMid::KW, GeoMid::KH}};
+    for (int g = 0; g < 3; ++g) {
         const int w = two_shapes[g][0], h = two_shapes[g][1], c = b->two_ctas[g];
         if (c > 0 && b->conv_tol <= 0.0 && (!want_w || want_w == w) && (!want_h || want_h == h) &&
             (!want_c || want_c == c))
@@ -724,8 +737,10 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
         return set_error(LBM_EM_EINVAL, "batch precision must be LBM_EM_F32, LBM_EM_F64 or LBM_EM_F32X2");
     if (o->tile_w < 0 || o->tile_h < 0 || o->ctas_per_sm < 0 || o->ctas_per_sm > 8)
         return set_error(LBM_EM_EINVAL, "bad tile shape or CTAs per SM");
-    if (o->tile_w && o->tile_w != 32 && o->tile_w != 64 && o->tile_w != 128 && o->tile_w != 256)
-        return set_error(LBM_EM_EINVAL, "tile_w must be 32, 64, 128 or 256");
+    if (o->tile_w && o->tile_w != 32 && o->tile_w != 40 && o->tile_w != 64 && o->tile_w != 128 && o->tile_w != 256)
+        return set_error(LBM_EM_EINVAL, "tile_w must be 32, 40, 64, 128 or 256");
+    if (o->tile_w == 40 && (o->precision != LBM_EM_F32 || o->conv_tol > 0.0 || (o->tile_h && o->tile_h != 12)))
+        return set_error(LBM_EM_EINVAL, "tile_w 40 is the two-step kernel's 40 x 12 tile (FP32, conv_tol 0)");
     if (!(o->conv_tol >= 0.0) || o->min_periods < 0) return set_error(LBM_EM_EINVAL, "conv_tol >= 0, min_periods >= 0");
     if (o->tile_h && (o->tile_h > 16)) return set_error(LBM_EM_EINVAL, "tile_h must be <= 16");
     for (int i = 0; i < n; ++i) {
@@ -864,10 +879,11 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
     }
     // FP32: tensor maps of every instance for the two-step kernel, for both tile shapes
     if (b->prec == LBM_EM_F32) {
-        const void *kern[2] = {(const void *)k_batch_step2<GeoWide>, (const void *)k_batch_step2<GeoTall>};
-        const size_t smem[2] = {GeoWide::kSmemBytes, GeoTall::kSmemBytes};
-        const int shape[2][2] = {{GeoWide::KW, GeoWide::KH}, {GeoTall::KW, GeoTall::KH}};
-        for (int g = 0; g < 2; ++g) {
+        const void *kern[3] = {(const void *)k_batch_step2<GeoWide>, (const void *)k_batch_step2<GeoTall>,
+                               (const void *)k_batch_step2<GeoMid>};
+        const size_t smem[3] = {GeoWide::kSmemBytes, GeoTall::kSmemBytes, GeoMid::kSmemBytes};
+        const int shape[3][2] = {{GeoWide::KW, GeoWide::KH}, {GeoTall::KW, GeoTall::KH}, {GeoMid::KW, GeoMid::KH}};
+        for (int g = 0; g < 3; ++g) {
             int per_sm = 0;
             BTRY(cudaFuncSetAttribute(kern[g], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem[g]),
                  "configuring the two-step batch kernel");

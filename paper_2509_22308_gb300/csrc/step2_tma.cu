@@ -8,7 +8,7 @@
 // few tile rows high whose halos meet in L2.  For each tile one thread issues two
 // cp.async.bulk.tensor copies on one mbarrier: the 11 planes over the tile and a two-site
 // halo (x from x0 - 4, so that the box starts on a 16-byte boundary: RW x RH x 11 floats)
-// and the material ids over the same rows (x from x0 - 16: MW x RH bytes).
+// and the material ids over the same rows (MW x RH bytes from x0 - 2 rounded down to 16).
 //   phase 1: f*(t) of the tile and a one-site halo, pulled from the stage (source at
 //            x = 0, collision), into the intermediate buffer, with each site's id;
 //   then the stage is free and the next tile's copies go out, so they run during
@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(NTH, 3)
 
     for (int i = 0; i < n_mine; ++i) {
         const int x0 = tx * KW, y0 = ty * KH;
+        const int ioff = x0 - 1 - id_box_x(x0);  // column of site x0 - 1 in the id box
         const bool ok = mbar_wait(&bar, (unsigned)i & 1u);
         if (__syncthreads_or(!ok)) {  // the tile's copies never completed: report, leave
             if (threadIdx.x == 0) atomicOr(a.err, kErrTimeout);
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(NTH, 3)
             Pop<float> p;
             pull_buf<RW, RH>(S.raw, nx, ny, x, y, lx + 3, ly + 1, p);
             if (x == 0 && src0) inject_source_t(a.src.kind, sp.g0, sp.inc0, p);
-            const uint8_t id = S.ids[(ly + 1) * MW + lx + MOFF - 1];
+            const uint8_t id = S.ids[(ly + 1) * MW + lx + ioff];
             const bool acc = ACC && lx >= 1 && lx <= KW && ly >= 1 && ly <= KH;
             double f3[3];
             if (update_site<POL, true>(p, S.table[id], acc ? f3 : nullptr, nullptr)) atomicOr(a.err, kErrUnstable);
@@ -165,6 +166,8 @@ static bool tile_boxes(int kw, int kh, int *rw, int *rh, int *mw) {
         *rw = GeoWide::RW, *rh = GeoWide::RH, *mw = GeoWide::MW;
     } else if (kw == GeoTall::KW && kh == GeoTall::KH) {
         *rw = GeoTall::RW, *rh = GeoTall::RH, *mw = GeoTall::MW;
+    } else if (kw == GeoMid::KW && kh == GeoMid::KH) {
+        *rw = GeoMid::RW, *rh = GeoMid::RH, *mw = GeoMid::MW;
     } else {
         return false;
     }

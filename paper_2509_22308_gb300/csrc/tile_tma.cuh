@@ -5,7 +5,7 @@
 // A tile is KW x KH sites at (x0, y0) (two shapes, Geo below).  Its stage holds the 11 planes over the tile and a
 // two-site halo, x0 - 4 .. x0 + KW + 3 and y0 - 2 .. y0 + KH + 1 (RW x RH floats per
 // plane; the box starts at x0 - 4 so that it begins on a 16-byte boundary), and the
-// material ids over the same rows from x0 - 16 (MW bytes per row).  Phase 1 writes the
+// material ids over the same rows from x0 - 2 rounded down to 16 bytes (MW bytes per row).  Phase 1 writes the
 // post-collision state of the tile and a one-site halo, x0 - 1 .. x0 + KW and y0 - 1 ..
 // y0 + KH (IW x IH), with each site's id, to the intermediate buffer.
 #pragma once
@@ -17,18 +17,23 @@
 namespace lbmem {
 namespace tma_tile {
 
-constexpr int NTH = kTmaThreads, MOFF = 16;
+constexpr int NTH = kTmaThreads;
 
-// Geometry of a KW_ x KH_ tile (KW_ a multiple of 16): the stage holds x0 - 4 .. x0 + KW + 3
-// and y0 - 2 .. y0 + KH + 1 (RW x RH), the id box x0 - 16 .. x0 - 16 + MW - 1 on the stage's
-// rows, the intermediate buffer x0 - 1 .. x0 + KW and y0 - 1 .. y0 + KH (IW x IH).
+// First column of a tile's id box: x0 - 2 rounded down to a multiple of 16 (a TMA box starts
+// on a 16-byte boundary), so the box reaches x0 - 2 .. x0 + KW + 1 from an offset of 2 .. 17.
+__host__ __device__ __forceinline__ int id_box_x(int x0) { return ((x0 - 2) >> 4) * 16; }
+
+// Geometry of a KW_ x KH_ tile (KW_ a multiple of 4, so that x0 - 4 floats starts on 16
+// bytes): the stage holds x0 - 4 .. x0 + KW + 3 and y0 - 2 .. y0 + KH + 1 (RW x RH), the id box
+// MW bytes from id_box_x(x0) on the stage's rows, the intermediate buffer x0 - 1 .. x0 + KW
+// and y0 - 1 .. y0 + KH (IW x IH).
 template <int KW_, int KH_>
 struct Geo {
     static constexpr int KW = KW_, KH = KH_;
     static constexpr int RW = KW + 8, RH = KH + 4, IW = KW + 2, IH = KH + 2;
-    static constexpr int MW = (MOFF + KW + 2 + 15) / 16 * 16;
+    static constexpr int MW = (17 + KW + 2 + 15) / 16 * 16;
     static_assert(RW * sizeof(float) % 16 == 0 && MW % 16 == 0, "TMA box rows must be multiples of 16 bytes");
-    static_assert(KW % 16 == 0, "x0 - 4 floats and x0 - 16 bytes must start on 16-byte boundaries");
+    static_assert(KW % 4 == 0, "x0 - 4 floats must start on a 16-byte boundary");
     static constexpr int STATE_FLOATS = NPLANES * RH * RW;
     static constexpr unsigned STATE_BYTES = STATE_FLOATS * sizeof(float), ID_BYTES = MW * RH;
     static constexpr size_t OFF_IDS = (STATE_BYTES + 127) / 128 * 128;          // 128-byte aligned
@@ -39,10 +44,12 @@ struct Geo {
     static_assert(STATE_BYTES % 16 == 0 && OFF_TABLE % 16 == 0, "shared-memory layout");
     static_assert(3 * (kSmemBytes + 1024 + 64) <= 233472, "three CTAs per SM");
 };
-// The single-domain kernel's tile, and the second shape the batch autotuner also times
-// (instance sizes that are multiples of 32 but not of 64 fill it without idle columns).
+// The single-domain kernel's tile, and the other shapes the batch autotuner also times
+// (instance sizes that are multiples of 32, or of 40, but not of 64 fill them without idle
+// columns: the paper's 160^2 and 200^2 maps).
 using GeoWide = Geo<kTmaTileW, kTmaTileH>;
 using GeoTall = Geo<32, 16>;
+using GeoMid = Geo<40, 12>;
 
 // f_i(r, t + 1) from post-collision values in a W x H x 11 shared-memory buffer; (cx, cy)
 // is the site's cell in the buffer; the upstream cell clamps at the lattice edge.
@@ -87,7 +94,7 @@ __device__ __forceinline__ void issue_tile(const CUtensorMap *fmap, const CUtens
                                            unsigned char *stage, uint64_t *bar) {
     mbar_arrive_expect_tx(bar, G::STATE_BYTES + G::ID_BYTES);
     tma_load_3d(stage, fmap, x0 - 4, y0 - 2, 0, bar);
-    tma_load_2d(stage + G::OFF_IDS, imap, x0 - MOFF, y0 - 2, bar);
+    tma_load_2d(stage + G::OFF_IDS, imap, id_box_x(x0), y0 - 2, bar);
 }
 
 // Source values of a launch's two times t and t + 1 in FP32 (g0, inc0 only for t >= 1).

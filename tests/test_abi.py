@@ -74,3 +74,15 @@ def test_bounded_wait_probe_rejects_limits_out_of_range(lib):
     fn.argtypes = [ctypes.c_int64]
     fn.restype = ctypes.c_int
     assert fn(0) == 1 and fn(-5) == 1 and fn(3_000_000_000) == 1  # LBM_EM_EINVAL
+
+
+def test_batch_rejects_the_40_wide_tile_outside_the_two_step_kernel(lib):
+    """40 x 12 tiles exist only in the FP32 two-step batch kernel (the one-step kernel needs a
+    power-of-two tile width); the options are checked before any device work."""
+    from paper_2509_22308_gb300 import lbm_em as L
+    inst = dict(nx=200, ny=200, a=50.0, phi0=0.3, eps1=2.0, eps2=4.0, pec2=False, period=150, periods=2,
+                R=75.0, ramp=150)
+    for prec, kw in (("f64", {}), ("f32", {"conv_tol": 1e-6}), ("f32", {"tile_h": 8})):
+        with pytest.raises(L.LbmEmError) as e:
+            L.Batch([inst], prec, tile_w=40, **kw)
+        assert e.value.status == L.EINVAL

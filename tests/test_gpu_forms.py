@@ -115,9 +115,9 @@ def test_batch_explicit_configuration():
     b.close()
 
 
-@pytest.mark.parametrize("shape", [(64, 8), (32, 16)], ids=lambda s: f"{s[0]}x{s[1]}")
+@pytest.mark.parametrize("shape", [(64, 8), (32, 16), (40, 12)], ids=lambda s: f"{s[0]}x{s[1]}")
 def test_batch_two_steps_per_launch_is_bit_identical(shape):
-    """The FP32 batch with two steps per launch (64 x 8 or 32 x 16 tiles staged by TMA with their halo)
+    """The FP32 batch with two steps per launch (64 x 8, 32 x 16 or 40 x 12 tiles staged by TMA with their halo)
     gives the same bits as the one-step batch kernel, for uneven sizes and run lengths
     (odd step counts end with a one-step launch), and matches the single-domain runs."""
     insts = _batch_instances()
