@@ -284,12 +284,13 @@ typedef struct {
 
 typedef struct {
     int32_t precision;       /* LBM_EM_F32, LBM_EM_F64 or LBM_EM_F32X2                      */
-    int32_t tile_w, tile_h;  /* tile shape (tile_w 32/64/128/256, tile_h <= 16); 0: autotuned.
-                                64 x 8 and 32 x 16 with 3 CTAs per SM are the configurations
-                                of the two-steps-per-launch kernel (FP32, conv_tol 0: each tile
-                                and its halo are copied to shared memory by the TMA unit and
-                                advance two steps there, same bits); the autotuner times
-                                both                                                     */
+    int32_t tile_w, tile_h;  /* tile shape (tile_w 32/40/64/128/256, tile_h <= 16); 0: autotuned.
+                                64 x 8, 32 x 16 and 40 x 12 with 3 CTAs per SM are the
+                                configurations of the two-steps-per-launch kernel (FP32,
+                                conv_tol 0: each tile and its halo are copied to shared memory
+                                by the TMA unit and advance two steps there, same bits; 40 is
+                                valid for it only).  With nothing pinned the autotuner times
+                                those three when they apply, else the one-step shapes      */
     int32_t ctas_per_sm;     /* persistent CTAs per SM; 0: autotuned                       */
     int32_t min_periods;     /* convergence exits: fewest periods an instance runs         */
     int32_t source_kind;     /* lbm_em_source_kind of every instance (0: HARD)              */

@@ -666,15 +666,6 @@ static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int
         bool two;
     };
     std::vector<Cand> cands;
-    const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 8}, {128, 4}, {256, 2}, {128, 8}, {256, 4}};
-    const int ctas[] = {2, 4, 8};
-    for (auto &sh : shapes)
-        for (int c : ctas) {
-            if (want_w && sh[0] != want_w) continue;
-            if (want_h && sh[1] != want_h) continue;
-            if (want_c && c != want_c) continue;
-            cands.push_back(Cand{sh[0], sh[1], c, false});
-        }
     const int two_shapes[3][2] = {{GeoWide::KW, GeoWide::KH}, {GeoTall::KW, GeoTall::KH}, {GeoMid::KW, GeoMid::KH}};
     for (int g = 0; g < 3; ++g) {
         const int w = two_shapes[g][0], h = two_shapes[g][1], c = b->two_ctas[g];
@@ -682,6 +673,20 @@ static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int
             (!want_c || want_c == c))
             cands.push_back(Cand{w, h, c, true});
     }
+    // One step per launch moves twice the bytes per update; on GB300 it lost to every two-step
+    // shape on every FP32 map measured, so with nothing pinned by the caller only the two-step
+    // shapes are timed when they apply (they do not for FP64, double-float or convergence exits).
+    const bool only_two = !cands.empty() && !want_w && !want_h && !want_c;
+    const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 8}, {128, 4}, {256, 2}, {128, 8}, {256, 4}};
+    const int ctas[] = {2, 4, 8};
+    for (auto &sh : shapes)
+        for (int c : ctas) {
+            if (only_two) break;
+            if (want_w && sh[0] != want_w) continue;
+            if (want_h && sh[1] != want_h) continue;
+            if (want_c && c != want_c) continue;
+            cands.push_back(Cand{sh[0], sh[1], c, false});
+        }
     if (cands.empty()) cands.push_back(Cand{want_w ? want_w : 64, want_h ? want_h : 4, want_c ? want_c : 4, false});
     if (cands.size() == 1) {
         b->ctas = cands[0].c;
