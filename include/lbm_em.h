@@ -74,12 +74,12 @@ typedef enum {
     LBM_EM_SRC_NONE = 2   /* no source (all edges open)                                  */
 } lbm_em_source_kind;
 
-/* lbm_em_grid.flags: how many time steps one kernel launch advances.  By default FP64 and
- * FP16-deviation advance one step per launch and FP32 two (the intermediate state of each
- * tile stays in shared memory) on lattices of at least 2^25 sites, one below that.  The
+/* lbm_em_grid.flags: how many time steps one kernel launch advances.  By default FP64,
+ * FP16-deviation and double-float advance one step per launch and FP32 two (each tile and
+ * its halo are copied to shared memory by the TMA unit and advance two steps there).  The
  * result does not depend on the choice: both modes give the same bits. */
 #define LBM_EM_FLAG_SINGLE_STEP 1  /* always one step per launch                          */
-#define LBM_EM_FLAG_TWO_STEP 2     /* two steps per launch for FP32 and FP16-deviation    */
+#define LBM_EM_FLAG_TWO_STEP 2     /* two steps per launch for FP32, FP16-dev, double-float */
 /* TE^z polarization (H_z, E_x, E_y), which the paper leaves for future work (Sec. I): the
  * same scheme and storage (11 planes), incident wave E_y = H_z = E0 sin(w t - k x).  Every
  * call that reports the TM triple (E_z, H_x, H_y) reports (H_z, E_x, E_y) instead: fields,

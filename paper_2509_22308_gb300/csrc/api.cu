@@ -473,14 +473,14 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     h->pitch = round_up(g->nx, 32);
     h->pstride = (size_t)h->pitch * (size_t)g->ny;
     h->srccfg = *s;
-    // two steps per launch: forced by the flag, else by default for FP32 lattices large
-    // enough (>= 2^25 sites) that the shared-memory tiles fill the GPU many times over;
-    // measured on GB300 it loses on smaller FP32 lattices and on the FP16-deviation form
+    // two steps per launch: forced by the flag, else the FP32 default (the TMA-staged kernel
+    // beat one step per launch on GB300 from 512^2 to 8192^2: 69 / 122 / 129 / 141 / 138
+    // against 58 / 85 / 74 / 76 / 75 GLUPS); the FP16-deviation and double-float forms
+    // default to one step (their two-step kernels are issue-bound and lose)
     if (g->flags & LBM_EM_FLAG_TWO_STEP)
         h->tb = g->precision != LBM_EM_F64;
     else
-        h->tb = g->precision == LBM_EM_F32 && !(g->flags & LBM_EM_FLAG_SINGLE_STEP) &&
-                (long long)g->nx * g->ny >= (1LL << 25);
+        h->tb = g->precision == LBM_EM_F32 && !(g->flags & LBM_EM_FLAG_SINGLE_STEP);
     for (int i = 0; i < 256; ++i) {
         h->eps_table[i] = 1.0;
         h->pec_id[i] = false;
