@@ -510,6 +510,10 @@ def main():
                 hs[key] = {"kernel": kern, "us_per_step": round(us, 2),
                           "glups": round(sites / (us / 1e6) / 1e9, 2), "achieved_gbs": round(gbs, 1),
                           "frac_hbm": round(gbs / peak, 4), "bytes_per_lu": BYTES_PER_LU[fp]}
+                if "two steps per launch" in kern:
+                    # the state crosses HBM once per two steps: half the one-pass bytes per update
+                    hs[key]["two_step_bytes_per_lu"] = BYTES_PER_LU[fp] / 2
+                    hs[key]["two_step_frac_hbm"] = round(gbs / 2 / peak, 4)
                 if fp == "f64":
                     ops = FP64_OPS_PER_LU + (1 if pol == "te" else 0)   # TE: 29 per update
                     hs[key]["fp64_ops_per_lu"] = ops
