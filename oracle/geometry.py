@@ -5,7 +5,7 @@ region II (dielectric eps_r1) and region III (dielectric eps_r2, or a perfect
 electric conductor for the metallo-dielectric cylinder), in vacuum (region I).
 Sec. IV.A notes the circle is represented by a staircase on the Cartesian lattice.
 
-Lattice frame (derived in the design doc): the incident wave travels along +x.  In the
+Lattice frame (derived here from the paper's frame): the incident wave travels along +x.  In the
 paper's frame region II occupies the polar angles [0, pi] and the wave travels
 towards phi0 + pi, so after rotating the wave onto +x the region-II half is the
 one whose points d (relative to the centre) satisfy d . n_d > 0 with

@@ -9,7 +9,7 @@
  * site) and forms every equilibrium with generic 3-D cross products, exactly as
  * Eq. (LBGK equation) and Eq. (equilibrium distribution functions) are written.
  *
- * Readings of the paper where it is silent (each is listed in the design doc):
+ * Readings of the paper where it is silent:
  *   - moments: D = sum_i e_i, E = D / eps_r ; B = sum_i h_i, H = B / mu_r   (Sec. III)
  *   - one step at time t: moments -> (optional Fourier accumulation of E_z, H_x,
  *     H_y with weight e^{i w t}) -> post-collision f* = 2 f^eq - f -> stream

@@ -7,7 +7,7 @@ arXiv 2509.22308, Sec. II.B:
   F~ = <F> / F0, M~ = <M> / M0 with F0 = pi a eps0 E0^2 / 4, M0 = 2 F0 a (Sec. II.B)
 Lattice units eps0 = mu0 = 1.  For TM^z fields E = (0, 0, Ez), H = (Hx, Hy, 0).
 
-The contour (reading listed in the design doc): a circle of radius R about the
+The contour (the paper integrates over any enclosing vacuum contour): a circle of radius R about the
 cylinder axis sampled at N points phi_k = 2 pi k / N, dl = R 2 pi / N, the
 phasors at each point bilinearly interpolated from the four surrounding sites.
 """
