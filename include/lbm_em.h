@@ -299,6 +299,8 @@ typedef struct {
                                 changes by <= conv_tol * W twice in a row (Sec. III), then
                                 runs one accumulated period; `periods` is the maximum     */
     void *stream;            /* cudaStream_t; NULL: private stream                         */
+    int32_t polarization;    /* 0: TM^z (E_z, H_x, H_y), the paper's case; 1: TE^z (H_z,
+                                E_x, E_y) for every instance (see LBM_EM_FLAG_TE)          */
 } lbm_em_batch_opts;
 
 typedef struct lbm_em_batch lbm_em_batch_t;

@@ -87,7 +87,7 @@ __device__ __forceinline__ MatT<T> mat_entry(const InstDesc &d, int r) {
 // energy this step (both uniform over the tile); without it no FP64 operation is compiled
 // in, so none can be predicated into the plain steps (see batch2_tile).  Returns the
 // thread's share of the tile's energy when sampling.
-template <typename T, bool BOOK, bool POW2>
+template <typename T, int POL, bool BOOK, bool POW2>
 __device__ __forceinline__ double batch_tile(const BatchArgs<T> &b, const Tile &tl, const InstDesc &d, long long t,
                                              bool acc, bool sample, bool src, const MatT<T> *smat,
                                              const double *ssrc) {
@@ -115,36 +115,38 @@ __device__ __forceinline__ double batch_tile(const BatchArgs<T> &b, const Tile &
         if (x == 0 && src) inject_source(d.src.kind, ssrc[0], ssrc[1], p);
         const size_t idx = (size_t)y * d.pitch + x;
         const MatT<T> m = smat[mat[idx]];
-        T E3, Hx, Hy, D;
-        moments(p, m, &E3, &Hx, &Hy, &D);
-        if (field_runaway(E3)) atomicOr(b.err + tl.inst, 1u);
+        // moments, runaway test, field triple (TM: E_z, H_x, H_y; TE: H_z, E_x, E_y) and energy
+        // density when wanted, collision: update_site, the single-domain kernels' site update
+        bool bad;
         if (BOOK) {
-            if (acc && y >= d.y0 && y <= d.y1) {
+            const bool acc_row = acc && y >= d.y0 && y <= d.y1;
+            double f3[3], w;
+            bad = update_site<POL, true>(p, m, acc_row ? f3 : nullptr, sample ? &w : nullptr);
+            if (acc_row) {
                 const int s = b.slot[d.slot_base + idx];
                 if (s >= 0) {
                     const double2 c = d.src.cs[(int)(t % (long long)d.period)];
-                    const double ez = (double)(D * m.inv_eps), hx = (double)Hx, hy = (double)Hy;
                     double *q = b.acc + 6 * ((size_t)d.acc_base + s);
-                    q[0] += ez * c.x;
-                    q[1] += ez * c.y;
-                    q[2] += hx * c.x;
-                    q[3] += hx * c.y;
-                    q[4] += hy * c.x;
-                    q[5] += hy * c.y;
+                    q[0] += f3[0] * c.x;
+                    q[1] += f3[0] * c.y;
+                    q[2] += f3[1] * c.x;
+                    q[3] += f3[1] * c.y;
+                    q[4] += f3[2] * c.x;
+                    q[5] += f3[2] * c.y;
                 }
             }
-            if (sample)
-                wsum_t += 0.5 * ((double)D * (double)(D * m.inv_eps) + (double)Hx * (double)Hx +
-                                 (double)Hy * (double)Hy);
+            if (sample) wsum_t += w;
+        } else {
+            bad = update_site<POL, true>(p, m, nullptr, nullptr);
         }
-        collide(p, E3, Hx, Hy);
+        if (bad) atomicOr(b.err + tl.inst, kErrUnstable);
         store_site(fout, d.pstride, idx, p);
     }
     return wsum_t;
 }
 
 // FP32: at most 85 registers so that 3 CTAs of 256 threads stay resident per SM.
-template <typename T>
+template <typename T, int POL>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
     k_batch_step(const BatchArgs<T> b, const long long *__restrict__ t_in, long long *__restrict__ t_out) {
     const long long t = *t_in;
@@ -167,13 +169,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
         __syncthreads();
         if (!(acc || sample)) {  // uniform over the block
             if (b.log2_tile_w >= 0)
-                batch_tile<T, false, true>(b, tl, d, t, false, false, src, smat, ssrc);
+                batch_tile<T, POL, false, true>(b, tl, d, t, false, false, src, smat, ssrc);
             else
-                batch_tile<T, false, false>(b, tl, d, t, false, false, src, smat, ssrc);
+                batch_tile<T, POL, false, false>(b, tl, d, t, false, false, src, smat, ssrc);
             continue;
         }
-        double wsum_t = b.log2_tile_w >= 0 ? batch_tile<T, true, true>(b, tl, d, t, acc, sample, src, smat, ssrc)
-                                           : batch_tile<T, true, false>(b, tl, d, t, acc, sample, src, smat, ssrc);
+        double wsum_t = b.log2_tile_w >= 0 ? batch_tile<T, POL, true, true>(b, tl, d, t, acc, sample, src, smat, ssrc)
+                                           : batch_tile<T, POL, true, false>(b, tl, d, t, acc, sample, src, smat, ssrc);
         if (sample) {  // block sum of the tile's energy into the instance's accumulator
             __shared__ double wsh[8];
             for (int o = 16; o > 0; o >>= 1) wsum_t += __shfl_down_sync(0xffffffffu, wsum_t, o);
@@ -247,7 +249,7 @@ __global__ void k_batch_source(const InstDesc *__restrict__ desc, int n, const l
 // instance accumulates Fourier sums at t or t + 1.  Both are template parameters so that
 // the common body carries no per-site branch on them.  c: the tile's record (shared
 // memory, copied to registers here).
-template <class G, bool ACC, bool TWO>
+template <class G, int POL, bool ACC, bool TWO>
 __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const TileCtx &c, long long t,
                                             const TileSmem &S, const SrcPairF &sp, const CUtensorMap *maps,
                                             int p, bool has_next, const int4 &next, uint64_t *bar) {
@@ -274,10 +276,10 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
         bool bad;
         if (ACC && interior && t >= acc_from && y >= ay0 && y <= ay1) {
             double f3[3];
-            bad = update_site<POL_TM, true>(q, smat[id], f3, nullptr);
+            bad = update_site<POL, true>(q, smat[id], f3, nullptr);
             batch_acc(f3, b.slot, b.acc, d, idx, t);
         } else {
-            bad = update_site<POL_TM, true>(q, smat[id], nullptr, nullptr);
+            bad = update_site<POL, true>(q, smat[id], nullptr, nullptr);
         }
         if (bad) atomicOr(err, kErrUnstable);
         if (TWO) {
@@ -304,10 +306,10 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
             bool bad;
             if (ACC && t + 1 >= acc_from && y >= ay0 && y <= ay1) {
                 double f3[3];
-                bad = update_site<POL_TM, true>(q, m, f3, nullptr);
+                bad = update_site<POL, true>(q, m, f3, nullptr);
                 batch_acc(f3, b.slot, b.acc, d, idx, t + 1);
             } else {
-                bad = update_site<POL_TM, true>(q, m, nullptr, nullptr);
+                bad = update_site<POL, true>(q, m, nullptr, nullptr);
             }
             if (bad) atomicOr(err, kErrUnstable);
             store_site(fout, ps, idx, q);
@@ -315,7 +317,7 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
     }
 }
 
-template <class G>
+template <class G, int POL>
 __global__ void __launch_bounds__(NTH, 3)
     k_batch_step2(const BatchArgs<float> b, const TileCtx *__restrict__ ctx, const SrcPairF *__restrict__ srcs,
                   const CUtensorMap *__restrict__ maps, int p, const long long *__restrict__ t_in,
@@ -364,14 +366,14 @@ __global__ void __launch_bounds__(NTH, 3)
         const bool acc = t + 1 >= sc.acc_from, two = t + 1 < sc.steps;  // uniform over the block
         if (two) {
             if (acc)
-                batch2_tile<G, true, true>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+                batch2_tile<G, POL, true, true>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
             else
-                batch2_tile<G, false, true>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+                batch2_tile<G, POL, false, true>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
         } else {
             if (acc)
-                batch2_tile<G, true, false>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+                batch2_tile<G, POL, true, false>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
             else
-                batch2_tile<G, false, false>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+                batch2_tile<G, POL, false, false>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
         }
         __syncthreads();  // shared memory is free for the next tile
         cur = nxt;
@@ -461,6 +463,7 @@ __global__ void __launch_bounds__(256) k_batch_contour(const ContourDesc *__rest
 
 struct lbm_em_batch {
     int dev = 0, n = 0, prec = LBM_EM_F32, sms = 0;
+    int pol = POL_TM;  // polarization of every instance (lbm_em_batch_opts.polarization)
     size_t elem = 4;
     cudaStream_t stream = nullptr, cap = nullptr;
     bool own_stream = false;
@@ -589,6 +592,20 @@ static cudaError_t batch_rasterize(lbm_em_batch *b) {
     return cudaSuccess;
 }
 
+// The two-step kernel of the batch's tile shape and polarization.
+template <int POL>
+static void launch_batch_step2(const lbm_em_batch *b, const BatchArgs<float> &a, int grid, int p, cudaStream_t s) {
+    if (b->tile_w == GeoWide::KW)
+        k_batch_step2<GeoWide, POL><<<grid, NTH, GeoWide::kSmemBytes, s>>>(a, b->d_ctx, b->d_srcs, b->d_maps[0], p,
+                                                                           b->d_time + p, b->d_time + (1 - p));
+    else if (b->tile_w == GeoTall::KW)
+        k_batch_step2<GeoTall, POL><<<grid, NTH, GeoTall::kSmemBytes, s>>>(a, b->d_ctx, b->d_srcs, b->d_maps[1], p,
+                                                                           b->d_time + p, b->d_time + (1 - p));
+    else
+        k_batch_step2<GeoMid, POL><<<grid, NTH, GeoMid::kSmemBytes, s>>>(a, b->d_ctx, b->d_srcs, b->d_maps[2], p,
+                                                                         b->d_time + p, b->d_time + (1 - p));
+}
+
 // One launch from the state in buf[p] (time word p) to buf[1 - p]: one step, or two with
 // b->two.  The caller alternates p launch by launch.
 static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, int p) {
@@ -597,30 +614,33 @@ static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, int p) {
         BatchArgs<df> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, ilog2(b->tile_w),
                         (const df *)b->buf[p], (df *)b->buf[1 - p], b->d_mat, b->d_slot,
                         b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
-        k_batch_step<df><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
+        if (b->pol == POL_TE)
+            k_batch_step<df, POL_TE><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
+        else
+            k_batch_step<df, POL_TM><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
     } else if (b->prec == LBM_EM_F64) {
         BatchArgs<double> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, ilog2(b->tile_w),
                             (const double *)b->buf[p], (double *)b->buf[1 - p], b->d_mat, b->d_slot,
                             b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
-        k_batch_step<double><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
+        if (b->pol == POL_TE)
+            k_batch_step<double, POL_TE><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
+        else
+            k_batch_step<double, POL_TM><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
     } else {
         BatchArgs<float> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, ilog2(b->tile_w),
                            (const float *)b->buf[p], (float *)b->buf[1 - p], b->d_mat, b->d_slot,
                            b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
         if (b->two) {
             k_batch_source<<<(b->n + 127) / 128, 128, 0, s>>>(b->d_desc, b->n, b->d_time + p, b->d_srcs);
-            if (b->tile_w == GeoWide::KW)
-                k_batch_step2<GeoWide><<<grid, NTH, GeoWide::kSmemBytes, s>>>(a, b->d_ctx, b->d_srcs, b->d_maps[0], p,
-                                                                              b->d_time + p, b->d_time + (1 - p));
-            else if (b->tile_w == GeoTall::KW)
-                k_batch_step2<GeoTall><<<grid, NTH, GeoTall::kSmemBytes, s>>>(a, b->d_ctx, b->d_srcs, b->d_maps[1], p,
-                                                                              b->d_time + p, b->d_time + (1 - p));
+            if (b->pol == POL_TE)
+                launch_batch_step2<POL_TE>(b, a, grid, p, s);
             else
-                k_batch_step2<GeoMid><<<grid, NTH, GeoMid::kSmemBytes, s>>>(a, b->d_ctx, b->d_srcs, b->d_maps[2], p,
-                                                                            b->d_time + p, b->d_time + (1 - p));
+                launch_batch_step2<POL_TM>(b, a, grid, p, s);
         }
+        else if (b->pol == POL_TE)
+            k_batch_step<float, POL_TE><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
         else
-            k_batch_step<float><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
+            k_batch_step<float, POL_TM><<<grid, 256, 0, s>>>(a, b->d_time + p, b->d_time + (1 - p));
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && b->conv_tol > 0.0) {
@@ -747,6 +767,8 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
     if (o->tile_w == 40 && (o->precision != LBM_EM_F32 || o->conv_tol > 0.0 || (o->tile_h && o->tile_h != 12)))
         return set_error(LBM_EM_EINVAL, "tile_w 40 is the two-step kernel's 40 x 12 tile (FP32, conv_tol 0)");
     if (!(o->conv_tol >= 0.0) || o->min_periods < 0) return set_error(LBM_EM_EINVAL, "conv_tol >= 0, min_periods >= 0");
+    if (o->polarization != 0 && o->polarization != 1)
+        return set_error(LBM_EM_EINVAL, "polarization must be 0 (TM^z) or 1 (TE^z)");
     if (o->tile_h && (o->tile_h > 16)) return set_error(LBM_EM_EINVAL, "tile_h must be <= 16");
     for (int i = 0; i < n; ++i) {
         const lbm_em_instance &s = specs[i];
@@ -765,6 +787,7 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev);
     b->n = n;
     b->prec = o->precision;
+    b->pol = o->polarization == 1 ? POL_TE : POL_TM;
     b->elem = b->prec == LBM_EM_F32 ? 4 : 8;
     b->specs.assign(specs, specs + n);
     lbm_em_status st = LBM_EM_OK;
@@ -884,13 +907,17 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
     }
     // FP32: tensor maps of every instance for the two-step kernel, for both tile shapes
     if (b->prec == LBM_EM_F32) {
-        const void *kern[3] = {(const void *)k_batch_step2<GeoWide>, (const void *)k_batch_step2<GeoTall>,
-                               (const void *)k_batch_step2<GeoMid>};
+        const void *kern[3] = {(const void *)k_batch_step2<GeoWide, POL_TM>, (const void *)k_batch_step2<GeoTall, POL_TM>,
+                               (const void *)k_batch_step2<GeoMid, POL_TM>};
+        const void *kern_te[3] = {(const void *)k_batch_step2<GeoWide, POL_TE>,
+                                  (const void *)k_batch_step2<GeoTall, POL_TE>, (const void *)k_batch_step2<GeoMid, POL_TE>};
         const size_t smem[3] = {GeoWide::kSmemBytes, GeoTall::kSmemBytes, GeoMid::kSmemBytes};
         const int shape[3][2] = {{GeoWide::KW, GeoWide::KH}, {GeoTall::KW, GeoTall::KH}, {GeoMid::KW, GeoMid::KH}};
         for (int g = 0; g < 3; ++g) {
             int per_sm = 0;
             BTRY(cudaFuncSetAttribute(kern[g], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem[g]),
+                 "configuring the two-step batch kernel");
+            BTRY(cudaFuncSetAttribute(kern_te[g], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem[g]),
                  "configuring the two-step batch kernel");
             BTRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[g], NTH, smem[g]),
                  "occupancy of the two-step batch kernel");

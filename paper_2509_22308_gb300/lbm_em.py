@@ -61,7 +61,7 @@ class Instance(ctypes.Structure):
 class BatchOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("min_periods", ctypes.c_int32), ("source_kind", ctypes.c_int32),
-                ("conv_tol", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("conv_tol", ctypes.c_double), ("stream", ctypes.c_void_p), ("polarization", ctypes.c_int32)]
 
 
 _P = ctypes.POINTER
@@ -330,7 +330,7 @@ class Batch:
     """Owner of one ``lbm_em_batch_t``."""
 
     def __init__(self, instances, precision="f32", tile_w=0, tile_h=0, ctas_per_sm=0, stream=None,
-                 conv_tol=0.0, min_periods=0, kind=SRC_HARD):
+                 conv_tol=0.0, min_periods=0, kind=SRC_HARD, polarization="tm"):
         L = load()
         n = len(instances)
         arr = (Instance * n)()
@@ -340,7 +340,8 @@ class Batch:
                               float(inst["R"]),
                               make_janus(inst["a"], inst["phi0"], inst["eps1"], inst["eps2"], inst["pec2"]))
         o = BatchOpts(PRECISIONS.get(precision, precision), int(tile_w), int(tile_h), int(ctas_per_sm),
-                      int(min_periods), int(kind), float(conv_tol), _stream_ptr(stream))
+                      int(min_periods), int(kind), float(conv_tol), _stream_ptr(stream),
+                      {"tm": 0, "te": 1}[polarization])
         b = ctypes.c_void_p()
         _call("lbm_em_batch_create", arr, n, ctypes.byref(o), ctypes.byref(b))
         self.b, self.n, self._L = b, n, L

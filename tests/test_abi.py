@@ -86,3 +86,13 @@ def test_batch_rejects_the_40_wide_tile_outside_the_two_step_kernel(lib):
         with pytest.raises(L.LbmEmError) as e:
             L.Batch([inst], prec, tile_w=40, **kw)
         assert e.value.status == L.EINVAL
+
+
+def test_batch_rejects_an_unknown_polarization(lib):
+    import ctypes as C
+    from paper_2509_22308_gb300 import lbm_em as L
+    arr = (L.Instance * 1)()
+    arr[0] = L.Instance(64, 64, 48, 2, 48, 0, 1.0, 20.0, L.make_janus(10.0, 0.3, 2.0, 4.0, False))
+    o = L.BatchOpts(L.F32, 0, 0, 0, 0, 0, 0.0, None, 2)
+    h = C.c_void_p()
+    assert L.load().lbm_em_batch_create(arr, 1, C.byref(o), C.byref(h)) == L.EINVAL

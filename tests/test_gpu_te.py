@@ -130,3 +130,38 @@ def test_te_far_field_matches_bessel_series():
     rel = np.abs(S - Sa) / Sa
     print(f"TE far field: steps={steps} median={np.median(rel):.4f} within5%={np.mean(rel < 0.05):.2f}")
     assert np.median(rel) < 0.05, (np.median(rel), steps)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_te_batch_matches_single_domain(prec):
+    """TE^z instances of uneven size in one batch: the forces of every instance equal its
+    single-domain TE run (same per-site arithmetic; only the contour sum order differs)."""
+    insts = W.small_cases()
+    b = L.Batch(insts, prec, polarization="te")
+    try:
+        b.run()
+        F, st = b.results()
+    finally:
+        b.close()
+    assert (st == L.OK).all()
+    for i, inst in enumerate(insts):
+        ref = L.run_instance(inst, prec, polarization="te")
+        assert np.max(np.abs(F[i] - ref)) < 1e-12 * np.sum(np.abs(ref)), (i, F[i], ref)
+
+
+def test_te_batch_two_steps_per_launch_is_bit_identical():
+    insts = W.small_cases()
+    insts[0] = dict(insts[0], period=61, ramp=61)  # an odd run length: the last launch takes one step
+    b2 = L.Batch(insts, "f32", tile_w=64, tile_h=8, ctas_per_sm=3, polarization="te")
+    b1 = L.Batch(insts, "f32", tile_w=64, tile_h=4, ctas_per_sm=4, polarization="te")
+    try:
+        assert b2.config() == (64, 8, 3)
+        b2.run()
+        b1.run()
+        F2, s2 = b2.results()
+        F1, _ = b1.results()
+    finally:
+        b1.close()
+        b2.close()
+    assert (s2 == L.OK).all()
+    assert np.array_equal(F1, F2)
