@@ -222,19 +222,8 @@ __device__ __forceinline__ void batch_acc(const double *f3, const int *slot, dou
 // that the kernel's bottleneck).
 using namespace tma_tile;
 
-// Tensor maps of instance i: maps[3 i + p] its state in buffer p, maps[3 i + 2] its ids.
-template <class G>
-__device__ __forceinline__ void batch_issue(const CUtensorMap *maps, int inst, int x0, int y0, int p,
-                                            unsigned char *stage, uint64_t *bar) {
-    issue_tile<G>(maps + 3 * inst + p, maps + 3 * inst + 2, x0, y0, stage, bar);
-}
-
-// The first tile j, j + gridDim.x, ... whose instance still runs at t; -1 if none.
-__device__ __forceinline__ int next_active(const TileCtx *ctx, int n, int j, long long t) {
-    for (; j < n; j += gridDim.x)
-        if (t < ctx[j].steps) return j;
-    return -1;
-}
+// Tensor maps of instance i (in the kernels' `maps`): maps[3 i + p] its state in buffer p,
+// maps[3 i + 2] its ids.
 
 // Source values of every instance at the launch's two times, once per launch (one thread
 // per instance), so that no step-kernel thread evaluates them in FP64.
@@ -249,10 +238,9 @@ __global__ void k_batch_source(const InstDesc *__restrict__ desc, int n, const l
 // instance accumulates Fourier sums at t or t + 1.  Both are template parameters so that
 // the common body carries no per-site branch on them.  c: the tile's record (shared
 // memory, copied to registers here).
-template <class G, int POL, bool ACC, bool TWO>
+template <class G, int POL, bool ACC, bool TWO, class OnStageFree>
 __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const TileCtx &c, long long t,
-                                            const TileSmem &S, const SrcPairF &sp, const CUtensorMap *maps,
-                                            int p, bool has_next, const int4 &next, uint64_t *bar) {
+                                            const TileSmem &S, const SrcPairF &sp, OnStageFree on_stage_free) {
     const int nx = c.nx, ny = c.ny, x0 = c.x0, y0 = c.y0, pitch = c.pitch, kind = c.kind;
     const int ay0 = c.ay0, ay1 = c.ay1;
     const size_t ps = (size_t)c.pstride;
@@ -290,10 +278,7 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
         }
     }
     __syncthreads();  // the stage is read
-    if (threadIdx.x == 0 && has_next) {
-        fence_proxy_async_smem();
-        batch_issue<G>(maps, next.x, next.y, next.z, p, S.stage, bar);
-    }
+    if (threadIdx.x == 0) on_stage_free();
     if constexpr (TWO) {
         for (int k = threadIdx.x; k < G::KW * G::KH; k += NTH) {
             const int lx = k % G::KW, ly = k / G::KW, x = x0 + lx, y = y0 + ly;
@@ -324,10 +309,9 @@ __global__ void __launch_bounds__(NTH, 3)
                   long long *__restrict__ t_out) {
     extern __shared__ unsigned char sm_dyn[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ TileCtx sc;  // the current tile's record
+    __shared__ __align__(128) TileCtx sc[2];  // tile records, copied with their tiles' state
     __shared__ SrcPairF sp;
     __shared__ int s_next;
-    __shared__ int4 s_nhead;  // inst, x0, y0 of the next tile (set and read by thread 0)
     const TileSmem S = carve<G>(sm_dyn);
     const long long t = *t_in;
     const int n = b.n_tiles;
@@ -337,46 +321,60 @@ __global__ void __launch_bounds__(NTH, 3)
         fence_mbar_init();
     }
     __syncthreads();
-    // the loop's tile index lives in thread 0 (which finds the next active tile and issues
-    // its copies) and reaches the block through shared memory
-    int cur = next_active(ctx, n, blockIdx.x, t);
-    if (threadIdx.x == 0 && cur >= 0) {
-        const int4 head = reinterpret_cast<const int4 *>(ctx + cur)[0];  // inst, x0, y0
-        batch_issue<G>(maps, head.x, head.y, head.z, p, S.stage, &bar);
-    }
+    // Tiles are ordered by decreasing run length, so once one of a CTA's tiles has finished
+    // all its later ones have: the next tile is the next grid-stride index if that runs.
+    // Thread 0 owns the walk: it issues each tile's copies (state, ids and its 128-byte
+    // record, on one mbarrier) and prefetches in registers what the next issue needs,
+    // so no global load sits on the path from a tile's arrival to its phase 1.
+    int cur = (int)blockIdx.x < n && t < ctx[blockIdx.x].steps ? (int)blockIdx.x : -1;
+    SrcPairF nsp{0.f, 0.f, 0.f, 0.f};  // thread 0: source values of the tile issued last
+    auto issue = [&](int j, int slot) {  // thread 0: the copies of tile j, record into sc[slot]
+        const int4 h = reinterpret_cast<const int4 *>(ctx + j)[0];  // inst, x0, y0
+        mbar_arrive_expect_tx(&bar, G::STATE_BYTES + G::ID_BYTES + (unsigned)sizeof(TileCtx));
+        tma_load_3d(S.stage, maps + 3 * h.x + p, h.y - 4, h.z - 2, 0, &bar);
+        tma_load_2d(S.stage + G::OFF_IDS, maps + 3 * h.x + 2, id_box_x(h.y), h.z - 2, &bar);
+        bulk_load(&sc[slot], ctx + j, (unsigned)sizeof(TileCtx), &bar);
+        nsp = h.y == 0 ? srcs[h.x] : SrcPairF{0.f, 0.f, 0.f, 0.f};
+    };
+    if (threadIdx.x == 0 && cur >= 0) issue(cur, 0);
     unsigned phase = 0;
-    while (cur >= 0) {  // uniform over the block
-        if (threadIdx.x < 8) reinterpret_cast<int4 *>(&sc)[threadIdx.x] = reinterpret_cast<const int4 *>(ctx + cur)[threadIdx.x];
+    for (int i = 0; cur >= 0; ++i) {  // uniform over the block
+        const int slot = i & 1, cand = cur + (int)gridDim.x;
+        // thread 0: the candidate next tile's run length, read here and used after phase 1
+        long long cand_steps = 0;
         if (threadIdx.x == 0) {
-            const int nxt = next_active(ctx, n, cur + gridDim.x, t);
-            s_next = nxt;
-            if (nxt >= 0) s_nhead = reinterpret_cast<const int4 *>(ctx + nxt)[0];
-        }
-        if (threadIdx.x == 32) {
-            const int4 h = reinterpret_cast<const int4 *>(ctx + cur)[0];
-            sp = h.y == 0 ? srcs[h.x] : SrcPairF{0.f, 0.f, 0.f, 0.f};
+            sp = nsp;
+            if (cand < n) cand_steps = ctx[cand].steps;
         }
         const bool ok = mbar_wait(&bar, phase);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {  // the tile's copies never completed: report, leave
-            if (threadIdx.x == 0) atomicOr(b.err + sc.inst, kErrTimeout);
+            if (threadIdx.x == 0) atomicOr(b.err + ctx[cur].inst, kErrTimeout);  // sc[slot] never arrived
             return;
         }
-        const int nxt = s_next;
-        const bool acc = t + 1 >= sc.acc_from, two = t + 1 < sc.steps;  // uniform over the block
+        const TileCtx &c = sc[slot];
+        auto on_stage_free = [&]() {  // thread 0, once phase 1 has read the stage
+            const bool next = cand < n && t < cand_steps;
+            s_next = next ? cand : -1;
+            if (next) {
+                fence_proxy_async_smem();
+                issue(cand, slot ^ 1);
+            }
+        };
+        const bool acc = t + 1 >= c.acc_from, two = t + 1 < c.steps;  // uniform over the block
         if (two) {
             if (acc)
-                batch2_tile<G, POL, true, true>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+                batch2_tile<G, POL, true, true>(b, c, t, S, sp, on_stage_free);
             else
-                batch2_tile<G, POL, false, true>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+                batch2_tile<G, POL, false, true>(b, c, t, S, sp, on_stage_free);
         } else {
             if (acc)
-                batch2_tile<G, POL, true, false>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+                batch2_tile<G, POL, true, false>(b, c, t, S, sp, on_stage_free);
             else
-                batch2_tile<G, POL, false, false>(b, sc, t, S, sp, maps, p, nxt >= 0, s_nhead, &bar);
+                batch2_tile<G, POL, false, false>(b, c, t, S, sp, on_stage_free);
         }
-        __syncthreads();  // shared memory is free for the next tile
-        cur = nxt;
+        __syncthreads();  // shared memory is free for the next tile; s_next is written
+        cur = s_next;
     }
 }
 
