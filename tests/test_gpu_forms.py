@@ -291,3 +291,49 @@ def test_design_map_symmetry_and_trajectory():
     tr = TR.integrate(fmap, 0.1, t_final=2.0e4, dt=2.0)
     assert abs(fmap(tr[-1, 3])[0, 2]) < 1e-3 * scale
     assert tr[-1, 1] > 0                          # drag pushes along +x
+
+
+def _random_shapes(seed, n, lo, hi):
+    rng = np.random.default_rng(seed)
+    return [(int(rng.integers(lo, hi)), int(rng.integers(lo, hi))) for _ in range(n)]
+
+
+@pytest.mark.parametrize("shape", _random_shapes(11, 8, 4, 300), ids=lambda s: f"{s[0]}x{s[1]}")
+def test_fp32_two_steps_on_random_shapes(shape):
+    """Seeded random lattice sizes (4 .. 299 per side): the TMA-staged two-step kernel gives the
+    bits of one step per launch."""
+    nx, ny = shape
+    a = max(min(nx, ny) / 4.0, 1.0)
+    inst = dict(nx=nx, ny=ny, a=a, phi0=1.1, eps1=2.5, eps2=6.0, pec2=False, period=30, periods=3, R=a,
+                ramp=30)
+    with L.solver_for_instance(inst, "f32", steps_per_launch="two") as s2, \
+            L.solver_for_instance(inst, "f32", steps_per_launch="one") as s1:
+        s2.step(37)
+        s1.step(37)
+        for x, y in zip(s2.fields(), s1.fields()):
+            assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("shape", [(64, 8), (32, 16), (40, 12)], ids=lambda s: f"{s[0]}x{s[1]}")
+def test_batch_two_steps_on_random_instance_sizes(shape):
+    """Seeded random instance sizes (24 .. 259 per side, ragged against every tile shape) and
+    run lengths in one batch: the two-step kernel's forces equal the one-step kernel's bits."""
+    insts = []
+    for k, (nx, ny) in enumerate(_random_shapes(23, 7, 24, 260)):
+        a = min(nx, ny) / 6.0
+        T = 24 + 6 * k
+        insts.append(dict(nx=nx, ny=ny, a=a, phi0=0.4 * k, eps1=2.0, eps2=1.0 + k, pec2=k % 3 == 0, period=T,
+                          periods=2 + k % 3, R=min(nx, ny) / 3.0, ramp=T))
+    b2 = L.Batch(insts, "f32", tile_w=shape[0], tile_h=shape[1], ctas_per_sm=3)
+    b1 = L.Batch(insts, "f32", tile_w=64, tile_h=4, ctas_per_sm=4)
+    try:
+        assert b2.config() == (shape[0], shape[1], 3)
+        b2.run()
+        b1.run()
+        F2, s2 = b2.results()
+        F1, s1 = b1.results()
+    finally:
+        b1.close()
+        b2.close()
+    assert (s2 == L.OK).all() and (s1 == L.OK).all()
+    assert np.array_equal(F1, F2)
