@@ -15,6 +15,7 @@
 // single-domain path.  Tile shape and CTAs per SM are chosen by timing a few steps of
 // each candidate on the actual packed data (then the state is cleared).
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -145,9 +146,11 @@ __device__ __forceinline__ double batch_tile(const BatchArgs<T> &b, const Tile &
     return wsum_t;
 }
 
-// FP32: at most 85 registers so that 3 CTAs of 256 threads stay resident per SM.
+// FP32 and FP64: at most 85 registers so that 3 CTAs of 256 threads stay resident per SM (FP64,
+// bound by its pipe, needs the warps: 102 registers and 2 CTAs per SM gave 9.9 design-map cells/s,
+// 80 registers and 3 CTAs 10.3, 64 registers and 4 CTAs 10.4 with 150-byte spills).
 template <typename T, int POL>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(256, std::is_same<T, df>::value ? 2 : 3)
     k_batch_step(const BatchArgs<T> b, const long long *__restrict__ t_in, long long *__restrict__ t_out) {
     const long long t = *t_in;
     if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + 1;
