@@ -15,9 +15,12 @@
 // single-domain path.  Tile shape and CTAs per SM are chosen by timing a few steps of
 // each candidate on the actual packed data (then the state is cleared).
 #include <algorithm>
+#include <array>
 #include <type_traits>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <numeric>
 #include <vector>
 
@@ -807,8 +810,14 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
         b->own_stream = true;
     }
     BTRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "cudaStreamCreate");
-    // layout
-    std::vector<ContourHost> ch(n);
+    // layout.  Contours, incident-wave constants and phase tables depend only on the lattice
+    // size, the contour and the period; the instances of a design map mostly share them, so
+    // each distinct one is built once (per instance they cost 0.5 s per 4096 instances).
+    std::vector<ContourHost> uniq;  // distinct contours
+    std::vector<int> cid(n);        // instance -> its contour in uniq
+    std::map<std::tuple<int, int, double, double, double, int, double, double>, int> contour_ids;
+    std::map<std::pair<int, double>, std::array<double, 4>> incident;  // (period, E0) -> P, P w
+    std::map<int, size_t> cs_at;    // period -> offset of its phase table in cs_all
     std::vector<double2> cs_all;
     std::vector<size_t> cs_off(n);
     b->desc.resize(n);
@@ -834,23 +843,44 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
         lbm_em_contour c{std::nan(""), std::nan(""), s.contour_radius, s.n_points, 0, s.janus.a};
         if (!std::isnan(s.janus.cx)) c.cx = s.janus.cx;
         if (!std::isnan(s.janus.cy)) c.cy = s.janus.cy;
-        ch[i].E0 = s.E0;
-        st = build_contour(s.nx, s.ny, &c, &ch[i]);
-        if (st) {
-            batch_free(b);
-            return set_error(st, "instance " + std::to_string(i) + ": " + g_last_error);
+        // NaN (the lattice centre) gets a sentinel: NaN keys would compare equal to anything
+        const auto key = std::make_tuple(s.nx, s.ny, std::isnan(c.cx) ? -1e300 : c.cx, std::isnan(c.cy) ? -1e300 : c.cy,
+                                         c.radius, c.n_points, c.a, s.E0);
+        auto found = contour_ids.find(key);
+        if (found == contour_ids.end()) {
+            ContourHost C;
+            C.E0 = s.E0;
+            st = build_contour(s.nx, s.ny, &c, &C);
+            if (st) {
+                batch_free(b);
+                return set_error(st, "instance " + std::to_string(i) + ": " + g_last_error);
+            }
+            found = contour_ids.emplace(key, (int)uniq.size()).first;
+            uniq.push_back(std::move(C));
         }
+        cid[i] = found->second;
+        const ContourHost &C = uniq[cid[i]];
         d.acc_base = (int)accs;
-        accs += ch[i].n_slots;
-        d.y0 = ch[i].y0;
-        d.y1 = ch[i].y1;
+        accs += C.n_slots;
+        d.y0 = C.y0;
+        d.y1 = C.y1;
         d.src.kind = o->source_kind;
         d.src.period = s.period_steps;
         d.src.ramp = s.ramp_steps;
-        incident_constants(s.period_steps, s.E0, &d.src.pr, &d.src.pi, &d.src.qr, &d.src.qi);
-        cs_off[i] = cs_all.size();
-        std::vector<double2> cs = phase_table(s.period_steps);
-        cs_all.insert(cs_all.end(), cs.begin(), cs.end());
+        auto inc = incident.find({s.period_steps, s.E0});
+        if (inc == incident.end()) {
+            std::array<double, 4> v;
+            incident_constants(s.period_steps, s.E0, &v[0], &v[1], &v[2], &v[3]);
+            inc = incident.emplace(std::make_pair(s.period_steps, s.E0), v).first;
+        }
+        d.src.pr = inc->second[0], d.src.pi = inc->second[1], d.src.qr = inc->second[2], d.src.qi = inc->second[3];
+        auto at = cs_at.find(s.period_steps);
+        if (at == cs_at.end()) {
+            at = cs_at.emplace(s.period_steps, cs_all.size()).first;
+            std::vector<double2> cs = phase_table(s.period_steps);
+            cs_all.insert(cs_all.end(), cs.begin(), cs.end());
+        }
+        cs_off[i] = at->second;
         const double eps[3] = {1.0, s.janus.eps1, s.janus.pec2 ? 0.0 : s.janus.eps2};
         for (int r = 0; r < 3; ++r) {
             const bool pec = r == 2 && s.janus.pec2;
@@ -890,15 +920,20 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
     // slot maps, contour points and per-instance contour descriptors
     {
         std::vector<int> smap(slot, -1);
-        std::vector<ContourPt> pts;
+        std::vector<ContourPt> pts;  // each distinct contour's points once, shared by its instances
+        std::vector<int> pts_at(uniq.size(), -1);
         std::vector<ContourDesc> cd(n);
         for (int i = 0; i < n; ++i) {
             const InstDesc &d = b->desc[i];
-            for (int s = 0; s < ch[i].n_slots; ++s)
-                smap[d.slot_base + (size_t)ch[i].site_xy[2 * s + 1] * d.pitch + ch[i].site_xy[2 * s]] = s;
-            cd[i] = ContourDesc{(int)pts.size(), (int)ch[i].pts.size(), d.acc_base, 0,
-                                2.0 / (double)specs[i].period_steps, ch[i].R, ch[i].dl, ch[i].F0, ch[i].M0};
-            pts.insert(pts.end(), ch[i].pts.begin(), ch[i].pts.end());
+            const ContourHost &C = uniq[cid[i]];
+            for (int s = 0; s < C.n_slots; ++s)
+                smap[d.slot_base + (size_t)C.site_xy[2 * s + 1] * d.pitch + C.site_xy[2 * s]] = s;
+            if (pts_at[cid[i]] < 0) {
+                pts_at[cid[i]] = (int)pts.size();
+                pts.insert(pts.end(), C.pts.begin(), C.pts.end());
+            }
+            cd[i] = ContourDesc{pts_at[cid[i]], (int)C.pts.size(), d.acc_base, 0,
+                                2.0 / (double)specs[i].period_steps, C.R, C.dl, C.F0, C.M0};
         }
         BTRY(cudaMemcpyAsync(b->d_slot, smap.data(), slot * sizeof(int), cudaMemcpyHostToDevice, b->stream), "upload slots");
         BTRY(cudaMalloc(&b->d_pts, pts.size() * sizeof(ContourPt)), "cudaMalloc(points)");
