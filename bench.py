@@ -34,7 +34,10 @@ WORKLOAD = "md_janus_512"
 # the 1-byte material id (FP16-deviation: 11 FP16 deviations + 3 FP32 fields each way)
 BYTES_PER_LU = {"f64": 11 * 8 * 2 + 1, "f32": 11 * 4 * 2 + 1, "f16dev": 2 * (11 * 2 + 3 * 4) + 1,
                 "f32x2": 11 * 8 * 2 + 1}
-STEP_KERNEL = {"f64": "k_step<double, false, TM>", "f32": "k_step<float, false, TM>", "f16dev": "k_step_f16<false>"}
+STEP_KERNEL = {"f64": "k_step<double, false, TM>", "f32": "k_step2_tma<false, TM> (two steps per launch)",
+               "f16dev": "k_step2_f16_tma<false> (two steps per launch)"}
+# lattice steps one launch of that kernel advances (the default mode of each form)
+STEPS_PER_LAUNCH = {"f64": 1, "f32": 2, "f16dev": 2}
 # FP64 pipe operations per lattice update of the step kernel: 12 for the moments
 # (sums of 5, 5 and 5 stored populations, one scaling), 16 for the equilibria and 2 f^eq - f
 FP64_OPS_PER_LU = 28
@@ -290,7 +293,8 @@ def main():
     d_out = torch.zeros((n_inst, 3), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     lus_per_step = sum(instance_lus(i) for i in instances)
-    launches_per_step = sum(2 + i["periods"] * i["period"] for i in instances)
+    spl = STEPS_PER_LAUNCH[prec]
+    launches_per_step = sum(2 + i["periods"] * i["period"] // spl for i in instances)
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
     def one_step(plain_events=None):
@@ -348,9 +352,10 @@ def main():
     # roofline of the dominant kernel, the plain step: its algorithmic work over the
     # window in which the plain steps of all instances ran (CUDA events on their streams)
     plain_ms = sum(windows)
-    plain_launches = sum(n for _, _, n, _ in plain) // n_inst
+    plain_launches = sum(n for _, _, n, _ in plain) // n_inst // spl
     plain_sites_steps = sum(n * sites for _, _, n, sites in plain)
-    plain_bytes = plain_sites_steps * BYTES_PER_LU[prec]
+    # a two-step kernel reads and writes the state once per launch, i.e. once per two steps
+    plain_bytes = plain_sites_steps * BYTES_PER_LU[prec] // spl
     avg_launch_us = plain_ms * 1e3 / plain_launches
     achieved = plain_bytes / (plain_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
@@ -438,6 +443,7 @@ def main():
         for fp in ("f32", "f16dev", "f32x2", "f64"):
             if fp == prec:
                 forms[fp] = {"mlups": out["value"] / world, "step_kernel_gbs": round(achieved, 1),
+                             "steps_per_launch": spl,
                              "frac_hbm": round(achieved / peak, 4)}
                 continue
             # sequential on one stream: a 512^2 FP32/FP16 state stays resident in L2 across steps
@@ -463,12 +469,15 @@ def main():
             ms = t0e.elapsed_time(t1e)
             pms = sum(a.elapsed_time(b) for a, b, _ in ev_)
             pn = sum(n for _, _, n in ev_)
-            gbs = pn * 512 * 512 * BYTES_PER_LU[fp] / (pms / 1e3) / 1e9
+            # state bytes per update: one read and one write per launch (two steps for FP32 and
+            # FP16-deviation, one for double-float and FP64)
+            gbs = pn * 512 * 512 * BYTES_PER_LU[fp] / STEPS_PER_LAUNCH.get(fp, 1) / (pms / 1e3) / 1e9
             res = np.array(res)
             ref = results if prec == "f64" else res
             drag = np.abs(ref[:, 0])
             err = np.abs(res - ref) / drag[:, None]
             forms[fp] = {"mlups": round(lus_per_step / (ms / 1e3) / 1e6, 1), "step_kernel_gbs": round(gbs, 1),
+                         "steps_per_launch": STEPS_PER_LAUNCH.get(fp, 1),
                          "frac_hbm": round(gbs / peak, 4),
                          "max_drag_err_rel": float(err[:, 0].max()),
                          "max_lift_torque_err_drag_scale": float(err[:, 1:].max())}
@@ -485,14 +494,14 @@ def main():
         hs = {}
         # TE^z lines: the same lattice and kernels with the TE moments and collision
         for fp, mode, pol in (("f32", "auto", "tm"), ("f32", "one", "tm"), ("f16dev", "auto", "tm"),
-                              ("f16dev", "two", "tm"), ("f64", "auto", "tm"), ("f32x2", "auto", "tm"),
+                              ("f16dev", "one", "tm"), ("f64", "auto", "tm"), ("f32x2", "auto", "tm"),
                               ("f32x2", "two", "tm"), ("f32", "auto", "te"), ("f64", "auto", "te")):
             key = fp + {"auto": "", "one": "_one_step_per_launch", "two": "_two_steps_per_launch"}[mode]
             key += "_te" if pol == "te" else ""
             P = "TE" if pol == "te" else "TM"
             kern = {("f32", "auto"): f"k_step2_tma<false, {P}> (two steps per launch, TMA-staged tiles)",
-                    ("f32", "one"): f"k_step<float, false, {P}>", ("f16dev", "auto"): "k_step_f16<false>",
-                    ("f16dev", "two"): "k_step2_f16<false> (two steps per launch)",
+                    ("f32", "one"): f"k_step<float, false, {P}>", ("f16dev", "one"): "k_step_f16<false>",
+                    ("f16dev", "auto"): "k_step2_f16_tma<false> (two steps per launch, TMA-staged tiles)",
                     ("f64", "auto"): f"k_step<double, false, {P}>",
                     ("f32x2", "auto"): f"k_step<df, false, {P}> (double-float)",
                     ("f32x2", "two"): f"k_step2<df, false, {P}> (double-float, two steps per launch)"}[(fp, mode)]

@@ -74,9 +74,9 @@ typedef enum {
     LBM_EM_SRC_NONE = 2   /* no source (all edges open)                                  */
 } lbm_em_source_kind;
 
-/* lbm_em_grid.flags: how many time steps one kernel launch advances.  By default FP64,
- * FP16-deviation and double-float advance one step per launch and FP32 two (each tile and
- * its halo are copied to shared memory by the TMA unit and advance two steps there).  The
+/* lbm_em_grid.flags: how many time steps one kernel launch advances.  By default FP64 and
+ * double-float advance one step per launch, FP32 and FP16-deviation two (each tile and its
+ * halo are copied to shared memory by the TMA unit and advance two steps there).  The
  * result does not depend on the choice: both modes give the same bits. */
 #define LBM_EM_FLAG_SINGLE_STEP 1  /* always one step per launch                          */
 #define LBM_EM_FLAG_TWO_STEP 2     /* two steps per launch for FP32, FP16-dev, double-float */

@@ -218,6 +218,7 @@ struct lbm_em {
     // FP32 two-step launches: tensor maps of the two state buffers and of the material
     // ids, and the persistent grid
     CUtensorMap tmap[2], idmap;
+    CUtensorMap f16_gmap[2], f16_fmap[2];  // FP16-deviation form: deviation and field planes per buffer
     int tma_ctas = 0;
     // contour and accumulators
     bool has_contour = false;
@@ -334,7 +335,8 @@ static cudaError_t enqueue_step(lbm_em *h, bool acc, cudaStream_t s, int p) {
 // Two steps in one launch (temporal blocking): buf[p] -> buf[1 - p].
 static cudaError_t enqueue_step2(lbm_em *h, bool acc, cudaStream_t s, int p) {
     if (h->prec == LBM_EM_F16DEV)
-        return launch_step2_f16(make_f16_args(h, p), h->d_time + p, h->d_time + (1 - p), acc, s);
+        return launch_step2_f16_tma(make_f16_args(h, p), &h->f16_gmap[p], &h->f16_fmap[p], &h->idmap, h->d_time + p,
+                                    h->d_time + (1 - p), acc, h->tma_ctas, s);
     if (h->prec == LBM_EM_F32X2)
         return launch_step2<df>(make_args<df>(h), (const df *)h->buf[p], (df *)h->buf[1 - p], h->d_time + p,
                                 h->d_time + (1 - p), acc, s);
@@ -473,14 +475,16 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     h->pitch = round_up(g->nx, 32);
     h->pstride = (size_t)h->pitch * (size_t)g->ny;
     h->srccfg = *s;
-    // two steps per launch: forced by the flag, else the FP32 default (the TMA-staged kernel
-    // beat one step per launch on GB300 from 512^2 to 8192^2: 69 / 122 / 129 / 141 / 138
-    // against 58 / 85 / 74 / 76 / 75 GLUPS); the FP16-deviation and double-float forms
-    // default to one step (their two-step kernels are issue-bound and lose)
+    // two steps per launch: forced by the flag, else the default of the FP32 and FP16-deviation
+    // forms, whose TMA-staged kernels beat one step per launch on GB300 at every size measured
+    // (FP32 from 512^2 to 8192^2: 69 / 122 / 129 / 141 / 138 against 58 / 85 / 74 / 76 / 75
+    // GLUPS; FP16-deviation at 512^2 / 2048^2 / 8192^2: 57.6 / 109 / 115.6 against 50.3 / 84.7 /
+    // 89.0); the double-float form defaults to one step (its two-step kernel, 93 KB of shared
+    // memory per CTA, loses)
     if (g->flags & LBM_EM_FLAG_TWO_STEP)
         h->tb = g->precision != LBM_EM_F64;
     else
-        h->tb = g->precision == LBM_EM_F32 && !(g->flags & LBM_EM_FLAG_SINGLE_STEP);
+        h->tb = (g->precision == LBM_EM_F32 || g->precision == LBM_EM_F16DEV) && !(g->flags & LBM_EM_FLAG_SINGLE_STEP);
     for (int i = 0; i < 256; ++i) {
         h->eps_table[i] = 1.0;
         h->pec_id[i] = false;
@@ -517,6 +521,14 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
             TRY(encode_plane_map(&h->tmap[b], (const float *)h->buf[b], h->nx, h->ny, h->pitch, h->pstride,
                                  kTmaTileW, kTmaTileH),
                 "encoding the tensor map of a state buffer");
+        TRY(encode_id_map(&h->idmap, h->d_mat, h->nx, h->ny, h->pitch, kTmaTileW, kTmaTileH),
+            "encoding the tensor map of the ids");
+    }
+    if (h->tb && h->prec == LBM_EM_F16DEV) {
+        TRY(step2_f16_tma_prepare(&h->tma_ctas), "configuring the TMA-staged two-step kernel");
+        for (int b = 0; b < 2; ++b)
+            TRY(encode_f16_maps(&h->f16_gmap[b], &h->f16_fmap[b], h->buf[b], h->nx, h->ny, h->pitch, h->pstride),
+                "encoding the tensor maps of a state buffer");
         TRY(encode_id_map(&h->idmap, h->d_mat, h->nx, h->ny, h->pitch, kTmaTileW, kTmaTileH),
             "encoding the tensor map of the ids");
     }

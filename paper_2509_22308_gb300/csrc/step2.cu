@@ -1,18 +1,14 @@
-// Two time steps per launch for the FP16-deviation and double-float forms: temporal
-// blocking of the fused stream-collide step (arXiv 2509.22308, Sec. III).  (The FP32
-// form's single-domain kernel stages its tiles with the copy engine, step2_tma.cu.)
+// Two time steps per launch for the double-float form: temporal blocking of the fused
+// stream-collide step (arXiv 2509.22308, Sec. III).  (The FP32 and FP16-deviation forms
+// stage their tiles with the copy engine: step2_tma.cu, step2_f16_tma.cu.)
 //
 // A CTA owns a TW x TH tile.  Phase 1 computes the post-collision f*(t) of the tile and
 // a one-site halo (pulled from global memory exactly as the one-step kernel does) into
 // shared memory; phase 2 pulls f(t + 1) of the tile from shared memory, collides and
-// writes f*(t + 1) (FP32) or the fields and deviations of t + 1 (FP16-deviation) to
-// global memory.  Each state element crosses HBM once per two steps (plus the halo,
-// which neighbouring CTAs read at about the same time and L2 serves); the per-site
-// arithmetic is the one-step kernel's, so the result is bit-identical to two one-step
-// launches (the FP16-deviation form rounds the intermediate state to FP16 exactly as
-// storing and reloading it would).
-#include <cuda_fp16.h>
-
+// writes f*(t + 1) to global memory.  Each state element crosses HBM once per two steps
+// (plus the halo, which neighbouring CTAs read at about the same time and L2 serves); the
+// per-site arithmetic is the one-step kernel's, so the result is bit-identical to two
+// one-step launches.
 #include "common.cuh"
 #include "step2.cuh"
 #include "step_f16.cuh"
@@ -60,64 +56,6 @@ __global__ void __launch_bounds__(NT) k_step2(const StepArgs<T> a, const T *__re
     }
 }
 
-template <bool ACC>
-__global__ void __launch_bounds__(NT) k_step2_f16(const F16Args a, const long long *__restrict__ t_in,
-                                                  long long *__restrict__ t_out) {
-    extern __shared__ float sm[];
-    __shared__ SrcPair sp;
-    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
-    const long long t = *t_in;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *t_out = t + 2;
-    source_pair(a.src, x0, t, &sp);
-    __syncthreads();
-    const bool src0 = t >= 1 && a.src.kind != SRC_NONE, src1 = a.src.kind != SRC_NONE;
-    // phase 1: time t; the shared memory receives what a pull would rebuild from the
-    // stored (FP16-rounded) state of time t, so this equals two one-step launches
-    for (int k = threadIdx.x; k < SW * SH; k += NT) {
-        const int lx = k % SW, ly = k / SW, x = x0 - 1 + lx, y = y0 - 1 + ly;
-        if (x < 0 || x >= a.nx || y < 0 || y >= a.ny) continue;
-        const size_t idx = (size_t)y * a.pitch + x;
-        const MatT<float> m = a.mtab[a.mat[idx]];
-        Pop<float> p;
-        pull_f16_planes(a, x, y, p);
-        if (x == 0 && src0) inject_source(a.src.kind, sp.g0, sp.inc0, p);
-        float E3, Hx, Hy, D;
-        moments(p, m, &E3, &Hx, &Hy, &D);
-        if (field_runaway(E3)) atomicOr(a.err, 1u);
-        if (ACC && lx >= 1 && lx <= TW && ly >= 1 && ly <= TH)
-            acc_site(a.accp, a.src, idx, y, t, 3.0 * (double)E3, (double)Hx, (double)Hy);
-        const Fld F = stored_fields(E3, Hx, Hy);
-        __half g[NPLANES];
-        encode_all(p, F, a.scale, g);
-        Pop<float> q;
-        rebuild_all(g, F, a.inv_scale, q);
-        put_smem(sm, ly, lx, q);
-    }
-    __syncthreads();
-    const size_t ps = a.pstride;
-    for (int k = threadIdx.x; k < TW * TH; k += NT) {
-        const int lx = k % TW, ly = k / TW, x = x0 + lx, y = y0 + ly;
-        if (x >= a.nx || y >= a.ny) continue;
-        Pop<float> p;
-        pull_smem(sm, a.nx, a.ny, x, y, lx + 1, ly + 1, p);
-        if (x == 0 && src1) inject_source(a.src.kind, sp.g1, sp.inc1, p);
-        const size_t idx = (size_t)y * a.pitch + x;
-        const MatT<float> m = a.mtab[a.mat[idx]];
-        float E3, Hx, Hy, D;
-        moments(p, m, &E3, &Hx, &Hy, &D);
-        if (field_runaway(E3)) atomicOr(a.err, 1u);
-        if (ACC) acc_site(a.accp, a.src, idx, y, t + 1, 3.0 * (double)E3, (double)Hx, (double)Hy);
-        const Fld F = stored_fields(E3, Hx, Hy);
-        __half g[NPLANES];
-        encode_all(p, F, a.scale, g);
-#pragma unroll
-        for (int q = 0; q < NPLANES; ++q) a.g_out[q * ps + idx] = g[q];
-        a.fe_out[idx] = F.e;
-        a.fhx_out[idx] = F.hx;
-        a.fhy_out[idx] = F.hy;
-    }
-}
-
 template <typename T>
 static cudaError_t allow_smem() {
     const int b = (int)step2_smem<T>();
@@ -131,15 +69,7 @@ static cudaError_t allow_smem() {
     return e;
 }
 
-cudaError_t step2_prepare() {
-    cudaError_t e = allow_smem<df>();
-    const int b = (int)kStep2Smem;
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step2_f16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step2_f16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    return e;
-}
+cudaError_t step2_prepare() { return allow_smem<df>(); }
 
 template <typename T>
 cudaError_t launch_step2(const StepArgs<T> &a, const T *fin, T *fout, const long long *t_in, long long *t_out,
@@ -161,15 +91,5 @@ cudaError_t launch_step2(const StepArgs<T> &a, const T *fin, T *fout, const long
 }
 template cudaError_t launch_step2<df>(const StepArgs<df> &, const df *, df *, const long long *, long long *, bool,
                                       cudaStream_t);
-
-cudaError_t launch_step2_f16(const F16Args &a, const long long *t_in, long long *t_out, bool accumulate,
-                             cudaStream_t s) {
-    dim3 grid((a.nx + TW - 1) / TW, (a.ny + TH - 1) / TH), block(NT);
-    if (accumulate)
-        k_step2_f16<true><<<grid, block, kStep2Smem, s>>>(a, t_in, t_out);
-    else
-        k_step2_f16<false><<<grid, block, kStep2Smem, s>>>(a, t_in, t_out);
-    return cudaGetLastError();
-}
 
 }  // namespace lbmem

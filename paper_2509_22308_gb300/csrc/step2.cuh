@@ -10,7 +10,6 @@ namespace lbmem {
 // with a one-site halo in shared memory (11 planes of SW x SH values: 46.5 KB in FP32,
 // 4 CTAs per SM; 93 KB in double-float, 2 CTAs per SM).
 constexpr int TW = 64, TH = 14, SW = TW + 2, SH = TH + 2, NT = 256;
-constexpr size_t kStep2Smem = (size_t)NPLANES * SH * SW * sizeof(float);
 template <typename T>
 constexpr size_t step2_smem() { return (size_t)NPLANES * SH * SW * sizeof(T); }
 
@@ -89,7 +88,5 @@ cudaError_t step2_prepare();
 template <typename T>
 cudaError_t launch_step2(const StepArgs<T> &a, const T *fin, T *fout, const long long *t_in, long long *t_out,
                          bool accumulate, cudaStream_t s);
-cudaError_t launch_step2_f16(const F16Args &a, const long long *t_in, long long *t_out, bool accumulate,
-                             cudaStream_t s);
 
 }  // namespace lbmem

@@ -10,6 +10,7 @@
 // below, so the one-step, two-step and field kernels of this form agree bit for bit.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -145,6 +146,19 @@ __device__ __forceinline__ void rebuild_all(const __half g[NPLANES], const Fld &
 
 cudaError_t launch_step_f16(const F16Args &a, const long long *t_in, long long *t_out, bool accumulate,
                             cudaStream_t s);
+
+// Two steps per launch on TMA-staged 64 x 8 tiles (step2_f16_tma.cu), bit-identical to two
+// launch_step_f16 calls.  encode_f16_maps builds the tensor maps of one buffer's deviation
+// planes (*gmap) and field planes (*fmap): buf 16-byte aligned, pitch and pstride multiples
+// of 8 (cudaErrorInvalidValue otherwise, or if the driver rejects a map).  The prepare call
+// (once per device, outside stream capture) allows the kernel's shared memory and returns
+// the persistent grid in *max_ctas; ids is the id map of encode_id_map for 64 x 8 tiles.
+cudaError_t encode_f16_maps(CUtensorMap *gmap, CUtensorMap *fmap, const void *buf, int nx, int ny, int pitch,
+                            size_t pstride);
+cudaError_t step2_f16_tma_prepare(int *max_ctas);
+cudaError_t launch_step2_f16_tma(const F16Args &a, const CUtensorMap *gmap, const CUtensorMap *fmap,
+                                 const CUtensorMap *ids, const long long *t_in, long long *t_out, bool accumulate,
+                                 int max_ctas, cudaStream_t s);
 cudaError_t launch_energy_f16(const F16Args &a, const long long *t_dev, double *energy, cudaStream_t s);
 cudaError_t launch_fields_f16(const F16Args &a, const long long *t_dev, double *ez, double *hx, double *hy,
                               cudaStream_t s);

@@ -180,19 +180,21 @@ def test_two_steps_per_launch_is_bit_identical(inst, prec):
         assert np.array_equal(a.force_torque(c), b.force_torque(c))
 
 
-@pytest.mark.parametrize("shape", [(7, 5), (32, 16), (128, 48), (33, 17), (200, 35)],
+@pytest.mark.parametrize("prec", ["f32", "f16dev"])
+@pytest.mark.parametrize("shape", [(7, 5), (32, 16), (64, 8), (128, 48), (33, 17), (200, 35)],
                          ids=lambda s: f"{s[0]}x{s[1]}")
-def test_fp32_two_steps_on_tile_edge_shapes(shape):
-    """The FP32 two-step kernel copies 32 x 16 tiles with their halo in boxes of 40 x 20 sites:
-    a lattice smaller than the box in both directions, exactly one tile, exact multiples of
-    the tile and one site beyond them all give the bits of one step per launch (fields, over
-    even and odd step counts)."""
+def test_two_steps_on_tile_edge_shapes(shape, prec):
+    """The TMA-staged two-step kernels copy 64 x 8 tiles with a two-site halo (boxes of 72 x 12
+    sites in FP32; 80 x 12 deviations and 72 x 12 fields in the FP16-deviation form): a
+    lattice smaller than the box in both directions, exactly one tile, exact multiples of the
+    tile and one site beyond them all give the bits of one step per launch (fields, over even
+    and odd step counts)."""
     nx, ny = shape
     a = min(nx, ny) / 3.0
     inst = dict(nx=nx, ny=ny, a=a, phi0=0.4, eps1=3.0, eps2=1.0, pec2=True, period=24, periods=3,
                 R=a, ramp=24)
-    with L.solver_for_instance(inst, "f32", steps_per_launch="two") as s2, \
-            L.solver_for_instance(inst, "f32", steps_per_launch="one") as s1:
+    with L.solver_for_instance(inst, prec, steps_per_launch="two") as s2, \
+            L.solver_for_instance(inst, prec, steps_per_launch="one") as s1:
         for n in (1, 2, 5, 33, 64):
             s2.step(n)
             s1.step(n)
