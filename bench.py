@@ -493,14 +493,16 @@ def main():
         big = W.md_janus_8192()[0]
         hs = {}
         # TE^z lines: the same lattice and kernels with the TE moments and collision
-        for fp, mode, pol in (("f32", "auto", "tm"), ("f32", "one", "tm"), ("f16dev", "auto", "tm"),
+        for fp, mode, pol in (("f32", "auto", "tm"), ("f32", "one", "tm"), ("f32", "three", "tm"), ("f16dev", "auto", "tm"),
                               ("f16dev", "one", "tm"), ("f64", "auto", "tm"), ("f32x2", "auto", "tm"),
                               ("f32x2", "two", "tm"), ("f32", "auto", "te"), ("f64", "auto", "te")):
-            key = fp + {"auto": "", "one": "_one_step_per_launch", "two": "_two_steps_per_launch"}[mode]
+            key = fp + {"auto": "", "one": "_one_step_per_launch", "two": "_two_steps_per_launch",
+                        "three": "_three_steps_per_launch"}[mode]
             key += "_te" if pol == "te" else ""
             P = "TE" if pol == "te" else "TM"
             kern = {("f32", "auto"): f"k_step2_tma<false, {P}> (two steps per launch, TMA-staged tiles)",
                     ("f32", "one"): f"k_step<float, false, {P}>", ("f16dev", "one"): "k_step_f16<false>",
+                    ("f32", "three"): f"k_step3_tma<false, {P}> (three steps per launch, TMA-staged tiles)",
                     ("f16dev", "auto"): "k_step2_f16_tma<false> (two steps per launch, TMA-staged tiles)",
                     ("f64", "auto"): f"k_step<double, false, {P}>",
                     ("f32x2", "auto"): f"k_step<df, false, {P}> (double-float)",
@@ -523,6 +525,9 @@ def main():
                     # the state crosses HBM once per two steps: half the one-pass bytes per update
                     hs[key]["two_step_bytes_per_lu"] = BYTES_PER_LU[fp] / 2
                     hs[key]["two_step_frac_hbm"] = round(gbs / 2 / peak, 4)
+                if "three steps per launch" in kern:
+                    hs[key]["three_step_bytes_per_lu"] = round(BYTES_PER_LU[fp] / 3, 2)
+                    hs[key]["three_step_frac_hbm"] = round(gbs / 3 / peak, 4)
                 if fp == "f64":
                     ops = FP64_OPS_PER_LU + (1 if pol == "te" else 0)   # TE: 29 per update
                     hs[key]["fp64_ops_per_lu"] = ops

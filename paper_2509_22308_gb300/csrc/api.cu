@@ -219,6 +219,9 @@ struct lbm_em {
     // ids, and the persistent grid
     CUtensorMap tmap[2], idmap;
     CUtensorMap f16_gmap[2], f16_fmap[2];  // FP16-deviation form: deviation and field planes per buffer
+    CUtensorMap tmap3[2], idmap3;          // FP32, three steps per launch
+    bool t3 = false;                       // three steps per launch (FP32)
+    int tma3_ctas = 0;
     int tma_ctas = 0;
     // contour and accumulators
     bool has_contour = false;
@@ -344,7 +347,16 @@ static cudaError_t enqueue_step2(lbm_em *h, bool acc, cudaStream_t s, int p) {
                             h->d_time + (1 - p), acc, h->tma_ctas, s);
 }
 
-// kGraphSteps steps starting from buffer 0 (an even number of launches, so the
+// Three steps in one launch (FP32): buf[p] -> buf[1 - p].
+static cudaError_t enqueue_step3(lbm_em *h, bool acc, cudaStream_t s, int p) {
+    return launch_step3_tma(make_args<float>(h), &h->tmap3[p], &h->idmap3, (float *)h->buf[1 - p], h->d_time + p,
+                            h->d_time + (1 - p), acc, h->tma3_ctas, s);
+}
+
+// Steps per captured graph: kGraphSteps, or 30 (ten launches) with three steps per launch.
+static int graph_steps(const lbm_em *h) { return h->t3 ? 30 : kGraphSteps; }
+
+// graph_steps(h) steps starting from buffer 0 (an even number of launches, so the
 // state is back in buffer 0 at the end).
 static lbm_em_status build_graph(lbm_em *h, bool acc, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
@@ -352,9 +364,11 @@ static lbm_em_status build_graph(lbm_em *h, bool acc, cudaGraphExec_t *out) {
                                    "cudaStreamBeginCapture");
     if (st) return st;
     cudaError_t e = cudaSuccess;
-    const int launches = h->tb ? kGraphSteps / 2 : kGraphSteps;
+    const int launches = h->t3 ? graph_steps(h) / 3 : h->tb ? kGraphSteps / 2 : kGraphSteps;
     for (int i = 0; i < launches && e == cudaSuccess; ++i)
-        e = h->tb ? enqueue_step2(h, acc, h->cap, i & 1) : enqueue_step(h, acc, h->cap, i & 1);
+        e = h->t3   ? enqueue_step3(h, acc, h->cap, i & 1)
+            : h->tb ? enqueue_step2(h, acc, h->cap, i & 1)
+                    : enqueue_step(h, acc, h->cap, i & 1);
     cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -365,13 +379,13 @@ static lbm_em_status build_graph(lbm_em *h, bool acc, cudaGraphExec_t *out) {
     return cuda_status(e, "cudaGraphInstantiate");
 }
 
-// With two steps per launch, launches start at even t only (an odd start takes one
-// single step first), so which intermediate states skip the storage rounding of the
-// FP16-deviation form does not depend on how a run is split into calls.
+// Every mode gives the same bits; two-step launches and their graphs start at even t (an
+// odd start takes one single step first), three-step launches anywhere, and a remainder
+// shorter than a launch's steps takes single steps.
 static lbm_em_status run_steps(lbm_em *h, int64_t n, bool acc) {
     while (n > 0) {
         const bool even = (h->t & 1) == 0;
-        if (h->cur == 0 && n >= kGraphSteps && (even || !h->tb)) {
+        if (h->cur == 0 && n >= graph_steps(h) && (even || !h->tb || h->t3)) {
             cudaGraphExec_t *g = acc ? &h->g_acc : &h->g_plain;
             if (!*g) {
                 lbm_em_status st = build_graph(h, acc, g);
@@ -379,9 +393,15 @@ static lbm_em_status run_steps(lbm_em *h, int64_t n, bool acc) {
             }
             lbm_em_status st = cuda_status(cudaGraphLaunch(*g, h->stream), "cudaGraphLaunch");
             if (st) return st;
-            h->t += kGraphSteps;
-            n -= kGraphSteps;
-        } else if (h->tb && n >= 2 && even) {
+            h->t += graph_steps(h);
+            n -= graph_steps(h);
+        } else if (h->t3 && n >= 3) {
+            lbm_em_status st = cuda_status(enqueue_step3(h, acc, h->stream, h->cur), "step launch");
+            if (st) return st;
+            h->cur ^= 1;
+            h->t += 3;
+            n -= 3;
+        } else if (h->tb && !h->t3 && n >= 2 && even) {
             lbm_em_status st = cuda_status(enqueue_step2(h, acc, h->stream, h->cur), "step launch");
             if (st) return st;
             h->cur ^= 1;
@@ -448,8 +468,11 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     if (!g || !out) return set_error(LBM_EM_EINVAL, "grid/out is NULL");
     *out = nullptr;
     if (g->nx < 4 || g->ny < 4) return set_error(LBM_EM_EINVAL, "nx and ny must be >= 4");
-    if (g->flags & ~(LBM_EM_FLAG_SINGLE_STEP | LBM_EM_FLAG_TWO_STEP | LBM_EM_FLAG_TE))
+    if (g->flags & ~(LBM_EM_FLAG_SINGLE_STEP | LBM_EM_FLAG_TWO_STEP | LBM_EM_FLAG_TE | LBM_EM_FLAG_THREE_STEP))
         return set_error(LBM_EM_EINVAL, "unknown grid flags");
+    if ((g->flags & LBM_EM_FLAG_THREE_STEP) &&
+        (g->precision != LBM_EM_F32 || (g->flags & (LBM_EM_FLAG_SINGLE_STEP | LBM_EM_FLAG_TWO_STEP))))
+        return set_error(LBM_EM_EINVAL, "LBM_EM_FLAG_THREE_STEP is for LBM_EM_F32 alone, without the other step flags");
     if ((g->flags & LBM_EM_FLAG_TE) && g->precision == LBM_EM_F16DEV)
         return set_error(LBM_EM_EINVAL, "TE^z is available in LBM_EM_F64 and LBM_EM_F32");
     if ((g->flags & LBM_EM_FLAG_SINGLE_STEP) && (g->flags & LBM_EM_FLAG_TWO_STEP))
@@ -485,6 +508,7 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
         h->tb = g->precision != LBM_EM_F64;
     else
         h->tb = (g->precision == LBM_EM_F32 || g->precision == LBM_EM_F16DEV) && !(g->flags & LBM_EM_FLAG_SINGLE_STEP);
+    h->t3 = (g->flags & LBM_EM_FLAG_THREE_STEP) != 0;
     for (int i = 0; i < 256; ++i) {
         h->eps_table[i] = 1.0;
         h->pec_id[i] = false;
@@ -523,6 +547,13 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
                 "encoding the tensor map of a state buffer");
         TRY(encode_id_map(&h->idmap, h->d_mat, h->nx, h->ny, h->pitch, kTmaTileW, kTmaTileH),
             "encoding the tensor map of the ids");
+    }
+    if (h->t3) {
+        TRY(step3_tma_prepare(&h->tma3_ctas), "configuring the three-step kernel");
+        for (int b = 0; b < 2; ++b)
+            TRY(encode_step3_maps(&h->tmap3[b], (const float *)h->buf[b], b == 0 ? &h->idmap3 : nullptr, h->d_mat,
+                                  h->nx, h->ny, h->pitch, h->pstride),
+                "encoding the tensor maps of the three-step kernel");
     }
     if (h->tb && h->prec == LBM_EM_F16DEV) {
         TRY(step2_f16_tma_prepare(&h->tma_ctas), "configuring the TMA-staged two-step kernel");

@@ -16,8 +16,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm_em.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
 F64, F32, F16DEV, F32X2 = 0, 1, 2, 3
-FLAG_SINGLE_STEP, FLAG_TWO_STEP = 1, 2
-STEP_MODES = {"auto": 0, "one": FLAG_SINGLE_STEP, "two": FLAG_TWO_STEP}
+FLAG_SINGLE_STEP, FLAG_TWO_STEP, FLAG_THREE_STEP = 1, 2, 8
+STEP_MODES = {"auto": 0, "one": FLAG_SINGLE_STEP, "two": FLAG_TWO_STEP, "three": FLAG_THREE_STEP}
 FLAG_TE = 4
 POLARIZATION_FLAGS = {"tm": 0, "te": FLAG_TE}
 SRC_HARD, SRC_OPEN, SRC_NONE = 0, 1, 2

@@ -96,3 +96,16 @@ def test_batch_rejects_an_unknown_polarization(lib):
     o = L.BatchOpts(L.F32, 0, 0, 0, 0, 0, 0.0, None, 2)
     h = C.c_void_p()
     assert L.load().lbm_em_batch_create(arr, 1, C.byref(o), C.byref(h)) == L.EINVAL
+
+
+def test_three_step_flag_is_fp32_only(lib):
+    """LBM_EM_FLAG_THREE_STEP (8) is accepted for FP32 alone and excludes the other step flags;
+    unknown flags are rejected.  The checks come before any device work."""
+    from paper_2509_22308_gb300 import lbm_em
+    P = lbm_em.PRECISIONS
+    for prec, flags in (("f64", 8), ("f16dev", 8), ("f32x2", 8), ("f32", 8 | 1), ("f32", 8 | 2), ("f32", 16)):
+        g = lbm_em.Grid(16, 16, P[prec], flags, None)
+        h = ctypes.c_void_p()
+        rc = lib.lbm_em_create_janus(ctypes.byref(g), ctypes.byref(lbm_em.make_janus(5, 0.3, 2.0)),
+                                     ctypes.byref(lbm_em.make_source(24)), ctypes.byref(h))
+        assert rc == lbm_em.EINVAL, (prec, flags, rc)

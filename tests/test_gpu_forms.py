@@ -180,27 +180,45 @@ def test_two_steps_per_launch_is_bit_identical(inst, prec):
         assert np.array_equal(a.force_torque(c), b.force_torque(c))
 
 
-@pytest.mark.parametrize("prec", ["f32", "f16dev"])
-@pytest.mark.parametrize("shape", [(7, 5), (32, 16), (64, 8), (128, 48), (33, 17), (200, 35)],
+@pytest.mark.parametrize("prec,mode", [("f32", "two"), ("f16dev", "two"), ("f32", "three")])
+@pytest.mark.parametrize("shape", [(7, 5), (32, 8), (32, 16), (64, 8), (128, 48), (33, 17), (33, 9), (200, 35)],
                          ids=lambda s: f"{s[0]}x{s[1]}")
-def test_two_steps_on_tile_edge_shapes(shape, prec):
-    """The TMA-staged two-step kernels copy 64 x 8 tiles with a two-site halo (boxes of 72 x 12
-    sites in FP32; 80 x 12 deviations and 72 x 12 fields in the FP16-deviation form): a
+def test_multi_steps_on_tile_edge_shapes(shape, prec, mode):
+    """The TMA-staged kernels copy 64 x 8 tiles with a two-site halo for two steps per launch
+    (boxes of 72 x 12 sites in FP32; 80 x 12 deviations and 72 x 12 fields in the
+    FP16-deviation form) and 32 x 8 tiles with a three-site halo for three (40 x 14): a
     lattice smaller than the box in both directions, exactly one tile, exact multiples of the
-    tile and one site beyond them all give the bits of one step per launch (fields, over even
-    and odd step counts)."""
+    tile and one site beyond them all give the bits of one step per launch (fields, over step
+    counts of every residue)."""
     nx, ny = shape
     a = min(nx, ny) / 3.0
     inst = dict(nx=nx, ny=ny, a=a, phi0=0.4, eps1=3.0, eps2=1.0, pec2=True, period=24, periods=3,
                 R=a, ramp=24)
-    with L.solver_for_instance(inst, prec, steps_per_launch="two") as s2, \
+    with L.solver_for_instance(inst, prec, steps_per_launch=mode) as s2, \
             L.solver_for_instance(inst, prec, steps_per_launch="one") as s1:
-        for n in (1, 2, 5, 33, 64):
+        for n in (1, 2, 5, 33, 64, 3, 31):
             s2.step(n)
             s1.step(n)
             for x, y in zip(s2.fields(), s1.fields()):
                 assert np.array_equal(x, y)
         assert np.abs(s2.fields()[0]).max() > 0  # the source has reached the field
+
+
+@pytest.mark.parametrize("pol", ["tm", "te"])
+@pytest.mark.parametrize("inst", W.small_cases()[:3], ids=lambda i: f"{i['nx']}x{i['ny']}")
+def test_three_steps_per_launch_is_bit_identical(inst, pol):
+    """Three steps per launch (FP32, 32 x 8 TMA tiles) equals one step per launch bit for bit,
+    for step counts of every residue modulo 3, through graphs of 30 steps and through the
+    accumulating period (forces)."""
+    with L.solver_for_instance(inst, "f32", steps_per_launch="three", polarization=pol) as a, \
+            L.solver_for_instance(inst, "f32", steps_per_launch="one", polarization=pol) as b:
+        for n in (1, 3, 2, 30, 31, 64, 5):
+            a.step(n)
+            b.step(n)
+            for x, y in zip(a.fields(), b.fields()):
+                assert np.array_equal(x, y)
+        c = L.make_contour(inst["R"], inst["a"])
+        assert np.array_equal(a.force_torque(c), b.force_torque(c))
 
 
 def test_f16dev_split_runs_agree_bitwise():
