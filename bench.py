@@ -224,7 +224,7 @@ def run_reference(args, rank, world):
 
 def profile_case():
     """Two launches of each step kernel (FP64; FP32 and FP16-deviation with two steps
-    per launch, then with one; double-float) on a 2048^2 lattice (state 0.3-0.7 GB per
+    per launch, then with one; double-float; FP32 with three steps per launch) on a 2048^2 lattice (state 0.3-0.7 GB per
     buffer, larger than L2, a few GB on the device in total), two launches of the FP64 step
     on one 512^2 instance of the benchmark workload, then a 24-instance FP32 design map."""
     import torch
@@ -234,9 +234,9 @@ def profile_case():
     inst = dict(nx=2048, ny=2048, a=128.0, phi0=0.5, eps1=4.0, eps2=1.0, pec2=True, period=240, periods=1,
                 R=192.0, ramp=240)
     for fp, mode in (("f64", "auto"), ("f32", "two"), ("f16dev", "two"), ("f32", "one"), ("f16dev", "one"),
-                     ("f32x2", "auto")):
+                     ("f32x2", "auto"), ("f32", "three")):
         with L.solver_for_instance(inst, fp, steps_per_launch=mode) as s:
-            s.step(4 if mode == "two" else 2)
+            s.step({"two": 4, "three": 6}.get(mode, 2))
             s.sync()
     # and two launches of the benchmark's own 512^2 FP64 instance (theta = 0)
     from paper_2509_22308_gb300 import workloads as W
