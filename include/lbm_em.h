@@ -75,14 +75,15 @@ typedef enum {
 } lbm_em_source_kind;
 
 /* lbm_em_grid.flags: how many time steps one kernel launch advances.  By default FP64 and
- * double-float advance one step per launch, FP32 and FP16-deviation two (each tile and its
- * halo are copied to shared memory by the TMA unit and advance two steps there); FP32 can
- * also advance three (LBM_EM_FLAG_THREE_STEP: fewer HBM bytes per step, more halo work;
- * faster on some lattice sizes).  The result does not depend on the choice: every mode gives
- * the same bits.  Invalid combinations return LBM_EM_EINVAL. */
+ * double-float advance one step per launch, FP16-deviation two, FP32 two below 2^25 sites and
+ * three from there on (each tile and its halo are copied to shared memory by the TMA unit
+ * and advance two or three steps there; three move fewer HBM bytes per step but do more halo
+ * work, and pay on the largest lattices).  The flags force a mode.  The result does not
+ * depend on the choice: every mode gives the same bits.  Invalid combinations return
+ * LBM_EM_EINVAL. */
 #define LBM_EM_FLAG_SINGLE_STEP 1  /* always one step per launch                          */
 #define LBM_EM_FLAG_TWO_STEP 2     /* two steps per launch for FP32, FP16-dev, double-float */
-#define LBM_EM_FLAG_THREE_STEP 8   /* three steps per launch (FP32 only; 32 x 8 tiles)       */
+#define LBM_EM_FLAG_THREE_STEP 8   /* three steps per launch (FP32 only; 28 x 12 tiles)      */
 /* TE^z polarization (H_z, E_x, E_y), which the paper leaves for future work (Sec. I): the
  * same scheme and storage (11 planes), incident wave E_y = H_z = E0 sin(w t - k x).  Every
  * call that reports the TM triple (E_z, H_x, H_y) reports (H_z, E_x, E_y) instead: fields,

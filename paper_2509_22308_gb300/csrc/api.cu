@@ -508,7 +508,13 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
         h->tb = g->precision != LBM_EM_F64;
     else
         h->tb = (g->precision == LBM_EM_F32 || g->precision == LBM_EM_F16DEV) && !(g->flags & LBM_EM_FLAG_SINGLE_STEP);
-    h->t3 = (g->flags & LBM_EM_FLAG_THREE_STEP) != 0;
+    // three steps per launch: forced by the flag, else the FP32 default from 2^25 sites on
+    // (measured on GB300, GLUPS three / two: 8192^2 144.2 / 138.0, 4096^2 140.2 / 139.3, 2048^2
+    // 130.5 / 129.1, 1024^2 111.3 / 124.9: the three-step kernel is issue-bound, and on smaller
+    // lattices the two-step kernel gains more from the L2 holding much of the state)
+    h->t3 = (g->flags & LBM_EM_FLAG_THREE_STEP) != 0 ||
+            (g->precision == LBM_EM_F32 && !(g->flags & (LBM_EM_FLAG_SINGLE_STEP | LBM_EM_FLAG_TWO_STEP)) &&
+             (long long)g->nx * g->ny >= (1LL << 25));
     for (int i = 0; i < 256; ++i) {
         h->eps_table[i] = 1.0;
         h->pec_id[i] = false;

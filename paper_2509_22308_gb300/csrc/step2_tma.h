@@ -40,11 +40,11 @@ cudaError_t launch_step2_tma(const StepArgs<float> &a, const CUtensorMap *fin, c
                              const long long *t_in, long long *t_out, bool accumulate, int max_ctas, cudaStream_t s);
 
 // Three steps per launch (step3_tma.cu): kTma3TileW x kTma3TileH tiles with a three-site
-// halo (stage box 40 x 14 x 11 floats, id box 64 x 14 bytes), 63 KB of shared memory per
+// halo (stage box 36 x 18 x 11 floats, id box 48 x 18 bytes), 74 KB of shared memory per
 // CTA, three CTAs per SM.  encode_step3_maps builds the stage map of one FP32 state buffer
 // and, if imap is not NULL, the id map (base and ids 16-byte aligned, pitch a multiple of
 // 16, pstride of 4; cudaErrorInvalidValue otherwise or if the driver rejects a map).
-constexpr int kTma3TileW = 32, kTma3TileH = 8;
+constexpr int kTma3TileW = 28, kTma3TileH = 12;
 cudaError_t encode_step3_maps(CUtensorMap *fmap, const float *base, CUtensorMap *imap, const uint8_t *ids, int nx,
                               int ny, int pitch, size_t pstride);
 cudaError_t step3_tma_prepare(int *max_ctas);

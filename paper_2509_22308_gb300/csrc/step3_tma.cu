@@ -3,14 +3,16 @@
 // the equilibria of Eq. equilibrium distribution functions), one step deeper than
 // step2_tma.cu.
 //
-// A persistent CTA walks 32 x 8 tiles (row-major, grid stride).  For each tile one thread
+// A persistent CTA walks 28 x 12 tiles (row-major, grid stride).  For each tile one thread
 // issues two cp.async.bulk.tensor copies on one mbarrier: the 11 planes over the tile and a
-// three-site halo (x from x0 - 4, the 16-byte boundary: 40 x 14 x 11 floats from y0 - 3)
-// and the material ids over the same rows (64 bytes a row from x0 - 3 rounded down to 16).
-//   phase 1: f*(t) of the tile and a two-site halo (36 x 12) from the stage into buffer 1;
+// three-site halo (x from x0 - 4, the 16-byte boundary: 36 x 18 x 11 floats from y0 - 3)
+// and the material ids over the same rows (48 bytes a row from x0 - 3 rounded down to 16).
+//   phase 1: f*(t) of the tile and a two-site halo (32 x 16) from the stage into buffer 1;
 //   then the stage is free and the next tile's copies go out;
-//   phase 2: f*(t + 1) of the tile and a one-site halo (34 x 10) from buffer 1 into buffer 2;
+//   phase 2: f*(t + 1) of the tile and a one-site halo (30 x 14) from buffer 1 into buffer 2;
 //   phase 3: f*(t + 2) of the tile from buffer 2, stored to global memory.
+// The tile shape keeps the halo work low (3.77 site updates per tile site per launch) and
+// phase 1 at exactly two passes of the 256 threads.
 // Each state element crosses HBM once per three steps (plus the halo rows, which
 // neighbouring CTAs read at about the same time and L2 serves).  The per-site arithmetic is
 // the one-step kernel's and every intermediate value stays FP32, so the result is

@@ -181,12 +181,12 @@ def test_two_steps_per_launch_is_bit_identical(inst, prec):
 
 
 @pytest.mark.parametrize("prec,mode", [("f32", "two"), ("f16dev", "two"), ("f32", "three")])
-@pytest.mark.parametrize("shape", [(7, 5), (32, 8), (32, 16), (64, 8), (128, 48), (33, 17), (33, 9), (200, 35)],
+@pytest.mark.parametrize("shape", [(7, 5), (28, 12), (32, 16), (64, 8), (128, 48), (33, 17), (29, 13), (200, 35)],
                          ids=lambda s: f"{s[0]}x{s[1]}")
 def test_multi_steps_on_tile_edge_shapes(shape, prec, mode):
     """The TMA-staged kernels copy 64 x 8 tiles with a two-site halo for two steps per launch
     (boxes of 72 x 12 sites in FP32; 80 x 12 deviations and 72 x 12 fields in the
-    FP16-deviation form) and 32 x 8 tiles with a three-site halo for three (40 x 14): a
+    FP16-deviation form) and 28 x 12 tiles with a three-site halo for three (36 x 18): a
     lattice smaller than the box in both directions, exactly one tile, exact multiples of the
     tile and one site beyond them all give the bits of one step per launch (fields, over step
     counts of every residue)."""
@@ -207,7 +207,7 @@ def test_multi_steps_on_tile_edge_shapes(shape, prec, mode):
 @pytest.mark.parametrize("pol", ["tm", "te"])
 @pytest.mark.parametrize("inst", W.small_cases()[:3], ids=lambda i: f"{i['nx']}x{i['ny']}")
 def test_three_steps_per_launch_is_bit_identical(inst, pol):
-    """Three steps per launch (FP32, 32 x 8 TMA tiles) equals one step per launch bit for bit,
+    """Three steps per launch (FP32, 28 x 12 TMA tiles) equals one step per launch bit for bit,
     for step counts of every residue modulo 3, through graphs of 30 steps and through the
     accumulating period (forces)."""
     with L.solver_for_instance(inst, "f32", steps_per_launch="three", polarization=pol) as a, \
