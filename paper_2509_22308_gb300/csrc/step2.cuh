@@ -1,4 +1,6 @@
-// Launchers of the two-steps-per-launch (temporally blocked) kernels, see step2.cu.
+// The double-float two-steps-per-launch kernel's tile and launcher (step2.cu), and the
+// helpers every temporally blocked kernel shares: the source values of a launch and the
+// Fourier accumulation of one site.
 #pragma once
 
 #include "common.cuh"
@@ -6,9 +8,8 @@
 
 namespace lbmem {
 
-// Tile of the two-steps-per-launch kernels of step2.cu and of the batch: TW x TH sites,
-// with a one-site halo in shared memory (11 planes of SW x SH values: 46.5 KB in FP32,
-// 4 CTAs per SM; 93 KB in double-float, 2 CTAs per SM).
+// Tile of the double-float two-step kernel: TW x TH sites with a one-site halo in shared
+// memory (11 planes of SW x SH double-float values: 93 KB, 2 CTAs per SM).
 constexpr int TW = 64, TH = 14, SW = TW + 2, SH = TH + 2, NT = 256;
 template <typename T>
 constexpr size_t step2_smem() { return (size_t)NPLANES * SH * SW * sizeof(T); }
