@@ -165,7 +165,10 @@ def _stream_ptr(stream):
 
 
 class Solver:
-    """Owner of one ``lbm_em_t`` handle; methods map one-to-one onto the C calls."""
+    """Owner of one ``lbm_em_t`` handle; methods map one-to-one onto the C calls.
+
+    ``steps_per_launch``: "auto" (the library's default for the form and lattice size), "one",
+    "two" (FP32, FP16-deviation, double-float) or "three" (FP32); the modes give the same bits."""
 
     def __init__(self, nx, ny, precision="f64", *, janus: Janus | None = None, eps_map=None, pec_mask=None,
                  source: Source, stream=None, steps_per_launch="auto", polarization="tm"):
