@@ -329,6 +329,9 @@ lbm_em_status lbm_em_batch_steps(lbm_em_batch_t *b, int64_t *steps);
 lbm_em_status lbm_em_batch_config(lbm_em_batch_t *b, int32_t *tile_w, int32_t *tile_h,
                                   int32_t *ctas_per_sm);
 
+/* Release every resource of the batch (NULL is accepted): waits for the work queued on the
+ * batch's stream, frees its device memory and graphs, and destroys the stream if the library
+ * created it.  Always LBM_EM_OK for a batch from lbm_em_batch_create or NULL. */
 lbm_em_status lbm_em_batch_destroy(lbm_em_batch_t *b);
 
 #ifdef __cplusplus

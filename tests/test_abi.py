@@ -30,6 +30,24 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_every_declaration_is_documented():
+    """Each function of the header comes right after its own comment block (arguments,
+    layout, ownership, errors)."""
+    lines = open(HEADER).read().split("\n")
+    decl = re.compile(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(lbm_em_[a-z_0-9]+)\s*\(")
+    seen = 0
+    for i, line in enumerate(lines):
+        m = decl.match(line)
+        if not m:
+            continue
+        seen += 1
+        j = i - 1
+        while j >= 0 and not lines[j].strip():
+            j -= 1
+        assert lines[j].rstrip().endswith("*/"), f"{m.group(1)} has no comment block of its own"
+    assert seen == len(declared_functions())
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), f"missing export {name}"
