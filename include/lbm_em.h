@@ -309,16 +309,29 @@ typedef struct {
 
 typedef struct lbm_em_batch lbm_em_batch_t;
 
-/* Pack n instances (uneven sizes allowed) into one multi-domain layout on the device. */
+/* Pack n instances (uneven sizes allowed) into one multi-domain layout on the device: a
+ * design map of Sec. IV (one instance per parameter cell, each the single-domain problem of
+ * Sec. II-III).  specs[0..n) and *o are copied (the caller keeps them); *out receives a handle
+ * the library owns until lbm_em_batch_destroy.  Instances sharing a lattice size, contour and
+ * period share one contour description and phase table.  Synchronous: with a tile shape or
+ * CTA count not pinned, the autotuner times a few steps of each candidate on the packed data
+ * and clears the state.  Errors: LBM_EM_EINVAL for a bad option or instance (the message
+ * names it), LBM_EM_ENOMEM / LBM_EM_ECUDA on device failure or without a GPU. */
 lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n,
                                   const lbm_em_batch_opts *o, lbm_em_batch_t **out);
 
-/* Rasterise every instance, then run each to completion (persistent kernel over the packed tile list,
- * replayed under a CUDA graph), then the contour integral of each.  Asynchronous. */
+/* Rasterise every instance (Sec. II), run each for its periods (Eq. LBGK equation, the last
+ * period with the Fourier accumulation of Sec. III) in a persistent kernel over the packed
+ * tile list replayed under a CUDA graph, then the contour integral of each (Sec. II.B).  A
+ * second call starts again from rest.  Asynchronous on the batch's stream; returns launch
+ * errors only: per-instance failures come back through lbm_em_batch_results. */
 lbm_em_status lbm_em_batch_run(lbm_em_batch_t *b);
 
-/* Wait and fetch results: out[3*i .. 3*i+2] = {F~x, F~y, M~z} of instance i and
- * status[i] (an lbm_em_status) per instance; either may be NULL. */
+/* Wait for the run and fetch: out[3*i .. 3*i+2] = {F~x, F~y, M~z} of instance i (normalised
+ * by F0, M0 of Sec. II.B) and status[i] per instance (LBM_EM_OK, LBM_EM_EUNSTABLE for a
+ * runaway field, LBM_EM_ETIMEOUT for a tile copy that never completed); caller-owned host
+ * arrays of 3 n doubles and n int32, either may be NULL.  Returns LBM_EM_ETIMEOUT or
+ * LBM_EM_EUNSTABLE if any instance has that status, LBM_EM_ESTATE before the first run. */
 lbm_em_status lbm_em_batch_results(lbm_em_batch_t *b, double *out, int32_t *status);
 
 /* Steps each instance ran in the last lbm_em_batch_run (its run length, shortened by a
