@@ -40,8 +40,10 @@ typedef enum {
     LBM_EM_EINVAL = 1,     /* bad argument (NULL, size, eps < 1, too many materials ...) */
     LBM_EM_ENOMEM = 2,     /* device or host allocation failed                          */
     LBM_EM_ECUDA = 3,      /* a CUDA runtime call failed (no device, launch error ...)  */
-    LBM_EM_EUNSTABLE = 4,  /* a field became non-finite or reached 3*2^20 (sticky)     */
-    LBM_EM_ETIMEOUT = 5,   /* a bounded device-side wait gave up                        */
+    LBM_EM_EUNSTABLE = 4,  /* a field became non-finite or |E| reached 3 * 2^(20 + k),
+                              2^k <= |E0| < 2^(k+1) (sticky)                             */
+    LBM_EM_ETIMEOUT = 5,   /* a bounded device-side wait gave up; the handle or batch
+                              must then be destroyed (it refuses further steps)         */
     LBM_EM_ESTATE = 6      /* call not valid in the handle's state                       */
 } lbm_em_status;
 
@@ -58,7 +60,8 @@ typedef enum {
                             arithmetic by error-free transformations; FP64-class results
                             (the FP64 parity bound holds) at HBM-bound speed on GB300,
                             whose FP64 pipe is 1/64 of its FP32 rate.  Not an IEEE
-                            binary64 computation; one step per launch, single domain.  */
+                            binary64 computation.  One step per launch by default
+                            (LBM_EM_FLAG_TWO_STEP selects two); the batch accepts it too */
 } lbm_em_precision;
 
 /* Left-edge plane-wave source (Sec. III: the wave enters through the left boundary, the
@@ -94,8 +97,8 @@ typedef enum {
 typedef struct {
     int32_t nx, ny;       /* lattice size, each >= 4                                      */
     int32_t precision;    /* lbm_em_precision                                             */
-    int32_t flags;        /* 0, LBM_EM_FLAG_SINGLE_STEP or LBM_EM_FLAG_TWO_STEP, optionally
-                             | LBM_EM_FLAG_TE                                             */
+    int32_t flags;        /* 0, LBM_EM_FLAG_SINGLE_STEP, LBM_EM_FLAG_TWO_STEP or
+                             LBM_EM_FLAG_THREE_STEP, optionally | LBM_EM_FLAG_TE          */
     void *stream;         /* cudaStream_t every kernel of the handle runs on; NULL: the
                              library creates a private non-blocking stream                */
 } lbm_em_grid;
@@ -105,7 +108,10 @@ typedef struct {
     int32_t ramp_steps;   /* >= 0: amplitude ramp sin^2(pi t / (2 ramp)) for t < ramp     */
     int32_t kind;         /* lbm_em_source_kind                                           */
     int32_t reserved;     /* 0                                                            */
-    double E0;            /* incident amplitude (the force scale F0 uses it)              */
+    double E0;            /* incident amplitude (the force scale F0 uses it).  The scheme is
+                             linear, so the runaway test and the FP16 deviation scale
+                             follow it: with 2^k <= |E0| < 2^(k+1) the test fires at
+                             |E| >= 3 * 2^(20 + k) and deviations are stored x 2^(10 - k)  */
 } lbm_em_source;
 
 /* Janus cylinder (Sec. II): radius a, region II (eps1) where d . n_d > 1e-9 with
@@ -164,7 +170,10 @@ lbm_em_status lbm_em_destroy(lbm_em_t *h);
 lbm_em_status lbm_em_step(lbm_em_t *h, int64_t n);
 
 /* Wait for the handle's stream; returns LBM_EM_EUNSTABLE if any step flagged a
- * non-finite or runaway field since creation (the flag is sticky). */
+ * non-finite or runaway field since creation (the flag is sticky), LBM_EM_ETIMEOUT if a
+ * tile copy of a step never completed.  After LBM_EM_ETIMEOUT a copy may still have been in
+ * flight when its thread block left, so the handle's state is undefined: lbm_em_step and
+ * lbm_em_accumulate then return LBM_EM_ESTATE, and the handle must be destroyed. */
 lbm_em_status lbm_em_sync(lbm_em_t *h);
 
 /* Current time step count (host view; equals the number of steps enqueued). */
@@ -249,6 +258,30 @@ const char *lbm_em_last_error(void);
  * on the legacy default stream; LBM_EM_EINVAL for a limit outside the range. */
 lbm_em_status lbm_em_probe_bounded_wait(int64_t limit_cycles);
 
+/* Diagnostic of the FP64 pipe (the paper has no counterpart), the ceiling of the FP64 step on
+ * GB300: enqueues on `stream` (a cudaStream_t; NULL: the legacy default stream) one launch of
+ * 8 independent FP64 fused multiply-add chains of `iters` steps (>= 1) in each of 8 x 256
+ * threads per SM, and writes the number of FMAs the launch performs to *fma_per_launch.  Time
+ * it with events on the same stream: FMAs / time is the measured FP64 operation rate.
+ * Asynchronous; LBM_EM_EINVAL for iters < 1 or a NULL output. */
+lbm_em_status lbm_em_probe_fp64_fma(void *stream, int64_t iters, double *fma_per_launch);
+
+/* Bytes this library has copied host -> device (*h2d) and device -> host (*d2h) in the calls
+ * of the solver and the batch since it was loaded (either pointer may be NULL): e.g. the
+ * transfer volume of one end-to-end run is the difference of two readings.  The library
+ * counts each copy when it enqueues it. */
+lbm_em_status lbm_em_transfer_bytes(uint64_t *h2d, uint64_t *d2h);
+
+/* Host-side fault injection for tests of the clean-up paths (the paper has no counterpart).
+ * Every device and pinned-host allocation the library makes counts as one attempt.  With
+ * fail_at > 0 the fail_at-th attempt after this call fails as if the device or host were out
+ * of memory, so the call that made it returns LBM_EM_ENOMEM after releasing what it had
+ * already allocated; fail_at = 0 disarms the hook.  *live (may be NULL) receives the number
+ * of device buffers and pinned blocks that handles and batches hold at the time of the call
+ * (pinned blocks parked for reuse between handles are not held by any).  Process-wide and
+ * thread-safe; nothing is injected on the device.  LBM_EM_EINVAL for fail_at < 0. */
+lbm_em_status lbm_em_test_alloc_hook(int64_t fail_at, int64_t *live);
+
 /* Rasterise a Janus disc on the device into host region ids [ny][nx]
  * (0 vacuum, 1 region II, 2 region III).  Sec. II, Sec. IV.A staircase. */
 lbm_em_status lbm_em_rasterize_janus(const lbm_em_janus *j, int32_t nx, int32_t ny, uint8_t *regions);
@@ -265,10 +298,12 @@ lbm_em_status lbm_em_rasterize_janus(const lbm_em_janus *j, int32_t nx, int32_t 
  * library holds it until the process exits) and then copied into regions[ny][nx] (host).
  *  - ny * (nx rounded up to a multiple of 32) must not exceed LBM_EM_NOALLOC_RASTER_BYTES;
  *    a larger request returns LBM_EM_EINVAL with a message and launches nothing.
- *  - The first call on a device looks up the array's address on that device
- *    (cudaGetSymbolAddress) and keeps it; make that first call before any CUDA stream
- *    capture is active.
- *  - Runs on the legacy default stream and returns once regions is filled.
+ *  - Each call looks up the array's address in the current context (cudaGetSymbolAddress,
+ *    which allocates nothing), so the address stays right after the caller resets the
+ *    device or recreates its primary context.
+ *  - Runs on the legacy default stream and copies synchronously, returning once regions is
+ *    filled.  Neither is allowed while a global- or thread-local-mode stream capture is
+ *    active, so no call may overlap one; such a call returns LBM_EM_ECUDA.
  *  - Every call shares the one array, which keeps the last call's contents; calls that
  *    overlap on the GPU (several host threads at once) race, so serialise them. */
 lbm_em_status lbm_em_rasterize_janus_noalloc(const lbm_em_janus *j, int32_t nx, int32_t ny, uint8_t *regions);
@@ -331,7 +366,8 @@ lbm_em_status lbm_em_batch_run(lbm_em_batch_t *b);
  * by F0, M0 of Sec. II.B) and status[i] per instance (LBM_EM_OK, LBM_EM_EUNSTABLE for a
  * runaway field, LBM_EM_ETIMEOUT for a tile copy that never completed); caller-owned host
  * arrays of 3 n doubles and n int32, either may be NULL.  Returns LBM_EM_ETIMEOUT or
- * LBM_EM_EUNSTABLE if any instance has that status, LBM_EM_ESTATE before the first run. */
+ * LBM_EM_EUNSTABLE if any instance has that status, LBM_EM_ESTATE before the first run.
+ * After LBM_EM_ETIMEOUT lbm_em_batch_run returns LBM_EM_ESTATE: destroy the batch. */
 lbm_em_status lbm_em_batch_results(lbm_em_batch_t *b, double *out, int32_t *status);
 
 /* Steps each instance ran in the last lbm_em_batch_run (its run length, shortened by a

@@ -173,6 +173,7 @@ static void prepare_pool(int dev) {
 }
 
 static cudaError_t pinned_get(size_t bytes, void **p, size_t *cap) {
+    if (alloc_should_fail()) return cudaErrorMemoryAllocation;
     size_t c = 4096;
     while (c < bytes) c <<= 1;
     {
@@ -182,15 +183,19 @@ static cudaError_t pinned_get(size_t bytes, void **p, size_t *cap) {
             *cap = it->first;
             *p = it->second;
             g_pinned_free.erase(it);
+            alloc_held(1);
             return cudaSuccess;
         }
     }
     *cap = c;
-    return cudaMallocHost(p, c);
+    const cudaError_t e = cudaMallocHost(p, c);
+    if (e == cudaSuccess) alloc_held(1);
+    return e;
 }
 
 static void pinned_put(void *p, size_t cap) {
     if (!p) return;
+    alloc_held(-1);
     std::lock_guard<std::mutex> lock(g_pool_mu);
     g_pinned_free.emplace(cap, p);
 }
@@ -214,6 +219,9 @@ struct lbm_em {
     lbm_em_source srccfg{};
     int64_t t = 0;
     int cur = 0;      // buffer holding the current state (and device time word)
+    // a bounded wait for a tile copy gave up (seen by lbm_em_sync): a copy may still have
+    // been in flight when its CTA left, so the handle refuses further steps
+    bool timed_out = false;
     bool tb = false;  // two steps per launch (temporal blocking) for the HBM-bound forms
     // FP32 two-step launches: tensor maps of the two state buffers and of the material
     // ids, and the persistent grid
@@ -246,12 +254,12 @@ struct lbm_em {
 
 template <typename P>
 static cudaError_t dev_alloc(lbm_em *h, P **p, size_t bytes) {
-    return cudaMallocAsync((void **)p, bytes, h->stream);
+    return dmalloc_async((void **)p, bytes, h->stream);
 }
 
 template <typename P>
 static void dev_free(lbm_em *h, P *&p) {
-    if (p) cudaFreeAsync((void *)p, h->stream);
+    dfree_async((void *)p, h->stream);
     p = nullptr;
 }
 
@@ -289,6 +297,7 @@ static StepArgs<T> make_args(const lbm_em *h) {
     a.accp.y0 = h->ch.y0;
     a.accp.y1 = h->ch.y1;
     a.err = h->d_err;
+    a.runaway = runaway_bits<T>(h->srccfg.E0);
     return a;
 }
 
@@ -306,8 +315,9 @@ static F16Args make_f16_args(const lbm_em *h, int p) {
     a.accp.y0 = h->ch.y0;
     a.accp.y1 = h->ch.y1;
     a.err = h->d_err;
-    a.scale = kF16Scale;
-    a.inv_scale = 1.0f / kF16Scale;
+    a.runaway = runaway_bits<float>(h->srccfg.E0);
+    a.scale = f16_scale(h->srccfg.E0);
+    a.inv_scale = 1.0f / a.scale;  // exact: a power of two
     const size_t hb = f16_half_bytes(h->pstride), fb = f16_plane_bytes(h->pstride);
     char *in = (char *)h->buf[p], *out = (char *)h->buf[1 - p];
     a.g = (const __half *)in;
@@ -585,7 +595,7 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     void *up = nullptr;
     TRY(upload_staging(h, cs.size() * sizeof(double2), &up), "pinned staging");
     std::memcpy(up, cs.data(), cs.size() * sizeof(double2));
-    TRY(cudaMemcpyAsync(h->d_cs, up, cs.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream),
+    TRY(copy_async(h->d_cs, up, cs.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream),
         "cudaMemcpy(phase table)");
     TRY(cudaEventRecord(h->up_ev, h->stream), "cudaEventRecord");
     h->src.kind = s->kind;
@@ -616,7 +626,7 @@ static lbm_em_status upload_table(lbm_em *h) {
         bytes = tab.size() * sizeof(tab[0]);
         std::memcpy(h->h_stage, tab.data(), bytes);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_mtab, h->h_stage, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = copy_async(h->d_mtab, h->h_stage, bytes, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->stage_ev, h->stream);
     return cuda_status(e, "uploading the material table");
 }
@@ -671,7 +681,7 @@ lbm_em_status lbm_em_create(const lbm_em_grid *g, const double *eps_map, const u
     st = cuda_status(upload_staging(h, n, &up), "pinned staging");
     if (!st) {
         std::memcpy(up, idv.data(), n);
-        st = cuda_status(cudaMemcpy2DAsync(h->d_mat, h->pitch, up, h->nx, h->nx, h->ny, cudaMemcpyHostToDevice,
+        st = cuda_status(copy2d_async(h->d_mat, h->pitch, up, h->nx, h->nx, h->ny, cudaMemcpyHostToDevice,
                                            h->stream),
                          "uploading material ids");
     }
@@ -752,9 +762,15 @@ lbm_em_status lbm_em_destroy(lbm_em_t *h) {
     return LBM_EM_OK;
 }
 
+static lbm_em_status refuse_after_timeout(const lbm_em *h) {
+    return h->timed_out ? set_error(LBM_EM_ESTATE, "a tile copy timed out on this handle: destroy it and create a new one")
+                        : LBM_EM_OK;
+}
+
 lbm_em_status lbm_em_step(lbm_em_t *h, int64_t n) {
     if (!h) return set_error(LBM_EM_EINVAL, "handle is NULL");
     if (n < 0) return set_error(LBM_EM_EINVAL, "n must be >= 0");
+    if (lbm_em_status st = refuse_after_timeout(h)) return st;
     cudaSetDevice(h->dev);
     return run_steps(h, n, false);
 }
@@ -763,12 +779,15 @@ lbm_em_status lbm_em_sync(lbm_em_t *h) {
     if (!h) return set_error(LBM_EM_EINVAL, "handle is NULL");
     cudaSetDevice(h->dev);
     unsigned err = 0;
-    lbm_em_status st = cuda_status(cudaMemcpyAsync(&err, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream),
+    lbm_em_status st = cuda_status(copy_async(&err, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream),
                                    "reading the error flag");
     if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (st) return st;
-    if (err & kErrTimeout) return set_error(LBM_EM_ETIMEOUT, "a bounded wait for a tile load gave up");
-    if (err) return set_error(LBM_EM_EUNSTABLE, "a field became non-finite or exceeded 3*2^20");
+    if (err & kErrTimeout) {
+        h->timed_out = true;
+        return set_error(LBM_EM_ETIMEOUT, "a bounded wait for a tile load gave up");
+    }
+    if (err) return set_error(LBM_EM_EUNSTABLE, "a field became non-finite or exceeded 3 * 2^20 times the source amplitude");
     return LBM_EM_OK;
 }
 
@@ -829,14 +848,14 @@ lbm_em_status lbm_em_set_contour(lbm_em_t *h, const lbm_em_contour *c) {
         st = cuda_status(cudaMemsetAsync(h->d_slot, 0xff, h->pstride * sizeof(int), h->stream), "clearing slots");
     }
     if (!st && band)
-        st = cuda_status(cudaMemcpyAsync(h->d_slot + (size_t)y0 * h->pitch, up, b_slot, cudaMemcpyHostToDevice,
+        st = cuda_status(copy_async(h->d_slot + (size_t)y0 * h->pitch, up, b_slot, cudaMemcpyHostToDevice,
                                          h->stream),
                          "uploading slots");
     if (!st)
-        st = cuda_status(cudaMemcpyAsync(h->d_pts, up + o_pts, b_pts, cudaMemcpyHostToDevice, h->stream),
+        st = cuda_status(copy_async(h->d_pts, up + o_pts, b_pts, cudaMemcpyHostToDevice, h->stream),
                          "uploading contour");
     if (!st)
-        st = cuda_status(cudaMemcpyAsync(h->d_inc, up + o_inc, b_inc, cudaMemcpyHostToDevice, h->stream),
+        st = cuda_status(copy_async(h->d_inc, up + o_inc, b_inc, cudaMemcpyHostToDevice, h->stream),
                          "uploading incident");
     if (!st) st = cuda_status(cudaEventRecord(h->up_ev, h->stream), "cudaEventRecord");
     if (!st)
@@ -854,6 +873,7 @@ lbm_em_status lbm_em_set_contour(lbm_em_t *h, const lbm_em_contour *c) {
 lbm_em_status lbm_em_accumulate(lbm_em_t *h, int64_t n) {
     if (!h) return set_error(LBM_EM_EINVAL, "handle is NULL");
     if (!h->has_contour) return set_error(LBM_EM_ESTATE, "no contour set");
+    if (lbm_em_status st = refuse_after_timeout(h)) return st;
     if (n < 0) return set_error(LBM_EM_EINVAL, "n must be >= 0");
     cudaSetDevice(h->dev);
     lbm_em_status st = run_steps(h, n, true);
@@ -870,7 +890,7 @@ lbm_em_status lbm_em_contour_integral(lbm_em_t *h, double out[3]) {
                                    "contour kernel");
     double res[3];
     if (!st)
-        st = cuda_status(cudaMemcpyAsync(res, h->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+        st = cuda_status(copy_async(res, h->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
                          "reading forces");
     if (!st) st = lbm_em_sync(h);
     if (st) return st;
@@ -912,7 +932,7 @@ lbm_em_status lbm_em_far_field(lbm_em_t *h, const double *angles, int32_t n_angl
     if (st) return st;
     double *d_ang = d + 3 * (size_t)n_angles;
     std::vector<double> res(3 * (size_t)n_angles);
-    st = cuda_status(cudaMemcpyAsync(d_ang, angles, n_angles * sizeof(double), cudaMemcpyHostToDevice, h->stream),
+    st = cuda_status(copy_async(d_ang, angles, n_angles * sizeof(double), cudaMemcpyHostToDevice, h->stream),
                      "uploading angles");
     if (!st)
         st = cuda_status(launch_farfield(h->d_acc, 2.0 / (double)h->n_acc, h->d_pts, (int)h->ch.pts.size(), h->d_inc,
@@ -920,7 +940,7 @@ lbm_em_status lbm_em_far_field(lbm_em_t *h, const double *angles, int32_t n_angl
                                          h->pol, d_ang, n_angles, d, h->stream),
                          "far-field kernel");
     if (!st)
-        st = cuda_status(cudaMemcpyAsync(res.data(), d, res.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+        st = cuda_status(copy_async(res.data(), d, res.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
                          "reading far field");
     if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     dev_free(h, d);
@@ -948,7 +968,7 @@ lbm_em_status lbm_em_energy(lbm_em_t *h, double *W) {
         st = cuda_status(e, "energy kernel");
     }
     double w = 0.0;
-    if (!st) st = cuda_status(cudaMemcpyAsync(&w, d, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "reading energy");
+    if (!st) st = cuda_status(copy_async(&w, d, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "reading energy");
     if (!st) st = lbm_em_sync(h);
     if (!st) *W = w;
     return st;
@@ -1013,7 +1033,7 @@ lbm_em_status lbm_em_get_fields(lbm_em_t *h, double *ez, double *hx, double *hy)
     double *dst[3] = {ez, hx, hy};
     for (int k = 0; k < 3 && !st; ++k)
         if (dst[k])
-            st = cuda_status(cudaMemcpyAsync(dst[k], h->d_fields + k * n, n * sizeof(double), cudaMemcpyDeviceToHost,
+            st = cuda_status(copy_async(dst[k], h->d_fields + k * n, n * sizeof(double), cudaMemcpyDeviceToHost,
                                              h->stream),
                              "reading fields");
     if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
@@ -1028,7 +1048,7 @@ lbm_em_status lbm_em_get_phasors(lbm_em_t *h, int32_t *site_xy, double *phasors,
     if (phasors) {
         if (h->n_acc <= 0) return set_error(LBM_EM_ESTATE, "no accumulated steps");
         cudaSetDevice(h->dev);
-        lbm_em_status st = cuda_status(cudaMemcpyAsync(phasors, h->d_acc, (size_t)h->ch.n_slots * 6 * sizeof(double),
+        lbm_em_status st = cuda_status(copy_async(phasors, h->d_acc, (size_t)h->ch.n_slots * 6 * sizeof(double),
                                                        cudaMemcpyDeviceToHost, h->stream),
                                        "reading accumulators");
         if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
@@ -1045,7 +1065,7 @@ lbm_em_status lbm_em_get_material(lbm_em_t *h, uint8_t *ids, double *eps_table) 
     if (eps_table)
         for (int i = 0; i < 256; ++i) eps_table[i] = h->pec_id[i] ? 0.0 : h->eps_table[i];
     if (ids) {
-        lbm_em_status st = cuda_status(cudaMemcpy2DAsync(ids, h->nx, h->d_mat, h->pitch, h->nx, h->ny,
+        lbm_em_status st = cuda_status(copy2d_async(ids, h->nx, h->d_mat, h->pitch, h->nx, h->ny,
                                                          cudaMemcpyDeviceToHost, h->stream),
                                        "reading material ids");
         if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
@@ -1076,9 +1096,9 @@ lbm_em_status lbm_em_save_state(lbm_em_t *h, void *buf, size_t *bytes) {
     std::memcpy(buf, &hd, sizeof(hd));
     char *p = (char *)buf + sizeof(hd);
     lbm_em_status st = cuda_status(
-        cudaMemcpyAsync(p, h->buf[h->cur], dist, cudaMemcpyDeviceToHost, h->stream), "saving distributions");
+        copy_async(p, h->buf[h->cur], dist, cudaMemcpyDeviceToHost, h->stream), "saving distributions");
     if (!st && accb)
-        st = cuda_status(cudaMemcpyAsync(p + dist, h->d_acc, accb, cudaMemcpyDeviceToHost, h->stream), "saving acc");
+        st = cuda_status(copy_async(p + dist, h->d_acc, accb, cudaMemcpyDeviceToHost, h->stream), "saving acc");
     if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (!st) *bytes = need;
     return st;
@@ -1103,11 +1123,11 @@ lbm_em_status lbm_em_load_state(lbm_em_t *h, const void *buf, size_t bytes) {
     // return before its DMA has reached the device, and the handle's non-blocking stream
     // would not wait for it
     lbm_em_status st = cuda_status(
-        cudaMemcpyAsync(h->buf[h->cur], p, dist, cudaMemcpyHostToDevice, h->stream), "loading distributions");
+        copy_async(h->buf[h->cur], p, dist, cudaMemcpyHostToDevice, h->stream), "loading distributions");
     if (!st && accb)
-        st = cuda_status(cudaMemcpyAsync(h->d_acc, p + dist, accb, cudaMemcpyHostToDevice, h->stream), "loading acc");
+        st = cuda_status(copy_async(h->d_acc, p + dist, accb, cudaMemcpyHostToDevice, h->stream), "loading acc");
     if (!st)
-        st = cuda_status(cudaMemcpyAsync(h->d_time + h->cur, &tt, sizeof(tt), cudaMemcpyHostToDevice, h->stream),
+        st = cuda_status(copy_async(h->d_time + h->cur, &tt, sizeof(tt), cudaMemcpyHostToDevice, h->stream),
                          "loading time");
     if (!st) st = cuda_status(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (st) return st;
@@ -1131,13 +1151,13 @@ lbm_em_status lbm_em_rasterize_janus(const lbm_em_janus *j, int32_t nx, int32_t 
     uint8_t *d = nullptr;
     cudaStream_t s = nullptr;
     st = cuda_status(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate");
-    if (!st) st = cuda_status(cudaMalloc(&d, (size_t)pitch * ny), "cudaMalloc");
+    if (!st) st = cuda_status(dmalloc(&d, (size_t)pitch * ny), "cudaMalloc");
     if (!st) st = cuda_status(launch_rasterize(nx, ny, pitch, cx, cy, j->a, -std::sin(j->phi0), -std::cos(j->phi0), d, s),
                               "rasterise kernel");
     if (!st)
-        st = cuda_status(cudaMemcpy2DAsync(regions, nx, d, pitch, nx, ny, cudaMemcpyDeviceToHost, s), "reading regions");
+        st = cuda_status(copy2d_async(regions, nx, d, pitch, nx, ny, cudaMemcpyDeviceToHost, s), "reading regions");
     if (!st) st = cuda_status(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-    cudaFree(d);
+    dfree(d);
     if (s) cudaStreamDestroy(s);
     return st;
 }

@@ -8,25 +8,28 @@ namespace lbmem {
 // Region id per site (Sec. II; staircase of Sec. IV.A): 0 outside |d| <= a,
 // 1 (region II) where d . n_d > 1e-9, 2 (region III) otherwise.  Explicit
 // round-to-nearest operations keep the decisions identical to a plain
-// evaluation of the same expressions in double precision.
+// evaluation of the same expressions in double precision.  Rows are walked with a
+// grid stride, so a lattice of any height (grid.y is limited to 65535) is covered.
 __global__ void k_rasterize(int nx, int ny, int pitch, double cx, double cy, double a2, double ndx,
                             double ndy, uint8_t *ids) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= nx || y >= ny) return;
-    const double dx = __dsub_rn((double)x, cx), dy = __dsub_rn((double)y, cy);
-    const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-    uint8_t id = 0;
-    if (r2 <= a2) {
-        const double side = __dadd_rn(__dmul_rn(dx, ndx), __dmul_rn(dy, ndy));
-        id = side > 1e-9 ? 1 : 2;
+    if (x >= nx) return;
+    const double dx = __dsub_rn((double)x, cx);
+    for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+        const double dy = __dsub_rn((double)y, cy);
+        const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+        uint8_t id = 0;
+        if (r2 <= a2) {
+            const double side = __dadd_rn(__dmul_rn(dx, ndx), __dmul_rn(dy, ndy));
+            id = side > 1e-9 ? 1 : 2;
+        }
+        ids[(size_t)y * pitch + x] = id;
     }
-    ids[(size_t)y * pitch + x] = id;
 }
 
 cudaError_t launch_rasterize(int nx, int ny, int pitch, double cx, double cy, double a, double ndx,
                              double ndy, uint8_t *ids, cudaStream_t s) {
-    dim3 block(256), grid((nx + 255) / 256, ny);
+    dim3 block(256), grid((nx + 255) / 256, ny < 65535 ? ny : 65535);
     k_rasterize<<<grid, block, 0, s>>>(nx, ny, pitch, cx, cy, a * a, ndx, ndy, ids);
     return cudaGetLastError();
 }

@@ -40,7 +40,8 @@ struct InstDesc {
     int nx, ny, pitch, period;
     size_t pstride, base, mat_base, slot_base;
     long long steps, acc_from;
-    int acc_base, y0, y1, pad;
+    int acc_base, y0, y1;
+    unsigned runaway;   // exponent-field threshold of the runaway test in the batch's type (runaway_bits)
     SourceParams src;
     double mtab[3][4];  // per region id: MatT in the batch's type, widened (exactly) to double
     MatT<float> mtabf[3];  // the same in FP32 (FP32 batches), so no tile converts on the FP64 pipe
@@ -56,7 +57,9 @@ struct Tile {
 struct alignas(16) TileCtx {
     int inst, x0, y0, nx;
     int ny, pitch, kind, ay0;  // ay0, ay1: rows holding contour stencil sites
-    int ay1, pad0, pad1, pad2;
+    int ay1;
+    unsigned runaway;          // FP32 runaway threshold of the instance (runaway_bits<float>)
+    int pad1, pad2;
     long long base, pstride, steps, acc_from;
     MatT<float> m[3];  // region table in FP32
 };
@@ -125,7 +128,7 @@ __device__ __forceinline__ double batch_tile(const BatchArgs<T> &b, const Tile &
         if (BOOK) {
             const bool acc_row = acc && y >= d.y0 && y <= d.y1;
             double f3[3], w;
-            bad = update_site<POL, true>(p, m, acc_row ? f3 : nullptr, sample ? &w : nullptr);
+            bad = update_site<POL, true>(p, m, d.runaway, acc_row ? f3 : nullptr, sample ? &w : nullptr);
             if (acc_row) {
                 const int s = b.slot[d.slot_base + idx];
                 if (s >= 0) {
@@ -141,7 +144,7 @@ __device__ __forceinline__ double batch_tile(const BatchArgs<T> &b, const Tile &
             }
             if (sample) wsum_t += w;
         } else {
-            bad = update_site<POL, true>(p, m, nullptr, nullptr);
+            bad = update_site<POL, true>(p, m, d.runaway, nullptr, nullptr);
         }
         if (bad) atomicOr(b.err + tl.inst, kErrUnstable);
         store_site(fout, d.pstride, idx, p);
@@ -249,6 +252,7 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
                                             const TileSmem &S, const SrcPairF &sp, OnStageFree on_stage_free) {
     const int nx = c.nx, ny = c.ny, x0 = c.x0, y0 = c.y0, pitch = c.pitch, kind = c.kind;
     const int ay0 = c.ay0, ay1 = c.ay1;
+    const unsigned rthr = c.runaway;
     const size_t ps = (size_t)c.pstride;
     const long long acc_from = c.acc_from;
     const MatT<float> *smat = c.m;
@@ -270,10 +274,10 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
         bool bad;
         if (ACC && interior && t >= acc_from && y >= ay0 && y <= ay1) {
             double f3[3];
-            bad = update_site<POL, true>(q, smat[id], f3, nullptr);
+            bad = update_site<POL, true>(q, smat[id], rthr, f3, nullptr);
             batch_acc(f3, b.slot, b.acc, d, idx, t);
         } else {
-            bad = update_site<POL, true>(q, smat[id], nullptr, nullptr);
+            bad = update_site<POL, true>(q, smat[id], rthr, nullptr, nullptr);
         }
         if (bad) atomicOr(err, kErrUnstable);
         if (TWO) {
@@ -297,10 +301,10 @@ __device__ __forceinline__ void batch2_tile(const BatchArgs<float> &b, const Til
             bool bad;
             if (ACC && t + 1 >= acc_from && y >= ay0 && y <= ay1) {
                 double f3[3];
-                bad = update_site<POL, true>(q, m, f3, nullptr);
+                bad = update_site<POL, true>(q, m, rthr, f3, nullptr);
                 batch_acc(f3, b.slot, b.acc, d, idx, t + 1);
             } else {
-                bad = update_site<POL, true>(q, m, nullptr, nullptr);
+                bad = update_site<POL, true>(q, m, rthr, nullptr, nullptr);
             }
             if (bad) atomicOr(err, kErrUnstable);
             store_site(fout, ps, idx, q);
@@ -498,6 +502,9 @@ struct lbm_em_batch {
     int two_ctas[3] = {0, 0, 0};
     cudaGraphExec_t graph = nullptr;
     bool ran = false;
+    // a bounded wait for a tile copy gave up (seen by lbm_em_batch_results): a copy may
+    // still have been in flight when its CTA left, so the batch refuses further runs
+    bool timed_out = false;
     // convergence exits
     double conv_tol = 0.0;
     int min_periods = 1;
@@ -510,25 +517,25 @@ static void batch_free(lbm_em_batch *b) {
     cudaSetDevice(b->dev);
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
-    cudaFree(b->buf[0]);
-    cudaFree(b->buf[1]);
-    cudaFree(b->d_mat);
-    cudaFree(b->d_slot);
-    cudaFree(b->d_acc);
-    cudaFree(b->d_out);
-    cudaFree(b->d_cs);
-    cudaFree(b->d_desc);
-    cudaFree(b->d_tiles);
-    cudaFree(b->d_cdesc);
-    cudaFree(b->d_pts);
-    cudaFree(b->d_time);
-    cudaFree(b->d_err);
-    cudaFree(b->d_energy);
-    cudaFree(b->d_prev);
-    cudaFree(b->d_settled);
-    for (CUtensorMap *m : b->d_maps) cudaFree(m);
-    cudaFree(b->d_ctx);
-    cudaFree(b->d_srcs);
+    dfree(b->buf[0]);
+    dfree(b->buf[1]);
+    dfree(b->d_mat);
+    dfree(b->d_slot);
+    dfree(b->d_acc);
+    dfree(b->d_out);
+    dfree(b->d_cs);
+    dfree(b->d_desc);
+    dfree(b->d_tiles);
+    dfree(b->d_cdesc);
+    dfree(b->d_pts);
+    dfree(b->d_time);
+    dfree(b->d_err);
+    dfree(b->d_energy);
+    dfree(b->d_prev);
+    dfree(b->d_settled);
+    for (CUtensorMap *m : b->d_maps) dfree(m);
+    dfree(b->d_ctx);
+    dfree(b->d_srcs);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -542,11 +549,11 @@ static lbm_em_status batch_tiles(lbm_em_batch *b, int tw, int th) {
         for (int y0 = 0; y0 < d.ny; y0 += th)
             for (int x0 = 0; x0 < d.nx; x0 += tw) tiles.push_back(Tile{i, x0, y0, 0});
     }
-    cudaFree(b->d_tiles);
+    dfree(b->d_tiles);
     b->d_tiles = nullptr;
-    lbm_em_status st = cuda_status(cudaMalloc(&b->d_tiles, tiles.size() * sizeof(Tile)), "cudaMalloc(tiles)");
+    lbm_em_status st = cuda_status(dmalloc(&b->d_tiles, tiles.size() * sizeof(Tile)), "cudaMalloc(tiles)");
     if (!st)
-        st = cuda_status(cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
+        st = cuda_status(copy_async(b->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
                                          b->stream),
                          "uploading tiles");
     b->n_tiles = (int)tiles.size();
@@ -561,14 +568,15 @@ static lbm_em_status batch_tiles(lbm_em_batch *b, int tw, int th) {
             std::memset(&c, 0, sizeof(c));
             c.inst = tl.inst, c.x0 = tl.x0, c.y0 = tl.y0, c.nx = d.nx;
             c.ny = d.ny, c.pitch = d.pitch, c.kind = d.src.kind, c.ay0 = d.y0, c.ay1 = d.y1;
+            c.runaway = runaway_bits<float>(b->specs[tl.inst].E0);
             c.base = (long long)d.base, c.pstride = (long long)d.pstride, c.steps = d.steps, c.acc_from = d.acc_from;
             for (int r = 0; r < 3; ++r) c.m[r] = d.mtabf[r];
         }
-        cudaFree(b->d_ctx);
+        dfree(b->d_ctx);
         b->d_ctx = nullptr;
-        st = cuda_status(cudaMalloc(&b->d_ctx, ctx.size() * sizeof(TileCtx)), "cudaMalloc(tile records)");
+        st = cuda_status(dmalloc(&b->d_ctx, ctx.size() * sizeof(TileCtx)), "cudaMalloc(tile records)");
         if (!st)
-            st = cuda_status(cudaMemcpyAsync(b->d_ctx, ctx.data(), ctx.size() * sizeof(TileCtx),
+            st = cuda_status(copy_async(b->d_ctx, ctx.data(), ctx.size() * sizeof(TileCtx),
                                              cudaMemcpyHostToDevice, b->stream),
                              "uploading tile records");  // pageable: staged before the call returns
     }
@@ -674,7 +682,7 @@ static lbm_em_status batch_clear(lbm_em_batch *b) {
     if (!st) st = cuda_status(cudaMemsetAsync(b->d_settled, 0, b->n * sizeof(int), b->stream), "clear");
     // run lengths may have been shortened on the device by a convergence exit
     if (!st)
-        st = cuda_status(cudaMemcpyAsync(b->d_desc, b->desc.data(), b->n * sizeof(InstDesc), cudaMemcpyHostToDevice,
+        st = cuda_status(copy_async(b->d_desc, b->desc.data(), b->n * sizeof(InstDesc), cudaMemcpyHostToDevice,
                                          b->stream),
                          "restoring descriptors");
     if (!st) st = cuda_status(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
@@ -864,6 +872,7 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
         accs += C.n_slots;
         d.y0 = C.y0;
         d.y1 = C.y1;
+        d.runaway = b->prec == LBM_EM_F64 ? runaway_bits<double>(s.E0) : runaway_bits<float>(s.E0);
         d.src.kind = o->source_kind;
         d.src.period = s.period_steps;
         d.src.ramp = s.ramp_steps;
@@ -899,24 +908,24 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
     b->mat_bytes = mat;
     b->slot_elems = slot;
     b->acc_slots = accs;
-    BTRY(cudaMalloc(&b->buf[0], base * b->elem), "cudaMalloc(batch distributions)");
-    BTRY(cudaMalloc(&b->buf[1], base * b->elem), "cudaMalloc(batch distributions)");
-    BTRY(cudaMalloc(&b->d_mat, mat), "cudaMalloc(batch materials)");
-    BTRY(cudaMalloc(&b->d_slot, slot * sizeof(int)), "cudaMalloc(batch slots)");
-    BTRY(cudaMalloc(&b->d_acc, std::max<size_t>(accs, 1) * 6 * sizeof(double)), "cudaMalloc(batch acc)");
-    BTRY(cudaMalloc(&b->d_out, (size_t)n * 3 * sizeof(double)), "cudaMalloc(batch out)");
-    BTRY(cudaMalloc(&b->d_cs, cs_all.size() * sizeof(double2)), "cudaMalloc(batch phases)");
-    BTRY(cudaMalloc(&b->d_desc, n * sizeof(InstDesc)), "cudaMalloc(batch desc)");
-    BTRY(cudaMalloc(&b->d_time, 2 * sizeof(long long)), "cudaMalloc(time)");
-    BTRY(cudaMalloc(&b->d_err, n * sizeof(unsigned)), "cudaMalloc(err)");
-    BTRY(cudaMalloc(&b->d_energy, n * sizeof(double)), "cudaMalloc(energy)");
-    BTRY(cudaMalloc(&b->d_prev, n * sizeof(double)), "cudaMalloc(energy)");
-    BTRY(cudaMalloc(&b->d_settled, n * sizeof(int)), "cudaMalloc(energy)");
+    BTRY(dmalloc(&b->buf[0], base * b->elem), "cudaMalloc(batch distributions)");
+    BTRY(dmalloc(&b->buf[1], base * b->elem), "cudaMalloc(batch distributions)");
+    BTRY(dmalloc(&b->d_mat, mat), "cudaMalloc(batch materials)");
+    BTRY(dmalloc(&b->d_slot, slot * sizeof(int)), "cudaMalloc(batch slots)");
+    BTRY(dmalloc(&b->d_acc, std::max<size_t>(accs, 1) * 6 * sizeof(double)), "cudaMalloc(batch acc)");
+    BTRY(dmalloc(&b->d_out, (size_t)n * 3 * sizeof(double)), "cudaMalloc(batch out)");
+    BTRY(dmalloc(&b->d_cs, cs_all.size() * sizeof(double2)), "cudaMalloc(batch phases)");
+    BTRY(dmalloc(&b->d_desc, n * sizeof(InstDesc)), "cudaMalloc(batch desc)");
+    BTRY(dmalloc(&b->d_time, 2 * sizeof(long long)), "cudaMalloc(time)");
+    BTRY(dmalloc(&b->d_err, n * sizeof(unsigned)), "cudaMalloc(err)");
+    BTRY(dmalloc(&b->d_energy, n * sizeof(double)), "cudaMalloc(energy)");
+    BTRY(dmalloc(&b->d_prev, n * sizeof(double)), "cudaMalloc(energy)");
+    BTRY(dmalloc(&b->d_settled, n * sizeof(int)), "cudaMalloc(energy)");
     b->conv_tol = o->conv_tol;
     b->min_periods = o->min_periods > 0 ? o->min_periods : 1;
-    BTRY(cudaMemcpyAsync(b->d_cs, cs_all.data(), cs_all.size() * sizeof(double2), cudaMemcpyHostToDevice, b->stream), "upload");
+    BTRY(copy_async(b->d_cs, cs_all.data(), cs_all.size() * sizeof(double2), cudaMemcpyHostToDevice, b->stream), "upload");
     for (int i = 0; i < n; ++i) b->desc[i].src.cs = b->d_cs + cs_off[i];
-    BTRY(cudaMemcpyAsync(b->d_desc, b->desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice, b->stream), "upload");
+    BTRY(copy_async(b->d_desc, b->desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice, b->stream), "upload");
     // slot maps, contour points and per-instance contour descriptors
     {
         std::vector<int> smap(slot, -1);
@@ -935,11 +944,11 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
             cd[i] = ContourDesc{pts_at[cid[i]], (int)C.pts.size(), d.acc_base, 0,
                                 2.0 / (double)specs[i].period_steps, C.R, C.dl, C.F0, C.M0};
         }
-        BTRY(cudaMemcpyAsync(b->d_slot, smap.data(), slot * sizeof(int), cudaMemcpyHostToDevice, b->stream), "upload slots");
-        BTRY(cudaMalloc(&b->d_pts, pts.size() * sizeof(ContourPt)), "cudaMalloc(points)");
-        BTRY(cudaMemcpyAsync(b->d_pts, pts.data(), pts.size() * sizeof(ContourPt), cudaMemcpyHostToDevice, b->stream), "upload");
-        BTRY(cudaMalloc(&b->d_cdesc, n * sizeof(ContourDesc)), "cudaMalloc(contour desc)");
-        BTRY(cudaMemcpyAsync(b->d_cdesc, cd.data(), n * sizeof(ContourDesc), cudaMemcpyHostToDevice, b->stream), "upload");
+        BTRY(copy_async(b->d_slot, smap.data(), slot * sizeof(int), cudaMemcpyHostToDevice, b->stream), "upload slots");
+        BTRY(dmalloc(&b->d_pts, pts.size() * sizeof(ContourPt)), "cudaMalloc(points)");
+        BTRY(copy_async(b->d_pts, pts.data(), pts.size() * sizeof(ContourPt), cudaMemcpyHostToDevice, b->stream), "upload");
+        BTRY(dmalloc(&b->d_cdesc, n * sizeof(ContourDesc)), "cudaMalloc(contour desc)");
+        BTRY(copy_async(b->d_cdesc, cd.data(), n * sizeof(ContourDesc), cudaMemcpyHostToDevice, b->stream), "upload");
     }
     // FP32: tensor maps of every instance for the two-step kernel, for both tile shapes
     if (b->prec == LBM_EM_F32) {
@@ -968,13 +977,13 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
                                    shape[g][1]),
                      "encoding an instance's id map");
             }
-            BTRY(cudaMalloc(&b->d_maps[g], maps.size() * sizeof(CUtensorMap)), "cudaMalloc(tensor maps)");
-            BTRY(cudaMemcpyAsync(b->d_maps[g], maps.data(), maps.size() * sizeof(CUtensorMap),
+            BTRY(dmalloc(&b->d_maps[g], maps.size() * sizeof(CUtensorMap)), "cudaMalloc(tensor maps)");
+            BTRY(copy_async(b->d_maps[g], maps.data(), maps.size() * sizeof(CUtensorMap),
                                  cudaMemcpyHostToDevice, b->stream),
                  "upload");
             b->two_ctas[g] = per_sm;
         }
-        BTRY(cudaMalloc(&b->d_srcs, (size_t)n * sizeof(SrcPairF)), "cudaMalloc(source values)");
+        BTRY(dmalloc(&b->d_srcs, (size_t)n * sizeof(SrcPairF)), "cudaMalloc(source values)");
     }
     // rasterise every instance on the device (again at every run)
     BTRY(batch_rasterize(b), "rasterise");
@@ -996,6 +1005,8 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
 
 lbm_em_status lbm_em_batch_run(lbm_em_batch_t *b) {
     if (!b) return set_error(LBM_EM_EINVAL, "batch is NULL");
+    if (b->timed_out)
+        return set_error(LBM_EM_ESTATE, "a tile copy timed out in this batch: destroy it and create a new one");
     cudaSetDevice(b->dev);
     lbm_em_status st = b->ran ? batch_clear(b) : LBM_EM_OK;
     if (!st) st = cuda_status(batch_rasterize(b), "rasterise");
@@ -1049,9 +1060,9 @@ lbm_em_status lbm_em_batch_results(lbm_em_batch_t *b, double *out, int32_t *stat
     std::vector<double> res((size_t)b->n * 3);
     std::vector<unsigned> err(b->n);
     lbm_em_status st = cuda_status(
-        cudaMemcpyAsync(res.data(), b->d_out, res.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "read");
+        copy_async(res.data(), b->d_out, res.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "read");
     if (!st)
-        st = cuda_status(cudaMemcpyAsync(err.data(), b->d_err, err.size() * sizeof(unsigned), cudaMemcpyDeviceToHost,
+        st = cuda_status(copy_async(err.data(), b->d_err, err.size() * sizeof(unsigned), cudaMemcpyDeviceToHost,
                                          b->stream),
                          "read");
     if (!st) st = cuda_status(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
@@ -1063,7 +1074,10 @@ lbm_em_status lbm_em_batch_results(lbm_em_batch_t *b, double *out, int32_t *stat
         any |= err[i] != 0;
         timeout |= (err[i] & kErrTimeout) != 0;
     }
-    if (timeout) return set_error(LBM_EM_ETIMEOUT, "a bounded wait for a tile load gave up");
+    if (timeout) {
+        b->timed_out = true;
+        return set_error(LBM_EM_ETIMEOUT, "a bounded wait for a tile load gave up");
+    }
     if (any) return set_error(LBM_EM_EUNSTABLE, "at least one instance became unstable");
     return LBM_EM_OK;
 }
@@ -1074,7 +1088,7 @@ lbm_em_status lbm_em_batch_steps(lbm_em_batch_t *b, int64_t *steps) {
     cudaSetDevice(b->dev);
     std::vector<InstDesc> d(b->n);
     lbm_em_status st = cuda_status(
-        cudaMemcpyAsync(d.data(), b->d_desc, b->n * sizeof(InstDesc), cudaMemcpyDeviceToHost, b->stream), "read");
+        copy_async(d.data(), b->d_desc, b->n * sizeof(InstDesc), cudaMemcpyDeviceToHost, b->stream), "read");
     if (!st) st = cuda_status(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
     if (st) return st;
     for (int i = 0; i < b->n; ++i) steps[i] = d[i].steps;

@@ -77,6 +77,8 @@ struct StepArgs {
     SourceParams src;
     AccParams accp;
     unsigned *err;        // sticky error word
+    unsigned runaway;     // exponent-field threshold of the runaway test (runaway_bits)
+    int pad2;
 };
 
 template <typename T>
@@ -297,12 +299,16 @@ __device__ __forceinline__ void collide_te(Pop<T> &p, T Ey3, T Ex3, T Hz) {
     p.hxz = Ex3 - p.hxz;
 }
 
-// |E_z/3| >= 2^20 or non-finite, tested on the exponent bits (integer ALU only).
-__device__ __forceinline__ bool field_runaway(double e3) {
-    return (unsigned)(__double2hiint(e3) & 0x7ff00000) >= 0x41300000u;
+// Runaway test on the exponent bits (integer ALU only): |E/3| >= 2^(20 + k) or non-finite,
+// where 2^k <= |E0| < 2^(k + 1) for the incident amplitude E0 (k = 0 for E0 = 0), so the test
+// fires when a field has grown by about 2^20 over its drive whatever the amplitude (the
+// scheme is linear: every field and force scales with E0).  thr is the threshold on the
+// exponent field of the type: runaway_bits<T>(E0) on the host.
+__device__ __forceinline__ bool field_runaway(double e3, unsigned thr) {
+    return (unsigned)(__double2hiint(e3) & 0x7ff00000) >= thr;
 }
-__device__ __forceinline__ bool field_runaway(float e3) {
-    return (__float_as_uint(e3) & 0x7f800000u) >= ((127u + 20u) << 23);
+__device__ __forceinline__ bool field_runaway(float e3, unsigned thr) {
+    return (__float_as_uint(e3) & 0x7f800000u) >= thr;
 }
 
 template <typename T>
@@ -322,14 +328,15 @@ __device__ __forceinline__ void store_site(T *__restrict__ f, size_t ps, size_t 
 
 // One site of either polarization: the field triple (TM: E_z, H_x, H_y; TE: H_z, E_x, E_y)
 // from the moments, into f3 when wanted; the energy density (D.E + H^2)/2 when wanted;
-// then, if COLLIDE, the post-collision populations.  Returns whether the field ran away.
+// then, if COLLIDE, the post-collision populations.  Returns whether the field ran away
+// (field_runaway with threshold rthr).
 template <int POL, bool COLLIDE, typename T>
-__device__ __forceinline__ bool update_site(Pop<T> &p, const MatT<T> &m, double *f3, double *w) {
+__device__ __forceinline__ bool update_site(Pop<T> &p, const MatT<T> &m, unsigned rthr, double *f3, double *w) {
     bool bad;
     if constexpr (POL == POL_TM) {
         T E3, Hx, Hy, D;
         moments(p, m, &E3, &Hx, &Hy, &D);
-        bad = field_runaway(E3);
+        bad = field_runaway(E3, rthr);
         if (f3) {
             f3[0] = (double)(D * m.inv_eps);
             f3[1] = (double)Hx;
@@ -340,7 +347,7 @@ __device__ __forceinline__ bool update_site(Pop<T> &p, const MatT<T> &m, double 
     } else {
         T Ey3, Ex3, Hz, Dy, Dx;
         moments_te(p, m, &Ey3, &Ex3, &Hz, &Dy, &Dx);
-        bad = field_runaway(Ey3) || field_runaway(Ex3);
+        bad = field_runaway(Ey3, rthr) || field_runaway(Ex3, rthr);
         if (f3) {
             f3[0] = (double)Hz;
             f3[1] = (double)(Dx * m.inv_eps);

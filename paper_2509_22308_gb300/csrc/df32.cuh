@@ -62,9 +62,10 @@ __device__ __forceinline__ df &operator+=(df &a, df b) { return a = a + b; }
 // a * b + c as a product and a sum (no fused double-word form is used)
 __device__ __forceinline__ df fmat(df a, df b, df c) { return a * b + c; }
 
-// |E/3| >= 2^20 or non-finite: the leading word decides
-__device__ __forceinline__ bool field_runaway(df e3) {
-    return (__float_as_uint(e3.hi) & 0x7f800000u) >= ((127u + 20u) << 23);
+// The runaway test of common.cuh (exponent field >= thr, the FP32 threshold): the leading
+// word decides
+__device__ __forceinline__ bool field_runaway(df e3, unsigned thr) {
+    return (__float_as_uint(e3.hi) & 0x7f800000u) >= thr;
 }
 
 }  // namespace lbmem

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(BX *BY) k_energy(const StepArgs<T> a, const T 
     if (x < a.nx && y < a.ny) {
         Pop<T> p;
         pull_site(a, f, x, y, *t_dev, p);
-        update_site<POL, false>(p, a.mtab[a.mat[(size_t)y * a.pitch + x]], nullptr, &w);
+        update_site<POL, false>(p, a.mtab[a.mat[(size_t)y * a.pitch + x]], a.runaway, nullptr, &w);
     }
     w = block_sum(w);
     if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(energy, w);

@@ -8,11 +8,14 @@
 //
 // The array is a file-scope __device__ variable: every GPU that loads the library
 // holds its 4 MiB until the process exits.  Host code cannot use the variable's name
-// as a device address (on the host it is only a stand-in symbol), so the first call on
-// each device looks the device address up with cudaGetSymbolAddress while that device
-// is current, caches it, and passes it to the kernel.
+// as a device address (on the host it is only a stand-in symbol), so each call looks
+// the device address up with cudaGetSymbolAddress while the caller's device is current
+// and passes it to the kernel.  The lookup is a host-side table query (no allocation,
+// no device work); doing it on every call instead of caching it per device keeps the
+// address right when the caller has reset the device (cudaDeviceReset) or otherwise
+// recreated its primary context, after which the module, and the array with it, can
+// sit at a different address.
 #include <cmath>
-#include <mutex>
 
 #include "../../include/lbm_em.h"
 #include "common.cuh"
@@ -25,21 +28,12 @@ namespace {
 
 static __device__ __align__(256) uint8_t g_raster_scratch[LBM_EM_NOALLOC_RASTER_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_raster_scratch on the current device (looked up once per device).
-lbm_em_status scratch_address(int dev, void **out) {
-    if (dev < 0 || dev >= kMaxDevices) return set_error(LBM_EM_EINVAL, "device index beyond 63");
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_raster_scratch);
-        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(no-allocation scratch)");
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+// Device address of g_raster_scratch in the current context.
+lbm_em_status scratch_address(void **out) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_raster_scratch);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(no-allocation scratch)");
+    *out = p;
     return LBM_EM_OK;
 }
 
@@ -59,11 +53,8 @@ extern "C" lbm_em_status lbm_em_rasterize_janus_noalloc(const lbm_em_janus *j, i
         cudaGetLastError();
         return set_error(LBM_EM_ECUDA, "no CUDA device available (the solver has no CPU path)");
     }
-    int dev = 0;
-    st = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
-    if (st) return st;
     void *scratch = nullptr;
-    st = scratch_address(dev, &scratch);
+    st = scratch_address(&scratch);
     if (st) return st;
     double cx, cy;
     janus_center(j, nx, ny, &cx, &cy);

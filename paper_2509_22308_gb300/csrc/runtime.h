@@ -1,7 +1,9 @@
 // Host-side helpers shared by the single-domain and the batched runtimes.
 #pragma once
 
+#include <cmath>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/lbm_em.h"
@@ -38,6 +40,51 @@ inline MatT<df> material_entry<df>(double eps, bool pec) {
     if (pec) return MatT<df>{df(0.0), df(0.0), df(0.0), df(1.0)};
     return MatT<df>{df(1.0 / (3.0 * eps)), df(6.0 * eps - 4.0), df(1.0 / eps), df(3.0 * eps)};
 }
+
+// Power-of-two scale of an amplitude: k with 2^k <= |E0| < 2^(k + 1), 0 for E0 = 0, clamped
+// to [-100, 100].  Every field and force of the (linear) scheme scales with E0, so the
+// reduced-precision forms and the runaway test use thresholds relative to 2^k.
+inline int amplitude_exponent(double E0) {
+    if (!(E0 != 0.0) || !std::isfinite(E0)) return 0;
+    int e = 0;
+    std::frexp(E0, &e);  // |E0| = m 2^e, 0.5 <= m < 1
+    const int k = e - 1;
+    return k < -100 ? -100 : k > 100 ? 100 : k;
+}
+
+// Threshold on the exponent field of the runaway test (field_runaway): |E/3| >= 2^(20 + k)
+// for the amplitude exponent k; FP32 (and the leading word of double-float) in bits 23-30,
+// FP64 in bits 20-30 of the high word.
+template <typename T>
+inline unsigned runaway_bits(double E0) {
+    const int k = amplitude_exponent(E0);
+    if constexpr (sizeof(T) == 8 && !std::is_same<T, df>::value)
+        return (unsigned)(1023 + 20 + k) << 20;
+    else
+        return (unsigned)(127 + 20 + k) << 23;
+}
+
+// Scale of the FP16 deviations, 2^(10 - k): with E0 = 1 deviations up to ~64 stay below the FP16
+// maximum after scaling and down to ~6e-8 stay normal, and the same holds relative to any E0.
+inline float f16_scale(double E0) { return std::ldexp(1.0f, 10 - amplitude_exponent(E0)); }
+
+// Allocation of device memory (cudaMalloc / stream-ordered cudaMallocAsync) and its release,
+// through the library's fault-injection hook and count (alloc.cu, lbm_em_test_alloc_hook).
+cudaError_t dmalloc(void **p, size_t bytes);
+cudaError_t dmalloc_async(void **p, size_t bytes, cudaStream_t s);
+void dfree(void *p);                     // NULL is ignored
+void dfree_async(void *p, cudaStream_t s);
+template <typename P>
+inline cudaError_t dmalloc(P **p, size_t bytes) { return dmalloc(reinterpret_cast<void **>(p), bytes); }
+// cudaMemcpyAsync / cudaMemcpy2DAsync (same arguments) that also count the bytes moved per
+// direction (lbm_em_transfer_bytes).
+cudaError_t copy_async(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s);
+cudaError_t copy2d_async(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width, size_t height,
+                         cudaMemcpyKind kind, cudaStream_t s);
+// One allocation attempt of any kind: true if the armed hook fails it.  alloc_held counts a
+// buffer or pinned block taken (+1) or given back (-1) by a handle or batch.
+bool alloc_should_fail();
+void alloc_held(long long delta);
 
 lbm_em_status check_source(const lbm_em_source *s);
 lbm_em_status check_janus(const lbm_em_janus *j);

@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(BX *BY) k_step(const StepArgs<T> a, const T *_
     const MatT<T> m = a.mtab[a.mat[idx]];
     const bool acc = ACC && y >= a.accp.y0 && y <= a.accp.y1 && a.accp.slot[idx] >= 0;
     double f3[3];
-    if (update_site<POL, true>(p, m, acc ? f3 : nullptr, nullptr)) atomicOr(a.err, 1u);
+    if (update_site<POL, true>(p, m, a.runaway, acc ? f3 : nullptr, nullptr)) atomicOr(a.err, 1u);
     if (acc) {
         const double2 c = a.src.cs[(int)(t % (long long)a.src.period)];
         double *q = a.accp.acc + 6 * (size_t)a.accp.slot[idx];
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(BX *BY) k_fields(const StepArgs<T> a, const T 
     pull_site(a, f, x, y, *t_dev, p);
     const size_t idx = (size_t)y * a.pitch + x;
     double f3[3];
-    update_site<POL, false>(p, a.mtab[a.mat[idx]], f3, nullptr);
+    update_site<POL, false>(p, a.mtab[a.mat[idx]], a.runaway, f3, nullptr);
     const size_t o = (size_t)y * a.nx + x;
     o0[o] = f3[0];
     o1[o] = f3[1];

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(NT) k_step2(const StepArgs<T> a, const T *__re
         const size_t idx = (size_t)y * a.pitch + x;
         const bool acc = ACC && lx >= 1 && lx <= TW && ly >= 1 && ly <= TH;
         double f3[3];
-        if (update_site<POL, true>(p, a.mtab[a.mat[idx]], acc ? f3 : nullptr, nullptr)) atomicOr(a.err, 1u);
+        if (update_site<POL, true>(p, a.mtab[a.mat[idx]], a.runaway, acc ? f3 : nullptr, nullptr)) atomicOr(a.err, 1u);
         if (acc) acc_site(a.accp, a.src, idx, y, t, f3[0], f3[1], f3[2]);
         put_smem(sm, ly, lx, p);
     }
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(NT) k_step2(const StepArgs<T> a, const T *__re
         if (x == 0 && src1) inject_source(a.src.kind, sp.g1, sp.inc1, p);
         const size_t idx = (size_t)y * a.pitch + x;
         double f3[3];
-        if (update_site<POL, true>(p, a.mtab[a.mat[idx]], ACC ? f3 : nullptr, nullptr)) atomicOr(a.err, 1u);
+        if (update_site<POL, true>(p, a.mtab[a.mat[idx]], a.runaway, ACC ? f3 : nullptr, nullptr)) atomicOr(a.err, 1u);
         if (ACC) acc_site(a.accp, a.src, idx, y, t + 1, f3[0], f3[1], f3[2]);
         store_site(fout, a.pstride, idx, p);
     }

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(NTH, 3)
             const uint8_t id = sids[(ly + 1) * MW + lx + ioff];
             float E3, Hx, Hy, D;
             moments(p, table[id], &E3, &Hx, &Hy, &D);
-            if (field_runaway(E3)) atomicOr(a.err, kErrUnstable);
+            if (field_runaway(E3, a.runaway)) atomicOr(a.err, kErrUnstable);
             if (ACC && lx >= 1 && lx <= KW && ly >= 1 && ly <= KH)
                 acc_site(a.accp, a.src, (size_t)y * a.pitch + x, y, t, 3.0 * (double)E3, (double)Hx, (double)Hy);
             const Fld F = stored_fields(E3, Hx, Hy);
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(NTH, 3)
             const size_t idx = (size_t)y * a.pitch + x;
             float E3, Hx, Hy, D;
             moments(p, table[inter_ids[(ly + 1) * IW + lx + 1]], &E3, &Hx, &Hy, &D);
-            if (field_runaway(E3)) atomicOr(a.err, kErrUnstable);
+            if (field_runaway(E3, a.runaway)) atomicOr(a.err, kErrUnstable);
             if (ACC) acc_site(a.accp, a.src, idx, y, t + 1, 3.0 * (double)E3, (double)Hx, (double)Hy);
             const Fld F = stored_fields(E3, Hx, Hy);
             __half g[NPLANES];

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(NTH, 3)
             const uint8_t id = S.ids[(ly + 1) * MW + lx + ioff];
             const bool acc = ACC && lx >= 1 && lx <= KW && ly >= 1 && ly <= KH;
             double f3[3];
-            if (update_site<POL, true>(p, S.table[id], acc ? f3 : nullptr, nullptr)) atomicOr(a.err, kErrUnstable);
+            if (update_site<POL, true>(p, S.table[id], a.runaway, acc ? f3 : nullptr, nullptr)) atomicOr(a.err, kErrUnstable);
             if (acc) acc_site(a.accp, a.src, (size_t)y * a.pitch + x, y, t, f3[0], f3[1], f3[2]);
             put_inter<G>(S.inter, ly, lx, p);
             S.inter_ids[ly * IW + lx] = id;
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(NTH, 3)
             if (x == 0 && src1) inject_source_t(a.src.kind, sp.g1, sp.inc1, p);
             const size_t idx = (size_t)y * a.pitch + x;
             double f3[3];
-            if (update_site<POL, true>(p, S.table[S.inter_ids[(ly + 1) * IW + lx + 1]], ACC ? f3 : nullptr, nullptr))
+            if (update_site<POL, true>(p, S.table[S.inter_ids[(ly + 1) * IW + lx + 1]], a.runaway, ACC ? f3 : nullptr, nullptr))
                 atomicOr(a.err, kErrUnstable);
             if (ACC) acc_site(a.accp, a.src, idx, y, t + 1, f3[0], f3[1], f3[2]);
             store_site(fout, a.pstride, idx, p);

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(NTH, 3)
             const uint8_t id = ids[(ly + 1) * MW + lx + ioff];
             const bool acc = ACC && lx >= 2 && lx < KW + 2 && ly >= 2 && ly < KH + 2;
             double f3[3];
-            if (update_site<POL, true>(p, table[id], acc ? f3 : nullptr, nullptr)) atomicOr(a.err, kErrUnstable);
+            if (update_site<POL, true>(p, table[id], a.runaway, acc ? f3 : nullptr, nullptr)) atomicOr(a.err, kErrUnstable);
             if (acc) acc_site(a.accp, a.src, (size_t)y * a.pitch + x, y, t, f3[0], f3[1], f3[2]);
             put_buf<AW, AH>(bufa, ly, lx, p);
             ids_a[ly * AW + lx] = id;
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(NTH, 3)
             const uint8_t id = ids_a[(ly + 1) * AW + lx + 1];
             const bool acc = ACC && lx >= 1 && lx <= KW && ly >= 1 && ly <= KH;
             double f3[3];
-            if (update_site<POL, true>(p, table[id], acc ? f3 : nullptr, nullptr)) atomicOr(a.err, kErrUnstable);
+            if (update_site<POL, true>(p, table[id], a.runaway, acc ? f3 : nullptr, nullptr)) atomicOr(a.err, kErrUnstable);
             if (acc) acc_site(a.accp, a.src, (size_t)y * a.pitch + x, y, t + 1, f3[0], f3[1], f3[2]);
             put_buf<BW, BH>(bufb, ly, lx, p);
             ids_b[ly * BW + lx] = id;
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(NTH, 3)
             if (x == 0 && src12) inject_source_t(a.src.kind, sp.g[2], sp.inc[2], p);
             const size_t idx = (size_t)y * a.pitch + x;
             double f3[3];
-            if (update_site<POL, true>(p, table[ids_b[(ly + 1) * BW + lx + 1]], ACC ? f3 : nullptr, nullptr))
+            if (update_site<POL, true>(p, table[ids_b[(ly + 1) * BW + lx + 1]], a.runaway, ACC ? f3 : nullptr, nullptr))
                 atomicOr(a.err, kErrUnstable);
             if (ACC) acc_site(a.accp, a.src, idx, y, t + 2, f3[0], f3[1], f3[2]);
             store_site(fout, a.pstride, idx, p);

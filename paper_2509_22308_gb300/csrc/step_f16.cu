@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(BX *BY) k_step_f16(const F16Args a, const long
     float E30, Hx0, Hy0, D0, E31, Hx1, Hy1, D1;
     moments(p0, m0, &E30, &Hx0, &Hy0, &D0);
     moments(p1, m1, &E31, &Hx1, &Hy1, &D1);
-    if (field_runaway(E30) || (has1 && field_runaway(E31))) atomicOr(a.err, 1u);
+    if (field_runaway(E30, a.runaway) || (has1 && field_runaway(E31, a.runaway))) atomicOr(a.err, 1u);
     const size_t idx = r + x0;
     if (ACC) {
         accumulate_site(a, idx, y, t, 3.0 * (double)E30, Hx0, Hy0);

@@ -17,10 +17,6 @@
 
 namespace lbmem {
 
-// Deviation scale 2^10: |g| up to ~64 E0 stays below the FP16 maximum, and
-// deviations down to ~6e-8 / 2^10 stay normal.
-constexpr float kF16Scale = 1024.0f;
-
 struct F16Args {
     int nx, ny, pitch, pad;
     size_t pstride;
@@ -29,7 +25,8 @@ struct F16Args {
     SourceParams src;
     AccParams accp;
     unsigned *err;
-    float scale, inv_scale;
+    unsigned runaway;             // FP32 runaway threshold (runaway_bits<float>)
+    float scale, inv_scale;       // deviation scale 2^(10 - k) (f16_scale) and its inverse
     const __half *g;              // 11 deviation planes (input)
     const float *fe, *fhx, *fhy;  // field planes (input)
     __half *g_out;

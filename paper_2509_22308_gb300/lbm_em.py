@@ -94,6 +94,9 @@ SIGNATURES = {
     "lbm_em_rasterize_janus": [_P(Janus), ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_uint8)],
     "lbm_em_rasterize_janus_noalloc": [_P(Janus), ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_uint8)],
     "lbm_em_probe_bounded_wait": [ctypes.c_int64],
+    "lbm_em_test_alloc_hook": [ctypes.c_int64, _P(ctypes.c_int64)],
+    "lbm_em_probe_fp64_fma": [_vp, ctypes.c_int64, _P(ctypes.c_double)],
+    "lbm_em_transfer_bytes": [_P(ctypes.c_uint64), _P(ctypes.c_uint64)],
     "lbm_em_batch_create": [_P(Instance), ctypes.c_int32, _P(BatchOpts), _P(_vp)],
     "lbm_em_batch_run": [_vp],
     "lbm_em_batch_results": [_vp, _P(ctypes.c_double), _P(ctypes.c_int32)],
@@ -298,6 +301,30 @@ class Solver:
         _call("lbm_em_load_state", self.h, ctypes.cast(buf, ctypes.c_void_p), ctypes.c_size_t(len(data)))
 
 
+def probe_fp64_fma(stream, iters) -> float:
+    """Enqueue one launch of the library's FP64 FMA-chain probe on ``stream`` (a torch stream
+    or a raw cudaStream_t); returns the number of FMAs the launch performs."""
+    n = ctypes.c_double()
+    _call("lbm_em_probe_fp64_fma", _stream_ptr(stream), ctypes.c_int64(int(iters)), ctypes.byref(n))
+    return n.value
+
+
+def transfer_bytes():
+    """(host -> device, device -> host) bytes the library has copied since it was loaded."""
+    h, d = ctypes.c_uint64(), ctypes.c_uint64()
+    _call("lbm_em_transfer_bytes", ctypes.byref(h), ctypes.byref(d))
+    return h.value, d.value
+
+
+def alloc_fault_hook(fail_at=0) -> int:
+    """Arm (fail_at > 0: the fail_at-th device or pinned allocation from now on fails with
+    ENOMEM) or disarm (0) the library's allocation fault injection; returns the number of
+    allocations the library's handles and batches currently hold."""
+    live = ctypes.c_int64()
+    _call("lbm_em_test_alloc_hook", ctypes.c_int64(int(fail_at)), ctypes.byref(live))
+    return live.value
+
+
 def rasterize_janus(j: Janus, nx, ny):
     out = np.zeros((ny, nx), dtype=np.uint8)
     _call("lbm_em_rasterize_janus", ctypes.byref(j), int(nx), int(ny), _u8ptr(out))
@@ -313,9 +340,10 @@ def rasterize_janus_noalloc(j: Janus, nx, ny):
 
 def solver_for_instance(inst: dict, precision="f64", stream=None, kind=SRC_HARD, steps_per_launch="auto",
                         polarization="tm") -> Solver:
-    """Solver for one workload instance dictionary (see ``workloads``)."""
+    """Solver for one workload instance dictionary (see ``workloads``; an optional "E0" key
+    sets the incident amplitude, 1 by default)."""
     j = make_janus(inst["a"], inst["phi0"], inst["eps1"], inst["eps2"], inst["pec2"])
-    s = make_source(inst["period"], inst.get("ramp"), kind)
+    s = make_source(inst["period"], inst.get("ramp"), kind, E0=inst.get("E0", 1.0))
     return Solver(inst["nx"], inst["ny"], precision, janus=j, source=s, stream=stream,
                   steps_per_launch=steps_per_launch, polarization=polarization)
 
@@ -339,7 +367,8 @@ class Batch:
         arr = (Instance * n)()
         for i, inst in enumerate(instances):
             arr[i] = Instance(int(inst["nx"]), int(inst["ny"]), int(inst["period"]), int(inst["periods"]),
-                              int(inst.get("ramp", inst["period"])), int(inst.get("n_points", 0)), 1.0,
+                              int(inst.get("ramp", inst["period"])), int(inst.get("n_points", 0)),
+                              float(inst.get("E0", 1.0)),
                               float(inst["R"]),
                               make_janus(inst["a"], inst["phi0"], inst["eps1"], inst["eps2"], inst["pec2"]))
         o = BatchOpts(PRECISIONS.get(precision, precision), int(tile_w), int(tile_h), int(ctas_per_sm),

@@ -144,12 +144,13 @@ def test_batch_reports_unstable_instance():
     b = L.Batch(insts, "f32")
     b._L.lbm_em_batch_destroy(b.b)
     b.b = None
-    # a runaway instance is flagged on its own
+    # an instance whose drive the FP32 form cannot represent (E0 = 1e39: non-finite fields) is
+    # flagged on its own
     import ctypes
     arr = (L.Instance * 2)()
     for i, inst in enumerate(insts):
         arr[i] = L.Instance(inst["nx"], inst["ny"], inst["period"], inst["periods"], inst["ramp"], 0,
-                            1e9 if i == 1 else 1.0, inst["R"],
+                            1e39 if i == 1 else 1.0, inst["R"],
                             L.make_janus(inst["a"], inst["phi0"], inst["eps1"], inst["eps2"], inst["pec2"]))
     o = L.BatchOpts(L.F32, 64, 4, 2, 0, 0, 0.0, None)
     h = ctypes.c_void_p()

@@ -164,10 +164,12 @@ def test_checkpoint_resume_is_bit_exact():
 
 
 def test_runaway_field_is_reported():
-    """A source amplitude far beyond the runaway threshold sets the sticky error word;
-    sync reports EUNSTABLE and the context stays usable."""
+    """A drive the FP32 form cannot represent (E0 = 1e39, beyond the FP32 range) makes the
+    fields non-finite and sets the sticky error word; sync reports EUNSTABLE and the context
+    stays usable.  (The threshold for finite fields is relative to E0:
+    test_gpu_amplitude.py.)"""
     j = L.make_janus(6, 0.3, 2.0)
-    with L.Solver(48, 40, "f32", janus=j, source=L.make_source(24, 0, E0=1e9)) as s:
+    with L.Solver(48, 40, "f32", janus=j, source=L.make_source(24, 0, E0=1e39)) as s:
         s.step(40)
         with pytest.raises(L.LbmEmError) as e:
             s.sync()
