@@ -78,15 +78,22 @@ typedef enum {
 } lbm_em_source_kind;
 
 /* lbm_em_grid.flags: how many time steps one kernel launch advances.  By default FP64 and
- * double-float advance one step per launch, FP16-deviation two, FP32 two below 2^25 sites and
- * three from there on (each tile and its halo are copied to shared memory by the TMA unit
- * and advance two or three steps there; three move fewer HBM bytes per step but do more halo
- * work, and pay on the largest lattices).  The flags force a mode.  The result does not
- * depend on the choice: every mode gives the same bits.  Invalid combinations return
- * LBM_EM_EINVAL. */
+ * double-float advance one step per launch; FP32 and FP16-deviation two below 2^21 sites (each
+ * tile and its halo are copied to shared memory by the TMA unit and advance two steps there)
+ * and four from 2^21 sites on (each warp streams a strip of the lattice through four time
+ * levels held in registers).  The flags force a mode.  In FP32, FP64 and double-float the
+ * result does not depend on the choice: every mode gives the same bits.  In FP16-deviation the
+ * four-step mode rounds the stored state to FP16 once per launch instead of once per step, so
+ * its bits differ from the other modes by FP16 rounding noise (its runs still give the same
+ * bits however they are split, as long as the splits fall on multiples of four steps).
+ * Invalid combinations return LBM_EM_EINVAL. */
 #define LBM_EM_FLAG_SINGLE_STEP 1  /* always one step per launch                          */
 #define LBM_EM_FLAG_TWO_STEP 2     /* two steps per launch for FP32, FP16-dev, double-float */
 #define LBM_EM_FLAG_THREE_STEP 8   /* three steps per launch (FP32 only; 28 x 12 tiles)      */
+/* four steps per launch (FP32 and FP16-dev): each warp streams a 64-column strip down the
+ * lattice and keeps four time levels in registers; FP32 gives the same bits, FP16-dev rounds
+ * its stored state once per launch instead of once per step (closer to FP32, other bits) */
+#define LBM_EM_FLAG_FOUR_STEP 16
 /* TE^z polarization (H_z, E_x, E_y), which the paper leaves for future work (Sec. I): the
  * same scheme and storage (11 planes), incident wave E_y = H_z = E0 sin(w t - k x).  Every
  * call that reports the TM triple (E_z, H_x, H_y) reports (H_z, E_x, E_y) instead: fields,
@@ -97,8 +104,8 @@ typedef enum {
 typedef struct {
     int32_t nx, ny;       /* lattice size, each >= 4                                      */
     int32_t precision;    /* lbm_em_precision                                             */
-    int32_t flags;        /* 0, LBM_EM_FLAG_SINGLE_STEP, LBM_EM_FLAG_TWO_STEP or
-                             LBM_EM_FLAG_THREE_STEP, optionally | LBM_EM_FLAG_TE          */
+    int32_t flags;        /* 0 or one of LBM_EM_FLAG_SINGLE_STEP, _TWO_STEP, _THREE_STEP,
+                             _FOUR_STEP, optionally | LBM_EM_FLAG_TE                      */
     void *stream;         /* cudaStream_t every kernel of the handle runs on; NULL: the
                              library creates a private non-blocking stream                */
 } lbm_em_grid;
@@ -175,6 +182,12 @@ lbm_em_status lbm_em_step(lbm_em_t *h, int64_t n);
  * flight when its thread block left, so the handle's state is undefined: lbm_em_step and
  * lbm_em_accumulate then return LBM_EM_ESTATE, and the handle must be destroyed. */
 lbm_em_status lbm_em_sync(lbm_em_t *h);
+
+/* Time steps one launch of the handle's step kernel advances (1, 2, 3 or 4), the mode that
+ * lbm_em_grid.flags forced or the default chose for the form and lattice size.  Runs of fewer
+ * steps, and the steps that bring an odd start time to an even one for two-step launches,
+ * take single-step launches. */
+lbm_em_status lbm_em_get_steps_per_launch(lbm_em_t *h, int32_t *n);
 
 /* Current time step count (host view; equals the number of steps enqueued). */
 lbm_em_status lbm_em_get_time(lbm_em_t *h, int64_t *t);

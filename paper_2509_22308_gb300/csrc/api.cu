@@ -20,6 +20,7 @@
 #include "step2.cuh"
 #include "step2_tma.h"
 #include "step_f16.cuh"
+#include "step_stream.h"
 
 using namespace lbmem;
 
@@ -229,6 +230,11 @@ struct lbm_em {
     CUtensorMap f16_gmap[2], f16_fmap[2];  // FP16-deviation form: deviation and field planes per buffer
     CUtensorMap tmap3[2], idmap3;          // FP32, three steps per launch
     bool t3 = false;                       // three steps per launch (FP32)
+    // four steps per launch (FP32, FP16-deviation): row-streaming kernel, its maps per buffer
+    // (FP32 state or FP16 deviations; FP16 fields) and of the ids, and its work plan
+    bool s4 = false;
+    CUtensorMap s4_smap[2], s4_fmap[2], s4_imap;
+    StreamPlan s4_plan{};
     int tma3_ctas = 0;
     int tma_ctas = 0;
     // contour and accumulators
@@ -268,12 +274,14 @@ static void dev_free(lbm_em *h, P *&p) {
 static cudaError_t upload_staging(lbm_em *h, size_t bytes, void **p) {
     cudaError_t e = cudaEventSynchronize(h->up_ev);
     if (e != cudaSuccess) return e;
-    if (h->up_cap < bytes) {
-        pinned_put(h->h_up, h->up_cap);
-        h->h_up = nullptr;
-        h->up_cap = 0;
-        e = pinned_get(bytes, &h->h_up, &h->up_cap);
+    if (h->up_cap < bytes) {  // the larger block first: a failed grow keeps the old one
+        void *np = nullptr;
+        size_t ncap = 0;
+        e = pinned_get(bytes, &np, &ncap);
         if (e != cudaSuccess) return e;
+        pinned_put(h->h_up, h->up_cap);
+        h->h_up = np;
+        h->up_cap = ncap;
     }
     *p = h->h_up;
     return cudaSuccess;
@@ -363,10 +371,39 @@ static cudaError_t enqueue_step3(lbm_em *h, bool acc, cudaStream_t s, int p) {
                             h->d_time + (1 - p), acc, h->tma3_ctas, s);
 }
 
-// Steps per captured graph: kGraphSteps, or 30 (ten launches) with three steps per launch.
-static int graph_steps(const lbm_em *h) { return h->t3 ? 30 : kGraphSteps; }
+// Four steps in one launch (FP32, FP16-deviation; no accumulation): buf[p] -> buf[1 - p].
+static cudaError_t enqueue_step4(lbm_em *h, cudaStream_t s, int p) {
+    if (h->prec == LBM_EM_F16DEV) {
+        const F16Args fa = make_f16_args(h, p);
+        return launch_step4_stream(make_args<float>(h), &fa, &h->s4_smap[p], &h->s4_fmap[p], &h->s4_imap, nullptr,
+                                   h->s4_plan, h->d_time + p, h->d_time + (1 - p), s);
+    }
+    return launch_step4_stream(make_args<float>(h), nullptr, &h->s4_smap[p], &h->s4_fmap[p], &h->s4_imap,
+                               (float *)h->buf[1 - p], h->s4_plan, h->d_time + p, h->d_time + (1 - p), s);
+}
 
-// graph_steps(h) steps starting from buffer 0 (an even number of launches, so the
+// Steps one launch advances: plain steps use the handle's mode; accumulating steps (the
+// Fourier period) use the two-step tile kernel where the four-step one is chosen.
+static int launch_steps(const lbm_em *h, bool acc) {
+    if (h->s4) return acc ? 2 : 4;
+    return h->t3 ? 3 : h->tb ? 2 : 1;
+}
+
+// Steps per captured graph: kGraphSteps (8, 16 or 32 launches), or 30 (ten launches) with
+// three steps per launch.
+static int graph_steps(const lbm_em *h, bool acc) { return launch_steps(h, acc) == 3 ? 30 : kGraphSteps; }
+
+// One launch of `m` steps from buffer p.
+static cudaError_t enqueue_mode(lbm_em *h, int m, bool acc, cudaStream_t s, int p) {
+    switch (m) {
+        case 4: return enqueue_step4(h, s, p);
+        case 3: return enqueue_step3(h, acc, s, p);
+        case 2: return enqueue_step2(h, acc, s, p);
+        default: return enqueue_step(h, acc, s, p);
+    }
+}
+
+// graph_steps(h, acc) steps starting from buffer 0 (an even number of launches, so the
 // state is back in buffer 0 at the end).
 static lbm_em_status build_graph(lbm_em *h, bool acc, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
@@ -374,11 +411,8 @@ static lbm_em_status build_graph(lbm_em *h, bool acc, cudaGraphExec_t *out) {
                                    "cudaStreamBeginCapture");
     if (st) return st;
     cudaError_t e = cudaSuccess;
-    const int launches = h->t3 ? graph_steps(h) / 3 : h->tb ? kGraphSteps / 2 : kGraphSteps;
-    for (int i = 0; i < launches && e == cudaSuccess; ++i)
-        e = h->t3   ? enqueue_step3(h, acc, h->cap, i & 1)
-            : h->tb ? enqueue_step2(h, acc, h->cap, i & 1)
-                    : enqueue_step(h, acc, h->cap, i & 1);
+    const int m = launch_steps(h, acc), launches = graph_steps(h, acc) / m;
+    for (int i = 0; i < launches && e == cudaSuccess; ++i) e = enqueue_mode(h, m, acc, h->cap, i & 1);
     cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -389,13 +423,15 @@ static lbm_em_status build_graph(lbm_em *h, bool acc, cudaGraphExec_t *out) {
     return cuda_status(e, "cudaGraphInstantiate");
 }
 
-// Every mode gives the same bits; two-step launches and their graphs start at even t (an
-// odd start takes one single step first), three-step launches anywhere, and a remainder
-// shorter than a launch's steps takes single steps.
+// Every FP32 mode gives the same bits (the four-step FP16-deviation launch rounds its stored
+// state once per launch, see step_stream.cu); two-step launches and their graphs start at
+// even t (an odd start takes one single step first), three- and four-step launches anywhere,
+// and a remainder shorter than a launch's steps takes single steps.
 static lbm_em_status run_steps(lbm_em *h, int64_t n, bool acc) {
+    const int m = launch_steps(h, acc), gs = graph_steps(h, acc);
     while (n > 0) {
         const bool even = (h->t & 1) == 0;
-        if (h->cur == 0 && n >= graph_steps(h) && (even || !h->tb || h->t3)) {
+        if (h->cur == 0 && n >= gs && (even || m != 2)) {
             cudaGraphExec_t *g = acc ? &h->g_acc : &h->g_plain;
             if (!*g) {
                 lbm_em_status st = build_graph(h, acc, g);
@@ -403,20 +439,14 @@ static lbm_em_status run_steps(lbm_em *h, int64_t n, bool acc) {
             }
             lbm_em_status st = cuda_status(cudaGraphLaunch(*g, h->stream), "cudaGraphLaunch");
             if (st) return st;
-            h->t += graph_steps(h);
-            n -= graph_steps(h);
-        } else if (h->t3 && n >= 3) {
-            lbm_em_status st = cuda_status(enqueue_step3(h, acc, h->stream, h->cur), "step launch");
+            h->t += gs;
+            n -= gs;
+        } else if (m > 1 && n >= m && (even || m != 2)) {
+            lbm_em_status st = cuda_status(enqueue_mode(h, m, acc, h->stream, h->cur), "step launch");
             if (st) return st;
             h->cur ^= 1;
-            h->t += 3;
-            n -= 3;
-        } else if (h->tb && !h->t3 && n >= 2 && even) {
-            lbm_em_status st = cuda_status(enqueue_step2(h, acc, h->stream, h->cur), "step launch");
-            if (st) return st;
-            h->cur ^= 1;
-            h->t += 2;
-            n -= 2;
+            h->t += m;
+            n -= m;
         } else {
             lbm_em_status st = cuda_status(enqueue_step(h, acc, h->stream, h->cur), "step launch");
             if (st) return st;
@@ -478,8 +508,14 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     if (!g || !out) return set_error(LBM_EM_EINVAL, "grid/out is NULL");
     *out = nullptr;
     if (g->nx < 4 || g->ny < 4) return set_error(LBM_EM_EINVAL, "nx and ny must be >= 4");
-    if (g->flags & ~(LBM_EM_FLAG_SINGLE_STEP | LBM_EM_FLAG_TWO_STEP | LBM_EM_FLAG_TE | LBM_EM_FLAG_THREE_STEP))
+    if (g->flags & ~(LBM_EM_FLAG_SINGLE_STEP | LBM_EM_FLAG_TWO_STEP | LBM_EM_FLAG_TE | LBM_EM_FLAG_THREE_STEP |
+                     LBM_EM_FLAG_FOUR_STEP))
         return set_error(LBM_EM_EINVAL, "unknown grid flags");
+    const int step_flags = g->flags & (LBM_EM_FLAG_SINGLE_STEP | LBM_EM_FLAG_TWO_STEP | LBM_EM_FLAG_THREE_STEP |
+                                       LBM_EM_FLAG_FOUR_STEP);
+    if (step_flags & (step_flags - 1)) return set_error(LBM_EM_EINVAL, "at most one steps-per-launch flag");
+    if ((g->flags & LBM_EM_FLAG_FOUR_STEP) && g->precision != LBM_EM_F32 && g->precision != LBM_EM_F16DEV)
+        return set_error(LBM_EM_EINVAL, "LBM_EM_FLAG_FOUR_STEP is for LBM_EM_F32 and LBM_EM_F16DEV");
     if ((g->flags & LBM_EM_FLAG_THREE_STEP) &&
         (g->precision != LBM_EM_F32 || (g->flags & (LBM_EM_FLAG_SINGLE_STEP | LBM_EM_FLAG_TWO_STEP))))
         return set_error(LBM_EM_EINVAL, "LBM_EM_FLAG_THREE_STEP is for LBM_EM_F32 alone, without the other step flags");
@@ -518,13 +554,23 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
         h->tb = g->precision != LBM_EM_F64;
     else
         h->tb = (g->precision == LBM_EM_F32 || g->precision == LBM_EM_F16DEV) && !(g->flags & LBM_EM_FLAG_SINGLE_STEP);
-    // three steps per launch: forced by the flag, else the FP32 default from 2^25 sites on
-    // (measured on GB300, GLUPS three / two: 8192^2 144.2 / 138.0, 4096^2 140.2 / 139.3, 2048^2
-    // 130.5 / 129.1, 1024^2 111.3 / 124.9: the three-step kernel is issue-bound, and on smaller
-    // lattices the two-step kernel gains more from the L2 holding much of the state)
-    h->t3 = (g->flags & LBM_EM_FLAG_THREE_STEP) != 0 ||
-            (g->precision == LBM_EM_F32 && !(g->flags & (LBM_EM_FLAG_SINGLE_STEP | LBM_EM_FLAG_TWO_STEP)) &&
-             (long long)g->nx * g->ny >= (1LL << 25));
+    // three steps per launch (28 x 12 tiles): forced by the flag only; the four-step kernel
+    // replaced it as the default on large lattices
+    h->t3 = (g->flags & LBM_EM_FLAG_THREE_STEP) != 0;
+    // four steps per launch (row-streaming kernel): forced by the flag, else the FP32 and
+    // FP16-deviation default from 2^21 sites on (measured on GB300, GLUPS four / two / three
+    // steps per launch, FP32: 8192^2 212.5 / 137.3 / 144.1, 4096^2 201.6 / 138.4 / 140.5, 2048^2
+    // 171.9 / 122.8 / 126.2, 1024^2 108.3 / 120.1 / 111.2, 512^2 31.9 / 67.6 / 68.7; FP16-deviation
+    // four / two: 182.8 / 115.4, 174.4 / 114.2, 151.5 / 105.6, 99.7 / 98.3, 29.0 / 58.3: on small
+    // lattices the strips cannot fill the GPU and the two-step kernel's state stays in L2); its
+    // accumulating periods run on the two-step tile kernel
+    h->s4 = (g->flags & LBM_EM_FLAG_FOUR_STEP) != 0 ||
+            ((g->precision == LBM_EM_F32 || g->precision == LBM_EM_F16DEV) && !step_flags &&
+             (long long)g->nx * g->ny >= (1LL << 21));
+    if (h->s4) {
+        h->t3 = false;
+        h->tb = true;
+    }
     for (int i = 0; i < 256; ++i) {
         h->eps_table[i] = 1.0;
         h->pec_id[i] = false;
@@ -570,6 +616,15 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
             TRY(encode_step3_maps(&h->tmap3[b], (const float *)h->buf[b], b == 0 ? &h->idmap3 : nullptr, h->d_mat,
                                   h->nx, h->ny, h->pitch, h->pstride),
                 "encoding the tensor maps of the three-step kernel");
+    }
+    if (h->s4) {
+        int warps = 0;
+        TRY(stream_prepare(h->prec == LBM_EM_F16DEV, &warps), "configuring the four-step kernel");
+        h->s4_plan = stream_plan(h->nx, h->ny, warps);
+        for (int b = 0; b < 2; ++b)
+            TRY(encode_stream_maps(&h->s4_smap[b], &h->s4_fmap[b], b == 0 ? &h->s4_imap : nullptr, h->buf[b],
+                                   h->prec == LBM_EM_F16DEV, h->d_mat, h->nx, h->ny, h->pitch, h->pstride),
+                "encoding the tensor maps of the four-step kernel");
     }
     if (h->tb && h->prec == LBM_EM_F16DEV) {
         TRY(step2_f16_tma_prepare(&h->tma_ctas), "configuring the TMA-staged two-step kernel");
@@ -788,6 +843,12 @@ lbm_em_status lbm_em_sync(lbm_em_t *h) {
         return set_error(LBM_EM_ETIMEOUT, "a bounded wait for a tile load gave up");
     }
     if (err) return set_error(LBM_EM_EUNSTABLE, "a field became non-finite or exceeded 3 * 2^20 times the source amplitude");
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_get_steps_per_launch(lbm_em_t *h, int32_t *n) {
+    if (!h || !n) return set_error(LBM_EM_EINVAL, "NULL argument");
+    *n = launch_steps(h, false);
     return LBM_EM_OK;
 }
 

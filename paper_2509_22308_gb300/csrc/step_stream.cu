@@ -1,0 +1,596 @@
+// Four time steps per launch for the FP32 and FP16-deviation forms: the fused stream-collide
+// step of arXiv 2509.22308, Sec. III (Eq. LBGK equation, Eq. equilibrium distribution
+// functions), temporally blocked in registers along a streaming row sweep.
+//
+// Work unit: one warp, a strip of 64 columns (two sites per lane) and a segment of rows.  The
+// strip's 56 inner columns are its output; the 4 columns on each side are the halo that four
+// steps consume (a site's value after k steps needs its neighbours after k - 1, so the valid
+// width shrinks by one column per side and step).  The warp walks down its rows: each row of
+// the stored state (time t - 1) arrives in shared memory through one cp.async.bulk.tensor copy
+// into a per-warp ring of row slots and goes straight into registers.  Time level k + 1 of row
+// q needs level k of rows q - 1, q and q + 1, so after row i has arrived the warp computes
+// level 1 of row i - 1, level 2 of row i - 2, level 3 of row i - 3 and level 4 of row i - 4,
+// and stores that one: a wavefront over (row, time).  Per level the registers keep the newest
+// row the next level still needs (9 of its populations) and the +y pair of the row before.
+// Neighbours along x come from the adjacent lane by warp shuffles, neighbours along y from
+// these registers.  No thread-block barrier is taken after the start: each warp waits only
+// for its own row copies (bounded waits, as in the tile kernels).
+//
+// The per-site arithmetic is the one-step kernel's (update_site), so the FP32 form gives the
+// bits of four one-step launches.  The FP16-deviation form rebuilds each stored row (fields
+// and FP16 deviations) into FP32 post-collision populations, runs levels 1-3 in FP32 and
+// stores the fields and deviations of level 4: its state is rounded to FP16 once per launch
+// instead of once per step, so it differs from one step per launch by FP16 rounding noise.
+//
+// Each state element crosses HBM once per four steps: 89 B per four FP32 updates, 69 B per
+// four FP16-deviation updates, plus the 8 halo columns of every 56 that the neighbouring
+// strips also read (served by L2 when they run at about the same time).
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
+#include "common.cuh"
+#include "step2_tma.h"
+#include "step_f16.cuh"
+#include "step_stream.h"
+#include "tma.cuh"
+
+namespace lbmem {
+
+namespace {
+
+constexpr int LW = kStreamLoadW, HALO = kStreamHalo, OUTW = kStreamOutW, NW = kStreamWarps, BT = kStreamSteps;
+constexpr int IDBOX = 80;                      // id bytes per row copy (from a 16-byte boundary)
+constexpr unsigned ROW32 = NPLANES * LW * 4;   // FP32 state row: 11 planes x 64 floats
+// FP16 deviations row: 11 planes x 72 halves from 4 columns before the strip, because a
+// copy of 2-byte elements must start on a multiple of 8 elements (16 bytes)
+constexpr int DEVW = LW + 8, DEVOFF = 4;
+constexpr unsigned ROWDEV = NPLANES * DEVW * 2;
+constexpr unsigned ROWFLD = 3 * LW * 4;        // FP32 fields row: 3 planes x 64 floats
+constexpr size_t r128(size_t b) { return (b + 127) / 128 * 128; }
+static_assert(LW == 64 && OUTW + 2 * HALO == LW && HALO % 4 == 0 && HALO >= BT,
+              "two sites per lane, a 16-byte aligned halo as wide as the steps");
+static_assert(IDBOX >= LW + 12 && IDBOX % 16 == 0, "the id box covers the strip from any 16-byte boundary");
+
+// Shared memory: the material table, then per warp RING row slots (state row, id row) and the
+// -y pairs of the last lattice row per level (the bottom edge, see below).  Level 0 (the stored
+// state) is read straight from the slots, so a row's slot stays in use until the row two further
+// on has arrived: 5 slots, 3 rows in use and 2 in flight.  The FP16-deviation form's copies
+// (deviations, then fields) fill the first 2432 bytes of the slot; on arrival each lane rebuilds
+// its two sites into FP32 populations and writes them over the slot in the FP32 row layout, so
+// from there on both forms read the same rows.
+template <bool F16>
+struct Layout {
+    static constexpr int RING = 5, KEEP = 2;
+    static constexpr size_t FLD = r128(ROWDEV);  // FP16 form: the field row, 128-byte aligned
+    static_assert(FLD + ROWFLD <= ROW32, "the FP16 copies fit under the FP32 row they are rebuilt into");
+    static constexpr size_t IDS = r128(ROW32);
+    static constexpr size_t SLOT = IDS + 128;
+    static constexpr size_t EDGE = BT * 32 * sizeof(float4);
+    static constexpr size_t WARP = RING * SLOT + EDGE;
+    static constexpr size_t TABLE = 256 * sizeof(MatT<float>);
+    static constexpr size_t SMEM = TABLE + NW * WARP + 128;  // + alignment slack
+};
+static_assert(3 * (Layout<false>::SMEM + 1024 + 256) <= 233472 && 3 * (Layout<true>::SMEM + 1024 + 256) <= 233472,
+              "three blocks per SM");
+
+struct SrcLevels {
+    float g[BT], inc[BT];
+};
+// Not inlined, called by one thread: see source_pair_f.
+static __device__ __noinline__ SrcLevels source_levels_f(const SourceParams src, long long t) {
+    SrcLevels v;
+    for (int k = 0; k < BT; ++k) v.g[k] = v.inc[k] = 0.f;
+    if (src.kind != SRC_NONE) {
+        for (int k = 0; k < BT; ++k) {
+            if (t + k < 1) continue;
+            double g, inc;
+            source_values(src, t + k, &g, &inc);
+            v.g[k] = (float)g;
+            v.inc[k] = (float)inc;
+        }
+    }
+    return v;
+}
+
+// The nine populations of a row that the next level reads at the row itself or from its x
+// neighbours, for this lane's sites A (even column, [0]) and B (odd column, [1]).  The +y
+// pair is read one row further down, the -y pair one row further up (not kept).
+struct Row9 {
+    float ez[2], epx[2], emx[2], epy[2], hxpx[2], hxmx[2], hxz[2], hypy[2], hyz[2];
+};
+
+__device__ __forceinline__ void keep_row(Row9 &r, const Pop<float> &a, const Pop<float> &b) {
+    r.ez[0] = a.ez, r.ez[1] = b.ez;
+    r.epx[0] = a.epx, r.epx[1] = b.epx;
+    r.emx[0] = a.emx, r.emx[1] = b.emx;
+    r.epy[0] = a.epy, r.epy[1] = b.epy;
+    r.hxpx[0] = a.hxpx, r.hxpx[1] = b.hxpx;
+    r.hxmx[0] = a.hxmx, r.hxmx[1] = b.hxmx;
+    r.hxz[0] = a.hxz, r.hxz[1] = b.hxz;
+    r.hypy[0] = a.hypy, r.hypy[1] = b.hypy;
+    r.hyz[0] = a.hyz, r.hyz[1] = b.hyz;
+}
+
+// f_i(q, next time) of sites A and B of this lane from the post-collision values of row q
+// (cur), the +y pair of row q - 1 (ey, hy) and the -y pair of row q + 1 (my, mh).  Along x
+// the upstream site is the adjacent one (across lanes by shuffles), or the site itself at
+// the lattice edge (the zero-gradient open edge).
+__device__ __forceinline__ void pull_row(const Row9 &cur, const float ey[2], const float hy[2], const float my[2],
+                                         const float mh[2], bool xa0, bool xa_last, bool xb_last, Pop<float> &a,
+                                         Pop<float> &b) {
+    const unsigned full = 0xffffffffu;
+    const float l_epx = __shfl_up_sync(full, cur.epx[1], 1);    // site B of the lane to the left
+    const float l_hxpx = __shfl_up_sync(full, cur.hxpx[1], 1);
+    const float r_emx = __shfl_down_sync(full, cur.emx[0], 1);  // site A of the lane to the right
+    const float r_hxmx = __shfl_down_sync(full, cur.hxmx[0], 1);
+    a.ez = cur.ez[0];
+    a.hxz = cur.hxz[0];
+    a.hyz = cur.hyz[0];
+    a.epx = xa0 ? cur.epx[0] : l_epx;
+    a.hxpx = xa0 ? cur.hxpx[0] : l_hxpx;
+    a.emx = xa_last ? cur.emx[0] : cur.emx[1];
+    a.hxmx = xa_last ? cur.hxmx[0] : cur.hxmx[1];
+    a.epy = ey[0];
+    a.hypy = hy[0];
+    a.emy = my[0];
+    a.hymy = mh[0];
+    b.ez = cur.ez[1];
+    b.hxz = cur.hxz[1];
+    b.hyz = cur.hyz[1];
+    b.epx = cur.epx[0];
+    b.hxpx = cur.hxpx[0];
+    b.emx = xb_last ? cur.emx[1] : r_emx;
+    b.hxmx = xb_last ? cur.hxmx[1] : r_hxmx;
+    b.epy = ey[1];
+    b.hypy = hy[1];
+    b.emy = my[1];
+    b.hymy = mh[1];
+}
+
+// One plane of a staged FP32 row: the lane's two sites.
+__device__ __forceinline__ float2 lds2(const float *row, int plane, int lane) {
+    return reinterpret_cast<const float2 *>(row + plane * LW)[lane];
+}
+
+template <bool F16>
+__device__ __forceinline__ void issue_row(const CUtensorMap *smap, const CUtensorMap *fmap, const CUtensorMap *imap,
+                                          int xs, int xid, int r, unsigned char *slot, uint64_t *bar) {
+    if constexpr (F16) {
+        mbar_arrive_expect_tx(bar, ROWDEV + ROWFLD + IDBOX);
+        tma_load_3d(slot, smap, xs - DEVOFF, r, 0, bar);  // xs - 4: a multiple of 8 halves
+        tma_load_3d(slot + Layout<F16>::FLD, fmap, xs, r, 0, bar);
+    } else {
+        mbar_arrive_expect_tx(bar, ROW32 + IDBOX);
+        tma_load_3d(slot, smap, xs, r, 0, bar);
+    }
+    tma_load_2d(slot + Layout<F16>::IDS, imap, xid, r, bar);
+}
+
+struct StreamArgs {
+    int nx, ny, pitch, n_strips, seg_rows, n_units;
+    size_t pstride;
+    const MatT<float> *mtab;
+    SourceParams src;
+    unsigned *err;
+    unsigned runaway;
+    float scale, inv_scale;       // FP16-deviation form
+    float *fout;                  // FP32 form: 11 planes
+    __half *g_out;                // FP16-deviation form: 11 deviation planes, 3 field planes
+    float *fe_out, *fhx_out, *fhy_out;
+};
+
+__device__ __forceinline__ void store2(float *p, bool two, float a, float b) {
+    if (two)
+        *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+    else
+        *p = a;
+}
+
+// FP32 store of level 4 of row q: 11 planes, two sites (one at an odd lattice's last column).
+__device__ __forceinline__ void store_row32(const StreamArgs &a, size_t idx, bool two, const Pop<float> &pa,
+                                            const Pop<float> &pb) {
+    float *f = a.fout + idx;
+    const size_t ps = a.pstride;
+    store2(f + P_EZ * ps, two, pa.ez, pb.ez);
+    store2(f + P_EPX * ps, two, pa.epx, pb.epx);
+    store2(f + P_EMX * ps, two, pa.emx, pb.emx);
+    store2(f + P_EPY * ps, two, pa.epy, pb.epy);
+    store2(f + P_EMY * ps, two, pa.emy, pb.emy);
+    store2(f + P_HXPX * ps, two, pa.hxpx, pb.hxpx);
+    store2(f + P_HXMX * ps, two, pa.hxmx, pb.hxmx);
+    store2(f + P_HXZ * ps, two, pa.hxz, pb.hxz);
+    store2(f + P_HYPY * ps, two, pa.hypy, pb.hypy);
+    store2(f + P_HYMY * ps, two, pa.hymy, pb.hymy);
+    store2(f + P_HYZ * ps, two, pa.hyz, pb.hyz);
+}
+
+// Time levels 1..3 of the wavefront: per level the kept row (row i - 1 - k when row i arrives,
+// 9 populations), the +y pair of the row before it, and the ids of row i - 1 - k.  Level 0 lives
+// in the ring; index 0 of these arrays is unused.
+struct Wave {
+    Row9 cur[BT];
+    float oe[BT][2], oh[BT][2];
+    unsigned ids[BT];
+};
+
+// One row of level 0 from a slot: FP32 as staged; FP16-deviation rebuilt in place first (see
+// Layout).  Returns the two ids of the row.
+template <bool F16>
+__device__ __forceinline__ unsigned take_row(unsigned char *sl, int idoff, int lane, float inv_scale) {
+    const unsigned id = *reinterpret_cast<const unsigned short *>(sl + Layout<F16>::IDS + idoff + 2 * lane);
+    if constexpr (F16) {
+        const __half *dv = reinterpret_cast<const __half *>(sl) + DEVOFF;
+        const float *fl = reinterpret_cast<const float *>(sl + Layout<F16>::FLD);
+        const float2 fe = reinterpret_cast<const float2 *>(fl)[lane];
+        const float2 fhx = reinterpret_cast<const float2 *>(fl + LW)[lane];
+        const float2 fhy = reinterpret_cast<const float2 *>(fl + 2 * LW)[lane];
+        __half ga[NPLANES], gb[NPLANES];
+#pragma unroll
+        for (int p = 0; p < NPLANES; ++p) {
+            const __half2 g2 = reinterpret_cast<const __half2 *>(dv + p * DEVW)[lane];
+            ga[p] = __low2half(g2);
+            gb[p] = __high2half(g2);
+        }
+        // the post-collision populations of the stored state: f* = f^eq - g
+        Pop<float> na, nb;
+        rebuild_all(ga, Fld{fe.x, fhx.x, fhy.x}, inv_scale, na);
+        rebuild_all(gb, Fld{fe.y, fhx.y, fhy.y}, inv_scale, nb);
+        __syncwarp();  // every lane has read the copies before any lane overwrites them
+        float2 *row = reinterpret_cast<float2 *>(sl);
+        row[P_EZ * 32 + lane] = make_float2(na.ez, nb.ez);
+        row[P_EPX * 32 + lane] = make_float2(na.epx, nb.epx);
+        row[P_EMX * 32 + lane] = make_float2(na.emx, nb.emx);
+        row[P_EPY * 32 + lane] = make_float2(na.epy, nb.epy);
+        row[P_EMY * 32 + lane] = make_float2(na.emy, nb.emy);
+        row[P_HXPX * 32 + lane] = make_float2(na.hxpx, nb.hxpx);
+        row[P_HXMX * 32 + lane] = make_float2(na.hxmx, nb.hxmx);
+        row[P_HXZ * 32 + lane] = make_float2(na.hxz, nb.hxz);
+        row[P_HYPY * 32 + lane] = make_float2(na.hypy, nb.hypy);
+        row[P_HYMY * 32 + lane] = make_float2(na.hymy, nb.hymy);
+        row[P_HYZ * 32 + lane] = make_float2(na.hyz, nb.hyz);
+        // each lane reads back only its own two sites (neighbours come by shuffles)
+    }
+    return id;
+}
+
+// F16: the FP16-deviation form (TM); otherwise FP32 of either polarization.
+template <bool F16, int POL>
+__global__ void __launch_bounds__(NW * 32, 3)
+    k_step4_stream(const StreamArgs a, const __grid_constant__ CUtensorMap smap,
+                   const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap imap,
+                   const long long *__restrict__ t_in, long long *__restrict__ t_out) {
+    using LY = Layout<F16>;
+    constexpr int RING = LY::RING;
+    extern __shared__ unsigned char sm_dyn[];
+    __shared__ __align__(8) uint64_t bars[NW][RING];
+    __shared__ SrcLevels sp;
+    unsigned char *s = sm_dyn + ((128u - (smem_u32(sm_dyn) & 127u)) & 127u);
+    MatT<float> *table = reinterpret_cast<MatT<float> *>(s);
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    unsigned char *ring = s + LY::TABLE + (size_t)warp * LY::WARP;
+    float4 *edge = reinterpret_cast<float4 *>(ring + RING * LY::SLOT);  // [BT][32]
+
+    const long long t = *t_in;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + BT;
+    if (threadIdx.x == 0) sp = source_levels_f(a.src, t);
+    for (int k = threadIdx.x; k < 256; k += NW * 32) table[k] = a.mtab[k];
+    if (lane == 0) {
+        for (int j = 0; j < RING; ++j) mbar_init(&bars[warp][j], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();  // the only block-wide barrier: from here on each warp runs alone
+    const int unit = (int)blockIdx.x * NW + warp;
+    if (unit >= a.n_units) return;
+    const int nx = a.nx, ny = a.ny;
+    const int strip = unit % a.n_strips, seg = unit / a.n_strips;
+    const int xs = strip * OUTW - HALO;         // first staged column (a multiple of 4)
+    const int xid = xs & ~15, idoff = xs - xid;  // first column of the id box, xs in it
+    const int xa = xs + 2 * lane, xb = xa + 1;  // this lane's sites
+    const int y0 = seg * a.seg_rows, y1 = min(y0 + a.seg_rows, ny);
+    const int ylo = max(y0 - BT, 0), yhi = min(y1 + BT, ny);
+    const bool xa0 = xa == 0, xa_last = xa == nx - 1, xb_last = xb == nx - 1;
+    // the strip's staged columns include a lattice edge: edge clamps (any lane) and the source
+    const bool xedge = xs <= 0 || xs + LW - 1 >= nx - 1;
+    const bool out_lane = lane >= HALO / 2 && lane < 32 - HALO / 2 && xa >= 0 && xa < nx;
+    const bool two = xb < nx;
+    const int kind = a.src.kind;
+    const bool src_lane = xa0 && kind != SRC_NONE;
+    const size_t ps = a.pstride;
+    const float inv_scale = a.inv_scale;
+
+    // prologue: the first RING rows in flight
+    if (lane == 0)
+        for (int j = 0; j < RING && ylo + j < yhi; ++j)
+            issue_row<F16>(&smap, &fmap, &imap, xs, xid, ylo + j, ring + j * LY::SLOT, &bars[warp][j]);
+
+    Wave wa, wb;
+#pragma unroll
+    for (int k = 0; k < BT; ++k) {
+        keep_row(wa.cur[k], Pop<float>{}, Pop<float>{});
+        wa.oe[k][0] = wa.oe[k][1] = wa.oh[k][0] = wa.oh[k][1] = 0.f;
+        wa.ids[k] = 0u;
+    }
+    bool bad = false, timeout = false;
+    // ring slots of rows i, i - 1, i - 2 and the barrier phase of row i (rows arrive in order)
+    int s0 = 0, s1 = RING - 1, s2 = RING - 2;
+    unsigned ph = 0;
+
+    // One wavefront row: row i arrives as level 0; level k + 1 of row q = i - 1 - k is computed
+    // from level k of rows q - 1, q and q + 1 (k = 0 from the ring, k >= 1 from `in`); `out`
+    // receives the kept rows for the next row.  FAST: an interior strip in the steady state
+    // (every level computes, no lattice edge in x or y, every level-4 row is stored) without any
+    // of the general path's tests.  Returns false after a bounded wait gave up.
+    auto row = [&](auto fast_tag, int i, const Wave &in, Wave &out) -> bool {
+        constexpr bool FAST = decltype(fast_tag)::value;
+        // level 0 of row i
+        if (FAST || i < yhi) {
+            const bool ok = mbar_wait(&bars[warp][s0], ph);
+            if (__any_sync(0xffffffffu, !ok)) return false;
+            take_row<F16>(ring + (size_t)s0 * LY::SLOT, idoff, lane, inv_scale);
+        }
+        Pop<float> na{}, nb{};  // level k of row i - k, the -y pair for level k + 1
+        bool have = FAST || i < yhi;
+        unsigned id_k0 = 0;
+#pragma unroll
+        for (int k = 0; k < BT; ++k) {
+            const int q = i - 1 - k;
+            const bool compute = FAST || (q >= ylo && q < ny);  // uniform over the warp
+            Pop<float> ca{}, cb{};
+            if (compute) {
+                unsigned idq;
+                if (k == 0) {
+                    // level 0 from the ring: rows q - 1, q, q + 1, clamped to q at the lattice's first
+                    // and last rows and at the segment's first row (whose row above was never
+                    // loaded: its level-1 value is a halo value no output depends on)
+                    const unsigned char *sq = ring + (size_t)s1 * LY::SLOT;
+                    const float *rq = reinterpret_cast<const float *>(sq);
+                    const float *ru =
+                        reinterpret_cast<const float *>(ring + (size_t)(FAST || q > ylo ? s2 : s1) * LY::SLOT);
+                    const float *rd =
+                        reinterpret_cast<const float *>(ring + (size_t)(FAST || q < ny - 1 ? s0 : s1) * LY::SLOT);
+                    Row9 c0;
+                    float ey[2], hy[2], my[2], mh[2];
+                    float2 v;
+                    v = lds2(rq, P_EZ, lane), c0.ez[0] = v.x, c0.ez[1] = v.y;
+                    v = lds2(rq, P_EPX, lane), c0.epx[0] = v.x, c0.epx[1] = v.y;
+                    v = lds2(rq, P_EMX, lane), c0.emx[0] = v.x, c0.emx[1] = v.y;
+                    v = lds2(rq, P_HXPX, lane), c0.hxpx[0] = v.x, c0.hxpx[1] = v.y;
+                    v = lds2(rq, P_HXMX, lane), c0.hxmx[0] = v.x, c0.hxmx[1] = v.y;
+                    v = lds2(rq, P_HXZ, lane), c0.hxz[0] = v.x, c0.hxz[1] = v.y;
+                    v = lds2(rq, P_HYZ, lane), c0.hyz[0] = v.x, c0.hyz[1] = v.y;
+                    v = lds2(ru, P_EPY, lane), ey[0] = v.x, ey[1] = v.y;
+                    v = lds2(ru, P_HYPY, lane), hy[0] = v.x, hy[1] = v.y;
+                    v = lds2(rd, P_EMY, lane), my[0] = v.x, my[1] = v.y;
+                    v = lds2(rd, P_HYMY, lane), mh[0] = v.x, mh[1] = v.y;
+                    if (FAST)
+                        pull_row(c0, ey, hy, my, mh, false, false, false, ca, cb);
+                    else
+                        pull_row(c0, ey, hy, my, mh, xa0, xa_last, xb_last, ca, cb);
+                    idq = *reinterpret_cast<const unsigned short *>(sq + LY::IDS + idoff + 2 * lane);
+                    id_k0 = idq;
+                } else {
+                    float ey[2], hy[2], my[2], mh[2];
+                    if (!FAST && q == 0) {  // top edge: the +y pair of row 0 itself
+                        ey[0] = in.cur[k].epy[0], ey[1] = in.cur[k].epy[1];
+                        hy[0] = in.cur[k].hypy[0], hy[1] = in.cur[k].hypy[1];
+                    } else {
+                        ey[0] = in.oe[k][0], ey[1] = in.oe[k][1], hy[0] = in.oh[k][0], hy[1] = in.oh[k][1];
+                    }
+                    if (!FAST && q == ny - 1) {  // bottom edge: the -y pair of the last row itself
+                        const float4 e = edge[k * 32 + lane];
+                        my[0] = e.x, my[1] = e.y, mh[0] = e.z, mh[1] = e.w;
+                    } else {
+                        my[0] = na.emy, my[1] = nb.emy, mh[0] = na.hymy, mh[1] = nb.hymy;
+                    }
+                    if (FAST)
+                        pull_row(in.cur[k], ey, hy, my, mh, false, false, false, ca, cb);
+                    else
+                        pull_row(in.cur[k], ey, hy, my, mh, xa0, xa_last, xb_last, ca, cb);
+                    idq = in.ids[k];
+                }
+                if (!FAST && src_lane && t + k >= 1) inject_source_t(kind, sp.g[k], sp.inc[k], ca);
+                const MatT<float> ma = table[idq & 0xffu], mb = table[(idq >> 8) & 0xffu];
+                const bool store = k == BT - 1 && out_lane && (FAST || (q >= y0 && q < y1));
+                if (F16 && k == BT - 1) {
+                    // the stored state of the last level: fields and FP16 deviations g = f - f^eq
+                    float E3a, Hxa, Hya, Da, E3b, Hxb, Hyb, Db;
+                    moments(ca, ma, &E3a, &Hxa, &Hya, &Da);
+                    moments(cb, mb, &E3b, &Hxb, &Hyb, &Db);
+                    if (store) {
+                        bad |= field_runaway(E3a, a.runaway) || (two && field_runaway(E3b, a.runaway));
+                        const Fld Fa = stored_fields(E3a, Hxa, Hya), Fb = stored_fields(E3b, Hxb, Hyb);
+                        __half ga[NPLANES], gb[NPLANES];
+                        encode_all(ca, Fa, a.scale, ga);
+                        encode_all(cb, Fb, a.scale, gb);
+                        const size_t idx = (size_t)q * a.pitch + xa;
+                        if (two) {
+#pragma unroll
+                            for (int p = 0; p < NPLANES; ++p)
+                                *reinterpret_cast<__half2 *>(a.g_out + p * ps + idx) = __halves2half2(ga[p], gb[p]);
+                            *reinterpret_cast<float2 *>(a.fe_out + idx) = make_float2(Fa.e, Fb.e);
+                            *reinterpret_cast<float2 *>(a.fhx_out + idx) = make_float2(Fa.hx, Fb.hx);
+                            *reinterpret_cast<float2 *>(a.fhy_out + idx) = make_float2(Fa.hy, Fb.hy);
+                        } else {
+#pragma unroll
+                            for (int p = 0; p < NPLANES; ++p) a.g_out[p * ps + idx] = ga[p];
+                            a.fe_out[idx] = Fa.e;
+                            a.fhx_out[idx] = Fa.hx;
+                            a.fhy_out[idx] = Fa.hy;
+                        }
+                    }
+                } else {
+                    const bool ra = update_site<POL, true>(ca, ma, a.runaway, nullptr, nullptr);
+                    const bool rb = update_site<POL, true>(cb, mb, a.runaway, nullptr, nullptr);
+                    if (store) {
+                        bad |= ra || (two && rb);
+                        store_row32(a, (size_t)q * a.pitch + xa, two, ca, cb);
+                    }
+                }
+            }
+            if (k == 0) {
+                // the slot of row i - 2 is no longer read: it receives row i + 3
+                __syncwarp();
+                if (lane == 0 && (FAST || i - 2 >= ylo) && i + RING - 2 < yhi) {
+                    fence_proxy_async_smem();
+                    issue_row<F16>(&smap, &fmap, &imap, xs, xid, i + RING - 2, ring + (size_t)s2 * LY::SLOT,
+                                   &bars[warp][s2]);
+                }
+            } else {
+                // level k moves on by one row: row i - k becomes the kept row
+                if (FAST || have) {
+                    if (!FAST && i - k == ny - 1) edge[k * 32 + lane] = make_float4(na.emy, nb.emy, na.hymy, nb.hymy);
+                    out.oe[k][0] = in.cur[k].epy[0], out.oe[k][1] = in.cur[k].epy[1];
+                    out.oh[k][0] = in.cur[k].hypy[0], out.oh[k][1] = in.cur[k].hypy[1];
+                    keep_row(out.cur[k], na, nb);
+                } else if (&in != &out) {
+                    out.cur[k] = in.cur[k];
+                    out.oe[k][0] = in.oe[k][0], out.oe[k][1] = in.oe[k][1];
+                    out.oh[k][0] = in.oh[k][0], out.oh[k][1] = in.oh[k][1];
+                }
+            }
+            na = ca;
+            nb = cb;
+            have = compute;
+        }
+        // ids: row i - 1 - k for level k + 1 at the next row
+#pragma unroll
+        for (int k = BT - 1; k > 1; --k) out.ids[k] = in.ids[k - 1];
+        out.ids[1] = id_k0;
+        // the ring moves on by one row
+        s2 = s1;
+        s1 = s0;
+        if (++s0 == RING) {
+            s0 = 0;
+            ph ^= 1u;
+        }
+        return true;
+    };
+
+    // steady-state rows of an interior strip: every level computes and stores, no lattice edge
+    const int f0 = max(y0 + BT, BT + 1), f1 = xedge ? f0 : min(min(y1 + BT, yhi), ny);
+    int i = ylo;
+    for (; i < f0 && i < y1 + BT; ++i)
+        if (!row(std::false_type{}, i, wa, wa)) {
+            timeout = true;
+            break;
+        }
+    for (; !timeout && i + 1 < f1; i += 2) {
+        if (!row(std::true_type{}, i, wa, wb) || !row(std::true_type{}, i + 1, wb, wa)) {
+            timeout = true;
+            break;
+        }
+    }
+    for (; !timeout && i < y1 + BT; ++i)
+        if (!row(std::false_type{}, i, wa, wa)) {
+            timeout = true;
+            break;
+        }
+    if (lane == 0 && timeout) atomicOr(a.err, kErrTimeout);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrUnstable);
+}
+
+template <bool F16, int POL>
+cudaError_t allow_smem_stream() {
+    return cudaFuncSetAttribute(k_step4_stream<F16, POL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Layout<F16>::SMEM);
+}
+
+}  // namespace
+
+StreamPlan stream_plan(int nx, int ny, int resident_warps) {
+    StreamPlan p;
+    p.n_strips = (nx + OUTW - 1) / OUTW;
+    // as many row segments as keep every strip's warps within one wave, but at least 16 rows
+    // each (shorter ones spend most of their time on the 4-row halo at each end)
+    int segs = resident_warps / p.n_strips;
+    if (segs < 1) segs = 1;
+    if (segs > (ny + 15) / 16) segs = (ny + 15) / 16;
+    p.seg_rows = (ny + segs - 1) / segs;
+    segs = (ny + p.seg_rows - 1) / p.seg_rows;
+    p.n_units = p.n_strips * segs;
+    p.grid = (p.n_units + NW - 1) / NW;
+    return p;
+}
+
+cudaError_t stream_prepare(bool f16, int *resident_warps) {
+    cudaError_t e = f16 ? allow_smem_stream<true, POL_TM>() : allow_smem_stream<false, POL_TM>();
+    if (e == cudaSuccess && !f16) e = allow_smem_stream<false, POL_TE>();
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = f16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step4_stream<true, POL_TM>, NW * 32,
+                                                                Layout<true>::SMEM)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step4_stream<false, POL_TM>, NW * 32,
+                                                                Layout<false>::SMEM);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess) *resident_warps = per_sm * sms * NW;
+    return e;
+}
+
+cudaError_t encode_stream_maps(CUtensorMap *smap, CUtensorMap *fmap, CUtensorMap *imap, const void *buf, bool f16,
+                               const uint8_t *ids, int nx, int ny, int pitch, size_t pstride) {
+    if (((uintptr_t)buf & 15u) || ((uintptr_t)ids & 15u) || (pitch % 16) || (pstride % 8))
+        return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (f16) {
+        const size_t hb = f16_half_bytes(pstride), fb = f16_plane_bytes(pstride);
+        const cuuint64_t gdims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)NPLANES};
+        const cuuint64_t gstrides[2] = {(cuuint64_t)pitch * 2, (cuuint64_t)pstride * 2};
+        const cuuint32_t gbox[3] = {(cuuint32_t)DEVW, 1u, (cuuint32_t)NPLANES};
+        e = encode_tiled(smap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, buf, gdims, gstrides, gbox);
+        if (e != cudaSuccess) return e;
+        const cuuint64_t fdims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 3};
+        const cuuint64_t fstrides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)fb};
+        const cuuint32_t fbox[3] = {(cuuint32_t)LW, 1u, 3u};
+        e = encode_tiled(fmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (const char *)buf + hb, fdims, fstrides, fbox);
+    } else {
+        const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)NPLANES};
+        const cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pstride * 4};
+        const cuuint32_t box[3] = {(cuuint32_t)LW, 1u, (cuuint32_t)NPLANES};
+        e = encode_tiled(smap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, buf, dims, strides, box);
+        if (e == cudaSuccess && fmap) *fmap = *smap;  // unused by the FP32 kernel
+    }
+    if (e != cudaSuccess || !imap) return e;
+    const cuuint64_t idims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+    const cuuint64_t istrides[1] = {(cuuint64_t)pitch};
+    const cuuint32_t ibox[2] = {(cuuint32_t)IDBOX, 1u};
+    return encode_tiled(imap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, ids, idims, istrides, ibox);
+}
+
+cudaError_t launch_step4_stream(const StepArgs<float> &sa, const F16Args *fa, const CUtensorMap *smap,
+                                const CUtensorMap *fmap, const CUtensorMap *imap, float *fout, const StreamPlan &plan,
+                                const long long *t_in, long long *t_out, cudaStream_t s) {
+    StreamArgs a{};
+    a.nx = sa.nx;
+    a.ny = sa.ny;
+    a.pitch = sa.pitch;
+    a.n_strips = plan.n_strips;
+    a.seg_rows = plan.seg_rows;
+    a.n_units = plan.n_units;
+    a.pstride = sa.pstride;
+    a.mtab = sa.mtab;
+    a.src = sa.src;
+    a.err = sa.err;
+    a.runaway = sa.runaway;
+    a.fout = fout;
+    if (fa) {
+        a.scale = fa->scale;
+        a.inv_scale = fa->inv_scale;
+        a.g_out = fa->g_out;
+        a.fe_out = fa->fe_out;
+        a.fhx_out = fa->fhx_out;
+        a.fhy_out = fa->fhy_out;
+        k_step4_stream<true, POL_TM><<<plan.grid, NW * 32, Layout<true>::SMEM, s>>>(a, *smap, *fmap, *imap, t_in, t_out);
+    } else if (sa.pol == POL_TE) {
+        k_step4_stream<false, POL_TE><<<plan.grid, NW * 32, Layout<false>::SMEM, s>>>(a, *smap, *smap, *imap, t_in,
+                                                                                      t_out);
+    } else {
+        k_step4_stream<false, POL_TM><<<plan.grid, NW * 32, Layout<false>::SMEM, s>>>(a, *smap, *smap, *imap, t_in,
+                                                                                      t_out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbmem

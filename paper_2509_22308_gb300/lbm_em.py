@@ -16,8 +16,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm_em.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
 F64, F32, F16DEV, F32X2 = 0, 1, 2, 3
-FLAG_SINGLE_STEP, FLAG_TWO_STEP, FLAG_THREE_STEP = 1, 2, 8
-STEP_MODES = {"auto": 0, "one": FLAG_SINGLE_STEP, "two": FLAG_TWO_STEP, "three": FLAG_THREE_STEP}
+FLAG_SINGLE_STEP, FLAG_TWO_STEP, FLAG_THREE_STEP, FLAG_FOUR_STEP = 1, 2, 8, 16
+STEP_MODES = {"auto": 0, "one": FLAG_SINGLE_STEP, "two": FLAG_TWO_STEP, "three": FLAG_THREE_STEP,
+              "four": FLAG_FOUR_STEP}
 FLAG_TE = 4
 POLARIZATION_FLAGS = {"tm": 0, "te": FLAG_TE}
 SRC_HARD, SRC_OPEN, SRC_NONE = 0, 1, 2
@@ -76,6 +77,7 @@ SIGNATURES = {
     "lbm_em_step": [_vp, ctypes.c_int64],
     "lbm_em_sync": [_vp],
     "lbm_em_get_time": [_vp, _P(ctypes.c_int64)],
+    "lbm_em_get_steps_per_launch": [_vp, _P(ctypes.c_int32)],
     "lbm_em_set_contour": [_vp, _P(Contour)],
     "lbm_em_accumulate": [_vp, ctypes.c_int64],
     "lbm_em_contour_integral": [_vp, _P(ctypes.c_double)],
@@ -226,6 +228,11 @@ class Solver:
     def t(self) -> int:
         v = ctypes.c_int64()
         _call("lbm_em_get_time", self.h, ctypes.byref(v))
+        return v.value
+
+    def steps_per_launch(self) -> int:
+        v = ctypes.c_int32()
+        _call("lbm_em_get_steps_per_launch", self.h, ctypes.byref(v))
         return v.value
 
     def set_contour(self, c: Contour):

@@ -117,11 +117,13 @@ def test_batch_rejects_an_unknown_polarization(lib):
 
 
 def test_three_step_flag_is_fp32_only(lib):
-    """LBM_EM_FLAG_THREE_STEP (8) is accepted for FP32 alone and excludes the other step flags;
-    unknown flags are rejected.  The checks come before any device work."""
+    """LBM_EM_FLAG_THREE_STEP (8) is accepted for FP32 alone, LBM_EM_FLAG_FOUR_STEP (16) for
+    FP32 and FP16-deviation; each excludes the other step flags; unknown flags are rejected.
+    The checks come before any device work."""
     from paper_2509_22308_gb300 import lbm_em
     P = lbm_em.PRECISIONS
-    for prec, flags in (("f64", 8), ("f16dev", 8), ("f32x2", 8), ("f32", 8 | 1), ("f32", 8 | 2), ("f32", 16)):
+    for prec, flags in (("f64", 8), ("f16dev", 8), ("f32x2", 8), ("f32", 8 | 1), ("f32", 8 | 2), ("f32", 32),
+                        ("f64", 16), ("f32x2", 16), ("f32", 16 | 2), ("f32", 16 | 8), ("f16dev", 16 | 1)):
         g = lbm_em.Grid(16, 16, P[prec], flags, None)
         h = ctypes.c_void_p()
         rc = lib.lbm_em_create_janus(ctypes.byref(g), ctypes.byref(lbm_em.make_janus(5, 0.3, 2.0)),

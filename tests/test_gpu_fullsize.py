@@ -13,8 +13,9 @@ scale, phasors at every stencil site within 1e-10.
 Multi-step launches against one step per launch: lattices of 1024^2 and 1536 x 1000 hold
 2 048-3 182 tiles of the two- and three-step kernels against a persistent grid of 3 thread
 blocks per SM, so each block walks several tiles, reusing its stage and flipping its
-mbarrier phase; fields after step counts of every residue and the forces of an accumulated
-period must be the same bits."""
+mbarrier phase; the four-step kernel cuts them into strips and row segments of several
+rows per warp, so its row ring wraps many times; fields after step counts of every residue
+and the forces of an accumulated period must be the same bits."""
 import os
 
 import numpy as np
@@ -114,12 +115,12 @@ def _same_bits(inst, prec, mode, pol="tm", counts=(1, 2, 3, 5, 30, 31, 64, 7)):
 
 
 @pytest.mark.parametrize("shape", BIG, ids=lambda s: f"{s[0]}x{s[1]}")
-@pytest.mark.parametrize("prec,mode", [("f32", "two"), ("f32", "three"), ("f16dev", "two")])
+@pytest.mark.parametrize("prec,mode", [("f32", "two"), ("f32", "three"), ("f32", "four"), ("f16dev", "two")])
 def test_multi_step_bit_identity_on_persistent_grid(shape, prec, mode):
     _same_bits(_big_inst(*shape), prec, mode)
 
 
 @pytest.mark.parametrize("shape", BIG, ids=lambda s: f"{s[0]}x{s[1]}")
-@pytest.mark.parametrize("mode", ["two", "three"])
+@pytest.mark.parametrize("mode", ["two", "three", "four"])
 def test_multi_step_bit_identity_on_persistent_grid_te(shape, mode):
     _same_bits(_big_inst(*shape, pec2=False), "f32", mode, pol="te")
