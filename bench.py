@@ -36,6 +36,14 @@ BYTES_PER_LU = {"f64": 11 * 8 * 2 + 1, "f32": 11 * 4 * 2 + 1, "f16dev": 2 * (11 
                 "f32x2": 11 * 8 * 2 + 1}
 STEP_KERNEL = {"f64": "k_step<double, false, TM>", "f32": "k_step2_tma<false, TM> (two steps per launch)",
                "f16dev": "k_step2_f16_tma<false> (two steps per launch)"}
+# step kernel of a form by steps per launch (polarization P)
+KERNELS = {("f32", 1): "k_step<float, false, {P}>", ("f32", 2): "k_step2_tma<false, {P}> (TMA-staged 64 x 8 tiles)",
+           ("f32", 3): "k_step3_tma<false, {P}> (TMA-staged 28 x 12 tiles)", ("f16dev", 1): "k_step_f16<false>",
+           ("f16dev", 2): "k_step2_f16_tma<false> (TMA-staged 64 x 8 tiles)", ("f64", 1): "k_step<double, false, {P}>",
+           ("f32", 4): "k_step4_stream<false, {P}> (row-streaming, 4 time levels in registers)",
+           ("f16dev", 4): "k_step4_stream<true, TM> (row-streaming, 4 time levels in registers)",
+           ("f32x2", 1): "k_step<df, false, {P}> (double-float)",
+           ("f32x2", 2): "k_step2<df, false, {P}> (double-float)"}
 # lattice steps one launch of that kernel advances (the default mode of each form)
 STEPS_PER_LAUNCH = {"f64": 1, "f32": 2, "f16dev": 2}
 # FP64 pipe operations per lattice update of the step kernel: 12 for the moments
@@ -56,10 +64,18 @@ def parse_args():
     p.add_argument("--design-map-instances", type=int, default=256)
     p.add_argument("--profile-case", action="store_true",
                    help="small case for ncu: two launches of each step kernel on a 2048^2 lattice and of the FP64 step on the 512^2 workload")
+    p.add_argument("--profile-only", default="",
+                   help="with --profile-case: only these form:mode pairs on the 2048^2 lattice (e.g. f32:four,f16dev:four)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU-baseline sample")
+    p.add_argument("--cpu-seconds", type=float, default=4.0,
+                   help="target length of each of the four CPU-baseline samples")
+    p.add_argument("--repeats", type=int, default=5, help="repeats of every secondary line (median and spread)")
+    p.add_argument("--ncu-summary", metavar="CSV",
+                   help="summarise an ncu --csv metrics capture of --profile-case into --ncu-out and exit")
+    p.add_argument("--ncu-out", default=os.path.join(ROOT, "profiles", "counters.json"))
+    p.add_argument("--ncu-command", default="", help="the command that made the capture (recorded in the summary)")
     return p.parse_args()
 
 
@@ -74,6 +90,7 @@ def measured_peaks():
 
 
 def kernel_source_sha():
+    """Hash of the sources of the FP64 step kernel (its counters go stale when they change)."""
     h = hashlib.sha256()
     for name in ("common.cuh", "step.cu"):
         with open(os.path.join(ROOT, "paper_2509_22308_gb300", "csrc", name), "rb") as f:
@@ -81,19 +98,66 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(precision):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None
-    when the summary is missing or the kernel source changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", f"k_step_{precision}_{WORKLOAD}.md")
+COUNTERS = os.path.join(ROOT, "profiles", "counters.json")
+FP64_OP_METRICS = ("sm__sass_thread_inst_executed_op_dadd_pred_on.sum",
+                   "sm__sass_thread_inst_executed_op_dmul_pred_on.sum",
+                   "sm__sass_thread_inst_executed_op_dfma_pred_on.sum")
+
+
+def profiled_counters(kernel_prefix):
+    """Per-launch counters of the FP64 step kernel on one 512^2 instance of the benchmark
+    workload, from the machine-readable ncu summary (bench.py --ncu-summary), or None when
+    it is missing or the kernel source changed since the capture."""
     try:
-        text = open(path).read()
-    except OSError:
+        with open(COUNTERS) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
         return None
-    m_sha = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
-    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_sha or not m_b or m_sha.group(1) != kernel_source_sha():
+    if d.get("source_sha256_16") != kernel_source_sha():
         return None
-    return float(m_b.group(1))
+    for name, k in d.get("kernels", {}).items():
+        if kernel_prefix in name and k.get("grid_sites") == 512 * 512:
+            return k
+    return None
+
+
+def summarize_ncu(csv_path, out_path, command):
+    """ncu --csv (metrics page) -> per-kernel mean of every metric per launch (JSON)."""
+    import csv
+    per = {}
+    with open(csv_path, newline="") as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for row in csv.DictReader(lines):
+        name = row.get("Kernel Name", "")
+        grid = row.get("Grid Size", "")
+        key = (name, grid, row.get("ID"))
+        try:
+            v = float(row["Metric Value"].replace(",", ""))
+        except (KeyError, ValueError):
+            continue
+        per.setdefault(key, {})[row["Metric Name"]] = v
+    kernels = {}
+    for (name, grid, _), metrics in per.items():
+        k = kernels.setdefault(f"{name} grid{grid}", {"launches": 0, "sum": {}})
+        k["launches"] += 1
+        for m, v in metrics.items():
+            k["sum"][m] = k["sum"].get(m, 0.0) + v
+    out = {"command": command, "source_sha256_16": kernel_source_sha(), "kernels": {}}
+    for name, k in kernels.items():
+        n = k["launches"]
+        e = {"launches": n, "per_launch": {m: v / n for m, v in k["sum"].items()}}
+        pl = e["per_launch"]
+        if "dram__bytes_read.sum" in pl and "dram__bytes_write.sum" in pl:
+            e["dram_bytes_per_launch"] = pl["dram__bytes_read.sum"] + pl["dram__bytes_write.sum"]
+        if all(m in pl for m in FP64_OP_METRICS):
+            e["fp64_ops_per_launch"] = sum(pl[m] for m in FP64_OP_METRICS)
+        # the profile case's FP64 step kernels run on one 512^2 instance (grid of 16 x 16 x 1 blocks of 32 x 8)
+        if "k_step<double" in name and "(16, 64, 1)" in name:
+            e["grid_sites"] = 512 * 512
+        out["kernels"][name] = e
+    with open(out_path, "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
+    print(f"wrote {out_path}: {len(out['kernels'])} kernels")
 
 
 class ClockSampler:
@@ -165,19 +229,36 @@ def instance_lus(inst):
     return inst["nx"] * inst["ny"] * inst["periods"] * inst["period"]
 
 
-def cpu_baseline(inst, target_s):
-    """The oracle as it stands, on the host cores: a bounded sample of one instance."""
-    import numpy as np
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sample(inst, threads, target_s):
+    """The oracle as it stands, on `threads` host cores: a bounded sample of one instance's
+    hot path (plain steps, one accumulated period, the contour integral)."""
     from oracle import geometry as G
     from oracle import lbm as OL
     from oracle import mst
     eps, pec, _ = G.janus_material(inst["nx"], inst["ny"], inst["a"], inst["phi0"], inst["eps1"],
                                    inst["eps2"], inst["pec2"])
-    threads = os.cpu_count() or 1
     sim = OL.Simulation(eps, pec, period=inst["period"], ramp_steps=inst["ramp"], nthreads=threads)
     t0 = time.perf_counter()
-    sim.advance(8)
-    per_step = (time.perf_counter() - t0) / 8
+    sim.advance(4)
+    per_step = (time.perf_counter() - t0) / 4
     T = inst["period"]
     n_plain = max(0, int(target_s / per_step) - T)
     t0 = time.perf_counter()
@@ -187,11 +268,26 @@ def cpu_baseline(inst, target_s):
     mst.force_torque(*sim.phasors(), cx, cy, inst["R"], mst.default_n_points(inst["R"]), inst["a"])
     el = time.perf_counter() - t0
     steps = n_plain + T
-    return {"value": inst["nx"] * inst["ny"] * steps / el / 1e6, "unit": "MLUPS", "cores": threads,
-            "kind": "oracle",
-            "sample": (f"FP64 full-vector C oracle, {threads} OpenMP threads: one {inst['nx']}x{inst['ny']} "
-                       f"instance of {WORKLOAD}, {n_plain} steps + 1 accumulated period ({T} steps) + "
-                       f"contour integral, {el:.1f} s")}
+    return {"mlups": round(inst["nx"] * inst["ny"] * steps / el / 1e6, 2), "threads": threads,
+            "steps": steps, "seconds": round(el, 2)}
+
+
+def cpu_baseline(cfg1, cfg2, target_s):
+    """The oracle on the host: the 256^2 homogeneous workload and one 512^2 instance of the
+    benchmark workload, each on one thread and on every core; the headline value is the
+    benchmark workload on every core."""
+    threads = os.cpu_count() or 1
+    runs = {}
+    for cname, inst in (("homogeneous_dielectric_256", cfg1), (WORKLOAD, cfg2)):
+        for th in sorted({1, threads}):
+            runs[f"{cname}_{th}_threads"] = oracle_sample(inst, th, target_s)
+    main = runs[f"{WORKLOAD}_{threads}_threads"]
+    return {"value": main["mlups"], "unit": "MLUPS", "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": (f"FP64 full-vector C oracle (OpenMP): bounded samples (~{target_s:.0f} s each) of one "
+                       f"{cfg2['nx']}x{cfg2['ny']} instance of {WORKLOAD} and of the 256x256 homogeneous workload, "
+                       "plain steps + 1 accumulated period + contour integral, on 1 thread and on every core; "
+                       f"value = {WORKLOAD} on {threads} threads"),
+            "runs": runs}
 
 
 def run_reference(args, rank, world):
@@ -203,41 +299,52 @@ def run_reference(args, rank, world):
     OL.build()
     inst = W.md_janus_512(1)[0]
     budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    threads = os.cpu_count() or 1
     vals, secs = [], []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        cb = cpu_baseline(inst, budget)
+        cb = oracle_sample(inst, threads, budget)
         if i >= args.warmup:
             vals.append(cb)
             secs.append(time.perf_counter() - t0)
-    value = statistics.median(v["value"] for v in vals)
+    value = statistics.median(v["mlups"] for v in vals)
+    sample = (f"FP64 full-vector C oracle, {threads} OpenMP threads: per step a bounded sample (~{budget:.0f} s) "
+              f"of one 512x512 instance of {WORKLOAD} (plain steps + 1 accumulated period + contour integral)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * statistics.median(secs), 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nx": 512, "ny": 512, "instances_sampled": 1},
-            "cpu_baseline": {"kind": "oracle", "cores": vals[0]["cores"], "sample": vals[0]["sample"],
-                             "value": value, "unit": "MLUPS"},
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "sample": sample, "value": value, "unit": "MLUPS",
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def profile_case():
-    """Two launches of each step kernel (FP64; FP32 and FP16-deviation with two steps
-    per launch, then with one; double-float; FP32 with three steps per launch) on a 2048^2 lattice (state 0.3-0.7 GB per
-    buffer, larger than L2, a few GB on the device in total), two launches of the FP64 step
-    on one 512^2 instance of the benchmark workload, then a 24-instance FP32 design map."""
+def profile_case(only=""):
+    """Two launches of each step kernel (FP64; FP32 and FP16-deviation with two steps per
+    launch, then with one; double-float; FP32 with three steps per launch; FP32 and
+    FP16-deviation with four) on a 2048^2 lattice (state 0.3-0.7 GB per buffer, larger than
+    L2, a few GB on the device in total), two launches of the FP64 step on one 512^2
+    instance of the benchmark workload, then a 24-instance FP32 design map."""
     import torch
     from paper_2509_22308_gb300 import build as B
     B.build()
     from paper_2509_22308_gb300 import lbm_em as L
     inst = dict(nx=2048, ny=2048, a=128.0, phi0=0.5, eps1=4.0, eps2=1.0, pec2=True, period=240, periods=1,
                 R=192.0, ramp=240)
-    for fp, mode in (("f64", "auto"), ("f32", "two"), ("f16dev", "two"), ("f32", "one"), ("f16dev", "one"),
-                     ("f32x2", "auto"), ("f32", "three")):
+    pairs = (("f64", "auto"), ("f32", "two"), ("f16dev", "two"), ("f32", "one"), ("f16dev", "one"),
+             ("f32x2", "auto"), ("f32", "three"), ("f32", "four"), ("f16dev", "four"))
+    if only:
+        pairs = tuple(tuple(p.split(":")) for p in only.split(","))
+    for fp, mode in pairs:
         with L.solver_for_instance(inst, fp, steps_per_launch=mode) as s:
-            s.step({"two": 4, "three": 6}.get(mode, 2))
+            s.step({"two": 4, "three": 6, "four": 8}.get(mode, 2))
             s.sync()
+    if only:
+        torch.cuda.synchronize()
+        print("profile case done")
+        return
     # and two launches of the benchmark's own 512^2 FP64 instance (theta = 0)
     from paper_2509_22308_gb300 import workloads as W
     with L.solver_for_instance(W.md_janus_512()[0], "f64") as s:
@@ -253,16 +360,49 @@ def profile_case():
     print("profile case done")
 
 
+def spread(vals):
+    """Median and spread of repeated measurements."""
+    v = sorted(vals)
+    return {"median": round(statistics.median(v), 3), "min": round(v[0], 3), "max": round(v[-1], 3),
+            "n": len(v)}
+
+
+def measure_fp64_peak(L, stream, torch, repeats=5):
+    """FP64 pipe rate (FMAs per second, each one FP64 pipe operation) of the library's FMA-chain
+    probe, CUDA events on the probe's stream: best of `repeats` launches of ~20 ms."""
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    L.probe_fp64_fma(stream, 64)
+    rates = []
+    for _ in range(repeats):
+        a, b = ev(), ev()
+        a.record(stream)
+        n = L.probe_fp64_fma(stream, 4096)
+        b.record(stream)
+        b.synchronize()
+        rates.append(n / (a.elapsed_time(b) / 1e3) / 1e12)
+    return max(rates), statistics.median(rates)
+
+
+# Single-domain step kernels on the 8192^2 lattice: (form, steps per launch, polarization)
+SINGLE_DOMAIN_LINES = (("f32", "auto", "tm"), ("f32", "one", "tm"), ("f32", "two", "tm"), ("f32", "three", "tm"),
+                       ("f32", "four", "tm"), ("f16dev", "auto", "tm"), ("f16dev", "one", "tm"),
+                       ("f16dev", "four", "tm"), ("f32", "four", "te"), ("f64", "auto", "tm"),
+                       ("f32x2", "auto", "tm"), ("f32x2", "two", "tm"), ("f32", "auto", "te"), ("f64", "auto", "te"))
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.ncu_summary:
+        summarize_ncu(args.ncu_summary, args.ncu_out, args.ncu_command)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
     if args.profile_case:
-        profile_case()
+        profile_case(args.profile_only)
         return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -345,6 +485,8 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    # the FP64 pipe's measured rate, inside the same clock record (the FP64 step's ceiling)
+    fp64_peak, fp64_peak_median = measure_fp64_peak(L, main, torch)
     clocks = sampler.stop()
     total_ms = max_over_ranks(sum(step_ms), dist)
     value = lus_per_step * args.steps * world / (total_ms / 1e3) / 1e6
@@ -359,19 +501,24 @@ def main():
     avg_launch_us = plain_ms * 1e3 / plain_launches
     achieved = plain_bytes / (plain_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = profiled_traffic(prec)
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    prof = profiled_counters(STEP_KERNEL[prec].split("<")[0] + "<double") if prec == "f64" else None
+    traffic = round(prof["dram_bytes_per_launch"]) if prof and "dram_bytes_per_launch" in prof else None
     if prec == "f64":
-        # the FP64 step is bound by the FP64 pipe: 2 FP64 operations per clock per SM
+        # the FP64 step is bound by the FP64 pipe: operations per update x updates / time,
+        # against the pipe's measured rate (FMA-chain probe, same run, same clock record)
         ops = plain_sites_steps * FP64_OPS_PER_LU
         achieved_t = ops / (plain_ms / 1e3) / 1e12
-        peak_t = SMS * FP64_OPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
-        roofline = {"bound": "alu", "achieved": round(achieved_t, 4), "peak": round(peak_t, 4), "unit": "TFLOP/s",
-                    "frac": round(achieved_t / peak_t, 4), "traffic": traffic, "kernel": STEP_KERNEL[prec],
+        derived_t = SMS * FP64_OPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
+        roofline = {"bound": "alu", "achieved": round(achieved_t, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                    "frac": round(achieved_t / fp64_peak, 4), "traffic": traffic, "kernel": STEP_KERNEL[prec],
                     "flop_convention": f"FP64 pipe operations (add, multiply or FMA = 1), {FP64_OPS_PER_LU} per "
                                        "lattice update",
-                    "peak_source": f"derived: {SMS} SMs x {FP64_OPS_PER_CLK_PER_SM} FP64 ops/clk x median SM clock "
-                                   f"{sm_mhz:.0f} MHz",
+                    "peak_source": "measured: the library's FP64 FMA-chain probe (lbm_em_probe_fp64_fma), best of "
+                                   f"5 launches in this run (median {fp64_peak_median:.4f})",
+                    "peak_derived": round(derived_t, 4),
+                    "peak_derived_source": f"{SMS} SMs x {FP64_OPS_PER_CLK_PER_SM} FP64 ops/clk x median SM clock "
+                                           f"{sm_mhz:.0f} MHz",
                     "algorithmic_ops_per_launch": 512 * 512 * FP64_OPS_PER_LU,
                     "avg_launch_us": round(avg_launch_us, 3),
                     "timing": f"{n_inst} instances on {n_inst} streams; avg_launch_us = plain-step window / "
@@ -379,6 +526,9 @@ def main():
                     "hbm_view": {"achieved_gbs": round(achieved, 1), "peak_gbs": peak,
                                  "frac": round(achieved / peak, 4),
                                  "algorithmic_bytes_per_launch": 512 * 512 * BYTES_PER_LU[prec]}}
+        if prof and "fp64_ops_per_launch" in prof:
+            roofline["fp64_ops_per_lu_measured"] = round(prof["fp64_ops_per_launch"] / (512 * 512), 3)
+            roofline["counters_source"] = "profiles/counters.json (ncu, one 512^2 instance of the workload)"
     else:
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -401,7 +551,8 @@ def main():
 
     if not args.no_e2e:
         # end to end through the C ABI with host buffers: create from host eps/PEC maps,
-        # run, read the three results back, destroy
+        # run, read the three results back, destroy; the bytes copied are counted by the
+        # library (lbm_em_transfer_bytes) and by the one read-back of the results here
         maps = []
         for i, j in zip(instances, janus):
             reg = L.rasterize_janus(j, i["nx"], i["ny"])
@@ -410,8 +561,10 @@ def main():
             pec = (reg == 2).astype(np.uint8)
             maps.append((eps, pec))
         e2e_ms = []
+        h2d = d2h = 0
         for k in range(args.steps + 1):
             torch.cuda.synchronize()
+            c0 = L.transfer_bytes()
             t0 = time.perf_counter()
             hs, outs = [], torch.zeros((n_inst, 3), dtype=torch.float64, device="cuda")
             for inst, (eps, pec), st in zip(instances, maps, streams):
@@ -424,158 +577,162 @@ def main():
             host = outs.cpu().numpy()
             for h_ in hs:
                 h_.close()
+            c1 = L.transfer_bytes()
             if k > 0:
                 e2e_ms.append((time.perf_counter() - t0) * 1e3)
+                h2d += c1[0] - c0[0]
+                d2h += c1[1] - c0[1] + host.nbytes
             assert np.allclose(host, results, rtol=1e-9, atol=1e-12)
         e2e_total = max_over_ranks(sum(e2e_ms), dist)
-        h2d = 0
-        for i in instances:
-            pitch = (i["nx"] + 31) // 32 * 32
-            n_pts = 2 * int(np.ceil(2 * np.pi * i["R"]))
-            # material ids, material table, phase table, contour slot map, contour points
-            h2d += i["nx"] * i["ny"] + 256 * 32 + i["period"] * 16 + pitch * i["ny"] * 4 + n_pts * 64
         out["e2e"] = {"value": round(lus_per_step * args.steps * world / (e2e_total / 1e3) / 1e6, 1),
-                      "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
-                      "d2h_bytes_per_step": int(len(instances) * (3 * 8 + 4))}
+                      "unit": "MLUPS", "h2d_bytes_per_step": int(h2d // args.steps),
+                      "d2h_bytes_per_step": int(d2h // args.steps),
+                      "bytes_source": "counted: the library's own host<->device copies (lbm_em_transfer_bytes) "
+                                      "plus the read-back of the results"}
 
     if not args.no_forms and rank == 0:
+        # every form on the benchmark workload, sequential on one stream (a 512^2 FP32 or FP16 state
+        # stays resident in L2 across steps), repeated; force errors against the FP64 results
         forms = {}
         for fp in ("f32", "f16dev", "f32x2", "f64"):
-            if fp == prec:
-                forms[fp] = {"mlups": out["value"] / world, "step_kernel_gbs": round(achieved, 1),
-                             "steps_per_launch": spl,
-                             "frac_hbm": round(achieved / peak, 4)}
-                continue
-            # sequential on one stream: a 512^2 FP32/FP16 state stays resident in L2 across steps
             ss = [L.solver_for_instance(inst, fp, main) for inst in instances]
             for s, c in zip(ss, contours):  # warm-up (graphs, contour set-up)
                 s.step(64)
                 s.force_torque(c)
-                s.reset()
-            ev_ = []
-            res = []
-            t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            t0e.record(main)
-            for s, inst, c in zip(ss, instances, contours):
-                n_plain = (inst["periods"] - 1) * inst["period"]
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(main)
-                s.step(n_plain)
-                b.record(main)
-                ev_.append((a, b, n_plain))
-                res.append(s.force_torque(c))
-            t1e.record(main)
-            t1e.synchronize()
-            ms = t0e.elapsed_time(t1e)
-            pms = sum(a.elapsed_time(b) for a, b, _ in ev_)
-            pn = sum(n for _, _, n in ev_)
-            # state bytes per update: one read and one write per launch (two steps for FP32 and
-            # FP16-deviation, one for double-float and FP64)
-            gbs = pn * 512 * 512 * BYTES_PER_LU[fp] / STEPS_PER_LAUNCH.get(fp, 1) / (pms / 1e3) / 1e9
+            smp = ClockSampler(local)
+            smp.start()
+            mlups, gbs_l = [], []
+            for _ in range(args.repeats):
+                ev_, res = [], []
+                t0e, t1e = ev(), ev()
+                t0e.record(main)
+                for s, inst, c in zip(ss, instances, contours):
+                    s.reset()
+                    n_plain = (inst["periods"] - 1) * inst["period"]
+                    a, b = ev(), ev()
+                    a.record(main)
+                    s.step(n_plain)
+                    b.record(main)
+                    ev_.append((a, b, n_plain))
+                    res.append(s.force_torque(c))
+                t1e.record(main)
+                t1e.synchronize()
+                ms = t0e.elapsed_time(t1e)
+                pms = sum(a.elapsed_time(b) for a, b, _ in ev_)
+                pn = sum(n for _, _, n in ev_)
+                mlups.append(lus_per_step / (ms / 1e3) / 1e6)
+                # one read and one write of the state per launch
+                gbs_l.append(pn * 512 * 512 * BYTES_PER_LU[fp] / STEPS_PER_LAUNCH.get(fp, 1) / (pms / 1e3) / 1e9)
+            fclk = smp.stop()
             res = np.array(res)
             ref = results if prec == "f64" else res
             drag = np.abs(ref[:, 0])
             err = np.abs(res - ref) / drag[:, None]
-            forms[fp] = {"mlups": round(lus_per_step / (ms / 1e3) / 1e6, 1), "step_kernel_gbs": round(gbs, 1),
-                         "steps_per_launch": STEPS_PER_LAUNCH.get(fp, 1),
-                         "frac_hbm": round(gbs / peak, 4),
+            g = statistics.median(gbs_l)
+            forms[fp] = {"mlups": round(statistics.median(mlups), 1), "mlups_spread": spread(mlups),
+                         "step_kernel_gbs": round(g, 1), "steps_per_launch": STEPS_PER_LAUNCH.get(fp, 1),
+                         "frac_hbm": round(g / peak, 4),
                          "max_drag_err_rel": float(err[:, 0].max()),
-                         "max_lift_torque_err_drag_scale": float(err[:, 1:].max())}
+                         "max_lift_torque_err_drag_scale": float(err[:, 1:].max()),
+                         "clocks": fclk}
             for s in ss:
                 s.close()
         out["forms"] = forms
 
     if not args.no_hbm_scale and rank == 0:
         # single-domain step kernel on an 8192^2 lattice (state far larger than the
-        # 129 MB L2): algorithmic bytes per lattice update x updates / CUDA-event time.
-        # The FP32 and FP16-deviation kernels advance two steps per launch (temporal
-        # blocking), so they can exceed the one-read-one-write-per-step roofline.
+        # 129 MB L2): algorithmic bytes per lattice update x updates / CUDA-event time, each
+        # line repeated (96 steps, whole launches of every mode) with its own clock record.
+        # Kernels that advance several steps per launch (temporal blocking) can exceed the
+        # one-read-one-write-per-step roofline; their lines add the fraction at their own traffic.
         big = W.md_janus_8192()[0]
+        sites = big["nx"] * big["ny"]
         hs = {}
-        # TE^z lines: the same lattice and kernels with the TE moments and collision
-        for fp, mode, pol in (("f32", "auto", "tm"), ("f32", "one", "tm"), ("f32", "two", "tm"), ("f16dev", "auto", "tm"),
-                              ("f16dev", "one", "tm"), ("f64", "auto", "tm"), ("f32x2", "auto", "tm"),
-                              ("f32x2", "two", "tm"), ("f32", "auto", "te"), ("f64", "auto", "te")):
+        for fp, mode, pol in SINGLE_DOMAIN_LINES:
             key = fp + {"auto": "", "one": "_one_step_per_launch", "two": "_two_steps_per_launch",
-                        "three": "_three_steps_per_launch"}[mode]
+                        "three": "_three_steps_per_launch", "four": "_four_steps_per_launch"}[mode]
             key += "_te" if pol == "te" else ""
-            P = "TE" if pol == "te" else "TM"
-            kern = {("f32", "auto"): f"k_step3_tma<false, {P}> (three steps per launch, TMA-staged tiles)",
-                    ("f32", "two"): f"k_step2_tma<false, {P}> (two steps per launch, TMA-staged tiles)",
-                    ("f32", "one"): f"k_step<float, false, {P}>", ("f16dev", "one"): "k_step_f16<false>",
-                    ("f32", "three"): f"k_step3_tma<false, {P}> (three steps per launch, TMA-staged tiles)",
-                    ("f16dev", "auto"): "k_step2_f16_tma<false> (two steps per launch, TMA-staged tiles)",
-                    ("f64", "auto"): f"k_step<double, false, {P}>",
-                    ("f32x2", "auto"): f"k_step<df, false, {P}> (double-float)",
-                    ("f32x2", "two"): f"k_step2<df, false, {P}> (double-float, two steps per launch)"}[(fp, mode)]
             with L.solver_for_instance(big, fp, main, steps_per_launch=mode, polarization=pol) as s:
                 s.step(4)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                n = 15 if "three steps" in kern else 16  # whole launches only
-                a.record(main)
-                s.step(n)
-                b.record(main)
-                b.synchronize()
-                us = a.elapsed_time(b) * 1e3 / n
-                sites = big["nx"] * big["ny"]
-                gbs = sites * BYTES_PER_LU[fp] / (us / 1e6) / 1e9
-                hs[key] = {"kernel": kern, "us_per_step": round(us, 2),
-                          "glups": round(sites / (us / 1e6) / 1e9, 2), "achieved_gbs": round(gbs, 1),
-                          "frac_hbm": round(gbs / peak, 4), "bytes_per_lu": BYTES_PER_LU[fp]}
-                if "two steps per launch" in kern:
-                    # the state crosses HBM once per two steps: half the one-pass bytes per update
-                    hs[key]["two_step_bytes_per_lu"] = BYTES_PER_LU[fp] / 2
-                    hs[key]["two_step_frac_hbm"] = round(gbs / 2 / peak, 4)
-                if "three steps per launch" in kern:
-                    hs[key]["three_step_bytes_per_lu"] = round(BYTES_PER_LU[fp] / 3, 2)
-                    hs[key]["three_step_frac_hbm"] = round(gbs / 3 / peak, 4)
-                if fp == "f64":
-                    ops = FP64_OPS_PER_LU + (1 if pol == "te" else 0)   # TE: 29 per update
-                    hs[key]["fp64_ops_per_lu"] = ops
-                    t_ops = sites * ops / (us / 1e6) / 1e12
-                    hs[key]["fp64_tops"] = round(t_ops, 4)
-                    hs[key]["frac_fp64_pipe"] = round(t_ops / (SMS * FP64_OPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12), 4)
+                smp = ClockSampler(local)
+                smp.start()
+                us_l = []
+                for _ in range(args.repeats):
+                    a, b = ev(), ev()
+                    a.record(main)
+                    s.step(96)
+                    b.record(main)
+                    b.synchronize()
+                    us_l.append(a.elapsed_time(b) * 1e3 / 96)
+                lclk = smp.stop()
+                spl_l = s.steps_per_launch()
+                kern = KERNELS[(fp, spl_l)].format(P=pol.upper())
+            us = statistics.median(us_l)
+            gbs = sites * BYTES_PER_LU[fp] / (us / 1e6) / 1e9
+            hs[key] = {"kernel": kern, "steps_per_launch": spl_l, "us_per_step": round(us, 2),
+                       "glups": round(sites / (us / 1e6) / 1e9, 2),
+                       "glups_spread": spread([sites / (u / 1e6) / 1e9 for u in us_l]),
+                       "achieved_gbs": round(gbs, 1), "frac_hbm": round(gbs / peak, 4),
+                       "bytes_per_lu": BYTES_PER_LU[fp], "clocks": lclk}
+            if spl_l > 1:
+                # the state crosses HBM once per launch: 1/spl of the one-pass bytes per update
+                hs[key]["own_bytes_per_lu"] = round(BYTES_PER_LU[fp] / spl_l, 2)
+                hs[key]["own_frac_hbm"] = round(gbs / spl_l / peak, 4)
+            if fp == "f64":
+                ops = FP64_OPS_PER_LU + (1 if pol == "te" else 0)   # TE: 29 per update
+                hs[key]["fp64_ops_per_lu"] = ops
+                t_ops = sites * ops / (us / 1e6) / 1e12
+                hs[key]["fp64_tops"] = round(t_ops, 4)
+                hs[key]["frac_fp64_measured"] = round(t_ops / fp64_peak, 4)
         out["single_domain_8192"] = hs
 
     if not args.no_design_map and rank == 0:
         # batched design diagram: seeded dielectric Janus instances, uneven sizes
         # (a in {16, 32, 64}, grid 16 a) and run lengths (20 periods of T = 3 a),
         # one persistent kernel under a CUDA graph; FP32 lattice, FP64 accumulation,
-        # force error against the same batch in FP64
+        # force error against the same batch in FP64; FP32 repeated, the FP64 and
+        # double-float comparisons twice
         dm = W.design_map_256(4, args.design_map_instances)
         res = {}
-        for fp in ("f32", "f32x2", "f64"):
+        for fp, reps in (("f32", args.repeats), ("f32x2", 2), ("f64", 2)):
             bt = L.Batch(dm, fp, stream=main)
-            if fp == "f32":            # untimed first run (graph capture, first touch)
+            bt.run()                   # untimed first run (graph capture, first touch)
+            bt.results()
+            smp = ClockSampler(local)
+            smp.start()
+            ms_l = []
+            for _ in range(reps):
+                a, b = ev(), ev()
+                a.record(main)
                 bt.run()
-                bt.results()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(main)
-            bt.run()
-            b.record(main)
-            b.synchronize()
+                b.record(main)
+                b.synchronize()
+                ms_l.append(a.elapsed_time(b))
+            dclk = smp.stop()
             F, _ = bt.results()
-            res[fp] = (a.elapsed_time(b), F, bt.config())
+            res[fp] = (ms_l, F, bt.config(), dclk)
             bt.close()
-        ms32, F32, cfg = res["f32"]
-        ms64, F64, _ = res["f64"]
-        msx2, FX2, _ = res["f32x2"]
+        ms32, F32, cfg, clk32 = res["f32"]
+        ms64, F64, _, _ = res["f64"]
+        msx2, FX2, _, _ = res["f32x2"]
         errs = np.max(np.abs(F32 - F64), axis=1) / np.abs(F64[:, 0])
         lus = sum(instance_lus(i) for i in dm)
-        out["design_map"] = {"instances": len(dm), "cells_per_s": round(len(dm) / (ms32 / 1e3), 2),
-                             "mlups": round(lus / (ms32 / 1e3) / 1e6, 1), "ms": round(ms32, 1),
-                             "fp64_cells_per_s": round(len(dm) / (ms64 / 1e3), 2),
-                             "fp64_mlups": round(lus / (ms64 / 1e3) / 1e6, 1), "fp64_ms": round(ms64, 1),
-                             "f32x2_cells_per_s": round(len(dm) / (msx2 / 1e3), 2),
+        m32 = statistics.median(ms32)
+        out["design_map"] = {"instances": len(dm), "cells_per_s": round(len(dm) / (m32 / 1e3), 2),
+                             "cells_per_s_spread": spread([len(dm) / (m / 1e3) for m in ms32]),
+                             "mlups": round(lus / (m32 / 1e3) / 1e6, 1), "ms": round(m32, 1),
+                             "fp64_cells_per_s": round(len(dm) / (statistics.median(ms64) / 1e3), 2),
+                             "fp64_mlups": round(lus / (statistics.median(ms64) / 1e3) / 1e6, 1),
+                             "f32x2_cells_per_s": round(len(dm) / (statistics.median(msx2) / 1e3), 2),
                              "f32x2_max_force_err_drag_scale":
                                  float((np.max(np.abs(FX2 - F64), axis=1) / np.abs(F64[:, 0])).max()),
                              "max_force_err_drag_scale": float(errs.max()),
                              "instances_within_1e-3": int(np.sum(errs <= 1e-3)),
-                             "tile_w": cfg[0], "tile_h": cfg[1], "ctas_per_sm": cfg[2],
+                             "tile_w": cfg[0], "tile_h": cfg[1], "ctas_per_sm": cfg[2], "clocks": clk32,
                              "precision": "f32 lattice, f64 accumulation; error against the same batch in f64"}
 
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        out["cpu_baseline"] = cpu_baseline(instances[0], args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(W.homogeneous_dielectric_256()[0], instances[0], args.cpu_seconds)
 
     for s in solvers:
         s.close()
