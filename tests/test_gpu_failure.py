@@ -35,6 +35,17 @@ def test_bounded_wait_gives_up_and_reports_timeout():
             assert np.array_equal(x, y)
 
 
+@pytest.fixture
+def quiet_gc():
+    """Handles of earlier tests that wait for the garbage collector would change the held
+    count in the middle of a test: collect them first and pause the collector."""
+    import gc
+    gc.collect()
+    gc.disable()
+    yield
+    gc.enable()
+
+
 def _make_janus_solver(inst):
     return L.solver_for_instance(inst, "f32")
 
@@ -66,7 +77,7 @@ def _fail_each_allocation(make, live0):
 
 
 @pytest.mark.parametrize("make", [_make_janus_solver, _make_map_solver], ids=["janus", "maps"])
-def test_allocation_failures_in_create_release_everything(make):
+def test_allocation_failures_in_create_release_everything(make, quiet_gc):
     """Host-side injection (nothing faults on the device): failing each device or pinned
     allocation of a create in turn returns ENOMEM and releases what the call had allocated;
     the handle that finally gets everything runs and equals an uninjected one, and so do
@@ -94,7 +105,7 @@ def test_allocation_failures_in_create_release_everything(make):
 
 
 @pytest.mark.parametrize("prec,shape", [("f32", (64, 8, 3)), ("f64", (64, 4, 2))], ids=["f32-two-step", "f64"])
-def test_allocation_failures_in_batch_create_release_everything(prec, shape):
+def test_allocation_failures_in_batch_create_release_everything(prec, shape, quiet_gc):
     insts = W.small_cases()
     live0 = L.alloc_fault_hook(0)
     b, failures = _fail_each_allocation(lambda: L.Batch(insts, prec, *shape), live0)
