@@ -65,7 +65,8 @@ def parse_args():
     p.add_argument("--profile-case", action="store_true",
                    help="small case for ncu: two launches of each step kernel on a 2048^2 lattice and of the FP64 step on the 512^2 workload")
     p.add_argument("--profile-only", default="",
-                   help="with --profile-case: only these form:mode pairs on the 2048^2 lattice (e.g. f32:four,f16dev:four)")
+                   help="with --profile-case: only these form:mode pairs (e.g. f32:four,f16dev:four)")
+    p.add_argument("--profile-n", type=int, default=2048, help="with --profile-only: the lattice size")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -321,7 +322,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def profile_case(only=""):
+def profile_case(only="", n=2048):
     """Two launches of each step kernel (FP64; FP32 and FP16-deviation with two steps per
     launch, then with one; double-float; FP32 with three steps per launch; FP32 and
     FP16-deviation with four) on a 2048^2 lattice (state 0.3-0.7 GB per buffer, larger than
@@ -331,8 +332,10 @@ def profile_case(only=""):
     from paper_2509_22308_gb300 import build as B
     B.build()
     from paper_2509_22308_gb300 import lbm_em as L
-    inst = dict(nx=2048, ny=2048, a=128.0, phi0=0.5, eps1=4.0, eps2=1.0, pec2=True, period=240, periods=1,
-                R=192.0, ramp=240)
+    if not only:
+        n = 2048
+    inst = dict(nx=n, ny=n, a=n / 16.0, phi0=0.5, eps1=4.0, eps2=1.0, pec2=True, period=240, periods=1,
+                R=0.09375 * n, ramp=240)
     pairs = (("f64", "auto"), ("f32", "two"), ("f16dev", "two"), ("f32", "one"), ("f16dev", "one"),
              ("f32x2", "auto"), ("f32", "three"), ("f32", "four"), ("f16dev", "four"))
     if only:
@@ -402,7 +405,7 @@ def main():
         run_reference(args, rank, world)
         return
     if args.profile_case:
-        profile_case(args.profile_only)
+        profile_case(args.profile_only, args.profile_n)
         return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

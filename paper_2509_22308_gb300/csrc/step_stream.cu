@@ -61,7 +61,7 @@ static_assert(IDBOX >= LW + 12 && IDBOX % 16 == 0, "the id box covers the strip 
 // from there on both forms read the same rows.
 template <bool F16>
 struct Layout {
-    static constexpr int RING = 5, KEEP = 2;
+    static constexpr int RING = 5;
     static constexpr size_t FLD = r128(ROWDEV);  // FP16 form: the field row, 128-byte aligned
     static_assert(FLD + ROWFLD <= ROW32, "the FP16 copies fit under the FP32 row they are rebuilt into");
     static constexpr size_t IDS = r128(ROW32);
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(NW * 32, 3)
         for (int j = 0; j < RING && ylo + j < yhi; ++j)
             issue_row<F16>(&smap, &fmap, &imap, xs, xid, ylo + j, ring + j * LY::SLOT, &bars[warp][j]);
 
-    Wave wa, wb;
+    Wave wa;
 #pragma unroll
     for (int k = 0; k < BT; ++k) {
         keep_row(wa.cur[k], Pop<float>{}, Pop<float>{});
@@ -467,20 +467,24 @@ __global__ void __launch_bounds__(NW * 32, 3)
         return true;
     };
 
-    // steady-state rows of an interior strip: every level computes and stores, no lattice edge
-    const int f0 = max(y0 + BT, BT + 1), f1 = xedge ? f0 : min(min(y1 + BT, yhi), ny);
+    // steady-state rows of an interior strip: every level computes and stores, no lattice edge.
+    // Measured on GB300 (8192^2, GLUPS): the FP16-deviation form gains from the separate path
+    // without edge tests (199.5 against 190.1), the FP32 form loses (196.9 against 220.4), so
+    // FP32 takes the general path for every row.  An L2 prefetch of the rows beyond the ring
+    // (cp.async.bulk.prefetch.tensor) lost in both forms (FP32 212.8 against 220.4, FP16 173.7
+    // against 199.5) and is not used.
+    const int f0 = max(y0 + BT, BT + 1), f1 = (xedge || !F16) ? f0 : min(min(y1 + BT, yhi), ny);
     int i = ylo;
     for (; i < f0 && i < y1 + BT; ++i)
         if (!row(std::false_type{}, i, wa, wa)) {
             timeout = true;
             break;
         }
-    for (; !timeout && i + 1 < f1; i += 2) {
-        if (!row(std::true_type{}, i, wa, wb) || !row(std::true_type{}, i + 1, wb, wa)) {
+    for (; !timeout && i < f1; ++i)
+        if (!row(std::true_type{}, i, wa, wa)) {
             timeout = true;
             break;
         }
-    }
     for (; !timeout && i < y1 + BT; ++i)
         if (!row(std::false_type{}, i, wa, wa)) {
             timeout = true;
