@@ -713,7 +713,7 @@ def main():
                 ms_l.append(a.elapsed_time(b))
             dclk = smp.stop()
             F, _ = bt.results()
-            res[fp] = (ms_l, F, bt.config(), dclk)
+            res[fp] = (ms_l, F, bt.config() + (bt.steps_per_launch(),), dclk)
             bt.close()
         ms32, F32, cfg, clk32 = res["f32"]
         ms64, F64, _, _ = res["f64"]
@@ -731,7 +731,8 @@ def main():
                                  float((np.max(np.abs(FX2 - F64), axis=1) / np.abs(F64[:, 0])).max()),
                              "max_force_err_drag_scale": float(errs.max()),
                              "instances_within_1e-3": int(np.sum(errs <= 1e-3)),
-                             "tile_w": cfg[0], "tile_h": cfg[1], "ctas_per_sm": cfg[2], "clocks": clk32,
+                             "tile_w": cfg[0], "tile_h": cfg[1], "ctas_per_sm": cfg[2], "steps_per_launch": cfg[3],
+                             "clocks": clk32,
                              "precision": "f32 lattice, f64 accumulation; error against the same batch in f64"}
 
     if not args.no_cpu_baseline and rank == 0 and world == 1:

@@ -78,9 +78,9 @@ typedef enum {
 } lbm_em_source_kind;
 
 /* lbm_em_grid.flags: how many time steps one kernel launch advances.  By default FP64 and
- * double-float advance one step per launch; FP32 and FP16-deviation two below 2^21 sites (each
- * tile and its halo are copied to shared memory by the TMA unit and advance two steps there)
- * and four from 2^21 sites on (each warp streams a strip of the lattice through four time
+ * double-float advance one step per launch; FP32 two below 2^21 sites and FP16-deviation two
+ * below 2^20 (each tile and its halo are copied to shared memory by the TMA unit and advance two
+ * steps there), four from there on (each warp streams a strip of the lattice through four time
  * levels held in registers).  The flags force a mode.  In FP32, FP64 and double-float the
  * result does not depend on the choice: every mode gives the same bits.  In FP16-deviation the
  * four-step mode rounds the stored state to FP16 once per launch instead of once per step, so
@@ -353,6 +353,13 @@ typedef struct {
     void *stream;            /* cudaStream_t; NULL: private stream                         */
     int32_t polarization;    /* 0: TM^z (E_z, H_x, H_y), the paper's case; 1: TE^z (H_z,
                                 E_x, E_y) for every instance (see LBM_EM_FLAG_TE)          */
+    int32_t steps_per_launch;/* 0: autotuned; 1, 2 or 4 pins the steps one launch advances.
+                                4 (FP32, conv_tol 0, nothing else pinned): persistent warps
+                                stream strips of 56 columns and row segments of every instance
+                                through four time levels held in registers (the autotuner picks
+                                the segment height, 64, 128 or 256 rows); same bits as one step
+                                per launch.  2: the TMA tile kernel above.  With 0 the
+                                autotuner times every kind that applies                    */
 } lbm_em_batch_opts;
 
 typedef struct lbm_em_batch lbm_em_batch_t;
@@ -387,9 +394,13 @@ lbm_em_status lbm_em_batch_results(lbm_em_batch_t *b, double *out, int32_t *stat
  * convergence exit when conv_tol > 0), steps[n].  Synchronous. */
 lbm_em_status lbm_em_batch_steps(lbm_em_batch_t *b, int64_t *steps);
 
-/* Chosen tile shape and CTAs per SM (after autotuning), for reporting. */
+/* Chosen tile shape and CTAs per SM (after autotuning), for reporting.  With four steps per
+ * launch: 56 (the strip width), the row-segment height and the kernel's blocks per SM. */
 lbm_em_status lbm_em_batch_config(lbm_em_batch_t *b, int32_t *tile_w, int32_t *tile_h,
                                   int32_t *ctas_per_sm);
+
+/* Steps one launch of the batch's chosen kernel advances (1, 2 or 4). */
+lbm_em_status lbm_em_batch_steps_per_launch(lbm_em_batch_t *b, int32_t *n);
 
 /* Release every resource of the batch (NULL is accepted): waits for the work queued on the
  * batch's stream, frees its device memory and graphs, and destroys the stream if the library

@@ -557,16 +557,17 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     // three steps per launch (28 x 12 tiles): forced by the flag only; the four-step kernel
     // replaced it as the default on large lattices
     h->t3 = (g->flags & LBM_EM_FLAG_THREE_STEP) != 0;
-    // four steps per launch (row-streaming kernel): forced by the flag, else the FP32 and
-    // FP16-deviation default from 2^21 sites on (measured on GB300, GLUPS four / two / three
-    // steps per launch, FP32: 8192^2 212.5 / 137.3 / 144.1, 4096^2 201.6 / 138.4 / 140.5, 2048^2
-    // 171.9 / 122.8 / 126.2, 1024^2 108.3 / 120.1 / 111.2, 512^2 31.9 / 67.6 / 68.7; FP16-deviation
-    // four / two: 182.8 / 115.4, 174.4 / 114.2, 151.5 / 105.6, 99.7 / 98.3, 29.0 / 58.3: on small
-    // lattices the strips cannot fill the GPU and the two-step kernel's state stays in L2); its
-    // accumulating periods run on the two-step tile kernel
+    // four steps per launch (row-streaming kernel): forced by the flag, else the default of FP32
+    // from 2^21 sites and of FP16-deviation from 2^20 sites on (measured on GB300, GLUPS four /
+    // two / three steps per launch, FP32: 8192^2 220.4 / 136.9 / 143.9, 4096^2 208.2 / 138.4 /
+    // 140.3, 2048^2 176.2 / 122.7 / 126.4, 1024^2 114.2 / 120.1 / 110.7, 512^2 33.5 / 70.3 / 70.0;
+    // FP16-deviation four / two: 198.2 / 115.5, 187.9 / 114.5, 160.4 / 105.5, 104.1 / 98.6,
+    // 30.5 / 58.3: on small lattices the strips cannot fill the GPU and the two-step kernel's
+    // state stays in L2); its accumulating periods run on the two-step tile kernel
     h->s4 = (g->flags & LBM_EM_FLAG_FOUR_STEP) != 0 ||
-            ((g->precision == LBM_EM_F32 || g->precision == LBM_EM_F16DEV) && !step_flags &&
-             (long long)g->nx * g->ny >= (1LL << 21));
+            (!step_flags && (long long)g->nx * g->ny >= (g->precision == LBM_EM_F32      ? (1LL << 21)
+                                                         : g->precision == LBM_EM_F16DEV ? (1LL << 20)
+                                                                                         : (1LL << 62)));
     if (h->s4) {
         h->t3 = false;
         h->tb = true;

@@ -30,6 +30,7 @@
 #include "runtime.h"
 #include "step2.cuh"
 #include "step2_tma.h"
+#include "step_stream.h"
 #include "tile_tma.cuh"
 
 using namespace lbmem;
@@ -340,6 +341,8 @@ __global__ void __launch_bounds__(NTH, 3)
     SrcPairF nsp{0.f, 0.f, 0.f, 0.f};  // thread 0: source values of the tile issued last
     auto issue = [&](int j, int slot) {  // thread 0: the copies of tile j, record into sc[slot]
         const int4 h = reinterpret_cast<const int4 *>(ctx + j)[0];  // inst, x0, y0
+        tmap_acquire(maps + 3 * h.x + p);
+        tmap_acquire(maps + 3 * h.x + 2);
         mbar_arrive_expect_tx(&bar, G::STATE_BYTES + G::ID_BYTES + (unsigned)sizeof(TileCtx));
         tma_load_3d(S.stage, maps + 3 * h.x + p, h.y - 4, h.z - 2, 0, &bar);
         tma_load_2d(S.stage + G::OFF_IDS, maps + 3 * h.x + 2, id_box_x(h.y), h.z - 2, &bar);
@@ -500,6 +503,17 @@ struct lbm_em_batch {
     TileCtx *d_ctx = nullptr;       // FP32: one record per tile of the tile list
     SrcPairF *d_srcs = nullptr;     // FP32: per instance, the source values of the current launch
     int two_ctas[3] = {0, 0, 0};
+    // four steps per launch (FP32, fixed run lengths): row-streaming kernel over work units
+    // (instance, strip, row segment of four_seg rows), per-instance records, tensor maps and
+    // source parameters, and the source values of the current launch
+    bool four = false;
+    int four_seg = 0, four_grid = 0, n_units = 0;
+    int4 *d_units = nullptr;
+    StreamInst *d_sinsts = nullptr;
+    SourceParams *d_srcp = nullptr;
+    SrcLevels *d_srcs4 = nullptr;
+    CUtensorMap *d_smaps4 = nullptr;
+    int want_spl = 0;  // lbm_em_batch_opts.steps_per_launch
     cudaGraphExec_t graph = nullptr;
     bool ran = false;
     // a bounded wait for a tile copy gave up (seen by lbm_em_batch_results): a copy may
@@ -536,6 +550,11 @@ static void batch_free(lbm_em_batch *b) {
     for (CUtensorMap *m : b->d_maps) dfree(m);
     dfree(b->d_ctx);
     dfree(b->d_srcs);
+    dfree(b->d_units);
+    dfree(b->d_sinsts);
+    dfree(b->d_srcp);
+    dfree(b->d_srcs4);
+    dfree(b->d_smaps4);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -580,6 +599,48 @@ static lbm_em_status batch_tiles(lbm_em_batch *b, int tw, int th) {
                                              cudaMemcpyHostToDevice, b->stream),
                              "uploading tile records");  // pageable: staged before the call returns
     }
+    return st;
+}
+
+// The four-step kernel's work units for row segments of `seg` rows: instance by decreasing run
+// length, then segment, then strip (neighbouring strips run side by side and share their halo
+// columns in L2); and the per-instance records with that segment height.
+static lbm_em_status batch_units(lbm_em_batch *b, int seg) {
+    std::vector<int4> units;
+    std::vector<StreamInst> si(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        const InstDesc &d = b->desc[i];
+        StreamInst &r = si[i];
+        std::memset(&r, 0, sizeof(r));
+        r.nx = d.nx, r.ny = d.ny, r.pitch = d.pitch, r.kind = d.src.kind;
+        r.seg_rows = seg, r.n_strips = (d.nx + kStreamOutW - 1) / kStreamOutW, r.ay0 = d.y0, r.ay1 = d.y1;
+        r.steps = d.steps, r.acc_from = d.acc_from, r.base = (long long)d.base, r.pstride = (long long)d.pstride;
+        r.slot_base = (long long)d.slot_base, r.acc_base = d.acc_base, r.period = d.period;
+        r.cs = d.src.cs;
+        r.runaway = runaway_bits<float>(b->specs[i].E0);
+        for (int q = 0; q < 3; ++q) r.m[q] = d.mtabf[q];
+    }
+    for (long long ii : b->order) {
+        const int i = (int)ii;
+        for (int y = 0; y < b->desc[i].ny; y += seg)
+            for (int st = 0; st < si[i].n_strips; ++st) units.push_back(make_int4(i, st, y / seg, 0));
+    }
+    dfree(b->d_units);
+    b->d_units = nullptr;
+    lbm_em_status st = cuda_status(dmalloc(&b->d_units, units.size() * sizeof(int4)), "cudaMalloc(units)");
+    if (!st)
+        st = cuda_status(copy_async(b->d_units, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                    b->stream),
+                         "uploading units");
+    if (!st && !b->d_sinsts)
+        st = cuda_status(dmalloc(&b->d_sinsts, si.size() * sizeof(StreamInst)), "cudaMalloc(stream records)");
+    if (!st)
+        st = cuda_status(copy_async(b->d_sinsts, si.data(), si.size() * sizeof(StreamInst), cudaMemcpyHostToDevice,
+                                    b->stream),
+                         "uploading stream records");
+    if (!st) st = cuda_status(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");  // pageable sources
+    b->n_units = (int)units.size();
+    b->four_seg = seg;
     return st;
 }
 
@@ -642,7 +703,11 @@ static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, int p) {
         BatchArgs<float> a{b->d_desc, b->d_tiles, b->n_tiles, b->tile_w, b->tile_h, ilog2(b->tile_w),
                            (const float *)b->buf[p], (float *)b->buf[1 - p], b->d_mat, b->d_slot,
                            b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
-        if (b->two) {
+        if (b->four) {
+            launch_batch_step4(b->d_sinsts, b->d_srcp, b->n, b->d_units, b->n_units, b->d_srcs4, b->d_smaps4, p,
+                               (float *)b->buf[1 - p], b->d_slot, b->d_acc, b->d_err, b->d_time + p,
+                               b->d_time + (1 - p), b->four_grid, b->pol, s);
+        } else if (b->two) {
             k_batch_source<<<(b->n + 127) / 128, 128, 0, s>>>(b->d_desc, b->n, b->d_time + p, b->d_srcs);
             if (b->pol == POL_TE)
                 launch_batch_step2<POL_TE>(b, a, grid, p, s);
@@ -663,14 +728,19 @@ static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, int p) {
     return e;
 }
 
-// A single step with the one-step kernel (the odd tail of a two-step run).
+// A single step with the one-step kernel (the tail of a multi-step run).
 static cudaError_t batch_launch_one(lbm_em_batch *b, cudaStream_t s, int p) {
-    const bool two = b->two;
+    const bool two = b->two, four = b->four;
     b->two = false;
+    b->four = false;
     cudaError_t e = batch_launch(b, s, p);
     b->two = two;
+    b->four = four;
     return e;
 }
+
+// Steps one launch of the batch's configuration advances.
+static int batch_spl(const lbm_em_batch *b) { return b->four ? 4 : b->two ? 2 : 1; }
 
 static lbm_em_status batch_clear(lbm_em_batch *b) {
     lbm_em_status st = cuda_status(cudaMemsetAsync(b->buf[0], 0, b->buf_elems * b->elem, b->stream), "clear");
@@ -690,56 +760,65 @@ static lbm_em_status batch_clear(lbm_em_batch *b) {
 }
 
 // Time a few steps of each (tile shape, CTAs per SM, steps per launch) candidate from the
-// cleared state; two steps per launch (TMA-staged 64 x 8, 32 x 16 and 40 x 12 tiles, as many CTAs
-// per SM as their shared memory allows) is a candidate for FP32 runs of fixed length.
+// cleared state.  FP32 runs of fixed length also have the two-step kernel (TMA-staged 64 x 8,
+// 32 x 16 and 40 x 12 tiles, as many CTAs per SM as their shared memory allows) and the
+// four-step row-streaming kernel (row segments of 64, 128 or 256 rows; its runs end with
+// one-step launches on 64 x 4 tiles).  lbm_em_batch_opts.steps_per_launch restricts the
+// candidates to one kind; a pinned tile shape or CTA count to the matching ones.
 static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int want_c) {
     struct Cand {
-        int w, h, c;
-        bool two;
+        int w, h, c, spl, seg;
     };
     std::vector<Cand> cands;
+    const bool pinned = want_w || want_h || want_c;
+    const bool multi = b->prec == LBM_EM_F32 && b->conv_tol <= 0.0;
+    if (multi && b->four_grid > 0 && !pinned && (b->want_spl == 0 || b->want_spl == 4))
+        for (int seg : {64, 128, 256}) cands.push_back(Cand{64, 4, 4, 4, seg});
     const int two_shapes[3][2] = {{GeoWide::KW, GeoWide::KH}, {GeoTall::KW, GeoTall::KH}, {GeoMid::KW, GeoMid::KH}};
     for (int g = 0; g < 3; ++g) {
         const int w = two_shapes[g][0], h = two_shapes[g][1], c = b->two_ctas[g];
-        if (c > 0 && b->conv_tol <= 0.0 && (!want_w || want_w == w) && (!want_h || want_h == h) &&
-            (!want_c || want_c == c))
-            cands.push_back(Cand{w, h, c, true});
+        if (c > 0 && multi && (b->want_spl == 0 || b->want_spl == 2) && (!want_w || want_w == w) &&
+            (!want_h || want_h == h) && (!want_c || want_c == c))
+            cands.push_back(Cand{w, h, c, 2, 0});
     }
     // One step per launch moves twice the bytes per update; on GB300 it lost to every two-step
-    // shape on every FP32 map measured, so with nothing pinned by the caller only the two-step
-    // shapes are timed when they apply (they do not for FP64, double-float or convergence exits).
-    const bool only_two = !cands.empty() && !want_w && !want_h && !want_c;
+    // shape on every FP32 map measured, so with nothing pinned by the caller only the multi-step
+    // candidates are timed when they apply (they do not for FP64, double-float or convergence exits).
+    const bool only_multi = !cands.empty() && !pinned && b->want_spl != 1;
     const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 8}, {128, 4}, {256, 2}, {128, 8}, {256, 4}};
     const int ctas[] = {2, 4, 8};
-    for (auto &sh : shapes)
-        for (int c : ctas) {
-            if (only_two) break;
-            if (want_w && sh[0] != want_w) continue;
-            if (want_h && sh[1] != want_h) continue;
-            if (want_c && c != want_c) continue;
-            cands.push_back(Cand{sh[0], sh[1], c, false});
-        }
-    if (cands.empty()) cands.push_back(Cand{want_w ? want_w : 64, want_h ? want_h : 4, want_c ? want_c : 4, false});
-    if (cands.size() == 1) {
-        b->ctas = cands[0].c;
-        b->two = cands[0].two;
-        return batch_tiles(b, cands[0].w, cands[0].h);
-    }
+    if (b->want_spl == 0 || b->want_spl == 1)
+        for (auto &sh : shapes)
+            for (int c : ctas) {
+                if (only_multi) break;
+                if (want_w && sh[0] != want_w) continue;
+                if (want_h && sh[1] != want_h) continue;
+                if (want_c && c != want_c) continue;
+                cands.push_back(Cand{sh[0], sh[1], c, 1, 0});
+            }
+    if (cands.empty()) cands.push_back(Cand{want_w ? want_w : 64, want_h ? want_h : 4, want_c ? want_c : 4, 1, 0});
+    auto apply = [&](const Cand &c) {
+        b->ctas = c.c;
+        b->two = c.spl == 2;
+        b->four = c.spl == 4;
+        lbm_em_status st = batch_tiles(b, c.w, c.h);
+        if (!st && b->four) st = batch_units(b, c.seg);
+        return st;
+    };
+    if (cands.size() == 1) return apply(cands[0]);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
     Cand bc = cands[0];
-    const int trial = 4;  // steps timed per candidate
+    const int trial = 8;  // steps timed per candidate
     lbm_em_status st = LBM_EM_OK;
     for (const Cand &c : cands) {
-        b->ctas = c.c;
-        b->two = c.two;
-        st = batch_tiles(b, c.w, c.h);
+        st = apply(c);
         if (st) break;
         st = batch_clear(b);
         if (st) break;
-        const int launches = c.two ? trial / 2 : trial;
+        const int launches = trial / c.spl;
         cudaError_t e = batch_launch(b, b->stream, 0);  // warm-up
         cudaEventRecord(e0, b->stream);
         for (int k = 1; k <= launches && e == cudaSuccess; ++k) e = batch_launch(b, b->stream, k & 1);
@@ -757,9 +836,7 @@ static lbm_em_status batch_autotune(lbm_em_batch *b, int want_w, int want_h, int
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st) return st;
-    b->ctas = bc.c;
-    b->two = bc.two;
-    st = batch_tiles(b, bc.w, bc.h);
+    st = apply(bc);
     if (!st) st = batch_clear(b);
     return st;
 }
@@ -782,6 +859,12 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
     if (o->polarization != 0 && o->polarization != 1)
         return set_error(LBM_EM_EINVAL, "polarization must be 0 (TM^z) or 1 (TE^z)");
     if (o->tile_h && (o->tile_h > 16)) return set_error(LBM_EM_EINVAL, "tile_h must be <= 16");
+    if (o->steps_per_launch != 0 && o->steps_per_launch != 1 && o->steps_per_launch != 2 && o->steps_per_launch != 4)
+        return set_error(LBM_EM_EINVAL, "steps_per_launch must be 0, 1, 2 or 4");
+    if ((o->steps_per_launch == 2 || o->steps_per_launch == 4) && (o->precision != LBM_EM_F32 || o->conv_tol > 0.0))
+        return set_error(LBM_EM_EINVAL, "two and four steps per launch are for LBM_EM_F32 without convergence exits");
+    if (o->steps_per_launch == 4 && (o->tile_w || o->tile_h || o->ctas_per_sm))
+        return set_error(LBM_EM_EINVAL, "four steps per launch take no tile shape or CTA count");
     for (int i = 0; i < n; ++i) {
         const lbm_em_instance &s = specs[i];
         if (s.nx < 4 || s.ny < 4 || s.period_steps < 4 || s.periods < 1 || s.ramp_steps < 0 || !std::isfinite(s.E0))
@@ -923,6 +1006,7 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
     BTRY(dmalloc(&b->d_settled, n * sizeof(int)), "cudaMalloc(energy)");
     b->conv_tol = o->conv_tol;
     b->min_periods = o->min_periods > 0 ? o->min_periods : 1;
+    b->want_spl = o->steps_per_launch;
     BTRY(copy_async(b->d_cs, cs_all.data(), cs_all.size() * sizeof(double2), cudaMemcpyHostToDevice, b->stream), "upload");
     for (int i = 0; i < n; ++i) b->desc[i].src.cs = b->d_cs + cs_off[i];
     BTRY(copy_async(b->d_desc, b->desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice, b->stream), "upload");
@@ -984,6 +1068,31 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
             b->two_ctas[g] = per_sm;
         }
         BTRY(dmalloc(&b->d_srcs, (size_t)n * sizeof(SrcPairF)), "cudaMalloc(source values)");
+        // the four-step kernel: per instance the three tensor maps of its rows, its source
+        // parameters, room for a launch's source values
+        if (o->conv_tol <= 0.0 && (o->steps_per_launch == 0 || o->steps_per_launch == 4)) {
+            int warps = 0;
+            BTRY(batch_stream_prepare(&warps), "configuring the four-step batch kernel");
+            b->four_grid = warps / kStreamWarps;
+            std::vector<CUtensorMap> maps(3 * (size_t)n);
+            std::vector<SourceParams> sp(n);
+            for (int i = 0; i < n; ++i) {
+                const InstDesc &d = b->desc[i];
+                BTRY(encode_batch_stream_maps(&maps[3 * i], (const float *)b->buf[0] + d.base,
+                                              (const float *)b->buf[1] + d.base, b->d_mat + d.mat_base, d.nx, d.ny,
+                                              d.pitch, d.pstride),
+                     "encoding an instance's row maps");
+                sp[i] = d.src;
+            }
+            BTRY(dmalloc(&b->d_smaps4, maps.size() * sizeof(CUtensorMap)), "cudaMalloc(row maps)");
+            BTRY(copy_async(b->d_smaps4, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                            b->stream),
+                 "upload");
+            BTRY(dmalloc(&b->d_srcp, (size_t)n * sizeof(SourceParams)), "cudaMalloc(source parameters)");
+            BTRY(copy_async(b->d_srcp, sp.data(), sp.size() * sizeof(SourceParams), cudaMemcpyHostToDevice, b->stream),
+                 "upload");
+            BTRY(dmalloc(&b->d_srcs4, (size_t)n * sizeof(SrcLevels)), "cudaMalloc(source values)");
+        }
     }
     // rasterise every instance on the device (again at every run)
     BTRY(batch_rasterize(b), "rasterise");
@@ -1008,7 +1117,9 @@ lbm_em_status lbm_em_batch_run(lbm_em_batch_t *b) {
     if (b->timed_out)
         return set_error(LBM_EM_ESTATE, "a tile copy timed out in this batch: destroy it and create a new one");
     cudaSetDevice(b->dev);
-    lbm_em_status st = b->ran ? batch_clear(b) : LBM_EM_OK;
+    // every run starts from the cleared state, the first one too: a batch whose tuning had a
+    // single candidate has never cleared its buffers, which hold what freed allocations left
+    lbm_em_status st = batch_clear(b);
     if (!st) st = cuda_status(batch_rasterize(b), "rasterise");
     if (st) return st;
     if (!b->graph) {
@@ -1027,9 +1138,9 @@ lbm_em_status lbm_em_batch_run(lbm_em_batch_t *b) {
         st = cuda_status(e, "cudaGraphInstantiate");
         if (st) return st;
     }
-    // the graph holds two launches (state buf[0] -> buf[1] -> buf[0]): 2 steps, or 4 with
-    // two steps per launch; the tail runs at most one two-step and one one-step launch
-    const long long per_graph = b->two ? 4 : 2;
+    // the graph holds two launches (state buf[0] -> buf[1] -> buf[0]) of spl steps each; the
+    // tail runs at most one more multi-step launch and then one-step launches
+    const long long spl = batch_spl(b), per_graph = 2 * spl;
     long long t = 0;
     int p = 0;
     while (t + per_graph <= b->max_steps) {
@@ -1037,15 +1148,17 @@ lbm_em_status lbm_em_batch_run(lbm_em_batch_t *b) {
         if (st) return st;
         t += per_graph;
     }
-    if (b->two && t + 2 <= b->max_steps) {
+    if (spl > 1 && t + spl <= b->max_steps) {
         st = cuda_status(batch_launch(b, b->stream, p), "batch step");
         if (st) return st;
         p ^= 1;
-        t += 2;
+        t += spl;
     }
-    if (t < b->max_steps) {
+    while (t < b->max_steps) {
         st = cuda_status(batch_launch_one(b, b->stream, p), "batch step");
         if (st) return st;
+        p ^= 1;
+        ++t;
     }
     k_batch_contour<<<b->n, 256, 0, b->stream>>>(b->d_cdesc, b->d_pts, b->d_acc, b->d_out);
     st = cuda_status(cudaGetLastError(), "batch contour");
@@ -1097,9 +1210,21 @@ lbm_em_status lbm_em_batch_steps(lbm_em_batch_t *b, int64_t *steps) {
 
 lbm_em_status lbm_em_batch_config(lbm_em_batch_t *b, int32_t *tile_w, int32_t *tile_h, int32_t *ctas_per_sm) {
     if (!b) return set_error(LBM_EM_EINVAL, "batch is NULL");
+    if (b->four) {  // the four-step kernel: strips of 56 output columns, row segments, its blocks per SM
+        if (tile_w) *tile_w = kStreamOutW;
+        if (tile_h) *tile_h = b->four_seg;
+        if (ctas_per_sm) *ctas_per_sm = b->four_grid / b->sms;
+        return LBM_EM_OK;
+    }
     if (tile_w) *tile_w = b->tile_w;
     if (tile_h) *tile_h = b->tile_h;
     if (ctas_per_sm) *ctas_per_sm = b->ctas;
+    return LBM_EM_OK;
+}
+
+lbm_em_status lbm_em_batch_steps_per_launch(lbm_em_batch_t *b, int32_t *n) {
+    if (!b || !n) return set_error(LBM_EM_EINVAL, "NULL argument");
+    *n = batch_spl(b);
     return LBM_EM_OK;
 }
 

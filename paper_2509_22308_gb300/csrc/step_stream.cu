@@ -74,9 +74,6 @@ struct Layout {
 static_assert(3 * (Layout<false>::SMEM + 1024 + 256) <= 233472 && 3 * (Layout<true>::SMEM + 1024 + 256) <= 233472,
               "three blocks per SM");
 
-struct SrcLevels {
-    float g[BT], inc[BT];
-};
 // Not inlined, called by one thread: see source_pair_f.
 static __device__ __noinline__ SrcLevels source_levels_f(const SourceParams src, long long t) {
     SrcLevels v;
@@ -187,24 +184,6 @@ __device__ __forceinline__ void store2(float *p, bool two, float a, float b) {
         *p = a;
 }
 
-// FP32 store of level 4 of row q: 11 planes, two sites (one at an odd lattice's last column).
-__device__ __forceinline__ void store_row32(const StreamArgs &a, size_t idx, bool two, const Pop<float> &pa,
-                                            const Pop<float> &pb) {
-    float *f = a.fout + idx;
-    const size_t ps = a.pstride;
-    store2(f + P_EZ * ps, two, pa.ez, pb.ez);
-    store2(f + P_EPX * ps, two, pa.epx, pb.epx);
-    store2(f + P_EMX * ps, two, pa.emx, pb.emx);
-    store2(f + P_EPY * ps, two, pa.epy, pb.epy);
-    store2(f + P_EMY * ps, two, pa.emy, pb.emy);
-    store2(f + P_HXPX * ps, two, pa.hxpx, pb.hxpx);
-    store2(f + P_HXMX * ps, two, pa.hxmx, pb.hxmx);
-    store2(f + P_HXZ * ps, two, pa.hxz, pb.hxz);
-    store2(f + P_HYPY * ps, two, pa.hypy, pb.hypy);
-    store2(f + P_HYMY * ps, two, pa.hymy, pb.hymy);
-    store2(f + P_HYZ * ps, two, pa.hyz, pb.hyz);
-}
-
 // Time levels 1..3 of the wavefront: per level the kept row (row i - 1 - k when row i arrives,
 // 9 populations), the +y pair of the row before it, and the ids of row i - 1 - k.  Level 0 lives
 // in the ring; index 0 of these arrays is unused.
@@ -215,10 +194,9 @@ struct Wave {
 };
 
 // One row of level 0 from a slot: FP32 as staged; FP16-deviation rebuilt in place first (see
-// Layout).  Returns the two ids of the row.
+// Layout).
 template <bool F16>
-__device__ __forceinline__ unsigned take_row(unsigned char *sl, int idoff, int lane, float inv_scale) {
-    const unsigned id = *reinterpret_cast<const unsigned short *>(sl + Layout<F16>::IDS + idoff + 2 * lane);
+__device__ __forceinline__ void take_row(unsigned char *sl, int lane, float inv_scale) {
     if constexpr (F16) {
         const __half *dv = reinterpret_cast<const __half *>(sl) + DEVOFF;
         const float *fl = reinterpret_cast<const float *>(sl + Layout<F16>::FLD);
@@ -251,58 +229,100 @@ __device__ __forceinline__ unsigned take_row(unsigned char *sl, int idoff, int l
         row[P_HYZ * 32 + lane] = make_float2(na.hyz, nb.hyz);
         // each lane reads back only its own two sites (neighbours come by shuffles)
     }
-    return id;
 }
 
-// F16: the FP16-deviation form (TM); otherwise FP32 of either polarization.
-template <bool F16, int POL>
-__global__ void __launch_bounds__(NW * 32, 3)
-    k_step4_stream(const StreamArgs a, const __grid_constant__ CUtensorMap smap,
-                   const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap imap,
-                   const long long *__restrict__ t_in, long long *__restrict__ t_out) {
+// What a warp needs of the lattice it works on: sizes, outputs and (ACC) the Fourier
+// accumulation of times acc_from <= t' < steps at the rows ay0 .. ay1.  The single-domain
+// kernel receives it as a grid-constant parameter, so its fields are read from the constant
+// bank instead of taking registers; the batch kernel keeps the current instance's in shared
+// memory.
+struct UnitCtx {
+    int nx, ny, pitch, kind;
+    unsigned runaway;
+    int ay0, ay1, period;
+    size_t pstride;
+    float scale, inv_scale;                       // FP16-deviation form
+    float *fout;                                  // FP32: the output state (11 planes)
+    __half *g_out;                                // FP16-deviation: output planes
+    float *fe_out, *fhx_out, *fhy_out;
+    long long acc_from, steps;
+    const int *slot;                              // the lattice's slot map (pitch layout)
+    double *acc;                                  // its accumulators (6 per slot)
+    const double2 *cs;                            // (cos w t, sin w t) for t mod period
+};
+
+// One work unit: a strip of the lattice (columns xs .. xs + 63, 16-byte aligned) and a segment
+// of rows (output rows y0 .. y1 - 1), from the stored state of time t - 1 to time t + 3; the
+// tensor maps of the input state and ids, the material constants by id (shared memory) and the
+// source values of the launch's four times.
+struct UnitRun {
+    int xs, y0, y1;
+    long long t;
+    const CUtensorMap *smap, *fmap, *imap;
+    const MatT<float> *table;
+    const float *src_g, *src_inc;
+};
+
+// A warp's row ring: the slot of the next row to arrive and the parity its barrier completes
+// with.  Slots are used strictly in turn, unit after unit.
+struct RingState {
+    unsigned char *ring;
+    uint64_t *bars;
+    float4 *edge;
+    int s0;
+    unsigned ph;
+};
+
+// Adds the phasor terms of one owned site at time tk (Sec. III: Fourier analysis over one
+// period) to its accumulators, when the site is a contour stencil site.
+__device__ __forceinline__ void acc_owned(const UnitCtx &u, int x, int q, long long tk, const double f3[3]) {
+    const int sl = u.slot[(size_t)q * u.pitch + x];
+    if (sl < 0) return;
+    const double2 c = u.cs[(int)(tk % (long long)u.period)];
+    double *a = u.acc + 6 * (size_t)sl;
+    a[0] += f3[0] * c.x;
+    a[1] += f3[0] * c.y;
+    a[2] += f3[1] * c.x;
+    a[3] += f3[1] * c.y;
+    a[4] += f3[2] * c.x;
+    a[5] += f3[2] * c.y;
+}
+
+// Four steps of one work unit (see the top of this file).  Returns false after a bounded wait
+// for a row copy gave up.  bad: set when a stored site's field ran away.
+template <bool F16, int POL, bool ACC>
+__device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, RingState &R, bool &bad) {
+    static_assert(!(F16 && ACC), "the FP16-deviation kernel does not accumulate");
     using LY = Layout<F16>;
     constexpr int RING = LY::RING;
-    extern __shared__ unsigned char sm_dyn[];
-    __shared__ __align__(8) uint64_t bars[NW][RING];
-    __shared__ SrcLevels sp;
-    unsigned char *s = sm_dyn + ((128u - (smem_u32(sm_dyn) & 127u)) & 127u);
-    MatT<float> *table = reinterpret_cast<MatT<float> *>(s);
-    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
-    unsigned char *ring = s + LY::TABLE + (size_t)warp * LY::WARP;
-    float4 *edge = reinterpret_cast<float4 *>(ring + RING * LY::SLOT);  // [BT][32]
-
-    const long long t = *t_in;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + BT;
-    if (threadIdx.x == 0) sp = source_levels_f(a.src, t);
-    for (int k = threadIdx.x; k < 256; k += NW * 32) table[k] = a.mtab[k];
-    if (lane == 0) {
-        for (int j = 0; j < RING; ++j) mbar_init(&bars[warp][j], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();  // the only block-wide barrier: from here on each warp runs alone
-    const int unit = (int)blockIdx.x * NW + warp;
-    if (unit >= a.n_units) return;
-    const int nx = a.nx, ny = a.ny;
-    const int strip = unit % a.n_strips, seg = unit / a.n_strips;
-    const int xs = strip * OUTW - HALO;         // first staged column (a multiple of 4)
-    const int xid = xs & ~15, idoff = xs - xid;  // first column of the id box, xs in it
-    const int xa = xs + 2 * lane, xb = xa + 1;  // this lane's sites
-    const int y0 = seg * a.seg_rows, y1 = min(y0 + a.seg_rows, ny);
+    const int lane = (int)threadIdx.x & 31;
+    unsigned char *const ring = R.ring;
+    uint64_t *const bars = R.bars;
+    float4 *const edge = R.edge;
+    const int nx = u.nx, ny = u.ny, xs = r.xs;
+    const int xid = xs & ~15, idoff = xs - xid;   // first column of the id box, xs in it
+    const int xa = xs + 2 * lane, xb = xa + 1;    // this lane's sites
+    const int y0 = r.y0, y1 = r.y1;
     const int ylo = max(y0 - BT, 0), yhi = min(y1 + BT, ny);
     const bool xa0 = xa == 0, xa_last = xa == nx - 1, xb_last = xb == nx - 1;
     // the strip's staged columns include a lattice edge: edge clamps (any lane) and the source
     const bool xedge = xs <= 0 || xs + LW - 1 >= nx - 1;
     const bool out_lane = lane >= HALO / 2 && lane < 32 - HALO / 2 && xa >= 0 && xa < nx;
     const bool two = xb < nx;
-    const int kind = a.src.kind;
+    const int kind = u.kind;
     const bool src_lane = xa0 && kind != SRC_NONE;
-    const size_t ps = a.pstride;
-    const float inv_scale = a.inv_scale;
+    const size_t ps = u.pstride;
+    const long long t = r.t;
 
+    // ring slots of rows i, i - 1, i - 2 and the barrier phase of row i
+    int s0 = R.s0, s1 = s0 == 0 ? RING - 1 : s0 - 1, s2 = s1 == 0 ? RING - 1 : s1 - 1;
+    unsigned ph = R.ph;
     // prologue: the first RING rows in flight
     if (lane == 0)
-        for (int j = 0; j < RING && ylo + j < yhi; ++j)
-            issue_row<F16>(&smap, &fmap, &imap, xs, xid, ylo + j, ring + j * LY::SLOT, &bars[warp][j]);
+        for (int j = 0; j < RING && ylo + j < yhi; ++j) {
+            const int sj = (s0 + j) % RING;
+            issue_row<F16>(r.smap, r.fmap, r.imap, xs, xid, ylo + j, ring + (size_t)sj * LY::SLOT, &bars[sj]);
+        }
 
     Wave wa;
 #pragma unroll
@@ -311,10 +331,6 @@ __global__ void __launch_bounds__(NW * 32, 3)
         wa.oe[k][0] = wa.oe[k][1] = wa.oh[k][0] = wa.oh[k][1] = 0.f;
         wa.ids[k] = 0u;
     }
-    bool bad = false, timeout = false;
-    // ring slots of rows i, i - 1, i - 2 and the barrier phase of row i (rows arrive in order)
-    int s0 = 0, s1 = RING - 1, s2 = RING - 2;
-    unsigned ph = 0;
 
     // One wavefront row: row i arrives as level 0; level k + 1 of row q = i - 1 - k is computed
     // from level k of rows q - 1, q and q + 1 (k = 0 from the ring, k >= 1 from `in`); `out`
@@ -325,9 +341,9 @@ __global__ void __launch_bounds__(NW * 32, 3)
         constexpr bool FAST = decltype(fast_tag)::value;
         // level 0 of row i
         if (FAST || i < yhi) {
-            const bool ok = mbar_wait(&bars[warp][s0], ph);
+            const bool ok = mbar_wait(&bars[s0], ph);
             if (__any_sync(0xffffffffu, !ok)) return false;
-            take_row<F16>(ring + (size_t)s0 * LY::SLOT, idoff, lane, inv_scale);
+            take_row<F16>(ring + (size_t)s0 * LY::SLOT, lane, u.inv_scale);
         }
         Pop<float> na{}, nb{};  // level k of row i - k, the -y pair for level k + 1
         bool have = FAST || i < yhi;
@@ -389,42 +405,68 @@ __global__ void __launch_bounds__(NW * 32, 3)
                         pull_row(in.cur[k], ey, hy, my, mh, xa0, xa_last, xb_last, ca, cb);
                     idq = in.ids[k];
                 }
-                if (!FAST && src_lane && t + k >= 1) inject_source_t(kind, sp.g[k], sp.inc[k], ca);
-                const MatT<float> ma = table[idq & 0xffu], mb = table[(idq >> 8) & 0xffu];
-                const bool store = k == BT - 1 && out_lane && (FAST || (q >= y0 && q < y1));
+                if (!FAST && src_lane && t + k >= 1) inject_source_t(kind, r.src_g[k], r.src_inc[k], ca);
+                const MatT<float> ma = r.table[idq & 0xffu], mb = r.table[(idq >> 8) & 0xffu];
+                const bool owned = out_lane && (FAST || (q >= y0 && q < y1));
+                const bool store = k == BT - 1 && owned;
                 if (F16 && k == BT - 1) {
                     // the stored state of the last level: fields and FP16 deviations g = f - f^eq
                     float E3a, Hxa, Hya, Da, E3b, Hxb, Hyb, Db;
                     moments(ca, ma, &E3a, &Hxa, &Hya, &Da);
                     moments(cb, mb, &E3b, &Hxb, &Hyb, &Db);
                     if (store) {
-                        bad |= field_runaway(E3a, a.runaway) || (two && field_runaway(E3b, a.runaway));
+                        bad |= field_runaway(E3a, u.runaway) || (two && field_runaway(E3b, u.runaway));
                         const Fld Fa = stored_fields(E3a, Hxa, Hya), Fb = stored_fields(E3b, Hxb, Hyb);
                         __half ga[NPLANES], gb[NPLANES];
-                        encode_all(ca, Fa, a.scale, ga);
-                        encode_all(cb, Fb, a.scale, gb);
-                        const size_t idx = (size_t)q * a.pitch + xa;
+                        encode_all(ca, Fa, u.scale, ga);
+                        encode_all(cb, Fb, u.scale, gb);
+                        const size_t idx = (size_t)q * u.pitch + xa;
                         if (two) {
 #pragma unroll
                             for (int p = 0; p < NPLANES; ++p)
-                                *reinterpret_cast<__half2 *>(a.g_out + p * ps + idx) = __halves2half2(ga[p], gb[p]);
-                            *reinterpret_cast<float2 *>(a.fe_out + idx) = make_float2(Fa.e, Fb.e);
-                            *reinterpret_cast<float2 *>(a.fhx_out + idx) = make_float2(Fa.hx, Fb.hx);
-                            *reinterpret_cast<float2 *>(a.fhy_out + idx) = make_float2(Fa.hy, Fb.hy);
+                                *reinterpret_cast<__half2 *>(u.g_out + p * ps + idx) = __halves2half2(ga[p], gb[p]);
+                            *reinterpret_cast<float2 *>(u.fe_out + idx) = make_float2(Fa.e, Fb.e);
+                            *reinterpret_cast<float2 *>(u.fhx_out + idx) = make_float2(Fa.hx, Fb.hx);
+                            *reinterpret_cast<float2 *>(u.fhy_out + idx) = make_float2(Fa.hy, Fb.hy);
                         } else {
 #pragma unroll
-                            for (int p = 0; p < NPLANES; ++p) a.g_out[p * ps + idx] = ga[p];
-                            a.fe_out[idx] = Fa.e;
-                            a.fhx_out[idx] = Fa.hx;
-                            a.fhy_out[idx] = Fa.hy;
+                            for (int p = 0; p < NPLANES; ++p) u.g_out[p * ps + idx] = ga[p];
+                            u.fe_out[idx] = Fa.e;
+                            u.fhx_out[idx] = Fa.hx;
+                            u.fhy_out[idx] = Fa.hy;
                         }
                     }
                 } else {
-                    const bool ra = update_site<POL, true>(ca, ma, a.runaway, nullptr, nullptr);
-                    const bool rb = update_site<POL, true>(cb, mb, a.runaway, nullptr, nullptr);
+                    bool ra, rb;
+                    if (ACC && t + k >= u.acc_from && t + k < u.steps && q >= u.ay0 && q <= u.ay1 &&
+                        (FAST || (q >= y0 && q < y1))) {
+                        // a row of contour stencil sites in the accumulated period (uniform over the
+                        // warp): the fields of the owned sites enter their Fourier sums
+                        double f3a[3], f3b[3];
+                        ra = update_site<POL, true>(ca, ma, u.runaway, f3a, nullptr);
+                        rb = update_site<POL, true>(cb, mb, u.runaway, f3b, nullptr);
+                        if (out_lane) {
+                            acc_owned(u, xa, q, t + k, f3a);
+                            if (two) acc_owned(u, xb, q, t + k, f3b);
+                        }
+                    } else {
+                        ra = update_site<POL, true>(ca, ma, u.runaway, nullptr, nullptr);
+                        rb = update_site<POL, true>(cb, mb, u.runaway, nullptr, nullptr);
+                    }
                     if (store) {
                         bad |= ra || (two && rb);
-                        store_row32(a, (size_t)q * a.pitch + xa, two, ca, cb);
+                        float *f = u.fout + (size_t)q * u.pitch + xa;
+                        store2(f + P_EZ * ps, two, ca.ez, cb.ez);
+                        store2(f + P_EPX * ps, two, ca.epx, cb.epx);
+                        store2(f + P_EMX * ps, two, ca.emx, cb.emx);
+                        store2(f + P_EPY * ps, two, ca.epy, cb.epy);
+                        store2(f + P_EMY * ps, two, ca.emy, cb.emy);
+                        store2(f + P_HXPX * ps, two, ca.hxpx, cb.hxpx);
+                        store2(f + P_HXMX * ps, two, ca.hxmx, cb.hxmx);
+                        store2(f + P_HXZ * ps, two, ca.hxz, cb.hxz);
+                        store2(f + P_HYPY * ps, two, ca.hypy, cb.hypy);
+                        store2(f + P_HYMY * ps, two, ca.hymy, cb.hymy);
+                        store2(f + P_HYZ * ps, two, ca.hyz, cb.hyz);
                     }
                 }
             }
@@ -433,8 +475,8 @@ __global__ void __launch_bounds__(NW * 32, 3)
                 __syncwarp();
                 if (lane == 0 && (FAST || i - 2 >= ylo) && i + RING - 2 < yhi) {
                     fence_proxy_async_smem();
-                    issue_row<F16>(&smap, &fmap, &imap, xs, xid, i + RING - 2, ring + (size_t)s2 * LY::SLOT,
-                                   &bars[warp][s2]);
+                    issue_row<F16>(r.smap, r.fmap, r.imap, xs, xid, i + RING - 2, ring + (size_t)s2 * LY::SLOT,
+                                   &bars[s2]);
                 }
             } else {
                 // level k moves on by one row: row i - k becomes the kept row
@@ -443,10 +485,6 @@ __global__ void __launch_bounds__(NW * 32, 3)
                     out.oe[k][0] = in.cur[k].epy[0], out.oe[k][1] = in.cur[k].epy[1];
                     out.oh[k][0] = in.cur[k].hypy[0], out.oh[k][1] = in.cur[k].hypy[1];
                     keep_row(out.cur[k], na, nb);
-                } else if (&in != &out) {
-                    out.cur[k] = in.cur[k];
-                    out.oe[k][0] = in.oe[k][0], out.oe[k][1] = in.oe[k][1];
-                    out.oh[k][0] = in.oh[k][0], out.oh[k][1] = in.oh[k][1];
                 }
             }
             na = ca;
@@ -457,12 +495,16 @@ __global__ void __launch_bounds__(NW * 32, 3)
 #pragma unroll
         for (int k = BT - 1; k > 1; --k) out.ids[k] = in.ids[k - 1];
         out.ids[1] = id_k0;
-        // the ring moves on by one row
-        s2 = s1;
-        s1 = s0;
-        if (++s0 == RING) {
-            s0 = 0;
-            ph ^= 1u;
+        // the ring moves on by one row when one arrived (the rows past the lattice's last row,
+        // at the bottom of its last segment, take none: the slot and barrier phase of the next
+        // row to arrive stay where they are, for the warp's next unit)
+        if (FAST || i < yhi) {
+            s2 = s1;
+            s1 = s0;
+            if (++s0 == RING) {
+                s0 = 0;
+                ph ^= 1u;
+            }
         }
         return true;
     };
@@ -474,24 +516,165 @@ __global__ void __launch_bounds__(NW * 32, 3)
     // (cp.async.bulk.prefetch.tensor) lost in both forms (FP32 212.8 against 220.4, FP16 173.7
     // against 199.5) and is not used.
     const int f0 = max(y0 + BT, BT + 1), f1 = (xedge || !F16) ? f0 : min(min(y1 + BT, yhi), ny);
+    bool ok = true;
     int i = ylo;
     for (; i < f0 && i < y1 + BT; ++i)
         if (!row(std::false_type{}, i, wa, wa)) {
-            timeout = true;
+            ok = false;
             break;
         }
-    for (; !timeout && i < f1; ++i)
+    for (; ok && i < f1; ++i)
         if (!row(std::true_type{}, i, wa, wa)) {
-            timeout = true;
+            ok = false;
             break;
         }
-    for (; !timeout && i < y1 + BT; ++i)
+    for (; ok && i < y1 + BT; ++i)
         if (!row(std::false_type{}, i, wa, wa)) {
-            timeout = true;
+            ok = false;
             break;
         }
-    if (lane == 0 && timeout) atomicOr(a.err, kErrTimeout);
+    R.s0 = s0;
+    R.ph = ph;
+    return ok;
+}
+
+// F16: the FP16-deviation form (TM); otherwise FP32 of either polarization.  One work unit per
+// warp: strip unit % n_strips, row segment unit / n_strips.
+template <bool F16, int POL>
+__global__ void __launch_bounds__(NW * 32, 3)
+    k_step4_stream(const __grid_constant__ UnitCtx u, const StreamArgs a, const __grid_constant__ CUtensorMap smap,
+                   const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap imap,
+                   const long long *__restrict__ t_in, long long *__restrict__ t_out) {
+    using LY = Layout<F16>;
+    constexpr int RING = LY::RING;
+    extern __shared__ unsigned char sm_dyn[];
+    __shared__ __align__(8) uint64_t bars[NW][RING];
+    __shared__ SrcLevels sp;
+    unsigned char *s = sm_dyn + ((128u - (smem_u32(sm_dyn) & 127u)) & 127u);
+    MatT<float> *table = reinterpret_cast<MatT<float> *>(s);
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    unsigned char *ring = s + LY::TABLE + (size_t)warp * LY::WARP;
+
+    const long long t = *t_in;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + BT;
+    if (threadIdx.x == 0) sp = source_levels_f(a.src, t);
+    for (int k = threadIdx.x; k < 256; k += NW * 32) table[k] = a.mtab[k];
+    if (lane == 0) {
+        for (int j = 0; j < RING; ++j) mbar_init(&bars[warp][j], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();  // the only block-wide barrier: from here on each warp runs alone
+    const int unit = (int)blockIdx.x * NW + warp;
+    if (unit >= a.n_units) return;
+    const int strip = unit % a.n_strips, seg = unit / a.n_strips;
+    UnitRun r;
+    r.xs = strip * OUTW - HALO;
+    r.y0 = seg * a.seg_rows;
+    r.y1 = min(r.y0 + a.seg_rows, u.ny);
+    r.t = t;
+    r.smap = &smap;
+    r.fmap = &fmap;
+    r.imap = &imap;
+    r.table = table;
+    r.src_g = sp.g;
+    r.src_inc = sp.inc;
+    RingState R{ring, bars[warp], reinterpret_cast<float4 *>(ring + RING * LY::SLOT), 0, 0u};
+    bool bad = false;
+    const bool ok = stream_unit<F16, POL, false>(u, r, R, bad);
+    if (lane == 0 && !ok) atomicOr(a.err, kErrTimeout);
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrUnstable);
+}
+
+// Batched design maps: persistent warps walk the work units of every instance (instance, strip,
+// row segment; ordered by decreasing run length, then segment, then strip), skipping instances
+// that have finished, four steps per launch.  Two instantiations run one after the other in
+// every launch and split the unfinished instances between them: ACC = false takes those with
+// no time of their accumulated (last) period among the launch's four, ACC = true the others,
+// whose Fourier sums it adds inside the levels whose time falls in that period.  (One kernel
+// doing both spilled: the accumulation's FP64 registers on top of the wavefront's.)  An
+// instance that ends inside a launch runs on past its end without accumulating; its state is
+// not needed afterwards.  FP32.
+template <int POL, bool ACC>
+__global__ void __launch_bounds__(NW * 32, 3)
+    k_batch_step4(const StreamInst *__restrict__ insts, const int4 *__restrict__ units, int n_units,
+                  const SrcLevels *__restrict__ srcs, const CUtensorMap *__restrict__ maps, int p,
+                  float *__restrict__ buf_out, const int *__restrict__ slot, double *__restrict__ acc,
+                  unsigned *__restrict__ err, const long long *__restrict__ t_in, long long *__restrict__ t_out) {
+    using LY = Layout<false>;
+    constexpr int RING = LY::RING;
+    extern __shared__ unsigned char sm_dyn[];
+    __shared__ __align__(8) uint64_t bars[NW][RING];
+    __shared__ MatT<float> wtab[NW][4];  // the current unit's region table, per warp
+    __shared__ UnitCtx uctx[NW];         // the current instance, per warp (read from here, not kept in registers)
+    __shared__ UnitRun urun[NW];         // the current unit, per warp
+    unsigned char *s = sm_dyn + ((128u - (smem_u32(sm_dyn) & 127u)) & 127u);
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    unsigned char *ring = s + LY::TABLE + (size_t)warp * LY::WARP;
+    const long long t = *t_in;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = t + BT;
+    if (lane == 0) {
+        for (int j = 0; j < RING; ++j) mbar_init(&bars[warp][j], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();  // the only block-wide barrier
+    RingState R{ring, bars[warp], reinterpret_cast<float4 *>(ring + RING * LY::SLOT), 0, 0u};
+    const int stride = (int)gridDim.x * NW;
+    for (int w = (int)blockIdx.x * NW + warp; w < n_units; w += stride) {
+        const int4 un = units[w];
+        const StreamInst &I = insts[un.x];
+        const long long steps = I.steps;
+        if (t >= steps || (t + BT - 1 >= I.acc_from) != ACC) continue;  // uniform over the warp
+        __syncwarp();              // the previous unit's reads of the table and context are done
+        if (lane < 3) wtab[warp][lane] = I.m[lane];
+        UnitCtx &u = uctx[warp];
+        if (lane == 0) {
+            u.nx = I.nx;
+            u.ny = I.ny;
+            u.pitch = I.pitch;
+            u.kind = I.kind;
+            u.runaway = I.runaway;
+            u.ay0 = I.ay0;
+            u.ay1 = I.ay1;
+            u.period = I.period;
+            u.pstride = (size_t)I.pstride;
+            u.fout = buf_out + I.base;
+            u.acc_from = I.acc_from;
+            u.steps = steps;
+            u.slot = slot + I.slot_base;
+            u.acc = acc + 6 * (size_t)I.acc_base;
+            u.cs = I.cs;
+        }
+        UnitRun &r = urun[warp];
+        if (lane == 0) {
+            r.xs = un.y * OUTW - HALO;
+            r.y0 = un.z * I.seg_rows;
+            r.y1 = min(r.y0 + I.seg_rows, I.ny);
+            r.t = t;
+            r.smap = maps + 3 * un.x + p;
+            r.fmap = r.smap;
+            r.imap = maps + 3 * un.x + 2;
+            tmap_acquire(r.smap);  // lane 0 issues every row copy of the unit
+            tmap_acquire(r.imap);
+            r.table = wtab[warp];
+            r.src_g = srcs[un.x].g;
+            r.src_inc = srcs[un.x].inc;
+        }
+        __syncwarp();
+        bool bad = false;
+        const bool ok = stream_unit<false, POL, ACC>(u, r, R, bad);
+        if (!ok) {  // a row copy never completed: report, leave
+            if (lane == 0) atomicOr(err + un.x, kErrTimeout);
+            return;
+        }
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err + un.x, kErrUnstable);
+    }
+}
+
+// The source values of every instance at the launch's four times, one thread per instance.
+__global__ void k_batch_source4(const SourceParams *__restrict__ src, int n, const long long *__restrict__ t_in,
+                                SrcLevels *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = source_levels_f(src[i], *t_in);
 }
 
 template <bool F16, int POL>
@@ -554,13 +737,63 @@ cudaError_t encode_stream_maps(CUtensorMap *smap, CUtensorMap *fmap, CUtensorMap
         const cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pstride * 4};
         const cuuint32_t box[3] = {(cuuint32_t)LW, 1u, (cuuint32_t)NPLANES};
         e = encode_tiled(smap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, buf, dims, strides, box);
-        if (e == cudaSuccess && fmap) *fmap = *smap;  // unused by the FP32 kernel
+        if (e == cudaSuccess && fmap) *fmap = *smap;  // unused by the FP32 kernel (may be NULL)
     }
     if (e != cudaSuccess || !imap) return e;
     const cuuint64_t idims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
     const cuuint64_t istrides[1] = {(cuuint64_t)pitch};
     const cuuint32_t ibox[2] = {(cuuint32_t)IDBOX, 1u};
     return encode_tiled(imap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, ids, idims, istrides, ibox);
+}
+
+template <int POL, bool ACC>
+cudaError_t allow_smem_batch4() {
+    return cudaFuncSetAttribute(k_batch_step4<POL, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Layout<false>::SMEM);
+}
+
+cudaError_t batch_stream_prepare(int *resident_warps) {
+    cudaError_t e = allow_smem_batch4<POL_TM, false>();
+    if (e == cudaSuccess) e = allow_smem_batch4<POL_TM, true>();
+    if (e == cudaSuccess) e = allow_smem_batch4<POL_TE, false>();
+    if (e == cudaSuccess) e = allow_smem_batch4<POL_TE, true>();
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step4<POL_TM, false>, NW * 32,
+                                                          Layout<false>::SMEM);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess) *resident_warps = per_sm * sms * NW;
+    return e;
+}
+
+cudaError_t encode_batch_stream_maps(CUtensorMap *maps, const float *buf0, const float *buf1, const uint8_t *ids,
+                                     int nx, int ny, int pitch, size_t pstride) {
+    cudaError_t e = encode_stream_maps(&maps[0], nullptr, &maps[2], buf0, false, ids, nx, ny, pitch, pstride);
+    if (e == cudaSuccess) e = encode_stream_maps(&maps[1], nullptr, nullptr, buf1, false, ids, nx, ny, pitch, pstride);
+    return e;
+}
+
+cudaError_t launch_batch_step4(const StreamInst *insts, const SourceParams *srcp, int n_inst, const int4 *units,
+                               int n_units, SrcLevels *srcs, const CUtensorMap *maps, int p, float *buf_out,
+                               const int *slot, double *acc, unsigned *err, const long long *t_in,
+                               long long *t_out, int grid, int pol, cudaStream_t s) {
+    k_batch_source4<<<(n_inst + 127) / 128, 128, 0, s>>>(srcp, n_inst, t_in, srcs);
+    const size_t sm = Layout<false>::SMEM;
+    // both write t + 4 to t_out; neither reads it
+    if (pol == POL_TE) {
+        k_batch_step4<POL_TE, false><<<grid, NW * 32, sm, s>>>(insts, units, n_units, srcs, maps, p, buf_out, slot,
+                                                              acc, err, t_in, t_out);
+        k_batch_step4<POL_TE, true><<<grid, NW * 32, sm, s>>>(insts, units, n_units, srcs, maps, p, buf_out, slot,
+                                                             acc, err, t_in, t_out);
+    } else {
+        k_batch_step4<POL_TM, false><<<grid, NW * 32, sm, s>>>(insts, units, n_units, srcs, maps, p, buf_out, slot,
+                                                              acc, err, t_in, t_out);
+        k_batch_step4<POL_TM, true><<<grid, NW * 32, sm, s>>>(insts, units, n_units, srcs, maps, p, buf_out, slot,
+                                                             acc, err, t_in, t_out);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step4_stream(const StepArgs<float> &sa, const F16Args *fa, const CUtensorMap *smap,
@@ -579,20 +812,29 @@ cudaError_t launch_step4_stream(const StepArgs<float> &sa, const F16Args *fa, co
     a.err = sa.err;
     a.runaway = sa.runaway;
     a.fout = fout;
+    UnitCtx u{};
+    u.nx = sa.nx;
+    u.ny = sa.ny;
+    u.pitch = sa.pitch;
+    u.kind = sa.src.kind;
+    u.runaway = sa.runaway;
+    u.pstride = sa.pstride;
+    u.fout = fout;
     if (fa) {
-        a.scale = fa->scale;
-        a.inv_scale = fa->inv_scale;
-        a.g_out = fa->g_out;
-        a.fe_out = fa->fe_out;
-        a.fhx_out = fa->fhx_out;
-        a.fhy_out = fa->fhy_out;
-        k_step4_stream<true, POL_TM><<<plan.grid, NW * 32, Layout<true>::SMEM, s>>>(a, *smap, *fmap, *imap, t_in, t_out);
+        a.scale = u.scale = fa->scale;
+        a.inv_scale = u.inv_scale = fa->inv_scale;
+        a.g_out = u.g_out = fa->g_out;
+        a.fe_out = u.fe_out = fa->fe_out;
+        a.fhx_out = u.fhx_out = fa->fhx_out;
+        a.fhy_out = u.fhy_out = fa->fhy_out;
+        k_step4_stream<true, POL_TM>
+            <<<plan.grid, NW * 32, Layout<true>::SMEM, s>>>(u, a, *smap, *fmap, *imap, t_in, t_out);
     } else if (sa.pol == POL_TE) {
-        k_step4_stream<false, POL_TE><<<plan.grid, NW * 32, Layout<false>::SMEM, s>>>(a, *smap, *smap, *imap, t_in,
-                                                                                      t_out);
+        k_step4_stream<false, POL_TE>
+            <<<plan.grid, NW * 32, Layout<false>::SMEM, s>>>(u, a, *smap, *smap, *imap, t_in, t_out);
     } else {
-        k_step4_stream<false, POL_TM><<<plan.grid, NW * 32, Layout<false>::SMEM, s>>>(a, *smap, *smap, *imap, t_in,
-                                                                                      t_out);
+        k_step4_stream<false, POL_TM>
+            <<<plan.grid, NW * 32, Layout<false>::SMEM, s>>>(u, a, *smap, *smap, *imap, t_in, t_out);
     }
     return cudaGetLastError();
 }

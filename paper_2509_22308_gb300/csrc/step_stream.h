@@ -33,6 +33,41 @@ cudaError_t stream_prepare(bool f16, int *resident_warps);
 cudaError_t encode_stream_maps(CUtensorMap *smap, CUtensorMap *fmap, CUtensorMap *imap, const void *buf, bool f16,
                                const uint8_t *ids, int nx, int ny, int pitch, size_t pstride);
 
+// The source values of a launch's four times (FP32, for the lanes at x = 0).
+struct SrcLevels {
+    float g[kStreamSteps], inc[kStreamSteps];
+};
+
+// One instance of a batched design map as the four-step batch kernel reads it: lattice, run
+// length and accumulated period, the rows holding contour stencil sites, the element offsets of
+// its state, slot map and accumulators in the packed buffers, its phase table and its region
+// table (vacuum, region II, region III) in FP32.
+struct alignas(16) StreamInst {
+    int nx, ny, pitch, kind;
+    int seg_rows, n_strips, ay0, ay1;
+    long long steps, acc_from;
+    long long base, pstride;
+    long long slot_base;
+    int acc_base, period;
+    const double2 *cs;
+    unsigned runaway;
+    int pad;
+    MatT<float> m[3];
+};
+
+// Once per device, outside stream capture: shared memory of the batch kernel, resident warps.
+cudaError_t batch_stream_prepare(int *resident_warps);
+// The three tensor maps of one instance (state in buffer 0, in buffer 1, ids) in maps[0..2].
+cudaError_t encode_batch_stream_maps(CUtensorMap *maps, const float *buf0, const float *buf1, const uint8_t *ids,
+                                     int nx, int ny, int pitch, size_t pstride);
+// Four steps of every unfinished instance: the source values of each instance at the launch's
+// four times into srcs (from srcp[n_inst]), then the persistent kernel over units[n_units]
+// (int4: instance, strip, segment), input state buffer p (maps[3 i + p]), output buf_out.
+cudaError_t launch_batch_step4(const StreamInst *insts, const SourceParams *srcp, int n_inst, const int4 *units,
+                               int n_units, SrcLevels *srcs, const CUtensorMap *maps, int p, float *buf_out,
+                               const int *slot, double *acc, unsigned *err, const long long *t_in,
+                               long long *t_out, int grid, int pol, cudaStream_t s);
+
 // Four steps: the state described by the maps (time word t_in) -> fout / the FP16-deviation
 // output planes of fa (t_out = t + 4).  FP32 of either polarization (a.pol), or the
 // FP16-deviation form (TM) when fa is not NULL.  No Fourier accumulation.

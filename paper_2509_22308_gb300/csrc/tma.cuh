@@ -35,6 +35,16 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// A tensor map kept in global memory (a table of them, one per batched instance) is read
+// by the copy engine through the tensor-map proxy, which caches descriptors by address: an
+// entry left from an earlier map at the same address (a freed and reallocated table) would
+// otherwise be used in place of the one the host has since copied there.  The thread that
+// issues copies with the map acquires it first; maps passed as __grid_constant__ kernel
+// parameters need no fence.
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap *map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)map) : "memory");
+}
+
 // One arrival that also expects `bytes` of transactions in the current phase.
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)

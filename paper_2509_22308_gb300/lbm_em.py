@@ -62,7 +62,8 @@ class Instance(ctypes.Structure):
 class BatchOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("min_periods", ctypes.c_int32), ("source_kind", ctypes.c_int32),
-                ("conv_tol", ctypes.c_double), ("stream", ctypes.c_void_p), ("polarization", ctypes.c_int32)]
+                ("conv_tol", ctypes.c_double), ("stream", ctypes.c_void_p), ("polarization", ctypes.c_int32),
+                ("steps_per_launch", ctypes.c_int32)]
 
 
 _P = ctypes.POINTER
@@ -104,6 +105,7 @@ SIGNATURES = {
     "lbm_em_batch_results": [_vp, _P(ctypes.c_double), _P(ctypes.c_int32)],
     "lbm_em_batch_steps": [_vp, _P(ctypes.c_int64)],
     "lbm_em_batch_config": [_vp, _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_int32)],
+    "lbm_em_batch_steps_per_launch": [_vp, _P(ctypes.c_int32)],
     "lbm_em_batch_destroy": [_vp],
 }
 
@@ -368,7 +370,7 @@ class Batch:
     """Owner of one ``lbm_em_batch_t``."""
 
     def __init__(self, instances, precision="f32", tile_w=0, tile_h=0, ctas_per_sm=0, stream=None,
-                 conv_tol=0.0, min_periods=0, kind=SRC_HARD, polarization="tm"):
+                 conv_tol=0.0, min_periods=0, kind=SRC_HARD, polarization="tm", steps_per_launch=0):
         L = load()
         n = len(instances)
         arr = (Instance * n)()
@@ -380,7 +382,7 @@ class Batch:
                               make_janus(inst["a"], inst["phi0"], inst["eps1"], inst["eps2"], inst["pec2"]))
         o = BatchOpts(PRECISIONS.get(precision, precision), int(tile_w), int(tile_h), int(ctas_per_sm),
                       int(min_periods), int(kind), float(conv_tol), _stream_ptr(stream),
-                      {"tm": 0, "te": 1}[polarization])
+                      {"tm": 0, "te": 1}[polarization], int(steps_per_launch))
         b = ctypes.c_void_p()
         _call("lbm_em_batch_create", arr, n, ctypes.byref(o), ctypes.byref(b))
         self.b, self.n, self._L = b, n, L
@@ -398,6 +400,11 @@ class Batch:
         out = np.zeros(self.n, dtype=np.int64)
         _call("lbm_em_batch_steps", self.b, out.ctypes.data_as(_P(ctypes.c_int64)))
         return out
+
+    def steps_per_launch(self) -> int:
+        v = ctypes.c_int32()
+        _call("lbm_em_batch_steps_per_launch", self.b, ctypes.byref(v))
+        return v.value
 
     def config(self):
         w, h, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

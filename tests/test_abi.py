@@ -129,3 +129,16 @@ def test_three_step_flag_is_fp32_only(lib):
         rc = lib.lbm_em_create_janus(ctypes.byref(g), ctypes.byref(lbm_em.make_janus(5, 0.3, 2.0)),
                                      ctypes.byref(lbm_em.make_source(24)), ctypes.byref(h))
         assert rc == lbm_em.EINVAL, (prec, flags, rc)
+
+
+def test_batch_steps_per_launch_is_validated_before_device_work(lib):
+    """lbm_em_batch_opts.steps_per_launch: 0, 1, 2 or 4; 2 and 4 need FP32 without convergence
+    exits, 4 takes no tile shape or CTA count."""
+    from paper_2509_22308_gb300 import lbm_em as L
+    arr = (L.Instance * 1)()
+    arr[0] = L.Instance(64, 64, 48, 2, 48, 0, 1.0, 20.0, L.make_janus(10.0, 0.3, 2.0, 4.0, False))
+    for prec, spl, conv, tw in ((L.F32, 3, 0.0, 0), (L.F64, 4, 0.0, 0), (L.F32X2, 2, 0.0, 0), (L.F32, 4, 1e-3, 0),
+                                (L.F32, 4, 0.0, 64)):
+        o = L.BatchOpts(prec, tw, 0, 0, 0, 0, conv, None, 0, spl)
+        h = ctypes.c_void_p()
+        assert lib.lbm_em_batch_create(arr, 1, ctypes.byref(o), ctypes.byref(h)) == L.EINVAL, (prec, spl, conv, tw)

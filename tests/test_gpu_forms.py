@@ -96,7 +96,7 @@ def test_batch_matches_single_domain(prec):
         ref = L.run_instance(inst, prec)
         assert np.max(np.abs(F[i] - ref)) < 1e-12 * np.sum(np.abs(ref)), (i, F[i], ref)
     w, h, c = b.config()
-    assert w in (32, 40, 64, 128, 256) and 1 <= h <= 16 and c >= 1
+    assert (w in (32, 40, 64, 128, 256) and 1 <= h <= 16 and c >= 1) or (w == 56 and h in (64, 128, 256) and c >= 1)
     b.run()                      # a second run starts from a cleared state
     F2, _ = b.results()
     assert np.array_equal(F, F2)
@@ -402,3 +402,140 @@ def test_f16dev_four_steps_track_one_step(shape):
         assert np.sqrt(num / den) < 2e-3
         for x, y in zip(f4, s4b.fields()):
             assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("pol", ["tm", "te"])
+def test_batch_four_steps_per_launch_is_bit_identical(pol):
+    """The FP32 batch with four steps per launch (persistent warps streaming every instance's
+    strips and row segments through four time levels in registers, Fourier sums accumulated
+    inside the levels of each instance's last period) gives the forces of the one-step batch
+    kernel bit for bit, for uneven sizes, periods and run lengths that are not multiples of four
+    (an instance ending inside a launch runs on past its end; the last steps take one-step
+    launches), and matches the single-domain runs."""
+    insts = _batch_instances()
+    insts[0] = dict(insts[0], period=61, ramp=61)    # 305 steps
+    insts[1] = dict(insts[1], period=45, ramp=45)    # 135 steps
+    b4 = L.Batch(insts, "f32", steps_per_launch=4, polarization=pol)
+    b1 = L.Batch(insts, "f32", tile_w=64, tile_h=4, ctas_per_sm=4, polarization=pol)
+    try:
+        assert b4.steps_per_launch() == 4
+        w, h, c = b4.config()
+        assert w == 56 and h in (64, 128, 256) and c >= 1
+        b4.run()
+        b1.run()
+        F4, s4 = b4.results()
+        F1, _ = b1.results()
+        b4.run()                  # a second run starts from a cleared state
+        F4b, _ = b4.results()
+    finally:
+        b1.close()
+        b4.close()
+    assert (s4 == L.OK).all()
+    assert np.array_equal(F1, F4) and np.array_equal(F4, F4b)
+    for i, inst in enumerate(insts):
+        ref = L.run_instance(inst, "f32", polarization=pol)
+        assert np.max(np.abs(F4[i] - ref)) < 1e-12 * np.sum(np.abs(ref))
+
+
+def test_batch_four_steps_on_random_instance_sizes():
+    """Seeded random instance sizes (24 .. 259 per side: strips and row segments cut ragged) and
+    run lengths: the four-step batch kernel's forces equal the one-step kernel's bits."""
+    insts = []
+    for k, (nx, ny) in enumerate(_random_shapes(31, 9, 24, 260)):
+        a = min(nx, ny) / 6.0
+        T = 24 + 5 * k
+        insts.append(dict(nx=nx, ny=ny, a=a, phi0=0.3 * k, eps1=2.0, eps2=1.5 + k, pec2=k % 3 == 1, period=T,
+                          periods=2 + k % 3, R=min(nx, ny) / 3.0, ramp=T))
+    b4 = L.Batch(insts, "f32", steps_per_launch=4)
+    b1 = L.Batch(insts, "f32", tile_w=64, tile_h=4, ctas_per_sm=4)
+    try:
+        b4.run()
+        b1.run()
+        F4, s4 = b4.results()
+        F1, s1 = b1.results()
+    finally:
+        b1.close()
+        b4.close()
+    assert (s4 == L.OK).all() and (s1 == L.OK).all()
+    assert np.array_equal(F1, F4)
+
+
+def test_batch_rejects_bad_steps_per_launch():
+    insts = _batch_instances()[:1]
+    for prec, kw in (("f32", {"steps_per_launch": 3}), ("f64", {"steps_per_launch": 4}),
+                     ("f32", {"steps_per_launch": 4, "conv_tol": 1e-3}),
+                     ("f32", {"steps_per_launch": 4, "tile_w": 64})):
+        with pytest.raises(L.LbmEmError) as e:
+            L.Batch(insts, prec, **kw)
+        assert e.value.status == L.EINVAL
+
+
+def test_batch_four_steps_many_units_per_warp():
+    """The 256-instance design map, shortened to 8 periods (the incident front crosses every
+    instance's contour by then): about 34 000 work units for about 1 800 persistent warps, so
+    every warp runs many units, including the last row segment of instances where the
+    wavefront drains past the lattice's last row; its row ring must carry its slot and barrier
+    phase over from unit to unit.  Forces equal the two-step kernel's bits (which equal one
+    step per launch), and no row copy times out."""
+    dm = [dict(i, periods=8) for i in W.design_map_256(4, 256)]
+    b4 = L.Batch(dm, "f32", steps_per_launch=4)
+    b2 = L.Batch(dm, "f32", tile_w=64, tile_h=8, ctas_per_sm=3, steps_per_launch=2)
+    try:
+        b4.run()
+        b2.run()
+        F4, s4 = b4.results()
+        F2, s2 = b2.results()
+    finally:
+        b2.close()
+        b4.close()
+    assert (s4 == L.OK).all() and (s2 == L.OK).all()
+    assert (np.abs(F2).sum(axis=1) > 0).all()
+    assert np.array_equal(F2, F4)
+
+
+def _reuse_instances():
+    out = []
+    for k, (nx, ny) in enumerate(_random_shapes(5, 12, 48, 130)):
+        a = min(nx, ny) / 6.0
+        out.append(dict(nx=nx, ny=ny, a=a, phi0=0.5 * k, eps1=2.5, eps2=4.0, pec2=k % 2 == 0, period=20,
+                        periods=10, R=min(nx, ny) / 3.0, ramp=20))
+    return out
+
+
+def test_batches_on_reused_memory_give_the_same_bits():
+    """Batches created, run and freed in turn, some while another batch is alive, are placed on
+    memory that freed batches left holding their final state, error words, accumulators and
+    tensor-map tables.  Every run, the first one of a batch whose tuning had a single candidate
+    included, starts from the cleared state with its own maps: all give the forces of the first
+    batch, and no copy times out."""
+    insts = _reuse_instances()
+
+    def two():
+        return L.Batch(insts, "f32", tile_w=64, tile_h=8, ctas_per_sm=3, steps_per_launch=2)
+
+    def four():
+        return L.Batch(insts, "f32", steps_per_launch=4)
+
+    def one():
+        return L.Batch(insts, "f32", tile_w=64, tile_h=4, ctas_per_sm=4)
+
+    def run(make):
+        b = make()
+        try:
+            b.run()
+            return b.results()
+        finally:
+            b.close()
+
+    F_ref, s_ref = run(two)
+    assert (s_ref == L.OK).all() and (np.abs(F_ref).sum(axis=1) > 0).all()
+    for pre in (None, two, four, one, None):
+        held = pre() if pre else None
+        try:
+            for make in (two, four, one, two):
+                F, st = run(make)
+                assert (st == L.OK).all()
+                assert np.array_equal(F, F_ref)
+        finally:
+            if held is not None:
+                held.close()
