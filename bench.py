@@ -65,7 +65,7 @@ def parse_args():
     p.add_argument("--profile-case", action="store_true",
                    help="small case for ncu: two launches of each step kernel on a 2048^2 lattice and of the FP64 step on the 512^2 workload")
     p.add_argument("--profile-only", default="",
-                   help="with --profile-case: only these form:mode pairs (e.g. f32:four,f16dev:four)")
+                   help="with --profile-case: only these form:mode pairs and design maps (e.g. f32:four,f16dev:four,batch4)")
     p.add_argument("--profile-n", type=int, default=2048, help="with --profile-only: the lattice size")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true")
@@ -327,38 +327,47 @@ def profile_case(only="", n=2048):
     launch, then with one; double-float; FP32 with three steps per launch; FP32 and
     FP16-deviation with four) on a 2048^2 lattice (state 0.3-0.7 GB per buffer, larger than
     L2, a few GB on the device in total), two launches of the FP64 step on one 512^2
-    instance of the benchmark workload, then a 24-instance FP32 design map."""
+    instance of the benchmark workload, then a 24-instance FP32 design map with two steps per
+    launch and the same map with four.  `only` picks some of them: "form:mode" pairs for the
+    lattice (of size n), "batch2" and "batch4" for the design maps."""
     import torch
     from paper_2509_22308_gb300 import build as B
     B.build()
     from paper_2509_22308_gb300 import lbm_em as L
+    from paper_2509_22308_gb300 import workloads as W
     if not only:
         n = 2048
     inst = dict(nx=n, ny=n, a=n / 16.0, phi0=0.5, eps1=4.0, eps2=1.0, pec2=True, period=240, periods=1,
                 R=0.09375 * n, ramp=240)
     pairs = (("f64", "auto"), ("f32", "two"), ("f16dev", "two"), ("f32", "one"), ("f16dev", "one"),
              ("f32x2", "auto"), ("f32", "three"), ("f32", "four"), ("f16dev", "four"))
+    maps = ("batch2", "batch4")
     if only:
-        pairs = tuple(tuple(p.split(":")) for p in only.split(","))
+        tokens = only.split(",")
+        pairs = tuple(tuple(p.split(":")) for p in tokens if ":" in p)
+        maps = tuple(p for p in tokens if ":" not in p)
     for fp, mode in pairs:
         with L.solver_for_instance(inst, fp, steps_per_launch=mode) as s:
             s.step({"two": 4, "three": 6, "four": 8}.get(mode, 2))
             s.sync()
-    if only:
-        torch.cuda.synchronize()
-        print("profile case done")
-        return
-    # and two launches of the benchmark's own 512^2 FP64 instance (theta = 0)
-    from paper_2509_22308_gb300 import workloads as W
-    with L.solver_for_instance(W.md_janus_512()[0], "f64") as s:
-        s.step(2)
-        s.sync()
-    # then a 24-instance FP32 design map (about 1 GB on the device) with the batch kernel's
-    # two-steps-per-launch configuration fixed (no autotuning launches before it)
-    b = L.Batch(W.design_map_256(4, 24), "f32", tile_w=64, tile_h=8, ctas_per_sm=3)
-    b.run()
-    b.results()
-    b.close()
+    if not only:
+        # two launches of the benchmark's own 512^2 FP64 instance (theta = 0)
+        with L.solver_for_instance(W.md_janus_512()[0], "f64") as s:
+            s.step(2)
+            s.sync()
+    # a 24-instance FP32 design map (about 1 GB on the device): the two-step batch kernel with
+    # its configuration fixed (no autotuning launches before it), then the four-step one
+    # (whose tuning times three row-segment heights before the run)
+    for m in maps:
+        if m == "batch2":
+            b = L.Batch(W.design_map_256(4, 24), "f32", tile_w=64, tile_h=8, ctas_per_sm=3)
+        elif m == "batch4":
+            b = L.Batch(W.design_map_256(4, 24), "f32", steps_per_launch=4)
+        else:
+            raise SystemExit(f"unknown profile case {m!r}")
+        b.run()
+        b.results()
+        b.close()
     torch.cuda.synchronize()
     print("profile case done")
 

@@ -51,10 +51,21 @@ __device__ __forceinline__ float eq2_emy(float e, float hx, float hy) { return _
 __device__ __forceinline__ float rebuild(float eq2, __half g, float inv_scale) {
     return __fmaf_rn(-__half2float(g), inv_scale, __fmul_rn(eq2, 0.5f));
 }
-// g = (f - eq2 / 2) * 2^10, rounded to FP16
-__device__ __forceinline__ __half encode(float f, float eq2, float scale) {
-    return __float2half_rn(__fmul_rn(__fsub_rn(f, __fmul_rn(eq2, 0.5f)), scale));
+// Encoding g = (f - eq2 / 2) * s, rounded to FP16, as one FMA: f * s - (eq2 / 2) * s.  The
+// scale s is a power of two, and scaling by one commutes with rounding, so the FMA's single
+// rounding gives the value of "subtract, round, scale"; a result that underflows FP32's normal
+// range in one form and not the other converts to the same FP16 zero or subnormal.  The
+// scaled halves of every 2 f^eq come from the scaled fields of the site (eq2 * s / 2 is a
+// sum or difference of two of them, by the same argument).
+struct EqS {
+    float z, px, mx, py, my, hx, hy;
+};
+__device__ __forceinline__ EqS eq_scaled(float e3, float hx3, float hy3, float scale) {
+    const float h = 0.5f * scale;
+    const float e = __fmul_rn(e3, h), hx = __fmul_rn(hx3, h), hy = __fmul_rn(hy3, h);
+    return EqS{e, __fsub_rn(e, hy), __fadd_rn(e, hy), __fadd_rn(e, hx), __fsub_rn(e, hx), hx, hy};
 }
+__device__ __forceinline__ float encode_f(float f, float eqs, float scale) { return __fmaf_rn(f, scale, -eqs); }
 
 // Stored fields of a site: E_z/3, H_x/3, H_y/3.
 struct Fld {
@@ -111,17 +122,38 @@ __device__ __forceinline__ void pull_f16(const F16Args &a, int x, int y, long lo
 
 // The 11 encoded deviations of a site whose pulled populations are p and stored fields F.
 __device__ __forceinline__ void encode_all(const Pop<float> &p, const Fld &F, float sc, __half g[NPLANES]) {
-    g[P_EZ] = encode(p.ez, F.e, sc);
-    g[P_EPX] = encode(p.epx, eq2_epx(F.e, F.hx, F.hy), sc);
-    g[P_EMX] = encode(p.emx, eq2_emx(F.e, F.hx, F.hy), sc);
-    g[P_EPY] = encode(p.epy, eq2_epy(F.e, F.hx, F.hy), sc);
-    g[P_EMY] = encode(p.emy, eq2_emy(F.e, F.hx, F.hy), sc);
-    g[P_HXPX] = encode(p.hxpx, F.hx, sc);
-    g[P_HXMX] = encode(p.hxmx, F.hx, sc);
-    g[P_HXZ] = encode(p.hxz, F.hx, sc);
-    g[P_HYPY] = encode(p.hypy, F.hy, sc);
-    g[P_HYMY] = encode(p.hymy, F.hy, sc);
-    g[P_HYZ] = encode(p.hyz, F.hy, sc);
+    const EqS q = eq_scaled(F.e, F.hx, F.hy, sc);
+    g[P_EZ] = __float2half_rn(encode_f(p.ez, q.z, sc));
+    g[P_EPX] = __float2half_rn(encode_f(p.epx, q.px, sc));
+    g[P_EMX] = __float2half_rn(encode_f(p.emx, q.mx, sc));
+    g[P_EPY] = __float2half_rn(encode_f(p.epy, q.py, sc));
+    g[P_EMY] = __float2half_rn(encode_f(p.emy, q.my, sc));
+    g[P_HXPX] = __float2half_rn(encode_f(p.hxpx, q.hx, sc));
+    g[P_HXMX] = __float2half_rn(encode_f(p.hxmx, q.hx, sc));
+    g[P_HXZ] = __float2half_rn(encode_f(p.hxz, q.hx, sc));
+    g[P_HYPY] = __float2half_rn(encode_f(p.hypy, q.hy, sc));
+    g[P_HYMY] = __float2half_rn(encode_f(p.hymy, q.hy, sc));
+    g[P_HYZ] = __float2half_rn(encode_f(p.hyz, q.hy, sc));
+}
+
+// encode_all of two sites at once, site a in the low and site b in the high half of each
+// pair (one paired conversion per population).
+__device__ __forceinline__ void encode_pair(const Pop<float> &a, const Pop<float> &b, const Fld &Fa, const Fld &Fb,
+                                            float sc, __half2 g[NPLANES]) {
+    const EqS qa = eq_scaled(Fa.e, Fa.hx, Fa.hy, sc), qb = eq_scaled(Fb.e, Fb.hx, Fb.hy, sc);
+#define LBMEM_ENC2(P, m, eq) g[P] = __floats2half2_rn(encode_f(a.m, qa.eq, sc), encode_f(b.m, qb.eq, sc))
+    LBMEM_ENC2(P_EZ, ez, z);
+    LBMEM_ENC2(P_EPX, epx, px);
+    LBMEM_ENC2(P_EMX, emx, mx);
+    LBMEM_ENC2(P_EPY, epy, py);
+    LBMEM_ENC2(P_EMY, emy, my);
+    LBMEM_ENC2(P_HXPX, hxpx, hx);
+    LBMEM_ENC2(P_HXMX, hxmx, hx);
+    LBMEM_ENC2(P_HXZ, hxz, hx);
+    LBMEM_ENC2(P_HYPY, hypy, hy);
+    LBMEM_ENC2(P_HYMY, hymy, hy);
+    LBMEM_ENC2(P_HYZ, hyz, hy);
+#undef LBMEM_ENC2
 }
 
 // What the next step's pull rebuilds from this site (its stored fields and encoded

@@ -417,20 +417,19 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
                     if (store) {
                         bad |= field_runaway(E3a, u.runaway) || (two && field_runaway(E3b, u.runaway));
                         const Fld Fa = stored_fields(E3a, Hxa, Hya), Fb = stored_fields(E3b, Hxb, Hyb);
-                        __half ga[NPLANES], gb[NPLANES];
-                        encode_all(ca, Fa, u.scale, ga);
-                        encode_all(cb, Fb, u.scale, gb);
+                        __half2 g2[NPLANES];
+                        encode_pair(ca, cb, Fa, Fb, u.scale, g2);
                         const size_t idx = (size_t)q * u.pitch + xa;
                         if (two) {
 #pragma unroll
                             for (int p = 0; p < NPLANES; ++p)
-                                *reinterpret_cast<__half2 *>(u.g_out + p * ps + idx) = __halves2half2(ga[p], gb[p]);
+                                *reinterpret_cast<__half2 *>(u.g_out + p * ps + idx) = g2[p];
                             *reinterpret_cast<float2 *>(u.fe_out + idx) = make_float2(Fa.e, Fb.e);
                             *reinterpret_cast<float2 *>(u.fhx_out + idx) = make_float2(Fa.hx, Fb.hx);
                             *reinterpret_cast<float2 *>(u.fhy_out + idx) = make_float2(Fa.hy, Fb.hy);
                         } else {
 #pragma unroll
-                            for (int p = 0; p < NPLANES; ++p) u.g_out[p * ps + idx] = ga[p];
+                            for (int p = 0; p < NPLANES; ++p) u.g_out[p * ps + idx] = __low2half(g2[p]);
                             u.fe_out[idx] = Fa.e;
                             u.fhx_out[idx] = Fa.hx;
                             u.fhy_out[idx] = Fa.hy;
@@ -685,13 +684,26 @@ cudaError_t allow_smem_stream() {
 
 }  // namespace
 
-StreamPlan stream_plan(int nx, int ny, int resident_warps) {
+StreamPlan stream_plan(int nx, int ny, int resident_warps, bool f16) {
+    // Units in k full waves of the resident warps (k x resident / strips row segments per
+    // strip): the warps of a wave start together and stream their rows in step, and later waves
+    // start as blocks of the earlier ones finish, which spreads the GPU's row copies and
+    // arithmetic over time; a wave only partly filled leaves SMs idle at the end.  Every segment
+    // pays a 4-row halo at each end, so k is the largest that keeps segments of at least 80
+    // rows, at most 3 (FP32) or 5 (FP16-deviation).  Measured on GB300 against the best
+    // number of waves at each size: within 1.6 % from 2048^2 to 8192^2 (8192^2: one wave 225.1 and
+    // 207.5 GLUPS, this plan 240.1 and 253.6).
     StreamPlan p;
     p.n_strips = (nx + OUTW - 1) / OUTW;
-    // as many row segments as keep every strip's warps within one wave, but at least 16 rows
-    // each (shorter ones spend most of their time on the 4-row halo at each end)
-    int segs = resident_warps / p.n_strips;
-    if (segs < 1) segs = 1;
+    const int max_waves = f16 ? 5 : 3, min_rows = 80;
+    int segs = 1;
+    for (int k = 1; k <= max_waves; ++k) {
+        int sk = (int)((long long)k * resident_warps / p.n_strips);
+        if (sk < 1) sk = 1;
+        if (k > 1 && (ny + sk - 1) / sk < min_rows) break;
+        segs = sk;
+    }
+    // but at least 16 rows each (shorter ones spend most of their time on the halo)
     if (segs > (ny + 15) / 16) segs = (ny + 15) / 16;
     p.seg_rows = (ny + segs - 1) / segs;
     segs = (ny + p.seg_rows - 1) / p.seg_rows;

@@ -124,3 +124,13 @@ def test_multi_step_bit_identity_on_persistent_grid(shape, prec, mode):
 @pytest.mark.parametrize("mode", ["two", "three", "four"])
 def test_multi_step_bit_identity_on_persistent_grid_te(shape, mode):
     _same_bits(_big_inst(*shape, pec2=False), "f32", mode, pol="te")
+
+
+@pytest.mark.parametrize("pol", ["tm", "te"])
+def test_four_steps_in_several_waves_of_units_bit_identical(pol):
+    """On 4096^2 the four-step kernel cuts each strip into twice as many row segments as one
+    wave of resident warps holds (84-row segments, two waves of thread blocks): fields after
+    step counts of every residue and an accumulated period's forces are the bits of one step
+    per launch."""
+    _same_bits(_big_inst(4096, 4096, pec2=pol == "tm"), "f32", "four", pol=pol, counts=(1, 2, 3, 4, 7, 32))
+
