@@ -343,7 +343,10 @@ typedef struct {
                                 by the TMA unit and advance two steps there, same bits; 40 is
                                 valid for it only).  With nothing pinned the autotuner times
                                 those three when they apply, else the one-step shapes      */
-    int32_t ctas_per_sm;     /* persistent CTAs per SM; 0: autotuned                       */
+    int32_t ctas_per_sm;     /* persistent CTAs per SM; 0: autotuned.  With
+                                steps_per_launch 4: 1 .. 3 runs the four-step kernel on a
+                                persistent grid of that many blocks per SM whose warps take
+                                the work units in turn (0: one warp per unit, the default) */
     int32_t min_periods;     /* convergence exits: fewest periods an instance runs         */
     int32_t source_kind;     /* lbm_em_source_kind of every instance (0: HARD)              */
     double conv_tol;         /* 0: every instance runs its `periods`; > 0: an instance stops
@@ -354,11 +357,11 @@ typedef struct {
     int32_t polarization;    /* 0: TM^z (E_z, H_x, H_y), the paper's case; 1: TE^z (H_z,
                                 E_x, E_y) for every instance (see LBM_EM_FLAG_TE)          */
     int32_t steps_per_launch;/* 0: autotuned; 1, 2 or 4 pins the steps one launch advances.
-                                4 (FP32, conv_tol 0, nothing else pinned): persistent warps
-                                stream strips of 56 columns and row segments of every instance
-                                through four time levels held in registers (the autotuner picks
-                                the segment height, 64, 128 or 256 rows); same bits as one step
-                                per launch.  2: the TMA tile kernel above.  With 0 the
+                                4 (FP32, conv_tol 0, nothing else pinned): one warp per work
+                                unit streams a strip of 56 columns and a row segment of an
+                                instance through four time levels held in registers (the
+                                autotuner picks the segment height, 64, 128 or 256 rows); same
+                                bits as one step per launch.  2: the TMA tile kernel above.  With 0 the
                                 autotuner times every kind that applies                    */
 } lbm_em_batch_opts;
 
@@ -376,8 +379,8 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n,
                                   const lbm_em_batch_opts *o, lbm_em_batch_t **out);
 
 /* Rasterise every instance (Sec. II), run each for its periods (Eq. LBGK equation, the last
- * period with the Fourier accumulation of Sec. III) in a persistent kernel over the packed
- * tile list replayed under a CUDA graph, then the contour integral of each (Sec. II.B).  A
+ * period with the Fourier accumulation of Sec. III) in kernels over the packed tiles or work
+ * units replayed under a CUDA graph, then the contour integral of each (Sec. II.B).  A
  * second call starts again from rest.  Asynchronous on the batch's stream; returns launch
  * errors only: per-instance failures come back through lbm_em_batch_results. */
 lbm_em_status lbm_em_batch_run(lbm_em_batch_t *b);
@@ -395,7 +398,8 @@ lbm_em_status lbm_em_batch_results(lbm_em_batch_t *b, double *out, int32_t *stat
 lbm_em_status lbm_em_batch_steps(lbm_em_batch_t *b, int64_t *steps);
 
 /* Chosen tile shape and CTAs per SM (after autotuning), for reporting.  With four steps per
- * launch: 56 (the strip width), the row-segment height and the kernel's blocks per SM. */
+ * launch: 56 (the strip width), the row-segment height and the kernel's resident blocks per
+ * SM. */
 lbm_em_status lbm_em_batch_config(lbm_em_batch_t *b, int32_t *tile_w, int32_t *tile_h,
                                   int32_t *ctas_per_sm);
 

@@ -584,9 +584,10 @@ __global__ void __launch_bounds__(NW * 32, 3)
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrUnstable);
 }
 
-// Batched design maps: persistent warps walk the work units of every instance (instance, strip,
-// row segment; ordered by decreasing run length, then segment, then strip), skipping instances
-// that have finished, four steps per launch.  Two instantiations run one after the other in
+// Batched design maps: the warps walk the work units of every instance (instance, strip, row
+// segment; ordered by decreasing run length, then segment, then strip) with a grid stride,
+// skipping instances that have finished, four steps per launch; the batch launches one warp per
+// unit, so each warp normally takes one.  Two instantiations run one after the other in
 // every launch and split the unfinished instances between them: ACC = false takes those with
 // no time of their accumulated (last) period among the launch's four, ACC = true the others,
 // whose Fourier sums it adds inside the levels whose time falls in that period.  (One kernel

@@ -61,8 +61,9 @@ cudaError_t batch_stream_prepare(int *resident_warps);
 cudaError_t encode_batch_stream_maps(CUtensorMap *maps, const float *buf0, const float *buf1, const uint8_t *ids,
                                      int nx, int ny, int pitch, size_t pstride);
 // Four steps of every unfinished instance: the source values of each instance at the launch's
-// four times into srcs (from srcp[n_inst]), then the persistent kernel over units[n_units]
-// (int4: instance, strip, segment), input state buffer p (maps[3 i + p]), output buf_out.
+// four times into srcs (from srcp[n_inst]), then the kernel over units[n_units] (int4:
+// instance, strip, segment; walked with a stride of grid x kStreamWarps warps), input state
+// buffer p (maps[3 i + p]), output buf_out.
 cudaError_t launch_batch_step4(const StreamInst *insts, const SourceParams *srcp, int n_inst, const int4 *units,
                                int n_units, SrcLevels *srcs, const CUtensorMap *maps, int p, float *buf_out,
                                const int *slot, double *acc, unsigned *err, const long long *t_in,

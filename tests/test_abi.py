@@ -133,7 +133,7 @@ def test_three_step_flag_is_fp32_only(lib):
 
 def test_batch_steps_per_launch_is_validated_before_device_work(lib):
     """lbm_em_batch_opts.steps_per_launch: 0, 1, 2 or 4; 2 and 4 need FP32 without convergence
-    exits, 4 takes no tile shape or CTA count."""
+    exits, 4 takes no tile shape."""
     from paper_2509_22308_gb300 import lbm_em as L
     arr = (L.Instance * 1)()
     arr[0] = L.Instance(64, 64, 48, 2, 48, 0, 1.0, 20.0, L.make_janus(10.0, 0.3, 2.0, 4.0, False))

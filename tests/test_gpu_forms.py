@@ -470,17 +470,22 @@ def test_batch_rejects_bad_steps_per_launch():
         assert e.value.status == L.EINVAL
 
 
-def test_batch_four_steps_many_units_per_warp():
+@pytest.mark.parametrize("ctas", [0, 1])
+def test_batch_four_steps_on_the_design_map(ctas):
     """The 256-instance design map, shortened to 8 periods (the incident front crosses every
-    instance's contour by then): about 34 000 work units for about 1 800 persistent warps, so
-    every warp runs many units, including the last row segment of instances where the
-    wavefront drains past the lattice's last row; its row ring must carry its slot and barrier
-    phase over from unit to unit.  Forces equal the two-step kernel's bits (which equal one
-    step per launch), and no row copy times out."""
+    instance's contour by then), about 34 000 work units, including the last row segment of
+    instances where the wavefront drains past the lattice's last row.  ctas 0: one warp per
+    unit; ctas 1: a persistent grid of one block per SM (608 warps), so every warp takes about
+    56 units in turn and its row ring carries its slot and barrier phase over from unit to
+    unit.  Forces equal the two-step kernel's bits (which equal one step per launch), and no
+    row copy times out."""
     dm = [dict(i, periods=8) for i in W.design_map_256(4, 256)]
-    b4 = L.Batch(dm, "f32", steps_per_launch=4)
+    b4 = L.Batch(dm, "f32", steps_per_launch=4, ctas_per_sm=ctas)
     b2 = L.Batch(dm, "f32", tile_w=64, tile_h=8, ctas_per_sm=3, steps_per_launch=2)
     try:
+        assert b4.steps_per_launch() == 4
+        if ctas:
+            assert b4.config()[2] == ctas
         b4.run()
         b2.run()
         F4, s4 = b4.results()
@@ -491,6 +496,12 @@ def test_batch_four_steps_many_units_per_warp():
     assert (s4 == L.OK).all() and (s2 == L.OK).all()
     assert (np.abs(F2).sum(axis=1) > 0).all()
     assert np.array_equal(F2, F4)
+
+
+def test_batch_four_steps_rejects_too_many_ctas():
+    with pytest.raises(L.LbmEmError) as e:
+        L.Batch(_batch_instances()[:1], "f32", steps_per_launch=4, ctas_per_sm=8)
+    assert e.value.status == L.EINVAL
 
 
 def _reuse_instances():
