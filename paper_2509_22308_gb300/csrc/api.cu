@@ -559,11 +559,12 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     h->t3 = (g->flags & LBM_EM_FLAG_THREE_STEP) != 0;
     // four steps per launch (row-streaming kernel): forced by the flag, else the default of FP32
     // from 2^21 sites and of FP16-deviation from 2^20 sites on (measured on GB300, GLUPS four /
-    // two / three steps per launch, FP32: 8192^2 220.4 / 136.9 / 143.9, 4096^2 208.2 / 138.4 /
-    // 140.3, 2048^2 176.2 / 122.7 / 126.4, 1024^2 114.2 / 120.1 / 110.7, 512^2 33.5 / 70.3 / 70.0;
-    // FP16-deviation four / two: 198.2 / 115.5, 187.9 / 114.5, 160.4 / 105.5, 104.1 / 98.6,
-    // 30.5 / 58.3: on small lattices the strips cannot fill the GPU and the two-step kernel's
-    // state stays in L2); its accumulating periods run on the two-step tile kernel
+    // two / three steps per launch, FP32: 8192^2 240.0 / 136.8 / 143.9, 4096^2 214.4 / 138.0 /
+    // 140.5, 2048^2 179.8 / 122.4 / 126.1, 1448^2 159.7 / 114.3 / 122.0, 1024^2 116.3 / 124.0 /
+    // 111.1, 512^2 34.6 / 70.4 / 70.3; FP16-deviation four / two: 8192^2 253.2 / 116.8, 2048^2
+    // 166.5 / 106.9, 1448^2 147.1 / 100.2, 1024^2 107.0 / 99.8, 768^2 61.2 / 87.2, 512^2 31.0 /
+    // 59.2: on small lattices the strips cannot fill the GPU and the two-step kernel's state
+    // stays in L2); its accumulating periods run on the two-step tile kernel
     h->s4 = (g->flags & LBM_EM_FLAG_FOUR_STEP) != 0 ||
             (!step_flags && (long long)g->nx * g->ny >= (g->precision == LBM_EM_F32      ? (1LL << 21)
                                                          : g->precision == LBM_EM_F16DEV ? (1LL << 20)
