@@ -334,11 +334,14 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
 
     // One wavefront row: row i arrives as level 0; level k + 1 of row q = i - 1 - k is computed
     // from level k of rows q - 1, q and q + 1 (k = 0 from the ring, k >= 1 from `in`); `out`
-    // receives the kept rows for the next row.  FAST: an interior strip in the steady state
-    // (every level computes, no lattice edge in x or y, every level-4 row is stored) without any
-    // of the general path's tests.  Returns false after a bounded wait gave up.
+    // receives the kept rows for the next row.  MODE 0: the general row; 1 and 2: a row in the
+    // steady state (every level computes, every level-4 row is stored, no lattice top or bottom)
+    // without those tests, 1 in an interior strip (no left or right edge either), 2 in a strip
+    // at the lattice's left or right edge.  Returns false after a bounded wait gave up.
     auto row = [&](auto fast_tag, int i, const Wave &in, Wave &out) -> bool {
-        constexpr bool FAST = decltype(fast_tag)::value;
+        constexpr int MODE = decltype(fast_tag)::value;
+        constexpr bool FAST = MODE != 0;  // no test at the lattice's top and bottom or the segment's ends
+        constexpr bool NOX = MODE == 1;   // and none at its left and right edges
         // level 0 of row i
         if (FAST || i < yhi) {
             const bool ok = mbar_wait(&bars[s0], ph);
@@ -379,7 +382,7 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
                     v = lds2(ru, P_HYPY, lane), hy[0] = v.x, hy[1] = v.y;
                     v = lds2(rd, P_EMY, lane), my[0] = v.x, my[1] = v.y;
                     v = lds2(rd, P_HYMY, lane), mh[0] = v.x, mh[1] = v.y;
-                    if (FAST)
+                    if (NOX)
                         pull_row(c0, ey, hy, my, mh, false, false, false, ca, cb);
                     else
                         pull_row(c0, ey, hy, my, mh, xa0, xa_last, xb_last, ca, cb);
@@ -399,13 +402,13 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
                     } else {
                         my[0] = na.emy, my[1] = nb.emy, mh[0] = na.hymy, mh[1] = nb.hymy;
                     }
-                    if (FAST)
+                    if (NOX)
                         pull_row(in.cur[k], ey, hy, my, mh, false, false, false, ca, cb);
                     else
                         pull_row(in.cur[k], ey, hy, my, mh, xa0, xa_last, xb_last, ca, cb);
                     idq = in.ids[k];
                 }
-                if (!FAST && src_lane && t + k >= 1) inject_source_t(kind, r.src_g[k], r.src_inc[k], ca);
+                if (!NOX && src_lane && t + k >= 1) inject_source_t(kind, r.src_g[k], r.src_inc[k], ca);
                 const MatT<float> ma = r.table[idq & 0xffu], mb = r.table[(idq >> 8) & 0xffu];
                 const bool owned = out_lane && (FAST || (q >= y0 && q < y1));
                 const bool store = k == BT - 1 && owned;
@@ -508,27 +511,40 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
         return true;
     };
 
-    // steady-state rows of an interior strip: every level computes and stores, no lattice edge.
-    // Measured on GB300 (8192^2, GLUPS): the FP16-deviation form gains from the separate path
-    // without edge tests (199.5 against 190.1), the FP32 form loses (196.9 against 220.4), so
-    // FP32 takes the general path for every row.  An L2 prefetch of the rows beyond the ring
-    // (cp.async.bulk.prefetch.tensor) lost in both forms (FP32 212.8 against 220.4, FP16 173.7
-    // against 199.5) and is not used.
-    const int f0 = max(y0 + BT, BT + 1), f1 = (xedge || !F16) ? f0 : min(min(y1 + BT, yhi), ny);
+    // Steady-state rows (every level computes and stores, no lattice top or bottom, no segment
+    // end) of the FP16-deviation form run a copy of the row without those tests, and without the
+    // left and right edge tests in interior strips.  Measured on GB300 (8192^2, GLUPS, one wave
+    // of units): the FP16-deviation form gains from the separate interior path (199.5 against
+    // 190.1), the FP32 form does not (196.9 against 220.4; with the several-wave plan 241.2
+    // against 240.0 on 8192^2 but 173.4 against 180.1 on 2048^2), so FP32 takes the general path
+    // for every row.  An L2 prefetch of the rows beyond the ring (cp.async.bulk.prefetch.tensor)
+    // lost in both forms (FP32 212.8 against 220.4, FP16 173.7 against 199.5) and is not used.
+    using General = std::integral_constant<int, 0>;
+    using Interior = std::integral_constant<int, 1>;
+    using EdgeStrip = std::integral_constant<int, 2>;
+    const int f0 = max(y0 + BT, BT + 1), f1 = !F16 ? f0 : min(min(y1 + BT, yhi), ny);
     bool ok = true;
     int i = ylo;
     for (; i < f0 && i < y1 + BT; ++i)
-        if (!row(std::false_type{}, i, wa, wa)) {
+        if (!row(General{}, i, wa, wa)) {
             ok = false;
             break;
         }
-    for (; ok && i < f1; ++i)
-        if (!row(std::true_type{}, i, wa, wa)) {
-            ok = false;
-            break;
-        }
+    if (F16 && xedge) {  // (FP32 never runs these loops: f1 = f0)
+        for (; ok && i < f1; ++i)
+            if (!row(EdgeStrip{}, i, wa, wa)) {
+                ok = false;
+                break;
+            }
+    } else {
+        for (; ok && i < f1; ++i)
+            if (!row(Interior{}, i, wa, wa)) {
+                ok = false;
+                break;
+            }
+    }
     for (; ok && i < y1 + BT; ++i)
-        if (!row(std::false_type{}, i, wa, wa)) {
+        if (!row(General{}, i, wa, wa)) {
             ok = false;
             break;
         }
@@ -685,18 +701,18 @@ cudaError_t allow_smem_stream() {
 
 }  // namespace
 
-StreamPlan stream_plan(int nx, int ny, int resident_warps, bool f16) {
+StreamPlan stream_plan(int nx, int ny, int resident_warps) {
     // Units in k full waves of the resident warps (k x resident / strips row segments per
     // strip): the warps of a wave start together and stream their rows in step, and later waves
     // start as blocks of the earlier ones finish, which spreads the GPU's row copies and
     // arithmetic over time; a wave only partly filled leaves SMs idle at the end.  Every segment
     // pays a 4-row halo at each end, so k is the largest that keeps segments of at least 80
-    // rows, at most 3 (FP32) or 5 (FP16-deviation).  Measured on GB300 against the best
-    // number of waves at each size: within 1.6 % from 2048^2 to 8192^2 (8192^2: one wave 225.1 and
-    // 207.5 GLUPS, this plan 240.1 and 253.6).
+    // rows, at most 3.  Measured on GB300 against the best number of waves at each size, both
+    // forms: within 1.5 % from 2048^2 to 8192^2 (8192^2: one wave 225.1 (FP32) and 240.4
+    // (FP16-deviation) GLUPS, three 240.1 and 264.6).
     StreamPlan p;
     p.n_strips = (nx + OUTW - 1) / OUTW;
-    const int max_waves = f16 ? 5 : 3, min_rows = 80;
+    const int max_waves = 3, min_rows = 80;
     int segs = 1;
     for (int k = 1; k <= max_waves; ++k) {
         int sk = (int)((long long)k * resident_warps / p.n_strips);
