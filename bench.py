@@ -248,9 +248,11 @@ def cpu_model():
     return "unknown"
 
 
-def oracle_sample(inst, threads, target_s):
+def oracle_sample(inst, threads, target_s, accumulate=True):
     """The oracle as it stands, on `threads` host cores: a bounded sample of one instance's
-    hot path (plain steps, one accumulated period, the contour integral)."""
+    hot path (plain steps, one accumulated period, the contour integral), or of its plain steps
+    only (accumulate=False: for lattices where one period alone would take far longer than
+    target_s)."""
     from oracle import geometry as G
     from oracle import lbm as OL
     from oracle import mst
@@ -260,33 +262,37 @@ def oracle_sample(inst, threads, target_s):
     t0 = time.perf_counter()
     sim.advance(4)
     per_step = (time.perf_counter() - t0) / 4
-    T = inst["period"]
-    n_plain = max(0, int(target_s / per_step) - T)
+    T = inst["period"] if accumulate else 0
+    n_plain = max(1 if not accumulate else 0, int(target_s / per_step) - T)
     t0 = time.perf_counter()
     sim.advance(n_plain)
-    sim.advance(T, accumulate=True)
-    cx, cy = G.default_center(inst["nx"], inst["ny"])
-    mst.force_torque(*sim.phasors(), cx, cy, inst["R"], mst.default_n_points(inst["R"]), inst["a"])
+    if accumulate:
+        sim.advance(T, accumulate=True)
+        cx, cy = G.default_center(inst["nx"], inst["ny"])
+        mst.force_torque(*sim.phasors(), cx, cy, inst["R"], mst.default_n_points(inst["R"]), inst["a"])
     el = time.perf_counter() - t0
     steps = n_plain + T
     return {"mlups": round(inst["nx"] * inst["ny"] * steps / el / 1e6, 2), "threads": threads,
             "steps": steps, "seconds": round(el, 2)}
 
 
-def cpu_baseline(cfg1, cfg2, target_s):
+def cpu_baseline(cfg1, cfg2, slice1024, target_s):
     """The oracle on the host: the 256^2 homogeneous workload and one 512^2 instance of the
-    benchmark workload, each on one thread and on every core; the headline value is the
-    benchmark workload on every core."""
+    benchmark workload (whole hot path), and a 1024^2 instance of the 256-instance design map
+    (plain steps), each on one thread and on every core; the headline value is the benchmark
+    workload on every core."""
     threads = os.cpu_count() or 1
     runs = {}
-    for cname, inst in (("homogeneous_dielectric_256", cfg1), (WORKLOAD, cfg2)):
+    for cname, inst, acc in (("homogeneous_dielectric_256", cfg1, True), (WORKLOAD, cfg2, True),
+                             ("design_map_1024_slice_plain_steps", slice1024, False)):
         for th in sorted({1, threads}):
-            runs[f"{cname}_{th}_threads"] = oracle_sample(inst, th, target_s)
+            runs[f"{cname}_{th}_threads"] = oracle_sample(inst, th, target_s, accumulate=acc)
     main = runs[f"{WORKLOAD}_{threads}_threads"]
     return {"value": main["mlups"], "unit": "MLUPS", "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": (f"FP64 full-vector C oracle (OpenMP): bounded samples (~{target_s:.0f} s each) of one "
                        f"{cfg2['nx']}x{cfg2['ny']} instance of {WORKLOAD} and of the 256x256 homogeneous workload, "
-                       "plain steps + 1 accumulated period + contour integral, on 1 thread and on every core; "
+                       "plain steps + 1 accumulated period + contour integral, and plain steps of a 1024x1024 "
+                       "instance of the 256-instance design map, on 1 thread and on every core; "
                        f"value = {WORKLOAD} on {threads} threads"),
             "runs": runs}
 
@@ -745,7 +751,9 @@ def main():
                              "precision": "f32 lattice, f64 accumulation; error against the same batch in f64"}
 
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        out["cpu_baseline"] = cpu_baseline(W.homogeneous_dielectric_256()[0], instances[0], args.cpu_seconds)
+        slice1024 = next(i for i in W.design_map_256(4, 256) if i["nx"] == 1024)
+        out["cpu_baseline"] = cpu_baseline(W.homogeneous_dielectric_256()[0], instances[0], slice1024,
+                                           args.cpu_seconds)
 
     for s in solvers:
         s.close()
