@@ -279,6 +279,17 @@ lbm_em_status lbm_em_probe_bounded_wait(int64_t limit_cycles);
  * Asynchronous; LBM_EM_EINVAL for iters < 1 or a NULL output. */
 lbm_em_status lbm_em_probe_fp64_fma(void *stream, int64_t iters, double *fma_per_launch);
 
+/* Check of the FP16-deviation rebuild that the four-step kernel uses (the paper has no
+ * counterpart): f = eq2 / 2 - g 2^m with each FP16 deviation g taken straight into a
+ * mixed-precision FMA, against converting g to FP32 first and using the FP32 FMA.  g2[n] holds
+ * pairs of FP16 deviations (low and high half, both are used), eq2[n] FP32 values of 2 f^eq, m
+ * the exponent of the inverse scale (-24 .. 15: -2^m is an FP16 number); host arrays, read
+ * only.  *mismatches = the number of the 2 n results whose bits differ (a NaN against a NaN
+ * counts as equal).  Synchronous, on the legacy default stream; LBM_EM_EINVAL for n < 1, m out
+ * of range or a NULL pointer, LBM_EM_ENOMEM if the device copies cannot be allocated. */
+lbm_em_status lbm_em_probe_f16_rebuild(const uint32_t *g2, const float *eq2, int64_t n, int32_t m,
+                                       int64_t *mismatches);
+
 /* Bytes this library has copied host -> device (*h2d) and device -> host (*d2h) in the calls
  * of the solver and the batch since it was loaded (either pointer may be NULL): e.g. the
  * transfer volume of one end-to-end run is the difference of two readings.  The library

@@ -622,7 +622,7 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     if (h->s4) {
         int warps = 0;
         TRY(stream_prepare(h->prec == LBM_EM_F16DEV, &warps), "configuring the four-step kernel");
-        h->s4_plan = stream_plan(h->nx, h->ny, warps);
+        h->s4_plan = stream_plan(h->nx, h->ny, warps, h->prec == LBM_EM_F16DEV);
         for (int b = 0; b < 2; ++b)
             TRY(encode_stream_maps(&h->s4_smap[b], &h->s4_fmap[b], b == 0 ? &h->s4_imap : nullptr, h->buf[b],
                                    h->prec == LBM_EM_F16DEV, h->d_mat, h->nx, h->ny, h->pitch, h->pstride),

@@ -7,9 +7,13 @@
 // This probe runs that same wait (mbar_wait) in one block on an mbarrier that nothing ever
 // arrives on, with a short limit, and reports the outcome exactly as a kernel's timeout is
 // reported: LBM_EM_ETIMEOUT.  No copy is in flight, so the device stays usable.
+#include <algorithm>
+#include <cmath>
+
 #include "../../include/lbm_em.h"
 #include "common.cuh"
 #include "runtime.h"
+#include "step_f16.cuh"
 #include "tma.cuh"
 
 namespace lbmem {
@@ -49,10 +53,62 @@ __global__ void __launch_bounds__(kFmaThreads) k_fp64_fma(long long iters, doubl
     if (s == -1.0) g_fp64_sink = s;  // never true for the host's arguments (every chain stays > 0)
 }
 
+// The FP16-deviation rebuild with the mixed-precision FMA (rebuild_h) against the converting one
+// (rebuild), both halves of every pair: counts the results whose bits differ.
+__global__ void k_f16_rebuild_probe(const unsigned *__restrict__ g2, const float *__restrict__ eq2, long long n,
+                                    unsigned short nis, float inv, unsigned long long *bad) {
+    unsigned long long d = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned g = g2[i];
+        const float e = eq2[i];
+        const __half lo = __ushort_as_half((unsigned short)(g & 0xffffu));
+        const __half hi = __ushort_as_half((unsigned short)(g >> 16));
+        const float m[2] = {rebuild_h<false>(e, g, nis), rebuild_h<true>(e, g, nis)};
+        const float r[2] = {rebuild(e, lo, inv), rebuild(e, hi, inv)};
+        for (int j = 0; j < 2; ++j)
+            d += !(__float_as_uint(m[j]) == __float_as_uint(r[j]) || (isnan(m[j]) && isnan(r[j])));
+    }
+    if (d) atomicAdd(bad, d);
+}
+
 }  // namespace
 }  // namespace lbmem
 
 using namespace lbmem;
+
+extern "C" lbm_em_status lbm_em_probe_f16_rebuild(const uint32_t *g2, const float *eq2, int64_t n, int32_t m,
+                                                   int64_t *mismatches) {
+    if (!g2 || !eq2 || !mismatches || n < 1 || m < -24 || m > 15)
+        return set_error(LBM_EM_EINVAL, "need arrays of n >= 1 values, an output and -24 <= m <= 15");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return set_error(LBM_EM_ECUDA, "no CUDA device available (the solver has no CPU path)");
+    }
+    // -2^m in FP16: normal from 2^-14, subnormal below
+    const unsigned short nis = (unsigned short)(0x8000u | (m >= -14 ? (unsigned)(m + 15) << 10 : 1u << (m + 24)));
+    void *dg = nullptr, *de = nullptr, *db = nullptr;
+    lbm_em_status st = cuda_status(dmalloc(&dg, (size_t)n * 4), "cudaMalloc(probe)");
+    if (!st) st = cuda_status(dmalloc(&de, (size_t)n * 4), "cudaMalloc(probe)");
+    if (!st) st = cuda_status(dmalloc(&db, 8), "cudaMalloc(probe)");
+    if (!st) st = cuda_status(copy_async(dg, g2, (size_t)n * 4, cudaMemcpyHostToDevice, 0), "upload");
+    if (!st) st = cuda_status(copy_async(de, eq2, (size_t)n * 4, cudaMemcpyHostToDevice, 0), "upload");
+    if (!st) st = cuda_status(cudaMemsetAsync(db, 0, 8, 0), "clear");
+    if (!st) {
+        const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+        k_f16_rebuild_probe<<<(unsigned)blocks, 256>>>((const unsigned *)dg, (const float *)de, (long long)n, nis,
+                                                       std::ldexp(1.0f, m), (unsigned long long *)db);
+        st = cuda_status(cudaGetLastError(), "probe launch");
+    }
+    unsigned long long bad = 0;
+    if (!st) st = cuda_status(copy_async(&bad, db, 8, cudaMemcpyDeviceToHost, 0), "read");
+    if (!st) st = cuda_status(cudaStreamSynchronize(0), "cudaStreamSynchronize");
+    dfree(dg);
+    dfree(de);
+    dfree(db);
+    if (!st) *mismatches = (int64_t)bad;
+    return st;
+}
 
 extern "C" lbm_em_status lbm_em_probe_fp64_fma(void *stream, int64_t iters, double *fma_per_launch) {
     if (iters < 1 || !fma_per_launch) return set_error(LBM_EM_EINVAL, "need iters >= 1 and an output");

@@ -47,10 +47,29 @@ __device__ __forceinline__ float eq2_emx(float e, float hx, float hy) { return _
 __device__ __forceinline__ float eq2_epy(float e, float hx, float hy) { return __fadd_rn(e, hx); }
 __device__ __forceinline__ float eq2_emy(float e, float hx, float hy) { return __fsub_rn(e, hx); }
 
-// f = eq2 / 2 - g / 2^10
+// f = eq2 / 2 - g * inv_scale (inv_scale = 2^(k - 10), the inverse of the deviation scale)
 __device__ __forceinline__ float rebuild(float eq2, __half g, float inv_scale) {
     return __fmaf_rn(-__half2float(g), inv_scale, __fmul_rn(eq2, 0.5f));
 }
+
+// f = eq2 / 2 + g * nis, nis = -2^(k - 10): the value of rebuild() with the FP16
+// deviation g taken straight into the FMA, one of the pair g2 (HI: the high half).  The
+// mixed-precision fma (PTX fma.rn.f32.f16, sm_100 and later) multiplies two FP16 operands and
+// adds an FP32 one with a single rounding to FP32; FP16 values and -2^(k - 10) are exact in FP32,
+// so this is the FP32 FMA of rebuild() without the separate conversion of g.  nis must be
+// exactly representable in FP16 (k >= -14).
+template <bool HI>
+__device__ __forceinline__ float rebuild_h(float eq2, unsigned g2, unsigned short nis) {
+    float r;
+    if constexpr (HI)
+        asm("{\n\t.reg .f16 l, h;\n\tmov.b32 {l, h}, %1;\n\tfma.rn.f32.f16 %0, h, %2, %3;\n\t}"
+            : "=f"(r) : "r"(g2), "h"(nis), "f"(__fmul_rn(eq2, 0.5f)));
+    else
+        asm("{\n\t.reg .f16 l, h;\n\tmov.b32 {l, h}, %1;\n\tfma.rn.f32.f16 %0, l, %2, %3;\n\t}"
+            : "=f"(r) : "r"(g2), "h"(nis), "f"(__fmul_rn(eq2, 0.5f)));
+    return r;
+}
+
 // Encoding g = (f - eq2 / 2) * s, rounded to FP16, as one FMA: f * s - (eq2 / 2) * s.  The
 // scale s is a power of two, and scaling by one commutes with rounding, so the FMA's single
 // rounding gives the value of "subtract, round, scale"; a result that underflows FP32's normal

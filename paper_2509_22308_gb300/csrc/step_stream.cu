@@ -17,16 +17,18 @@
 // for its own row copies (bounded waits, as in the tile kernels).
 //
 // The per-site arithmetic is the one-step kernel's (update_site), so the FP32 form gives the
-// bits of four one-step launches.  The FP16-deviation form rebuilds each stored row (fields
-// and FP16 deviations) into FP32 post-collision populations, runs levels 1-3 in FP32 and
-// stores the fields and deviations of level 4: its state is rounded to FP16 once per launch
-// instead of once per step, so it differs from one step per launch by FP16 rounding noise.
+// bits of four one-step launches.  The FP16-deviation form rebuilds the stored state (fields
+// and FP16 deviations) into FP32 post-collision populations as level 0 reads it, runs levels
+// 1-3 in FP32 and stores the fields and deviations of level 4: its state is rounded to FP16
+// once per launch instead of once per step, so it differs from one step per launch by FP16
+// rounding noise.
 //
 // Each state element crosses HBM once per four steps: 89 B per four FP32 updates, 69 B per
 // four FP16-deviation updates, plus the 8 halo columns of every 56 that the neighbouring
 // strips also read (served by L2 when they run at about the same time).
 #include <cuda_fp16.h>
 
+#include <cmath>
 #include <type_traits>
 
 #include "common.cuh"
@@ -56,9 +58,10 @@ static_assert(IDBOX >= LW + 12 && IDBOX % 16 == 0, "the id box covers the strip 
 // -y pairs of the last lattice row per level (the bottom edge, see below).  Level 0 (the stored
 // state) is read straight from the slots, so a row's slot stays in use until the row two further
 // on has arrived: 5 slots, 3 rows in use and 2 in flight.  The FP16-deviation form's copies
-// (deviations, then fields) fill the first 2432 bytes of the slot; on arrival each lane rebuilds
-// its two sites into FP32 populations and writes them over the slot in the FP32 row layout, so
-// from there on both forms read the same rows.
+// (deviations, then fields) fill the first 2432 bytes of the slot.  With the mixed-precision
+// rebuild (|E0| >= 2^-14) level 0 reads them as they are and rebuilds each population where it
+// reads it; otherwise, on arrival, each lane rebuilds its two sites into FP32 populations and
+// writes them over the slot in the FP32 row layout, which level 0 then reads as in FP32.
 template <bool F16>
 struct Layout {
     static constexpr int RING = 5;
@@ -193,16 +196,36 @@ struct Wave {
     unsigned ids[BT];
 };
 
+// The stored fields of a lane's two sites in an FP16-deviation row slot, one of its deviation
+// pairs, and a plane's two rebuilt populations f* = eq2 / 2 + g nis (rebuild_h, step_f16.cuh).
+struct Fld2 {
+    float2 e, hx, hy;
+};
+__device__ __forceinline__ Fld2 slot_fields(const unsigned char *sl, int lane) {
+    const float2 *fl = reinterpret_cast<const float2 *>(sl + Layout<true>::FLD);
+    return Fld2{fl[lane], fl[LW / 2 + lane], fl[LW + lane]};
+}
+__device__ __forceinline__ unsigned slot_dev(const unsigned char *sl, int plane, int lane) {
+    return reinterpret_cast<const unsigned *>(reinterpret_cast<const __half *>(sl) + DEVOFF + plane * DEVW)[lane];
+}
+__device__ __forceinline__ void rebuild2(float eq2a, float eq2b, unsigned g2, unsigned short nis, float o[2]) {
+    o[0] = rebuild_h<false>(eq2a, g2, nis);
+    o[1] = rebuild_h<true>(eq2b, g2, nis);
+}
+
 // One row of level 0 from a slot: FP32 as staged; FP16-deviation rebuilt in place first (see
-// Layout).
-template <bool F16>
+// Layout) by converting each deviation (inv_scale = 2^(k - 10)), unless MIX: then the level-0
+// reads rebuild each population with the mixed-precision FMA (slot_fields, slot_dev below).
+template <bool F16, bool MIX>
 __device__ __forceinline__ void take_row(unsigned char *sl, int lane, float inv_scale) {
-    if constexpr (F16) {
+    if constexpr (F16 && !MIX) {
         const __half *dv = reinterpret_cast<const __half *>(sl) + DEVOFF;
         const float *fl = reinterpret_cast<const float *>(sl + Layout<F16>::FLD);
         const float2 fe = reinterpret_cast<const float2 *>(fl)[lane];
         const float2 fhx = reinterpret_cast<const float2 *>(fl + LW)[lane];
         const float2 fhy = reinterpret_cast<const float2 *>(fl + 2 * LW)[lane];
+        // the post-collision populations of the stored state: f* = f^eq - g
+        Pop<float> na, nb;
         __half ga[NPLANES], gb[NPLANES];
 #pragma unroll
         for (int p = 0; p < NPLANES; ++p) {
@@ -210,8 +233,6 @@ __device__ __forceinline__ void take_row(unsigned char *sl, int lane, float inv_
             ga[p] = __low2half(g2);
             gb[p] = __high2half(g2);
         }
-        // the post-collision populations of the stored state: f* = f^eq - g
-        Pop<float> na, nb;
         rebuild_all(ga, Fld{fe.x, fhx.x, fhy.x}, inv_scale, na);
         rebuild_all(gb, Fld{fe.y, fhx.y, fhy.y}, inv_scale, nb);
         __syncwarp();  // every lane has read the copies before any lane overwrites them
@@ -242,6 +263,7 @@ struct UnitCtx {
     int ay0, ay1, period;
     size_t pstride;
     float scale, inv_scale;                       // FP16-deviation form
+    unsigned short nis;                           // -inv_scale in FP16 (the MIX kernel)
     float *fout;                                  // FP32: the output state (11 planes)
     __half *g_out;                                // FP16-deviation: output planes
     float *fe_out, *fhx_out, *fhy_out;
@@ -289,8 +311,9 @@ __device__ __forceinline__ void acc_owned(const UnitCtx &u, int x, int q, long l
 }
 
 // Four steps of one work unit (see the top of this file).  Returns false after a bounded wait
-// for a row copy gave up.  bad: set when a stored site's field ran away.
-template <bool F16, int POL, bool ACC>
+// for a row copy gave up.  bad: set when a stored site's field ran away.  SPLIT: the
+// steady-state rows take the copies of the row loop without the general loop's tests.
+template <bool F16, int POL, bool ACC, bool SPLIT, bool MIX = false>
 __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, RingState &R, bool &bad) {
     static_assert(!(F16 && ACC), "the FP16-deviation kernel does not accumulate");
     using LY = Layout<F16>;
@@ -346,7 +369,7 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
         if (FAST || i < yhi) {
             const bool ok = mbar_wait(&bars[s0], ph);
             if (__any_sync(0xffffffffu, !ok)) return false;
-            take_row<F16>(ring + (size_t)s0 * LY::SLOT, lane, u.inv_scale);
+            take_row<F16, MIX>(ring + (size_t)s0 * LY::SLOT, lane, u.inv_scale);
         }
         Pop<float> na{}, nb{};  // level k of row i - k, the -y pair for level k + 1
         bool have = FAST || i < yhi;
@@ -363,25 +386,48 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
                     // and last rows and at the segment's first row (whose row above was never
                     // loaded: its level-1 value is a halo value no output depends on)
                     const unsigned char *sq = ring + (size_t)s1 * LY::SLOT;
-                    const float *rq = reinterpret_cast<const float *>(sq);
-                    const float *ru =
-                        reinterpret_cast<const float *>(ring + (size_t)(FAST || q > ylo ? s2 : s1) * LY::SLOT);
-                    const float *rd =
-                        reinterpret_cast<const float *>(ring + (size_t)(FAST || q < ny - 1 ? s0 : s1) * LY::SLOT);
+                    const unsigned char *su = ring + (size_t)(FAST || q > ylo ? s2 : s1) * LY::SLOT;
+                    const unsigned char *sd = ring + (size_t)(FAST || q < ny - 1 ? s0 : s1) * LY::SLOT;
                     Row9 c0;
                     float ey[2], hy[2], my[2], mh[2];
-                    float2 v;
-                    v = lds2(rq, P_EZ, lane), c0.ez[0] = v.x, c0.ez[1] = v.y;
-                    v = lds2(rq, P_EPX, lane), c0.epx[0] = v.x, c0.epx[1] = v.y;
-                    v = lds2(rq, P_EMX, lane), c0.emx[0] = v.x, c0.emx[1] = v.y;
-                    v = lds2(rq, P_HXPX, lane), c0.hxpx[0] = v.x, c0.hxpx[1] = v.y;
-                    v = lds2(rq, P_HXMX, lane), c0.hxmx[0] = v.x, c0.hxmx[1] = v.y;
-                    v = lds2(rq, P_HXZ, lane), c0.hxz[0] = v.x, c0.hxz[1] = v.y;
-                    v = lds2(rq, P_HYZ, lane), c0.hyz[0] = v.x, c0.hyz[1] = v.y;
-                    v = lds2(ru, P_EPY, lane), ey[0] = v.x, ey[1] = v.y;
-                    v = lds2(ru, P_HYPY, lane), hy[0] = v.x, hy[1] = v.y;
-                    v = lds2(rd, P_EMY, lane), my[0] = v.x, my[1] = v.y;
-                    v = lds2(rd, P_HYMY, lane), mh[0] = v.x, mh[1] = v.y;
+                    if constexpr (F16 && MIX) {
+                        // the stored deviations rebuilt where they are read, each with its own row's
+                        // fields: row q's seven in-row populations, row q - 1's +y pair, row q + 1's
+                        // -y pair (every population of every row is read, and rebuilt, once)
+                        const unsigned short nis = u.nis;
+                        const Fld2 Q = slot_fields(sq, lane), U = slot_fields(su, lane), D = slot_fields(sd, lane);
+                        rebuild2(Q.e.x, Q.e.y, slot_dev(sq, P_EZ, lane), nis, c0.ez);
+                        rebuild2(eq2_epx(Q.e.x, Q.hx.x, Q.hy.x), eq2_epx(Q.e.y, Q.hx.y, Q.hy.y),
+                                 slot_dev(sq, P_EPX, lane), nis, c0.epx);
+                        rebuild2(eq2_emx(Q.e.x, Q.hx.x, Q.hy.x), eq2_emx(Q.e.y, Q.hx.y, Q.hy.y),
+                                 slot_dev(sq, P_EMX, lane), nis, c0.emx);
+                        rebuild2(Q.hx.x, Q.hx.y, slot_dev(sq, P_HXPX, lane), nis, c0.hxpx);
+                        rebuild2(Q.hx.x, Q.hx.y, slot_dev(sq, P_HXMX, lane), nis, c0.hxmx);
+                        rebuild2(Q.hx.x, Q.hx.y, slot_dev(sq, P_HXZ, lane), nis, c0.hxz);
+                        rebuild2(Q.hy.x, Q.hy.y, slot_dev(sq, P_HYZ, lane), nis, c0.hyz);
+                        rebuild2(eq2_epy(U.e.x, U.hx.x, U.hy.x), eq2_epy(U.e.y, U.hx.y, U.hy.y),
+                                 slot_dev(su, P_EPY, lane), nis, ey);
+                        rebuild2(U.hy.x, U.hy.y, slot_dev(su, P_HYPY, lane), nis, hy);
+                        rebuild2(eq2_emy(D.e.x, D.hx.x, D.hy.x), eq2_emy(D.e.y, D.hx.y, D.hy.y),
+                                 slot_dev(sd, P_EMY, lane), nis, my);
+                        rebuild2(D.hy.x, D.hy.y, slot_dev(sd, P_HYMY, lane), nis, mh);
+                    } else {
+                        const float *rq = reinterpret_cast<const float *>(sq);
+                        const float *ru = reinterpret_cast<const float *>(su);
+                        const float *rd = reinterpret_cast<const float *>(sd);
+                        float2 v;
+                        v = lds2(rq, P_EZ, lane), c0.ez[0] = v.x, c0.ez[1] = v.y;
+                        v = lds2(rq, P_EPX, lane), c0.epx[0] = v.x, c0.epx[1] = v.y;
+                        v = lds2(rq, P_EMX, lane), c0.emx[0] = v.x, c0.emx[1] = v.y;
+                        v = lds2(rq, P_HXPX, lane), c0.hxpx[0] = v.x, c0.hxpx[1] = v.y;
+                        v = lds2(rq, P_HXMX, lane), c0.hxmx[0] = v.x, c0.hxmx[1] = v.y;
+                        v = lds2(rq, P_HXZ, lane), c0.hxz[0] = v.x, c0.hxz[1] = v.y;
+                        v = lds2(rq, P_HYZ, lane), c0.hyz[0] = v.x, c0.hyz[1] = v.y;
+                        v = lds2(ru, P_EPY, lane), ey[0] = v.x, ey[1] = v.y;
+                        v = lds2(ru, P_HYPY, lane), hy[0] = v.x, hy[1] = v.y;
+                        v = lds2(rd, P_EMY, lane), my[0] = v.x, my[1] = v.y;
+                        v = lds2(rd, P_HYMY, lane), mh[0] = v.x, mh[1] = v.y;
+                    }
                     if (NOX)
                         pull_row(c0, ey, hy, my, mh, false, false, false, ca, cb);
                     else
@@ -511,18 +557,20 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
         return true;
     };
 
-    // Steady-state rows (every level computes and stores, no lattice top or bottom, no segment
-    // end) of the FP16-deviation form run a copy of the row without those tests, and without the
-    // left and right edge tests in interior strips.  Measured on GB300 (8192^2, GLUPS, one wave
-    // of units): the FP16-deviation form gains from the separate interior path (199.5 against
-    // 190.1), the FP32 form does not (196.9 against 220.4; with the several-wave plan 241.2
-    // against 240.0 on 8192^2 but 173.4 against 180.1 on 2048^2), so FP32 takes the general path
-    // for every row.  An L2 prefetch of the rows beyond the ring (cp.async.bulk.prefetch.tensor)
-    // lost in both forms (FP32 212.8 against 220.4, FP16 173.7 against 199.5) and is not used.
+    // With SPLIT, the steady-state rows (every level computes and stores, no lattice top or
+    // bottom, no segment end) run copies of the row without those tests: one for interior strips,
+    // without the left and right edge tests too, one for the two strips at the lattice's edges.
+    // Measured on GB300 (GLUPS on 8192^2 / 2048^2): FP32 with the general loop for every row
+    // 240.1 / 180.3, with both copies 257.2 / 195.0; FP16-deviation with the interior copy only
+    // (the edge strips, on the general loop, then finish last) 253.5 / 166.8, with both copies
+    // 263.4 / 187.2.  The batch kernel takes the copies where it does not accumulate (256-instance
+    // design map 116.6 -> 129.6 cells/s); with the accumulation they spill.  An L2
+    // prefetch of the rows beyond the ring (cp.async.bulk.prefetch.tensor) lost in both forms
+    // (FP32 212.8 against 220.4, FP16 173.7 against 199.5, with one wave of units) and is not used.
     using General = std::integral_constant<int, 0>;
     using Interior = std::integral_constant<int, 1>;
     using EdgeStrip = std::integral_constant<int, 2>;
-    const int f0 = max(y0 + BT, BT + 1), f1 = !F16 ? f0 : min(min(y1 + BT, yhi), ny);
+    const int f0 = max(y0 + BT, BT + 1), f1 = !SPLIT ? f0 : min(min(y1 + BT, yhi), ny);
     bool ok = true;
     int i = ylo;
     for (; i < f0 && i < y1 + BT; ++i)
@@ -530,7 +578,7 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
             ok = false;
             break;
         }
-    if (F16 && xedge) {  // (FP32 never runs these loops: f1 = f0)
+    if (SPLIT && xedge) {  // (without SPLIT these loops never run: f1 = f0)
         for (; ok && i < f1; ++i)
             if (!row(EdgeStrip{}, i, wa, wa)) {
                 ok = false;
@@ -553,9 +601,11 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
     return ok;
 }
 
-// F16: the FP16-deviation form (TM); otherwise FP32 of either polarization.  One work unit per
-// warp: strip unit % n_strips, row segment unit / n_strips.
-template <bool F16, int POL>
+
+// F16: the FP16-deviation form (TM; MIX: rebuilt with the mixed-precision FMA); otherwise FP32
+// of either polarization.  One work unit per warp: strip unit % n_strips, row segment unit /
+// n_strips.
+template <bool F16, int POL, bool MIX>
 __global__ void __launch_bounds__(NW * 32, 3)
     k_step4_stream(const __grid_constant__ UnitCtx u, const StreamArgs a, const __grid_constant__ CUtensorMap smap,
                    const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap imap,
@@ -595,7 +645,7 @@ __global__ void __launch_bounds__(NW * 32, 3)
     r.src_inc = sp.inc;
     RingState R{ring, bars[warp], reinterpret_cast<float4 *>(ring + RING * LY::SLOT), 0, 0u};
     bool bad = false;
-    const bool ok = stream_unit<F16, POL, false>(u, r, R, bad);
+    const bool ok = stream_unit<F16, POL, false, true, MIX>(u, r, R, bad);
     if (lane == 0 && !ok) atomicOr(a.err, kErrTimeout);
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrUnstable);
 }
@@ -677,7 +727,7 @@ __global__ void __launch_bounds__(NW * 32, 3)
         }
         __syncwarp();
         bool bad = false;
-        const bool ok = stream_unit<false, POL, ACC>(u, r, R, bad);
+        const bool ok = stream_unit<false, POL, ACC, !ACC>(u, r, R, bad);
         if (!ok) {  // a row copy never completed: report, leave
             if (lane == 0) atomicOr(err + un.x, kErrTimeout);
             return;
@@ -693,26 +743,27 @@ __global__ void k_batch_source4(const SourceParams *__restrict__ src, int n, con
     if (i < n) out[i] = source_levels_f(src[i], *t_in);
 }
 
-template <bool F16, int POL>
+template <bool F16, int POL, bool MIX>
 cudaError_t allow_smem_stream() {
-    return cudaFuncSetAttribute(k_step4_stream<F16, POL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_step4_stream<F16, POL, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Layout<F16>::SMEM);
 }
 
 }  // namespace
 
-StreamPlan stream_plan(int nx, int ny, int resident_warps) {
+StreamPlan stream_plan(int nx, int ny, int resident_warps, bool f16) {
     // Units in k full waves of the resident warps (k x resident / strips row segments per
     // strip): the warps of a wave start together and stream their rows in step, and later waves
     // start as blocks of the earlier ones finish, which spreads the GPU's row copies and
     // arithmetic over time; a wave only partly filled leaves SMs idle at the end.  Every segment
-    // pays a 4-row halo at each end, so k is the largest that keeps segments of at least 80
-    // rows, at most 3.  Measured on GB300 against the best number of waves at each size, both
-    // forms: within 1.5 % from 2048^2 to 8192^2 (8192^2: one wave 225.1 (FP32) and 240.4
-    // (FP16-deviation) GLUPS, three 240.1 and 264.6).
+    // pays a 4-row halo at each end, so k is the largest that keeps segments of at least
+    // min_rows rows, at most max_waves: FP32 5 waves of at least 45 rows, FP16-deviation 3 of
+    // at least 80 (measured on GB300 from 2048^2 to 8192^2, each within 1.1 % of the best number
+    // of waves at every size; 8192^2: one wave 227.9 (FP32) and 240.4 (FP16) GLUPS, the plan
+    // 266.3 and 265.0).
     StreamPlan p;
     p.n_strips = (nx + OUTW - 1) / OUTW;
-    const int max_waves = 3, min_rows = 80;
+    const int max_waves = f16 ? 3 : 5, min_rows = f16 ? 80 : 45;
     int segs = 1;
     for (int k = 1; k <= max_waves; ++k) {
         int sk = (int)((long long)k * resident_warps / p.n_strips);
@@ -730,16 +781,17 @@ StreamPlan stream_plan(int nx, int ny, int resident_warps) {
 }
 
 cudaError_t stream_prepare(bool f16, int *resident_warps) {
-    cudaError_t e = f16 ? allow_smem_stream<true, POL_TM>() : allow_smem_stream<false, POL_TM>();
-    if (e == cudaSuccess && !f16) e = allow_smem_stream<false, POL_TE>();
+    cudaError_t e = f16 ? allow_smem_stream<true, POL_TM, false>() : allow_smem_stream<false, POL_TM, false>();
+    if (e == cudaSuccess && f16) e = allow_smem_stream<true, POL_TM, true>();
+    if (e == cudaSuccess && !f16) e = allow_smem_stream<false, POL_TE, false>();
     int dev = 0, sms = 0, per_sm = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = f16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step4_stream<true, POL_TM>, NW * 32,
-                                                                Layout<true>::SMEM)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step4_stream<false, POL_TM>, NW * 32,
-                                                                Layout<false>::SMEM);
+        e = f16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step4_stream<true, POL_TM, true>,
+                                                                NW * 32, Layout<true>::SMEM)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step4_stream<false, POL_TM, false>,
+                                                                NW * 32, Layout<false>::SMEM);
     if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
     if (e == cudaSuccess) *resident_warps = per_sm * sms * NW;
     return e;
@@ -856,13 +908,21 @@ cudaError_t launch_step4_stream(const StepArgs<float> &sa, const F16Args *fa, co
         a.fe_out = u.fe_out = fa->fe_out;
         a.fhx_out = u.fhx_out = fa->fhx_out;
         a.fhy_out = u.fhy_out = fa->fhy_out;
-        k_step4_stream<true, POL_TM>
-            <<<plan.grid, NW * 32, Layout<true>::SMEM, s>>>(u, a, *smap, *fmap, *imap, t_in, t_out);
+        // -inv_scale = -2^m in FP16: exact from 2^-24 (subnormal below 2^-14) to 2^15
+        const int m = std::ilogb(fa->inv_scale);
+        if (m >= -24 && m <= 15) {
+            u.nis = (unsigned short)(0x8000u | (m >= -14 ? (unsigned)(m + 15) << 10 : 1u << (m + 24)));
+            k_step4_stream<true, POL_TM, true>
+                <<<plan.grid, NW * 32, Layout<true>::SMEM, s>>>(u, a, *smap, *fmap, *imap, t_in, t_out);
+        } else {
+            k_step4_stream<true, POL_TM, false>
+                <<<plan.grid, NW * 32, Layout<true>::SMEM, s>>>(u, a, *smap, *fmap, *imap, t_in, t_out);
+        }
     } else if (sa.pol == POL_TE) {
-        k_step4_stream<false, POL_TE>
+        k_step4_stream<false, POL_TE, false>
             <<<plan.grid, NW * 32, Layout<false>::SMEM, s>>>(u, a, *smap, *smap, *imap, t_in, t_out);
     } else {
-        k_step4_stream<false, POL_TM>
+        k_step4_stream<false, POL_TM, false>
             <<<plan.grid, NW * 32, Layout<false>::SMEM, s>>>(u, a, *smap, *smap, *imap, t_in, t_out);
     }
     return cudaGetLastError();

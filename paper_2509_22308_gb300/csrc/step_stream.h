@@ -15,11 +15,11 @@ constexpr int kStreamLoadW = 64, kStreamHalo = 4, kStreamOutW = 56, kStreamWarps
 
 // How a lattice is cut into work units (a strip of kStreamOutW columns and a segment of
 // seg_rows rows each, one per warp): strips first, then row segments for a few full waves of
-// the resident warps (see stream_plan).
+// the resident warps (see stream_plan).  f16: the FP16-deviation kernel.
 struct StreamPlan {
     int n_strips, seg_rows, n_units, grid;
 };
-StreamPlan stream_plan(int nx, int ny, int resident_warps);
+StreamPlan stream_plan(int nx, int ny, int resident_warps, bool f16);
 
 // Once per device, outside stream capture: allows the kernels' shared memory and returns
 // the warps resident on the whole GPU (blocks per SM x SMs x kStreamWarps).

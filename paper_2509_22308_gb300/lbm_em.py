@@ -99,6 +99,8 @@ SIGNATURES = {
     "lbm_em_probe_bounded_wait": [ctypes.c_int64],
     "lbm_em_test_alloc_hook": [ctypes.c_int64, _P(ctypes.c_int64)],
     "lbm_em_probe_fp64_fma": [_vp, ctypes.c_int64, _P(ctypes.c_double)],
+    "lbm_em_probe_f16_rebuild": [_P(ctypes.c_uint32), _P(ctypes.c_float), ctypes.c_int64, ctypes.c_int32,
+                                 _P(ctypes.c_int64)],
     "lbm_em_transfer_bytes": [_P(ctypes.c_uint64), _P(ctypes.c_uint64)],
     "lbm_em_batch_create": [_P(Instance), ctypes.c_int32, _P(BatchOpts), _P(_vp)],
     "lbm_em_batch_run": [_vp],
@@ -316,6 +318,19 @@ def probe_fp64_fma(stream, iters) -> float:
     n = ctypes.c_double()
     _call("lbm_em_probe_fp64_fma", _stream_ptr(stream), ctypes.c_int64(int(iters)), ctypes.byref(n))
     return n.value
+
+
+def probe_f16_rebuild(g2, eq2, m) -> int:
+    """Bit mismatches between the four-step kernel's mixed-precision FP16 rebuild and the
+    converting one, over the pairs g2 (uint32) and values eq2 (float32) at inverse scale 2^m."""
+    g = np.ascontiguousarray(g2, dtype=np.uint32)
+    e = np.ascontiguousarray(eq2, dtype=np.float32)
+    if g.shape != e.shape:
+        raise ValueError("g2 and eq2 must have the same shape")
+    out = ctypes.c_int64()
+    _call("lbm_em_probe_f16_rebuild", g.ctypes.data_as(_P(ctypes.c_uint32)), e.ctypes.data_as(_P(ctypes.c_float)),
+          ctypes.c_int64(g.size), ctypes.c_int32(int(m)), ctypes.byref(out))
+    return out.value
 
 
 def transfer_bytes():

@@ -66,6 +66,38 @@ def test_reduced_precision_forms_meet_tolerances_at_any_amplitude(forces, name, 
         assert e < 4.0 * e1 + 1e-9, (prec, E0, e, e1)
 
 
+@pytest.mark.parametrize("E0", [1e-3, 1e3])
+def test_f16dev_four_steps_meet_tolerances_at_any_amplitude(forces, E0):
+    """The four-step FP16-deviation kernel takes the scale 2^(10 - k) of E0 like the other
+    kernels of the form: on the 512^2 metallo-dielectric instance its forces at E0 = 1e-3 and
+    1e3 are within the form's bound of FP64 and as accurate as at E0 = 1."""
+    md = W.md_janus_512()[2]
+    e = {}
+    for amp in (1.0, E0):
+        F64 = forces["md_janus_512", amp, "f64"]
+        F4 = L.run_instance(dict(md, E0=amp), "f16dev", steps_per_launch="four")
+        e[amp] = np.max(np.abs(F4 - F64)) / abs(F64[0])
+    assert e[E0] < 1e-3, e
+    assert e[E0] < 4.0 * e[1.0] + 1e-9, e
+
+
+@pytest.mark.parametrize("m", [-24, -20, -15, -14, -10, -1, 0, 15])
+def test_mixed_precision_fp16_rebuild_is_the_converting_one(m):
+    """The four-step FP16-deviation kernel rebuilds each stored deviation with the mixed-precision
+    FMA (FP16 deviation times -2^m plus an FP32 equilibrium, one rounding) wherever -2^m is an
+    FP16 number, |E0| >= 2^-14; the other kernels of the form convert the deviation to FP32 and
+    use the FP32 FMA.  Both must give the same bits for every FP16 value (normal, subnormal,
+    zero, infinite, NaN) against equilibria from subnormal to large, at every inverse scale the
+    kernel takes this path for."""
+    rng = np.random.default_rng(100 + m)
+    lo = np.tile(np.arange(65536, dtype=np.uint32), 8)
+    hi = rng.integers(0, 65536, lo.size, dtype=np.uint32)
+    g2 = lo | (hi << 16)
+    mag = 10.0 ** rng.uniform(-45.0, 10.0, lo.size)
+    eq2 = (np.where(rng.random(lo.size) < 0.5, -mag, mag) * (rng.random(lo.size) > 0.01)).astype(np.float32)
+    assert L.probe_f16_rebuild(g2, eq2, m) == 0
+
+
 HEADER = 40  # bytes of the checkpoint header (magic, precision, nx, ny, slots, t, n_acc)
 
 
