@@ -758,9 +758,9 @@ StreamPlan stream_plan(int nx, int ny, int resident_warps, bool f16) {
     // arithmetic over time; a wave only partly filled leaves SMs idle at the end.  Every segment
     // pays a 4-row halo at each end, so k is the largest that keeps segments of at least
     // min_rows rows, at most max_waves: FP32 5 waves of at least 45 rows, FP16-deviation 3 of
-    // at least 80 (measured on GB300 from 2048^2 to 8192^2, each within 1.1 % of the best number
-    // of waves at every size; 8192^2: one wave 227.9 (FP32) and 240.4 (FP16) GLUPS, the plan
-    // 266.3 and 265.0).
+    // at least 80 (measured on GB300 from 2048^2 to 8192^2, each within 1.5 % of the best number
+    // of waves at every size; 8192^2: one wave 227.9 (FP32) and 254.9 (FP16) GLUPS, the plan
+    // 266.3 and 277.5).
     StreamPlan p;
     p.n_strips = (nx + OUTW - 1) / OUTW;
     const int max_waves = f16 ? 3 : 5, min_rows = f16 ? 80 : 45;
