@@ -316,6 +316,9 @@ __device__ __forceinline__ void acc_owned(const UnitCtx &u, int x, int q, long l
 template <bool F16, int POL, bool ACC, bool SPLIT, bool MIX = false>
 __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, RingState &R, bool &bad) {
     static_assert(!(F16 && ACC), "the FP16-deviation kernel does not accumulate");
+    // the steady-state copies treat every computed row as owned, which holds for the stored level
+    // only: the Fourier sums of the levels before it would count halo rows twice
+    static_assert(!(ACC && SPLIT), "accumulating units take the general row loop");
     using LY = Layout<F16>;
     constexpr int RING = LY::RING;
     const int lane = (int)threadIdx.x & 31;
@@ -657,11 +660,13 @@ __global__ void __launch_bounds__(NW * 32, 3)
 // every launch and split the unfinished instances between them: ACC = false takes those with
 // no time of their accumulated (last) period among the launch's four, ACC = true the others,
 // whose Fourier sums it adds inside the levels whose time falls in that period.  (One kernel
-// doing both spilled: the accumulation's FP64 registers on top of the wavefront's.)  An
+// doing both spilled: the accumulation's FP64 registers on top of the wavefront's.)  ACC = true
+// runs 2 blocks per SM, so that those registers fit without spilling (256-instance design map
+// 129.3 -> 131.5 cells/s against 3 blocks with 306 bytes spilled), and the general row loop.  An
 // instance that ends inside a launch runs on past its end without accumulating; its state is
 // not needed afterwards.  FP32.
 template <int POL, bool ACC>
-__global__ void __launch_bounds__(NW * 32, 3)
+__global__ void __launch_bounds__(NW * 32, ACC ? 2 : 3)
     k_batch_step4(const StreamInst *__restrict__ insts, const int4 *__restrict__ units, int n_units,
                   const SrcLevels *__restrict__ srcs, const CUtensorMap *__restrict__ maps, int p,
                   float *__restrict__ buf_out, const int *__restrict__ slot, double *__restrict__ acc,
