@@ -85,8 +85,7 @@ extern "C" lbm_em_status lbm_em_probe_f16_rebuild(const uint32_t *g2, const floa
         cudaGetLastError();
         return set_error(LBM_EM_ECUDA, "no CUDA device available (the solver has no CPU path)");
     }
-    // -2^m in FP16: normal from 2^-14, subnormal below
-    const unsigned short nis = (unsigned short)(0x8000u | (m >= -14 ? (unsigned)(m + 15) << 10 : 1u << (m + 24)));
+    const unsigned short nis = f16_neg_pow2_bits(m);
     void *dg = nullptr, *de = nullptr, *db = nullptr;
     lbm_em_status st = cuda_status(dmalloc(&dg, (size_t)n * 4), "cudaMalloc(probe)");
     if (!st) st = cuda_status(dmalloc(&de, (size_t)n * 4), "cudaMalloc(probe)");

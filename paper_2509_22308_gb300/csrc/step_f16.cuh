@@ -58,6 +58,12 @@ __device__ __forceinline__ float rebuild(float eq2, __half g, float inv_scale) {
 // adds an FP32 one with a single rounding to FP32; FP16 values and -2^(k - 10) are exact in FP32,
 // so this is the FP32 FMA of rebuild() without the separate conversion of g.  nis must be
 // exactly representable in FP16 (k >= -14).
+// The FP16 bit pattern of -2^m, -24 <= m <= 15 (normal from 2^-14, subnormal below): the
+// nis operand of rebuild_h.
+inline unsigned short f16_neg_pow2_bits(int m) {
+    return (unsigned short)(0x8000u | (m >= -14 ? (unsigned)(m + 15) << 10 : 1u << (m + 24)));
+}
+
 template <bool HI>
 __device__ __forceinline__ float rebuild_h(float eq2, unsigned g2, unsigned short nis) {
     float r;

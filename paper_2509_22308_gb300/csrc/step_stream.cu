@@ -916,7 +916,7 @@ cudaError_t launch_step4_stream(const StepArgs<float> &sa, const F16Args *fa, co
         // -inv_scale = -2^m in FP16: exact from 2^-24 (subnormal below 2^-14) to 2^15
         const int m = std::ilogb(fa->inv_scale);
         if (m >= -24 && m <= 15) {
-            u.nis = (unsigned short)(0x8000u | (m >= -14 ? (unsigned)(m + 15) << 10 : 1u << (m + 24)));
+            u.nis = f16_neg_pow2_bits(m);
             k_step4_stream<true, POL_TM, true>
                 <<<plan.grid, NW * 32, Layout<true>::SMEM, s>>>(u, a, *smap, *fmap, *imap, t_in, t_out);
         } else {
