@@ -28,6 +28,7 @@
 // strips also read (served by L2 when they run at about the same time).
 #include <cuda_fp16.h>
 
+#include <climits>
 #include <cmath>
 #include <type_traits>
 
@@ -271,6 +272,7 @@ struct UnitCtx {
     const int *slot;                              // the lattice's slot map (pitch layout)
     double *acc;                                  // its accumulators (6 per slot)
     const double2 *cs;                            // (cos w t, sin w t) for t mod period
+    float *stage;                                 // STAGE: 12 FP32 fields per slot (see stream_unit)
 };
 
 // One work unit: a strip of the lattice (columns xs .. xs + 63, 16-byte aligned) and a segment
@@ -295,12 +297,39 @@ struct RingState {
     unsigned ph;
 };
 
-// Adds the phasor terms of one owned site at time tk (Sec. III: Fourier analysis over one
-// period) to its accumulators, when the site is a contour stencil site.
-__device__ __forceinline__ void acc_owned(const UnitCtx &u, int x, int q, long long tk, const double f3[3]) {
-    const int sl = u.slot[(size_t)q * u.pitch + x];
+// update_site<POL, true> (common.cuh) with the fields that enter the Fourier sums returned in
+// FP32: f3 holds the values update_site converts to FP64.  Converting only at the contour's
+// stencil sites (acc_owned) keeps FP64 conversions, slow on GB300's FP64 pipe, off the other
+// sites of the stencil rows.
+template <int POL>
+__device__ __forceinline__ bool update_site_f3(Pop<float> &p, const MatT<float> &m, unsigned rthr, float f3[3]) {
+    bool bad;
+    if constexpr (POL == POL_TM) {
+        float E3, Hx, Hy, D;
+        moments(p, m, &E3, &Hx, &Hy, &D);
+        bad = field_runaway(E3, rthr);
+        f3[0] = D * m.inv_eps;
+        f3[1] = Hx;
+        f3[2] = Hy;
+        collide(p, E3, Hx, Hy);
+    } else {
+        float Ey3, Ex3, Hz, Dy, Dx;
+        moments_te(p, m, &Ey3, &Ex3, &Hz, &Dy, &Dx);
+        bad = field_runaway(Ey3, rthr) || field_runaway(Ex3, rthr);
+        f3[0] = Hz;
+        f3[1] = Dx * m.inv_eps;
+        f3[2] = Dy * m.inv_eps;
+        collide_te(p, Ey3, Ex3, Hz);
+    }
+    return bad;
+}
+
+// Adds the phasor terms of one owned site (Sec. III: Fourier analysis over one period) to its
+// accumulators, when the site is a contour stencil site (its slot sl >= 0); c = (cos, sin) of
+// the site's time.
+__device__ __forceinline__ void acc_owned(const UnitCtx &u, int sl, double2 c, const float f3f[3]) {
     if (sl < 0) return;
-    const double2 c = u.cs[(int)(tk % (long long)u.period)];
+    const double f3[3] = {(double)f3f[0], (double)f3f[1], (double)f3f[2]};
     double *a = u.acc + 6 * (size_t)sl;
     a[0] += f3[0] * c.x;
     a[1] += f3[0] * c.y;
@@ -310,10 +339,25 @@ __device__ __forceinline__ void acc_owned(const UnitCtx &u, int x, int q, long l
     a[5] += f3[2] * c.y;
 }
 
+// STAGE: the FP32 fields of one owned stencil site (slot sl >= 0) at level k of the launch.
+__device__ __forceinline__ void stage_owned(float *stage, int sl, int k, const float f3f[3]) {
+    if (sl < 0) return;
+    float *s = stage + 12 * (size_t)sl + 3 * k;
+    s[0] = f3f[0];
+    s[1] = f3f[1];
+    s[2] = f3f[2];
+}
+
 // Four steps of one work unit (see the top of this file).  Returns false after a bounded wait
 // for a row copy gave up.  bad: set when a stored site's field ran away.  SPLIT: the
-// steady-state rows take the copies of the row loop without the general loop's tests.
-template <bool F16, int POL, bool ACC, bool SPLIT, bool MIX = false>
+// steady-state rows take the copies of the row loop without the general loop's tests.  ACC
+// with STAGE: instead of adding each stencil site's Fourier terms to its FP64 sums, store its
+// FP32 fields at level k to stage[12 slot + 3 k ..] for k_stage_flush, which adds them after the
+// launch in the same order (every level of the launch accumulates; the single domain).  The
+// direct adds cost a few FP64 instructions per stencil site, which on GB300's FP64 pipe made
+// the units along the contour's vertical tangents (a stencil site in every row) the launch's
+// long tail.
+template <bool F16, int POL, bool ACC, bool SPLIT, bool MIX = false, bool STAGE = false>
 __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, RingState &R, bool &bad) {
     static_assert(!(F16 && ACC), "the FP16-deviation kernel does not accumulate");
     // the steady-state copies treat every computed row as owned, which holds for the stored level
@@ -350,6 +394,13 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
             issue_row<F16>(r.smap, r.fmap, r.imap, xs, xid, ylo + j, ring + (size_t)sj * LY::SLOT, &bars[sj]);
         }
 
+    // ACC: (cos, sin) of the launch's four times, the phases of the levels' Fourier terms
+    double2 phase[BT];
+    if constexpr (ACC && !STAGE) {
+#pragma unroll
+        for (int k = 0; k < BT; ++k) phase[k] = u.cs[(int)((t + k) % (long long)u.period)];
+    }
+
     Wave wa;
 #pragma unroll
     for (int k = 0; k < BT; ++k) {
@@ -373,6 +424,19 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
             const bool ok = mbar_wait(&bars[s0], ph);
             if (__any_sync(0xffffffffu, !ok)) return false;
             take_row<F16, MIX>(ring + (size_t)s0 * LY::SLOT, lane, u.inv_scale);
+        }
+        // ACC: the slots of this lane's two sites in the rows whose Fourier sums the levels take,
+        // loaded before the levels' arithmetic so that the loads' latency overlaps it
+        int2 slots[BT];
+        if constexpr (ACC) {
+#pragma unroll
+            for (int k = 0; k < BT; ++k) {
+                const int q = i - 1 - k;
+                slots[k] = make_int2(-1, -1);
+                if (out_lane && t + k >= u.acc_from && t + k < u.steps && q >= u.ay0 && q <= u.ay1 &&
+                    (FAST || (q >= y0 && q < y1)))  // xa even, pitch a multiple of 32: 8-byte aligned
+                    slots[k] = *reinterpret_cast<const int2 *>(u.slot + (size_t)q * u.pitch + xa);
+            }
         }
         Pop<float> na{}, nb{};  // level k of row i - k, the -y pair for level k + 1
         bool have = FAST || i < yhi;
@@ -493,12 +557,17 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
                         (FAST || (q >= y0 && q < y1))) {
                         // a row of contour stencil sites in the accumulated period (uniform over the
                         // warp): the fields of the owned sites enter their Fourier sums
-                        double f3a[3], f3b[3];
-                        ra = update_site<POL, true>(ca, ma, u.runaway, f3a, nullptr);
-                        rb = update_site<POL, true>(cb, mb, u.runaway, f3b, nullptr);
+                        float f3a[3], f3b[3];
+                        ra = update_site_f3<POL>(ca, ma, u.runaway, f3a);
+                        rb = update_site_f3<POL>(cb, mb, u.runaway, f3b);
                         if (out_lane) {
-                            acc_owned(u, xa, q, t + k, f3a);
-                            if (two) acc_owned(u, xb, q, t + k, f3b);
+                            if constexpr (STAGE) {
+                                stage_owned(u.stage, slots[k].x, k, f3a);
+                                if (two) stage_owned(u.stage, slots[k].y, k, f3b);
+                            } else {
+                                acc_owned(u, slots[k].x, phase[k], f3a);
+                                if (two) acc_owned(u, slots[k].y, phase[k], f3b);
+                            }
                         }
                     } else {
                         ra = update_site<POL, true>(ca, ma, u.runaway, nullptr, nullptr);
@@ -606,9 +675,10 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
 
 
 // F16: the FP16-deviation form (TM; MIX: rebuilt with the mixed-precision FMA); otherwise FP32
-// of either polarization.  One work unit per warp: strip unit % n_strips, row segment unit /
-// n_strips.
-template <bool F16, int POL, bool MIX>
+// of either polarization, with ACC the FP32 fields of every level at the contour's stencil sites
+// into the staging buffer (the general row loop; k_stage_flush adds them to the Fourier sums).  One work unit per
+// warp: strip unit % n_strips, row segment unit / n_strips.
+template <bool F16, int POL, bool MIX, bool ACC>
 __global__ void __launch_bounds__(NW * 32, 3)
     k_step4_stream(const __grid_constant__ UnitCtx u, const StreamArgs a, const __grid_constant__ CUtensorMap smap,
                    const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap imap,
@@ -648,7 +718,7 @@ __global__ void __launch_bounds__(NW * 32, 3)
     r.src_inc = sp.inc;
     RingState R{ring, bars[warp], reinterpret_cast<float4 *>(ring + RING * LY::SLOT), 0, 0u};
     bool bad = false;
-    const bool ok = stream_unit<F16, POL, false, true, MIX>(u, r, R, bad);
+    const bool ok = stream_unit<F16, POL, ACC, !ACC, MIX, ACC>(u, r, R, bad);
     if (lane == 0 && !ok) atomicOr(a.err, kErrTimeout);
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrUnstable);
 }
@@ -748,9 +818,34 @@ __global__ void k_batch_source4(const SourceParams *__restrict__ src, int n, con
     if (i < n) out[i] = source_levels_f(src[i], *t_in);
 }
 
-template <bool F16, int POL, bool MIX>
+// After an accumulating launch from time *t_in: adds every stencil slot's staged FP32 fields of
+// the launch's four levels to its Fourier sums (Sec. III), in time order, exactly as the
+// one-step kernel adds them step by step.
+__global__ void k_stage_flush(const float *__restrict__ stage, double *__restrict__ acc, int n_slots,
+                              const double2 *__restrict__ cs, int period, const long long *__restrict__ t_in) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_slots) return;
+    const long long t = *t_in;
+    const float *s = stage + 12 * (size_t)i;
+    double *a = acc + 6 * (size_t)i;
+    double a0 = a[0], a1 = a[1], a2 = a[2], a3 = a[3], a4 = a[4], a5 = a[5];
+#pragma unroll
+    for (int k = 0; k < BT; ++k) {
+        const double2 c = cs[(int)((t + k) % (long long)period)];
+        const double f0 = (double)s[3 * k], f1 = (double)s[3 * k + 1], f2 = (double)s[3 * k + 2];
+        a0 += f0 * c.x;
+        a1 += f0 * c.y;
+        a2 += f1 * c.x;
+        a3 += f1 * c.y;
+        a4 += f2 * c.x;
+        a5 += f2 * c.y;
+    }
+    a[0] = a0, a[1] = a1, a[2] = a2, a[3] = a3, a[4] = a4, a[5] = a5;
+}
+
+template <bool F16, int POL, bool MIX, bool ACC>
 cudaError_t allow_smem_stream() {
-    return cudaFuncSetAttribute(k_step4_stream<F16, POL, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_step4_stream<F16, POL, MIX, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Layout<F16>::SMEM);
 }
 
@@ -785,20 +880,28 @@ StreamPlan stream_plan(int nx, int ny, int resident_warps, bool f16) {
     return p;
 }
 
-cudaError_t stream_prepare(bool f16, int *resident_warps) {
-    cudaError_t e = f16 ? allow_smem_stream<true, POL_TM, false>() : allow_smem_stream<false, POL_TM, false>();
-    if (e == cudaSuccess && f16) e = allow_smem_stream<true, POL_TM, true>();
-    if (e == cudaSuccess && !f16) e = allow_smem_stream<false, POL_TE, false>();
-    int dev = 0, sms = 0, per_sm = 0;
+cudaError_t stream_prepare(bool f16, int *resident_warps, int *resident_warps_acc) {
+    cudaError_t e = f16 ? allow_smem_stream<true, POL_TM, false, false>() : allow_smem_stream<false, POL_TM, false, false>();
+    if (e == cudaSuccess && f16) e = allow_smem_stream<true, POL_TM, true, false>();
+    if (e == cudaSuccess && !f16) e = allow_smem_stream<false, POL_TE, false, false>();
+    if (e == cudaSuccess && !f16) e = allow_smem_stream<false, POL_TM, false, true>();
+    if (e == cudaSuccess && !f16) e = allow_smem_stream<false, POL_TE, false, true>();
+    int dev = 0, sms = 0, per_sm = 0, per_sm_acc = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = f16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step4_stream<true, POL_TM, true>,
+        e = f16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step4_stream<true, POL_TM, true, false>,
                                                                 NW * 32, Layout<true>::SMEM)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step4_stream<false, POL_TM, false>,
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step4_stream<false, POL_TM, false, false>,
                                                                 NW * 32, Layout<false>::SMEM);
-    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
-    if (e == cudaSuccess) *resident_warps = per_sm * sms * NW;
+    if (e == cudaSuccess && !f16)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_acc, k_step4_stream<false, POL_TM, false, true>,
+                                                          NW * 32, Layout<false>::SMEM);
+    if (e == cudaSuccess && (per_sm < 1 || (!f16 && per_sm_acc < 1))) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess) {
+        *resident_warps = per_sm * sms * NW;
+        *resident_warps_acc = per_sm_acc * sms * NW;
+    }
     return e;
 }
 
@@ -884,7 +987,10 @@ cudaError_t launch_batch_step4(const StreamInst *insts, const SourceParams *srcp
 
 cudaError_t launch_step4_stream(const StepArgs<float> &sa, const F16Args *fa, const CUtensorMap *smap,
                                 const CUtensorMap *fmap, const CUtensorMap *imap, float *fout, const StreamPlan &plan,
-                                const long long *t_in, long long *t_out, cudaStream_t s) {
+                                const long long *t_in, long long *t_out, bool accumulate, float *stage, int n_slots,
+                                cudaStream_t s) {
+    // the FP16-deviation kernel does not accumulate; the accumulating one needs the staging buffer
+    if (accumulate && (fa || (!stage && n_slots > 0))) return cudaErrorInvalidValue;
     StreamArgs a{};
     a.nx = sa.nx;
     a.ny = sa.ny;
@@ -906,6 +1012,17 @@ cudaError_t launch_step4_stream(const StepArgs<float> &sa, const F16Args *fa, co
     u.runaway = sa.runaway;
     u.pstride = sa.pstride;
     u.fout = fout;
+    if (accumulate) {  // every level of the launch, at the contour's stencil rows
+        u.acc_from = 0;
+        u.steps = LLONG_MAX;
+        u.ay0 = sa.accp.y0;
+        u.ay1 = sa.accp.y1;
+        u.slot = sa.accp.slot;
+        u.acc = sa.accp.acc;
+        u.cs = sa.src.cs;
+        u.period = sa.src.period;
+        u.stage = stage;
+    }
     if (fa) {
         a.scale = u.scale = fa->scale;
         a.inv_scale = u.inv_scale = fa->inv_scale;
@@ -917,19 +1034,30 @@ cudaError_t launch_step4_stream(const StepArgs<float> &sa, const F16Args *fa, co
         const int m = std::ilogb(fa->inv_scale);
         if (m >= -24 && m <= 15) {
             u.nis = f16_neg_pow2_bits(m);
-            k_step4_stream<true, POL_TM, true>
+            k_step4_stream<true, POL_TM, true, false>
                 <<<plan.grid, NW * 32, Layout<true>::SMEM, s>>>(u, a, *smap, *fmap, *imap, t_in, t_out);
         } else {
-            k_step4_stream<true, POL_TM, false>
+            k_step4_stream<true, POL_TM, false, false>
                 <<<plan.grid, NW * 32, Layout<true>::SMEM, s>>>(u, a, *smap, *fmap, *imap, t_in, t_out);
         }
     } else if (sa.pol == POL_TE) {
-        k_step4_stream<false, POL_TE, false>
-            <<<plan.grid, NW * 32, Layout<false>::SMEM, s>>>(u, a, *smap, *smap, *imap, t_in, t_out);
+        if (accumulate)
+            k_step4_stream<false, POL_TE, false, true>
+                <<<plan.grid, NW * 32, Layout<false>::SMEM, s>>>(u, a, *smap, *smap, *imap, t_in, t_out);
+        else
+            k_step4_stream<false, POL_TE, false, false>
+                <<<plan.grid, NW * 32, Layout<false>::SMEM, s>>>(u, a, *smap, *smap, *imap, t_in, t_out);
     } else {
-        k_step4_stream<false, POL_TM, false>
-            <<<plan.grid, NW * 32, Layout<false>::SMEM, s>>>(u, a, *smap, *smap, *imap, t_in, t_out);
+        if (accumulate)
+            k_step4_stream<false, POL_TM, false, true>
+                <<<plan.grid, NW * 32, Layout<false>::SMEM, s>>>(u, a, *smap, *smap, *imap, t_in, t_out);
+        else
+            k_step4_stream<false, POL_TM, false, false>
+                <<<plan.grid, NW * 32, Layout<false>::SMEM, s>>>(u, a, *smap, *smap, *imap, t_in, t_out);
     }
+    if (accumulate && n_slots > 0)
+        k_stage_flush<<<(n_slots + 127) / 128, 128, 0, s>>>(stage, sa.accp.acc, n_slots, sa.src.cs, sa.src.period,
+                                                            t_in);
     return cudaGetLastError();
 }
 

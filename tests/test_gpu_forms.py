@@ -225,6 +225,33 @@ def test_three_steps_per_launch_is_bit_identical(inst, pol):
         assert np.array_equal(a.force_torque(c), b.force_torque(c))
 
 
+@pytest.mark.parametrize("pol", ["tm", "te"])
+@pytest.mark.parametrize("inst", W.small_cases()[:3], ids=lambda i: f"{i['nx']}x{i['ny']}")
+def test_four_steps_per_launch_accumulates_bit_identically(inst, pol):
+    """Four steps per launch (FP32) takes the Fourier sums of the accumulated period inside the
+    launch's time levels (its accumulating kernel): fields, the phasors at every stencil site and
+    the forces equal one step per launch bit for bit, through graphs of 32 steps, remainders of
+    every residue modulo 4, and an accumulated period that starts at an odd time."""
+    with L.solver_for_instance(inst, "f32", steps_per_launch="four", polarization=pol) as a, \
+            L.solver_for_instance(inst, "f32", steps_per_launch="one", polarization=pol) as b:
+        assert a.steps_per_launch() == 4
+        for n in (1, 4, 2, 32, 35, 64, 3):
+            a.step(n)
+            b.step(n)
+            for x, y in zip(a.fields(), b.fields()):
+                assert np.array_equal(x, y)
+        c = L.make_contour(inst["R"], inst["a"])
+        for extra in (0, 1):  # a second period from an odd start
+            a.step(extra)
+            b.step(extra)
+            assert np.array_equal(a.force_torque(c), b.force_torque(c))
+            (xa, pa), (xb, pb) = a.phasors(), b.phasors()
+            assert np.array_equal(xa, xb) and np.array_equal(pa, pb)
+            assert np.abs(pa).max() > 0
+        for x, y in zip(a.fields(), b.fields()):
+            assert np.array_equal(x, y)
+
+
 def test_f16dev_split_runs_agree_bitwise():
     """The FP16-deviation form gives the same bits however a run is split into calls."""
     inst = W.small_cases()[2]
