@@ -513,6 +513,8 @@ struct lbm_em_batch {
     SourceParams *d_srcp = nullptr;
     SrcLevels *d_srcs4 = nullptr;
     CUtensorMap *d_smaps4 = nullptr;
+    float *d_stage4 = nullptr;  // staged stencil fields of the accumulating launches (12 per slot)
+    int *d_slot_inst = nullptr; // each accumulator slot's instance
     int want_spl = 0;  // lbm_em_batch_opts.steps_per_launch
     cudaGraphExec_t graph = nullptr;
     bool ran = false;
@@ -555,6 +557,8 @@ static void batch_free(lbm_em_batch *b) {
     dfree(b->d_srcp);
     dfree(b->d_srcs4);
     dfree(b->d_smaps4);
+    dfree(b->d_stage4);
+    dfree(b->d_slot_inst);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -709,8 +713,9 @@ static cudaError_t batch_launch(lbm_em_batch *b, cudaStream_t s, int p) {
                            b->d_acc, b->d_err, b->d_energy, b->conv_tol > 0.0};
         if (b->four) {
             launch_batch_step4(b->d_sinsts, b->d_srcp, b->n, b->d_units, b->n_units, b->d_srcs4, b->d_smaps4, p,
-                               (float *)b->buf[1 - p], b->d_slot, b->d_acc, b->d_err, b->d_time + p,
-                               b->d_time + (1 - p), b->four_blocks, b->pol, s);
+                               (float *)b->buf[1 - p], b->d_slot, b->d_acc, b->d_stage4, b->d_slot_inst,
+                               (int)b->acc_slots, b->d_err, b->d_time + p, b->d_time + (1 - p), b->four_blocks,
+                               b->pol, s);
         } else if (b->two) {
             k_batch_source<<<(b->n + 127) / 128, 128, 0, s>>>(b->d_desc, b->n, b->d_time + p, b->d_srcs);
             if (b->pol == POL_TE)
@@ -1102,6 +1107,20 @@ lbm_em_status lbm_em_batch_create(const lbm_em_instance *specs, int32_t n, const
             BTRY(copy_async(b->d_srcp, sp.data(), sp.size() * sizeof(SourceParams), cudaMemcpyHostToDevice, b->stream),
                  "upload");
             BTRY(dmalloc(&b->d_srcs4, (size_t)n * sizeof(SrcLevels)), "cudaMalloc(source values)");
+            // the accumulating launches' staged fields (12 floats per stencil slot) and each
+            // slot's instance, for the flush that adds them to the Fourier sums
+            if (accs > 0) {
+                std::vector<int> owner(accs);
+                for (int i = 0; i < n; ++i) {
+                    const size_t end = i + 1 < n ? (size_t)b->desc[i + 1].acc_base : accs;
+                    for (size_t q = (size_t)b->desc[i].acc_base; q < end; ++q) owner[q] = i;
+                }
+                BTRY(dmalloc(&b->d_stage4, accs * 12 * sizeof(float)), "cudaMalloc(accumulation stage)");
+                BTRY(dmalloc(&b->d_slot_inst, accs * sizeof(int)), "cudaMalloc(slot instances)");
+                BTRY(copy_async(b->d_slot_inst, owner.data(), accs * sizeof(int), cudaMemcpyHostToDevice, b->stream),
+                     "upload");
+                BTRY(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");  // pageable source
+            }
         }
     }
     // rasterise every instance on the device (again at every run)

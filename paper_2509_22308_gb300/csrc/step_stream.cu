@@ -272,7 +272,7 @@ struct UnitCtx {
     const int *slot;                              // the lattice's slot map (pitch layout)
     double *acc;                                  // its accumulators (6 per slot)
     const double2 *cs;                            // (cos w t, sin w t) for t mod period
-    float *stage;                                 // STAGE: 12 FP32 fields per slot (see stream_unit)
+    float *stage;                                 // ACC: 12 staged FP32 fields per slot (see stream_unit)
 };
 
 // One work unit: a strip of the lattice (columns xs .. xs + 63, 16-byte aligned) and a segment
@@ -298,9 +298,7 @@ struct RingState {
 };
 
 // update_site<POL, true> (common.cuh) with the fields that enter the Fourier sums returned in
-// FP32: f3 holds the values update_site converts to FP64.  Converting only at the contour's
-// stencil sites (acc_owned) keeps FP64 conversions, slow on GB300's FP64 pipe, off the other
-// sites of the stencil rows.
+// FP32: f3 holds the values update_site converts to FP64 (the flush kernels convert them).
 template <int POL>
 __device__ __forceinline__ bool update_site_f3(Pop<float> &p, const MatT<float> &m, unsigned rthr, float f3[3]) {
     bool bad;
@@ -324,22 +322,9 @@ __device__ __forceinline__ bool update_site_f3(Pop<float> &p, const MatT<float> 
     return bad;
 }
 
-// Adds the phasor terms of one owned site (Sec. III: Fourier analysis over one period) to its
-// accumulators, when the site is a contour stencil site (its slot sl >= 0); c = (cos, sin) of
-// the site's time.
-__device__ __forceinline__ void acc_owned(const UnitCtx &u, int sl, double2 c, const float f3f[3]) {
-    if (sl < 0) return;
-    const double f3[3] = {(double)f3f[0], (double)f3f[1], (double)f3f[2]};
-    double *a = u.acc + 6 * (size_t)sl;
-    a[0] += f3[0] * c.x;
-    a[1] += f3[0] * c.y;
-    a[2] += f3[1] * c.x;
-    a[3] += f3[1] * c.y;
-    a[4] += f3[2] * c.x;
-    a[5] += f3[2] * c.y;
-}
-
-// STAGE: the FP32 fields of one owned stencil site (slot sl >= 0) at level k of the launch.
+// ACC: the FP32 fields of one owned stencil site (slot sl >= 0) at level k of the launch, into
+// the staging buffer that a flush kernel adds to the site's Fourier sums (Sec. III: Fourier
+// analysis over one period) after the launch.
 __device__ __forceinline__ void stage_owned(float *stage, int sl, int k, const float f3f[3]) {
     if (sl < 0) return;
     float *s = stage + 12 * (size_t)sl + 3 * k;
@@ -350,14 +335,13 @@ __device__ __forceinline__ void stage_owned(float *stage, int sl, int k, const f
 
 // Four steps of one work unit (see the top of this file).  Returns false after a bounded wait
 // for a row copy gave up.  bad: set when a stored site's field ran away.  SPLIT: the
-// steady-state rows take the copies of the row loop without the general loop's tests.  ACC
-// with STAGE: instead of adding each stencil site's Fourier terms to its FP64 sums, store its
-// FP32 fields at level k to stage[12 slot + 3 k ..] for k_stage_flush, which adds them after the
-// launch in the same order (every level of the launch accumulates; the single domain).  The
-// direct adds cost a few FP64 instructions per stencil site, which on GB300's FP64 pipe made
-// the units along the contour's vertical tangents (a stencil site in every row) the launch's
-// long tail.
-template <bool F16, int POL, bool ACC, bool SPLIT, bool MIX = false, bool STAGE = false>
+// steady-state rows take the copies of the row loop without the general loop's tests.  ACC:
+// instead of adding each stencil site's Fourier terms to its FP64 sums, store its FP32 fields at
+// level k to stage[12 slot + 3 k ..] (u.stage); a flush kernel adds them after the launch in the
+// same order and arithmetic as one step per launch.  Adding them here cost a few FP64
+// instructions per stencil site, which on GB300's FP64 pipe made the units along the contour's
+// vertical tangents (a stencil site in every row) the launch's long tail.
+template <bool F16, int POL, bool ACC, bool SPLIT, bool MIX = false>
 __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, RingState &R, bool &bad) {
     static_assert(!(F16 && ACC), "the FP16-deviation kernel does not accumulate");
     // the steady-state copies treat every computed row as owned, which holds for the stored level
@@ -393,13 +377,6 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
             const int sj = (s0 + j) % RING;
             issue_row<F16>(r.smap, r.fmap, r.imap, xs, xid, ylo + j, ring + (size_t)sj * LY::SLOT, &bars[sj]);
         }
-
-    // ACC: (cos, sin) of the launch's four times, the phases of the levels' Fourier terms
-    double2 phase[BT];
-    if constexpr (ACC && !STAGE) {
-#pragma unroll
-        for (int k = 0; k < BT; ++k) phase[k] = u.cs[(int)((t + k) % (long long)u.period)];
-    }
 
     Wave wa;
 #pragma unroll
@@ -561,13 +538,8 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
                         ra = update_site_f3<POL>(ca, ma, u.runaway, f3a);
                         rb = update_site_f3<POL>(cb, mb, u.runaway, f3b);
                         if (out_lane) {
-                            if constexpr (STAGE) {
-                                stage_owned(u.stage, slots[k].x, k, f3a);
-                                if (two) stage_owned(u.stage, slots[k].y, k, f3b);
-                            } else {
-                                acc_owned(u, slots[k].x, phase[k], f3a);
-                                if (two) acc_owned(u, slots[k].y, phase[k], f3b);
-                            }
+                            stage_owned(u.stage, slots[k].x, k, f3a);
+                            if (two) stage_owned(u.stage, slots[k].y, k, f3b);
                         }
                     } else {
                         ra = update_site<POL, true>(ca, ma, u.runaway, nullptr, nullptr);
@@ -718,7 +690,7 @@ __global__ void __launch_bounds__(NW * 32, 3)
     r.src_inc = sp.inc;
     RingState R{ring, bars[warp], reinterpret_cast<float4 *>(ring + RING * LY::SLOT), 0, 0u};
     bool bad = false;
-    const bool ok = stream_unit<F16, POL, ACC, !ACC, MIX, ACC>(u, r, R, bad);
+    const bool ok = stream_unit<F16, POL, ACC, !ACC, MIX>(u, r, R, bad);
     if (lane == 0 && !ok) atomicOr(a.err, kErrTimeout);
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrUnstable);
 }
@@ -729,17 +701,15 @@ __global__ void __launch_bounds__(NW * 32, 3)
 // unit, so each warp normally takes one.  Two instantiations run one after the other in
 // every launch and split the unfinished instances between them: ACC = false takes those with
 // no time of their accumulated (last) period among the launch's four, ACC = true the others,
-// whose Fourier sums it adds inside the levels whose time falls in that period.  (One kernel
-// doing both spilled: the accumulation's FP64 registers on top of the wavefront's.)  ACC = true
-// runs 2 blocks per SM, so that those registers fit without spilling (256-instance design map
-// 129.3 -> 131.5 cells/s against 3 blocks with 306 bytes spilled), and the general row loop.  An
-// instance that ends inside a launch runs on past its end without accumulating; its state is
-// not needed afterwards.  FP32.
+// whose stencil sites' fields it stages for the levels whose time falls in that period
+// (k_batch_flush4 adds them to the Fourier sums after it; ACC = true takes the general row
+// loop).  An instance that ends inside a launch runs on past its end without accumulating; its
+// state is not needed afterwards.  FP32.
 template <int POL, bool ACC>
-__global__ void __launch_bounds__(NW * 32, ACC ? 2 : 3)
+__global__ void __launch_bounds__(NW * 32, 3)
     k_batch_step4(const StreamInst *__restrict__ insts, const int4 *__restrict__ units, int n_units,
                   const SrcLevels *__restrict__ srcs, const CUtensorMap *__restrict__ maps, int p,
-                  float *__restrict__ buf_out, const int *__restrict__ slot, double *__restrict__ acc,
+                  float *__restrict__ buf_out, const int *__restrict__ slot, float *__restrict__ stage,
                   unsigned *__restrict__ err, const long long *__restrict__ t_in, long long *__restrict__ t_out) {
     using LY = Layout<false>;
     constexpr int RING = LY::RING;
@@ -782,7 +752,7 @@ __global__ void __launch_bounds__(NW * 32, ACC ? 2 : 3)
             u.acc_from = I.acc_from;
             u.steps = steps;
             u.slot = slot + I.slot_base;
-            u.acc = acc + 6 * (size_t)I.acc_base;
+            u.stage = stage + 12 * (size_t)I.acc_base;
             u.cs = I.cs;
         }
         UnitRun &r = urun[warp];
@@ -832,6 +802,37 @@ __global__ void k_stage_flush(const float *__restrict__ stage, double *__restric
 #pragma unroll
     for (int k = 0; k < BT; ++k) {
         const double2 c = cs[(int)((t + k) % (long long)period)];
+        const double f0 = (double)s[3 * k], f1 = (double)s[3 * k + 1], f2 = (double)s[3 * k + 2];
+        a0 += f0 * c.x;
+        a1 += f0 * c.y;
+        a2 += f1 * c.x;
+        a3 += f1 * c.y;
+        a4 += f2 * c.x;
+        a5 += f2 * c.y;
+    }
+    a[0] = a0, a[1] = a1, a[2] = a2, a[3] = a3, a[4] = a4, a[5] = a5;
+}
+
+// The batch's flush after each four-step launch from time *t_in: every stencil slot of the packed
+// accumulators (slot_inst: its instance) adds the staged fields of the levels whose time lies
+// in its instance's accumulated period, in time order; the same test selects the levels the
+// accumulating kernel staged.
+__global__ void k_batch_flush4(const float *__restrict__ stage, double *__restrict__ acc,
+                               const int *__restrict__ slot_inst, const StreamInst *__restrict__ insts, int n_slots,
+                               const long long *__restrict__ t_in) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_slots) return;
+    const long long t = *t_in;
+    const StreamInst &I = insts[slot_inst[i]];
+    if (t + BT - 1 < I.acc_from || t >= I.steps) return;
+    const float *s = stage + 12 * (size_t)i;
+    double *a = acc + 6 * (size_t)i;
+    double a0 = a[0], a1 = a[1], a2 = a[2], a3 = a[3], a4 = a[4], a5 = a[5];
+#pragma unroll
+    for (int k = 0; k < BT; ++k) {
+        const long long tk = t + k;
+        if (tk < I.acc_from || tk >= I.steps) continue;
+        const double2 c = I.cs[(int)(tk % (long long)I.period)];
         const double f0 = (double)s[3 * k], f1 = (double)s[3 * k + 1], f2 = (double)s[3 * k + 2];
         a0 += f0 * c.x;
         a1 += f0 * c.y;
@@ -966,22 +967,25 @@ cudaError_t encode_batch_stream_maps(CUtensorMap *maps, const float *buf0, const
 
 cudaError_t launch_batch_step4(const StreamInst *insts, const SourceParams *srcp, int n_inst, const int4 *units,
                                int n_units, SrcLevels *srcs, const CUtensorMap *maps, int p, float *buf_out,
-                               const int *slot, double *acc, unsigned *err, const long long *t_in,
-                               long long *t_out, int grid, int pol, cudaStream_t s) {
+                               const int *slot, double *acc, float *stage, const int *slot_inst, int n_slots,
+                               unsigned *err, const long long *t_in, long long *t_out, int grid, int pol,
+                               cudaStream_t s) {
     k_batch_source4<<<(n_inst + 127) / 128, 128, 0, s>>>(srcp, n_inst, t_in, srcs);
     const size_t sm = Layout<false>::SMEM;
     // both write t + 4 to t_out; neither reads it
     if (pol == POL_TE) {
         k_batch_step4<POL_TE, false><<<grid, NW * 32, sm, s>>>(insts, units, n_units, srcs, maps, p, buf_out, slot,
-                                                              acc, err, t_in, t_out);
+                                                              stage, err, t_in, t_out);
         k_batch_step4<POL_TE, true><<<grid, NW * 32, sm, s>>>(insts, units, n_units, srcs, maps, p, buf_out, slot,
-                                                             acc, err, t_in, t_out);
+                                                             stage, err, t_in, t_out);
     } else {
         k_batch_step4<POL_TM, false><<<grid, NW * 32, sm, s>>>(insts, units, n_units, srcs, maps, p, buf_out, slot,
-                                                              acc, err, t_in, t_out);
+                                                              stage, err, t_in, t_out);
         k_batch_step4<POL_TM, true><<<grid, NW * 32, sm, s>>>(insts, units, n_units, srcs, maps, p, buf_out, slot,
-                                                             acc, err, t_in, t_out);
+                                                             stage, err, t_in, t_out);
     }
+    if (n_slots > 0)
+        k_batch_flush4<<<(n_slots + 255) / 256, 256, 0, s>>>(stage, acc, slot_inst, insts, n_slots, t_in);
     return cudaGetLastError();
 }
 

@@ -64,11 +64,14 @@ cudaError_t encode_batch_stream_maps(CUtensorMap *maps, const float *buf0, const
 // Four steps of every unfinished instance: the source values of each instance at the launch's
 // four times into srcs (from srcp[n_inst]), then the kernel over units[n_units] (int4:
 // instance, strip, segment; walked with a stride of grid x kStreamWarps warps), input state
-// buffer p (maps[3 i + p]), output buf_out.
+// buffer p (maps[3 i + p]), output buf_out; the stencil sites of instances in their accumulated
+// period staged in stage (12 floats per slot of the packed accumulators acc[6 n_slots]) and
+// added to acc by a flush over the slots (slot_inst[n_slots]: each slot's instance).
 cudaError_t launch_batch_step4(const StreamInst *insts, const SourceParams *srcp, int n_inst, const int4 *units,
                                int n_units, SrcLevels *srcs, const CUtensorMap *maps, int p, float *buf_out,
-                               const int *slot, double *acc, unsigned *err, const long long *t_in,
-                               long long *t_out, int grid, int pol, cudaStream_t s);
+                               const int *slot, double *acc, float *stage, const int *slot_inst, int n_slots,
+                               unsigned *err, const long long *t_in, long long *t_out, int grid, int pol,
+                               cudaStream_t s);
 
 // Four steps: the state described by the maps (time word t_in) -> fout / the FP16-deviation
 // output planes of fa (t_out = t + 4).  FP32 of either polarization (a.pol), or the
