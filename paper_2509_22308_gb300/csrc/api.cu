@@ -243,7 +243,7 @@ struct lbm_em {
     ContourHost ch;
     int *d_slot = nullptr;
     double *d_acc = nullptr;
-    float *d_stage = nullptr;  // FP32 four-step accumulation: 12 staged fields per stencil slot
+    float *d_stage = nullptr;  // four-step accumulation: 12 staged fields per stencil slot
     ContourPt *d_pts = nullptr;
     double2 *d_inc = nullptr;   // incident E_z phasor at every stencil site (far field)
     double *d_out = nullptr;
@@ -372,23 +372,22 @@ static cudaError_t enqueue_step3(lbm_em *h, bool acc, cudaStream_t s, int p) {
                             h->d_time + (1 - p), acc, h->tma3_ctas, s);
 }
 
-// Four steps in one launch (FP32 with or without the Fourier accumulation, FP16-deviation
-// without): buf[p] -> buf[1 - p].
+// Four steps in one launch, with or without the Fourier accumulation: buf[p] -> buf[1 - p].
 static cudaError_t enqueue_step4(lbm_em *h, bool acc, cudaStream_t s, int p) {
     if (h->prec == LBM_EM_F16DEV) {
         const F16Args fa = make_f16_args(h, p);
         return launch_step4_stream(make_args<float>(h), &fa, &h->s4_smap[p], &h->s4_fmap[p], &h->s4_imap, nullptr,
-                                   h->s4_plan, h->d_time + p, h->d_time + (1 - p), false, nullptr, 0, s);
+                                   acc ? h->s4_plan_acc : h->s4_plan, h->d_time + p, h->d_time + (1 - p), acc,
+                                   h->d_stage, acc ? h->ch.n_slots : 0, s);
     }
     return launch_step4_stream(make_args<float>(h), nullptr, &h->s4_smap[p], &h->s4_fmap[p], &h->s4_imap,
                                (float *)h->buf[1 - p], acc ? h->s4_plan_acc : h->s4_plan, h->d_time + p,
                                h->d_time + (1 - p), acc, h->d_stage, acc ? h->ch.n_slots : 0, s);
 }
 
-// Steps one launch advances: the handle's mode; the FP16-deviation form's accumulating steps
-// (the Fourier period) use its two-step tile kernel where the four-step one is chosen.
+// Steps one launch advances: the handle's mode (accumulating steps too).
 static int launch_steps(const lbm_em *h, bool acc) {
-    if (h->s4) return acc && h->prec == LBM_EM_F16DEV ? 2 : 4;
+    if (h->s4) return 4;
     return h->t3 ? 3 : h->tb ? 2 : 1;
 }
 
@@ -568,7 +567,7 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     // 111.1, 512^2 34.6 / 70.4 / 70.3; FP16-deviation four / two: 8192^2 253.2 / 116.8, 2048^2
     // 166.5 / 106.9, 1448^2 147.1 / 100.2, 1024^2 107.0 / 99.8, 768^2 61.2 / 87.2, 512^2 31.0 /
     // 59.2: on small lattices the strips cannot fill the GPU and the two-step kernel's state
-    // stays in L2); FP16-deviation runs its accumulating periods on the two-step tile kernel
+    // stays in L2)
     h->s4 = (g->flags & LBM_EM_FLAG_FOUR_STEP) != 0 ||
             (!step_flags && (long long)g->nx * g->ny >= (g->precision == LBM_EM_F32      ? (1LL << 21)
                                                          : g->precision == LBM_EM_F16DEV ? (1LL << 20)
@@ -627,7 +626,7 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
         int warps = 0, warps_acc = 0;
         TRY(stream_prepare(h->prec == LBM_EM_F16DEV, &warps, &warps_acc), "configuring the four-step kernel");
         h->s4_plan = stream_plan(h->nx, h->ny, warps, h->prec == LBM_EM_F16DEV);
-        if (h->prec != LBM_EM_F16DEV) h->s4_plan_acc = stream_plan(h->nx, h->ny, warps_acc, false);
+        h->s4_plan_acc = stream_plan(h->nx, h->ny, warps_acc, h->prec == LBM_EM_F16DEV);
         for (int b = 0; b < 2; ++b)
             TRY(encode_stream_maps(&h->s4_smap[b], &h->s4_fmap[b], b == 0 ? &h->s4_imap : nullptr, h->buf[b],
                                    h->prec == LBM_EM_F16DEV, h->d_mat, h->nx, h->ny, h->pitch, h->pstride),
@@ -904,7 +903,7 @@ lbm_em_status lbm_em_set_contour(lbm_em_t *h, const lbm_em_contour *c) {
     if (!st) st = cuda_status(dev_alloc(h, &h->d_acc, (size_t)ch.n_slots * 6 * sizeof(double)), "allocating acc");
     if (!st) st = cuda_status(dev_alloc(h, &h->d_pts, b_pts), "allocating the contour");
     if (!st) st = cuda_status(dev_alloc(h, &h->d_inc, b_inc), "allocating the incident table");
-    if (!st && h->s4 && h->prec != LBM_EM_F16DEV && ch.n_slots > 0)
+    if (!st && h->s4 && ch.n_slots > 0)
         st = cuda_status(dev_alloc(h, &h->d_stage, (size_t)ch.n_slots * 12 * sizeof(float)),
                          "allocating the accumulation stage");
     char *up = nullptr;

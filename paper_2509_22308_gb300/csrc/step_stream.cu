@@ -343,7 +343,6 @@ __device__ __forceinline__ void stage_owned(float *stage, int sl, int k, const f
 // vertical tangents (a stencil site in every row) the launch's long tail.
 template <bool F16, int POL, bool ACC, bool SPLIT, bool MIX = false>
 __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, RingState &R, bool &bad) {
-    static_assert(!(F16 && ACC), "the FP16-deviation kernel does not accumulate");
     // the steady-state copies treat every computed row as owned, which holds for the stored level
     // only: the Fourier sums of the levels before it would count halo rows twice
     static_assert(!(ACC && SPLIT), "accumulating units take the general row loop");
@@ -507,6 +506,13 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
                     float E3a, Hxa, Hya, Da, E3b, Hxb, Hyb, Db;
                     moments(ca, ma, &E3a, &Hxa, &Hya, &Da);
                     moments(cb, mb, &E3b, &Hxb, &Hyb, &Db);
+                    if constexpr (ACC) {  // the fields of the stored level, staged as at the others
+                        if (owned && t + k >= u.acc_from && t + k < u.steps && q >= u.ay0 && q <= u.ay1) {
+                            const float f3a[3] = {Da * ma.inv_eps, Hxa, Hya}, f3b[3] = {Db * mb.inv_eps, Hxb, Hyb};
+                            stage_owned(u.stage, slots[k].x, k, f3a);
+                            if (two) stage_owned(u.stage, slots[k].y, k, f3b);
+                        }
+                    }
                     if (store) {
                         bad |= field_runaway(E3a, u.runaway) || (two && field_runaway(E3b, u.runaway));
                         const Fld Fa = stored_fields(E3a, Hxa, Hya), Fb = stored_fields(E3b, Hxb, Hyb);
@@ -884,6 +890,8 @@ StreamPlan stream_plan(int nx, int ny, int resident_warps, bool f16) {
 cudaError_t stream_prepare(bool f16, int *resident_warps, int *resident_warps_acc) {
     cudaError_t e = f16 ? allow_smem_stream<true, POL_TM, false, false>() : allow_smem_stream<false, POL_TM, false, false>();
     if (e == cudaSuccess && f16) e = allow_smem_stream<true, POL_TM, true, false>();
+    if (e == cudaSuccess && f16) e = allow_smem_stream<true, POL_TM, true, true>();
+    if (e == cudaSuccess && f16) e = allow_smem_stream<true, POL_TM, false, true>();
     if (e == cudaSuccess && !f16) e = allow_smem_stream<false, POL_TE, false, false>();
     if (e == cudaSuccess && !f16) e = allow_smem_stream<false, POL_TM, false, true>();
     if (e == cudaSuccess && !f16) e = allow_smem_stream<false, POL_TE, false, true>();
@@ -895,10 +903,12 @@ cudaError_t stream_prepare(bool f16, int *resident_warps, int *resident_warps_ac
                                                                 NW * 32, Layout<true>::SMEM)
                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step4_stream<false, POL_TM, false, false>,
                                                                 NW * 32, Layout<false>::SMEM);
-    if (e == cudaSuccess && !f16)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_acc, k_step4_stream<false, POL_TM, false, true>,
-                                                          NW * 32, Layout<false>::SMEM);
-    if (e == cudaSuccess && (per_sm < 1 || (!f16 && per_sm_acc < 1))) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess)
+        e = f16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_acc, k_step4_stream<true, POL_TM, true, true>,
+                                                                NW * 32, Layout<true>::SMEM)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_acc, k_step4_stream<false, POL_TM, false, true>,
+                                                                NW * 32, Layout<false>::SMEM);
+    if (e == cudaSuccess && (per_sm < 1 || per_sm_acc < 1)) e = cudaErrorInvalidConfiguration;
     if (e == cudaSuccess) {
         *resident_warps = per_sm * sms * NW;
         *resident_warps_acc = per_sm_acc * sms * NW;
@@ -993,8 +1003,7 @@ cudaError_t launch_step4_stream(const StepArgs<float> &sa, const F16Args *fa, co
                                 const CUtensorMap *fmap, const CUtensorMap *imap, float *fout, const StreamPlan &plan,
                                 const long long *t_in, long long *t_out, bool accumulate, float *stage, int n_slots,
                                 cudaStream_t s) {
-    // the FP16-deviation kernel does not accumulate; the accumulating one needs the staging buffer
-    if (accumulate && (fa || (!stage && n_slots > 0))) return cudaErrorInvalidValue;
+    if (accumulate && !stage && n_slots > 0) return cudaErrorInvalidValue;  // needs the staging buffer
     StreamArgs a{};
     a.nx = sa.nx;
     a.ny = sa.ny;
@@ -1036,14 +1045,20 @@ cudaError_t launch_step4_stream(const StepArgs<float> &sa, const F16Args *fa, co
         a.fhy_out = u.fhy_out = fa->fhy_out;
         // -inv_scale = -2^m in FP16: exact from 2^-24 (subnormal below 2^-14) to 2^15
         const int m = std::ilogb(fa->inv_scale);
-        if (m >= -24 && m <= 15) {
-            u.nis = f16_neg_pow2_bits(m);
+        const bool mix = m >= -24 && m <= 15;
+        if (mix) u.nis = f16_neg_pow2_bits(m);
+        if (mix && accumulate)
+            k_step4_stream<true, POL_TM, true, true>
+                <<<plan.grid, NW * 32, Layout<true>::SMEM, s>>>(u, a, *smap, *fmap, *imap, t_in, t_out);
+        else if (mix)
             k_step4_stream<true, POL_TM, true, false>
                 <<<plan.grid, NW * 32, Layout<true>::SMEM, s>>>(u, a, *smap, *fmap, *imap, t_in, t_out);
-        } else {
+        else if (accumulate)
+            k_step4_stream<true, POL_TM, false, true>
+                <<<plan.grid, NW * 32, Layout<true>::SMEM, s>>>(u, a, *smap, *fmap, *imap, t_in, t_out);
+        else
             k_step4_stream<true, POL_TM, false, false>
                 <<<plan.grid, NW * 32, Layout<true>::SMEM, s>>>(u, a, *smap, *fmap, *imap, t_in, t_out);
-        }
     } else if (sa.pol == POL_TE) {
         if (accumulate)
             k_step4_stream<false, POL_TE, false, true>

@@ -23,7 +23,7 @@ StreamPlan stream_plan(int nx, int ny, int resident_warps, bool f16);
 
 // Once per device, outside stream capture: allows the kernels' shared memory and returns
 // the warps resident on the whole GPU (blocks per SM x SMs x kStreamWarps), of the plain kernel
-// and (FP32) of the accumulating one.
+// and of the accumulating one.
 cudaError_t stream_prepare(bool f16, int *resident_warps, int *resident_warps_acc);
 
 // Tensor maps of one state buffer: FP32 (smap: 11 planes, box 64 x 1 x 11 floats) or
@@ -75,9 +75,9 @@ cudaError_t launch_batch_step4(const StreamInst *insts, const SourceParams *srcp
 
 // Four steps: the state described by the maps (time word t_in) -> fout / the FP16-deviation
 // output planes of fa (t_out = t + 4).  FP32 of either polarization (a.pol), or the
-// FP16-deviation form (TM) when fa is not NULL.  accumulate (FP32 only): the Fourier sums of
-// the four times at the n_slots stencil sites of a.accp, with the phases a.src.cs, through the
-// staging buffer stage (12 floats per slot) and a second launch that adds it to a.accp.acc.
+// FP16-deviation form (TM) when fa is not NULL.  accumulate: the Fourier sums of the four times
+// at the n_slots stencil sites of a.accp, with the phases a.src.cs, through the staging buffer
+// stage (12 floats per slot) and a second launch that adds it to a.accp.acc.
 cudaError_t launch_step4_stream(const StepArgs<float> &a, const F16Args *fa, const CUtensorMap *smap,
                                 const CUtensorMap *fmap, const CUtensorMap *imap, float *fout, const StreamPlan &plan,
                                 const long long *t_in, long long *t_out, bool accumulate, float *stage, int n_slots,
