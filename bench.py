@@ -65,7 +65,7 @@ def parse_args():
     p.add_argument("--profile-case", action="store_true",
                    help="small case for ncu: two launches of each step kernel on a 2048^2 lattice and of the FP64 step on the 512^2 workload")
     p.add_argument("--profile-only", default="",
-                   help="with --profile-case: only these form:mode pairs and design maps (e.g. f32:four,f16dev:four,batch4)")
+                   help="with --profile-case: only these form:mode[:acc] items and design maps (e.g. f32:four,f32:four:acc,batch4)")
     p.add_argument("--profile-n", type=int, default=2048, help="with --profile-only: the lattice size")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true")
@@ -335,7 +335,8 @@ def profile_case(only="", n=2048):
     L2, a few GB on the device in total), two launches of the FP64 step on one 512^2
     instance of the benchmark workload, then a 24-instance FP32 design map with two steps per
     launch and the same map with four.  `only` picks some of them: "form:mode" pairs for the
-    lattice (of size n), "batch2" and "batch4" for the design maps."""
+    lattice (of size n; "form:mode:acc" then also accumulates one period on the contour R), "batch2"
+    and "batch4" for the design maps."""
     import torch
     from paper_2509_22308_gb300 import build as B
     B.build()
@@ -352,9 +353,11 @@ def profile_case(only="", n=2048):
         tokens = only.split(",")
         pairs = tuple(tuple(p.split(":")) for p in tokens if ":" in p)
         maps = tuple(p for p in tokens if ":" not in p)
-    for fp, mode in pairs:
+    for fp, mode, *acc in pairs:
         with L.solver_for_instance(inst, fp, steps_per_launch=mode) as s:
             s.step({"two": 4, "three": 6, "four": 8}.get(mode, 2))
+            if acc:
+                s.force_torque(L.make_contour(inst["R"], inst["a"]))
             s.sync()
     if not only:
         # two launches of the benchmark's own 512^2 FP64 instance (theta = 0)
