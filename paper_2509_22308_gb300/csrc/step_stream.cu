@@ -26,6 +26,12 @@
 // Each state element crosses HBM once per four steps: 89 B per four FP32 updates, 69 B per
 // four FP16-deviation updates, plus the 8 halo columns of every 56 that the neighbouring
 // strips also read (served by L2 when they run at about the same time).
+//
+// Accumulating launches (the Fourier sums of the last period, Sec. III) store the FP32 fields
+// of the contour's stencil sites at each level into a staging buffer; a one-thread-per-slot
+// flush adds them to the FP64 sums after the launch (k_stage_flush; k_batch_flush4 for the
+// batch, whose kernel k_batch_step4 runs the same work unit over the packed instances of a
+// design map).
 #include <cuda_fp16.h>
 
 #include <climits>
