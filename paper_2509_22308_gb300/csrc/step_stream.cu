@@ -619,8 +619,9 @@ __device__ __forceinline__ bool stream_unit(const UnitCtx &u, const UnitRun &r, 
     // Measured on GB300 (GLUPS on 8192^2 / 2048^2): FP32 with the general loop for every row
     // 240.1 / 180.3, with both copies 257.2 / 195.0; FP16-deviation with the interior copy only
     // (the edge strips, on the general loop, then finish last) 253.5 / 166.8, with both copies
-    // 263.4 / 187.2.  The batch kernel takes the copies where it does not accumulate (256-instance
-    // design map 116.6 -> 129.6 cells/s); with the accumulation they spill.  An L2
+    // 263.4 / 187.2.  Every kernel takes the copies except the accumulating ones (see the check at
+    // the top of this function); the batch's gain: 256-instance design map 116.6 -> 129.6 cells/s.
+    // An L2
     // prefetch of the rows beyond the ring (cp.async.bulk.prefetch.tensor) lost in both forms
     // (FP32 212.8 against 220.4, FP16 173.7 against 199.5, with one wave of units) and is not used.
     using General = std::integral_constant<int, 0>;
