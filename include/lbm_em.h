@@ -78,8 +78,8 @@ typedef enum {
 } lbm_em_source_kind;
 
 /* lbm_em_grid.flags: how many time steps one kernel launch advances.  By default FP64 and
- * double-float advance one step per launch; FP32 two below 2^21 sites and FP16-deviation two
- * below 2^20 (each tile and its halo are copied to shared memory by the TMA unit and advance two
+ * double-float advance one step per launch; FP32 and FP16-deviation two below 2^20 sites
+ * (each tile and its halo are copied to shared memory by the TMA unit and advance two
  * steps there), four from there on (each warp streams a strip of the lattice through four time
  * levels held in registers).  The flags force a mode.  In FP32, FP64 and double-float the
  * result does not depend on the choice: every mode gives the same bits.  In FP16-deviation the

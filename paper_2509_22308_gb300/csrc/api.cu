@@ -561,17 +561,16 @@ static lbm_em_status create_common(const lbm_em_grid *g, const lbm_em_source *s,
     // replaced it as the default on large lattices
     h->t3 = (g->flags & LBM_EM_FLAG_THREE_STEP) != 0;
     // four steps per launch (row-streaming kernel): forced by the flag, else the default of FP32
-    // from 2^21 sites and of FP16-deviation from 2^20 sites on (measured on GB300, GLUPS four /
-    // two / three steps per launch, FP32: 8192^2 240.0 / 136.8 / 143.9, 4096^2 214.4 / 138.0 /
-    // 140.5, 2048^2 179.8 / 122.4 / 126.1, 1448^2 159.7 / 114.3 / 122.0, 1024^2 116.3 / 124.0 /
-    // 111.1, 512^2 34.6 / 70.4 / 70.3; FP16-deviation four / two: 8192^2 253.2 / 116.8, 2048^2
-    // 166.5 / 106.9, 1448^2 147.1 / 100.2, 1024^2 107.0 / 99.8, 768^2 61.2 / 87.2, 512^2 31.0 /
-    // 59.2: on small lattices the strips cannot fill the GPU and the two-step kernel's state
-    // stays in L2)
+    // and FP16-deviation from 2^20 sites on (measured on GB300, GLUPS four / two steps per
+    // launch, FP32: 8192^2 267.9 / 136.8, 4096^2 241.5 / 138.0, 2048^2 193.1 / 122.4, 1448^2
+    // 184.4 / 114.3, 1024^2 135.0 / 117.4, 768^2 76.7 / 100.8, 512^2 34.6 / 70.4; FP16-deviation:
+    // 8192^2 277.7 / 116.8, 2048^2 197.7 / 106.9, 1448^2 171.3 / 100.2, 1024^2 127.8 / 99.2,
+    // 768^2 67.7 / 86.5, 512^2 31.0 / 59.2; three steps per launch never led: 8192^2 143.9,
+    // 1024^2 111.1: on small lattices the strips cannot fill the GPU and the two-step kernel's
+    // state stays in L2)
     h->s4 = (g->flags & LBM_EM_FLAG_FOUR_STEP) != 0 ||
-            (!step_flags && (long long)g->nx * g->ny >= (g->precision == LBM_EM_F32      ? (1LL << 21)
-                                                         : g->precision == LBM_EM_F16DEV ? (1LL << 20)
-                                                                                         : (1LL << 62)));
+            (!step_flags && (g->precision == LBM_EM_F32 || g->precision == LBM_EM_F16DEV) &&
+             (long long)g->nx * g->ny >= (1LL << 20));
     if (h->s4) {
         h->t3 = false;
         h->tb = true;
